@@ -1,0 +1,90 @@
+"""The learned initial-guess network in FP64 (oracle).
+
+Per atom, rotation-invariant features f_i (the permanent field and the fields at its
+frame atoms, expressed in the atom's local frame, plus its polarizability and kind)
+pass through a two-hidden-layer perceptron
+    h1 = relu(f W1 + b1),  h2 = relu(h1 W2 + b2),  y = h2 W3 + b3,
+and the guess is mu0_i = alpha_i E_i + s_out R_i y_i (R_i the atom's frame). Training
+minimises L = (1 / 2B) sum_i |y_i - t_i|^2 over a batch of B atoms, with t_i the
+converged dipole's correction to alpha_i E_i in the local frame, divided by s_out.
+Adam updates follow Kingma & Ba (2015).
+"""
+import numpy as np
+
+from . import frames
+
+N_FEAT = 16
+E_SCALE = 0.05      # typical permanent-field magnitude, e/A^2
+OUT_SCALE = 0.02    # typical correction magnitude, e*A
+
+
+def features(xyz, box, frame, alpha, E):
+    """Feature matrix [N, 16]: e_i (3), e at the z-atom (3) and x-atom (3) in i's frame,
+    |e_i|, alpha_i, one-hot kind (global / z-then-x / bisector), 1, 0; e = E / E_SCALE."""
+    n = xyz.shape[0]
+    rot = frames.frame_matrices(xyz, box, frame)
+    e = E / E_SCALE
+    loc = np.einsum("nba,nb->na", rot, e)
+    fz = np.where(frame[:, 1] >= 0, frame[:, 1], np.arange(n))
+    fx = np.where(frame[:, 2] >= 0, frame[:, 2], np.arange(n))
+    has = (frame[:, 0] != 0)[:, None]
+    ez = np.where(has, np.einsum("nba,nb->na", rot, e[fz]), 0.0)
+    ex = np.where(has, np.einsum("nba,nb->na", rot, e[fx]), 0.0)
+    kind = np.eye(3)[frame[:, 0]]
+    return np.concatenate([loc, ez, ex, np.linalg.norm(e, axis=1, keepdims=True), alpha[:, None],
+                           kind, np.ones((n, 1)), np.zeros((n, 1))], axis=1), rot
+
+
+def forward(params, X):
+    W1, b1, W2, b2, W3, b3 = params
+    Z1 = X @ W1 + b1
+    H1 = np.maximum(Z1, 0.0)
+    Z2 = H1 @ W2 + b2
+    H2 = np.maximum(Z2, 0.0)
+    Y = H2 @ W3 + b3
+    return Y, (X, Z1, H1, Z2, H2)
+
+
+def loss_and_grads(params, X, T):
+    """L = (1/2B) sum |Y - T|^2 and its gradients w.r.t. (W1, b1, W2, b2, W3, b3)."""
+    W1, b1, W2, b2, W3, b3 = params
+    Y, (X, Z1, H1, Z2, H2) = forward(params, X)
+    B = X.shape[0]
+    dY = (Y - T) / B
+    L = 0.5 * np.sum((Y - T) ** 2) / B
+    dW3 = H2.T @ dY
+    db3 = dY.sum(0)
+    dZ2 = (dY @ W3.T) * (Z2 > 0)
+    dW2 = H1.T @ dZ2
+    db2 = dZ2.sum(0)
+    dZ1 = (dZ2 @ W2.T) * (Z1 > 0)
+    dW1 = X.T @ dZ1
+    db1 = dZ1.sum(0)
+    return L, (dW1, db1, dW2, db2, dW3, db3)
+
+
+def adam_step(params, grads, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (t counts from 1); returns new params, m, v."""
+    out_p, out_m, out_v = [], [], []
+    for p, g, mm, vv in zip(params, grads, m, v):
+        mm = b1 * mm + (1 - b1) * g
+        vv = b2 * vv + (1 - b2) * g * g
+        mh = mm / (1 - b1 ** t)
+        vh = vv / (1 - b2 ** t)
+        out_p.append(p - lr * mh / (np.sqrt(vh) + eps))
+        out_m.append(mm)
+        out_v.append(vv)
+    return out_p, out_m, out_v
+
+
+def guess(params, xyz, box, frame, alpha, E):
+    """mu0 = alpha E + OUT_SCALE * R y."""
+    X, rot = features(xyz, box, frame, alpha, E)
+    Y, _ = forward(params, X)
+    return alpha[:, None] * E + OUT_SCALE * np.einsum("nab,nb->na", rot, Y)
+
+
+def targets(xyz, box, frame, alpha, E, mu):
+    """Local-frame correction t = R^T (mu - alpha E) / OUT_SCALE."""
+    rot = frames.frame_matrices(xyz, box, frame)
+    return np.einsum("nba,nb->na", rot, mu - alpha[:, None] * E) / OUT_SCALE

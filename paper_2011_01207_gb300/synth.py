@@ -1,0 +1,290 @@
+"""Seeded synthetic inputs for the polarization solve.
+
+Rigid-water boxes, a random-walk chain solvated in water, and small rigid-body moves
+that stand in for MD steps. The paper's benchmark systems (water boxes from 648 atoms
+up, DHFR at 23,558 atoms, STMV at ~1.07 M atoms; Sec. 2.2 error study, Sec. 3 tables)
+are represented here only by their sizes and densities.
+
+This module places atoms and assigns parameters. It holds none of the method's
+arithmetic: no local frame is evaluated, no field, no solve. The CUDA library and the
+FP64 oracle both take its arrays as inputs, and neither is imported here.
+
+Multipole values are synthetic (AMOEBA-like magnitudes with the symmetry each frame
+allows); they are conventions, not fitted parameters.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FRAME_NONE = 0        # multipoles given in the global frame
+FRAME_Z_THEN_X = 1    # z toward the z-atom, x from the x-atom orthogonalised
+FRAME_BISECTOR = 2    # z along the bisector of the two frame bonds, x from the x-atom
+
+# rigid water geometry
+R_OH = 0.9572
+THETA_HOH = np.deg2rad(104.52)
+
+# synthetic water multipoles in each atom's local frame (e, e*A, e*A^2; traceless)
+WATER_Q = (-0.51966, 0.25983)
+WATER_DIP = (np.array([0.0, 0.0, 0.076]), np.array([-0.020, 0.0, -0.031]))
+# xx, xy, xz, yy, yz, zz
+WATER_QUAD = (np.array([0.200, 0.0, 0.0, -0.220, 0.0, 0.020]),
+              np.array([-0.019, 0.0, -0.029, -0.054, 0.0, 0.073]))
+WATER_ALPHA = (0.837, 0.496)
+CHAIN_ALPHAS = (1.334, 1.073, 0.837, 0.496)
+
+
+@dataclass
+class System:
+    """Atom arrays in the caller's order. Lengths in A, charges in e."""
+    xyz: np.ndarray          # [N,3] float64 (any periodic image)
+    box: np.ndarray          # [3] float64 orthorhombic edge lengths
+    q: np.ndarray            # [N]
+    dip: np.ndarray          # [N,3] local-frame dipole, e*A
+    quad: np.ndarray         # [N,6] local-frame traceless quadrupole xx,xy,xz,yy,yz,zz, e*A^2
+    alpha: np.ndarray        # [N] isotropic polarizability, A^3
+    frame: np.ndarray        # [N,3] int32: frame type, z-atom, x-atom (-1 if unused)
+    excl: np.ndarray         # [M,2] int32 pairs i<j with permanent->induced scale 0
+    mol: np.ndarray          # [N] int32 molecule index
+    rigid: np.ndarray = field(default=None)   # [N] int32: 1 for rigid-water atoms
+
+    @property
+    def n(self) -> int:
+        return self.xyz.shape[0]
+
+    def copy(self) -> "System":
+        return System(*(np.array(getattr(self, k)) for k in
+                        ("xyz", "box", "q", "dip", "quad", "alpha", "frame", "excl", "mol", "rigid")))
+
+    def excl_csr(self):
+        """Exclusions as CSR over atoms (both directions): offsets [N+1], atoms [2M]."""
+        n = self.n
+        a = np.concatenate([self.excl[:, 0], self.excl[:, 1]])
+        b = np.concatenate([self.excl[:, 1], self.excl[:, 0]])
+        order = np.lexsort((b, a))
+        a, b = a[order], b[order]
+        offs = np.zeros(n + 1, np.int32)
+        np.add.at(offs, a + 1, 1)
+        return np.cumsum(offs).astype(np.int32), b.astype(np.int32)
+
+
+def _random_rotations(rng, n):
+    """Uniform random rotation matrices from normalised Gaussian quaternions."""
+    qt = rng.normal(size=(n, 4))
+    qt /= np.linalg.norm(qt, axis=1, keepdims=True)
+    w, x, y, z = qt.T
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)], -1),
+        np.stack([2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)], -1),
+        np.stack([2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)], -1),
+    ], 1)
+
+
+def _water_template():
+    """O, H1, H2 in a molecule-fixed frame with the bisector along +z."""
+    s, c = np.sin(THETA_HOH / 2), np.cos(THETA_HOH / 2)
+    return np.array([[0.0, 0.0, 0.0], [R_OH * s, 0.0, R_OH * c], [-R_OH * s, 0.0, R_OH * c]])
+
+
+def _close_molecules(xyz, box, mol, dmin):
+    """Molecule ids owning an atom closer than dmin to an atom of another molecule."""
+    from scipy.spatial import cKDTree
+    wrapped = np.mod(xyz, box)
+    wrapped[wrapped >= box] = 0.0
+    tree = cKDTree(wrapped, boxsize=box)
+    pairs = tree.query_pairs(dmin, output_type="ndarray")
+    if len(pairs) == 0:
+        return np.zeros(0, np.int64)
+    inter = mol[pairs[:, 0]] != mol[pairs[:, 1]]
+    return np.unique(mol[pairs[inter].ravel()])
+
+
+def _orient_waters(rng, o_sites, box, dmin_inter, fixed_xyz=None, dmin_fixed=None,
+                   max_rounds=400):
+    """Random orientations for waters whose O sits at o_sites; redraw clashing ones."""
+    m = len(o_sites)
+    tmpl = _water_template()
+    rot = _random_rotations(rng, m)
+    for _ in range(max_rounds):
+        xyz = (o_sites[:, None, :] + np.einsum("mab,kb->mka", rot, tmpl)).reshape(-1, 3)
+        mol = np.repeat(np.arange(m), 3)
+        bad = _close_molecules(xyz, box, mol, dmin_inter)
+        if fixed_xyz is not None:
+            from scipy.spatial import cKDTree
+            t = cKDTree(np.mod(fixed_xyz, box) % box, boxsize=box)
+            hits = t.query_ball_point(np.mod(xyz, box) % box, dmin_fixed, return_length=True)
+            bad = np.union1d(bad, np.unique(mol[hits > 0]))
+        if len(bad) == 0:
+            return xyz
+        rot[bad] = _random_rotations(rng, len(bad))
+    raise RuntimeError("could not place waters without clashes")
+
+
+def _water_arrays(xyz_w, offset):
+    """Parameters, frames and exclusions for consecutive O,H,H waters."""
+    m = xyz_w.shape[0] // 3
+    n = 3 * m
+    q = np.tile([WATER_Q[0], WATER_Q[1], WATER_Q[1]], m)
+    dip = np.tile(np.stack([WATER_DIP[0], WATER_DIP[1], WATER_DIP[1]]), (m, 1))
+    quad = np.tile(np.stack([WATER_QUAD[0], WATER_QUAD[1], WATER_QUAD[1]]), (m, 1))
+    alpha = np.tile([WATER_ALPHA[0], WATER_ALPHA[1], WATER_ALPHA[1]], m)
+    base = offset + 3 * np.arange(m)
+    frame = np.empty((n, 3), np.int32)
+    frame[0::3] = np.stack([np.full(m, FRAME_BISECTOR), base + 1, base + 2], 1)
+    frame[1::3] = np.stack([np.full(m, FRAME_Z_THEN_X), base, base + 2], 1)
+    frame[2::3] = np.stack([np.full(m, FRAME_Z_THEN_X), base, base + 1], 1)
+    excl = np.concatenate([np.stack([base, base + 1], 1), np.stack([base, base + 2], 1),
+                           np.stack([base + 1, base + 2], 1)]).astype(np.int32)
+    return q, dip, quad, alpha, frame, excl
+
+
+def water_box(n_mol: int, box_len: float, seed: int, jitter: float = 0.12,
+              dmin_inter: float = 1.7) -> System:
+    """n_mol rigid waters, O on a jittered cubic lattice, uniform random orientations.
+
+    O-H 0.9572 A, H-O-H 104.52 deg. Orientations are redrawn until no atom pair of two
+    different molecules is closer than dmin_inter.
+    """
+    rng = np.random.default_rng(seed)
+    box = np.full(3, float(box_len))
+    nl = int(np.ceil(n_mol ** (1.0 / 3.0) - 1e-9))
+    g = (np.arange(nl) + 0.5) * (box_len / nl)
+    sites = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    if len(sites) > n_mol:
+        sites = sites[np.sort(rng.choice(len(sites), n_mol, replace=False))]
+    sites = sites + rng.uniform(-jitter, jitter, size=sites.shape)
+    xyz = _orient_waters(rng, sites, box, dmin_inter)
+    q, dip, quad, alpha, frame, excl = _water_arrays(xyz, 0)
+    mol = np.repeat(np.arange(n_mol), 3).astype(np.int32)
+    return System(xyz, box, q, dip, quad, alpha, frame, excl, mol, np.ones(3 * n_mol, np.int32))
+
+
+def _random_walk_chain(rng, n, box, radius, bond=1.53, angle_deg=111.0, dmin=2.2):
+    """Self-avoiding walk with fixed bond length and angle, confined to a sphere."""
+    center = box / 2
+    ang = np.deg2rad(angle_deg)
+    pts = np.zeros((n, 3))
+    pts[0] = center + rng.normal(size=3)
+    d = rng.normal(size=3)
+    pts[1] = pts[0] + bond * d / np.linalg.norm(d)
+    i = 2
+    fails = 0
+    while i < n:
+        b1 = pts[i - 1] - pts[i - 2]
+        b1 /= np.linalg.norm(b1)
+        ok = False
+        for _ in range(60):
+            perp = rng.normal(size=3)
+            perp -= perp.dot(b1) * b1
+            perp /= np.linalg.norm(perp)
+            step = bond * (np.cos(np.pi - ang) * b1 + np.sin(np.pi - ang) * perp)
+            cand = pts[i - 1] + step
+            if np.linalg.norm(cand - center) > radius:
+                continue
+            if i >= 3:
+                dd = pts[: i - 2] - cand
+                dd -= box * np.round(dd / box)
+                if np.min(np.einsum("ij,ij->i", dd, dd)) < dmin * dmin:
+                    continue
+            ok = True
+            break
+        if ok:
+            pts[i] = cand
+            i += 1
+            fails = 0
+        else:
+            fails += 1
+            i = max(2, i - 1 - min(fails, 20))   # backtrack
+    return pts
+
+
+def solvated_chain(n_chain: int, n_water: int, box_len: float, seed: int,
+                   dmin_chain: float = 2.2, dmin_solv: float = 2.2,
+                   dmin_inter: float = 1.6) -> System:
+    """Random-walk chain (globule) with random multipoles, surrounded by rigid waters.
+
+    Chain: bonds 1.53 A, angle 111 deg, non-bonded atoms >= dmin_chain apart, inside a
+    sphere sized for a loose globule. Charges ~N(0,0.3) made neutral, dipoles ~N(0,0.1)
+    per component, quadrupoles sym(N(0,0.1)) with the trace removed, polarizabilities
+    drawn from {1.334, 1.073, 0.837, 0.496}; multipoles are in the global frame; 1-2 and
+    1-3 pairs have permanent->induced scale 0. Waters fill lattice sites at least
+    dmin_solv (+ the O-H reach) away from every chain atom.
+    """
+    rng = np.random.default_rng(seed)
+    box = np.full(3, float(box_len))
+    radius = (3.0 * n_chain / (4.0 * np.pi * 0.055)) ** (1.0 / 3.0) + 1.0
+    chain = _random_walk_chain(rng, n_chain, box, radius, dmin=dmin_chain) if n_chain else np.zeros((0, 3))
+    qc = rng.normal(0.0, 0.3, n_chain)
+    qc -= qc.mean() if n_chain else 0.0
+    dc = rng.normal(0.0, 0.1, (n_chain, 3))
+    g = rng.normal(0.0, 0.1, (n_chain, 3, 3))
+    g = 0.5 * (g + g.transpose(0, 2, 1))
+    g -= np.eye(3)[None] * (np.trace(g, axis1=1, axis2=2) / 3.0)[:, None, None]
+    quadc = np.stack([g[:, 0, 0], g[:, 0, 1], g[:, 0, 2], g[:, 1, 1], g[:, 1, 2], g[:, 2, 2]], 1)
+    alc = rng.choice(CHAIN_ALPHAS, n_chain)
+    framec = np.tile(np.array([FRAME_NONE, -1, -1], np.int32), (n_chain, 1))
+    exc = [np.stack([np.arange(n_chain - k), np.arange(k, n_chain)], 1) for k in (1, 2) if n_chain > k]
+    exclc = np.concatenate(exc).astype(np.int32) if exc else np.zeros((0, 2), np.int32)
+
+    # candidate O sites on a lattice finer than the water spacing, away from the chain
+    spacing = 2.9
+    nl = int(np.floor(box_len / spacing))
+    gg = (np.arange(nl) + 0.5) * (box_len / nl)
+    sites = np.stack(np.meshgrid(gg, gg, gg, indexing="ij"), -1).reshape(-1, 3)
+    if n_chain:
+        from scipy.spatial import cKDTree
+        t = cKDTree(np.mod(chain, box) % box, boxsize=box)
+        near = t.query_ball_point(sites, dmin_solv + R_OH, return_length=True)
+        sites = sites[near == 0]
+    if len(sites) < n_water:
+        raise RuntimeError(f"only {len(sites)} free water sites for {n_water} waters")
+    sites = sites[np.sort(rng.choice(len(sites), n_water, replace=False))]
+    sites = sites + rng.uniform(-0.1, 0.1, sites.shape)
+    xyz_w = _orient_waters(rng, sites, box, dmin_inter,
+                           fixed_xyz=chain if n_chain else None, dmin_fixed=dmin_solv)
+    q, dip, quad, alpha, frame, excl = _water_arrays(xyz_w, n_chain)
+    mol = np.concatenate([np.zeros(n_chain, np.int32), 1 + np.repeat(np.arange(n_water), 3)]).astype(np.int32)
+    return System(
+        np.concatenate([chain, xyz_w]), box,
+        np.concatenate([qc, q]), np.concatenate([dc, dip]), np.concatenate([quadc, quad]),
+        np.concatenate([alc, alpha]), np.concatenate([framec, frame]).astype(np.int32),
+        np.concatenate([exclc, excl]).astype(np.int32), mol,
+        np.concatenate([np.zeros(n_chain, np.int32), np.ones(3 * n_water, np.int32)]))
+
+
+def perturb(sys: System, seed: int, sigma_t: float = 0.005, sigma_r: float = 0.01) -> System:
+    """One synthetic 'MD step': rigid waters translate ~N(0, sigma_t) per axis and rotate
+    about their O by an angle vector ~N(0, sigma_r); other atoms move ~N(0, sigma_t)."""
+    rng = np.random.default_rng(seed)
+    out = sys.copy()
+    n = sys.n
+    rigid = sys.rigid if sys.rigid is not None else np.zeros(n, np.int32)
+    free = np.nonzero(rigid == 0)[0]
+    out.xyz[free] += rng.normal(0.0, sigma_t, (len(free), 3))
+    o_idx = np.nonzero((rigid == 1) & (sys.frame[:, 0] == FRAME_BISECTOR))[0]
+    if len(o_idx):
+        h1 = sys.frame[o_idx, 1]
+        h2 = sys.frame[o_idx, 2]
+        w = rng.normal(0.0, sigma_r, (len(o_idx), 3))
+        th = np.linalg.norm(w, axis=1, keepdims=True)
+        k = w / np.maximum(th, 1e-300)
+        t = rng.normal(0.0, sigma_t, (len(o_idx), 3))
+        for h in (h1, h2):
+            v = sys.xyz[h] - sys.xyz[o_idx]
+            v = v * np.cos(th) + np.cross(k, v) * np.sin(th) + k * np.einsum("ij,ij->i", k, v)[:, None] * (1 - np.cos(th))
+            out.xyz[h] = sys.xyz[o_idx] + t + v
+        out.xyz[o_idx] = sys.xyz[o_idx] + t
+    return out
+
+
+def water_cfg(n_mol: int) -> float:
+    """Cubic edge (A) for n_mol waters at 0.0333 molecules/A^3 (the configs' density)."""
+    return (n_mol / 0.03334) ** (1.0 / 3.0)
+
+
+def replica_sizes(n_rep: int, lo: int, hi: int, seed: int):
+    """Seeded replica sizes (atoms, rounded down to whole waters) uniform in [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    return (rng.integers(lo, hi + 1, n_rep) // 3 * 3).astype(np.int64)
