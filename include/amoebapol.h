@@ -1,0 +1,150 @@
+/*
+ * amoebapol.h - C ABI of the GB300 (sm_103a) AMOEBA induced-dipole solver.
+ *
+ * The library computes the hot path of a polarizable MD step (paper Sec. 1.2-2.3):
+ * the permanent multipole field that forms the right-hand side, the induced dipoles
+ * by diagonally preconditioned conjugate gradient on the Thole-damped, Ewald-screened
+ * dipole operator (real space over 32-atom blocks + smooth PME), and the polarization
+ * energy and forces.
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are device memory owned by the caller (e.g. the data of a
+ *     PyTorch CUDA tensor), contiguous, row-major, in the caller's atom order. The
+ *     library never frees them and keeps no pointer to them after the call returns.
+ *   - Pointers named h_* are host memory owned by the caller.
+ *   - Units: Angstrom, elementary charge, kcal/mol; dipoles in e*A; field in e/A^2;
+ *     convergence tolerances in Debye (1 e*A = 4.80321 D).
+ *   - Work is enqueued on the stream given to ap_create; a call returns once its work
+ *     is enqueued unless it is documented to synchronize.
+ *   - Return value: AP_OK (0), a negative AP_ERR_* code, or a positive warning.
+ *     No C++ exception crosses the ABI. ap_last_error() describes the last failure.
+ *   - A context is used by one host thread at a time.
+ *   - Calls operate on "the current configuration": the positions and multipoles most
+ *     recently passed to permanent_field(), with the block lists of the last
+ *     build_neighbour_blocks().
+ */
+#ifndef AMOEBAPOL_H
+#define AMOEBAPOL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AP_OK               0
+#define AP_NOT_CONVERGED    1   /* warning: max_iter reached, output holds the last iterate */
+#define AP_ERR_ARG         -1   /* null pointer, bad size, box smaller than 2*(cutoff+buffer) ... */
+#define AP_ERR_CUDA        -2   /* a CUDA / cuFFT call failed (message in ap_last_error) */
+#define AP_ERR_CAPACITY    -3   /* a fixed-size internal list overflowed */
+#define AP_ERR_NONFINITE   -4   /* NaN or Inf found in an input or a reduction */
+#define AP_ERR_TIMEOUT     -5   /* a bounded device wait expired */
+#define AP_ERR_STATE       -6   /* calls made out of order (e.g. solve before field) */
+
+#define AP_MIXED  0   /* FP32 pair/PME arithmetic, FP64 accumulation and PCG reductions */
+#define AP_FP64   1   /* FP64 everywhere (reference-grade, slow on GB300) */
+
+#define AP_FRAME_NONE      0   /* multipoles given in the global frame */
+#define AP_FRAME_Z_THEN_X  1   /* z toward the z-atom, x from the x-atom orthogonalised */
+#define AP_FRAME_BISECTOR  2   /* z along the bisector of the bonds to the z- and x-atoms */
+
+typedef struct ap_ctx ap_ctx;
+
+typedef struct {
+    int    n_atoms;       /* atoms in the system (> 0), fixed for the context */
+    double box[3];        /* orthorhombic edge lengths, A; each >= 2*(cutoff+buffer) */
+    double cutoff;        /* real-space cutoff r_c, A (paper Sec. 3: 7 A) */
+    double buffer;        /* neighbour-list buffer, A (lists valid while no atom moved > buffer/2) */
+    double ewald_beta;    /* Ewald splitting parameter beta, 1/A */
+    int    grid[3];       /* PME grid K_x, K_y, K_z (even, >= 2*pme_order) */
+    int    pme_order;     /* B-spline order; must be 5 (the paper's default, Sec. 1.2.2) */
+    double thole_a;       /* Thole damping parameter a (AMOEBA: 0.39) */
+    int    precision;     /* AP_MIXED or AP_FP64 */
+} ap_params;
+
+typedef struct {
+    int    iterations;    /* PCG iterations performed (matrix-vector products after the initial residual) */
+    int    status;        /* AP_OK or AP_NOT_CONVERGED */
+    double eps_debye;     /* final RMS of alpha_i r_i in Debye (the convergence measure) */
+    double eps_initial;   /* the same measure for the initial guess */
+} ap_solve_info;
+
+/* Create a context: validates the parameters, allocates device workspace, creates the
+ * FFT plans and a second internal stream. `stream` is a cudaStream_t (NULL = legacy
+ * default stream). Synchronizes. On failure *out is NULL and the code is returned. */
+int ap_create(ap_ctx** out, const ap_params* params, void* stream);
+
+/* Free everything the context owns. Synchronizes its streams first. NULL is a no-op. */
+void ap_destroy(ap_ctx* ctx);
+
+/* Message for the last failure on this context (or of the last ap_create when ctx is
+ * NULL). The string is owned by the library and valid until the next call. */
+const char* ap_last_error(const ap_ctx* ctx);
+
+/* a1 - Neighbour blocks (paper Sec. 2.3: cells with at most 32 atoms, 32-atom groups
+ * following the cell numbering, adjacency of groups within cutoff+buffer, and the
+ * bonded-pair scaling handled per group pair, Sec. 1.2.1).
+ *   d_xyz          [n][3] double, positions (any periodic image).
+ *   d_excl_offsets [n+1] int, CSR offsets of the pairs whose permanent->induced scale
+ *                  is 0 (1-2 / 1-3 / intramolecular); may list each pair in both rows.
+ *   d_excl_atoms   [d_excl_offsets[n]] int, partner atoms.
+ *   n_excl_entries the value d_excl_offsets[n] (a host copy, for sizing).
+ * Sorts atoms spatially into 32-atom blocks, builds the list of interacting block
+ * pairs and their 32x32-bit exclusion masks. Grows internal lists as needed
+ * (allocates), synchronizes. Must precede permanent_field(); call again when any atom
+ * has moved more than buffer/2 since the last build. */
+int build_neighbour_blocks(ap_ctx* ctx, const double* d_xyz, const int* d_excl_offsets,
+                           const int* d_excl_atoms, int n_excl_entries);
+
+/* a2+a3 - Permanent field E_i at every atom (right-hand side of A mu = E):
+ * Ewald real space over the blocks with Thole damping (scale 0 for excluded pairs),
+ * smooth-PME reciprocal space (paper Sec. 1.2.2: spread, FFT, convolution, inverse
+ * FFT, gather) and the self term 4 beta^3/(3 sqrt(pi)) d_i.
+ *   d_xyz    [n][3] double positions; sets the current configuration.
+ *   d_mpole  [n][10] double local-frame multipoles: q, dx, dy, dz,
+ *            Qxx, Qxy, Qxz, Qyy, Qyz, Qzz (traceless; potential q/R + d.R/R^3 + R.Q.R/R^5).
+ *   d_frame  [n][3] int: AP_FRAME_* type, z-atom, x-atom (-1 when unused).
+ *   d_alpha  [n] double polarizabilities, A^3 (> 0).
+ *   d_field  [n][3] double output, or NULL to keep the field only inside the context.
+ * The context keeps the field for induced_dipoles_pcg() and polarization_energy_forces(). */
+int permanent_field(ap_ctx* ctx, const double* d_xyz, const double* d_mpole,
+                    const int* d_frame, const double* d_alpha, double* d_field);
+
+/* a4+a5+a6+a7 - Induced dipoles: solve (alpha^-1 - T) mu = E by conjugate gradient with
+ * the diagonal preconditioner diag(alpha) (paper Sec. 1.3 and Sec. 3). Every iteration
+ * applies T = T_real (blocked pair kernel) + T_rec (smooth PME) + self; the convergence
+ * test eps = 4.80321 sqrt(sum |alpha_i r_i|^2 / n) <= tol_debye runs on the device.
+ *   d_guess   [n][3] double initial dipoles, or NULL for mu0 = alpha E.
+ *   tol_debye convergence threshold, Debye (> 0).
+ *   max_iter  iteration limit (>= 1).
+ *   d_mu      [n][3] double output dipoles, e*A.
+ *   h_info    optional host struct filled with the iteration count and residuals;
+ *             when non-NULL the call synchronizes.
+ * Returns AP_NOT_CONVERGED (> 0) when max_iter was reached (d_mu holds the last iterate;
+ * reported only when h_info is non-NULL). */
+int induced_dipoles_pcg(ap_ctx* ctx, const double* d_guess, double tol_debye, int max_iter,
+                        double* d_mu, ap_solve_info* h_info);
+
+/* a9 - Polarization energy and forces at fixed dipoles (variational):
+ * E_pol = -(f/2) sum_i mu_i . E_i with f = 332.063713, and F = -dE_pol/dx including the
+ * reciprocal-space terms and the forces on frame atoms from multipole rotation.
+ *   d_mu      [n][3] double induced dipoles (e.g. from induced_dipoles_pcg).
+ *   d_energy  [1] double output, kcal/mol.
+ *   d_forces  [n][3] double output, kcal/mol/A (overwritten).
+ * Uses the configuration and field of the last permanent_field() call. */
+int polarization_energy_forces(ap_ctx* ctx, const double* d_mu, double* d_energy,
+                               double* d_forces);
+
+/* a5+a6 alone, for tests and diagnostics: d_out = T v = (T_real + T_rec + self) v for the
+ * current configuration; d_v and d_out are [n][3] double in caller order. */
+int dipole_field_matvec(ap_ctx* ctx, const double* d_v, double* d_out);
+
+/* Diagnostics for benchmarks: number of 32-atom blocks, interacting block pairs
+ * (tiles) and block pairs carrying exclusion masks of the current lists. */
+int ap_list_stats(const ap_ctx* ctx, int* h_blocks, int* h_tiles, int* h_excl_tiles);
+
+/* The stream the context enqueues on (cudaStream_t), and its secondary stream. */
+void* ap_stream(const ap_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMOEBAPOL_H */

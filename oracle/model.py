@@ -186,3 +186,47 @@ def solve_energy(sysobj, params, xyz=None, tol=1e-11):
     E = o.permanent_field()
     mu, _ = o.pcg(E, tol=tol, maxiter=2000)
     return o.energy(mu, E)
+
+
+def row_fields(sysobj, params, rows, vec=None):
+    """Permanent field E_i and, if vec is given, (T vec)_i for the atoms in `rows` only.
+
+    Real space by brute force over all atoms (minimum image) for each listed row, the
+    reciprocal part from one full smooth-PME evaluation gathered at the rows, plus the
+    self terms. For spot checks of large systems, where pairs of every atom would not fit.
+    """
+    from .radial import damped_r
+    xyz = np.asarray(sysobj.xyz, np.float64)
+    box = np.asarray(sysobj.box, np.float64)
+    n = xyz.shape[0]
+    rows = np.asarray(rows)
+    dip, quad, _ = frames.rotate_multipoles(xyz, box, sysobj.frame, sysobj.dip, sysobj.quad)
+    q = np.asarray(sysobj.q, np.float64)
+    alpha = np.asarray(sysobj.alpha, np.float64)
+    I, J, R = [], [], []
+    for i in rows:
+        d = xyz[i] - xyz
+        d -= box * np.round(d / box)
+        r2 = np.einsum("ij,ij->i", d, d)
+        keep = (r2 < params.cutoff ** 2) & (np.arange(n) != i)
+        js = np.nonzero(keep)[0]
+        I.append(np.full(len(js), i))
+        J.append(js)
+        R.append(d[js])
+    I, J, R = np.concatenate(I), np.concatenate(J), np.concatenate(R)
+    sigma = pairs.scale_of_pairs(I, J, sysobj.excl, n, R, box)
+    E = realspace.real_field(n, I, J, R, sigma, q, dip, quad, alpha, params.beta, params.thole_a)[rows]
+    sub = xyz[rows]
+    grid = spme.spread(xyz, box, params.grid, params.order, q, dip, quad)
+    phi = spme.convolve(grid, box, params.grid, params.order, params.beta)
+    E += -spme.gather(phi, sub, box, params.grid, params.order, 1)[1]
+    E += params.self_coef * dip[rows]
+    if vec is None:
+        return E, None
+    v = np.asarray(vec, np.float64)
+    Tv = realspace.real_dipole_field(n, I, J, R, v, alpha, params.beta, params.thole_a)[rows]
+    gv = spme.spread(xyz, box, params.grid, params.order, np.zeros(n), v, np.zeros((n, 3, 3)))
+    phv = spme.convolve(gv, box, params.grid, params.order, params.beta)
+    Tv += -spme.gather(phv, sub, box, params.grid, params.order, 1)[1]
+    Tv += params.self_coef * v[rows]
+    return E, Tv

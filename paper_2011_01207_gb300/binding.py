@@ -1,0 +1,238 @@
+"""ctypes binding of libamoebapol.so (argument marshalling only).
+
+Every function has the name of the C entry point it calls and takes PyTorch CUDA tensors
+(used only as device memory). Nothing here computes any part of the method: a missing
+library or GPU raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+AP_OK, AP_NOT_CONVERGED = 0, 1
+AP_MIXED, AP_FP64 = 0, 1
+_ERRORS = {-1: "AP_ERR_ARG", -2: "AP_ERR_CUDA", -3: "AP_ERR_CAPACITY", -4: "AP_ERR_NONFINITE",
+           -5: "AP_ERR_TIMEOUT", -6: "AP_ERR_STATE"}
+
+# every symbol the public header declares
+EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks", "permanent_field",
+           "induced_dipoles_pcg", "polarization_energy_forces", "dipole_field_matvec", "ap_list_stats",
+           "ap_stream")
+
+
+class ApParams(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int), ("box", ctypes.c_double * 3), ("cutoff", ctypes.c_double),
+                ("buffer", ctypes.c_double), ("ewald_beta", ctypes.c_double), ("grid", ctypes.c_int * 3),
+                ("pme_order", ctypes.c_int), ("thole_a", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class ApSolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("eps_debye", ctypes.c_double),
+                ("eps_initial", ctypes.c_double)]
+
+
+class ApError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load(path: str = LIB) -> ctypes.CDLL:
+    """Load the library (built by build.build_library); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ApError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "ap_create": (I, [ctypes.POINTER(P), ctypes.POINTER(ApParams), P]),
+        "ap_destroy": (None, [P]),
+        "ap_last_error": (ctypes.c_char_p, [P]),
+        "build_neighbour_blocks": (I, [P, P, P, P, I]),
+        "permanent_field": (I, [P, P, P, P, P, P]),
+        "induced_dipoles_pcg": (I, [P, P, D, I, P, ctypes.POINTER(ApSolveInfo)]),
+        "polarization_energy_forces": (I, [P, P, P, P]),
+        "dipole_field_matvec": (I, [P, P, P]),
+        "ap_list_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "ap_stream": (P, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t, dtype=None, shape=None, name="tensor", allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ApError(f"{name} is required")
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise ApError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ApError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ApError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ApError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(ctx, code, what):
+    if code < 0:
+        msg = load().ap_last_error(ctx).decode(errors="replace")
+        raise ApError(f"{what} failed: {_ERRORS.get(code, code)}: {msg}")
+    return code
+
+
+def ap_create(params: ApParams, stream: int = 0):
+    lib = load()
+    ctx = ctypes.c_void_p()
+    code = lib.ap_create(ctypes.byref(ctx), ctypes.byref(params), ctypes.c_void_p(stream))
+    if code != 0:
+        raise ApError(f"ap_create failed: {_ERRORS.get(code, code)}: {lib.ap_last_error(None).decode()}")
+    return ctx
+
+
+def ap_destroy(ctx):
+    load().ap_destroy(ctx)
+
+
+def build_neighbour_blocks(ctx, xyz, excl_offsets, excl_atoms, n_excl: int):
+    import torch
+    n = xyz.shape[0]
+    return _check(ctx, load().build_neighbour_blocks(
+        ctx, _ptr(xyz, torch.float64, (n, 3), "xyz"), _ptr(excl_offsets, torch.int32, (n + 1,), "excl_offsets"),
+        _ptr(excl_atoms, torch.int32, None, "excl_atoms"), int(n_excl)), "build_neighbour_blocks")
+
+
+def permanent_field(ctx, xyz, mpole, frame, alpha, field=None):
+    import torch
+    n = xyz.shape[0]
+    return _check(ctx, load().permanent_field(
+        ctx, _ptr(xyz, torch.float64, (n, 3), "xyz"), _ptr(mpole, torch.float64, (n, 10), "mpole"),
+        _ptr(frame, torch.int32, (n, 3), "frame"), _ptr(alpha, torch.float64, (n,), "alpha"),
+        _ptr(field, torch.float64, (n, 3), "field", allow_none=True)), "permanent_field")
+
+
+def induced_dipoles_pcg(ctx, guess, tol_debye: float, max_iter: int, mu, want_info: bool = True):
+    import torch
+    n = mu.shape[0]
+    info = ApSolveInfo()
+    code = load().induced_dipoles_pcg(
+        ctx, _ptr(guess, torch.float64, (n, 3), "guess", allow_none=True), float(tol_debye), int(max_iter),
+        _ptr(mu, torch.float64, (n, 3), "mu"), ctypes.byref(info) if want_info else None)
+    _check(ctx, code, "induced_dipoles_pcg")
+    return info if want_info else None
+
+
+def polarization_energy_forces(ctx, mu, energy, forces):
+    import torch
+    n = mu.shape[0]
+    return _check(ctx, load().polarization_energy_forces(
+        ctx, _ptr(mu, torch.float64, (n, 3), "mu"), _ptr(energy, torch.float64, (1,), "energy"),
+        _ptr(forces, torch.float64, (n, 3), "forces")), "polarization_energy_forces")
+
+
+def dipole_field_matvec(ctx, v, out):
+    import torch
+    n = v.shape[0]
+    return _check(ctx, load().dipole_field_matvec(
+        ctx, _ptr(v, torch.float64, (n, 3), "v"), _ptr(out, torch.float64, (n, 3), "out")), "dipole_field_matvec")
+
+
+def ap_list_stats(ctx):
+    b, t, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    load().ap_list_stats(ctx, ctypes.byref(b), ctypes.byref(t), ctypes.byref(e))
+    return b.value, t.value, e.value
+
+
+# ---- marshalling helpers ---------------------------------------------------------------
+def make_params(n, box, cutoff=7.0, buffer=2.0, beta=0.5446, grid=(24, 24, 24), thole_a=0.39,
+                precision=AP_MIXED) -> ApParams:
+    p = ApParams()
+    p.n_atoms = int(n)
+    for d in range(3):
+        p.box[d] = float(box[d])
+        p.grid[d] = int(grid[d])
+    p.cutoff, p.buffer, p.ewald_beta, p.thole_a = float(cutoff), float(buffer), float(beta), float(thole_a)
+    p.pme_order = 5
+    p.precision = int(precision)
+    return p
+
+
+class Context:
+    """Owns an ap_ctx and the device copies of one system's inputs (torch tensors)."""
+
+    def __init__(self, sysobj, cutoff=7.0, buffer=2.0, beta=0.5446, grid=(24, 24, 24), thole_a=0.39,
+                 precision=AP_MIXED, device="cuda", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise ApError("no CUDA device")
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n = sysobj.n
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.params = make_params(self.n, sysobj.box, cutoff, buffer, beta, grid, thole_a, precision)
+        self.ctx = ap_create(self.params, self.stream.cuda_stream)
+        self.upload(sysobj)
+
+    def upload(self, sysobj):
+        t = self.torch
+        dev = self.device
+        self.xyz = t.tensor(np.ascontiguousarray(sysobj.xyz, np.float64), device=dev)
+        mp = np.concatenate([sysobj.q[:, None], sysobj.dip, sysobj.quad], axis=1)
+        self.mpole = t.tensor(np.ascontiguousarray(mp, np.float64), device=dev)
+        self.frame = t.tensor(np.ascontiguousarray(sysobj.frame, np.int32), device=dev)
+        self.alpha = t.tensor(np.ascontiguousarray(sysobj.alpha, np.float64), device=dev)
+        off, atoms = sysobj.excl_csr()
+        self.excl_off = t.tensor(off, device=dev)
+        self.excl_atoms = t.tensor(atoms if len(atoms) else np.zeros(1, np.int32), device=dev)
+        self.n_excl = int(off[-1])
+        self.field = t.zeros((self.n, 3), dtype=t.float64, device=dev)
+        self.mu = t.zeros((self.n, 3), dtype=t.float64, device=dev)
+        self.forces = t.zeros((self.n, 3), dtype=t.float64, device=dev)
+        self.energy = t.zeros(1, dtype=t.float64, device=dev)
+
+    def set_positions(self, xyz):
+        self.xyz.copy_(self.torch.as_tensor(np.ascontiguousarray(xyz, np.float64)), non_blocking=False)
+
+    def build(self):
+        return build_neighbour_blocks(self.ctx, self.xyz, self.excl_off, self.excl_atoms, self.n_excl)
+
+    def permanent_field(self, out=True):
+        return permanent_field(self.ctx, self.xyz, self.mpole, self.frame, self.alpha, self.field if out else None)
+
+    def solve(self, tol=1e-5, max_iter=200, guess=None, want_info=True):
+        return induced_dipoles_pcg(self.ctx, guess, tol, max_iter, self.mu, want_info)
+
+    def energy_forces(self, mu=None):
+        polarization_energy_forces(self.ctx, self.mu if mu is None else mu, self.energy, self.forces)
+        return self.energy, self.forces
+
+    def matvec(self, v, out):
+        return dipole_field_matvec(self.ctx, v, out)
+
+    def stats(self):
+        return ap_list_stats(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            ap_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

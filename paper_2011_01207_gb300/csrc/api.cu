@@ -1,0 +1,209 @@
+// C-ABI entry points: context lifecycle, argument checks, and the four calls of the path.
+#include "common.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+static std::string g_create_error;
+
+int ap_fail(ap_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg; else g_create_error = msg;
+    return code;
+}
+
+int dipole_field_apply(ap_ctx *ctx, const double *d_v, double *d_out);
+
+namespace {
+
+template <class P>
+int dalloc(ap_ctx *ctx, P **p, size_t bytes) {
+    AP_CUDA(cudaMalloc((void **)p, bytes));
+    AP_CUDA(cudaMemset(*p, 0, bytes));
+    return AP_OK;
+}
+
+void free_all(ap_ctx *c) {
+    void *ptrs[] = {c->perm, c->iperm, c->bcenter, c->tiles, c->tshift, c->tile_excl, c->excl_mask, c->cell_count,
+                    c->tmp_int, c->excl_off, c->excl_atoms, c->posq, c->dipd, c->quad0, c->quad1, c->alpha,
+                    c->E, c->acc, c->rec, c->rot, c->mpl, c->frame_s, c->fvec, c->mu, c->r, c->qv, c->p, c->st,
+                    c->grid, c->cgrid, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->plan_r2c) cufftDestroy(c->plan_r2c);
+    if (c->plan_c2r) cufftDestroy(c->plan_c2r);
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->s1) cudaStreamDestroy(c->s1);
+}
+
+int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
+    ctx->prm = *P;
+    ctx->prec = P->precision;
+    ctx->n = P->n_atoms;
+    ctx->n_blocks = (P->n_atoms + 31) / 32;
+    ctx->n_pad = ctx->n_blocks * 32;
+    ctx->s0 = (cudaStream_t)stream;
+    for (int d = 0; d < 3; ++d) ctx->K[d] = P->grid[d];
+    int dev = 0;
+    AP_CUDA(cudaGetDevice(&dev));
+    AP_CUDA(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    int lo = 0, hi = 0;
+    AP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    AP_CUDA(cudaStreamCreateWithPriority(&ctx->s1, cudaStreamNonBlocking, hi));   // reciprocal branch first
+    AP_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    AP_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+
+    const size_t np = ctx->n_pad, nb = ctx->n_blocks;
+    const size_t es = ctx->prec == AP_FP64 ? 8 : 4;   // element size of T
+    int r;
+    if ((r = dalloc(ctx, &ctx->perm, sizeof(int) * np))) return r;
+    if ((r = dalloc(ctx, &ctx->iperm, sizeof(int) * np))) return r;
+    if ((r = dalloc(ctx, &ctx->bcenter, sizeof(float4) * nb))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->posq, 4 * es * np))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->dipd, 4 * es * np))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->quad0, 4 * es * np))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->quad1, 4 * es * np))) return r;
+    if ((r = dalloc(ctx, &ctx->alpha, sizeof(double) * np))) return r;
+    if ((r = dalloc(ctx, &ctx->E, sizeof(double) * 3 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->acc, sizeof(double) * 3 * np))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->rec, es * 3 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->rot, sizeof(double) * 9 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->mpl, sizeof(double) * 10 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->frame_s, sizeof(int) * 3 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->fvec, sizeof(double) * 6 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->mu, sizeof(double) * 3 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->r, sizeof(double) * 3 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->qv, sizeof(double) * 3 * np))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->p, 4 * es * np))) return r;
+    if ((r = dalloc(ctx, &ctx->st, sizeof(PcgState)))) return r;
+    AP_CUDA(cudaMallocHost((void **)&ctx->st_host, sizeof(PcgState)));
+    ctx->ngrid = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
+    ctx->ncgrid = (size_t)(P->grid[0] / 2 + 1) * P->grid[1] * P->grid[2];
+    if ((r = dalloc(ctx, (char **)&ctx->grid, es * ctx->ngrid))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->grid2, es * ctx->ngrid))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->cgrid, 2 * es * ctx->ncgrid))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->green, es * ctx->ncgrid))) return r;
+    if ((r = dalloc(ctx, &ctx->frc, sizeof(double) * 3 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->gdip, sizeof(double) * 3 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->gquad, sizeof(double) * 6 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->mu_s, sizeof(double) * 3 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->gbuf, sizeof(double) * 30 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->red, sizeof(double) * 64))) return r;
+    if ((r = pme_init(ctx))) return r;
+    AP_CUDA(cudaDeviceSynchronize());
+    return AP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ap_create(ap_ctx **out, const ap_params *P, void *stream) {
+    g_create_error.clear();
+    if (!out) return ap_fail(nullptr, AP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!P) return ap_fail(nullptr, AP_ERR_ARG, "params is NULL");
+    if (P->n_atoms <= 0) return ap_fail(nullptr, AP_ERR_ARG, "n_atoms must be > 0");
+    if (P->precision != AP_MIXED && P->precision != AP_FP64) return ap_fail(nullptr, AP_ERR_ARG, "unknown precision");
+    if (P->pme_order != 5) return ap_fail(nullptr, AP_ERR_ARG, "pme_order must be 5");
+    if (!(P->cutoff > 0) || !(P->buffer >= 0) || !(P->ewald_beta > 0) || !(P->thole_a >= 0))
+        return ap_fail(nullptr, AP_ERR_ARG, "cutoff, buffer, ewald_beta and thole_a must be positive");
+    for (int d = 0; d < 3; ++d) {
+        if (!(P->box[d] >= 2.0 * (P->cutoff + P->buffer)))
+            return ap_fail(nullptr, AP_ERR_ARG, "each box edge must be >= 2*(cutoff+buffer)");
+        if (P->grid[d] < 8 || P->grid[d] > 4096) return ap_fail(nullptr, AP_ERR_ARG, "grid sizes must be in [8, 4096]");
+    }
+    ap_ctx *ctx = new (std::nothrow) ap_ctx();
+    if (!ctx) return ap_fail(nullptr, AP_ERR_ARG, "out of host memory");
+    int r = create_impl(ctx, P, stream);
+    if (r) {
+        g_create_error = ctx->err;
+        free_all(ctx);
+        delete ctx;
+        return r;
+    }
+    *out = ctx;
+    return AP_OK;
+}
+
+void ap_destroy(ap_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->s0) cudaStreamSynchronize(ctx->s0);
+    if (ctx->s1) cudaStreamSynchronize(ctx->s1);
+    free_all(ctx);
+    delete ctx;
+}
+
+const char *ap_last_error(const ap_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int build_neighbour_blocks(ap_ctx *ctx, const double *d_xyz, const int *d_excl_offsets, const int *d_excl_atoms,
+                           int n_excl_entries) {
+    if (!ctx) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!d_xyz) return ap_fail(ctx, AP_ERR_ARG, "d_xyz is NULL");
+    if (n_excl_entries < 0 || (n_excl_entries > 0 && (!d_excl_offsets || !d_excl_atoms)))
+        return ap_fail(ctx, AP_ERR_ARG, "bad exclusion lists");
+    return nb_build(ctx, d_xyz, d_excl_offsets, d_excl_atoms, n_excl_entries);
+}
+
+int permanent_field(ap_ctx *ctx, const double *d_xyz, const double *d_mpole, const int *d_frame,
+                    const double *d_alpha, double *d_field) {
+    if (!ctx) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!d_xyz || !d_mpole || !d_frame || !d_alpha) return ap_fail(ctx, AP_ERR_ARG, "null input pointer");
+    if (!ctx->lists_valid) return ap_fail(ctx, AP_ERR_STATE, "build_neighbour_blocks() must come first");
+    int r = cfg_load(ctx, d_xyz, d_mpole, d_frame, d_alpha);
+    if (r) return r;
+    AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+    AP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->s0));
+    AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
+    if ((r = pme_multipole_field(ctx, ctx->s1))) return r;
+    if ((r = real_field_launch(ctx, ctx->s0))) return r;
+    AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));
+    AP_CUDA(cudaStreamWaitEvent(ctx->s0, ctx->ev_join, 0));
+    if ((r = field_finish(ctx, d_field))) return r;
+    AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+    ctx->config_valid = 1;
+    return AP_OK;
+}
+
+int induced_dipoles_pcg(ap_ctx *ctx, const double *d_guess, double tol_debye, int max_iter, double *d_mu,
+                        ap_solve_info *h_info) {
+    if (!ctx) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!d_mu) return ap_fail(ctx, AP_ERR_ARG, "d_mu is NULL");
+    if (!(tol_debye > 0) || max_iter < 1) return ap_fail(ctx, AP_ERR_ARG, "tol_debye must be > 0 and max_iter >= 1");
+    if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
+    return pcg_solve(ctx, d_guess, tol_debye, max_iter, d_mu, h_info);
+}
+
+int polarization_energy_forces(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
+    if (!ctx) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!d_mu || !d_energy || !d_forces) return ap_fail(ctx, AP_ERR_ARG, "null pointer");
+    if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
+    return forces_run(ctx, d_mu, d_energy, d_forces);
+}
+
+int dipole_field_matvec(ap_ctx *ctx, const double *d_v, double *d_out) {
+    if (!ctx) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!d_v || !d_out) return ap_fail(ctx, AP_ERR_ARG, "null pointer");
+    if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
+    return dipole_field_apply(ctx, d_v, d_out);
+}
+
+int ap_list_stats(const ap_ctx *ctx, int *h_blocks, int *h_tiles, int *h_excl_tiles) {
+    if (!ctx) return AP_ERR_ARG;
+    if (h_blocks) *h_blocks = ctx->n_blocks;
+    if (h_tiles) *h_tiles = ctx->n_tiles;
+    if (h_excl_tiles) *h_excl_tiles = ctx->n_excl_tiles;
+    return AP_OK;
+}
+
+void *ap_stream(const ap_ctx *ctx) { return ctx ? (void *)ctx->s0 : nullptr; }
+
+}  // extern "C"

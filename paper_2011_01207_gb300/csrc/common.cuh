@@ -1,0 +1,151 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/amoebapol.h"
+
+#define AP_WARP 32
+#define AP_BLOCK_ATOMS 32          // atoms per block (one warp lane each), paper Sec. 2.3: B_size = 32
+
+// physical constants (readings: the paper gives none)
+#define AP_COULOMB 332.063713       // kcal A / (mol e^2)
+#define AP_DEBYE 4.80321            // Debye per e*A
+#define AP_SQRT_PI 1.7724538509055159
+
+// 32-byte aligned 4-vector of doubles (the CUDA 13 double4 is deprecated)
+struct __align__(32) dvec4 { double x, y, z, w; };
+
+template <class T> struct V4;
+template <> struct V4<float> { typedef float4 type; };
+template <> struct V4<double> { typedef dvec4 type; };
+
+template <class T> struct FftTypes;
+template <> struct FftTypes<float> { typedef cufftComplex cplx; };
+template <> struct FftTypes<double> { typedef cufftDoubleComplex cplx; };
+
+// device-side solver state (one per context)
+struct PcgState {
+    double rz;         // r . z of the current iterate
+    double pq;         // accumulator: p . A p
+    double rz_new;     // accumulator: r . z after the update
+    double zz;         // accumulator: |alpha r|^2 after the update
+    double gamma;      // step length of the current iteration
+    double beta;       // conjugation coefficient for the next direction
+    double eps;        // convergence measure (Debye)
+    double eps0;       // measure for the initial guess
+    double tol;        // threshold (Debye)
+    int iter;          // iterations done
+    int max_iter;
+    int done;          // 1 when converged or out of iterations
+    int status;        // AP_OK / AP_NOT_CONVERGED
+    unsigned int blocks_done;   // last-block-done counter for the update kernel
+    int nonfinite;     // set when a reduction produced NaN/Inf
+    int guard;         // iterations started by the graph loop (hard bound on the WHILE node)
+};
+
+struct ap_ctx {
+    ap_params prm;
+    int prec = AP_MIXED;
+    int n = 0, n_pad = 0, n_blocks = 0;
+    cudaStream_t s0 = nullptr;          // caller's stream
+    cudaStream_t s1 = nullptr;          // internal stream (reciprocal branch)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::string err;
+    int sm_count = 0;
+
+    // neighbour blocks
+    int *perm = nullptr;      // [n_pad] slot -> atom (-1 for padding)
+    int *iperm = nullptr;     // [n] atom -> slot
+    float4 *bcenter = nullptr;   // [n_blocks] block centre (x,y,z) at the last build
+    int2 *tiles = nullptr;       // [cap_tiles] block pairs (I <= J), sorted by I then J
+    float4 *tshift = nullptr;    // [cap_tiles] periodic shift added to x_i - x_j
+    int *tile_excl = nullptr;    // [cap_tiles] exclusion-mask slot or -1
+    unsigned *excl_mask = nullptr;  // [cap_excl][32]
+    int n_tiles = 0, cap_tiles = 0, n_excl_tiles = 0, cap_excl = 0;
+    int minimg = 1;              // per-pair minimum image (small boxes) vs per-tile shifts
+    int lists_valid = 0;
+    // scratch for the build
+    int *cell_count = nullptr; int cap_cells = 0;
+    int *tmp_int = nullptr; int cap_tmp = 0;
+    int *excl_off = nullptr, *excl_atoms = nullptr; int cap_excl_atoms = 0;   // copy of the CSR
+
+    // configuration (sorted slots; element type T = float or double)
+    void *posq = nullptr;     // T4: x, y, z, q
+    void *dipd = nullptr;     // T4: dx, dy, dz, alpha^-1/2 (Thole)
+    void *quad0 = nullptr;    // T4: Qxx, Qxy, Qxz, Qyy
+    void *quad1 = nullptr;    // T4: Qyz, Qzz, alpha, 0
+    double *alpha = nullptr;  // [n_pad]
+    double *E = nullptr;      // [3][n_pad] permanent field (SoA)
+    double *acc = nullptr;    // [3][n_pad] real-space accumulator
+    void *rec = nullptr;      // T [3][n_pad] reciprocal field from the gather
+    double *rot = nullptr;    // [n_pad][9] frame matrices (columns x,y,z)
+    double *mpl = nullptr;    // [n_pad][10] local multipoles (sorted), for torques
+    int *frame_s = nullptr;   // [n_pad][3] frames in slot indices (type, z-slot, x-slot)
+    double *fvec = nullptr;   // [n_pad][6] minimum-image vectors to the z- and x-atoms
+    int config_valid = 0;
+
+    // PCG
+    double *mu = nullptr, *r = nullptr, *qv = nullptr;   // [3][n_pad]
+    void *p = nullptr;        // T4 [n_pad] search direction
+    PcgState *st = nullptr;   // device
+    PcgState *st_host = nullptr;  // pinned mirror
+
+    // PME
+    int K[3] = {0, 0, 0};
+    size_t ngrid = 0, ncgrid = 0;
+    void *grid = nullptr;     // T [Kz][Ky][Kx]
+    void *cgrid = nullptr;    // complex [Kz][Ky][Kx/2+1]
+    void *green = nullptr;    // T [Kz][Ky][Kx/2+1]  B(m) C(m)
+    void *grid2 = nullptr;    // second real grid (potential of the permanent multipoles, kept for forces)
+    cufftHandle plan_r2c = 0, plan_c2r = 0;
+
+    // forces
+    double *frc = nullptr;    // [3][n_pad] force accumulator (sorted)
+    double *gdip = nullptr;   // [3][n_pad] dU/d(global dipole)
+    double *gquad = nullptr;  // [6][n_pad] dU/d(global quadrupole)
+    double *red = nullptr;    // small reduction scratch
+    double *mu_s = nullptr;   // [3][n_pad] dipoles given to the force call (sorted)
+    double *gbuf = nullptr;   // [30][n_pad] PME potential derivatives for the forces
+
+    // graph of the solve loop
+    cudaGraphExec_t solve_exec = nullptr;
+    int graph_ok = 0;         // 1 when the conditional-while graph is usable
+    int graph_tried = 0;
+};
+
+// error helpers -------------------------------------------------------------------------
+int ap_fail(ap_ctx *c, int code, const std::string &msg);
+#define AP_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return ap_fail(ctx, AP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+#define AP_CUFFT(call)                                                                   \
+    do {                                                                                 \
+        cufftResult r_ = (call);                                                         \
+        if (r_ != CUFFT_SUCCESS)                                                         \
+            return ap_fail(ctx, AP_ERR_CUDA, std::string(#call) + ": cufft error " + std::to_string((int)r_)); \
+    } while (0)
+
+// launch helpers --------------------------------------------------------------------------
+static inline int ap_grid_for(long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+// entry points implemented in the translation units ------------------------------------
+int nb_build(ap_ctx *ctx, const double *d_xyz, const int *d_off, const int *d_atoms, int n_excl);
+int cfg_load(ap_ctx *ctx, const double *d_xyz, const double *d_mpole, const int *d_frame,
+             const double *d_alpha);
+int real_field_launch(ap_ctx *ctx, cudaStream_t s);
+int real_matvec_launch(ap_ctx *ctx, const void *p, cudaStream_t s);
+int real_forces_launch(ap_ctx *ctx, cudaStream_t s);
+int pme_init(ap_ctx *ctx);
+int pme_multipole_field(ap_ctx *ctx, cudaStream_t s);              // permanent: grid2 keeps phi_M
+int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s);  // T_rec p -> rec
+int field_finish(ap_ctx *ctx, double *d_field_out);
+int pcg_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double *d_mu,
+              ap_solve_info *info);
+int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces);

@@ -1,0 +1,391 @@
+// a9 - Polarization energy and forces at fixed induced dipoles ("final force evaluation",
+// paper Sec. 1.2).
+//
+// E_pol = -(f/2) sum_i mu_i . E_i. At the solution of A mu = E, dE_pol/dx at fixed mu is the
+// gradient of  -f sum_{i<j} mu_i T_ij mu_j - f sum_i mu_i . E_i  (variational property):
+//   real space: each unordered pair carries
+//       U_ij = -f [mu_i . E(R; M_j) + mu_j . E(-R; M_i) + mu_i . T(R) mu_j],  R = x_i - x_j;
+//   reciprocal: f <dQ_mu/dx, phi_M + phi_mu> + f <dQ_M/dx, phi_mu>, from the smooth-PME
+//               potentials' derivatives up to third order at the atoms;
+//   frames:     global multipoles rotate with their frame atoms: dU/d(global dipole) and
+//               dU/d(global quadrupole) are chained through the frame construction.
+// Pair arithmetic in T, accumulation in FP64 as in the other real-space kernels.
+#include "common.cuh"
+#include "pair_math.cuh"
+
+#include <cmath>
+
+void unsort3(ap_ctx *ctx, const double *src, double *out, cudaStream_t s);
+int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s);
+
+namespace {
+
+template <class T>
+__device__ __forceinline__ T sh(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+__device__ __forceinline__ void flush12(double *frc, double *gdip, double *gquad, int n_pad, int s, const float *a) {
+    for (int c = 0; c < 3; ++c) atomicAdd(frc + c * n_pad + s, (double)a[c]);
+    for (int c = 0; c < 3; ++c) atomicAdd(gdip + c * n_pad + s, (double)a[3 + c]);
+    for (int c = 0; c < 6; ++c) atomicAdd(gquad + c * n_pad + s, (double)a[6 + c]);
+}
+__device__ __forceinline__ void flush12(double *frc, double *gdip, double *gquad, int n_pad, int s, const double *a) {
+    for (int c = 0; c < 3; ++c) atomicAdd(frc + c * n_pad + s, a[c]);
+    for (int c = 0; c < 3; ++c) atomicAdd(gdip + c * n_pad + s, a[3 + c]);
+    for (int c = 0; c < 6; ++c) atomicAdd(gquad + c * n_pad + s, a[6 + c]);
+}
+
+// out_a = sum_b mu_b dE_b/dR_a for the field E(R) of a multipole (q, d, Q) at the origin
+template <class T>
+__device__ __forceinline__ void mu_dot_field_grad(T q, const T *d, const T *Q /*xx xy xz yy yz zz*/, const T *mu,
+                                                  T dx, T dy, T dz, T R1, T R2, T R3, T R4, T *out) {
+    const T R[3] = {dx, dy, dz};
+    const T QR[3] = {Q[0] * dx + Q[1] * dy + Q[2] * dz, Q[1] * dx + Q[3] * dy + Q[4] * dz,
+                     Q[2] * dx + Q[4] * dy + Q[5] * dz};
+    const T Qm[3] = {Q[0] * mu[0] + Q[1] * mu[1] + Q[2] * mu[2], Q[1] * mu[0] + Q[3] * mu[1] + Q[4] * mu[2],
+                     Q[2] * mu[0] + Q[4] * mu[1] + Q[5] * mu[2]};
+    const T muR = mu[0] * dx + mu[1] * dy + mu[2] * dz;
+    const T dR = d[0] * dx + d[1] * dy + d[2] * dz;
+    const T dmu = d[0] * mu[0] + d[1] * mu[1] + d[2] * mu[2];
+    const T RQR = QR[0] * dx + QR[1] * dy + QR[2] * dz;
+    const T muQR = mu[0] * QR[0] + mu[1] * QR[1] + mu[2] * QR[2];
+    const T cR = -q * muR * R2 + dmu * R2 - dR * muR * R3 + T(2.0 / 3.0) * muQR * R3 - RQR * muR * R4 * T(1.0 / 3.0);
+    const T cmu = q * R1 + dR * R2 + RQR * R3 * T(1.0 / 3.0);
+    const T cd = muR * R2;
+    const T cQm = -T(2.0 / 3.0) * R2;
+    const T cQR = T(2.0 / 3.0) * muR * R3;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a] = cR * R[a] + cmu * mu[a] + cd * d[a] + cQm * Qm[a] + cQR * QR[a];
+}
+
+// one warp per tile (grid-stride); accumulators per lane: force (3), dU/dd (3), dU/dQ (6)
+template <class T, bool MINIMG>
+__global__ void __launch_bounds__(128) k_pair_forces(
+    const int2 *__restrict__ tiles, const float4 *__restrict__ tshift, const int *__restrict__ tile_excl,
+    const unsigned *__restrict__ masks, int ntiles, const typename V4<T>::type *__restrict__ posq,
+    const typename V4<T>::type *__restrict__ dipd, const typename V4<T>::type *__restrict__ quad0,
+    const typename V4<T>::type *__restrict__ quad1, const typename V4<T>::type *__restrict__ muv,
+    double *__restrict__ frc, double *__restrict__ gdip, double *__restrict__ gquad, int n_pad, PairConsts<T> pc,
+    double fconst) {
+    typedef typename V4<T>::type T4;
+    const int lane = threadIdx.x & 31;
+    const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long nw = ((long)gridDim.x * blockDim.x) >> 5;
+    const T f = (T)fconst;
+    const T third = T(1.0 / 3.0);
+    for (long t = gw; t < ntiles; t += nw) {
+        const int2 IJ = tiles[t];
+        const int si = IJ.x * 32 + lane, sj = IJ.y * 32 + lane;
+        T4 a = posq[si], b = dipd[si], c = quad0[si], d = quad1[si], m = muv[si];
+        const T xi = a.x, yi = a.y, zi = a.z, qi = a.w, ti = b.w;
+        const T ndi[3] = {-b.x, -b.y, -b.z};
+        const T Qi[6] = {c.x, c.y, c.z, c.w, d.x, d.y};
+        const T mi[3] = {m.x, m.y, m.z};
+        a = posq[sj]; b = dipd[sj]; c = quad0[sj]; d = quad1[sj]; m = muv[sj];
+        T xj = a.x, yj = a.y, zj = a.z, qj = a.w, tj = b.w;
+        T dj[3] = {b.x, b.y, b.z};
+        T Qj[6] = {c.x, c.y, c.z, c.w, d.x, d.y};
+        T mj[3] = {m.x, m.y, m.z};
+        T sx = 0, sy = 0, sz = 0;
+        if (!MINIMG) {
+            float4 shv = tshift[t];
+            sx = shv.x; sy = shv.y; sz = shv.z;
+        }
+        const int slot = tile_excl[t];
+        const unsigned mask = slot >= 0 ? masks[slot * 32 + lane] : 0u;
+        const bool diag = IJ.x == IJ.y;
+        T ai[12], aj[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ai[k] = aj[k] = 0;
+        for (int s = 0; s < 32; ++s) {
+            const int jl = (lane + s) & 31;
+            if (!(diag && s == 0)) {
+                T dx = xi - xj, dy = yi - yj, dz = zi - zj;
+                if (MINIMG) {
+                    dx -= pc.L[0] * ap_rint(dx * pc.iL[0]);
+                    dy -= pc.L[1] * ap_rint(dy * pc.iL[1]);
+                    dz -= pc.L[2] * ap_rint(dz * pc.iL[2]);
+                } else {
+                    dx += sx; dy += sy; dz += sz;
+                }
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < pc.rc2) {
+                    const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+                    T B[4], U[4], oml[4];
+                    screened<T, 4>(pc, r, rinv, rinv2, B, U);
+                    thole_oml<T, 4>(pc.thole_a * r2 * r * ti * tj, oml);
+                    const bool ex = (mask >> jl) & 1u;
+                    T Rd[4], Ru[3];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) Rd[k] = B[k] - (ex ? U[k] : oml[k] * U[k]);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) Ru[k] = B[k] - oml[k] * U[k];
+                    // dU_ij/dR = -f [ mu_i.G(R; M_j) - mu_j.G(R; q_i, -d_i, Q_i) + d(mu_i T mu_j)/dR ]
+                    T A[3], Bv[3];
+                    mu_dot_field_grad<T>(qj, dj, Qj, mi, dx, dy, dz, Rd[0], Rd[1], Rd[2], Rd[3], A);
+                    mu_dot_field_grad<T>(qi, ndi, Qi, mj, dx, dy, dz, Rd[0], Rd[1], Rd[2], Rd[3], Bv);
+                    const T mij = mi[0] * mj[0] + mi[1] * mj[1] + mi[2] * mj[2];
+                    const T mir = mi[0] * dx + mi[1] * dy + mi[2] * dz;
+                    const T mjr = mj[0] * dx + mj[1] * dy + mj[2] * dz;
+                    const T cR = Ru[1] * mij - Ru[2] * mir * mjr;
+                    const T R[3] = {dx, dy, dz};
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const T g = -f * (A[k] - Bv[k] + cR * R[k] + Ru[1] * (mi[k] * mjr + mj[k] * mir));
+                        ai[k] -= g;                                   // F_i = -dU/dR
+                        ai[3 + k] += -f * (-Rd[0] * mj[k] + Rd[1] * mjr * R[k]);   // dU/dd_i (source i, target j)
+                        if (!diag) {
+                            aj[k] += g;                               // F_j = +dU/dR
+                            aj[3 + k] += -f * (-Rd[0] * mi[k] + Rd[1] * mir * R[k]);
+                        }
+                    }
+                    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        const T RR = R[ia[k]] * R[ib[k]];
+                        const T symj = mj[ia[k]] * R[ib[k]] + R[ia[k]] * mj[ib[k]];
+                        ai[6 + k] += -f * third * (Rd[1] * symj - Rd[2] * mjr * RR);
+                        if (!diag) {
+                            const T symi = mi[ia[k]] * R[ib[k]] + R[ia[k]] * mi[ib[k]];
+                            aj[6 + k] += -f * third * (-Rd[1] * symi + Rd[2] * mir * RR);
+                        }
+                    }
+                }
+            }
+            const int src = (lane + 1) & 31;
+            xj = sh(xj, src); yj = sh(yj, src); zj = sh(zj, src); qj = sh(qj, src); tj = sh(tj, src);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { dj[k] = sh(dj[k], src); mj[k] = sh(mj[k], src); }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Qj[k] = sh(Qj[k], src);
+            if (!diag) {
+#pragma unroll
+                for (int k = 0; k < 12; ++k) aj[k] = sh(aj[k], src);
+            }
+        }
+        if (si < pc.n) flush12(frc, gdip, gquad, n_pad, si, ai);
+        if (!diag && sj < pc.n) flush12(frc, gdip, gquad, n_pad, sj, aj);
+    }
+}
+
+// reciprocal-space gradient and source terms per atom
+// D: phi_mu derivatives [20][n_pad] then phi_M derivatives [10][n_pad] (component order of pme.cu)
+template <class T>
+__global__ void k_recip_forces(const double *__restrict__ D, const double *__restrict__ mu,
+                               const typename V4<T>::type *__restrict__ posq,
+                               const typename V4<T>::type *__restrict__ dipd,
+                               const typename V4<T>::type *__restrict__ quad0,
+                               const typename V4<T>::type *__restrict__ quad1, int n, int n_pad, double f,
+                               double self_coef, double *__restrict__ frc, double *__restrict__ gdip,
+                               double *__restrict__ gquad) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    auto Du = [&](int c) { return D[(size_t)c * n_pad + s]; };
+    auto DM = [&](int c) { return D[(size_t)(20 + c) * n_pad + s]; };
+    const double m[3] = {mu[s], mu[n_pad + s], mu[2 * n_pad + s]};
+    typename V4<T>::type a = posq[s], b = dipd[s], c = quad0[s], d = quad1[s];
+    const double q = a.w, dd[3] = {b.x, b.y, b.z};
+    const double Qxx = c.x, Qxy = c.y, Qxz = c.z, Qyy = c.w, Qyz = d.x, Qzz = d.y;
+    // symmetric Hessians: index (xx yy zz xy xz yz) -> 4..9
+    double Hu[3][3] = {{Du(4), Du(7), Du(8)}, {Du(7), Du(5), Du(9)}, {Du(8), Du(9), Du(6)}};
+    double HM[3][3] = {{DM(4), DM(7), DM(8)}, {DM(7), DM(5), DM(9)}, {DM(8), DM(9), DM(6)}};
+    const double gu[3] = {Du(1), Du(2), Du(3)};
+    // sum_bc Q_bc T_abc with T the third derivatives of phi_mu
+    const double Txxx = Du(10), Tyyy = Du(11), Tzzz = Du(12), Txxy = Du(13), Txxz = Du(14), Txyy = Du(15),
+                 Tyyz = Du(16), Txzz = Du(17), Tyzz = Du(18), Txyz = Du(19);
+    const double QT[3] = {
+        Qxx * Txxx + Qyy * Txyy + Qzz * Txzz + 2 * (Qxy * Txxy + Qxz * Txxz + Qyz * Txyz),
+        Qxx * Txxy + Qyy * Tyyy + Qzz * Tyzz + 2 * (Qxy * Txyy + Qxz * Txyz + Qyz * Tyyz),
+        Qxx * Txxz + Qyy * Tyyz + Qzz * Tzzz + 2 * (Qxy * Txyz + Qxz * Txzz + Qyz * Tyzz)};
+    for (int k = 0; k < 3; ++k) {
+        double g = 0.0;
+        for (int l = 0; l < 3; ++l) g += m[l] * (Hu[k][l] + HM[k][l]) + dd[l] * Hu[k][l];
+        g += q * gu[k] + QT[k] / 3.0;
+        frc[k * n_pad + s] -= f * g;
+        gdip[k * n_pad + s] += f * gu[k] - f * self_coef * m[k];
+    }
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; ++k) gquad[k * n_pad + s] += f / 3.0 * Hu[ia[k]][ib[k]];
+}
+
+__device__ __forceinline__ double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+__device__ __forceinline__ void cross3(const double *a, const double *b, double *o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// frame chain rule: dU/dR = G_d d_l^T + 2 G_Q R Q_l, then through the axis construction
+__global__ void k_frame_forces(const double *__restrict__ gdip, const double *__restrict__ gquad,
+                               const double *__restrict__ rot, const double *__restrict__ mpl,
+                               const double *__restrict__ fvec, const int *__restrict__ frame_s, int n, int n_pad,
+                               double *__restrict__ frc) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int type = frame_s[3 * s];
+    if (type != AP_FRAME_Z_THEN_X && type != AP_FRAME_BISECTOR) return;
+    const int zs = frame_s[3 * s + 1], xs = frame_s[3 * s + 2];
+    double R[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) R[a][b] = rot[9 * s + 3 * a + b];
+    const double *m = mpl + 10 * s;
+    const double dl[3] = {m[1], m[2], m[3]};
+    const double Ql[3][3] = {{m[4], m[5], m[6]}, {m[5], m[7], m[8]}, {m[6], m[8], m[9]}};
+    const double Gd[3] = {gdip[s], gdip[n_pad + s], gdip[2 * n_pad + s]};
+    const double g6[6] = {gquad[s], gquad[n_pad + s], gquad[2 * n_pad + s], gquad[3 * n_pad + s],
+                          gquad[4 * n_pad + s], gquad[5 * n_pad + s]};
+    const double GQ[3][3] = {{g6[0], g6[1], g6[2]}, {g6[1], g6[3], g6[4]}, {g6[2], g6[4], g6[5]}};
+    double RQ[3][3], dR[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) RQ[a][b] = R[a][0] * Ql[0][b] + R[a][1] * Ql[1][b] + R[a][2] * Ql[2][b];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            dR[a][b] = Gd[a] * dl[b] + 2.0 * (GQ[a][0] * RQ[0][b] + GQ[a][1] * RQ[1][b] + GQ[a][2] * RQ[2][b]);
+    double gx[3], gy[3], gz[3], xa[3], za[3];
+    for (int a = 0; a < 3; ++a) {
+        gx[a] = dR[a][0]; gy[a] = dR[a][1]; gz[a] = dR[a][2];
+        xa[a] = R[a][0]; za[a] = R[a][2];
+    }
+    double t[3];
+    cross3(gy, za, t);
+    for (int a = 0; a < 3; ++a) gx[a] += t[a];
+    cross3(xa, gy, t);
+    for (int a = 0; a < 3; ++a) gz[a] += t[a];
+    const double *vz = fvec + 6 * s, *vx = fvec + 6 * s + 3;
+    double g_vz[3], g_vx[3];
+    if (type == AP_FRAME_Z_THEN_X) {
+        const double vxz = dot3(vx, za);
+        double w[3];
+        for (int a = 0; a < 3; ++a) w[a] = vx[a] - vxz * za[a];
+        const double nw = sqrt(dot3(w, w)), nz = sqrt(dot3(vz, vz));
+        const double gxx = dot3(gx, xa);
+        double gw[3];
+        for (int a = 0; a < 3; ++a) gw[a] = (gx[a] - gxx * xa[a]) / nw;
+        const double gwz = dot3(gw, za);
+        for (int a = 0; a < 3; ++a) {
+            g_vx[a] = gw[a] - gwz * za[a];
+            gz[a] = gz[a] - gwz * vx[a] - vxz * gw[a];
+        }
+        const double gzz = dot3(gz, za);
+        for (int a = 0; a < 3; ++a) g_vz[a] = (gz[a] - gzz * za[a]) / nz;
+    } else {
+        const double n1 = sqrt(dot3(vz, vz)), n2 = sqrt(dot3(vx, vx));
+        double u1[3], u2[3], sv[3], w[3];
+        for (int a = 0; a < 3; ++a) { u1[a] = vz[a] / n1; u2[a] = vx[a] / n2; sv[a] = u1[a] + u2[a]; }
+        const double u2z = dot3(u2, za);
+        for (int a = 0; a < 3; ++a) w[a] = u2[a] - u2z * za[a];
+        const double nw = sqrt(dot3(w, w)), ns = sqrt(dot3(sv, sv));
+        const double gxx = dot3(gx, xa);
+        double gw[3], gu2[3], gs[3];
+        for (int a = 0; a < 3; ++a) gw[a] = (gx[a] - gxx * xa[a]) / nw;
+        const double gwz = dot3(gw, za);
+        for (int a = 0; a < 3; ++a) {
+            gu2[a] = gw[a] - gwz * za[a];
+            gz[a] = gz[a] - gwz * u2[a] - u2z * gw[a];
+        }
+        const double gzz = dot3(gz, za);
+        for (int a = 0; a < 3; ++a) gs[a] = (gz[a] - gzz * za[a]) / ns;
+        for (int a = 0; a < 3; ++a) gu2[a] += gs[a];
+        const double a1 = dot3(gs, u1), a2 = dot3(gu2, u2);
+        for (int a = 0; a < 3; ++a) {
+            g_vz[a] = (gs[a] - a1 * u1[a]) / n1;
+            g_vx[a] = (gu2[a] - a2 * u2[a]) / n2;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        atomicAdd(frc + a * n_pad + zs, -g_vz[a]);
+        atomicAdd(frc + a * n_pad + xs, -g_vx[a]);
+        atomicAdd(frc + a * n_pad + s, g_vz[a] + g_vx[a]);
+    }
+}
+
+template <class T>
+__global__ void k_mu_load(const double *__restrict__ mu_in, const int *__restrict__ perm, int n, int n_pad,
+                          double *__restrict__ mu_s, typename V4<T>::type *__restrict__ p) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    double m[3] = {0, 0, 0};
+    if (s < n) {
+        int i = perm[s];
+        for (int c = 0; c < 3; ++c) m[c] = mu_in[3 * i + c];
+    }
+    for (int c = 0; c < 3; ++c) mu_s[c * n_pad + s] = m[c];
+    typename V4<T>::type v;
+    v.x = (T)m[0]; v.y = (T)m[1]; v.z = (T)m[2]; v.w = (T)0;
+    p[s] = v;
+}
+
+__global__ void k_energy(const double *__restrict__ mu, const double *__restrict__ E, int n_pad, double scale,
+                         double *__restrict__ out) {
+    __shared__ double sm[8];
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (s < n_pad)
+        for (int c = 0; c < 3; ++c) v += mu[c * n_pad + s] * E[c * n_pad + s];
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
+        atomicAdd(out, scale * t);
+    }
+}
+
+template <class T>
+int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
+    typedef typename V4<T>::type T4;
+    cudaStream_t s = ctx->s0;
+    const int n = ctx->n, n_pad = ctx->n_pad;
+    const double f = AP_COULOMB;
+    const double self_coef = 4.0 * std::pow(ctx->prm.ewald_beta, 3) / (3.0 * AP_SQRT_PI);
+    k_mu_load<T><<<ap_grid_for(n_pad, 256), 256, 0, s>>>(d_mu, ctx->perm, n, n_pad, ctx->mu_s, (T4 *)ctx->p);
+    AP_CUDA(cudaMemsetAsync(ctx->frc, 0, sizeof(double) * 3 * n_pad, s));
+    AP_CUDA(cudaMemsetAsync(ctx->gdip, 0, sizeof(double) * 3 * n_pad, s));
+    AP_CUDA(cudaMemsetAsync(ctx->gquad, 0, sizeof(double) * 6 * n_pad, s));
+    AP_CUDA(cudaMemsetAsync(ctx->red + 8, 0, sizeof(double), s));
+    // energy
+    k_energy<<<ap_grid_for(n_pad, 256), 256, 0, s>>>(ctx->mu_s, ctx->E, n_pad, -0.5 * f, ctx->red + 8);
+    // real space
+    PairConsts<T> pc;
+    {
+        const ap_params &P = ctx->prm;
+        const double b = P.ewald_beta;
+        pc.beta = (T)b;
+        pc.c[0] = 0;
+        for (int k = 1; k <= 4; ++k) pc.c[k] = (T)(std::pow(2.0 * b * b, k) / (b * AP_SQRT_PI));
+        pc.thole_a = (T)P.thole_a;
+        pc.rc2 = (T)(P.cutoff * P.cutoff);
+        for (int dd = 0; dd < 3; ++dd) { pc.L[dd] = (T)P.box[dd]; pc.iL[dd] = (T)(1.0 / P.box[dd]); }
+        pc.n = n;
+    }
+    auto kern = ctx->minimg ? k_pair_forces<T, true> : k_pair_forces<T, false>;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+    int grid = std::max(1, per_sm) * ctx->sm_count;
+    kern<<<grid, 128, 0, s>>>(ctx->tiles, ctx->tshift, ctx->tile_excl, ctx->excl_mask, ctx->n_tiles,
+                              (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
+                              (const T4 *)ctx->quad1, (const T4 *)ctx->p, ctx->frc, ctx->gdip, ctx->gquad, n_pad,
+                              pc, f);
+    AP_CUDA(cudaGetLastError());
+    // reciprocal space
+    int rc = pme_forces_derivs(ctx, ctx->p, ctx->gbuf, s);
+    if (rc) return rc;
+    k_recip_forces<T><<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gbuf, ctx->mu_s, (const T4 *)ctx->posq,
+                                                         (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
+                                                         (const T4 *)ctx->quad1, n, n_pad, f, self_coef, ctx->frc,
+                                                         ctx->gdip, ctx->gquad);
+    k_frame_forces<<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gdip, ctx->gquad, ctx->rot, ctx->mpl, ctx->fvec,
+                                                       ctx->frame_s, n, n_pad, ctx->frc);
+    AP_CUDA(cudaGetLastError());
+    unsort3(ctx, ctx->frc, d_forces, s);
+    AP_CUDA(cudaMemcpyAsync(d_energy, ctx->red + 8, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+}  // namespace
+
+int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
+    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, d_mu, d_energy, d_forces)
+                                : forces_t<float>(ctx, d_mu, d_energy, d_forces);
+}

@@ -1,0 +1,54 @@
+// Radial functions of one atom pair, shared by the real-space tile kernels.
+//
+// Screened:  B_0 = erfc(beta r)/r,  B_n = [(2n-1) B_{n-1} + (2 beta^2)^n e^{-beta^2 r^2}/(beta sqrt(pi))] / r^2
+// Coulomb:   U_n = (2n-1)!! / r^(2n+1)
+// Thole:     s = a r^3 / sqrt(alpha_i alpha_j),  1 - lambda_3 = e^-s, 1 - lambda_5 = (1+s) e^-s,
+//            1 - lambda_7 = (1 + s + 3/5 s^2) e^-s, 1 - lambda_9 = (1 + s + 18/35 s^2 + 9/35 s^3) e^-s
+// Kernel:    R_n = B_n - (1 - sigma lambda_{2n+1}) U_n  (sigma = 1, or 0 for excluded pairs)
+#pragma once
+#include <cuda_runtime.h>
+
+__device__ __forceinline__ float ap_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double ap_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float ap_exp(float x) { return expf(x); }
+__device__ __forceinline__ double ap_exp(double x) { return exp(x); }
+__device__ __forceinline__ float ap_erfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double ap_erfc(double x) { return erfc(x); }
+__device__ __forceinline__ float ap_rint(float x) { return rintf(x); }
+__device__ __forceinline__ double ap_rint(double x) { return rint(x); }
+
+template <class T>
+struct PairConsts {
+    T beta;            // Ewald beta
+    T c[5];            // c[n] = (2 beta^2)^n / (beta sqrt(pi)), n = 1..4 (c[0] unused)
+    T thole_a;
+    T rc2;             // cutoff^2
+    T L[3], iL[3];     // box and its inverse
+    int n;             // real atoms; slots >= n are padding
+};
+
+// Screened B_1..B_nmax and Coulomb U_1..U_nmax at r (rinv = 1/r, rinv2 = 1/r^2).
+template <class T, int NMAX>
+__device__ __forceinline__ void screened(const PairConsts<T> &pc, T r, T rinv, T rinv2, T *B, T *U) {
+    T x = pc.beta * r;
+    T e2 = ap_exp(-x * x);
+    T b = ap_erfc(x) * rinv;
+    T u = rinv;
+#pragma unroll
+    for (int k = 1; k <= NMAX; ++k) {
+        b = (T(2 * k - 1) * b + pc.c[k] * e2) * rinv2;
+        u = T(2 * k - 1) * u * rinv2;
+        B[k - 1] = b;
+        U[k - 1] = u;
+    }
+}
+
+// 1 - lambda_{2k+1} for k = 1..NMAX from the Thole argument s
+template <class T, int NMAX>
+__device__ __forceinline__ void thole_oml(T s, T *oml) {
+    T e = ap_exp(-s);
+    oml[0] = e;
+    if (NMAX > 1) oml[1] = (T(1) + s) * e;
+    if (NMAX > 2) oml[2] = (T(1) + s + T(0.6) * s * s) * e;
+    if (NMAX > 3) oml[3] = (T(1) + s + s * s * (T(18.0 / 35.0) + T(9.0 / 35.0) * s)) * e;
+}

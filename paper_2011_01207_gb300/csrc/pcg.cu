@@ -1,0 +1,405 @@
+// a4 + a7 - Initial guess and the preconditioned conjugate gradient (paper Sec. 1.3: PCG with
+// one polarization matrix-vector product per iteration; Sec. 3: diagonal preconditioner,
+// threshold 1e-5).
+//
+//   mu_0 = guess (default alpha E);  r_0 = E - A mu_0;  z_0 = alpha r_0;  p_0 = z_0
+//   loop:  q = A p;  gamma = (r.z)/(p.q);  mu += gamma p;  r -= gamma q;  z = alpha r
+//          eps = 4.80321 sqrt(sum |z|^2 / n);  stop if eps <= tol
+//          beta = (r.z)_new/(r.z)_old;  p = z + beta p
+// with A = alpha^-1 - T and T p = T_real p (blocked pair kernel) + T_rec p (PME) + self p.
+//
+// Vectors mu, r, q are FP64; the search direction p is stored in T for the pair and PME
+// kernels; dot products and norms are FP64 block reductions finished with FP64 atomics.
+// The convergence test runs on the device: the update kernel's last block decides, and
+// inside a CUDA graph it drives a conditional WHILE node, so a whole solve is one graph
+// launch with no host round trip per iteration (the paper's host-synchronous loop is what
+// made DHFR drop to 12 ns/day, Sec. 3).
+#include "common.cuh"
+
+#include <cmath>
+
+void unsort3(ap_ctx *ctx, const double *src, double *out, cudaStream_t s);
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// block-wide sum of two values, lane 0 of warp 0 returns them
+template <int NT>
+__device__ __forceinline__ void block_sum2(double &a, double &b) {
+    __shared__ double sa[NT / 32], sb[NT / 32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = l < NT / 32 ? sa[l] : 0.0;
+        b = l < NT / 32 ? sb[l] : 0.0;
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
+}
+
+constexpr int NT = 256;
+
+// mu_0 and the matvec input p := mu_0 (caller-order guess gathered into slots)
+template <class T>
+__global__ void k_init_guess(const double *__restrict__ guess, const double *__restrict__ E,
+                             const double *__restrict__ alpha, const int *__restrict__ perm, int n, int n_pad,
+                             double *__restrict__ mu, typename V4<T>::type *__restrict__ p) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    double m[3] = {0.0, 0.0, 0.0};
+    if (s < n) {
+        if (guess) {
+            int i = perm[s];
+            for (int c = 0; c < 3; ++c) m[c] = guess[3 * i + c];
+        } else {
+            for (int c = 0; c < 3; ++c) m[c] = alpha[s] * E[c * n_pad + s];
+        }
+    }
+    for (int c = 0; c < 3; ++c) mu[c * n_pad + s] = m[c];
+    typename V4<T>::type v;
+    v.x = (T)m[0]; v.y = (T)m[1]; v.z = (T)m[2]; v.w = (T)0;
+    p[s] = v;
+}
+
+// r_0 = E - A mu_0, partial sums of r.z and z.z; clears acc and p
+template <class T>
+__global__ void k_init_residual(const double *__restrict__ E, const double *__restrict__ alpha,
+                                const double *__restrict__ mu, double *__restrict__ acc,
+                                const T *__restrict__ rec, double self_coef, int n_pad, double *__restrict__ r,
+                                typename V4<T>::type *__restrict__ p, PcgState *st) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double rz = 0.0, zz = 0.0;
+    if (s < n_pad) {
+        const double a = alpha[s];
+        for (int c = 0; c < 3; ++c) {
+            const int k = c * n_pad + s;
+            double Amu = a > 0.0 ? mu[k] / a - acc[k] - (double)rec[k] - self_coef * mu[k] : 0.0;
+            double rr = a > 0.0 ? E[k] - Amu : 0.0;
+            r[k] = rr;
+            acc[k] = 0.0;
+            rz += rr * a * rr;
+            zz += a * rr * a * rr;
+        }
+        typename V4<T>::type v;
+        v.x = v.y = v.z = v.w = (T)0;
+        p[s] = v;
+    }
+    block_sum2<NT>(rz, zz);
+    if (threadIdx.x == 0) {
+        atomicAdd(&st->rz_new, rz);
+        atomicAdd(&st->zz, zz);
+    }
+}
+
+__global__ void k_init_finish(PcgState *st, int n, double tol, int max_iter) {
+    double eps = AP_DEBYE * sqrt(st->zz / n);
+    st->rz = st->rz_new;
+    st->eps = eps;
+    st->eps0 = eps;
+    st->tol = tol;
+    st->iter = 0;
+    st->max_iter = max_iter;
+    st->beta = 0.0;
+    st->gamma = 0.0;
+    st->nonfinite = !isfinite(eps);
+    st->done = (eps <= tol) || st->nonfinite;
+    st->status = AP_OK;
+    st->pq = st->rz_new = st->zz = 0.0;
+    st->blocks_done = 0;
+    st->guard = 0;
+}
+
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const PcgState *st) {
+    cudaGraphSetConditional(h, (st->done || st->max_iter < 1) ? 0u : 1u);
+}
+
+// last node of every loop iteration: continue only while not done, and never beyond
+// max_iter iterations whatever the update kernel did (the WHILE node cannot spin forever)
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, PcgState *st) {
+    st->guard += 1;
+    const bool more = !st->done && st->guard < st->max_iter;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// p = alpha r + beta p
+template <class T>
+__global__ void k_direction(const double *__restrict__ r, const double *__restrict__ alpha, int n_pad,
+                            typename V4<T>::type *__restrict__ p, const PcgState *__restrict__ st) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    const double b = st->beta, a = alpha[s];
+    typename V4<T>::type v = p[s];
+    v.x = (T)(a * r[s] + b * (double)v.x);
+    v.y = (T)(a * r[n_pad + s] + b * (double)v.y);
+    v.z = (T)(a * r[2 * n_pad + s] + b * (double)v.z);
+    p[s] = v;
+}
+
+// q = A p = p/alpha - T_real p - T_rec p - self p; partial p.q; clears acc
+template <class T>
+__global__ void k_apply(const typename V4<T>::type *__restrict__ p, const double *__restrict__ alpha,
+                        double *__restrict__ acc, const T *__restrict__ rec, double self_coef, int n_pad,
+                        double *__restrict__ q, PcgState *st) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double pq = 0.0, dummy = 0.0;
+    if (s < n_pad) {
+        const double a = alpha[s];
+        typename V4<T>::type v = p[s];
+        const double pv[3] = {(double)v.x, (double)v.y, (double)v.z};
+        for (int c = 0; c < 3; ++c) {
+            const int k = c * n_pad + s;
+            double qq = a > 0.0 ? pv[c] / a - acc[k] - (double)rec[k] - self_coef * pv[c] : 0.0;
+            q[k] = qq;
+            acc[k] = 0.0;
+            pq += pv[c] * qq;
+        }
+    }
+    block_sum2<NT>(pq, dummy);
+    if (threadIdx.x == 0) atomicAdd(&st->pq, pq);
+}
+
+// mu += gamma p; r -= gamma q; partial r.z, z.z; the last block closes the iteration
+template <class T>
+__global__ void k_update(const typename V4<T>::type *__restrict__ p, const double *__restrict__ q,
+                         const double *__restrict__ alpha, int n, int n_pad, double *__restrict__ mu,
+                         double *__restrict__ r, PcgState *st) {
+    __shared__ bool last;
+    const double gamma = st->rz / st->pq;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double rz = 0.0, zz = 0.0;
+    if (s < n_pad) {
+        const double a = alpha[s];
+        typename V4<T>::type v = p[s];
+        const double pv[3] = {(double)v.x, (double)v.y, (double)v.z};
+        for (int c = 0; c < 3; ++c) {
+            const int k = c * n_pad + s;
+            mu[k] += gamma * pv[c];
+            const double rr = r[k] - gamma * q[k];
+            r[k] = rr;
+            rz += rr * a * rr;
+            zz += a * rr * a * rr;
+        }
+    }
+    block_sum2<NT>(rz, zz);
+    if (threadIdx.x == 0) {
+        atomicAdd(&st->rz_new, rz);
+        atomicAdd(&st->zz, zz);
+        __threadfence();
+        unsigned prev = atomicAdd(&st->blocks_done, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        volatile PcgState *vs = st;
+        const double rzn = vs->rz_new, zzt = vs->zz;
+        const double eps = AP_DEBYE * sqrt(zzt / n);
+        st->gamma = gamma;
+        st->iter += 1;
+        st->eps = eps;
+        const bool bad = !isfinite(eps) || !isfinite(gamma);
+        if (bad) st->nonfinite = 1;
+        if (eps <= st->tol || bad) {
+            st->done = 1;
+            st->status = AP_OK;
+        } else if (st->iter >= st->max_iter) {
+            st->done = 1;
+            st->status = AP_NOT_CONVERGED;
+        }
+        st->beta = rzn / st->rz;
+        st->rz = rzn;
+        st->pq = 0.0;
+        st->rz_new = 0.0;
+        st->zz = 0.0;
+        st->blocks_done = 0;
+    }
+}
+
+template <class T>
+int matvec_into(ap_ctx *ctx, const void *p) {
+    // reciprocal branch on s1, real space on s0, joined before the caller continues
+    AP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->s0));
+    AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
+    int rc = pme_dipole_field(ctx, p, ctx->s1);
+    if (rc) return rc;
+    rc = real_matvec_launch(ctx, p, ctx->s0);
+    if (rc) return rc;
+    AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));
+    AP_CUDA(cudaStreamWaitEvent(ctx->s0, ctx->ev_join, 0));
+    return AP_OK;
+}
+
+double self_coef(const ap_ctx *ctx) { return 4.0 * std::pow(ctx->prm.ewald_beta, 3) / (3.0 * AP_SQRT_PI); }
+
+template <class T>
+int enqueue_iteration(ap_ctx *ctx, cudaGraphConditionalHandle h, int use_cond) {
+    typedef typename V4<T>::type T4;
+    const int nb = ap_grid_for(ctx->n_pad, NT);
+    k_direction<T><<<nb, NT, 0, ctx->s0>>>(ctx->r, ctx->alpha, ctx->n_pad, (T4 *)ctx->p, ctx->st);
+    AP_CUDA(cudaGetLastError());
+    int rc = matvec_into<T>(ctx, ctx->p);
+    if (rc) return rc;
+    k_apply<T><<<nb, NT, 0, ctx->s0>>>((const T4 *)ctx->p, ctx->alpha, ctx->acc, (const T *)ctx->rec,
+                                        self_coef(ctx), ctx->n_pad, ctx->qv, ctx->st);
+    k_update<T><<<nb, NT, 0, ctx->s0>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n, ctx->n_pad, ctx->mu,
+                                         ctx->r, ctx->st);
+    if (use_cond) k_loop_cond<<<1, 1, 0, ctx->s0>>>(h, ctx->st);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+// the solve loop as one graph: [set condition] -> WHILE { one iteration }
+template <class T>
+int build_graph(ap_ctx *ctx) {
+    ctx->graph_tried = 1;
+    cudaGraph_t g = nullptr;
+    AP_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return AP_OK;
+    }
+    cudaKernelNodeParams kp = {};
+    const PcgState *stp = ctx->st;
+    void *args[2] = {(void *)&h, (void *)&stp};
+    kp.func = (void *)k_set_cond;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    cudaGraphNode_t n_set, n_while;
+    AP_CUDA(cudaGraphAddKernelNode(&n_set, g, nullptr, 0, &kp));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    AP_CUDA(cudaGraphAddNode(&n_while, g, &n_set, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    AP_CUDA(cudaStreamBeginCaptureToGraph(ctx->s0, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_iteration<T>(ctx, h, 1);
+    cudaGraph_t captured = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(ctx->s0, &captured);
+    if (rc || ec != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        ctx->err.clear();
+        return AP_OK;      // fall back to the host loop
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return AP_OK;
+    }
+    cudaGraphDestroy(g);
+    ctx->solve_exec = ex;
+    ctx->graph_ok = 1;
+    return AP_OK;
+}
+
+template <class T>
+int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double *d_mu, ap_solve_info *info) {
+    typedef typename V4<T>::type T4;
+    const int nb = ap_grid_for(ctx->n_pad, NT);
+    cudaStream_t s = ctx->s0;
+    AP_CUDA(cudaMemsetAsync(ctx->st, 0, sizeof(PcgState), s));
+    AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, s));
+    k_init_guess<T><<<nb, NT, 0, s>>>(d_guess, ctx->E, ctx->alpha, ctx->perm, ctx->n, ctx->n_pad, ctx->mu,
+                                       (T4 *)ctx->p);
+    AP_CUDA(cudaGetLastError());
+    int rc = matvec_into<T>(ctx, ctx->p);
+    if (rc) return rc;
+    k_init_residual<T><<<nb, NT, 0, s>>>(ctx->E, ctx->alpha, ctx->mu, ctx->acc, (const T *)ctx->rec,
+                                          self_coef(ctx), ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->st);
+    k_init_finish<<<1, 1, 0, s>>>(ctx->st, ctx->n, tol, max_iter);
+    AP_CUDA(cudaGetLastError());
+    if (!ctx->graph_tried) {
+        rc = build_graph<T>(ctx);
+        if (rc) return rc;
+    }
+    if (ctx->graph_ok) {
+        AP_CUDA(cudaGraphLaunch(ctx->solve_exec, s));
+    } else {
+        // host-driven loop: one status read per iteration
+        for (int it = 0; it < max_iter; ++it) {
+            AP_CUDA(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+            AP_CUDA(cudaStreamSynchronize(s));
+            if (ctx->st_host->done) break;
+            rc = enqueue_iteration<T>(ctx, 0, 0);
+            if (rc) return rc;
+        }
+    }
+    unsort3(ctx, ctx->mu, d_mu, s);
+    AP_CUDA(cudaGetLastError());
+    if (info) {
+        AP_CUDA(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+        AP_CUDA(cudaStreamSynchronize(s));
+        info->iterations = ctx->st_host->iter;
+        info->eps_debye = ctx->st_host->eps;
+        info->eps_initial = ctx->st_host->eps0;
+        info->status = ctx->st_host->status;
+        if (ctx->st_host->nonfinite) return ap_fail(ctx, AP_ERR_NONFINITE, "non-finite value in the PCG reductions");
+        return ctx->st_host->status;
+    }
+    return AP_OK;
+}
+
+}  // namespace
+
+int pcg_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double *d_mu, ap_solve_info *info) {
+    return ctx->prec == AP_FP64 ? solve_t<double>(ctx, d_guess, tol, max_iter, d_mu, info)
+                                : solve_t<float>(ctx, d_guess, tol, max_iter, d_mu, info);
+}
+
+// a plain T p for tests: out[n][3] (caller order) = (T_real + T_rec + self) applied to v
+template <class T>
+__global__ void k_load_vec(const double *__restrict__ v, const int *__restrict__ perm, int n, int n_pad,
+                           typename V4<T>::type *__restrict__ p) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    typename V4<T>::type w;
+    w.x = w.y = w.z = w.w = (T)0;
+    if (s < n) {
+        int i = perm[s];
+        w.x = (T)v[3 * i]; w.y = (T)v[3 * i + 1]; w.z = (T)v[3 * i + 2];
+    }
+    p[s] = w;
+}
+
+template <class T>
+__global__ void k_tp_out(const typename V4<T>::type *__restrict__ p, const double *__restrict__ acc,
+                         const T *__restrict__ rec, double self_coef, int n_pad, double *__restrict__ out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    typename V4<T>::type v = p[s];
+    const double pv[3] = {(double)v.x, (double)v.y, (double)v.z};
+    for (int c = 0; c < 3; ++c) out[c * n_pad + s] = acc[c * n_pad + s] + (double)rec[c * n_pad + s] + self_coef * pv[c];
+}
+
+template <class T>
+int apply_t(ap_ctx *ctx, const double *d_v, double *d_out) {
+    typedef typename V4<T>::type T4;
+    const int nb = ap_grid_for(ctx->n_pad, NT);
+    AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+    k_load_vec<T><<<nb, NT, 0, ctx->s0>>>(d_v, ctx->perm, ctx->n, ctx->n_pad, (T4 *)ctx->p);
+    int rc = matvec_into<T>(ctx, ctx->p);
+    if (rc) return rc;
+    k_tp_out<T><<<nb, NT, 0, ctx->s0>>>((const T4 *)ctx->p, ctx->acc, (const T *)ctx->rec, self_coef(ctx),
+                                         ctx->n_pad, ctx->qv);
+    unsort3(ctx, ctx->qv, d_out, ctx->s0);
+    AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+int dipole_field_apply(ap_ctx *ctx, const double *d_v, double *d_out) {
+    return ctx->prec == AP_FP64 ? apply_t<double>(ctx, d_v, d_out) : apply_t<float>(ctx, d_v, d_out);
+}

@@ -1,0 +1,412 @@
+// a3 / a6 - Smooth particle-mesh Ewald (paper Sec. 1.2.2, "Reciprocal space scheme": spread
+// the multipolar density with order-5 B-splines, forward FFT, product with the reciprocal
+// kernel, backward FFT, gather with B-spline derivatives; Fig. reci_scheme: atomics on
+// the grid). FFTs are cuFFT; spread, convolution and gather are the kernels below.
+//
+// Conventions (shared with the oracle by definition, not by code):
+//   u_a = K_a x_a / L_a, b = floor(u_a), w = u_a - b; stencil points k = (b - t) mod K_a,
+//   t = 0..4, weight M_5(w + t); a site spreads (q + d.grad + (1/3) Q:grad grad) of its
+//   weights, each Cartesian derivative being (K_a / L_a) d/du_a;
+//   phi_grid = C2R[ B(m) C(m) R2C[Q] ] (cuFFT's unnormalised inverse);
+//   C(m) = exp(-pi^2 |m|^2 / beta^2) / (pi V |m|^2), C(0) = 0, m aliased to [-K/2, K/2);
+//   B(m) = prod_a |b_a(m_a)|^2, |b(m)|^2 = 1/|sum_{k=0}^{3} M_5(k+1) e^{2 pi i m k / K}|^2,
+//   replaced by the mean of its neighbours where the sum vanishes (m = K/2).
+// Grid layout: [z][y][x], x contiguous; complex half grid [z][y][x/2+1].
+#include "common.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace {
+
+template <class T>
+struct Stencil {
+    int k[3][5];        // grid indices per dimension
+    T th[3][5];         // M_5(w + t)
+    T d1[3][5];         // first u-derivative
+    T d2[3][5];         // second
+    T d3[3][5];         // third
+};
+
+// B-spline values of orders 2..5 at w + t, t = 0..4, by the two-term recursion
+// M_n(x) = [x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)] / (n - 1), starting from M_1 = 1 on [0,1).
+template <class T, int NDER>
+__device__ __forceinline__ void bspline5(T w, T *th, T *d1, T *d2, T *d3) {
+    T m[4][6];           // m[n-2][t+1] = M_n(w + t), with m[.][0] = M_n(w - 1) = 0
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int t = 0; t < 6; ++t) m[a][t] = T(0);
+    // M_2(w + t): t = 0 -> w, t = 1 -> 1 - w
+    m[0][1] = w;
+    m[0][2] = T(1) - w;
+#pragma unroll
+    for (int n = 3; n <= 5; ++n) {
+        const T inv = T(1) / T(n - 1);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            const T x = w + T(t);
+            m[n - 2][t + 1] = (x * m[n - 3][t + 1] + (T(n) - x) * m[n - 3][t]) * inv;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        th[t] = m[3][t + 1];
+        if (NDER >= 1) d1[t] = m[2][t + 1] - m[2][t];
+        if (NDER >= 2) d2[t] = m[1][t + 1] - T(2) * m[1][t] + (t >= 1 ? m[1][t - 1] : T(0));
+        if (NDER >= 3)
+            d3[t] = m[0][t + 1] - T(3) * m[0][t] + (t >= 1 ? T(3) * m[0][t - 1] : T(0)) -
+                    (t >= 2 ? m[0][t - 2] : T(0));
+    }
+}
+
+template <class T>
+struct PmeConsts {
+    int K[3];
+    T s[3];           // K_a / L_a
+    int n;
+};
+
+template <class T, int NDER>
+__device__ __forceinline__ void make_stencil(const PmeConsts<T> &pc, T x, T y, T z, Stencil<T> &st) {
+    T xyz[3] = {x, y, z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        T u = xyz[d] * pc.s[d];
+        T b = floor(u);
+        T w = u - b;
+        int K = pc.K[d];
+        int ib = (int)b % K;
+        if (ib < 0) ib += K;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            int k = ib - t;
+            st.k[d][t] = k < 0 ? k + K : k;
+        }
+        bspline5<T, NDER>(w, st.th[d], st.d1[d], st.d2[d], st.d3[d]);
+    }
+}
+
+// spread permanent multipoles (q, d, Q) ------------------------------------------------
+template <class T>
+__global__ void k_spread_multipoles(const typename V4<T>::type *__restrict__ posq,
+                                    const typename V4<T>::type *__restrict__ dipd,
+                                    const typename V4<T>::type *__restrict__ quad0,
+                                    const typename V4<T>::type *__restrict__ quad1, T *__restrict__ grid,
+                                    PmeConsts<T> pc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pc.n) return;
+    typename V4<T>::type a = posq[i], b = dipd[i], c = quad0[i], d = quad1[i];
+    Stencil<T> st;
+    make_stencil<T, 2>(pc, a.x, a.y, a.z, st);
+    const T sx = pc.s[0], sy = pc.s[1], sz = pc.s[2];
+    const T q = a.w, dx = b.x * sx, dy = b.y * sy, dz = b.z * sz;
+    const T third = T(1.0 / 3.0);
+    const T Qxx = c.x * sx * sx * third, Qyy = c.w * sy * sy * third, Qzz = d.y * sz * sz * third;
+    const T Qxy = c.y * sx * sy * T(2.0 / 3.0), Qxz = c.z * sx * sz * T(2.0 / 3.0), Qyz = d.x * sy * sz * T(2.0 / 3.0);
+    const int Kx = pc.K[0], Ky = pc.K[1];
+#pragma unroll 1
+    for (int t3 = 0; t3 < 5; ++t3) {
+        const T z0 = st.th[2][t3], z1 = st.d1[2][t3], z2 = st.d2[2][t3];
+#pragma unroll 1
+        for (int t2 = 0; t2 < 5; ++t2) {
+            const T y0 = st.th[1][t2], y1 = st.d1[1][t2], y2 = st.d2[1][t2];
+            const T A = q * y0 * z0 + dy * y1 * z0 + dz * y0 * z1 + Qyy * y2 * z0 + Qzz * y0 * z2 + Qyz * y1 * z1;
+            const T Bc = dx * y0 * z0 + Qxy * y1 * z0 + Qxz * y0 * z1;
+            const T Cc = Qxx * y0 * z0;
+            T *row = grid + ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
+#pragma unroll
+            for (int t1 = 0; t1 < 5; ++t1)
+                atomicAdd(row + st.k[0][t1], st.th[0][t1] * A + st.d1[0][t1] * Bc + st.d2[0][t1] * Cc);
+        }
+    }
+}
+
+// spread induced dipoles p --------------------------------------------------------------
+template <class T>
+__global__ void k_spread_dipoles(const typename V4<T>::type *__restrict__ posq,
+                                 const typename V4<T>::type *__restrict__ pv, T *__restrict__ grid,
+                                 PmeConsts<T> pc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pc.n) return;
+    typename V4<T>::type a = posq[i], b = pv[i];
+    Stencil<T> st;
+    make_stencil<T, 1>(pc, a.x, a.y, a.z, st);
+    const T px = b.x * pc.s[0], py = b.y * pc.s[1], pz = b.z * pc.s[2];
+    const int Kx = pc.K[0], Ky = pc.K[1];
+#pragma unroll 1
+    for (int t3 = 0; t3 < 5; ++t3) {
+        const T z0 = st.th[2][t3], z1 = st.d1[2][t3];
+#pragma unroll
+        for (int t2 = 0; t2 < 5; ++t2) {
+            const T y0 = st.th[1][t2], y1 = st.d1[1][t2];
+            const T A = py * y1 * z0 + pz * y0 * z1;
+            const T Bc = px * y0 * z0;
+            T *row = grid + ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
+#pragma unroll
+            for (int t1 = 0; t1 < 5; ++t1) atomicAdd(row + st.k[0][t1], st.th[0][t1] * A + st.d1[0][t1] * Bc);
+        }
+    }
+}
+
+// k-space product with B(m) C(m) ----------------------------------------------------------
+template <class T>
+__global__ void k_convolve(typename FftTypes<T>::cplx *__restrict__ c, const T *__restrict__ green, size_t m) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    T g = green[i];
+    c[i].x *= g;
+    c[i].y *= g;
+}
+
+// gather the field -grad(phi) at every atom ---------------------------------------------
+template <class T>
+__global__ void k_gather_field(const typename V4<T>::type *__restrict__ posq, const T *__restrict__ phi,
+                               T *__restrict__ out, int n_pad, PmeConsts<T> pc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pc.n) return;
+    typename V4<T>::type a = posq[i];
+    Stencil<T> st;
+    make_stencil<T, 1>(pc, a.x, a.y, a.z, st);
+    const int Kx = pc.K[0], Ky = pc.K[1];
+    T gx = 0, gy = 0, gz = 0;
+#pragma unroll 1
+    for (int t3 = 0; t3 < 5; ++t3) {
+        const T z0 = st.th[2][t3], z1 = st.d1[2][t3];
+#pragma unroll
+        for (int t2 = 0; t2 < 5; ++t2) {
+            const T y0 = st.th[1][t2], y1 = st.d1[1][t2];
+            const T *row = phi + ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
+            T s0 = 0, s1 = 0;
+#pragma unroll
+            for (int t1 = 0; t1 < 5; ++t1) {
+                const T v = row[st.k[0][t1]];
+                s0 += st.th[0][t1] * v;
+                s1 += st.d1[0][t1] * v;
+            }
+            gx += s1 * y0 * z0;
+            gy += s0 * y1 * z0;
+            gz += s0 * y0 * z1;
+        }
+    }
+    out[i] = -gx * pc.s[0];
+    out[n_pad + i] = -gy * pc.s[1];
+    out[2 * n_pad + i] = -gz * pc.s[2];
+}
+
+// derivatives of phi up to third order (20 components) for the forces -------------------
+// component order: [0] phi; [1..3] x y z; [4..9] xx yy zz xy xz yz;
+// [10..19] xxx yyy zzz xxy xxz xyy yyz xzz yzz xyz
+template <class T>
+__global__ void k_gather_derivs(const typename V4<T>::type *__restrict__ posq, const T *__restrict__ phi,
+                                double *__restrict__ out, int n_pad, int ncomp, PmeConsts<T> pc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pc.n) return;
+    typename V4<T>::type a = posq[i];
+    Stencil<T> st;
+    make_stencil<T, 3>(pc, a.x, a.y, a.z, st);
+    const int Kx = pc.K[0], Ky = pc.K[1];
+    T D[20];
+#pragma unroll
+    for (int c = 0; c < 20; ++c) D[c] = 0;
+#pragma unroll 1
+    for (int t3 = 0; t3 < 5; ++t3) {
+        const T z[4] = {st.th[2][t3], st.d1[2][t3], st.d2[2][t3], st.d3[2][t3]};
+#pragma unroll 1
+        for (int t2 = 0; t2 < 5; ++t2) {
+            const T y[4] = {st.th[1][t2], st.d1[1][t2], st.d2[1][t2], st.d3[1][t2]};
+            const T *row = phi + ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
+            T S[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int t1 = 0; t1 < 5; ++t1) {
+                const T v = row[st.k[0][t1]];
+                S[0] += st.th[0][t1] * v;
+                S[1] += st.d1[0][t1] * v;
+                S[2] += st.d2[0][t1] * v;
+                S[3] += st.d3[0][t1] * v;
+            }
+            D[0] += S[0] * y[0] * z[0];
+            D[1] += S[1] * y[0] * z[0];
+            D[2] += S[0] * y[1] * z[0];
+            D[3] += S[0] * y[0] * z[1];
+            D[4] += S[2] * y[0] * z[0];
+            D[5] += S[0] * y[2] * z[0];
+            D[6] += S[0] * y[0] * z[2];
+            D[7] += S[1] * y[1] * z[0];
+            D[8] += S[1] * y[0] * z[1];
+            D[9] += S[0] * y[1] * z[1];
+            D[10] += S[3] * y[0] * z[0];
+            D[11] += S[0] * y[3] * z[0];
+            D[12] += S[0] * y[0] * z[3];
+            D[13] += S[2] * y[1] * z[0];
+            D[14] += S[2] * y[0] * z[1];
+            D[15] += S[1] * y[2] * z[0];
+            D[16] += S[0] * y[2] * z[1];
+            D[17] += S[1] * y[0] * z[2];
+            D[18] += S[0] * y[1] * z[2];
+            D[19] += S[1] * y[1] * z[1];
+        }
+    }
+    const T sx = pc.s[0], sy = pc.s[1], sz = pc.s[2];
+    const T f[20] = {1, sx, sy, sz, sx * sx, sy * sy, sz * sz, sx * sy, sx * sz, sy * sz,
+                     sx * sx * sx, sy * sy * sy, sz * sz * sz, sx * sx * sy, sx * sx * sz, sx * sy * sy,
+                     sy * sy * sz, sx * sz * sz, sy * sz * sz, sx * sy * sz};
+    for (int c = 0; c < ncomp; ++c) out[(size_t)c * n_pad + i] = (double)(D[c] * f[c]);
+}
+
+template <class T>
+PmeConsts<T> pme_consts(const ap_ctx *ctx) {
+    PmeConsts<T> pc;
+    for (int d = 0; d < 3; ++d) {
+        pc.K[d] = ctx->K[d];
+        pc.s[d] = (T)(ctx->K[d] / ctx->prm.box[d]);
+    }
+    pc.n = ctx->n;
+    return pc;
+}
+
+// cardinal B-spline M_n(x) on the host (for the moduli), by the same recursion
+double bspline_host(int n, double x) {
+    if (n == 1) return (x >= 0.0 && x < 1.0) ? 1.0 : 0.0;
+    return (x * bspline_host(n - 1, x) + (n - x) * bspline_host(n - 1, x - 1.0)) / (n - 1);
+}
+
+std::vector<double> moduli(int K, int order) {
+    std::vector<double> b(K);
+    std::vector<char> bad(K, 0);
+    for (int m = 0; m < K; ++m) {
+        double re = 0, im = 0;
+        for (int k = 0; k <= order - 2; ++k) {
+            double v = bspline_host(order, k + 1.0);
+            double arg = 2.0 * M_PI * m * k / K;
+            re += v * std::cos(arg);
+            im += v * std::sin(arg);
+        }
+        double den = re * re + im * im;
+        if (den < 1e-10) bad[m] = 1; else b[m] = 1.0 / den;
+    }
+    for (int m = 0; m < K; ++m)
+        if (bad[m]) b[m] = 0.5 * (b[(m + K - 1) % K] + b[(m + 1) % K]);
+    return b;
+}
+
+template <class T>
+int init_t(ap_ctx *ctx) {
+    const int Kx = ctx->K[0], Ky = ctx->K[1], Kz = ctx->K[2];
+    const int hx = Kx / 2 + 1;
+    const ap_params &P = ctx->prm;
+    std::vector<double> bx = moduli(Kx, P.pme_order), by = moduli(Ky, P.pme_order), bz = moduli(Kz, P.pme_order);
+    std::vector<T> g((size_t)Kz * Ky * hx);
+    const double vol = P.box[0] * P.box[1] * P.box[2];
+    const double b2 = P.ewald_beta * P.ewald_beta;
+    for (int iz = 0; iz < Kz; ++iz) {
+        double mz = (iz <= Kz / 2 ? iz : iz - Kz) / P.box[2];
+        if (2 * iz == Kz) mz = -mz;   // K/2 aliases to -K/2 (same |m|)
+        for (int iy = 0; iy < Ky; ++iy) {
+            double my = (iy <= Ky / 2 ? iy : iy - Ky) / P.box[1];
+            for (int ix = 0; ix < hx; ++ix) {
+                double mx = ix / P.box[0];
+                double m2 = mx * mx + my * my + mz * mz;
+                double v = 0.0;
+                if (ix || iy || iz)
+                    v = std::exp(-M_PI * M_PI * m2 / b2) / (M_PI * vol * m2) * bx[ix] * by[iy] * bz[iz];
+                g[((size_t)iz * Ky + iy) * hx + ix] = (T)v;
+            }
+        }
+    }
+    AP_CUDA(cudaMemcpy(ctx->green, g.data(), sizeof(T) * g.size(), cudaMemcpyHostToDevice));
+    bool dbl = sizeof(T) == 8;
+    AP_CUFFT(cufftPlan3d(&ctx->plan_r2c, Kz, Ky, Kx, dbl ? CUFFT_D2Z : CUFFT_R2C));
+    AP_CUFFT(cufftPlan3d(&ctx->plan_c2r, Kz, Ky, Kx, dbl ? CUFFT_Z2D : CUFFT_C2R));
+    return AP_OK;
+}
+
+template <class T>
+int fft_roundtrip(ap_ctx *ctx, T *in, T *out, cudaStream_t s) {
+    typedef typename FftTypes<T>::cplx C;
+    AP_CUFFT(cufftSetStream(ctx->plan_r2c, s));
+    AP_CUFFT(cufftSetStream(ctx->plan_c2r, s));
+    if (sizeof(T) == 8) {
+        AP_CUFFT(cufftExecD2Z(ctx->plan_r2c, (cufftDoubleReal *)in, (cufftDoubleComplex *)ctx->cgrid));
+    } else {
+        AP_CUFFT(cufftExecR2C(ctx->plan_r2c, (cufftReal *)in, (cufftComplex *)ctx->cgrid));
+    }
+    k_convolve<T><<<ap_grid_for((long)ctx->ncgrid, 256), 256, 0, s>>>((C *)ctx->cgrid, (const T *)ctx->green,
+                                                                     ctx->ncgrid);
+    AP_CUDA(cudaGetLastError());
+    if (sizeof(T) == 8) {
+        AP_CUFFT(cufftExecZ2D(ctx->plan_c2r, (cufftDoubleComplex *)ctx->cgrid, (cufftDoubleReal *)out));
+    } else {
+        AP_CUFFT(cufftExecC2R(ctx->plan_c2r, (cufftComplex *)ctx->cgrid, (cufftReal *)out));
+    }
+    return AP_OK;
+}
+
+template <class T>
+int multipole_field_t(ap_ctx *ctx, cudaStream_t s) {
+    typedef typename V4<T>::type T4;
+    PmeConsts<T> pc = pme_consts<T>(ctx);
+    AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
+    k_spread_multipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(
+        (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0, (const T4 *)ctx->quad1,
+        (T *)ctx->grid, pc);
+    AP_CUDA(cudaGetLastError());
+    int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid2, s);
+    if (r) return r;
+    k_gather_field<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid2,
+                                                              (T *)ctx->rec, ctx->n_pad, pc);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+template <class T>
+int dipole_field_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
+    typedef typename V4<T>::type T4;
+    PmeConsts<T> pc = pme_consts<T>(ctx);
+    AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
+    k_spread_dipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)p,
+                                                                (T *)ctx->grid, pc);
+    AP_CUDA(cudaGetLastError());
+    int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
+    if (r) return r;
+    k_gather_field<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid,
+                                                              (T *)ctx->rec, ctx->n_pad, pc);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+// forces: phi_mu derivatives (20 comps, into gbuf[0..19]) and phi_M second derivatives
+// (components 4..9, into gbuf[20..25]); the spread of mu uses ctx->p as scratch.
+template <class T>
+int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
+    typedef typename V4<T>::type T4;
+    PmeConsts<T> pc = pme_consts<T>(ctx);
+    AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
+    k_spread_dipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)mu4,
+                                                                (T *)ctx->grid, pc);
+    AP_CUDA(cudaGetLastError());
+    int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
+    if (r) return r;
+    k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid,
+                                                               gbuf, ctx->n_pad, 20, pc);
+    k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid2,
+                                                               gbuf + (size_t)20 * ctx->n_pad, ctx->n_pad, 10, pc);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+}  // namespace
+
+int pme_init(ap_ctx *ctx) { return ctx->prec == AP_FP64 ? init_t<double>(ctx) : init_t<float>(ctx); }
+
+int pme_multipole_field(ap_ctx *ctx, cudaStream_t s) {
+    return ctx->prec == AP_FP64 ? multipole_field_t<double>(ctx, s) : multipole_field_t<float>(ctx, s);
+}
+
+int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s) {
+    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, s) : dipole_field_t<float>(ctx, p, s);
+}
+
+int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
+    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, mu4, gbuf, s) : forces_t<float>(ctx, mu4, gbuf, s);
+}

@@ -152,3 +152,15 @@ def test_pcg_residual_is_true_residual():
     mu, info = o.pcg(E, tol=1e-6)
     assert info["converged"] and 5 <= info["iters"] <= 30
     assert o.residual_eps(E - o.apply_A(mu)) < 1.01e-6
+
+
+def test_row_fields_match_full_oracle():
+    from paper_2011_01207_gb300 import synth
+    s = synth.water_box(64, 12.5, 5)
+    p = Params(beta=0.5446, cutoff=6.0, grid=(16, 16, 16))
+    o = Oracle(s, p)
+    v = np.random.default_rng(1).normal(size=(s.n, 3))
+    rows = np.array([0, 7, 100, s.n - 1])
+    Er, Tv = model.row_fields(s, p, rows, v)
+    np.testing.assert_allclose(Er, o.permanent_field()[rows], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(Tv, o.apply_T(v)[rows], rtol=0, atol=1e-12)
