@@ -222,35 +222,39 @@ __global__ void k_update(const typename V4<T>::type *__restrict__ p, const doubl
     }
 }
 
+// T p: reciprocal branch on `aux`, real space on `main`, joined back into `main`
 template <class T>
-int matvec_into(ap_ctx *ctx, const void *p) {
-    // reciprocal branch on s1, real space on s0, joined before the caller continues
-    AP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->s0));
-    AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
-    int rc = pme_dipole_field(ctx, p, ctx->s1);
+int matvec_into(ap_ctx *ctx, const void *p, cudaStream_t main, cudaStream_t aux) {
+    AP_CUDA(cudaEventRecord(ctx->ev_fork, main));
+    AP_CUDA(cudaStreamWaitEvent(aux, ctx->ev_fork, 0));
+    int rc = pme_dipole_field(ctx, p, aux);
     if (rc) return rc;
-    rc = real_matvec_launch(ctx, p, ctx->s0);
+    rc = real_matvec_launch(ctx, p, main);
     if (rc) return rc;
-    AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));
-    AP_CUDA(cudaStreamWaitEvent(ctx->s0, ctx->ev_join, 0));
+    AP_CUDA(cudaEventRecord(ctx->ev_join, aux));
+    AP_CUDA(cudaStreamWaitEvent(main, ctx->ev_join, 0));
     return AP_OK;
 }
+
+template <class T>
+int matvec_into(ap_ctx *ctx, const void *p) { return matvec_into<T>(ctx, p, ctx->s0, ctx->s1); }
 
 double self_coef(const ap_ctx *ctx) { return 4.0 * std::pow(ctx->prm.ewald_beta, 3) / (3.0 * AP_SQRT_PI); }
 
 template <class T>
-int enqueue_iteration(ap_ctx *ctx, cudaGraphConditionalHandle h, int use_cond) {
+int enqueue_iteration(ap_ctx *ctx, cudaGraphConditionalHandle h, int use_cond, cudaStream_t main,
+                      cudaStream_t aux) {
     typedef typename V4<T>::type T4;
     const int nb = ap_grid_for(ctx->n_pad, NT);
-    k_direction<T><<<nb, NT, 0, ctx->s0>>>(ctx->r, ctx->alpha, ctx->n_pad, (T4 *)ctx->p, ctx->st);
+    k_direction<T><<<nb, NT, 0, main>>>(ctx->r, ctx->alpha, ctx->n_pad, (T4 *)ctx->p, ctx->st);
     AP_CUDA(cudaGetLastError());
-    int rc = matvec_into<T>(ctx, ctx->p);
+    int rc = matvec_into<T>(ctx, ctx->p, main, aux);
     if (rc) return rc;
-    k_apply<T><<<nb, NT, 0, ctx->s0>>>((const T4 *)ctx->p, ctx->alpha, ctx->acc, (const T *)ctx->rec,
-                                        self_coef(ctx), ctx->n_pad, ctx->qv, ctx->st);
-    k_update<T><<<nb, NT, 0, ctx->s0>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n, ctx->n_pad, ctx->mu,
-                                         ctx->r, ctx->st);
-    if (use_cond) k_loop_cond<<<1, 1, 0, ctx->s0>>>(h, ctx->st);
+    k_apply<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->alpha, ctx->acc, (const T *)ctx->rec,
+                                     self_coef(ctx), ctx->n_pad, ctx->qv, ctx->st);
+    k_update<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n, ctx->n_pad, ctx->mu,
+                                      ctx->r, ctx->st);
+    if (use_cond) k_loop_cond<<<1, 1, 0, main>>>(h, ctx->st);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -283,10 +287,15 @@ int build_graph(ap_ctx *ctx) {
     cp.conditional.size = 1;
     AP_CUDA(cudaGraphAddNode(&n_while, g, &n_set, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    AP_CUDA(cudaStreamBeginCaptureToGraph(ctx->s0, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_iteration<T>(ctx, h, 1);
+    // capture on a library-owned stream: the caller's may be the legacy default stream,
+    // which cannot be captured; the instantiated graph is launched on the caller's stream
+    cudaStream_t cs = nullptr;
+    AP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    AP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_iteration<T>(ctx, h, 1, cs, ctx->s1);
     cudaGraph_t captured = nullptr;
-    cudaError_t ec = cudaStreamEndCapture(ctx->s0, &captured);
+    cudaError_t ec = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
     if (rc || ec != cudaSuccess) {
         cudaGetLastError();
         cudaGraphDestroy(g);
@@ -322,8 +331,11 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
     k_init_finish<<<1, 1, 0, s>>>(ctx->st, ctx->n, tol, max_iter);
     AP_CUDA(cudaGetLastError());
     if (!ctx->graph_tried) {
-        rc = build_graph<T>(ctx);
-        if (rc) return rc;
+        if (build_graph<T>(ctx) != AP_OK) {   // no graph: the host-driven loop below
+            cudaGetLastError();
+            ctx->err.clear();
+            ctx->graph_ok = 0;
+        }
     }
     if (ctx->graph_ok) {
         AP_CUDA(cudaGraphLaunch(ctx->solve_exec, s));
@@ -333,7 +345,7 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
             AP_CUDA(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
             AP_CUDA(cudaStreamSynchronize(s));
             if (ctx->st_host->done) break;
-            rc = enqueue_iteration<T>(ctx, 0, 0);
+            rc = enqueue_iteration<T>(ctx, 0, 0, ctx->s0, ctx->s1);
             if (rc) return rc;
         }
     }
