@@ -1,0 +1,370 @@
+"""Benchmark: polarization step time on the 96,000-atom water box (32,000 rigid waters,
+98.7 A cube, PME grid 100^3, order 5, cutoff 7 A + 2 A list buffer, mixed precision, PCG
+to 1e-5 D RMS).
+
+One step = one pass of the whole hot path on a new synthetic configuration: neighbour
+blocks (rebuilt every REBUILD steps, amortised), permanent field (real + PME + self), the
+guess, the PCG solve, and the polarization energy and forces. Inputs (every step's
+positions) are resident on the device before timing; the L2 is flushed between timed
+steps (the working set, ~60 MB, fits the 129 MB L2). `--impl reference` times the FP64
+oracle on the host cores on a bounded sample of the same workload.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "polarization solve ms/MD-step and PCG iters at 1e-5 D RMS, learned vs plain"
+N_MOL, BOX, GRID, SEED, TRAJ_SEED = 32000, 98.7, (100, 100, 100), 1002, 2002
+CUTOFF, BUFFER, BETA, TOL = 7.0, 2.0, 0.5446, 1e-5
+REBUILD = 20                       # steps between neighbour-list rebuilds
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+# FP32 operations per in-cutoff pair of the real-space matvec kernel (counted from its
+# source: vector 6, r^2 5, rsqrt/r/r^-2 3, screening with erfc/exp 32, B1/B2 and U1/U2 10,
+# Thole 8, R1/R2 4, two field updates 36; FMA = 2)
+FLOPS_PER_PAIR_MATVEC = 104
+WORKLOAD = "water_96000_atoms_98.7A_grid100_rc7+2_mixed_pcg1e-5"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_system():
+    from paper_2011_01207_gb300 import synth
+    return synth.water_box(N_MOL, BOX, SEED)
+
+
+def trajectory(s, steps, seed=TRAJ_SEED):
+    from paper_2011_01207_gb300 import synth
+    out = [s.xyz.copy()]
+    cur = s
+    for k in range(1, steps):
+        cur = synth.perturb(cur, seed + k)
+        out.append(cur.xyz.copy())
+    return np.stack(out)
+
+
+def pairs_within(xyz, box, rc):
+    from scipy.spatial import cKDTree
+    w = np.mod(xyz, box)
+    w[w >= box] = 0.0
+    return len(cKDTree(w, boxsize=box).query_pairs(rc, output_type="ndarray"))
+
+
+def launches_per_step(iters, n, rebuild_frac):
+    """Kernels of this library launched by one step (cuFFT's own kernels not counted)."""
+    pad = 1 if n % 32 else 0
+    field = 6 + pad                       # load, [pad], spread, convolve, gather, pair field, assemble
+    solve = 1 + 4 + 2 + 1 + 8 * iters + 1  # guess, matvec(4), residual, finish, cond, 8/iter, unsort
+    forces = 10
+    build = 14 * rebuild_frac
+    return field + solve + forces + build
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2011_01207_gb300 import binding, build as _build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    _build.build_library()
+    dev = torch.device("cuda", local)
+    s = make_system()
+    total = args.warmup + args.steps
+    traj = trajectory(s, total)
+    pos = torch.tensor(traj, device=dev)                       # [steps, N, 3], resident before timing
+    ctx = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=GRID, precision=binding.AP_MIXED,
+                          device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k, xyz):
+        if k % REBUILD == 0:
+            binding.build_neighbour_blocks(ctx.ctx, xyz, ctx.excl_off, ctx.excl_atoms, ctx.n_excl)
+        binding.permanent_field(ctx.ctx, xyz, ctx.mpole, ctx.frame, ctx.alpha, None)
+        binding.induced_dipoles_pcg(ctx.ctx, None, TOL, 200, ctx.mu, want_info=False)
+        binding.polarization_energy_forces(ctx.ctx, ctx.mu, ctx.energy, ctx.forces)
+
+    iters, times = [], []
+    for k in range(args.warmup):
+        step(k, pos[k])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(args.warmup, total):
+        flush.fill_(k & 0xff)                                    # untimed: evict the L2
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(k, pos[k])
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        iters.append(binding.ap_solve_info_last(ctx.ctx).iterations)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public API with host buffers: pinned positions in, forces and
+    # energy out, copies inside the timed region
+    host_pos = torch.tensor(traj[-1], dtype=torch.float64).pin_memory()
+    host_f = torch.empty((s.n, 3), dtype=torch.float64).pin_memory()
+    host_e = torch.empty(1, dtype=torch.float64).pin_memory()
+    dev_pos = torch.empty((s.n, 3), dtype=torch.float64, device=dev)
+    e2e = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dev_pos.copy_(host_pos, non_blocking=True)
+        step(args.warmup + k, dev_pos)
+        host_f.copy_(ctx.forces, non_blocking=True)
+        host_e.copy_(ctx.energy, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e.append(a.elapsed_time(b))
+    e2e_ms = float(np.mean(e2e))
+
+    # dominant kernel: per-launch durations with CUDA events on the launch stream
+    it_mean = float(np.mean(iters))
+    kern = {k: binding.ap_time_kernel(ctx.ctx, k, 30) for k in
+            ("real_matvec", "spread_dipoles", "gather_field", "convolve", "real_field", "spread_multipoles")}
+    per_step = {"real_matvec": kern["real_matvec"] * (it_mean + 1),
+                "spread_dipoles": kern["spread_dipoles"] * (it_mean + 1),
+                "gather_field": kern["gather_field"] * (it_mean + 1),
+                "real_field": kern["real_field"], "spread_multipoles": kern["spread_multipoles"]}
+    npairs = pairs_within(traj[-1], s.box, CUTOFF)
+    hbm_peak, peak_kind = _peaks()
+    flop = npairs * FLOPS_PER_PAIR_MATVEC
+    achieved = flop / (kern["real_matvec"] * 1e-3) / 1e12
+    roofline = {"kernel": "real_matvec (a5 tile kernel)", "bound": "alu", "achieved": round(achieved, 3),
+                "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "traffic": None, "flop_per_launch": flop, "pairs_in_cutoff": npairs,
+                "launch_ms": round(kern["real_matvec"], 4),
+                "peak_note": "FP32 FMA peak from 152 SMs x 128 lanes x 2 x 2070 MHz",
+                "spread_dipoles_gbs": round((s.n * 32 + GRID[0] * GRID[1] * GRID[2] * 4) / (kern["spread_dipoles"] * 1e-3) / 1e9, 1),
+                "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind}
+    nb, nt, ne = ctx.stats()
+    result = {
+        "metric": METRIC, "value": round(ms, 4), "unit": "ms/step", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 pair/PME arithmetic, f64 accumulation", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "atoms": s.n, "guess": "plain alpha*E", "pcg_iters_mean": it_mean,
+                   "pcg_iters": [int(min(iters)), int(max(iters))], "rebuild_every": REBUILD,
+                   "l2": "flushed between timed steps (256 MB write)", "blocks": nb, "tiles": nt,
+                   "excl_tiles": ne, "replicas": world, "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "e2e": {"value": round(e2e_ms, 4), "unit": "ms/step", "h2d_bytes_per_step": int(s.n * 3 * 8),
+                "d2h_bytes_per_step": int(s.n * 3 * 8 + 8)},
+        "gpu_launches": int(round(launches_per_step(it_mean, s.n, 1.0 / REBUILD) * args.steps)),
+        "kernel_ms": {k: round(v, 4) for k, v in kern.items()},
+        "kernel_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
+        "roofline": roofline,
+        "clocks": clk,
+        "wall_s_timed_region": round(t_wall, 3),
+    }
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(s, it_mean, samples=1)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def oracle_step_sample(s, iters, rows=256, seed=0):
+    """One bounded sample of the oracle on the same workload: the full smooth-PME passes of
+    a step (multipole field, one dipole matvec, force derivatives) over all atoms, and the
+    real-space sums for `rows` sampled atoms scaled by N/rows; the matvec is counted
+    (iters + 1) times. Returns (estimated ms per step, seconds of CPU work)."""
+    from oracle import Params, frames, realspace, spme, pairs as opairs
+    p = Params(beta=BETA, grid=GRID, cutoff=CUTOFF)
+    n = s.n
+    rng = np.random.default_rng(seed)
+    sel = rng.choice(n, rows, replace=False)
+    t0 = time.perf_counter()
+    dip, quad, _ = frames.rotate_multipoles(s.xyz, s.box, s.frame, s.dip, s.quad)
+    t_rot = time.perf_counter() - t0
+    # pairs of the sampled rows
+    I, J, R = [], [], []
+    for i in sel:
+        d = s.xyz[i] - s.xyz
+        d -= s.box * np.round(d / s.box)
+        r2 = np.einsum("ij,ij->i", d, d)
+        js = np.nonzero((r2 < CUTOFF ** 2) & (np.arange(n) != i))[0]
+        I.append(np.full(len(js), i)); J.append(js); R.append(d[js])
+    I, J, R = np.concatenate(I), np.concatenate(J), np.concatenate(R)
+    t_pairs = (time.perf_counter() - t0 - t_rot) * n / rows
+    sig = opairs.scale_of_pairs(I, J, s.excl, n, R, s.box)
+    z3, z33 = np.zeros((n, 3)), np.zeros((n, 3, 3))
+    mu = s.alpha[:, None] * np.ones((n, 3)) * 0.01
+    t = time.perf_counter()
+    realspace.real_field(n, I, J, R, sig, s.q, dip, quad, s.alpha, BETA, 0.39)
+    t_real_field = (time.perf_counter() - t) * n / rows
+    t = time.perf_counter()
+    spme.recip_derivs(s.xyz, s.box, BETA, GRID, 5, s.q, dip, quad, 1)
+    t_rec_field = time.perf_counter() - t
+    t = time.perf_counter()
+    realspace.real_dipole_field(n, I, J, R, mu, s.alpha, BETA, 0.39)
+    t_real_mv = (time.perf_counter() - t) * n / rows
+    t = time.perf_counter()
+    spme.recip_derivs(s.xyz, s.box, BETA, GRID, 5, np.zeros(n), mu, z33, 1)
+    t_rec_mv = time.perf_counter() - t
+    t = time.perf_counter()
+    realspace.real_forces(n, I, J, R, sig, s.q, dip, quad, s.alpha, mu, BETA, 0.39, 332.063713)
+    t_real_f = (time.perf_counter() - t) * n / rows
+    t = time.perf_counter()
+    spme.recip_derivs(s.xyz, s.box, BETA, GRID, 5, np.zeros(n), mu, z33, 3)
+    spme.recip_derivs(s.xyz, s.box, BETA, GRID, 5, s.q, dip, quad, 2)
+    t_rec_f = time.perf_counter() - t
+    work = time.perf_counter() - t0
+    est = (t_rot + t_pairs + t_real_field + t_rec_field + (iters + 1) * (t_real_mv + t_rec_mv)
+           + t_real_f + t_rec_f)
+    return est * 1e3, work
+
+
+ORACLE_SAMPLE = ("per step: rotation of all multipoles; smooth-PME passes over all 96,000 atoms "
+                 "(multipole field, one dipole matvec, force derivatives to third order); real-space "
+                 "pair sums (field, matvec, forces) for 256 sampled atoms scaled by N/256; the matvec "
+                 "counted (PCG iterations + 1) times; NumPy FP64, single thread")
+
+
+def cpu_baseline(s, iters, samples=1):
+    vals = [oracle_step_sample(s, iters, seed=k)[0] for k in range(samples)]
+    return {"value": round(float(np.mean(vals)), 1), "unit": "ms/step", "cores": 1, "kind": "oracle",
+            "sample": ORACLE_SAMPLE}
+
+
+def oracle_iterations():
+    """PCG iterations of the oracle at 1e-5 D on a 648-atom box of the same water model."""
+    from oracle import Oracle, Params
+    from paper_2011_01207_gb300 import synth
+    small = synth.water_box(216, 18.64, 1001)
+    o = Oracle(small, Params(beta=BETA, grid=(24, 24, 24), cutoff=CUTOFF))
+    _, info = o.pcg(o.permanent_field(), tol=TOL)
+    return info["iters"]
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    s = make_system()
+    iters = oracle_iterations()
+    vals, works = [], []
+    for k in range(args.warmup + args.steps):
+        v, w = oracle_step_sample(s, iters, rows=64, seed=k)
+        if k >= args.warmup:
+            vals.append(v)
+            works.append(w)
+    value = float(np.mean(vals))
+    sample = ORACLE_SAMPLE.replace("256", "64") + f"; PCG iterations {iters} (oracle, 648-atom box, 1e-5 D)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms/step",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(value, 1), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "atoms": s.n, "guess": "plain alpha*E"},
+        "cpu_baseline": {"value": round(value, 1), "unit": "ms/step", "cores": 1, "kind": "oracle",
+                         "sample": sample, "cpu_seconds_per_step": round(float(np.mean(works)), 2)},
+        "e2e": {"value": round(value, 1), "unit": "ms/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

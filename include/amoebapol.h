@@ -141,8 +141,24 @@ int dipole_field_matvec(ap_ctx* ctx, const double* d_v, double* d_out);
  * (tiles) and block pairs carrying exclusion masks of the current lists. */
 int ap_list_stats(const ap_ctx* ctx, int* h_blocks, int* h_tiles, int* h_excl_tiles);
 
-/* The stream the context enqueues on (cudaStream_t), and its secondary stream. */
+/* The stream the context enqueues on (cudaStream_t). */
 void* ap_stream(const ap_ctx* ctx);
+
+/* Iterations and residuals of the most recent induced_dipoles_pcg() on this context.
+ * Synchronizes the context's stream. */
+int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
+
+/* Benchmark support: launch one kernel of the path `reps` times on the context's stream
+ * on the current configuration (inputs as left by the last calls), timing each launch
+ * with CUDA events, and return the mean duration in ms. Overwrites scratch buffers
+ * only (the stored field, dipoles and lists are untouched). Synchronizes. */
+#define AP_KERNEL_REAL_MATVEC       0   /* a5: real-space dipole-field tile kernel */
+#define AP_KERNEL_REAL_FIELD        1   /* a2: real-space permanent-field tile kernel */
+#define AP_KERNEL_SPREAD_DIPOLES    2   /* a6: B-spline spread of dipoles onto the grid */
+#define AP_KERNEL_CONVOLVE          3   /* a3/a6: k-space product with B(m)C(m) */
+#define AP_KERNEL_GATHER_FIELD      4   /* a3/a6: B-spline gather of the field */
+#define AP_KERNEL_SPREAD_MULTIPOLES 5   /* a3: spread of the permanent multipoles */
+int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
 
 #ifdef __cplusplus
 }

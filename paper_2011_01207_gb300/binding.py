@@ -21,7 +21,9 @@ _ERRORS = {-1: "AP_ERR_ARG", -2: "AP_ERR_CUDA", -3: "AP_ERR_CAPACITY", -4: "AP_E
 # every symbol the public header declares
 EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks", "permanent_field",
            "induced_dipoles_pcg", "polarization_energy_forces", "dipole_field_matvec", "ap_list_stats",
-           "ap_stream")
+           "ap_stream", "ap_solve_info_last", "ap_time_kernel")
+KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
+           "spread_multipoles": 5}
 
 
 class ApParams(ctypes.Structure):
@@ -62,6 +64,8 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "dipole_field_matvec": (I, [P, P, P]),
         "ap_list_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "ap_stream": (P, [P]),
+        "ap_solve_info_last": (I, [P, ctypes.POINTER(ApSolveInfo)]),
+        "ap_time_kernel": (I, [P, I, I, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -155,6 +159,19 @@ def ap_list_stats(ctx):
     b, t, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     load().ap_list_stats(ctx, ctypes.byref(b), ctypes.byref(t), ctypes.byref(e))
     return b.value, t.value, e.value
+
+
+def ap_solve_info_last(ctx):
+    info = ApSolveInfo()
+    _check(ctx, load().ap_solve_info_last(ctx, ctypes.byref(info)), "ap_solve_info_last")
+    return info
+
+
+def ap_time_kernel(ctx, which, reps=20):
+    ms = ctypes.c_double()
+    k = KERNELS[which] if isinstance(which, str) else int(which)
+    _check(ctx, load().ap_time_kernel(ctx, k, int(reps), ctypes.byref(ms)), "ap_time_kernel")
+    return ms.value
 
 
 # ---- marshalling helpers ---------------------------------------------------------------

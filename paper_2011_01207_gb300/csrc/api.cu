@@ -13,6 +13,7 @@ int ap_fail(ap_ctx *c, int code, const std::string &msg) {
 }
 
 int dipole_field_apply(ap_ctx *ctx, const double *d_v, double *d_out);
+int pme_stage_launch(ap_ctx *ctx, int stage, cudaStream_t s);
 
 namespace {
 
@@ -205,5 +206,52 @@ int ap_list_stats(const ap_ctx *ctx, int *h_blocks, int *h_tiles, int *h_excl_ti
 }
 
 void *ap_stream(const ap_ctx *ctx) { return ctx ? (void *)ctx->s0 : nullptr; }
+
+int ap_solve_info_last(ap_ctx *ctx, ap_solve_info *h_info) {
+    if (!ctx || !h_info) return AP_ERR_ARG;
+    ctx->err.clear();
+    AP_CUDA(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, ctx->s0));
+    AP_CUDA(cudaStreamSynchronize(ctx->s0));
+    h_info->iterations = ctx->st_host->iter;
+    h_info->eps_debye = ctx->st_host->eps;
+    h_info->eps_initial = ctx->st_host->eps0;
+    h_info->status = ctx->st_host->status;
+    return AP_OK;
+}
+
+int ap_time_kernel(ap_ctx *ctx, int which, int reps, double *h_ms) {
+    if (!ctx || !h_ms || reps < 1) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
+    cudaEvent_t a, b;
+    AP_CUDA(cudaEventCreate(&a));
+    AP_CUDA(cudaEventCreate(&b));
+    double total = 0.0;
+    for (int r = 0; r < reps; ++r) {
+        AP_CUDA(cudaEventRecord(a, ctx->s0));
+        int rc = AP_OK;
+        switch (which) {
+        case AP_KERNEL_REAL_MATVEC: rc = real_matvec_launch(ctx, ctx->p, ctx->s0); break;
+        case AP_KERNEL_REAL_FIELD: rc = real_field_launch(ctx, ctx->s0); break;
+        case AP_KERNEL_SPREAD_DIPOLES: rc = pme_stage_launch(ctx, 0, ctx->s0); break;
+        case AP_KERNEL_CONVOLVE: rc = pme_stage_launch(ctx, 1, ctx->s0); break;
+        case AP_KERNEL_GATHER_FIELD: rc = pme_stage_launch(ctx, 2, ctx->s0); break;
+        case AP_KERNEL_SPREAD_MULTIPOLES: rc = pme_stage_launch(ctx, 3, ctx->s0); break;
+        default: rc = ap_fail(ctx, AP_ERR_ARG, "unknown kernel id");
+        }
+        if (rc) { cudaEventDestroy(a); cudaEventDestroy(b); return rc; }
+        AP_CUDA(cudaEventRecord(b, ctx->s0));
+        AP_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        AP_CUDA(cudaEventElapsedTime(&ms, a, b));
+        total += ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    // the timed launches accumulated into scratch buffers: clear them for the next call
+    AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+    *h_ms = total / reps;
+    return AP_OK;
+}
 
 }  // extern "C"

@@ -395,7 +395,41 @@ int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
     return AP_OK;
 }
 
+template <class T>
+int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
+    typedef typename V4<T>::type T4;
+    typedef typename FftTypes<T>::cplx C;
+    PmeConsts<T> pc = pme_consts<T>(ctx);
+    switch (stage) {
+    case 0:
+        k_spread_dipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->p,
+                                                                    (T *)ctx->grid, pc);
+        break;
+    case 1:
+        k_convolve<T><<<ap_grid_for((long)ctx->ncgrid, 256), 256, 0, s>>>((C *)ctx->cgrid, (const T *)ctx->green,
+                                                                         ctx->ncgrid);
+        break;
+    case 2:
+        k_gather_field<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid,
+                                                                  (T *)ctx->rec, ctx->n_pad, pc);
+        break;
+    case 3:
+        k_spread_multipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(
+            (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0, (const T4 *)ctx->quad1,
+            (T *)ctx->grid, pc);
+        break;
+    default:
+        return ap_fail(ctx, AP_ERR_ARG, "unknown PME stage");
+    }
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
 }  // namespace
+
+int pme_stage_launch(ap_ctx *ctx, int stage, cudaStream_t s) {
+    return ctx->prec == AP_FP64 ? stage_t<double>(ctx, stage, s) : stage_t<float>(ctx, stage, s);
+}
 
 int pme_init(ap_ctx *ctx) { return ctx->prec == AP_FP64 ? init_t<double>(ctx) : init_t<float>(ctx); }
 
