@@ -17,6 +17,7 @@
 #include "common.cuh"
 
 #include <cmath>
+#include <cstdlib>
 
 void unsort3(ap_ctx *ctx, const double *src, double *out, cudaStream_t s);
 
@@ -263,6 +264,10 @@ int enqueue_iteration(ap_ctx *ctx, cudaGraphConditionalHandle h, int use_cond, c
 template <class T>
 int build_graph(ap_ctx *ctx) {
     ctx->graph_tried = 1;
+    // AP_SOLVE_GRAPH=0 keeps the host-driven loop (the same kernels, launched one by one):
+    // profilers cannot attribute kernels inside graphs that hold conditional nodes
+    const char *env = getenv("AP_SOLVE_GRAPH");
+    if (env && env[0] == '0') return AP_OK;
     cudaGraph_t g = nullptr;
     AP_CUDA(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
