@@ -160,6 +160,26 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 #define AP_KERNEL_SPREAD_MULTIPOLES 5   /* a3: spread of the permanent multipoles */
 int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
 
+/* Polarization energy without allocation - the paper has no counterpart; it is a
+ * convenience for callers that cannot allocate device memory: code whose device memory
+ * all belongs to another framework's pool, loops that forbid allocation after set-up,
+ * and callers that hold no ap_ctx (creating one allocates the whole workspace).
+ * Computes E_pol = -(f/2) sum_i mu_i . E_i, f = 332.063713, the energy that
+ * polarization_energy_forces() returns for the same dipoles and field.
+ *   d_mu, d_field  [n][3] double device arrays (any common atom order).
+ *   n              1 <= n <= 16,777,216 (larger n returns AP_ERR_ARG, nothing launched).
+ *   d_energy       [1] double device output, kcal/mol.
+ *   stream         cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Allocates nothing and calls no allocating routine: its scratch is a 32 KB array of
+ * block partial sums that every GPU loading the library holds until the process exits.
+ * The first call on each device looks up that array's device address (with the
+ * device current); make that first call before any stream capture. All calls share
+ * the array and it keeps the last call's partials, so calls whose kernels overlap on the
+ * GPU (e.g. on two streams at once) race and must be serialised by the caller.
+ * Errors are described by ap_last_error(NULL). Returns once the work is enqueued. */
+int polarization_energy_noalloc(const double* d_mu, const double* d_field, int n,
+                                double* d_energy, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

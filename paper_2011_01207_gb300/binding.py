@@ -21,7 +21,7 @@ _ERRORS = {-1: "AP_ERR_ARG", -2: "AP_ERR_CUDA", -3: "AP_ERR_CAPACITY", -4: "AP_E
 # every symbol the public header declares
 EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks", "permanent_field",
            "induced_dipoles_pcg", "polarization_energy_forces", "dipole_field_matvec", "ap_list_stats",
-           "ap_stream", "ap_solve_info_last", "ap_time_kernel")
+           "ap_stream", "ap_solve_info_last", "ap_time_kernel", "polarization_energy_noalloc")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5}
 
@@ -66,6 +66,7 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "ap_stream": (P, [P]),
         "ap_solve_info_last": (I, [P, ctypes.POINTER(ApSolveInfo)]),
         "ap_time_kernel": (I, [P, I, I, ctypes.POINTER(D)]),
+        "polarization_energy_noalloc": (I, [P, P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -172,6 +173,17 @@ def ap_time_kernel(ctx, which, reps=20):
     k = KERNELS[which] if isinstance(which, str) else int(which)
     _check(ctx, load().ap_time_kernel(ctx, k, int(reps), ctypes.byref(ms)), "ap_time_kernel")
     return ms.value
+
+
+def polarization_energy_noalloc(mu, field, energy, stream=None):
+    """Context-free energy (no device allocation); `stream` is a torch stream or None."""
+    import torch
+    n = mu.shape[0]
+    sp = ctypes.c_void_p((stream or torch.cuda.current_stream(mu.device)).cuda_stream)
+    code = load().polarization_energy_noalloc(
+        _ptr(mu, torch.float64, (n, 3), "mu"), _ptr(field, torch.float64, (n, 3), "field"), int(n),
+        _ptr(energy, torch.float64, (1,), "energy"), sp)
+    return _check(None, code, "polarization_energy_noalloc")
 
 
 # ---- marshalling helpers ---------------------------------------------------------------
