@@ -28,7 +28,9 @@ void free_all(ap_ctx *c) {
     void *ptrs[] = {c->perm, c->iperm, c->bcenter, c->tiles, c->tshift, c->tile_excl, c->excl_mask, c->cell_count,
                     c->tmp_int, c->excl_off, c->excl_atoms, c->posq, c->dipd, c->quad0, c->quad1, c->alpha,
                     c->E, c->acc, c->rec, c->rot, c->mpl, c->frame_s, c->fvec, c->mu, c->r, c->qv, c->p, c->st,
-                    c->grid, c->cgrid, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf};
+                    c->grid, c->cgrid, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf,
+                    c->tile_off, c->chunk_j, c->chunk_pos, c->chunk_src, c->chunk_mask, c->chunk_flag, c->nchunk,
+                    c->work, c->n_work, c->red_part, c->pmask, c->pmask_t};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -63,6 +65,9 @@ int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
     if ((r = dalloc(ctx, &ctx->perm, sizeof(int) * np))) return r;
     if ((r = dalloc(ctx, &ctx->iperm, sizeof(int) * np))) return r;
     if ((r = dalloc(ctx, &ctx->bcenter, sizeof(float4) * nb))) return r;
+    if ((r = dalloc(ctx, &ctx->tile_off, sizeof(int) * (nb + 1)))) return r;
+    if ((r = dalloc(ctx, &ctx->nchunk, sizeof(int) * nb))) return r;
+    if ((r = dalloc(ctx, &ctx->n_work, sizeof(int) * 4))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->posq, 4 * es * np))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->dipd, 4 * es * np))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->quad0, 4 * es * np))) return r;
@@ -80,6 +85,7 @@ int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
     if ((r = dalloc(ctx, &ctx->qv, sizeof(double) * 3 * np))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->p, 4 * es * np))) return r;
     if ((r = dalloc(ctx, &ctx->st, sizeof(PcgState)))) return r;
+    if ((r = dalloc(ctx, &ctx->red_part, sizeof(double) * 3 * ((np + 255) / 256 + 1)))) return r;
     AP_CUDA(cudaMallocHost((void **)&ctx->st_host, sizeof(PcgState)));
     ctx->ngrid = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
     ctx->ncgrid = (size_t)(P->grid[0] / 2 + 1) * P->grid[1] * P->grid[2];
@@ -158,6 +164,7 @@ int permanent_field(ap_ctx *ctx, const double *d_xyz, const double *d_mpole, con
     if (!ctx->lists_valid) return ap_fail(ctx, AP_ERR_STATE, "build_neighbour_blocks() must come first");
     int r = cfg_load(ctx, d_xyz, d_mpole, d_frame, d_alpha);
     if (r) return r;
+    if ((r = filter_launch(ctx, ctx->s0))) return r;
     AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
     AP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->s0));
     AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));

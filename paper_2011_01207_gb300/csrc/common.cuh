@@ -66,7 +66,20 @@ struct ap_ctx {
     int *tile_excl = nullptr;    // [cap_tiles] exclusion-mask slot or -1
     unsigned *excl_mask = nullptr;  // [cap_excl][32]
     int n_tiles = 0, cap_tiles = 0, n_excl_tiles = 0, cap_excl = 0;
+    int *tile_off = nullptr;     // [n_blocks+1] first tile of each block
     int minimg = 1;              // per-pair minimum image (small boxes) vs per-tile shifts
+    // per-configuration filtered chunks (capacity cap_chunks = cap_tiles chunks of 32)
+    int *chunk_j = nullptr;      // [cap][32] j slot or -1
+    void *chunk_pos = nullptr;   // T4 [cap][32] j position (image next to block I) and Thole factor
+    int *chunk_src = nullptr;    // [cap][32] exclusion source (slot << 5 | j-lane) or -1
+    unsigned *chunk_mask = nullptr;  // [cap][32] exclusion bits (i-lane word, bit = chunk position)
+    int *chunk_flag = nullptr;   // [cap] 1 if the chunk holds excluded pairs
+    int *nchunk = nullptr;       // [n_blocks]
+    int2 *work = nullptr;        // [n_blocks + cap] (I, chunk) items, chunk -1 = diagonal block
+    int *n_work = nullptr;       // device: [0] work items, [1] in-range pairs of the configuration
+    unsigned *pmask = nullptr;   // [work][32] in-range pair bits per item (i-lane word, bit = j-lane)
+    unsigned *pmask_t = nullptr; // [work][32] the transpose (j-lane word, bit = i-lane)
+    int cap_chunks = 0;
     int lists_valid = 0;
     // scratch for the build
     int *cell_count = nullptr; int cap_cells = 0;
@@ -92,6 +105,7 @@ struct ap_ctx {
     double *mu = nullptr, *r = nullptr, *qv = nullptr;   // [3][n_pad]
     void *p = nullptr;        // T4 [n_pad] search direction
     PcgState *st = nullptr;   // device
+    double *red_part = nullptr;   // [3 * ceil(n_pad/256)] per-block partial sums of the PCG dots
     PcgState *st_host = nullptr;  // pinned mirror
 
     // PME
@@ -117,6 +131,37 @@ struct ap_ctx {
     int graph_tried = 0;
 };
 
+// arguments of the real-space kernels that iterate the filtered work items
+struct WorkArgs {
+    const int2 *work;
+    const int *n_work;
+    const int *chunk_j;
+    const void *chunk_pos;
+    const unsigned *chunk_mask;
+    const int *chunk_flag;
+    const int *tile_excl;      // for the diagonal block's own mask
+    const int *tile_off;
+    const unsigned *excl_mask;
+    const unsigned *pmask;
+    const unsigned *pmask_t;
+};
+
+inline WorkArgs work_args(const ap_ctx *ctx) {
+    WorkArgs w;
+    w.work = ctx->work;
+    w.n_work = ctx->n_work;
+    w.chunk_j = ctx->chunk_j;
+    w.chunk_pos = ctx->chunk_pos;
+    w.chunk_mask = ctx->chunk_mask;
+    w.chunk_flag = ctx->chunk_flag;
+    w.tile_excl = ctx->tile_excl;
+    w.tile_off = ctx->tile_off;
+    w.excl_mask = ctx->excl_mask;
+    w.pmask = ctx->pmask;
+    w.pmask_t = ctx->pmask_t;
+    return w;
+}
+
 // error helpers -------------------------------------------------------------------------
 int ap_fail(ap_ctx *c, int code, const std::string &msg);
 #define AP_CUDA(call)                                                                    \
@@ -139,6 +184,8 @@ static inline int ap_grid_for(long n, int threads) { return (int)((n + threads -
 int nb_build(ap_ctx *ctx, const double *d_xyz, const int *d_off, const int *d_atoms, int n_excl);
 int cfg_load(ap_ctx *ctx, const double *d_xyz, const double *d_mpole, const int *d_frame,
              const double *d_alpha);
+int filter_launch(ap_ctx *ctx, cudaStream_t s);
+int filter_alloc(ap_ctx *ctx);
 int real_field_launch(ap_ctx *ctx, cudaStream_t s);
 int real_matvec_launch(ap_ctx *ctx, const void *p, cudaStream_t s);
 int real_forces_launch(ap_ctx *ctx, cudaStream_t s);

@@ -1,0 +1,229 @@
+// Per-configuration list filtering (paper Sec. 2.3.2, "List filtering": an atom belongs to a
+// group's neighbourhood when it is within range of some atom of the group; neighbour lists
+// are padded with phantom atoms to a multiple of B_size).
+//
+// The block-pair lists are built with cutoff + buffer and reused for many steps; once the
+// positions of a step are known they stay fixed for the field, every PCG matrix-vector
+// product and the forces. So at each configuration, for every block I, the atoms of its
+// partner blocks J > I that lie within r_c of I's bounding box are packed into 32-wide
+// chunks (positions pre-shifted to the periodic image next to I, padding with NaN phantoms)
+// with their exclusion bits carried over. The real-space kernels then run over
+//   work = [(I, diagonal block), (I, chunk 0), (I, chunk 1), ...] for every I,
+// which keeps only ~1/4 of the candidate pairs of the block-pair tiles while preserving the
+// 32 x 32 warp tile and the shuffle rotation.
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace {
+
+template <class T, bool MINIMG>
+__global__ void __launch_bounds__(256) k_filter(
+    const int2 *__restrict__ tiles, const int *__restrict__ tile_off, const float4 *__restrict__ tshift,
+    const int *__restrict__ tile_excl, const unsigned *__restrict__ excl_mask,
+    const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd, int nb,
+    T rc2, T Lx, T Ly, T Lz, int *__restrict__ chunk_j, typename V4<T>::type *__restrict__ chunk_pos,
+    int *__restrict__ chunk_src, unsigned *__restrict__ chunk_mask, int *__restrict__ chunk_flag,
+    int *__restrict__ nchunk) {
+    typedef typename V4<T>::type T4;
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (I >= nb) return;
+    // bounding box of block I at the current positions (padding slots hold NaN)
+    T4 pi = posq[I * 32 + lane];
+    const bool vi = isfinite((float)pi.x);
+    T lo[3] = {vi ? pi.x : T(1e30), vi ? pi.y : T(1e30), vi ? pi.z : T(1e30)};
+    T hi[3] = {vi ? pi.x : T(-1e30), vi ? pi.y : T(-1e30), vi ? pi.z : T(-1e30)};
+    for (int off = 16; off; off >>= 1)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
+            hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
+        }
+    const T cx = T(0.5) * (lo[0] + hi[0]), cy = T(0.5) * (lo[1] + hi[1]), cz = T(0.5) * (lo[2] + hi[2]);
+    const int base = tile_off[I];
+    int count = 0;
+    for (int t = base; t < tile_off[I + 1]; ++t) {
+        const int J = tiles[t].y;
+        if (J == I) continue;
+        const int sj = J * 32 + lane;
+        T4 q = posq[sj];
+        T x = q.x, y = q.y, z = q.z;
+        if (MINIMG) {
+            x -= Lx * rint((x - cx) / Lx);
+            y -= Ly * rint((y - cy) / Ly);
+            z -= Lz * rint((z - cz) / Lz);
+        } else {
+            const float4 sh = tshift[t];
+            // pairs use x_i - x_j + shift: store x_j - shift, the image of j next to I
+            x -= (T)sh.x; y -= (T)sh.y; z -= (T)sh.z;
+        }
+        const T gx = max(T(0), max(lo[0] - x, x - hi[0]));
+        const T gy = max(T(0), max(lo[1] - y, y - hi[1]));
+        const T gz = max(T(0), max(lo[2] - z, z - hi[2]));
+        const bool sel = isfinite((float)x) && (gx * gx + gy * gy + gz * gz < rc2);
+        const unsigned m = __ballot_sync(0xffffffffu, sel);
+        if (sel) {
+            const int k = count + __popc(m & ((1u << lane) - 1u));
+            const int e = tile_excl[t];
+            const size_t slot = (size_t)(base + (k >> 5)) * 32 + (k & 31);
+            chunk_j[slot] = sj;
+            T4 v;
+            v.x = x; v.y = y; v.z = z; v.w = dipd[sj].w;
+            chunk_pos[slot] = v;
+            chunk_src[slot] = e >= 0 ? (e << 5) | lane : -1;
+        }
+        count += __popc(m);
+    }
+    const int nc = (count + 31) >> 5;
+    // phantom padding of the last chunk
+    if (nc > 0) {
+        const int k = count + lane;
+        if (k < nc * 32) {
+            const size_t slot = (size_t)(base + (k >> 5)) * 32 + (k & 31);
+            chunk_j[slot] = -1;
+            T4 v;
+            v.x = v.y = v.z = (T)NAN; v.w = T(0);
+            chunk_pos[slot] = v;
+            chunk_src[slot] = -1;
+        }
+    }
+    __syncwarp();
+    // exclusion masks of the chunks: word i-lane -> bit chunk position
+    for (int c = 0; c < nc; ++c) {
+        const size_t cs = (size_t)(base + c) * 32;
+        const int src = chunk_src[cs + lane];
+        const unsigned any = __ballot_sync(0xffffffffu, src >= 0);
+        if (lane == 0) chunk_flag[base + c] = any ? 1 : 0;
+        if (!any) continue;
+        unsigned mine = 0u;
+        for (int il = 0; il < 32; ++il) {
+            const bool b = src >= 0 && ((excl_mask[(size_t)(src >> 5) * 32 + il] >> (src & 31)) & 1u);
+            const unsigned w = __ballot_sync(0xffffffffu, b);
+            if (lane == il) mine = w;
+        }
+        chunk_mask[cs + lane] = mine;
+    }
+    if (lane == 0) nchunk[I] = nc;
+}
+
+// flat work list (I, -1) then (I, chunk) for every block, in block order (one CTA)
+__global__ void k_worklist(const int *__restrict__ nchunk, const int *__restrict__ tile_off, int nb,
+                           int2 *__restrict__ work, int *__restrict__ n_work) {
+    __shared__ int sums[1024];
+    const int t = threadIdx.x;
+    const int per = (nb + 1023) / 1024;
+    const int b = t * per, e = min(nb, b + per);
+    int s = 0;
+    for (int k = b; k < e; ++k) s += 1 + nchunk[k];
+    sums[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int v = t >= off ? sums[t - off] : 0;
+        __syncthreads();
+        sums[t] += v;
+        __syncthreads();
+    }
+    int pos = sums[t] - s;
+    for (int k = b; k < e; ++k) {
+        work[pos++] = make_int2(k, -1);
+        for (int c = 0; c < nchunk[k]; ++c) work[pos++] = make_int2(k, tile_off[k] + c);
+    }
+    if (t == 1023) *n_work = sums[1023];
+}
+
+// per-item in-range pair masks at the current configuration: word (item, i-lane) has bit
+// j-lane set when the pair is within r_c (diagonal items: j-lane > i-lane, each pair once)
+template <class T, bool MINIMG>
+__global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work, const int *__restrict__ n_work,
+                                                  const typename V4<T>::type *__restrict__ posq,
+                                                  const typename V4<T>::type *__restrict__ chunk_pos, T rc2, T Lx,
+                                                  T Ly, T Lz, unsigned *__restrict__ pmask,
+                                                  unsigned *__restrict__ pmask_t, int *__restrict__ pcount) {
+    typedef typename V4<T>::type T4;
+    const int lane = threadIdx.x & 31;
+    const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long nw = ((long)gridDim.x * blockDim.x) >> 5;
+    const long nitems = *n_work;
+    for (long t = w; t < nitems; t += nw) {
+        const int2 it = work[t];
+        const T4 a = posq[it.x * 32 + lane];
+        const T4 b = it.y < 0 ? posq[it.x * 32 + lane] : chunk_pos[(size_t)it.y * 32 + lane];
+        T xj = b.x, yj = b.y, zj = b.z;
+        unsigned m = 0u;
+        for (int s = 0; s < 32; ++s) {
+            const int jl = (lane + s) & 31;
+            T dx = a.x - xj, dy = a.y - yj, dz = a.z - zj;
+            if (MINIMG) {
+                dx -= Lx * rint(dx / Lx);
+                dy -= Ly * rint(dy / Ly);
+                dz -= Lz * rint(dz / Lz);
+            }
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            const bool in = (r2 < rc2) && (it.y >= 0 || jl > lane);
+            m |= in ? (1u << jl) : 0u;
+            const int src = (lane + 1) & 31;
+            xj = __shfl_sync(0xffffffffu, xj, src);
+            yj = __shfl_sync(0xffffffffu, yj, src);
+            zj = __shfl_sync(0xffffffffu, zj, src);
+        }
+        pmask[(size_t)t * 32 + lane] = m;
+        // transpose: word of j-lane c has bit i-lane set for every in-range pair (i, c)
+        unsigned col = 0u;
+        for (int c = 0; c < 32; ++c) {
+            const unsigned w = __ballot_sync(0xffffffffu, (m >> c) & 1u);
+            if (lane == c) col = w;
+        }
+        pmask_t[(size_t)t * 32 + lane] = col;
+        int c = __popc(m);
+        for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+        if (lane == 0) atomicAdd(pcount, c);
+    }
+}
+
+template <class T>
+int filter_t(ap_ctx *ctx, cudaStream_t s) {
+    typedef typename V4<T>::type T4;
+    const ap_params &P = ctx->prm;
+    const T rc2 = (T)(P.cutoff * P.cutoff * (1.0 + 1e-5));
+    const int nb = ctx->n_blocks;
+    auto kern = ctx->minimg ? k_filter<T, true> : k_filter<T, false>;
+    kern<<<ap_grid_for((long)nb * 32, 256), 256, 0, s>>>(
+        ctx->tiles, ctx->tile_off, ctx->tshift, ctx->tile_excl, ctx->excl_mask, (const T4 *)ctx->posq,
+        (const T4 *)ctx->dipd, nb, rc2, (T)P.box[0], (T)P.box[1], (T)P.box[2], ctx->chunk_j, (T4 *)ctx->chunk_pos,
+        ctx->chunk_src, ctx->chunk_mask, ctx->chunk_flag, ctx->nchunk);
+    k_worklist<<<1, 1024, 0, s>>>(ctx->nchunk, ctx->tile_off, nb, ctx->work, ctx->n_work);
+    AP_CUDA(cudaMemsetAsync(ctx->n_work + 1, 0, sizeof(int), s));
+    const T rcm = (T)(P.cutoff * P.cutoff);
+    auto km = ctx->minimg ? k_pairmask<T, true> : k_pairmask<T, false>;
+    km<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->work, ctx->n_work, (const T4 *)ctx->posq, (const T4 *)ctx->chunk_pos, rcm,
+                                         (T)P.box[0], (T)P.box[1], (T)P.box[2], ctx->pmask, ctx->pmask_t, ctx->n_work + 1);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+}  // namespace
+
+int filter_launch(ap_ctx *ctx, cudaStream_t s) {
+    return ctx->prec == AP_FP64 ? filter_t<double>(ctx, s) : filter_t<float>(ctx, s);
+}
+
+// (re)allocate the chunk arrays after a list build: capacity = block-pair tiles
+int filter_alloc(ap_ctx *ctx) {
+    const long cap = ctx->cap_tiles;
+    if (cap <= ctx->cap_chunks) return AP_OK;
+    void *ptrs[] = {ctx->chunk_j, ctx->chunk_pos, ctx->chunk_src, ctx->chunk_mask, ctx->chunk_flag, ctx->work,
+                    ctx->pmask, ctx->pmask_t};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    const size_t es = ctx->prec == AP_FP64 ? 8 : 4;
+    AP_CUDA(cudaMalloc((void **)&ctx->chunk_j, sizeof(int) * 32 * cap));
+    AP_CUDA(cudaMalloc((void **)&ctx->chunk_pos, 4 * es * 32 * cap));
+    AP_CUDA(cudaMalloc((void **)&ctx->chunk_src, sizeof(int) * 32 * cap));
+    AP_CUDA(cudaMalloc((void **)&ctx->chunk_mask, sizeof(unsigned) * 32 * cap));
+    AP_CUDA(cudaMalloc((void **)&ctx->chunk_flag, sizeof(int) * cap));
+    AP_CUDA(cudaMalloc((void **)&ctx->work, sizeof(int2) * (cap + ctx->n_blocks)));
+    AP_CUDA(cudaMalloc((void **)&ctx->pmask, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
+    AP_CUDA(cudaMalloc((void **)&ctx->pmask_t, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
+    ctx->cap_chunks = (int)cap;
+    return AP_OK;
+}

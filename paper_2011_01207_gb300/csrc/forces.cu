@@ -60,8 +60,7 @@ __device__ __forceinline__ void mu_dot_field_grad(T q, const T *d, const T *Q /*
 // one warp per tile (grid-stride); accumulators per lane: force (3), dU/dd (3), dU/dQ (6)
 template <class T, bool MINIMG>
 __global__ void __launch_bounds__(128) k_pair_forces(
-    const int2 *__restrict__ tiles, const float4 *__restrict__ tshift, const int *__restrict__ tile_excl,
-    const unsigned *__restrict__ masks, int ntiles, const typename V4<T>::type *__restrict__ posq,
+    WorkArgs wa, const typename V4<T>::type *__restrict__ posq,
     const typename V4<T>::type *__restrict__ dipd, const typename V4<T>::type *__restrict__ quad0,
     const typename V4<T>::type *__restrict__ quad1, const typename V4<T>::type *__restrict__ muv,
     double *__restrict__ frc, double *__restrict__ gdip, double *__restrict__ gquad, int n_pad, PairConsts<T> pc,
@@ -70,29 +69,43 @@ __global__ void __launch_bounds__(128) k_pair_forces(
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
+    const long nitems = *wa.n_work;
+    const T4 *cpos = (const T4 *)wa.chunk_pos;
     const T f = (T)fconst;
     const T third = T(1.0 / 3.0);
-    for (long t = gw; t < ntiles; t += nw) {
-        const int2 IJ = tiles[t];
-        const int si = IJ.x * 32 + lane, sj = IJ.y * 32 + lane;
+    for (long t = gw; t < nitems; t += nw) {
+        const int2 it = wa.work[t];
+        const bool diag = it.y < 0;
+        const int si = it.x * 32 + lane;
         T4 a = posq[si], b = dipd[si], c = quad0[si], d = quad1[si], m = muv[si];
         const T xi = a.x, yi = a.y, zi = a.z, qi = a.w, ti = b.w;
         const T ndi[3] = {-b.x, -b.y, -b.z};
         const T Qi[6] = {c.x, c.y, c.z, c.w, d.x, d.y};
         const T mi[3] = {m.x, m.y, m.z};
-        a = posq[sj]; b = dipd[sj]; c = quad0[sj]; d = quad1[sj]; m = muv[sj];
-        T xj = a.x, yj = a.y, zj = a.z, qj = a.w, tj = b.w;
-        T dj[3] = {b.x, b.y, b.z};
-        T Qj[6] = {c.x, c.y, c.z, c.w, d.x, d.y};
-        T mj[3] = {m.x, m.y, m.z};
-        T sx = 0, sy = 0, sz = 0;
-        if (!MINIMG) {
-            float4 shv = tshift[t];
-            sx = shv.x; sy = shv.y; sz = shv.z;
+        int sj;
+        T xj, yj, zj, tj;
+        unsigned mask;
+        if (diag) {
+            sj = si;
+            xj = xi; yj = yi; zj = zi; tj = ti;
+            const int e = wa.tile_excl[wa.tile_off[it.x]];
+            mask = e >= 0 ? wa.excl_mask[(size_t)e * 32 + lane] : 0u;
+        } else {
+            const size_t cs = (size_t)it.y * 32 + lane;
+            sj = wa.chunk_j[cs];
+            const T4 p = cpos[cs];
+            xj = p.x; yj = p.y; zj = p.z; tj = p.w;
+            mask = wa.chunk_flag[it.y] ? wa.chunk_mask[cs] : 0u;
         }
-        const int slot = tile_excl[t];
-        const unsigned mask = slot >= 0 ? masks[slot * 32 + lane] : 0u;
-        const bool diag = IJ.x == IJ.y;
+        T qj = 0;
+        T dj[3] = {0, 0, 0}, Qj[6] = {0, 0, 0, 0, 0, 0}, mj[3] = {0, 0, 0};
+        if (sj >= 0) {
+            a = posq[sj]; b = dipd[sj]; c = quad0[sj]; d = quad1[sj]; m = muv[sj];
+            qj = a.w;
+            dj[0] = b.x; dj[1] = b.y; dj[2] = b.z;
+            Qj[0] = c.x; Qj[1] = c.y; Qj[2] = c.z; Qj[3] = c.w; Qj[4] = d.x; Qj[5] = d.y;
+            mj[0] = m.x; mj[1] = m.y; mj[2] = m.z;
+        }
         T ai[12], aj[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) ai[k] = aj[k] = 0;
@@ -104,8 +117,6 @@ __global__ void __launch_bounds__(128) k_pair_forces(
                     dx -= pc.L[0] * ap_rint(dx * pc.iL[0]);
                     dy -= pc.L[1] * ap_rint(dy * pc.iL[1]);
                     dz -= pc.L[2] * ap_rint(dz * pc.iL[2]);
-                } else {
-                    dx += sx; dy += sy; dz += sz;
                 }
                 const T r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < pc.rc2) {
@@ -163,7 +174,7 @@ __global__ void __launch_bounds__(128) k_pair_forces(
             }
         }
         if (si < pc.n) flush12(frc, gdip, gquad, n_pad, si, ai);
-        if (!diag && sj < pc.n) flush12(frc, gdip, gquad, n_pad, sj, aj);
+        if (!diag && sj >= 0) flush12(frc, gdip, gquad, n_pad, sj, aj);
     }
 }
 
@@ -362,8 +373,7 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
     int grid = std::max(1, per_sm) * ctx->sm_count;
-    kern<<<grid, 128, 0, s>>>(ctx->tiles, ctx->tshift, ctx->tile_excl, ctx->excl_mask, ctx->n_tiles,
-                              (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
+    kern<<<grid, 128, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
                               (const T4 *)ctx->quad1, (const T4 *)ctx->p, ctx->frc, ctx->gdip, ctx->gquad, n_pad,
                               pc, f);
     AP_CUDA(cudaGetLastError());

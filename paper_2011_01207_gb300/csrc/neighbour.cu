@@ -336,10 +336,12 @@ int nb_build(ap_ctx *ctx, const double *d_xyz, const int *d_off, const int *d_at
         AP_CUDA(cudaFreeAsync(flag, s));
         AP_CUDA(cudaFreeAsync(err, s));
     }
+    AP_CUDA(cudaMemcpyAsync(ctx->tile_off, tile_off, sizeof(int) * (nb + 1), cudaMemcpyDeviceToDevice, s));
     AP_CUDA(cudaFreeAsync(half, s));
     AP_CUDA(cudaFreeAsync(hmax, s));
     AP_CUDA(cudaStreamSynchronize(s));
     AP_CUDA(cudaGetLastError());
+    if ((r = filter_alloc(ctx))) return r;
     ctx->lists_valid = 1;
     ctx->config_valid = 0;
     ctx->graph_ok = 0;             // pointers may have moved: rebuild the solve graph

@@ -27,12 +27,27 @@ struct PairConsts {
     int n;             // real atoms; slots >= n are padding
 };
 
+// erfc(x) given e2 = exp(-x^2), x >= 0. FP32: the rational approximation of Abramowitz &
+// Stegun, Handbook of Mathematical Functions (1964), formula 7.1.26,
+//   erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-x^2},  t = 1 / (1 + p x),
+// absolute error <= 1.5e-7, which reuses the e^{-x^2} the recursion needs anyway.
+// FP64: the library erfc.
+__device__ __forceinline__ float erfc_e2(float x, float e2) {
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f),
+                                         -0.284496736f), 0.254829592f);
+    return poly * e2;
+}
+__device__ __forceinline__ double erfc_e2(double x, double) { return erfc(x); }
+__device__ __forceinline__ float ap_fexp(float x) { return __expf(x); }
+__device__ __forceinline__ double ap_fexp(double x) { return exp(x); }
+
 // Screened B_1..B_nmax and Coulomb U_1..U_nmax at r (rinv = 1/r, rinv2 = 1/r^2).
 template <class T, int NMAX>
 __device__ __forceinline__ void screened(const PairConsts<T> &pc, T r, T rinv, T rinv2, T *B, T *U) {
     T x = pc.beta * r;
-    T e2 = ap_exp(-x * x);
-    T b = ap_erfc(x) * rinv;
+    T e2 = ap_fexp(-x * x);
+    T b = erfc_e2(x, e2) * rinv;
     T u = rinv;
 #pragma unroll
     for (int k = 1; k <= NMAX; ++k) {
@@ -46,7 +61,7 @@ __device__ __forceinline__ void screened(const PairConsts<T> &pc, T r, T rinv, T
 // 1 - lambda_{2k+1} for k = 1..NMAX from the Thole argument s
 template <class T, int NMAX>
 __device__ __forceinline__ void thole_oml(T s, T *oml) {
-    T e = ap_exp(-s);
+    T e = ap_fexp(-s);
     oml[0] = e;
     if (NMAX > 1) oml[1] = (T(1) + s) * e;
     if (NMAX > 2) oml[2] = (T(1) + s + T(0.6) * s * s) * e;

@@ -74,7 +74,7 @@ template <class T>
 __global__ void k_init_residual(const double *__restrict__ E, const double *__restrict__ alpha,
                                 const double *__restrict__ mu, double *__restrict__ acc,
                                 const T *__restrict__ rec, double self_coef, int n_pad, double *__restrict__ r,
-                                typename V4<T>::type *__restrict__ p, PcgState *st) {
+                                typename V4<T>::type *__restrict__ p, double *__restrict__ part) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double rz = 0.0, zz = 0.0;
     if (s < n_pad) {
@@ -94,14 +94,29 @@ __global__ void k_init_residual(const double *__restrict__ E, const double *__re
     }
     block_sum2<NT>(rz, zz);
     if (threadIdx.x == 0) {
-        atomicAdd(&st->rz_new, rz);
-        atomicAdd(&st->zz, zz);
+        part[blockIdx.x] = rz;
+        part[gridDim.x + blockIdx.x] = zz;
     }
 }
 
-__global__ void k_init_finish(PcgState *st, int n, double tol, int max_iter) {
-    double eps = AP_DEBYE * sqrt(st->zz / n);
-    st->rz = st->rz_new;
+// sum of nparts partials (one block of NT threads, fixed order: deterministic)
+__device__ __forceinline__ void sum_partials2(const double *part, int nparts, double &a, double &b) {
+    a = 0.0;
+    b = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += NT) {
+        a += part[k];
+        b += part[nparts + k];
+    }
+    block_sum2<NT>(a, b);
+}
+
+__global__ void k_init_finish(PcgState *st, const double *__restrict__ part, int nparts, int n, double tol,
+                              int max_iter) {
+    double rz, zz;
+    sum_partials2(part, nparts, rz, zz);
+    if (threadIdx.x != 0) return;
+    double eps = AP_DEBYE * sqrt(zz / n);
+    st->rz = rz;
     st->eps = eps;
     st->eps0 = eps;
     st->tol = tol;
@@ -121,12 +136,33 @@ __global__ void k_set_cond(cudaGraphConditionalHandle h, const PcgState *st) {
     cudaGraphSetConditional(h, (st->done || st->max_iter < 1) ? 0u : 1u);
 }
 
-// last node of every loop iteration: continue only while not done, and never beyond
-// max_iter iterations whatever the update kernel did (the WHILE node cannot spin forever)
-__global__ void k_loop_cond(cudaGraphConditionalHandle h, PcgState *st) {
+// closes an iteration (one block): sums the update's partials in a fixed order, sets the
+// convergence measure, beta and the stop decision; inside the graph it also drives the
+// WHILE node - never beyond max_iter iterations, so the loop cannot spin forever
+__global__ void k_finish_iter(PcgState *st, const double *__restrict__ part, int nparts, int n,
+                              cudaGraphConditionalHandle h, int use_cond) {
+    double rzn, zzt;
+    sum_partials2(part, nparts, rzn, zzt);
+    if (threadIdx.x != 0) return;
+    const double eps = AP_DEBYE * sqrt(zzt / n);
+    st->iter += 1;
     st->guard += 1;
-    const bool more = !st->done && st->guard < st->max_iter;
-    cudaGraphSetConditional(h, more ? 1u : 0u);
+    st->eps = eps;
+    const bool bad = !isfinite(eps) || !isfinite(st->gamma);
+    if (bad) st->nonfinite = 1;
+    if (eps <= st->tol || bad) {
+        st->done = 1;
+        st->status = AP_OK;
+    } else if (st->iter >= st->max_iter) {
+        st->done = 1;
+        st->status = AP_NOT_CONVERGED;
+    }
+    st->beta = rzn / st->rz;
+    st->rz = rzn;
+    if (use_cond) {
+        const bool more = !st->done && st->guard < st->max_iter;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
 }
 
 // p = alpha r + beta p
@@ -147,7 +183,7 @@ __global__ void k_direction(const double *__restrict__ r, const double *__restri
 template <class T>
 __global__ void k_apply(const typename V4<T>::type *__restrict__ p, const double *__restrict__ alpha,
                         double *__restrict__ acc, const T *__restrict__ rec, double self_coef, int n_pad,
-                        double *__restrict__ q, PcgState *st) {
+                        double *__restrict__ q, double *__restrict__ part) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double pq = 0.0, dummy = 0.0;
     if (s < n_pad) {
@@ -163,16 +199,30 @@ __global__ void k_apply(const typename V4<T>::type *__restrict__ p, const double
         }
     }
     block_sum2<NT>(pq, dummy);
-    if (threadIdx.x == 0) atomicAdd(&st->pq, pq);
+    if (threadIdx.x == 0) part[blockIdx.x] = pq;
 }
 
-// mu += gamma p; r -= gamma q; partial r.z, z.z; the last block closes the iteration
+// mu += gamma p; r -= gamma q; partial r.z and z.z per block (gamma from the p.q partials)
 template <class T>
 __global__ void k_update(const typename V4<T>::type *__restrict__ p, const double *__restrict__ q,
-                         const double *__restrict__ alpha, int n, int n_pad, double *__restrict__ mu,
-                         double *__restrict__ r, PcgState *st) {
-    __shared__ bool last;
-    const double gamma = st->rz / st->pq;
+                         const double *__restrict__ alpha, int n_pad, double *__restrict__ mu,
+                         double *__restrict__ r, PcgState *st, const double *__restrict__ part_pq,
+                         double *__restrict__ part) {
+    __shared__ double s_gamma;
+    double pq, dummy;
+    {
+        double a = 0.0;
+        for (int k = threadIdx.x; k < gridDim.x; k += NT) a += part_pq[k];
+        pq = a;
+        dummy = 0.0;
+        block_sum2<NT>(pq, dummy);
+        if (threadIdx.x == 0) {
+            s_gamma = st->rz / pq;
+            if (blockIdx.x == 0) st->gamma = s_gamma;
+        }
+        __syncthreads();
+    }
+    const double gamma = s_gamma;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double rz = 0.0, zz = 0.0;
     if (s < n_pad) {
@@ -190,36 +240,8 @@ __global__ void k_update(const typename V4<T>::type *__restrict__ p, const doubl
     }
     block_sum2<NT>(rz, zz);
     if (threadIdx.x == 0) {
-        atomicAdd(&st->rz_new, rz);
-        atomicAdd(&st->zz, zz);
-        __threadfence();
-        unsigned prev = atomicAdd(&st->blocks_done, 1u);
-        last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        volatile PcgState *vs = st;
-        const double rzn = vs->rz_new, zzt = vs->zz;
-        const double eps = AP_DEBYE * sqrt(zzt / n);
-        st->gamma = gamma;
-        st->iter += 1;
-        st->eps = eps;
-        const bool bad = !isfinite(eps) || !isfinite(gamma);
-        if (bad) st->nonfinite = 1;
-        if (eps <= st->tol || bad) {
-            st->done = 1;
-            st->status = AP_OK;
-        } else if (st->iter >= st->max_iter) {
-            st->done = 1;
-            st->status = AP_NOT_CONVERGED;
-        }
-        st->beta = rzn / st->rz;
-        st->rz = rzn;
-        st->pq = 0.0;
-        st->rz_new = 0.0;
-        st->zz = 0.0;
-        st->blocks_done = 0;
+        part[blockIdx.x] = rz;
+        part[gridDim.x + blockIdx.x] = zz;
     }
 }
 
@@ -251,11 +273,12 @@ int enqueue_iteration(ap_ctx *ctx, cudaGraphConditionalHandle h, int use_cond, c
     AP_CUDA(cudaGetLastError());
     int rc = matvec_into<T>(ctx, ctx->p, main, aux);
     if (rc) return rc;
+    double *part_pq = ctx->red_part, *part_rz = ctx->red_part + nb;
     k_apply<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->alpha, ctx->acc, (const T *)ctx->rec,
-                                     self_coef(ctx), ctx->n_pad, ctx->qv, ctx->st);
-    k_update<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n, ctx->n_pad, ctx->mu,
-                                      ctx->r, ctx->st);
-    if (use_cond) k_loop_cond<<<1, 1, 0, main>>>(h, ctx->st);
+                                     self_coef(ctx), ctx->n_pad, ctx->qv, part_pq);
+    k_update<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
+                                      part_pq, part_rz);
+    k_finish_iter<<<1, NT, 0, main>>>(ctx->st, part_rz, nb, ctx->n, h, use_cond);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -332,8 +355,8 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
     int rc = matvec_into<T>(ctx, ctx->p);
     if (rc) return rc;
     k_init_residual<T><<<nb, NT, 0, s>>>(ctx->E, ctx->alpha, ctx->mu, ctx->acc, (const T *)ctx->rec,
-                                          self_coef(ctx), ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->st);
-    k_init_finish<<<1, 1, 0, s>>>(ctx->st, ctx->n, tol, max_iter);
+                                          self_coef(ctx), ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->red_part);
+    k_init_finish<<<1, NT, 0, s>>>(ctx->st, ctx->red_part, nb, ctx->n, tol, max_iter);
     AP_CUDA(cudaGetLastError());
     if (!ctx->graph_tried) {
         if (build_graph<T>(ctx) != AP_OK) {   // no graph: the host-driven loop below

@@ -14,6 +14,7 @@
 // Grid layout: [z][y][x], x contiguous; complex half grid [z][y][x/2+1].
 #include "common.cuh"
 
+#include <climits>
 #include <cmath>
 #include <vector>
 

@@ -43,54 +43,71 @@ __device__ __forceinline__ void flush3(double *acc, int n_pad, int slot, double 
 template <class T>
 __device__ __forceinline__ T shfl1(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
+// Work items come from the per-configuration filter: (I, -1) is block I against itself,
+// (I, c) is block I against filtered chunk c (32 atoms of partner blocks, positions already
+// in the periodic image next to I, padding = NaN phantoms). Items are sorted by I, so a
+// warp keeps block I's i-side sums in FP64 registers across consecutive items.
+
 // ---------------------------------------------------------------------------------------
 // a2: permanent multipole field, E_i += E(R; q_j, d_j, Q_j) and E_j += E(-R; q_i, d_i, Q_i)
 template <class T, bool MINIMG>
 __global__ void __launch_bounds__(256) k_perm_field(
-    const int2 *__restrict__ tiles, const float4 *__restrict__ tshift, const int *__restrict__ tile_excl,
-    const unsigned *__restrict__ masks, int ntiles, const typename V4<T>::type *__restrict__ posq,
-    const typename V4<T>::type *__restrict__ dipd, const typename V4<T>::type *__restrict__ quad0,
-    const typename V4<T>::type *__restrict__ quad1, double *__restrict__ acc, int n_pad, PairConsts<T> pc) {
+    WorkArgs wa, const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
+    const typename V4<T>::type *__restrict__ quad0, const typename V4<T>::type *__restrict__ quad1,
+    double *__restrict__ acc, int n_pad, PairConsts<T> pc) {
     typedef typename V4<T>::type T4;
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
-    const long t0 = ntiles * gw / nw, t1 = ntiles * (gw + 1) / nw;
+    const long nitems = *wa.n_work;
+    const long t0 = nitems * gw / nw, t1 = nitems * (gw + 1) / nw;
+    const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
     double ax = 0, ay = 0, az = 0;
     T xi = 0, yi = 0, zi = 0, qi = 0, dix = 0, diy = 0, diz = 0, ti = 0;
     T qxx = 0, qxy = 0, qxz = 0, qyy = 0, qyz = 0, qzz = 0;
     for (long t = t0; t < t1; ++t) {
-        const int2 IJ = tiles[t];
-        if (IJ.x != curI) {
+        const int2 it = wa.work[t];
+        if (it.x != curI) {
             if (curI >= 0 && curI * 32 + lane < pc.n) flush3(acc, n_pad, curI * 32 + lane, ax, ay, az);
             ax = ay = az = 0;
-            curI = IJ.x;
+            curI = it.x;
             const int si = curI * 32 + lane;
             T4 a = posq[si], b = dipd[si], c = quad0[si], d = quad1[si];
             xi = a.x; yi = a.y; zi = a.z; qi = a.w;
             dix = b.x; diy = b.y; diz = b.z; ti = b.w;
             qxx = c.x; qxy = c.y; qxz = c.z; qyy = c.w; qyz = d.x; qzz = d.y;
         }
-        const int sj = IJ.y * 32 + lane;
-        T4 a = posq[sj], b = dipd[sj], c = quad0[sj], d = quad1[sj];
-        T xj = a.x, yj = a.y, zj = a.z, qj = a.w, djx = b.x, djy = b.y, djz = b.z, tj = b.w;
-        T pxx = c.x, pxy = c.y, pxz = c.z, pyy = c.w, pyz = d.x, pzz = d.y;
-        T sx = 0, sy = 0, sz = 0;
-        if (!MINIMG) {
-            float4 sh = tshift[t];
-            sx = sh.x; sy = sh.y; sz = sh.z;
+        const bool diag = it.y < 0;
+        int sj;
+        T xj, yj, zj, tj;
+        unsigned mask;
+        if (diag) {
+            sj = curI * 32 + lane;
+            const T4 a = posq[sj];
+            xj = a.x; yj = a.y; zj = a.z; tj = ti;
+            const int e = wa.tile_excl[wa.tile_off[curI]];
+            mask = e >= 0 ? wa.excl_mask[(size_t)e * 32 + lane] : 0u;
+        } else {
+            const size_t cs = (size_t)it.y * 32 + lane;
+            sj = wa.chunk_j[cs];
+            const T4 a = cpos[cs];
+            xj = a.x; yj = a.y; zj = a.z; tj = a.w;
+            mask = wa.chunk_flag[it.y] ? wa.chunk_mask[cs] : 0u;
         }
-        const int slot = tile_excl[t];
-        const unsigned mask = slot >= 0 ? masks[slot * 32 + lane] : 0u;
-        const bool diag = IJ.x == IJ.y;
+        T qj = 0, djx = 0, djy = 0, djz = 0, pxx = 0, pxy = 0, pxz = 0, pyy = 0, pyz = 0, pzz = 0;
+        if (sj >= 0) {
+            const T4 a = posq[sj], b = dipd[sj], c = quad0[sj], d = quad1[sj];
+            qj = a.w; djx = b.x; djy = b.y; djz = b.z;
+            pxx = c.x; pxy = c.y; pxz = c.z; pyy = c.w; pyz = d.x; pzz = d.y;
+        }
         T fx = 0, fy = 0, fz = 0, gx = 0, gy = 0, gz = 0;
 #pragma unroll 2
         for (int s = 0; s < 32; ++s) {
             const int jl = (lane + s) & 31;
             if (!(diag && s == 0)) {
                 T dx, dy, dz;
-                pair_vector<T, MINIMG>(pc, xi, yi, zi, xj, yj, zj, sx, sy, sz, dx, dy, dz);
+                pair_vector<T, MINIMG>(pc, xi, yi, zi, xj, yj, zj, T(0), T(0), T(0), dx, dy, dz);
                 const T r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < pc.rc2) {
                     const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
@@ -108,7 +125,7 @@ __global__ void __launch_bounds__(256) k_perm_field(
                     T Qz = pxz * dx + pyz * dy + pzz * dz;
                     T RQR = Qx * dx + Qy * dy + Qz * dz;
                     T fac = qj * R1 + dR * R2 + RQR * R3 * T(1.0 / 3.0);
-                    T q2 = T(2.0 / 3.0) * R2;
+                    const T q2 = T(2.0 / 3.0) * R2;
                     fx += fac * dx - R1 * djx - q2 * Qx;
                     fy += fac * dy - R1 * djy - q2 * Qy;
                     fz += fac * dz - R1 * djz - q2 * Qz;
@@ -134,77 +151,153 @@ __global__ void __launch_bounds__(256) k_perm_field(
             gx = shfl1(gx, src); gy = shfl1(gy, src); gz = shfl1(gz, src);
         }
         ax += (double)fx; ay += (double)fy; az += (double)fz;
-        if (!diag && sj < pc.n) flush3(acc, n_pad, sj, (double)gx, (double)gy, (double)gz);
+        if (!diag && sj >= 0) flush3(acc, n_pad, sj, (double)gx, (double)gy, (double)gz);
     }
     if (curI >= 0 && curI * 32 + lane < pc.n) flush3(acc, n_pad, curI * 32 + lane, ax, ay, az);
 }
 
 // ---------------------------------------------------------------------------------------
-// a5: dipole-field matrix-vector product, E_i += -R1 p_j + R2 (p_j.R) R (and i <-> j)
+// a5: dipole-field matrix-vector product, E_i += -R1 p_j + R2 (p_j.R) R (and i <-> j).
+// Positions are fixed during a solve, so the in-range pairs of every work item and their
+// transposed bit matrix were found once per configuration. Per item, a warp stages the
+// 32 i-atoms and 32 j-atoms in shared memory and writes a queue of "pair sides"
+// (target atom, source atom): the row bits give the field at each i-atom, the column bits
+// the field at each j-atom. The queue is sorted by target, and each lane takes an equal
+// contiguous slice of it, accumulating in registers while the target stays the same and
+// adding to a shared per-target sum only when it changes (a few times per lane per item).
+// So every lane evaluates one in-range pair side per step, whatever the pair distribution;
+// the field expression is even in R, so one code path serves both sides.
+template <class T>
+struct MvSmem {
+    typename V4<T>::type pos[64];    // x, y, z, Thole factor: [0,32) block I, [32,64) the item's j atoms
+    typename V4<T>::type p[64];      // dipoles of the same atoms
+    T acc[3][64];                    // per-target sums of the item
+    unsigned short queue[2048];      // (target << 5) | source-lane, sorted by target
+};
+
 template <class T, bool MINIMG>
-__global__ void __launch_bounds__(256) k_matvec(
-    const int2 *__restrict__ tiles, const float4 *__restrict__ tshift, int ntiles,
-    const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
+__global__ void __launch_bounds__(128) k_matvec(
+    WorkArgs wa, const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
     const typename V4<T>::type *__restrict__ pv, double *__restrict__ acc, int n_pad, PairConsts<T> pc) {
     typedef typename V4<T>::type T4;
+    __shared__ MvSmem<T> smem[4];
+    MvSmem<T> &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
-    const long t0 = ntiles * gw / nw, t1 = ntiles * (gw + 1) / nw;
+    const long nitems = *wa.n_work;
+    const long t0 = nitems * gw / nw, t1 = nitems * (gw + 1) / nw;
+    const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
     double ax = 0, ay = 0, az = 0;
-    T xi = 0, yi = 0, zi = 0, ti = 0, pix = 0, piy = 0, piz = 0;
     for (long t = t0; t < t1; ++t) {
-        const int2 IJ = tiles[t];
-        if (IJ.x != curI) {
+        const int2 it = wa.work[t];
+        __syncwarp();   // every lane is done with the previous item's staging
+        if (it.x != curI) {
             if (curI >= 0 && curI * 32 + lane < pc.n) flush3(acc, n_pad, curI * 32 + lane, ax, ay, az);
             ax = ay = az = 0;
-            curI = IJ.x;
+            curI = it.x;
             const int si = curI * 32 + lane;
-            T4 a = posq[si], b = pv[si];
-            xi = a.x; yi = a.y; zi = a.z; ti = dipd[si].w;
-            pix = b.x; piy = b.y; piz = b.z;
+            T4 a = posq[si];
+            a.w = dipd[si].w;
+            S.pos[lane] = a;
+            S.p[lane] = pv[si];
         }
-        const int sj = IJ.y * 32 + lane;
-        T4 a = posq[sj], b = pv[sj];
-        T xj = a.x, yj = a.y, zj = a.z, tj = dipd[sj].w, pjx = b.x, pjy = b.y, pjz = b.z;
-        T sx = 0, sy = 0, sz = 0;
-        if (!MINIMG) {
-            float4 sh = tshift[t];
-            sx = sh.x; sy = sh.y; sz = sh.z;
+        const bool diag = it.y < 0;
+        int sj = -1;
+        if (diag) {
+            S.pos[32 + lane] = S.pos[lane];
+            S.p[32 + lane] = S.p[lane];
+        } else {
+            const size_t cs = (size_t)it.y * 32 + lane;
+            sj = wa.chunk_j[cs];
+            S.pos[32 + lane] = cpos[cs];
+            T4 z;
+            z.x = z.y = z.z = z.w = T(0);
+            S.p[32 + lane] = sj >= 0 ? pv[sj] : z;
         }
-        const bool diag = IJ.x == IJ.y;
-        T fx = 0, fy = 0, fz = 0, gx = 0, gy = 0, gz = 0;
-#pragma unroll 4
-        for (int s = 0; s < 32; ++s) {
-            if (!(diag && s == 0)) {
-                T dx, dy, dz;
-                pair_vector<T, MINIMG>(pc, xi, yi, zi, xj, yj, zj, sx, sy, sz, dx, dy, dz);
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < pc.rc2) {
-                    const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
-                    T B[2], U[2], oml[2];
-                    screened<T, 2>(pc, r, rinv, rinv2, B, U);
-                    thole_oml<T, 2>(pc.thole_a * r2 * r * ti * tj, oml);
-                    const T R1 = B[0] - oml[0] * U[0];
-                    const T R2 = B[1] - oml[1] * U[1];
-                    T pr = (pjx * dx + pjy * dy + pjz * dz) * R2;
-                    fx += pr * dx - R1 * pjx;
-                    fy += pr * dy - R1 * pjy;
-                    fz += pr * dz - R1 * pjz;
-                    pr = (pix * dx + piy * dy + piz * dz) * R2;
-                    gx += pr * dx - R1 * pix;
-                    gy += pr * dy - R1 * piy;
-                    gz += pr * dz - R1 * piz;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            S.acc[c][lane] = T(0);
+            S.acc[c][32 + lane] = T(0);
+        }
+        // queue: row sides (target i-lane, source j-lane), then column sides (target 32 + j-lane)
+        unsigned row = wa.pmask[(size_t)t * 32 + lane];
+        unsigned col = wa.pmask_t[(size_t)t * 32 + lane];
+        const int nr = __popc(row), nc = __popc(col);
+        int ir = nr, ic = nc;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int vr = __shfl_up_sync(0xffffffffu, ir, off);
+            const int vc = __shfl_up_sync(0xffffffffu, ic, off);
+            if (lane >= off) { ir += vr; ic += vc; }
+        }
+        const int prow = __shfl_sync(0xffffffffu, ir, 31);
+        const int total = prow + __shfl_sync(0xffffffffu, ic, 31);
+        int pos = ir - nr;
+        while (row) {
+            const int b = __ffs(row) - 1;
+            row &= row - 1u;
+            S.queue[pos++] = (unsigned short)((lane << 5) | b);
+        }
+        pos = prow + ic - nc;
+        while (col) {
+            const int b = __ffs(col) - 1;
+            col &= col - 1u;
+            S.queue[pos++] = (unsigned short)(((32 + lane) << 5) | b);
+        }
+        __syncwarp();
+        const int per = (total + 31) >> 5;
+        const int e0 = lane * per, e1 = min(total, e0 + per);
+        int cur = -1;
+        T4 self;
+        self.x = self.y = self.z = self.w = T(0);
+        T f0 = 0, f1 = 0, f2 = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int q = S.queue[e];
+            const int tg = q >> 5;
+            if (tg != cur) {
+                if (cur >= 0) {
+                    atomicAdd(&S.acc[0][cur], f0);
+                    atomicAdd(&S.acc[1][cur], f1);
+                    atomicAdd(&S.acc[2][cur], f2);
                 }
+                f0 = f1 = f2 = T(0);
+                cur = tg;
+                self = S.pos[tg];
             }
-            const int src = (lane + 1) & 31;
-            xj = shfl1(xj, src); yj = shfl1(yj, src); zj = shfl1(zj, src); tj = shfl1(tj, src);
-            pjx = shfl1(pjx, src); pjy = shfl1(pjy, src); pjz = shfl1(pjz, src);
-            gx = shfl1(gx, src); gy = shfl1(gy, src); gz = shfl1(gz, src);
+            const int src = (q & 31) + (tg < 32 ? 32 : 0);   // a row side's source is a j atom
+            const T4 other = S.pos[src], po = S.p[src];
+            T dx, dy, dz;
+            pair_vector<T, MINIMG>(pc, self.x, self.y, self.z, other.x, other.y, other.z, T(0), T(0), T(0), dx, dy, dz);
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+            T B[2], U[2], oml[2];
+            screened<T, 2>(pc, r, rinv, rinv2, B, U);
+            thole_oml<T, 2>(pc.thole_a * r2 * r * self.w * other.w, oml);
+            const T R1 = B[0] - oml[0] * U[0];
+            const T R2 = B[1] - oml[1] * U[1];
+            const T pr = (po.x * dx + po.y * dy + po.z * dz) * R2;
+            f0 += pr * dx - R1 * po.x;
+            f1 += pr * dy - R1 * po.y;
+            f2 += pr * dz - R1 * po.z;
         }
-        ax += (double)fx; ay += (double)fy; az += (double)fz;
-        if (!diag && sj < pc.n) flush3(acc, n_pad, sj, (double)gx, (double)gy, (double)gz);
+        if (cur >= 0) {
+            atomicAdd(&S.acc[0][cur], f0);
+            atomicAdd(&S.acc[1][cur], f1);
+            atomicAdd(&S.acc[2][cur], f2);
+        }
+        __syncwarp();
+        ax += (double)S.acc[0][lane];
+        ay += (double)S.acc[1][lane];
+        az += (double)S.acc[2][lane];
+        if (diag) {
+            ax += (double)S.acc[0][32 + lane];
+            ay += (double)S.acc[1][32 + lane];
+            az += (double)S.acc[2][32 + lane];
+        } else if (sj >= 0) {
+            flush3(acc, n_pad, sj, (double)S.acc[0][32 + lane], (double)S.acc[1][32 + lane],
+                   (double)S.acc[2][32 + lane]);
+        }
     }
     if (curI >= 0 && curI * 32 + lane < pc.n) flush3(acc, n_pad, curI * 32 + lane, ax, ay, az);
 }
@@ -227,6 +320,7 @@ PairConsts<T> make_consts(const ap_ctx *ctx) {
     return pc;
 }
 
+
 template <class K>
 int resident_grid(ap_ctx *ctx, K kernel, int threads) {
     int per_sm = 0;
@@ -242,8 +336,7 @@ int perm_field_t(ap_ctx *ctx, cudaStream_t s) {
     static int grids[2] = {0, 0};
     int &grid = grids[ctx->minimg];
     if (!grid) grid = resident_grid(ctx, kern, 256);
-    kern<<<grid, 256, 0, s>>>(ctx->tiles, ctx->tshift, ctx->tile_excl, ctx->excl_mask, ctx->n_tiles,
-                              (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
+    kern<<<grid, 256, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
                               (const T4 *)ctx->quad1, ctx->acc, ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
@@ -256,9 +349,9 @@ int matvec_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
     auto kern = ctx->minimg ? k_matvec<T, true> : k_matvec<T, false>;
     static int grids[2] = {0, 0};
     int &grid = grids[ctx->minimg];
-    if (!grid) grid = resident_grid(ctx, kern, 256);
-    kern<<<grid, 256, 0, s>>>(ctx->tiles, ctx->tshift, ctx->n_tiles, (const T4 *)ctx->posq,
-                              (const T4 *)ctx->dipd, (const T4 *)p, ctx->acc, ctx->n_pad, pc);
+    if (!grid) grid = resident_grid(ctx, kern, 128);
+    kern<<<grid, 128, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)p, ctx->acc,
+                              ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
