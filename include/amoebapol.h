@@ -160,6 +160,35 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 #define AP_KERNEL_SPREAD_MULTIPOLES 5   /* a3: spread of the permanent multipoles */
 int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
 
+/* a8 - Learned initial guess. The paper has no learned component; any PCG start is
+ * valid (the solve converges to the same tolerance), so a better start only saves
+ * iterations. A per-atom perceptron 16 -> 128 -> 128 -> 3 (ReLU) maps rotation-invariant
+ * features to a correction of the direct-field guess:
+ *   mu0_i = alpha_i E_i + 0.02 R_i y_i,   R_i the atom's local frame (identity for
+ *   global-frame atoms). Features (16, FP32): the permanent field E/0.05 in the atom's
+ *   frame (3), the same for its z-atom (3) and x-atom (3), |E|/0.05, alpha, one-hot frame
+ *   kind (none, Z-then-X, bisector), 1, 0.
+ * Master parameters are FP32, ap_mlp_param_count() floats in the order W1 [16][128],
+ * b1 [128], W2 [128][128], b2 [128], W3 [128][3], b3 [3] (W[in][out]). The kernels use a
+ * packed copy (BF16 weights in tensor-core operand layout, FP32 biases) of
+ * ap_mlp_packed_bytes() bytes. Inference and training run on the tcgen05 tensor cores
+ * (BF16 operands, FP32 accumulation in tensor memory). */
+int ap_mlp_param_count(void);
+int ap_mlp_packed_bytes(void);
+/* Pack d_params (FP32 master) into d_packed (device, ap_mlp_packed_bytes()). Async. */
+int ap_mlp_pack(const float* d_params, void* d_packed, void* stream);
+/* y = MLP(feat) for n rows: d_feat [n][16] FP32, d_y [n][3] FP32 (device). Async. */
+int ap_mlp_forward(const void* d_packed, const float* d_feat, int n, float* d_y, void* stream);
+/* AP_OK, or AP_ERR_TIMEOUT once if a bounded tensor-core wait of an earlier MLP kernel
+ * gave up (then its outputs are invalid). Synchronizes the device. */
+int ap_mlp_status(void);
+/* Features of the current configuration (caller order) into d_feat [n][16]; with d_mu
+ * [n][3] given, also training targets d_target [n][3] = R^T (mu - alpha E) / 0.02. */
+int ap_mlp_features(ap_ctx* ctx, const double* d_mu, float* d_feat, float* d_target);
+/* mu0 [n][3] (double, caller order) = the learned guess for the current configuration,
+ * to pass as d_guess to induced_dipoles_pcg(). */
+int ap_learned_guess(ap_ctx* ctx, const void* d_packed, double* d_mu0);
+
 /* Polarization energy without allocation - the paper has no counterpart; it is a
  * convenience for callers that cannot allocate device memory: code whose device memory
  * all belongs to another framework's pool, loops that forbid allocation after set-up,

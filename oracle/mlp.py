@@ -35,12 +35,15 @@ def features(xyz, box, frame, alpha, E):
                            kind, np.ones((n, 1)), np.zeros((n, 1))], axis=1), rot
 
 
-def forward(params, X):
+def forward(params, X, round_hidden=None):
+    """round_hidden (optional) is applied to the hidden activations before they enter the
+    next layer, to emulate a reduced-precision storage of them; None keeps FP64."""
     W1, b1, W2, b2, W3, b3 = params
+    rh = round_hidden or (lambda a: a)
     Z1 = X @ W1 + b1
-    H1 = np.maximum(Z1, 0.0)
+    H1 = rh(np.maximum(Z1, 0.0))
     Z2 = H1 @ W2 + b2
-    H2 = np.maximum(Z2, 0.0)
+    H2 = rh(np.maximum(Z2, 0.0))
     Y = H2 @ W3 + b3
     return Y, (X, Z1, H1, Z2, H2)
 
@@ -63,6 +66,36 @@ def loss_and_grads(params, X, T):
     return L, (dW1, db1, dW2, db2, dW3, db3)
 
 
+def bf16_round(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(a, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def init_params(seed, nin=N_FEAT, nh=128, nout=3):
+    """He-style seeded initialisation (the random numbers the method draws, as inputs)."""
+    rng = np.random.default_rng(seed)
+    return [rng.normal(size=(nin, nh)) * np.sqrt(2.0 / nin), np.zeros(nh),
+            rng.normal(size=(nh, nh)) * np.sqrt(2.0 / nh), np.zeros(nh),
+            rng.normal(size=(nh, nout)) * np.sqrt(1.0 / nh), np.zeros(nout)]
+
+
+def flatten(params):
+    return np.concatenate([p.ravel() for p in params])
+
+
+def unflatten(v, nin=N_FEAT, nh=128, nout=3):
+    shapes = [(nin, nh), (nh,), (nh, nh), (nh,), (nh, nout), (nout,)]
+    out, k = [], 0
+    for sh in shapes:
+        m = int(np.prod(sh))
+        out.append(np.asarray(v[k:k + m], np.float64).reshape(sh))
+        k += m
+    return out
+
+
 def adam_step(params, grads, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam update (t counts from 1); returns new params, m, v."""
     out_p, out_m, out_v = [], [], []
@@ -77,10 +110,12 @@ def adam_step(params, grads, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     return out_p, out_m, out_v
 
 
-def guess(params, xyz, box, frame, alpha, E):
+def guess(params, xyz, box, frame, alpha, E, round_input=None, round_hidden=None):
     """mu0 = alpha E + OUT_SCALE * R y."""
     X, rot = features(xyz, box, frame, alpha, E)
-    Y, _ = forward(params, X)
+    if round_input is not None:
+        X = round_input(X)
+    Y, _ = forward(params, X, round_hidden)
     return alpha[:, None] * E + OUT_SCALE * np.einsum("nab,nb->na", rot, Y)
 
 

@@ -21,7 +21,9 @@ _ERRORS = {-1: "AP_ERR_ARG", -2: "AP_ERR_CUDA", -3: "AP_ERR_CAPACITY", -4: "AP_E
 # every symbol the public header declares
 EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks", "permanent_field",
            "induced_dipoles_pcg", "polarization_energy_forces", "dipole_field_matvec", "ap_list_stats",
-           "ap_stream", "ap_solve_info_last", "ap_time_kernel", "polarization_energy_noalloc")
+           "ap_stream", "ap_solve_info_last", "ap_time_kernel", "polarization_energy_noalloc",
+           "ap_mlp_param_count", "ap_mlp_packed_bytes", "ap_mlp_pack", "ap_mlp_forward", "ap_mlp_status",
+           "ap_mlp_features", "ap_learned_guess")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5}
 
@@ -67,6 +69,13 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "ap_solve_info_last": (I, [P, ctypes.POINTER(ApSolveInfo)]),
         "ap_time_kernel": (I, [P, I, I, ctypes.POINTER(D)]),
         "polarization_energy_noalloc": (I, [P, P, I, P, P]),
+        "ap_mlp_param_count": (I, []),
+        "ap_mlp_packed_bytes": (I, []),
+        "ap_mlp_pack": (I, [P, P, P]),
+        "ap_mlp_forward": (I, [P, P, I, P, P]),
+        "ap_mlp_status": (I, []),
+        "ap_mlp_features": (I, [P, P, P, P]),
+        "ap_learned_guess": (I, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -184,6 +193,55 @@ def polarization_energy_noalloc(mu, field, energy, stream=None):
         _ptr(mu, torch.float64, (n, 3), "mu"), _ptr(field, torch.float64, (n, 3), "field"), int(n),
         _ptr(energy, torch.float64, (1,), "energy"), sp)
     return _check(None, code, "polarization_energy_noalloc")
+
+
+def _stream_ptr(t, stream=None):
+    import torch
+    return ctypes.c_void_p((stream or torch.cuda.current_stream(t.device)).cuda_stream)
+
+
+def ap_mlp_param_count():
+    return load().ap_mlp_param_count()
+
+
+def ap_mlp_packed_bytes():
+    return load().ap_mlp_packed_bytes()
+
+
+def ap_mlp_pack(params, packed, stream=None):
+    import torch
+    _check(None, load().ap_mlp_pack(_ptr(params, torch.float32, (ap_mlp_param_count(),), "params"),
+                                    _ptr(packed, torch.uint8, (ap_mlp_packed_bytes(),), "packed"),
+                                    _stream_ptr(params, stream)), "ap_mlp_pack")
+
+
+def ap_mlp_forward(packed, feat, y, stream=None):
+    import torch
+    n = feat.shape[0]
+    _check(None, load().ap_mlp_forward(_ptr(packed, torch.uint8, (ap_mlp_packed_bytes(),), "packed"),
+                                       _ptr(feat, torch.float32, (n, 16), "feat"), int(n),
+                                       _ptr(y, torch.float32, (n, 3), "y"), _stream_ptr(feat, stream)),
+           "ap_mlp_forward")
+
+
+def ap_mlp_status():
+    return _check(None, load().ap_mlp_status(), "ap_mlp_status")
+
+
+def ap_mlp_features(ctx, feat, mu=None, target=None):
+    import torch
+    n = feat.shape[0]
+    _check(ctx, load().ap_mlp_features(ctx, _ptr(mu, torch.float64, (n, 3), "mu", allow_none=True),
+                                       _ptr(feat, torch.float32, (n, 16), "feat"),
+                                       _ptr(target, torch.float32, (n, 3), "target", allow_none=True)),
+           "ap_mlp_features")
+
+
+def ap_learned_guess(ctx, packed, mu0):
+    import torch
+    n = mu0.shape[0]
+    _check(ctx, load().ap_learned_guess(ctx, _ptr(packed, torch.uint8, (ap_mlp_packed_bytes(),), "packed"),
+                                        _ptr(mu0, torch.float64, (n, 3), "mu0")), "ap_learned_guess")
 
 
 # ---- marshalling helpers ---------------------------------------------------------------

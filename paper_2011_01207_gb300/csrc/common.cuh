@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cufft.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <string>
 
@@ -124,6 +125,8 @@ struct ap_ctx {
     double *red = nullptr;    // small reduction scratch
     double *mu_s = nullptr;   // [3][n_pad] dipoles given to the force call (sorted)
     double *gbuf = nullptr;   // [30][n_pad] PME potential derivatives for the forces
+    float *mlp_feat = nullptr;   // [n_pad][16] learned-guess features (slot order)
+    float *mlp_y = nullptr;      // [n_pad][3] network outputs (slot order)
 
     // graph of the solve loop
     cudaGraphExec_t solve_exec = nullptr;

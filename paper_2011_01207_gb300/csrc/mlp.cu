@@ -1,0 +1,337 @@
+// a8 - Learned initial guess: a per-atom perceptron 16 -> 128 -> 128 -> 3 (ReLU) whose output
+// corrects the direct-field guess, mu0_i = alpha_i E_i + s_out R_i y_i (R_i the atom's frame).
+// Features are rotation-invariant (fields expressed in the atom's local frame), so the
+// guess rotates with the system. BF16 weights and activations, FP32 accumulation on the
+// tcgen05 tensor cores with TMEM accumulators; one CTA of 128 threads handles 128 atoms at a
+// time (M = 128), one thread per atom row for the epilogues.
+//
+// The paper has no learned component; this is the guess of the solver's PCG (any guess is
+// allowed: PCG still converges to the same tolerance, it only changes the iteration count).
+#include "common.cuh"
+#include "tc.cuh"
+
+#include <cmath>
+
+#define MLP_IN 16
+#define MLP_H 128
+#define MLP_OUT 3
+#define MLP_OUTP 16
+// packed parameter block (bytes)
+#define MLP_W1T_OFF 0                      // bf16 W1^T [128][16], core-matrix layout
+#define MLP_W2T_OFF 4096                   // bf16 W2^T [128][128]
+#define MLP_W3T_OFF (4096 + 32768)         // bf16 W3^T [16][128] (rows >= 3 zero)
+#define MLP_B1_OFF (MLP_W3T_OFF + 4096)    // fp32 b1[128]
+#define MLP_B2_OFF (MLP_B1_OFF + 512)      // fp32 b2[128]
+#define MLP_B3_OFF (MLP_B2_OFF + 512)      // fp32 b3[16]
+#define MLP_PACKED_BYTES (MLP_B3_OFF + 64)
+// master parameters (fp32): W1 [16][128], b1, W2 [128][128], b2, W3 [128][3], b3
+#define MLP_P_W1 0
+#define MLP_P_B1 (MLP_P_W1 + MLP_IN * MLP_H)
+#define MLP_P_W2 (MLP_P_B1 + MLP_H)
+#define MLP_P_B2 (MLP_P_W2 + MLP_H * MLP_H)
+#define MLP_P_W3 (MLP_P_B2 + MLP_H)
+#define MLP_P_B3 (MLP_P_W3 + MLP_H * MLP_OUT)
+#define MLP_NPARAM (MLP_P_B3 + MLP_OUT)
+
+#define MLP_E_SCALE 0.05
+#define MLP_OUT_SCALE 0.02
+
+static __device__ int g_mlp_error;   // set when a bounded tensor-core wait gave up
+
+namespace {
+
+__global__ void k_mlp_pack(const float *__restrict__ p, unsigned char *__restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    __nv_bfloat16 *w1 = (__nv_bfloat16 *)(out + MLP_W1T_OFF);
+    __nv_bfloat16 *w2 = (__nv_bfloat16 *)(out + MLP_W2T_OFF);
+    __nv_bfloat16 *w3 = (__nv_bfloat16 *)(out + MLP_W3T_OFF);
+    if (t < MLP_H * MLP_IN) {   // W1t[n][k] = W1[k][n]
+        const int n = t / MLP_IN, k = t % MLP_IN;
+        w1[tc::cm_offset(n, k, MLP_IN) / 2] = __float2bfloat16(p[MLP_P_W1 + k * MLP_H + n]);
+    }
+    if (t < MLP_H * MLP_H) {    // W2t[n][k] = W2[k][n]
+        const int n = t / MLP_H, k = t % MLP_H;
+        w2[tc::cm_offset(n, k, MLP_H) / 2] = __float2bfloat16(p[MLP_P_W2 + k * MLP_H + n]);
+    }
+    if (t < MLP_OUTP * MLP_H) { // W3t[o][h] = W3[h][o], zero rows o >= 3
+        const int o = t / MLP_H, h = t % MLP_H;
+        w3[tc::cm_offset(o, h, MLP_H) / 2] = __float2bfloat16(o < MLP_OUT ? p[MLP_P_W3 + h * MLP_OUT + o] : 0.f);
+    }
+    float *b1 = (float *)(out + MLP_B1_OFF), *b2 = (float *)(out + MLP_B2_OFF), *b3 = (float *)(out + MLP_B3_OFF);
+    if (t < MLP_H) {
+        b1[t] = p[MLP_P_B1 + t];
+        b2[t] = p[MLP_P_B2 + t];
+    }
+    if (t < MLP_OUTP) b3[t] = t < MLP_OUT ? p[MLP_P_B3 + t] : 0.f;
+}
+
+struct __align__(16) FwdSmem {
+    unsigned char w1[4096];
+    unsigned char w2[32768];
+    unsigned char w3[4096];
+    unsigned char a[32768];      // activations: X [128][16] or H [128][128], core-matrix layout
+    float b1[MLP_H], b2[MLP_H], b3[MLP_OUTP];
+    uint64_t mbar;
+    uint32_t taddr;
+};
+
+// bias + ReLU of this thread's TMEM row (128 columns) -> bf16 row of the next A operand
+__device__ __forceinline__ void epilogue_relu(uint32_t trow, const float *bias, unsigned char *a, int row) {
+#pragma unroll 1
+    for (int c = 0; c < MLP_H; c += 32) {
+        float v[32];
+        tc::tmem_ld32(trow + c, v);
+#pragma unroll
+        for (int g = 0; g < 32; g += 8) {
+            __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16(fmaxf(v[g + e] + bias[c + g + e], 0.f));
+            *(uint4 *)(a + tc::cm_offset(row, c + g, MLP_H)) = *(const uint4 *)h;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_mlp_forward(const unsigned char *__restrict__ packed,
+                                                     const float *__restrict__ feat, int n, float *__restrict__ y) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    FwdSmem &S = *reinterpret_cast<FwdSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // weights and biases into shared memory (the packed block mirrors the layout)
+    {
+        const uint4 *src = (const uint4 *)packed;
+        uint4 *dw = (uint4 *)S.w1;
+        for (int k = tid; k < (4096 + 32768 + 4096) / 16; k += 128) dw[k] = src[k];
+        const float *bsrc = (const float *)(packed + MLP_B1_OFF);
+        for (int k = tid; k < MLP_H; k += 128) {
+            S.b1[k] = bsrc[k];
+            S.b2[k] = bsrc[MLP_H + k];
+        }
+        if (tid < MLP_OUTP) S.b3[tid] = bsrc[2 * MLP_H + tid];
+    }
+    if (warp == 0) tc::tmem_alloc(&S.taddr, 128);
+    if (tid == 0) tc::mbar_init(&S.mbar, 1);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = S.taddr;
+    const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+    const uint32_t sa = tc::smem_u32(S.a), sw1 = tc::smem_u32(S.w1), sw2 = tc::smem_u32(S.w2),
+                   sw3 = tc::smem_u32(S.w3);
+    constexpr uint32_t ID1 = tc::idesc_bf16(128, MLP_H, 0, 0);
+    constexpr uint32_t ID3 = tc::idesc_bf16(128, MLP_OUTP, 0, 0);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int ntiles = (n + 127) / 128;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int atom = tile * 128 + tid;
+        // features -> bf16 A operand [128][16]
+        {
+            __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) h[k] = __float2bfloat16(atom < n ? feat[(size_t)atom * 16 + k] : 0.f);
+            *(uint4 *)(S.a + tc::cm_offset(tid, 0, MLP_IN)) = *(const uint4 *)&h[0];
+            *(uint4 *)(S.a + tc::cm_offset(tid, 8, MLP_IN)) = *(const uint4 *)&h[8];
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+            tc::mma_bf16(tbase, tc::smem_desc(sa, 128, 256), tc::smem_desc(sw1, 128, 256), ID1, 0);
+            tc::commit(&S.mbar);
+        }
+        ok = tc::mbar_wait(&S.mbar, phase);
+        phase ^= 1;
+        tc::fence_after();
+        if (ok) epilogue_relu(trow, S.b1, S.a, tid);
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0 && ok) {
+            for (int kk = 0; kk < MLP_H / 16; ++kk)
+                tc::mma_bf16(tbase, tc::smem_desc(sa + kk * 256, 128, 2048), tc::smem_desc(sw2 + kk * 256, 128, 2048),
+                             ID1, kk > 0);
+            tc::commit(&S.mbar);
+        }
+        if (ok) {
+            ok = tc::mbar_wait(&S.mbar, phase);
+            phase ^= 1;
+        }
+        tc::fence_after();
+        if (ok) epilogue_relu(trow, S.b2, S.a, tid);
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0 && ok) {
+            for (int kk = 0; kk < MLP_H / 16; ++kk)
+                tc::mma_bf16(tbase, tc::smem_desc(sa + kk * 256, 128, 2048), tc::smem_desc(sw3 + kk * 256, 128, 2048),
+                             ID3, kk > 0);
+            tc::commit(&S.mbar);
+        }
+        if (ok) {
+            ok = tc::mbar_wait(&S.mbar, phase);
+            phase ^= 1;
+        }
+        tc::fence_after();
+        if (ok) {
+            float v[32];
+            tc::tmem_ld32(trow, v);
+            if (atom < n)
+                for (int o = 0; o < MLP_OUT; ++o) y[(size_t)atom * MLP_OUT + o] = v[o] + S.b3[o];
+        }
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+    }
+    if (!ok && tid == 0) atomicExch(&g_mlp_error, 1);
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 128);
+}
+
+// features in slot order: e = E/E_SCALE in the atom's frame, the same for its z- and x-atoms,
+// |e|, alpha, one-hot frame kind, 1, 0
+__global__ void k_features(const double *__restrict__ E, const double *__restrict__ rot,
+                           const double *__restrict__ alpha, const int *__restrict__ frame_s, int n, int n_pad,
+                           float *__restrict__ feat) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double *R = rot + 9 * s;
+    auto loc = [&](int slot, double *o) {
+        const double e[3] = {E[slot] / MLP_E_SCALE, E[n_pad + slot] / MLP_E_SCALE, E[2 * n_pad + slot] / MLP_E_SCALE};
+        for (int b = 0; b < 3; ++b) o[b] = R[0 * 3 + b] * e[0] + R[1 * 3 + b] * e[1] + R[2 * 3 + b] * e[2];
+    };
+    double f[16];
+    loc(s, f);
+    const int type = frame_s[3 * s];
+    const bool has = type != AP_FRAME_NONE;
+    if (has) {
+        loc(frame_s[3 * s + 1], f + 3);
+        loc(frame_s[3 * s + 2], f + 6);
+    } else {
+        for (int k = 3; k < 9; ++k) f[k] = 0.0;
+    }
+    const double ex = E[s] / MLP_E_SCALE, ey = E[n_pad + s] / MLP_E_SCALE, ez = E[2 * n_pad + s] / MLP_E_SCALE;
+    f[9] = sqrt(ex * ex + ey * ey + ez * ez);
+    f[10] = alpha[s];
+    f[11] = type == AP_FRAME_NONE;
+    f[12] = type == AP_FRAME_Z_THEN_X;
+    f[13] = type == AP_FRAME_BISECTOR;
+    f[14] = 1.0;
+    f[15] = 0.0;
+    for (int k = 0; k < 16; ++k) feat[(size_t)s * 16 + k] = (float)f[k];
+}
+
+// mu0 = alpha E + s_out R y (slot order in, caller order out)
+__global__ void k_guess_assemble(const double *__restrict__ E, const double *__restrict__ rot,
+                                 const double *__restrict__ alpha, const float *__restrict__ y,
+                                 const int *__restrict__ perm, int n, int n_pad, double *__restrict__ mu0) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double *R = rot + 9 * s;
+    const double yy[3] = {y[3 * s], y[3 * s + 1], y[3 * s + 2]};
+    const int i = perm[s];
+    for (int a = 0; a < 3; ++a)
+        mu0[3 * i + a] = alpha[s] * E[a * n_pad + s] +
+                         MLP_OUT_SCALE * (R[3 * a] * yy[0] + R[3 * a + 1] * yy[1] + R[3 * a + 2] * yy[2]);
+}
+
+// caller-order features and targets t = R^T (mu - alpha E) / s_out
+__global__ void k_features_out(const float *__restrict__ fs, const double *__restrict__ E,
+                               const double *__restrict__ rot, const double *__restrict__ alpha,
+                               const int *__restrict__ perm, const double *__restrict__ mu, int n, int n_pad,
+                               float *__restrict__ feat, float *__restrict__ target) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int i = perm[s];
+    for (int k = 0; k < 16; ++k) feat[(size_t)i * 16 + k] = fs[(size_t)s * 16 + k];
+    if (target && mu) {
+        const double *R = rot + 9 * s;
+        double d[3];
+        for (int a = 0; a < 3; ++a) d[a] = mu[3 * i + a] - alpha[s] * E[a * n_pad + s];
+        for (int b = 0; b < 3; ++b)
+            target[3 * i + b] = (float)((R[b] * d[0] + R[3 + b] * d[1] + R[6 + b] * d[2]) / MLP_OUT_SCALE);
+    }
+}
+
+int forward_launch(const void *packed, const float *feat, int n, float *y, cudaStream_t s) {
+    static bool attr = false;
+    const size_t bytes = sizeof(FwdSmem);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return ap_fail(nullptr, AP_ERR_CUDA, std::string("mlp smem: ") + cudaGetErrorString(e));
+        attr = true;
+    }
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ntiles = (n + 127) / 128;
+    const int grid = std::max(1, std::min(ntiles, 2 * sms));
+    k_mlp_forward<<<grid, 128, bytes, s>>>((const unsigned char *)packed, feat, n, y);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ap_fail(nullptr, AP_ERR_CUDA, std::string("mlp forward: ") + cudaGetErrorString(e));
+    return AP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ap_mlp_param_count(void) { return MLP_NPARAM; }
+int ap_mlp_packed_bytes(void) { return MLP_PACKED_BYTES; }
+
+int ap_mlp_pack(const float *d_params, void *d_packed, void *stream) {
+    if (!d_params || !d_packed) return ap_fail(nullptr, AP_ERR_ARG, "null pointer");
+    k_mlp_pack<<<(MLP_H * MLP_H + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_params, (unsigned char *)d_packed);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ap_fail(nullptr, AP_ERR_CUDA, std::string("mlp pack: ") + cudaGetErrorString(e));
+    return AP_OK;
+}
+
+int ap_mlp_forward(const void *d_packed, const float *d_feat, int n, float *d_y, void *stream) {
+    if (!d_packed || !d_feat || !d_y || n <= 0) return ap_fail(nullptr, AP_ERR_ARG, "bad arguments");
+    return forward_launch(d_packed, d_feat, n, d_y, (cudaStream_t)stream);
+}
+
+int ap_mlp_status(void) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_mlp_error, sizeof(int)) != cudaSuccess) return AP_ERR_CUDA;
+    if (v) {
+        int z = 0;
+        cudaMemcpyToSymbol(g_mlp_error, &z, sizeof(int));
+        return AP_ERR_TIMEOUT;
+    }
+    return AP_OK;
+}
+
+int ap_mlp_features(ap_ctx *ctx, const double *d_mu, float *d_feat, float *d_target) {
+    if (!ctx || !d_feat) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
+    if (d_target && !d_mu) return ap_fail(ctx, AP_ERR_ARG, "targets need the dipoles");
+    const int n = ctx->n;
+    k_features<<<ap_grid_for(n, 128), 128, 0, ctx->s0>>>(ctx->E, ctx->rot, ctx->alpha, ctx->frame_s, n, ctx->n_pad,
+                                                        ctx->mlp_feat);
+    k_features_out<<<ap_grid_for(n, 128), 128, 0, ctx->s0>>>(ctx->mlp_feat, ctx->E, ctx->rot, ctx->alpha, ctx->perm,
+                                                            d_mu, n, ctx->n_pad, d_feat, d_target);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+int ap_learned_guess(ap_ctx *ctx, const void *d_packed, double *d_mu0) {
+    if (!ctx || !d_packed || !d_mu0) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
+    const int n = ctx->n;
+    k_features<<<ap_grid_for(n, 128), 128, 0, ctx->s0>>>(ctx->E, ctx->rot, ctx->alpha, ctx->frame_s, n, ctx->n_pad,
+                                                        ctx->mlp_feat);
+    int r = forward_launch(d_packed, ctx->mlp_feat, n, ctx->mlp_y, ctx->s0);
+    if (r) return ap_fail(ctx, r, ap_last_error(nullptr));
+    k_guess_assemble<<<ap_grid_for(n, 128), 128, 0, ctx->s0>>>(ctx->E, ctx->rot, ctx->alpha, ctx->mlp_y, ctx->perm, n,
+                                                              ctx->n_pad, d_mu0);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+}  // extern "C"
