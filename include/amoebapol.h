@@ -179,6 +179,19 @@ int ap_mlp_packed_bytes(void);
 int ap_mlp_pack(const float* d_params, void* d_packed, void* stream);
 /* y = MLP(feat) for n rows: d_feat [n][16] FP32, d_y [n][3] FP32 (device). Async. */
 int ap_mlp_forward(const void* d_packed, const float* d_feat, int n, float* d_y, void* stream);
+/* Gradient of L = (1/2n) sum_i |y_i - t_i|^2 over n rows (d_feat [n][16], d_target [n][3])
+ * at the parameters held in d_packed, ADDED to d_grad (FP32, ap_mlp_param_count(), master
+ * order); the loss is added to *d_loss (double). Forward and backward GEMMs on the tensor
+ * cores. Async. */
+int ap_mlp_gradient(const void* d_packed, const float* d_feat, const float* d_target, int n,
+                    float* d_grad, double* d_loss, void* stream);
+/* One Adam step (Kingma & Ba 2015; beta 0.9 / 0.999, eps 1e-8, bias-corrected with `step`
+ * >= 1): gradient of the batch at d_packed (which must hold d_params packed), update of
+ * d_params with moments d_m, d_v, then d_grad cleared and d_packed re-packed.
+ * d_grad must be zero on entry; *d_loss receives the batch loss added. Async. */
+int ap_mlp_train_step(float* d_params, float* d_grad, float* d_m, float* d_v, int step, float lr,
+                      const float* d_feat, const float* d_target, int n, double* d_loss,
+                      void* d_packed, void* stream);
 /* AP_OK, or AP_ERR_TIMEOUT once if a bounded tensor-core wait of an earlier MLP kernel
  * gave up (then its outputs are invalid). Synchronizes the device. */
 int ap_mlp_status(void);

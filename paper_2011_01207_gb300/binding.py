@@ -23,7 +23,7 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "induced_dipoles_pcg", "polarization_energy_forces", "dipole_field_matvec", "ap_list_stats",
            "ap_stream", "ap_solve_info_last", "ap_time_kernel", "polarization_energy_noalloc",
            "ap_mlp_param_count", "ap_mlp_packed_bytes", "ap_mlp_pack", "ap_mlp_forward", "ap_mlp_status",
-           "ap_mlp_features", "ap_learned_guess")
+           "ap_mlp_features", "ap_learned_guess", "ap_mlp_gradient", "ap_mlp_train_step")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5}
 
@@ -76,6 +76,8 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "ap_mlp_status": (I, []),
         "ap_mlp_features": (I, [P, P, P, P]),
         "ap_learned_guess": (I, [P, P, P]),
+        "ap_mlp_gradient": (I, [P, P, P, I, P, P, P]),
+        "ap_mlp_train_step": (I, [P, P, P, P, I, ctypes.c_float, P, P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -222,6 +224,29 @@ def ap_mlp_forward(packed, feat, y, stream=None):
                                        _ptr(feat, torch.float32, (n, 16), "feat"), int(n),
                                        _ptr(y, torch.float32, (n, 3), "y"), _stream_ptr(feat, stream)),
            "ap_mlp_forward")
+
+
+def ap_mlp_gradient(packed, feat, target, grad, loss, stream=None):
+    import torch
+    n = feat.shape[0]
+    _check(None, load().ap_mlp_gradient(_ptr(packed, torch.uint8, (ap_mlp_packed_bytes(),), "packed"),
+                                        _ptr(feat, torch.float32, (n, 16), "feat"),
+                                        _ptr(target, torch.float32, (n, 3), "target"), int(n),
+                                        _ptr(grad, torch.float32, (ap_mlp_param_count(),), "grad"),
+                                        _ptr(loss, torch.float64, (1,), "loss"), _stream_ptr(feat, stream)),
+           "ap_mlp_gradient")
+
+
+def ap_mlp_train_step(params, grad, m, v, step, lr, feat, target, loss, packed, stream=None):
+    import torch
+    n = feat.shape[0]
+    P = ap_mlp_param_count()
+    _check(None, load().ap_mlp_train_step(
+        _ptr(params, torch.float32, (P,), "params"), _ptr(grad, torch.float32, (P,), "grad"),
+        _ptr(m, torch.float32, (P,), "m"), _ptr(v, torch.float32, (P,), "v"), int(step), float(lr),
+        _ptr(feat, torch.float32, (n, 16), "feat"), _ptr(target, torch.float32, (n, 3), "target"), int(n),
+        _ptr(loss, torch.float64, (1,), "loss"), _ptr(packed, torch.uint8, (ap_mlp_packed_bytes(),), "packed"),
+        _stream_ptr(feat, stream)), "ap_mlp_train_step")
 
 
 def ap_mlp_status():

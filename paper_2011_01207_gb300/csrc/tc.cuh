@@ -4,8 +4,10 @@
 // 8 rows x 16 bytes (8 bf16), stored as 128 contiguous bytes. For a tile of R rows and K
 // columns (K contiguous within a core matrix), core matrix (r/8, k/8) sits at byte offset
 // ((r/8) * (K/8) + k/8) * 128, so neighbours along K are 128 B apart and neighbours along
-// the rows are (K/8) * 128 B apart. The same bytes read as an MN-major operand (rows = K)
-// have neighbours along MN 128 B apart and along K (K/8)*128 B apart.
+// the rows are (K/8) * 128 B apart. The same bytes can be read as an MN-major operand
+// (their rows become the K dimension). Descriptor offsets: K-major no-swizzle takes
+// leading = stride between core matrices along K, stride = along M/N; MN-major no-swizzle
+// takes leading = along K, stride = along M/N.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>

@@ -75,3 +75,53 @@ def test_features_and_guess_match_oracle():
     t_o = omlp.targets(s.xyz, s.box, s.frame, s.alpha, E, want)
     np.testing.assert_allclose(tgt.cpu().numpy(), t_o, rtol=1e-5, atol=1e-5)
     c.close()
+
+
+@pytest.mark.parametrize("n", [128, 777, 5000])
+def test_gradient_matches_oracle(n):
+    """Tensor-core backward (BF16 operands) vs the oracle's FP64 analytic gradients at
+    the BF16-rounded parameters and inputs: relative error per parameter block."""
+    params = omlp.init_params(21)
+    params[1] = np.random.default_rng(4).normal(size=128) * 0.1
+    params[3] = np.random.default_rng(5).normal(size=128) * 0.1
+    rng = np.random.default_rng(n)
+    X = rng.normal(size=(n, 16))
+    T = rng.normal(size=(n, 3))
+    grad = torch.zeros(binding.ap_mlp_param_count(), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    binding.ap_mlp_gradient(_packed(params), torch.tensor(X, dtype=torch.float32, device="cuda"),
+                            torch.tensor(T, dtype=torch.float32, device="cuda"), grad, loss)
+    torch.cuda.synchronize()
+    assert binding.ap_mlp_status() == 0
+    L, G = omlp.loss_and_grads(_bf16_params(params), omlp.bf16_round(X), T)
+    assert abs(float(loss.cpu()[0]) - L) < 1e-2 * L
+    g = omlp.unflatten(grad.cpu().numpy().astype(np.float64))
+    for k, (gg, go) in enumerate(zip(g, G)):
+        err = np.linalg.norm(gg - go) / max(np.linalg.norm(go), 1e-30)
+        assert err < 4e-2, (k, err)
+
+
+def test_training_reduces_loss():
+    """Fit a seeded teacher network's outputs: 300 Adam steps on the GPU kernels."""
+    teacher = omlp.init_params(99)
+    rng = np.random.default_rng(7)
+    X = rng.normal(size=(4096, 16))
+    T, _ = omlp.forward(teacher, X)
+    P = binding.ap_mlp_param_count()
+    params = torch.tensor(omlp.flatten(omlp.init_params(1)), dtype=torch.float32, device="cuda")
+    grad = torch.zeros(P, dtype=torch.float32, device="cuda")
+    m = torch.zeros(P, dtype=torch.float32, device="cuda")
+    v = torch.zeros(P, dtype=torch.float32, device="cuda")
+    packed = torch.zeros(binding.ap_mlp_packed_bytes(), dtype=torch.uint8, device="cuda")
+    binding.ap_mlp_pack(params, packed)
+    feat = torch.tensor(X, dtype=torch.float32, device="cuda")
+    tgt = torch.tensor(T, dtype=torch.float32, device="cuda")
+    losses = []
+    for step in range(1, 301):
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        binding.ap_mlp_train_step(params, grad, m, v, step, 2e-3, feat, tgt, loss, packed)
+        losses.append(loss)
+    torch.cuda.synchronize()
+    assert binding.ap_mlp_status() == 0
+    l0, l1 = float(losses[0].cpu()[0]), float(losses[-1].cpu()[0])
+    assert l1 < 0.1 * l0, (l0, l1)
