@@ -92,5 +92,5 @@ def test_features_rotation_invariant(water_small):
 def test_bf16_round_ties_to_even():
     # 1 + 2^-8 is halfway between bfloat16 neighbours 1 and 1 + 2^-7: ties go to even (1)
     vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -2.5, 3.0e-3])
-    want = np.array([1.0, 1.0, 1.0 + 2 ** -7, -2.5, 0.0029907226562500])
+    want = np.array([1.0, 1.0, 1.0 + 2 ** -7, -2.5, 197 * 2.0 ** -16])   # 3e-3 = 196.6 * 2^-16
     np.testing.assert_array_equal(mlp.bf16_round(vals), want)
