@@ -165,9 +165,11 @@ int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
  * iterations. A per-atom perceptron 16 -> 128 -> 128 -> 3 (ReLU) maps rotation-invariant
  * features to a correction of the direct-field guess:
  *   mu0_i = alpha_i E_i + 0.02 R_i y_i,   R_i the atom's local frame (identity for
- *   global-frame atoms). Features (16, FP32): the permanent field E/0.05 in the atom's
- *   frame (3), the same for its z-atom (3) and x-atom (3), |E|/0.05, alpha, one-hot frame
- *   kind (none, Z-then-X, bisector), 1, 0.
+ *   global-frame atoms). Features (16, FP32), with fields divided by 0.05 e/A^2: the
+ *   permanent field E_i in the atom's frame (3); the short-range first-order induced
+ *   field E1_i = sum_{j: r_ij < 4 A} T_ij (alpha_j E_j) (real-space dipole kernel) in
+ *   the same frame (3); E at the z-atom and at the x-atom in i's frame (3 + 3); |E_i|;
+ *   |E1_i|; alpha_i; frame kind (0 global, 0.5 Z-then-X, 1 bisector).
  * Master parameters are FP32, ap_mlp_param_count() floats in the order W1 [16][128],
  * b1 [128], W2 [128][128], b2 [128], W3 [128][3], b3 [3] (W[in][out]). The kernels use a
  * packed copy (BF16 weights in tensor-core operand layout, FP32 biases) of

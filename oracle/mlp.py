@@ -1,7 +1,8 @@
 """The learned initial-guess network in FP64 (oracle).
 
-Per atom, rotation-invariant features f_i (the permanent field and the fields at its
-frame atoms, expressed in the atom's local frame, plus its polarizability and kind)
+Per atom, rotation-invariant features f_i (the permanent field, the short-range
+first-order induced field and the fields at its frame atoms, all expressed in the atom's
+local frame, plus its polarizability and frame kind)
 pass through a two-hidden-layer perceptron
     h1 = relu(f W1 + b1),  h2 = relu(h1 W2 + b2),  y = h2 W3 + b3,
 and the guess is mu0_i = alpha_i E_i + s_out R_i y_i (R_i the atom's frame). Training
@@ -18,21 +19,34 @@ E_SCALE = 0.05      # typical permanent-field magnitude, e/A^2
 OUT_SCALE = 0.02    # typical correction magnitude, e*A
 
 
-def features(xyz, box, frame, alpha, E):
-    """Feature matrix [N, 16]: e_i (3), e at the z-atom (3) and x-atom (3) in i's frame,
-    |e_i|, alpha_i, one-hot kind (global / z-then-x / bisector), 1, 0; e = E / E_SCALE."""
+SHORT_RANGE = 4.0   # A
+
+
+def short_field(n, I, J, R, alpha, E, beta, thole_a, rs=SHORT_RANGE):
+    """E1_i = sum over pairs closer than rs of the real-space dipole field of alpha_j E_j."""
+    from .realspace import real_dipole_field
+    keep = np.einsum("pa,pa->p", R, R) < rs * rs
+    return real_dipole_field(n, I[keep], J[keep], R[keep], alpha[:, None] * E, alpha, beta, thole_a)
+
+
+def features(xyz, box, frame, alpha, E, E1):
+    """Feature matrix [N, 16], fields divided by E_SCALE: E_i and E1_i in the atom's
+    frame (3 + 3), E at the z-atom and x-atom in i's frame (3 + 3), |E_i|, |E1_i|,
+    alpha_i, frame kind (0 global, 0.5 Z-then-X, 1 bisector)."""
     n = xyz.shape[0]
     rot = frames.frame_matrices(xyz, box, frame)
     e = E / E_SCALE
     loc = np.einsum("nba,nb->na", rot, e)
+    loc1 = np.einsum("nba,nb->na", rot, E1 / E_SCALE)
     fz = np.where(frame[:, 1] >= 0, frame[:, 1], np.arange(n))
     fx = np.where(frame[:, 2] >= 0, frame[:, 2], np.arange(n))
     has = (frame[:, 0] != 0)[:, None]
     ez = np.where(has, np.einsum("nba,nb->na", rot, e[fz]), 0.0)
     ex = np.where(has, np.einsum("nba,nb->na", rot, e[fx]), 0.0)
-    kind = np.eye(3)[frame[:, 0]]
-    return np.concatenate([loc, ez, ex, np.linalg.norm(e, axis=1, keepdims=True), alpha[:, None],
-                           kind, np.ones((n, 1)), np.zeros((n, 1))], axis=1), rot
+    kind = np.array([0.0, 0.5, 1.0])[frame[:, 0]]
+    return np.concatenate([loc, loc1, ez, ex, np.linalg.norm(loc, axis=1, keepdims=True),
+                           np.linalg.norm(loc1, axis=1, keepdims=True), alpha[:, None], kind[:, None]],
+                          axis=1), rot
 
 
 def forward(params, X, round_hidden=None):
@@ -110,9 +124,9 @@ def adam_step(params, grads, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     return out_p, out_m, out_v
 
 
-def guess(params, xyz, box, frame, alpha, E, round_input=None, round_hidden=None):
+def guess(params, xyz, box, frame, alpha, E, E1, round_input=None, round_hidden=None):
     """mu0 = alpha E + OUT_SCALE * R y."""
-    X, rot = features(xyz, box, frame, alpha, E)
+    X, rot = features(xyz, box, frame, alpha, E, E1)
     if round_input is not None:
         X = round_input(X)
     Y, _ = forward(params, X, round_hidden)

@@ -30,7 +30,7 @@ void free_all(ap_ctx *c) {
                     c->E, c->acc, c->rec, c->rot, c->mpl, c->frame_s, c->fvec, c->mu, c->r, c->qv, c->p, c->st,
                     c->grid, c->cgrid, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf,
                     c->tile_off, c->chunk_j, c->chunk_pos, c->chunk_src, c->chunk_mask, c->chunk_flag, c->nchunk,
-                    c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y};
+                    c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y, c->smask, c->smask_t, c->e1s};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -101,6 +101,7 @@ int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
     if ((r = dalloc(ctx, &ctx->red, sizeof(double) * 64))) return r;
     if ((r = dalloc(ctx, &ctx->mlp_feat, sizeof(float) * 16 * np))) return r;
     if ((r = dalloc(ctx, &ctx->mlp_y, sizeof(float) * 3 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->e1s, sizeof(double) * 3 * np))) return r;
     if ((r = pme_init(ctx))) return r;
     AP_CUDA(cudaDeviceSynchronize());
     return AP_OK;

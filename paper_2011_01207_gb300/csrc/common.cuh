@@ -16,6 +16,7 @@
 #define AP_COULOMB 332.063713       // kcal A / (mol e^2)
 #define AP_DEBYE 4.80321            // Debye per e*A
 #define AP_SQRT_PI 1.7724538509055159
+#define AP_SHORT_RANGE 4.0          // A, radius of the learned guess's neighbourhood feature
 
 // 32-byte aligned 4-vector of doubles (the CUDA 13 double4 is deprecated)
 struct __align__(32) dvec4 { double x, y, z, w; };
@@ -80,6 +81,9 @@ struct ap_ctx {
     int *n_work = nullptr;       // device: [0] work items, [1] in-range pairs of the configuration
     unsigned *pmask = nullptr;   // [work][32] in-range pair bits per item (i-lane word, bit = j-lane)
     unsigned *pmask_t = nullptr; // [work][32] the transpose (j-lane word, bit = i-lane)
+    unsigned *smask = nullptr;   // [work][32] pairs closer than AP_SHORT_RANGE (learned-guess feature)
+    unsigned *smask_t = nullptr; // its transpose
+    double *e1s = nullptr;       // [3][n_pad] short-range first-order induced field (feature)
     int cap_chunks = 0;
     int lists_valid = 0;
     // scratch for the build
@@ -147,6 +151,8 @@ struct WorkArgs {
     const unsigned *excl_mask;
     const unsigned *pmask;
     const unsigned *pmask_t;
+    const unsigned *smask;
+    const unsigned *smask_t;
 };
 
 inline WorkArgs work_args(const ap_ctx *ctx) {
@@ -162,6 +168,8 @@ inline WorkArgs work_args(const ap_ctx *ctx) {
     w.excl_mask = ctx->excl_mask;
     w.pmask = ctx->pmask;
     w.pmask_t = ctx->pmask_t;
+    w.smask = ctx->smask;
+    w.smask_t = ctx->smask_t;
     return w;
 }
 
@@ -191,6 +199,7 @@ int filter_launch(ap_ctx *ctx, cudaStream_t s);
 int filter_alloc(ap_ctx *ctx);
 int real_field_launch(ap_ctx *ctx, cudaStream_t s);
 int real_matvec_launch(ap_ctx *ctx, const void *p, cudaStream_t s);
+int short_matvec_launch(ap_ctx *ctx, const void *p, double *out, cudaStream_t s);
 int real_forces_launch(ap_ctx *ctx, cudaStream_t s);
 int pme_init(ap_ctx *ctx);
 int pme_multipole_field(ap_ctx *ctx, cudaStream_t s);              // permanent: grid2 keeps phi_M

@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work,
                                                   const typename V4<T>::type *__restrict__ posq,
                                                   const typename V4<T>::type *__restrict__ chunk_pos, T rc2, T Lx,
                                                   T Ly, T Lz, unsigned *__restrict__ pmask,
-                                                  unsigned *__restrict__ pmask_t, int *__restrict__ pcount) {
+                                                  unsigned *__restrict__ pmask_t, T rs2, unsigned *__restrict__ smask,
+                                                  unsigned *__restrict__ smask_t, int *__restrict__ pcount) {
     typedef typename V4<T>::type T4;
     const int lane = threadIdx.x & 31;
     const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work,
         const T4 a = posq[it.x * 32 + lane];
         const T4 b = it.y < 0 ? posq[it.x * 32 + lane] : chunk_pos[(size_t)it.y * 32 + lane];
         T xj = b.x, yj = b.y, zj = b.z;
-        unsigned m = 0u;
+        unsigned m = 0u, ms = 0u;
         for (int s = 0; s < 32; ++s) {
             const int jl = (lane + s) & 31;
             T dx = a.x - xj, dy = a.y - yj, dz = a.z - zj;
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work,
             const T r2 = dx * dx + dy * dy + dz * dz;
             const bool in = (r2 < rc2) && (it.y >= 0 || jl > lane);
             m |= in ? (1u << jl) : 0u;
+            ms |= (in && r2 < rs2) ? (1u << jl) : 0u;
             const int src = (lane + 1) & 31;
             xj = __shfl_sync(0xffffffffu, xj, src);
             yj = __shfl_sync(0xffffffffu, yj, src);
@@ -174,6 +176,13 @@ __global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work,
             if (lane == c) col = w;
         }
         pmask_t[(size_t)t * 32 + lane] = col;
+        smask[(size_t)t * 32 + lane] = ms;
+        unsigned cols = 0u;
+        for (int c = 0; c < 32; ++c) {
+            const unsigned w = __ballot_sync(0xffffffffu, (ms >> c) & 1u);
+            if (lane == c) cols = w;
+        }
+        smask_t[(size_t)t * 32 + lane] = cols;
         int c = __popc(m);
         for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
         if (lane == 0) atomicAdd(pcount, c);
@@ -196,7 +205,8 @@ int filter_t(ap_ctx *ctx, cudaStream_t s) {
     const T rcm = (T)(P.cutoff * P.cutoff);
     auto km = ctx->minimg ? k_pairmask<T, true> : k_pairmask<T, false>;
     km<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->work, ctx->n_work, (const T4 *)ctx->posq, (const T4 *)ctx->chunk_pos, rcm,
-                                         (T)P.box[0], (T)P.box[1], (T)P.box[2], ctx->pmask, ctx->pmask_t, ctx->n_work + 1);
+                                         (T)P.box[0], (T)P.box[1], (T)P.box[2], ctx->pmask, ctx->pmask_t,
+                                         (T)(AP_SHORT_RANGE * AP_SHORT_RANGE), ctx->smask, ctx->smask_t, ctx->n_work + 1);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -212,7 +222,7 @@ int filter_alloc(ap_ctx *ctx) {
     const long cap = ctx->cap_tiles;
     if (cap <= ctx->cap_chunks) return AP_OK;
     void *ptrs[] = {ctx->chunk_j, ctx->chunk_pos, ctx->chunk_src, ctx->chunk_mask, ctx->chunk_flag, ctx->work,
-                    ctx->pmask, ctx->pmask_t};
+                    ctx->pmask, ctx->pmask_t, ctx->smask, ctx->smask_t};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     const size_t es = ctx->prec == AP_FP64 ? 8 : 4;
@@ -224,6 +234,8 @@ int filter_alloc(ap_ctx *ctx) {
     AP_CUDA(cudaMalloc((void **)&ctx->work, sizeof(int2) * (cap + ctx->n_blocks)));
     AP_CUDA(cudaMalloc((void **)&ctx->pmask, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
     AP_CUDA(cudaMalloc((void **)&ctx->pmask_t, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
+    AP_CUDA(cudaMalloc((void **)&ctx->smask, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
+    AP_CUDA(cudaMalloc((void **)&ctx->smask_t, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
     ctx->cap_chunks = (int)cap;
     return AP_OK;
 }

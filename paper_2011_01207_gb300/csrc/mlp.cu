@@ -190,37 +190,48 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const unsigned char *__rest
     if (warp == 0) tc::tmem_dealloc(tbase, 128);
 }
 
-// features in slot order: e = E/E_SCALE in the atom's frame, the same for its z- and x-atoms,
-// |e|, alpha, one-hot frame kind, 1, 0
-__global__ void k_features(const double *__restrict__ E, const double *__restrict__ rot,
+// features in slot order (e = field / E_SCALE): e_i in the atom's frame (3), the short-range
+// first-order induced field e1_i in the same frame (3), e at the z- and x-atoms in i's frame
+// (3 + 3), |e_i|, |e1_i|, alpha_i, frame kind (0 global, 0.5 Z-then-X, 1 bisector)
+__global__ void k_features(const double *__restrict__ E, const double *__restrict__ E1, const double *__restrict__ rot,
                            const double *__restrict__ alpha, const int *__restrict__ frame_s, int n, int n_pad,
                            float *__restrict__ feat) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const double *R = rot + 9 * s;
-    auto loc = [&](int slot, double *o) {
-        const double e[3] = {E[slot] / MLP_E_SCALE, E[n_pad + slot] / MLP_E_SCALE, E[2 * n_pad + slot] / MLP_E_SCALE};
+    auto loc = [&](const double *F, int slot, double *o) {
+        const double e[3] = {F[slot] / MLP_E_SCALE, F[n_pad + slot] / MLP_E_SCALE, F[2 * n_pad + slot] / MLP_E_SCALE};
         for (int b = 0; b < 3; ++b) o[b] = R[0 * 3 + b] * e[0] + R[1 * 3 + b] * e[1] + R[2 * 3 + b] * e[2];
     };
     double f[16];
-    loc(s, f);
+    loc(E, s, f);
+    loc(E1, s, f + 3);
     const int type = frame_s[3 * s];
-    const bool has = type != AP_FRAME_NONE;
-    if (has) {
-        loc(frame_s[3 * s + 1], f + 3);
-        loc(frame_s[3 * s + 2], f + 6);
+    if (type != AP_FRAME_NONE) {
+        loc(E, frame_s[3 * s + 1], f + 6);
+        loc(E, frame_s[3 * s + 2], f + 9);
     } else {
-        for (int k = 3; k < 9; ++k) f[k] = 0.0;
+        for (int k = 6; k < 12; ++k) f[k] = 0.0;
     }
-    const double ex = E[s] / MLP_E_SCALE, ey = E[n_pad + s] / MLP_E_SCALE, ez = E[2 * n_pad + s] / MLP_E_SCALE;
-    f[9] = sqrt(ex * ex + ey * ey + ez * ez);
-    f[10] = alpha[s];
-    f[11] = type == AP_FRAME_NONE;
-    f[12] = type == AP_FRAME_Z_THEN_X;
-    f[13] = type == AP_FRAME_BISECTOR;
-    f[14] = 1.0;
-    f[15] = 0.0;
+    f[12] = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    f[13] = sqrt(f[3] * f[3] + f[4] * f[4] + f[5] * f[5]);
+    f[14] = alpha[s];
+    f[15] = type == AP_FRAME_BISECTOR ? 1.0 : (type == AP_FRAME_Z_THEN_X ? 0.5 : 0.0);
     for (int k = 0; k < 16; ++k) feat[(size_t)s * 16 + k] = (float)f[k];
+}
+
+// p = alpha E (input of the short-range feature field)
+template <class T>
+__global__ void k_alpha_field(const double *__restrict__ E, const double *__restrict__ alpha, int n_pad,
+                              typename V4<T>::type *__restrict__ p) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    typename V4<T>::type v;
+    v.x = (T)(alpha[s] * E[s]);
+    v.y = (T)(alpha[s] * E[n_pad + s]);
+    v.z = (T)(alpha[s] * E[2 * n_pad + s]);
+    v.w = (T)0;
+    p[s] = v;
 }
 
 // mu0 = alpha E + s_out R y (slot order in, caller order out)
@@ -500,6 +511,22 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ g, float *__re
     g[k] = 0.f;
 }
 
+int features_slots(ap_ctx *ctx) {
+    const int n = ctx->n;
+    cudaStream_t st = ctx->s0;
+    if (ctx->prec == AP_FP64)
+        k_alpha_field<double><<<ap_grid_for(ctx->n_pad, 256), 256, 0, st>>>(ctx->E, ctx->alpha, ctx->n_pad, (dvec4 *)ctx->p);
+    else
+        k_alpha_field<float><<<ap_grid_for(ctx->n_pad, 256), 256, 0, st>>>(ctx->E, ctx->alpha, ctx->n_pad, (float4 *)ctx->p);
+    AP_CUDA(cudaMemsetAsync(ctx->e1s, 0, sizeof(double) * 3 * ctx->n_pad, st));
+    int r = short_matvec_launch(ctx, ctx->p, ctx->e1s, st);
+    if (r) return r;
+    k_features<<<ap_grid_for(n, 128), 128, 0, st>>>(ctx->E, ctx->e1s, ctx->rot, ctx->alpha, ctx->frame_s, n, ctx->n_pad,
+                                                   ctx->mlp_feat);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
 int forward_launch(const void *packed, const float *feat, int n, float *y, cudaStream_t s) {
     static bool attr = false;
     const size_t bytes = sizeof(FwdSmem);
@@ -605,8 +632,8 @@ int ap_mlp_features(ap_ctx *ctx, const double *d_mu, float *d_feat, float *d_tar
     if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
     if (d_target && !d_mu) return ap_fail(ctx, AP_ERR_ARG, "targets need the dipoles");
     const int n = ctx->n;
-    k_features<<<ap_grid_for(n, 128), 128, 0, ctx->s0>>>(ctx->E, ctx->rot, ctx->alpha, ctx->frame_s, n, ctx->n_pad,
-                                                        ctx->mlp_feat);
+    int r = features_slots(ctx);
+    if (r) return r;
     k_features_out<<<ap_grid_for(n, 128), 128, 0, ctx->s0>>>(ctx->mlp_feat, ctx->E, ctx->rot, ctx->alpha, ctx->perm,
                                                             d_mu, n, ctx->n_pad, d_feat, d_target);
     AP_CUDA(cudaGetLastError());
@@ -618,9 +645,9 @@ int ap_learned_guess(ap_ctx *ctx, const void *d_packed, double *d_mu0) {
     ctx->err.clear();
     if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
     const int n = ctx->n;
-    k_features<<<ap_grid_for(n, 128), 128, 0, ctx->s0>>>(ctx->E, ctx->rot, ctx->alpha, ctx->frame_s, n, ctx->n_pad,
-                                                        ctx->mlp_feat);
-    int r = forward_launch(d_packed, ctx->mlp_feat, n, ctx->mlp_y, ctx->s0);
+    int r = features_slots(ctx);
+    if (r) return r;
+    r = forward_launch(d_packed, ctx->mlp_feat, n, ctx->mlp_y, ctx->s0);
     if (r) return ap_fail(ctx, r, ap_last_error(nullptr));
     k_guess_assemble<<<ap_grid_for(n, 128), 128, 0, ctx->s0>>>(ctx->E, ctx->rot, ctx->alpha, ctx->mlp_y, ctx->perm, n,
                                                               ctx->n_pad, d_mu0);

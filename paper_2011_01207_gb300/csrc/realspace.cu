@@ -175,7 +175,7 @@ struct MvSmem {
     unsigned short queue[2048];      // (target << 5) | source-lane, sorted by target
 };
 
-template <class T, bool MINIMG>
+template <class T, bool MINIMG, bool SHORT = false>
 __global__ void __launch_bounds__(128) k_matvec(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
     const typename V4<T>::type *__restrict__ pv, double *__restrict__ acc, int n_pad, PairConsts<T> pc) {
@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(128) k_matvec(
             S.acc[c][32 + lane] = T(0);
         }
         // queue: row sides (target i-lane, source j-lane), then column sides (target 32 + j-lane)
-        unsigned row = wa.pmask[(size_t)t * 32 + lane];
-        unsigned col = wa.pmask_t[(size_t)t * 32 + lane];
+        unsigned row = SHORT ? wa.smask[(size_t)t * 32 + lane] : wa.pmask[(size_t)t * 32 + lane];
+        unsigned col = SHORT ? wa.smask_t[(size_t)t * 32 + lane] : wa.pmask_t[(size_t)t * 32 + lane];
         const int nr = __popc(row), nc = __popc(col);
         int ir = nr, ic = nc;
         for (int off = 1; off < 32; off <<= 1) {
@@ -356,7 +356,25 @@ int matvec_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
     return AP_OK;
 }
 
+template <class T>
+int short_t(ap_ctx *ctx, const void *p, double *out, cudaStream_t s) {
+    typedef typename V4<T>::type T4;
+    PairConsts<T> pc = make_consts<T>(ctx);
+    auto kern = ctx->minimg ? k_matvec<T, true, true> : k_matvec<T, false, true>;
+    static int grids[2] = {0, 0};
+    int &grid = grids[ctx->minimg];
+    if (!grid) grid = resident_grid(ctx, kern, 128);
+    kern<<<grid, 128, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)p, out,
+                              ctx->n_pad, pc);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
 }  // namespace
+
+int short_matvec_launch(ap_ctx *ctx, const void *p, double *out, cudaStream_t s) {
+    return ctx->prec == AP_FP64 ? short_t<double>(ctx, p, out, s) : short_t<float>(ctx, p, out, s);
+}
 
 int real_field_launch(ap_ctx *ctx, cudaStream_t s) {
     return ctx->prec == AP_FP64 ? perm_field_t<double>(ctx, s) : perm_field_t<float>(ctx, s);

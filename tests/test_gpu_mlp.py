@@ -58,13 +58,15 @@ def test_features_and_guess_match_oracle():
     feat = torch.zeros((s.n, 16), dtype=torch.float32, device="cuda")
     binding.ap_mlp_features(c.ctx, feat)
     E = c.field.cpu().numpy()
-    Xo, _ = omlp.features(s.xyz, s.box, s.frame, s.alpha, E)
+    o = Oracle(s, Params(beta=0.5446, grid=(32, 32, 32), cutoff=7.0))
+    E1 = omlp.short_field(s.n, o.I, o.J, o.R, s.alpha, E, 0.5446, 0.39)
+    Xo, _ = omlp.features(s.xyz, s.box, s.frame, s.alpha, E, E1)
     np.testing.assert_allclose(feat.cpu().numpy(), Xo, rtol=2e-6, atol=2e-6)
     params = omlp.init_params(5)
     mu0 = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
     binding.ap_learned_guess(c.ctx, _packed(params), mu0)
     torch.cuda.synchronize()
-    want = omlp.guess(_bf16_params(params), s.xyz, s.box, s.frame, s.alpha, E,
+    want = omlp.guess(_bf16_params(params), s.xyz, s.box, s.frame, s.alpha, E, E1,
                       lambda a: omlp.bf16_round(np.asarray(a, np.float32)), omlp.bf16_round)
     got = mu0.cpu().numpy()
     assert np.abs(got - want).max() < 2e-3 * omlp.OUT_SCALE * 10

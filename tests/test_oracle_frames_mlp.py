@@ -81,11 +81,11 @@ def test_features_rotation_invariant(water_small):
     s = water_small
     rng = np.random.default_rng(1)
     E = rng.normal(size=(s.n, 3))
-    X, _ = mlp.features(s.xyz, s.box, s.frame, s.alpha, E)
+    E1 = rng.normal(size=(s.n, 3))
+    X, _ = mlp.features(s.xyz, s.box, s.frame, s.alpha, E, E1)
     x = s.xyz
-    xr = np.stack([-x[:, 1], x[:, 0], x[:, 2]], 1)
-    Er = np.stack([-E[:, 1], E[:, 0], E[:, 2]], 1)
-    Xr, _ = mlp.features(xr, s.box, s.frame, s.alpha, Er)
+    rot = lambda v: np.stack([-v[:, 1], v[:, 0], v[:, 2]], 1)
+    Xr, _ = mlp.features(rot(x), s.box, s.frame, s.alpha, rot(E), rot(E1))
     np.testing.assert_allclose(Xr, X, atol=1e-12)
 
 
