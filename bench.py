@@ -43,6 +43,22 @@ FLOPS_PER_PAIR_MATVEC = 104
 WORKLOAD = "water_96000_atoms_98.7A_grid100_rc7+2_mixed_pcg1e-5"
 
 
+def captured_traffic():
+    """DRAM bytes per launch of the real-space matvec from the committed ncu capture, if the
+    kernel's sources are unchanged since (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "real_matvec_water96k.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    h = hashlib.sha256()
+    for f in d["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return d["dram_bytes_per_launch"] if h.hexdigest()[:16] == d["source_sha256_16"] else None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -246,7 +262,7 @@ def run_ours(args):
     achieved = flop / (kern["real_matvec"] * 1e-3) / 1e12
     roofline = {"kernel": "real_matvec (a5 tile kernel)", "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
-                "traffic": None, "flop_per_launch": flop, "pairs_in_cutoff": npairs,
+                "traffic": captured_traffic(), "traffic_unit": "bytes per launch (ncu, cold caches)", "flop_per_launch": flop, "pairs_in_cutoff": npairs,
                 "launch_ms": round(kern["real_matvec"], 4),
                 "peak_note": "FP32 FMA peak from 152 SMs x 128 lanes x 2 x 2070 MHz",
                 "spread_dipoles_gbs": round((s.n * 32 + GRID[0] * GRID[1] * GRID[2] * 4) / (kern["spread_dipoles"] * 1e-3) / 1e9, 1),
