@@ -160,6 +160,41 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 #define AP_KERNEL_SPREAD_MULTIPOLES 5   /* a3: spread of the permanent multipoles */
 int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
 
+/* Batched replicas: many independent systems of uneven size advanced by one CUDA-graph
+ * launch (the paper runs independent trajectories as separate jobs; here they share the
+ * GPU). Each replica is an ordinary context created with its own non-default stream and
+ * with lists already built; ap_batch_capture() records one step of every replica
+ * (permanent_field, optional ap_learned_guess, induced_dipoles_pcg, optional
+ * polarization_energy_forces) as parallel branches of a single graph. The graph reads and
+ * writes the device buffers named in `steps` at capture time: refill their contents
+ * (e.g. new positions) and call ap_batch_launch() once per step. Lists are rebuilt
+ * outside the graph (build_neighbour_blocks synchronizes); recapture after a rebuild.
+ * Per-replica iteration counts: ap_solve_info_last() on each context. */
+typedef struct ap_batch ap_batch;
+typedef struct {
+    const double* d_xyz;         /* [n][3] positions buffer of the replica */
+    const double* d_mpole;       /* [n][10] local multipoles */
+    const int*    d_frame;       /* [n][3] frames */
+    const double* d_alpha;       /* [n] polarizabilities */
+    const void*   d_mlp_packed;  /* packed network for the learned guess, or NULL for alpha E */
+    double*       d_mu0;         /* [n][3] scratch for the learned guess (NULL if plain) */
+    double        tol_debye;
+    int           max_iter;
+    double*       d_mu;          /* [n][3] output dipoles */
+    double*       d_energy;      /* [1] output energy, or NULL to skip energy and forces */
+    double*       d_forces;      /* [n][3] output forces, or NULL */
+} ap_batch_step;
+int ap_batch_create(ap_batch** out, ap_ctx* const* ctxs, int n_ctx);
+int ap_batch_capture(ap_batch* b, const ap_batch_step* steps);
+int ap_batch_launch(ap_batch* b, void* stream);
+void ap_batch_destroy(ap_batch* b);
+
+/* Launch-shape autotuner: times the real-space matvec with 1, 1/2 and 1/4 of the
+ * resident grid and the PME spread+gather with 64, 128 and 256 threads per block on the
+ * current configuration, and keeps the fastest for this context. h_choice[2] (optional)
+ * receives the grid divisor and the thread count. Synchronizes. */
+int ap_autotune(ap_ctx* ctx, int reps, int* h_choice);
+
 /* a8 - Learned initial guess. The paper has no learned component; any PCG start is
  * valid (the solve converges to the same tolerance), so a better start only saves
  * iterations. A per-atom perceptron 16 -> 128 -> 128 -> 3 (ReLU) maps rotation-invariant

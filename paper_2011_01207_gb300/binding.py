@@ -23,7 +23,8 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "induced_dipoles_pcg", "polarization_energy_forces", "dipole_field_matvec", "ap_list_stats",
            "ap_stream", "ap_solve_info_last", "ap_time_kernel", "polarization_energy_noalloc",
            "ap_mlp_param_count", "ap_mlp_packed_bytes", "ap_mlp_pack", "ap_mlp_forward", "ap_mlp_status",
-           "ap_mlp_features", "ap_learned_guess", "ap_mlp_gradient", "ap_mlp_train_step")
+           "ap_mlp_features", "ap_learned_guess", "ap_mlp_gradient", "ap_mlp_train_step",
+           "ap_batch_create", "ap_batch_capture", "ap_batch_launch", "ap_batch_destroy", "ap_autotune")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5}
 
@@ -37,6 +38,13 @@ class ApParams(ctypes.Structure):
 class ApSolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("eps_debye", ctypes.c_double),
                 ("eps_initial", ctypes.c_double)]
+
+
+class ApBatchStep(ctypes.Structure):
+    _fields_ = [("d_xyz", ctypes.c_void_p), ("d_mpole", ctypes.c_void_p), ("d_frame", ctypes.c_void_p),
+                ("d_alpha", ctypes.c_void_p), ("d_mlp_packed", ctypes.c_void_p), ("d_mu0", ctypes.c_void_p),
+                ("tol_debye", ctypes.c_double), ("max_iter", ctypes.c_int), ("d_mu", ctypes.c_void_p),
+                ("d_energy", ctypes.c_void_p), ("d_forces", ctypes.c_void_p)]
 
 
 class ApError(RuntimeError):
@@ -78,6 +86,11 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "ap_learned_guess": (I, [P, P, P]),
         "ap_mlp_gradient": (I, [P, P, P, I, P, P, P]),
         "ap_mlp_train_step": (I, [P, P, P, P, I, ctypes.c_float, P, P, I, P, P, P]),
+        "ap_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I]),
+        "ap_batch_capture": (I, [P, ctypes.POINTER(ApBatchStep)]),
+        "ap_batch_launch": (I, [P, P]),
+        "ap_batch_destroy": (None, [P]),
+        "ap_autotune": (I, [P, I, ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -267,6 +280,54 @@ def ap_learned_guess(ctx, packed, mu0):
     n = mu0.shape[0]
     _check(ctx, load().ap_learned_guess(ctx, _ptr(packed, torch.uint8, (ap_mlp_packed_bytes(),), "packed"),
                                         _ptr(mu0, torch.float64, (n, 3), "mu0")), "ap_learned_guess")
+
+
+def ap_autotune(ctx, reps=5):
+    ch = (ctypes.c_int * 2)()
+    _check(ctx, load().ap_autotune(ctx, int(reps), ch), "ap_autotune")
+    return int(ch[0]), int(ch[1])
+
+
+class Batch:
+    """One CUDA graph advancing several replica Contexts (each on its own stream)."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.ctx.value for c in self.contexts])
+        self.ptr = ctypes.c_void_p()
+        _check(None, load().ap_batch_create(ctypes.byref(self.ptr), arr, len(self.contexts)), "ap_batch_create")
+        self._keep = []
+
+    def capture(self, tol=1e-5, max_iter=200, packed=None, forces=True):
+        steps = (ApBatchStep * len(self.contexts))()
+        self._keep = []
+        for k, c in enumerate(self.contexts):
+            st = steps[k]
+            st.d_xyz, st.d_mpole = c.xyz.data_ptr(), c.mpole.data_ptr()
+            st.d_frame, st.d_alpha = c.frame.data_ptr(), c.alpha.data_ptr()
+            if packed is not None:
+                mu0 = c.torch.zeros((c.n, 3), dtype=c.torch.float64, device=c.device)
+                self._keep.append(mu0)
+                st.d_mlp_packed, st.d_mu0 = packed.data_ptr(), mu0.data_ptr()
+            st.tol_debye, st.max_iter = float(tol), int(max_iter)
+            st.d_mu = c.mu.data_ptr()
+            if forces:
+                st.d_energy, st.d_forces = c.energy.data_ptr(), c.forces.data_ptr()
+        _check(None, load().ap_batch_capture(self.ptr, steps), "ap_batch_capture")
+
+    def launch(self, stream):
+        _check(None, load().ap_batch_launch(self.ptr, ctypes.c_void_p(stream.cuda_stream)), "ap_batch_launch")
+
+    def close(self):
+        if self.ptr is not None:
+            load().ap_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- marshalling helpers ---------------------------------------------------------------

@@ -40,6 +40,8 @@ void free_all(ap_ctx *c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->s1) cudaStreamDestroy(c->s1);
+    if (c->s2) cudaStreamDestroy(c->s2);
+    if (c->s3) cudaStreamDestroy(c->s3);
 }
 
 int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
@@ -56,6 +58,8 @@ int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
     int lo = 0, hi = 0;
     AP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     AP_CUDA(cudaStreamCreateWithPriority(&ctx->s1, cudaStreamNonBlocking, hi));   // reciprocal branch first
+    AP_CUDA(cudaStreamCreateWithFlags(&ctx->s2, cudaStreamNonBlocking));
+    AP_CUDA(cudaStreamCreateWithPriority(&ctx->s3, cudaStreamNonBlocking, hi));
     AP_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     AP_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
 

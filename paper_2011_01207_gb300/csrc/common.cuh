@@ -55,6 +55,7 @@ struct ap_ctx {
     int n = 0, n_pad = 0, n_blocks = 0;
     cudaStream_t s0 = nullptr;          // caller's stream
     cudaStream_t s1 = nullptr;          // internal stream (reciprocal branch)
+    cudaStream_t s2 = nullptr, s3 = nullptr;   // capture of the solve loop's body (main, reciprocal)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     int sm_count = 0;
@@ -132,6 +133,9 @@ struct ap_ctx {
     float *mlp_feat = nullptr;   // [n_pad][16] learned-guess features (slot order)
     float *mlp_y = nullptr;      // [n_pad][3] network outputs (slot order)
 
+    // launch shapes chosen by ap_autotune (0 = default)
+    int tune_mv_div = 1;      // matvec grid = resident CTAs / tune_mv_div
+    int tune_pme_threads = 128;
     // graph of the solve loop
     cudaGraphExec_t solve_exec = nullptr;
     int graph_ok = 0;         // 1 when the conditional-while graph is usable

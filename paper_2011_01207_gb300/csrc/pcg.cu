@@ -358,6 +358,39 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
                                           self_coef(ctx), ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->red_part);
     k_init_finish<<<1, NT, 0, s>>>(ctx->st, ctx->red_part, nb, ctx->n, tol, max_iter);
     AP_CUDA(cudaGetLastError());
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    AP_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap == cudaStreamCaptureStatusActive) {
+        // the caller is capturing a larger graph: add the WHILE node to it directly
+        if (info) return ap_fail(ctx, AP_ERR_ARG, "h_info must be NULL while the stream is being captured");
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        AP_CUDA(cudaStreamGetCaptureInfo(s, &cap, nullptr, &g, &deps, nullptr, &ndeps));
+        cudaGraphConditionalHandle h;
+        AP_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+        k_set_cond<<<1, 1, 0, s>>>(h, ctx->st);
+        AP_CUDA(cudaGetLastError());
+        AP_CUDA(cudaStreamGetCaptureInfo(s, &cap, nullptr, &g, &deps, nullptr, &ndeps));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        AP_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+        AP_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        AP_CUDA(cudaStreamBeginCaptureToGraph(ctx->s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        rc = enqueue_iteration<T>(ctx, h, 1, ctx->s2, ctx->s3);
+        cudaGraph_t captured = nullptr;
+        cudaError_t ec = cudaStreamEndCapture(ctx->s2, &captured);
+        if (rc) return rc;
+        if (ec != cudaSuccess) return ap_fail(ctx, AP_ERR_CUDA, std::string("body capture: ") + cudaGetErrorString(ec));
+        unsort3(ctx, ctx->mu, d_mu, s);
+        AP_CUDA(cudaGetLastError());
+        return AP_OK;
+    }
     if (!ctx->graph_tried) {
         if (build_graph<T>(ctx) != AP_OK) {   // no graph: the host-driven loop below
             cudaGetLastError();

@@ -354,7 +354,7 @@ int multipole_field_t(ap_ctx *ctx, cudaStream_t s) {
     AP_CUDA(cudaGetLastError());
     int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid2, s);
     if (r) return r;
-    k_gather_field<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid2,
+    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid2,
                                                               (T *)ctx->rec, ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
@@ -365,12 +365,12 @@ int dipole_field_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
     AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
-    k_spread_dipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)p,
+    k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T4 *)p,
                                                                 (T *)ctx->grid, pc);
     AP_CUDA(cudaGetLastError());
     int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
     if (r) return r;
-    k_gather_field<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid,
+    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid,
                                                               (T *)ctx->rec, ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
@@ -383,7 +383,7 @@ int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
     AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
-    k_spread_dipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)mu4,
+    k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T4 *)mu4,
                                                                 (T *)ctx->grid, pc);
     AP_CUDA(cudaGetLastError());
     int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
@@ -403,7 +403,7 @@ int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
     PmeConsts<T> pc = pme_consts<T>(ctx);
     switch (stage) {
     case 0:
-        k_spread_dipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->p,
+        k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->p,
                                                                     (T *)ctx->grid, pc);
         break;
     case 1:
@@ -411,7 +411,7 @@ int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
                                                                          ctx->ncgrid);
         break;
     case 2:
-        k_gather_field<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid,
+        k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid,
                                                                   (T *)ctx->rec, ctx->n_pad, pc);
         break;
     case 3:

@@ -348,8 +348,9 @@ int matvec_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
     PairConsts<T> pc = make_consts<T>(ctx);
     auto kern = ctx->minimg ? k_matvec<T, true> : k_matvec<T, false>;
     static int grids[2] = {0, 0};
-    int &grid = grids[ctx->minimg];
-    if (!grid) grid = resident_grid(ctx, kern, 128);
+    int &g0 = grids[ctx->minimg];
+    if (!g0) g0 = resident_grid(ctx, kern, 128);
+    const int grid = std::max(ctx->sm_count, g0 / std::max(1, ctx->tune_mv_div));
     kern<<<grid, 128, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)p, ctx->acc,
                               ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
