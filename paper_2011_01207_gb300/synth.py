@@ -162,13 +162,53 @@ def water_box(n_mol: int, box_len: float, seed: int, jitter: float = 0.12,
 
 
 def _random_walk_chain(rng, n, box, radius, bond=1.53, angle_deg=111.0, dmin=2.2):
-    """Self-avoiding walk with fixed bond length and angle, confined to a sphere."""
+    """Self-avoiding walk with fixed bond length and angle, confined to a sphere.
+
+    Non-bonded atoms (|i - j| >= 3) stay at least dmin apart (periodic); earlier atoms
+    are looked up in a cell hash of edge >= dmin."""
     center = box / 2
     ang = np.deg2rad(angle_deg)
+    ncell = np.maximum(1, np.floor(box / dmin).astype(int))
+    csize = box / ncell
+    cells = {}
+    keys = [None] * n
+
+    def key(p):
+        return tuple((np.floor(np.mod(p, box) / csize).astype(int)) % ncell)
+
+    def add(i, p):
+        k = key(p)
+        keys[i] = k
+        cells.setdefault(k, []).append(i)
+
+    def remove_from(i0):
+        for j in range(i0, n):
+            if keys[j] is None:
+                break
+            cells[keys[j]].remove(j)
+            keys[j] = None
+
+    def clear(p, i):
+        k = key(p)
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    kk = ((k[0] + dx) % ncell[0], (k[1] + dy) % ncell[1], (k[2] + dz) % ncell[2])
+                    for j in cells.get(kk, ()):
+                        if j <= i - 3:
+                            d = pts[j] - p
+                            d -= box * np.round(d / box)
+                            if d.dot(d) < dmin * dmin:
+                                return False
+        return True
+
     pts = np.zeros((n, 3))
     pts[0] = center + rng.normal(size=3)
-    d = rng.normal(size=3)
-    pts[1] = pts[0] + bond * d / np.linalg.norm(d)
+    add(0, pts[0])
+    if n > 1:
+        d = rng.normal(size=3)
+        pts[1] = pts[0] + bond * d / np.linalg.norm(d)
+        add(1, pts[1])
     i = 2
     fails = 0
     while i < n:
@@ -179,42 +219,40 @@ def _random_walk_chain(rng, n, box, radius, bond=1.53, angle_deg=111.0, dmin=2.2
             perp = rng.normal(size=3)
             perp -= perp.dot(b1) * b1
             perp /= np.linalg.norm(perp)
-            step = bond * (np.cos(np.pi - ang) * b1 + np.sin(np.pi - ang) * perp)
-            cand = pts[i - 1] + step
+            cand = pts[i - 1] + bond * (np.cos(np.pi - ang) * b1 + np.sin(np.pi - ang) * perp)
             if np.linalg.norm(cand - center) > radius:
                 continue
-            if i >= 3:
-                dd = pts[: i - 2] - cand
-                dd -= box * np.round(dd / box)
-                if np.min(np.einsum("ij,ij->i", dd, dd)) < dmin * dmin:
-                    continue
-            ok = True
-            break
+            if clear(cand, i):
+                ok = True
+                break
         if ok:
             pts[i] = cand
+            add(i, cand)
             i += 1
             fails = 0
         else:
             fails += 1
             i = max(2, i - 1 - min(fails, 20))   # backtrack
+            remove_from(i)
     return pts
 
 
 def solvated_chain(n_chain: int, n_water: int, box_len: float, seed: int,
                    dmin_chain: float = 2.2, dmin_solv: float = 2.2,
-                   dmin_inter: float = 1.6) -> System:
+                   dmin_inter: float = 1.6, globule_density: float = 0.055) -> System:
     """Random-walk chain (globule) with random multipoles, surrounded by rigid waters.
 
     Chain: bonds 1.53 A, angle 111 deg, non-bonded atoms >= dmin_chain apart, inside a
     sphere sized for a loose globule. Charges ~N(0,0.3) made neutral, dipoles ~N(0,0.1)
     per component, quadrupoles sym(N(0,0.1)) with the trace removed, polarizabilities
     drawn from {1.334, 1.073, 0.837, 0.496}; multipoles are in the global frame; 1-2 and
-    1-3 pairs have permanent->induced scale 0. Waters fill lattice sites at least
-    dmin_solv (+ the O-H reach) away from every chain atom.
+    1-3 pairs have permanent->induced scale 0. The walk is confined to a sphere holding
+    the chain at globule_density atoms/A^3. Waters fill lattice sites at least dmin_solv
+    (+ the O-H reach) away from every chain atom.
     """
     rng = np.random.default_rng(seed)
     box = np.full(3, float(box_len))
-    radius = (3.0 * n_chain / (4.0 * np.pi * 0.055)) ** (1.0 / 3.0) + 1.0
+    radius = (3.0 * n_chain / (4.0 * np.pi * globule_density)) ** (1.0 / 3.0) + 1.0
     chain = _random_walk_chain(rng, n_chain, box, radius, dmin=dmin_chain) if n_chain else np.zeros((0, 3))
     qc = rng.normal(0.0, 0.3, n_chain)
     qc -= qc.mean() if n_chain else 0.0
@@ -228,16 +266,20 @@ def solvated_chain(n_chain: int, n_water: int, box_len: float, seed: int,
     exc = [np.stack([np.arange(n_chain - k), np.arange(k, n_chain)], 1) for k in (1, 2) if n_chain > k]
     exclc = np.concatenate(exc).astype(np.int32) if exc else np.zeros((0, 2), np.int32)
 
-    # candidate O sites on a lattice finer than the water spacing, away from the chain
-    spacing = 2.9
-    nl = int(np.floor(box_len / spacing))
-    gg = (np.arange(nl) + 0.5) * (box_len / nl)
-    sites = np.stack(np.meshgrid(gg, gg, gg, indexing="ij"), -1).reshape(-1, 3)
-    if n_chain:
-        from scipy.spatial import cKDTree
-        t = cKDTree(np.mod(chain, box) % box, boxsize=box)
-        near = t.query_ball_point(sites, dmin_solv + R_OH, return_length=True)
-        sites = sites[near == 0]
+    # candidate O sites on a lattice finer than the water spacing, away from the chain;
+    # refined (down to 2.55 A, above the 2.5 A O-O floor) until there are enough of them
+    nl = int(np.floor(box_len / 2.9))
+    while True:
+        gg = (np.arange(nl) + 0.5) * (box_len / nl)
+        sites = np.stack(np.meshgrid(gg, gg, gg, indexing="ij"), -1).reshape(-1, 3)
+        if n_chain:
+            from scipy.spatial import cKDTree
+            t = cKDTree(np.mod(chain, box) % box, boxsize=box)
+            near = t.query_ball_point(sites, dmin_solv + R_OH, return_length=True)
+            sites = sites[near == 0]
+        if len(sites) >= 1.05 * n_water or box_len / (nl + 1) < 2.55:
+            break
+        nl += 1
     if len(sites) < n_water:
         raise RuntimeError(f"only {len(sites)} free water sites for {n_water} waters")
     sites = sites[np.sort(rng.choice(len(sites), n_water, replace=False))]
