@@ -251,11 +251,13 @@ def run_ours(args):
     # dominant kernel: per-launch durations with CUDA events on the launch stream
     it_mean = float(np.mean(iters))
     kern = {k: binding.ap_time_kernel(ctx.ctx, k, 30) for k in
-            ("real_matvec", "spread_dipoles", "gather_field", "convolve", "real_field", "spread_multipoles")}
+            ("real_matvec", "spread_dipoles", "gather_field", "convolve", "real_field", "spread_multipoles",
+             "pair_forces")}
     per_step = {"real_matvec": kern["real_matvec"] * (it_mean + 1),
                 "spread_dipoles": kern["spread_dipoles"] * (it_mean + 1),
                 "gather_field": kern["gather_field"] * (it_mean + 1),
-                "real_field": kern["real_field"], "spread_multipoles": kern["spread_multipoles"]}
+                "real_field": kern["real_field"], "spread_multipoles": kern["spread_multipoles"],
+                "pair_forces": kern["pair_forces"]}
     npairs = pairs_within(traj[-1], s.box, CUTOFF)
     hbm_peak, peak_kind = _peaks()
     flop = npairs * FLOPS_PER_PAIR_MATVEC

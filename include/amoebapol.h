@@ -158,6 +158,8 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 #define AP_KERNEL_CONVOLVE          3   /* a3/a6: k-space product with B(m)C(m) */
 #define AP_KERNEL_GATHER_FIELD      4   /* a3/a6: B-spline gather of the field */
 #define AP_KERNEL_SPREAD_MULTIPOLES 5   /* a3: spread of the permanent multipoles */
+#define AP_KERNEL_PAIR_FORCES       6   /* a9: real-space polarization forces and torque sources,
+                                           at the dipoles of the last energy/force call */
 int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
 
 /* Batched replicas: many independent systems of uneven size advanced by one CUDA-graph

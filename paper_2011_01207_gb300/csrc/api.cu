@@ -14,6 +14,7 @@ int ap_fail(ap_ctx *c, int code, const std::string &msg) {
 
 int dipole_field_apply(ap_ctx *ctx, const double *d_v, double *d_out);
 int pme_stage_launch(ap_ctx *ctx, int stage, cudaStream_t s);
+int pair_forces_launch(ap_ctx *ctx, cudaStream_t s);
 
 namespace {
 
@@ -30,7 +31,8 @@ void free_all(ap_ctx *c) {
                     c->E, c->acc, c->rec, c->rot, c->mpl, c->frame_s, c->fvec, c->mu, c->r, c->qv, c->p, c->st,
                     c->grid, c->cgrid, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf,
                     c->tile_off, c->chunk_j, c->chunk_pos, c->chunk_src, c->chunk_mask, c->chunk_flag, c->nchunk,
-                    c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y, c->smask, c->smask_t, c->e1s};
+                    c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y, c->smask, c->smask_t, c->e1s,
+                    c->dg};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -87,6 +89,7 @@ int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
     if ((r = dalloc(ctx, &ctx->mu, sizeof(double) * 3 * np))) return r;
     if ((r = dalloc(ctx, &ctx->r, sizeof(double) * 3 * np))) return r;
     if ((r = dalloc(ctx, &ctx->qv, sizeof(double) * 3 * np))) return r;
+    if ((r = dalloc(ctx, &ctx->dg, sizeof(double) * np))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->p, 4 * es * np))) return r;
     if ((r = dalloc(ctx, &ctx->st, sizeof(PcgState)))) return r;
     if ((r = dalloc(ctx, &ctx->red_part, sizeof(double) * 3 * ((np + 255) / 256 + 1)))) return r;
@@ -251,6 +254,7 @@ int ap_time_kernel(ap_ctx *ctx, int which, int reps, double *h_ms) {
         case AP_KERNEL_CONVOLVE: rc = pme_stage_launch(ctx, 1, ctx->s0); break;
         case AP_KERNEL_GATHER_FIELD: rc = pme_stage_launch(ctx, 2, ctx->s0); break;
         case AP_KERNEL_SPREAD_MULTIPOLES: rc = pme_stage_launch(ctx, 3, ctx->s0); break;
+        case AP_KERNEL_PAIR_FORCES: rc = pair_forces_launch(ctx, ctx->s0); break;
         default: rc = ap_fail(ctx, AP_ERR_ARG, "unknown kernel id");
         }
         if (rc) { cudaEventDestroy(a); cudaEventDestroy(b); return rc; }
@@ -264,6 +268,11 @@ int ap_time_kernel(ap_ctx *ctx, int which, int reps, double *h_ms) {
     cudaEventDestroy(b);
     // the timed launches accumulated into scratch buffers: clear them for the next call
     AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+    if (which == AP_KERNEL_PAIR_FORCES) {
+        AP_CUDA(cudaMemsetAsync(ctx->frc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+        AP_CUDA(cudaMemsetAsync(ctx->gdip, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+        AP_CUDA(cudaMemsetAsync(ctx->gquad, 0, sizeof(double) * 6 * ctx->n_pad, ctx->s0));
+    }
     *h_ms = total / reps;
     return AP_OK;
 }

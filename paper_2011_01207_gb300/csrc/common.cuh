@@ -44,7 +44,8 @@ struct PcgState {
     int max_iter;
     int done;          // 1 when converged or out of iterations
     int status;        // AP_OK / AP_NOT_CONVERGED
-    unsigned int blocks_done;   // last-block-done counter for the update kernel
+    unsigned int blocks_done;   // last-block-done counter of the q = A p kernel
+    unsigned int blocks_done2;  // last-block-done counter of the update kernel
     int nonfinite;     // set when a reduction produced NaN/Inf
     int guard;         // iterations started by the graph loop (hard bound on the WHILE node)
 };
@@ -109,6 +110,7 @@ struct ap_ctx {
 
     // PCG
     double *mu = nullptr, *r = nullptr, *qv = nullptr;   // [3][n_pad]
+    double *dg = nullptr;     // [n_pad] diagonal of A: 1/alpha - self coefficient (0 for padding)
     void *p = nullptr;        // T4 [n_pad] search direction
     PcgState *st = nullptr;   // device
     double *red_part = nullptr;   // [3 * ceil(n_pad/256)] per-block partial sums of the PCG dots

@@ -20,14 +20,6 @@ int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s
 
 namespace {
 
-template <class T>
-__device__ __forceinline__ T sh(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-
-__device__ __forceinline__ void flush12(double *frc, double *gdip, double *gquad, int n_pad, int s, const float *a) {
-    for (int c = 0; c < 3; ++c) atomicAdd(frc + c * n_pad + s, (double)a[c]);
-    for (int c = 0; c < 3; ++c) atomicAdd(gdip + c * n_pad + s, (double)a[3 + c]);
-    for (int c = 0; c < 6; ++c) atomicAdd(gquad + c * n_pad + s, (double)a[6 + c]);
-}
 __device__ __forceinline__ void flush12(double *frc, double *gdip, double *gquad, int n_pad, int s, const double *a) {
     for (int c = 0; c < 3; ++c) atomicAdd(frc + c * n_pad + s, a[c]);
     for (int c = 0; c < 3; ++c) atomicAdd(gdip + c * n_pad + s, a[3 + c]);
@@ -57,7 +49,30 @@ __device__ __forceinline__ void mu_dot_field_grad(T q, const T *d, const T *Q /*
     for (int a = 0; a < 3; ++a) out[a] = cR * R[a] + cmu * mu[a] + cd * d[a] + cQm * Qm[a] + cQR * QR[a];
 }
 
-// one warp per tile (grid-stride); accumulators per lane: force (3), dU/dd (3), dU/dQ (6)
+// One warp per work item, pair-side queue as in the real-space field kernels: every
+// in-range pair gives the side (target t, source s) for both atoms, and with
+// R = x_t - x_s the same expressions give t's force and t's dU/dd, dU/dQ. Per side the
+// kernel accumulates, without the constant factors,
+//   F_t / f         += mu_t.G(R; M_s) - mu_s.G(R; q_t, -d_t, Q_t) + d(mu_t T mu_s)/dR
+//   dU/dd_t / (-f)  += -R_1 mu_s + R_2 (mu_s.R) R
+//   dU/dQ_t / (-f/3) += R_2 sym(mu_s R) - R_3 (mu_s.R) R R
+// so the pair's force is evaluated once per side (twice per pair) in exchange for lanes
+// that only ever see in-range pairs.
+template <class T>
+struct FoSmem {
+    typename V4<T>::type pos[64];   // x, y, z, Thole factor: [0,32) block I, [32,64) the item's j atoms
+    typename V4<T>::type qd[64];    // charge, dipole
+    typename V4<T>::type qa[64];    // Qxx, Qxy, Qxz, Qyy
+    typename V4<T>::type mu[64];    // induced dipole
+    T qb[2][64];                    // Qyz, Qzz
+    T acc[12][64];                  // per-target sums of the item
+    unsigned ex[32];                // exclusion words: lane i, bit j
+    unsigned short queue[2048];
+};
+
+template <class T>
+constexpr int fo_warps() { return sizeof(T) == 4 ? 4 : 2; }
+
 template <class T, bool MINIMG>
 __global__ void __launch_bounds__(128) k_pair_forces(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq,
@@ -66,116 +81,172 @@ __global__ void __launch_bounds__(128) k_pair_forces(
     double *__restrict__ frc, double *__restrict__ gdip, double *__restrict__ gquad, int n_pad, PairConsts<T> pc,
     double fconst) {
     typedef typename V4<T>::type T4;
+    __shared__ FoSmem<T> smem[fo_warps<T>()];
+    FoSmem<T> &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
     const long nitems = *wa.n_work;
+    const long t0 = nitems * gw / nw, t1 = nitems * (gw + 1) / nw;
     const T4 *cpos = (const T4 *)wa.chunk_pos;
-    const T f = (T)fconst;
-    const T third = T(1.0 / 3.0);
-    for (long t = gw; t < nitems; t += nw) {
+    const double sc[12] = {fconst, fconst, fconst, -fconst, -fconst, -fconst, -fconst / 3, -fconst / 3,
+                           -fconst / 3, -fconst / 3, -fconst / 3, -fconst / 3};
+    int curI = -1;
+    double ai[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ai[k] = 0.0;
+    for (long t = t0; t < t1; ++t) {
         const int2 it = wa.work[t];
+        __syncwarp();
+        if (it.x != curI) {
+            if (curI >= 0 && curI * 32 + lane < pc.n) flush12(frc, gdip, gquad, n_pad, curI * 32 + lane, ai);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) ai[k] = 0.0;
+            curI = it.x;
+            const int si = curI * 32 + lane;
+            const T4 a = posq[si], b = dipd[si], c = quad0[si], d = quad1[si];
+            T4 p, m;
+            p.x = a.x; p.y = a.y; p.z = a.z; p.w = b.w;
+            m.x = a.w; m.y = b.x; m.z = b.y; m.w = b.z;
+            S.pos[lane] = p;
+            S.qd[lane] = m;
+            S.qa[lane] = c;
+            S.mu[lane] = muv[si];
+            S.qb[0][lane] = d.x;
+            S.qb[1][lane] = d.y;
+        }
         const bool diag = it.y < 0;
-        const int si = it.x * 32 + lane;
-        T4 a = posq[si], b = dipd[si], c = quad0[si], d = quad1[si], m = muv[si];
-        const T xi = a.x, yi = a.y, zi = a.z, qi = a.w, ti = b.w;
-        const T ndi[3] = {-b.x, -b.y, -b.z};
-        const T Qi[6] = {c.x, c.y, c.z, c.w, d.x, d.y};
-        const T mi[3] = {m.x, m.y, m.z};
-        int sj;
-        T xj, yj, zj, tj;
-        unsigned mask;
+        int sj = -1;
+        unsigned ex;
         if (diag) {
-            sj = si;
-            xj = xi; yj = yi; zj = zi; tj = ti;
-            const int e = wa.tile_excl[wa.tile_off[it.x]];
-            mask = e >= 0 ? wa.excl_mask[(size_t)e * 32 + lane] : 0u;
+            S.pos[32 + lane] = S.pos[lane];
+            S.qd[32 + lane] = S.qd[lane];
+            S.qa[32 + lane] = S.qa[lane];
+            S.mu[32 + lane] = S.mu[lane];
+            S.qb[0][32 + lane] = S.qb[0][lane];
+            S.qb[1][32 + lane] = S.qb[1][lane];
+            const int e = wa.tile_excl[wa.tile_off[curI]];
+            ex = e >= 0 ? wa.excl_mask[(size_t)e * 32 + lane] : 0u;
         } else {
             const size_t cs = (size_t)it.y * 32 + lane;
             sj = wa.chunk_j[cs];
-            const T4 p = cpos[cs];
-            xj = p.x; yj = p.y; zj = p.z; tj = p.w;
-            mask = wa.chunk_flag[it.y] ? wa.chunk_mask[cs] : 0u;
-        }
-        T qj = 0;
-        T dj[3] = {0, 0, 0}, Qj[6] = {0, 0, 0, 0, 0, 0}, mj[3] = {0, 0, 0};
-        if (sj >= 0) {
-            a = posq[sj]; b = dipd[sj]; c = quad0[sj]; d = quad1[sj]; m = muv[sj];
-            qj = a.w;
-            dj[0] = b.x; dj[1] = b.y; dj[2] = b.z;
-            Qj[0] = c.x; Qj[1] = c.y; Qj[2] = c.z; Qj[3] = c.w; Qj[4] = d.x; Qj[5] = d.y;
-            mj[0] = m.x; mj[1] = m.y; mj[2] = m.z;
-        }
-        T ai[12], aj[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) ai[k] = aj[k] = 0;
-        for (int s = 0; s < 32; ++s) {
-            const int jl = (lane + s) & 31;
-            if (!(diag && s == 0)) {
-                T dx = xi - xj, dy = yi - yj, dz = zi - zj;
-                if (MINIMG) {
-                    dx -= pc.L[0] * ap_rint(dx * pc.iL[0]);
-                    dy -= pc.L[1] * ap_rint(dy * pc.iL[1]);
-                    dz -= pc.L[2] * ap_rint(dz * pc.iL[2]);
-                }
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < pc.rc2) {
-                    const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
-                    T B[4], U[4], oml[4];
-                    screened<T, 4>(pc, r, rinv, rinv2, B, U);
-                    thole_oml<T, 4>(pc.thole_a * r2 * r * ti * tj, oml);
-                    const bool ex = (mask >> jl) & 1u;
-                    T Rd[4], Ru[3];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) Rd[k] = B[k] - (ex ? U[k] : oml[k] * U[k]);
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) Ru[k] = B[k] - oml[k] * U[k];
-                    // dU_ij/dR = -f [ mu_i.G(R; M_j) - mu_j.G(R; q_i, -d_i, Q_i) + d(mu_i T mu_j)/dR ]
-                    T A[3], Bv[3];
-                    mu_dot_field_grad<T>(qj, dj, Qj, mi, dx, dy, dz, Rd[0], Rd[1], Rd[2], Rd[3], A);
-                    mu_dot_field_grad<T>(qi, ndi, Qi, mj, dx, dy, dz, Rd[0], Rd[1], Rd[2], Rd[3], Bv);
-                    const T mij = mi[0] * mj[0] + mi[1] * mj[1] + mi[2] * mj[2];
-                    const T mir = mi[0] * dx + mi[1] * dy + mi[2] * dz;
-                    const T mjr = mj[0] * dx + mj[1] * dy + mj[2] * dz;
-                    const T cR = Ru[1] * mij - Ru[2] * mir * mjr;
-                    const T R[3] = {dx, dy, dz};
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const T g = -f * (A[k] - Bv[k] + cR * R[k] + Ru[1] * (mi[k] * mjr + mj[k] * mir));
-                        ai[k] -= g;                                   // F_i = -dU/dR
-                        ai[3 + k] += -f * (-Rd[0] * mj[k] + Rd[1] * mjr * R[k]);   // dU/dd_i (source i, target j)
-                        if (!diag) {
-                            aj[k] += g;                               // F_j = +dU/dR
-                            aj[3 + k] += -f * (-Rd[0] * mi[k] + Rd[1] * mir * R[k]);
-                        }
-                    }
-                    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        const T RR = R[ia[k]] * R[ib[k]];
-                        const T symj = mj[ia[k]] * R[ib[k]] + R[ia[k]] * mj[ib[k]];
-                        ai[6 + k] += -f * third * (Rd[1] * symj - Rd[2] * mjr * RR);
-                        if (!diag) {
-                            const T symi = mi[ia[k]] * R[ib[k]] + R[ia[k]] * mi[ib[k]];
-                            aj[6 + k] += -f * third * (-Rd[1] * symi + Rd[2] * mir * RR);
-                        }
-                    }
-                }
+            S.pos[32 + lane] = cpos[cs];
+            T4 m, c, d, u;
+            m.x = m.y = m.z = m.w = T(0);
+            c = m;
+            d = m;
+            u = m;
+            if (sj >= 0) {
+                const T4 a = posq[sj], b = dipd[sj];
+                c = quad0[sj];
+                d = quad1[sj];
+                u = muv[sj];
+                m.x = a.w; m.y = b.x; m.z = b.y; m.w = b.z;
             }
-            const int src = (lane + 1) & 31;
-            xj = sh(xj, src); yj = sh(yj, src); zj = sh(zj, src); qj = sh(qj, src); tj = sh(tj, src);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) { dj[k] = sh(dj[k], src); mj[k] = sh(mj[k], src); }
-#pragma unroll
-            for (int k = 0; k < 6; ++k) Qj[k] = sh(Qj[k], src);
-            if (!diag) {
-#pragma unroll
-                for (int k = 0; k < 12; ++k) aj[k] = sh(aj[k], src);
-            }
+            S.qd[32 + lane] = m;
+            S.qa[32 + lane] = c;
+            S.mu[32 + lane] = u;
+            S.qb[0][32 + lane] = d.x;
+            S.qb[1][32 + lane] = d.y;
+            ex = wa.chunk_flag[it.y] ? wa.chunk_mask[cs] : 0u;
         }
-        if (si < pc.n) flush12(frc, gdip, gquad, n_pad, si, ai);
-        if (!diag && sj >= 0) flush12(frc, gdip, gquad, n_pad, sj, aj);
+        S.ex[lane] = ex;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            S.acc[k][lane] = T(0);
+            S.acc[k][32 + lane] = T(0);
+        }
+        const int total = build_side_queue(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
+                                           S.queue);
+        __syncwarp();
+        const int per = (total + 31) >> 5;
+        const int e0 = lane * per, e1 = min(total, e0 + per);
+        int cur = -1;
+        T4 self, sm, sa, smu;
+        T syz = 0, szz = 0;
+        self.x = self.y = self.z = self.w = T(0);
+        sm = sa = smu = self;
+        T f[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) f[k] = T(0);
+        for (int e = e0; e < e1; ++e) {
+            const int q = S.queue[e];
+            const int tg = q >> 5, sl = q & 31;
+            if (tg != cur) {
+                if (cur >= 0) {
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) atomicAdd(&S.acc[k][cur], f[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 12; ++k) f[k] = T(0);
+                cur = tg;
+                self = S.pos[tg];
+                sm = S.qd[tg];
+                sa = S.qa[tg];
+                smu = S.mu[tg];
+                syz = S.qb[0][tg];
+                szz = S.qb[1][tg];
+            }
+            const int src = tg < 32 ? 32 + sl : sl;
+            const bool exb = tg < 32 ? (S.ex[tg] >> sl) & 1u : (S.ex[sl] >> (tg - 32)) & 1u;
+            const T4 o = S.pos[src], om = S.qd[src], oa = S.qa[src], ou = S.mu[src];
+            const T oyz = S.qb[0][src], ozz = S.qb[1][src];
+            T dx = self.x - o.x, dy = self.y - o.y, dz = self.z - o.z;
+            if (MINIMG) {
+                dx -= pc.L[0] * ap_rint(dx * pc.iL[0]);
+                dy -= pc.L[1] * ap_rint(dy * pc.iL[1]);
+                dz -= pc.L[2] * ap_rint(dz * pc.iL[2]);
+            }
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+            T B[4], U[4], oml[4];
+            screened<T, 4>(pc, r, rinv, rinv2, B, U);
+            thole_oml<T, 4>(pc.thole_a * r2 * r * self.w * o.w, oml);
+            T Rd[4], Ru[3];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Rd[k] = B[k] - (exb ? U[k] : oml[k] * U[k]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Ru[k] = B[k] - oml[k] * U[k];
+            const T mt[3] = {smu.x, smu.y, smu.z}, ms[3] = {ou.x, ou.y, ou.z};
+            const T ds[3] = {om.y, om.z, om.w}, ndt[3] = {-sm.y, -sm.z, -sm.w};
+            const T Qs[6] = {oa.x, oa.y, oa.z, oa.w, oyz, ozz};
+            const T Qt[6] = {sa.x, sa.y, sa.z, sa.w, syz, szz};
+            T A[3], Bv[3];
+            mu_dot_field_grad<T>(om.x, ds, Qs, mt, dx, dy, dz, Rd[0], Rd[1], Rd[2], Rd[3], A);
+            mu_dot_field_grad<T>(sm.x, ndt, Qt, ms, dx, dy, dz, Rd[0], Rd[1], Rd[2], Rd[3], Bv);
+            const T mts = mt[0] * ms[0] + mt[1] * ms[1] + mt[2] * ms[2];
+            const T mtr = mt[0] * dx + mt[1] * dy + mt[2] * dz;
+            const T msr = ms[0] * dx + ms[1] * dy + ms[2] * dz;
+            const T cR = Ru[1] * mts - Ru[2] * mtr * msr;
+            const T R[3] = {dx, dy, dz};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                f[k] += A[k] - Bv[k] + cR * R[k] + Ru[1] * (mt[k] * msr + ms[k] * mtr);
+                f[3 + k] += -Rd[0] * ms[k] + Rd[1] * msr * R[k];
+            }
+            const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                f[6 + k] += Rd[1] * (ms[ia[k]] * R[ib[k]] + R[ia[k]] * ms[ib[k]]) - Rd[2] * msr * R[ia[k]] * R[ib[k]];
+        }
+        if (cur >= 0) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) atomicAdd(&S.acc[k][cur], f[k]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ai[k] += sc[k] * (double)S.acc[k][lane];
+        if (diag) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) ai[k] += sc[k] * (double)S.acc[k][32 + lane];
+        } else if (sj >= 0) {
+            double aj[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) aj[k] = sc[k] * (double)S.acc[k][32 + lane];
+            flush12(frc, gdip, gquad, n_pad, sj, aj);
+        }
     }
+    if (curI >= 0 && curI * 32 + lane < pc.n) flush12(frc, gdip, gquad, n_pad, curI * 32 + lane, ai);
 }
 
 // reciprocal-space gradient and source terms per atom
@@ -342,6 +413,36 @@ __global__ void k_energy(const double *__restrict__ mu, const double *__restrict
     }
 }
 
+// the real-space force kernel over the current work items with the dipoles in ctx->p,
+// accumulating into ctx->frc, ctx->gdip and ctx->gquad
+template <class T>
+int pair_forces_t(ap_ctx *ctx, cudaStream_t s) {
+    typedef typename V4<T>::type T4;
+    PairConsts<T> pc;
+    const ap_params &P = ctx->prm;
+    const double b = P.ewald_beta;
+    pc.beta = (T)b;
+    pc.c[0] = 0;
+    for (int k = 1; k <= 4; ++k) pc.c[k] = (T)(std::pow(2.0 * b * b, k) / (b * AP_SQRT_PI));
+    pc.thole_a = (T)P.thole_a;
+    pc.rc2 = (T)(P.cutoff * P.cutoff);
+    for (int dd = 0; dd < 3; ++dd) { pc.L[dd] = (T)P.box[dd]; pc.iL[dd] = (T)(1.0 / P.box[dd]); }
+    pc.n = ctx->n;
+    auto kern = ctx->minimg ? k_pair_forces<T, true> : k_pair_forces<T, false>;
+    static int grids[2] = {0, 0};
+    int &grid = grids[ctx->minimg];
+    if (!grid) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * fo_warps<T>(), 0);
+        grid = std::max(1, per_sm) * ctx->sm_count;
+    }
+    kern<<<grid, 32 * fo_warps<T>(), 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd,
+                                            (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, (const T4 *)ctx->p,
+                                            ctx->frc, ctx->gdip, ctx->gquad, ctx->n_pad, pc, AP_COULOMB);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
 template <class T>
 int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
     typedef typename V4<T>::type T4;
@@ -357,28 +458,10 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
     // energy
     k_energy<<<ap_grid_for(n_pad, 256), 256, 0, s>>>(ctx->mu_s, ctx->E, n_pad, -0.5 * f, ctx->red + 8);
     // real space
-    PairConsts<T> pc;
-    {
-        const ap_params &P = ctx->prm;
-        const double b = P.ewald_beta;
-        pc.beta = (T)b;
-        pc.c[0] = 0;
-        for (int k = 1; k <= 4; ++k) pc.c[k] = (T)(std::pow(2.0 * b * b, k) / (b * AP_SQRT_PI));
-        pc.thole_a = (T)P.thole_a;
-        pc.rc2 = (T)(P.cutoff * P.cutoff);
-        for (int dd = 0; dd < 3; ++dd) { pc.L[dd] = (T)P.box[dd]; pc.iL[dd] = (T)(1.0 / P.box[dd]); }
-        pc.n = n;
-    }
-    auto kern = ctx->minimg ? k_pair_forces<T, true> : k_pair_forces<T, false>;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
-    int grid = std::max(1, per_sm) * ctx->sm_count;
-    kern<<<grid, 128, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
-                              (const T4 *)ctx->quad1, (const T4 *)ctx->p, ctx->frc, ctx->gdip, ctx->gquad, n_pad,
-                              pc, f);
-    AP_CUDA(cudaGetLastError());
+    int rc = pair_forces_t<T>(ctx, s);
+    if (rc) return rc;
     // reciprocal space
-    int rc = pme_forces_derivs(ctx, ctx->p, ctx->gbuf, s);
+    rc = pme_forces_derivs(ctx, ctx->p, ctx->gbuf, s);
     if (rc) return rc;
     k_recip_forces<T><<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gbuf, ctx->mu_s, (const T4 *)ctx->posq,
                                                          (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
@@ -394,6 +477,10 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
 }
 
 }  // namespace
+
+int pair_forces_launch(ap_ctx *ctx, cudaStream_t s) {
+    return ctx->prec == AP_FP64 ? pair_forces_t<double>(ctx, s) : pair_forces_t<float>(ctx, s);
+}
 
 int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
     return ctx->prec == AP_FP64 ? forces_t<double>(ctx, d_mu, d_energy, d_forces)

@@ -67,3 +67,33 @@ __device__ __forceinline__ void thole_oml(T s, T *oml) {
     if (NMAX > 2) oml[2] = (T(1) + s + T(0.6) * s * s) * e;
     if (NMAX > 3) oml[3] = (T(1) + s + s * s * (T(18.0 / 35.0) + T(9.0 / 35.0) * s)) * e;
 }
+
+// Pair-side queue of one 32 x 32 work item (one warp). `row` is lane i's word of in-range
+// bits over the item's j atoms, `col` lane j's word over the i atoms (the transpose). Each
+// in-range pair gives two sides, written as (target << 5) | source-lane and sorted by target:
+// the row sides (target i, source j) first, then the column sides (target 32 + j, source i).
+// Returns the number of entries (at most 2048); every lane gets the same value.
+__device__ __forceinline__ int build_side_queue(unsigned row, unsigned col, int lane, unsigned short *queue) {
+    const int nr = __popc(row), nc = __popc(col);
+    int ir = nr, ic = nc;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int vr = __shfl_up_sync(0xffffffffu, ir, off);
+        const int vc = __shfl_up_sync(0xffffffffu, ic, off);
+        if (lane >= off) { ir += vr; ic += vc; }
+    }
+    const int prow = __shfl_sync(0xffffffffu, ir, 31);
+    const int total = prow + __shfl_sync(0xffffffffu, ic, 31);
+    int pos = ir - nr;
+    while (row) {
+        const int b = __ffs(row) - 1;
+        row &= row - 1u;
+        queue[pos++] = (unsigned short)((lane << 5) | b);
+    }
+    pos = prow + ic - nc;
+    while (col) {
+        const int b = __ffs(col) - 1;
+        col &= col - 1u;
+        queue[pos++] = (unsigned short)(((32 + lane) << 5) | b);
+    }
+    return total;
+}

@@ -48,12 +48,16 @@ __device__ __forceinline__ void block_sum2(double &a, double &b) {
 constexpr int NT = 256;
 
 // mu_0 and the matvec input p := mu_0 (caller-order guess gathered into slots)
+// also the diagonal of A, 1/alpha - self coefficient, so the iterations need no division
 template <class T>
 __global__ void k_init_guess(const double *__restrict__ guess, const double *__restrict__ E,
                              const double *__restrict__ alpha, const int *__restrict__ perm, int n, int n_pad,
-                             double *__restrict__ mu, typename V4<T>::type *__restrict__ p) {
+                             double *__restrict__ mu, typename V4<T>::type *__restrict__ p, double self_coef,
+                             double *__restrict__ dg) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_pad) return;
+    const double al = alpha[s];
+    dg[s] = al > 0.0 ? 1.0 / al - self_coef : 0.0;
     double m[3] = {0.0, 0.0, 0.0};
     if (s < n) {
         if (guess) {
@@ -73,15 +77,16 @@ __global__ void k_init_guess(const double *__restrict__ guess, const double *__r
 template <class T>
 __global__ void k_init_residual(const double *__restrict__ E, const double *__restrict__ alpha,
                                 const double *__restrict__ mu, double *__restrict__ acc,
-                                const T *__restrict__ rec, double self_coef, int n_pad, double *__restrict__ r,
-                                typename V4<T>::type *__restrict__ p, double *__restrict__ part) {
+                                const T *__restrict__ rec, const double *__restrict__ dg, int n_pad,
+                                double *__restrict__ r, typename V4<T>::type *__restrict__ p,
+                                double *__restrict__ part) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double rz = 0.0, zz = 0.0;
     if (s < n_pad) {
-        const double a = alpha[s];
+        const double a = alpha[s], d = dg[s];
         for (int c = 0; c < 3; ++c) {
             const int k = c * n_pad + s;
-            double Amu = a > 0.0 ? mu[k] / a - acc[k] - (double)rec[k] - self_coef * mu[k] : 0.0;
+            double Amu = a > 0.0 ? mu[k] * d - acc[k] - (double)rec[k] : 0.0;
             double rr = a > 0.0 ? E[k] - Amu : 0.0;
             r[k] = rr;
             acc[k] = 0.0;
@@ -104,8 +109,8 @@ __device__ __forceinline__ void sum_partials2(const double *part, int nparts, do
     a = 0.0;
     b = 0.0;
     for (int k = threadIdx.x; k < nparts; k += NT) {
-        a += part[k];
-        b += part[nparts + k];
+        a += __ldcg(part + k);
+        b += __ldcg(part + nparts + k);
     }
     block_sum2<NT>(a, b);
 }
@@ -136,14 +141,12 @@ __global__ void k_set_cond(cudaGraphConditionalHandle h, const PcgState *st) {
     cudaGraphSetConditional(h, (st->done || st->max_iter < 1) ? 0u : 1u);
 }
 
-// closes an iteration (one block): sums the update's partials in a fixed order, sets the
-// convergence measure, beta and the stop decision; inside the graph it also drives the
-// WHILE node - never beyond max_iter iterations, so the loop cannot spin forever
-__global__ void k_finish_iter(PcgState *st, const double *__restrict__ part, int nparts, int n,
-                              cudaGraphConditionalHandle h, int use_cond) {
-    double rzn, zzt;
-    sum_partials2(part, nparts, rzn, zzt);
-    if (threadIdx.x != 0) return;
+// closes an iteration (thread 0 of the update kernel's last block, after the partials are
+// summed in a fixed order): sets the convergence measure, beta and the stop decision; inside
+// the graph it also drives the WHILE node - never beyond max_iter iterations, so the loop
+// cannot spin forever
+__device__ void finish_iteration(PcgState *st, double rzn, double zzt, int n, cudaGraphConditionalHandle h,
+                                 int use_cond) {
     const double eps = AP_DEBYE * sqrt(zzt / n);
     st->iter += 1;
     st->guard += 1;
@@ -165,6 +168,21 @@ __global__ void k_finish_iter(PcgState *st, const double *__restrict__ part, int
     }
 }
 
+// true in exactly one block per launch, the last to finish, once every block's partial sums
+// are globally visible; the counter is reset for the next launch
+__device__ __forceinline__ bool last_block(unsigned int *counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int ticket = atomicAdd(counter, 1u);
+        last = ticket == gridDim.x - 1;
+        if (last) *counter = 0u;
+    }
+    __syncthreads();
+    return last;
+}
+
 // p = alpha r + beta p
 template <class T>
 __global__ void k_direction(const double *__restrict__ r, const double *__restrict__ alpha, int n_pad,
@@ -179,20 +197,21 @@ __global__ void k_direction(const double *__restrict__ r, const double *__restri
     p[s] = v;
 }
 
-// q = A p = p/alpha - T_real p - T_rec p - self p; partial p.q; clears acc
+// q = A p = (1/alpha - self) p - T_real p - T_rec p; partial p.q; clears acc. The last
+// block sums the partials and sets gamma = (r.z) / (p.q).
 template <class T>
-__global__ void k_apply(const typename V4<T>::type *__restrict__ p, const double *__restrict__ alpha,
-                        double *__restrict__ acc, const T *__restrict__ rec, double self_coef, int n_pad,
-                        double *__restrict__ q, double *__restrict__ part) {
+__global__ void k_apply(const typename V4<T>::type *__restrict__ p, const double *__restrict__ dg,
+                        double *__restrict__ acc, const T *__restrict__ rec, int n_pad, double *__restrict__ q,
+                        double *__restrict__ part, PcgState *st) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double pq = 0.0, dummy = 0.0;
     if (s < n_pad) {
-        const double a = alpha[s];
+        const double d = dg[s];
         typename V4<T>::type v = p[s];
         const double pv[3] = {(double)v.x, (double)v.y, (double)v.z};
         for (int c = 0; c < 3; ++c) {
             const int k = c * n_pad + s;
-            double qq = a > 0.0 ? pv[c] / a - acc[k] - (double)rec[k] - self_coef * pv[c] : 0.0;
+            const double qq = pv[c] * d - acc[k] - (double)rec[k];
             q[k] = qq;
             acc[k] = 0.0;
             pq += pv[c] * qq;
@@ -200,29 +219,24 @@ __global__ void k_apply(const typename V4<T>::type *__restrict__ p, const double
     }
     block_sum2<NT>(pq, dummy);
     if (threadIdx.x == 0) part[blockIdx.x] = pq;
+    if (!last_block(&st->blocks_done)) return;
+    double tot = 0.0, dummy2 = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += NT) tot += __ldcg(part + k);
+    block_sum2<NT>(tot, dummy2);
+    if (threadIdx.x == 0) {
+        st->pq = tot;
+        st->gamma = st->rz / tot;
+    }
 }
 
-// mu += gamma p; r -= gamma q; partial r.z and z.z per block (gamma from the p.q partials)
+// mu += gamma p; r -= gamma q; partial r.z and z.z per block; the last block sums them and
+// closes the iteration
 template <class T>
 __global__ void k_update(const typename V4<T>::type *__restrict__ p, const double *__restrict__ q,
                          const double *__restrict__ alpha, int n_pad, double *__restrict__ mu,
-                         double *__restrict__ r, PcgState *st, const double *__restrict__ part_pq,
-                         double *__restrict__ part) {
-    __shared__ double s_gamma;
-    double pq, dummy;
-    {
-        double a = 0.0;
-        for (int k = threadIdx.x; k < gridDim.x; k += NT) a += part_pq[k];
-        pq = a;
-        dummy = 0.0;
-        block_sum2<NT>(pq, dummy);
-        if (threadIdx.x == 0) {
-            s_gamma = st->rz / pq;
-            if (blockIdx.x == 0) st->gamma = s_gamma;
-        }
-        __syncthreads();
-    }
-    const double gamma = s_gamma;
+                         double *__restrict__ r, PcgState *st, double *__restrict__ part, int n,
+                         cudaGraphConditionalHandle h, int use_cond) {
+    const double gamma = st->gamma;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double rz = 0.0, zz = 0.0;
     if (s < n_pad) {
@@ -234,8 +248,9 @@ __global__ void k_update(const typename V4<T>::type *__restrict__ p, const doubl
             mu[k] += gamma * pv[c];
             const double rr = r[k] - gamma * q[k];
             r[k] = rr;
-            rz += rr * a * rr;
-            zz += a * rr * a * rr;
+            const double z = a * rr;
+            rz += rr * z;
+            zz += z * z;
         }
     }
     block_sum2<NT>(rz, zz);
@@ -243,6 +258,10 @@ __global__ void k_update(const typename V4<T>::type *__restrict__ p, const doubl
         part[blockIdx.x] = rz;
         part[gridDim.x + blockIdx.x] = zz;
     }
+    if (!last_block(&st->blocks_done2)) return;
+    double rzn, zzt;
+    sum_partials2(part, gridDim.x, rzn, zzt);
+    if (threadIdx.x == 0) finish_iteration(st, rzn, zzt, n, h, use_cond);
 }
 
 // T p: reciprocal branch on `aux`, real space on `main`, joined back into `main`
@@ -274,11 +293,10 @@ int enqueue_iteration(ap_ctx *ctx, cudaGraphConditionalHandle h, int use_cond, c
     int rc = matvec_into<T>(ctx, ctx->p, main, aux);
     if (rc) return rc;
     double *part_pq = ctx->red_part, *part_rz = ctx->red_part + nb;
-    k_apply<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->alpha, ctx->acc, (const T *)ctx->rec,
-                                     self_coef(ctx), ctx->n_pad, ctx->qv, part_pq);
+    k_apply<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->dg, ctx->acc, (const T *)ctx->rec, ctx->n_pad, ctx->qv,
+                                     part_pq, ctx->st);
     k_update<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
-                                      part_pq, part_rz);
-    k_finish_iter<<<1, NT, 0, main>>>(ctx->st, part_rz, nb, ctx->n, h, use_cond);
+                                      part_rz, ctx->n, h, use_cond);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -350,12 +368,12 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
     AP_CUDA(cudaMemsetAsync(ctx->st, 0, sizeof(PcgState), s));
     AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, s));
     k_init_guess<T><<<nb, NT, 0, s>>>(d_guess, ctx->E, ctx->alpha, ctx->perm, ctx->n, ctx->n_pad, ctx->mu,
-                                       (T4 *)ctx->p);
+                                       (T4 *)ctx->p, self_coef(ctx), ctx->dg);
     AP_CUDA(cudaGetLastError());
     int rc = matvec_into<T>(ctx, ctx->p);
     if (rc) return rc;
-    k_init_residual<T><<<nb, NT, 0, s>>>(ctx->E, ctx->alpha, ctx->mu, ctx->acc, (const T *)ctx->rec,
-                                          self_coef(ctx), ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->red_part);
+    k_init_residual<T><<<nb, NT, 0, s>>>(ctx->E, ctx->alpha, ctx->mu, ctx->acc, (const T *)ctx->rec, ctx->dg,
+                                          ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->red_part);
     k_init_finish<<<1, NT, 0, s>>>(ctx->st, ctx->red_part, nb, ctx->n, tol, max_iter);
     AP_CUDA(cudaGetLastError());
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

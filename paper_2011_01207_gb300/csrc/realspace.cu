@@ -1,14 +1,16 @@
-// a2 / a5 - Real-space pair kernels over 32 x 32 atom tiles (paper Sec. 2.3, Fig. groups_inte:
-// a group of B_size atoms against another, B_size^2 interactions with the j data read
-// from neighbouring lanes by warp intrinsics instead of global memory).
+// a2 / a5 - Real-space pair kernels over 32-atom groups (paper Sec. 2.3: a group of B_size
+// atoms against another, B_size^2 interactions, with the paper's group-to-atom list
+// filtering).
 //
-// One warp owns a contiguous run of tiles (block pairs I <= J, sorted by I). Lane l holds
-// atom l of block I in registers; the 32 atoms of block J start one per lane and rotate
-// one lane per step (__shfl_sync), so after 32 steps every (i, j) pair has met once and
-// the j-side partial sums are back in their own lanes. Diagonal tiles (I == J) visit each
-// ordered pair and add only to i. Pair arithmetic is in T (FP32 in the mixed mode); a
-// tile row's 32 terms are summed in T, then added in FP64 - across a warp's tiles of the
-// same I in registers, and into the global FP64 accumulators with atomics.
+// A work item is block I against one filtered 32-atom chunk of its partner blocks (or
+// against itself). The in-range pairs of every item are known as 32-bit masks (row and
+// transposed) from the per-configuration filter. A warp stages the item's 64 atoms in
+// shared memory and turns the masks into a queue of pair sides (target, source) sorted by
+// target; each lane then takes an equal contiguous slice, so no lane evaluates an
+// out-of-range pair and the work per lane is even whatever the pair distribution. Pair
+// arithmetic is in T (FP32 in the mixed mode); sums per target are kept in T within an
+// item (registers, then a shared per-target slot), and in FP64 across items: block I's in
+// registers while consecutive items share I, the chunk atoms' with FP64 atomics.
 #include "common.cuh"
 #include "pair_math.cuh"
 
@@ -40,22 +42,39 @@ __device__ __forceinline__ void flush3(double *acc, int n_pad, int slot, double 
     atomicAdd(acc + 2 * n_pad + slot, c);
 }
 
-template <class T>
-__device__ __forceinline__ T shfl1(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-
 // Work items come from the per-configuration filter: (I, -1) is block I against itself,
 // (I, c) is block I against filtered chunk c (32 atoms of partner blocks, positions already
 // in the periodic image next to I, padding = NaN phantoms). Items are sorted by I, so a
 // warp keeps block I's i-side sums in FP64 registers across consecutive items.
 
 // ---------------------------------------------------------------------------------------
-// a2: permanent multipole field, E_i += E(R; q_j, d_j, Q_j) and E_j += E(-R; q_i, d_i, Q_i)
+// a2: permanent multipole field, E_i += E(R; q_j, d_j, Q_j) and E_j += E(-R; q_i, d_i, Q_i).
+// Same pair-side queue as the matvec below: every in-range pair gives the side "field at
+// the target from the source's multipole" for both atoms, and with R = x_target - x_source
+// one expression serves both sides. The exclusion bit of the pair (sigma = 0 in R_n) is
+// looked up in the item's 32-word mask.
+template <class T>
+struct PfSmem {
+    typename V4<T>::type pos[64];   // x, y, z, Thole factor: [0,32) block I, [32,64) the item's j atoms
+    typename V4<T>::type qd[64];    // charge, dipole
+    typename V4<T>::type qa[64];    // Qxx, Qxy, Qxz, Qyy
+    T qb[2][64];                    // Qyz, Qzz
+    T acc[3][64];                   // per-target sums of the item
+    unsigned ex[32];                // exclusion words: lane i, bit j
+    unsigned short queue[2048];
+};
+
+template <class T>
+__host__ __device__ constexpr int pf_warps() { return sizeof(T) == 4 ? 4 : 2; }
+
 template <class T, bool MINIMG>
-__global__ void __launch_bounds__(256) k_perm_field(
+__global__ void __launch_bounds__(128) k_perm_field(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
     const typename V4<T>::type *__restrict__ quad0, const typename V4<T>::type *__restrict__ quad1,
     double *__restrict__ acc, int n_pad, PairConsts<T> pc) {
     typedef typename V4<T>::type T4;
+    __shared__ PfSmem<T> smem[pf_warps<T>()];
+    PfSmem<T> &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
@@ -64,94 +83,126 @@ __global__ void __launch_bounds__(256) k_perm_field(
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
     double ax = 0, ay = 0, az = 0;
-    T xi = 0, yi = 0, zi = 0, qi = 0, dix = 0, diy = 0, diz = 0, ti = 0;
-    T qxx = 0, qxy = 0, qxz = 0, qyy = 0, qyz = 0, qzz = 0;
     for (long t = t0; t < t1; ++t) {
         const int2 it = wa.work[t];
+        __syncwarp();
         if (it.x != curI) {
             if (curI >= 0 && curI * 32 + lane < pc.n) flush3(acc, n_pad, curI * 32 + lane, ax, ay, az);
             ax = ay = az = 0;
             curI = it.x;
             const int si = curI * 32 + lane;
-            T4 a = posq[si], b = dipd[si], c = quad0[si], d = quad1[si];
-            xi = a.x; yi = a.y; zi = a.z; qi = a.w;
-            dix = b.x; diy = b.y; diz = b.z; ti = b.w;
-            qxx = c.x; qxy = c.y; qxz = c.z; qyy = c.w; qyz = d.x; qzz = d.y;
+            const T4 a = posq[si], b = dipd[si], c = quad0[si], d = quad1[si];
+            T4 p, m;
+            p.x = a.x; p.y = a.y; p.z = a.z; p.w = b.w;
+            m.x = a.w; m.y = b.x; m.z = b.y; m.w = b.z;
+            S.pos[lane] = p;
+            S.qd[lane] = m;
+            S.qa[lane] = c;
+            S.qb[0][lane] = d.x;
+            S.qb[1][lane] = d.y;
         }
         const bool diag = it.y < 0;
-        int sj;
-        T xj, yj, zj, tj;
-        unsigned mask;
+        int sj = -1;
+        unsigned ex;
         if (diag) {
-            sj = curI * 32 + lane;
-            const T4 a = posq[sj];
-            xj = a.x; yj = a.y; zj = a.z; tj = ti;
+            S.pos[32 + lane] = S.pos[lane];
+            S.qd[32 + lane] = S.qd[lane];
+            S.qa[32 + lane] = S.qa[lane];
+            S.qb[0][32 + lane] = S.qb[0][lane];
+            S.qb[1][32 + lane] = S.qb[1][lane];
             const int e = wa.tile_excl[wa.tile_off[curI]];
-            mask = e >= 0 ? wa.excl_mask[(size_t)e * 32 + lane] : 0u;
+            ex = e >= 0 ? wa.excl_mask[(size_t)e * 32 + lane] : 0u;
         } else {
             const size_t cs = (size_t)it.y * 32 + lane;
             sj = wa.chunk_j[cs];
-            const T4 a = cpos[cs];
-            xj = a.x; yj = a.y; zj = a.z; tj = a.w;
-            mask = wa.chunk_flag[it.y] ? wa.chunk_mask[cs] : 0u;
-        }
-        T qj = 0, djx = 0, djy = 0, djz = 0, pxx = 0, pxy = 0, pxz = 0, pyy = 0, pyz = 0, pzz = 0;
-        if (sj >= 0) {
-            const T4 a = posq[sj], b = dipd[sj], c = quad0[sj], d = quad1[sj];
-            qj = a.w; djx = b.x; djy = b.y; djz = b.z;
-            pxx = c.x; pxy = c.y; pxz = c.z; pyy = c.w; pyz = d.x; pzz = d.y;
-        }
-        T fx = 0, fy = 0, fz = 0, gx = 0, gy = 0, gz = 0;
-#pragma unroll 2
-        for (int s = 0; s < 32; ++s) {
-            const int jl = (lane + s) & 31;
-            if (!(diag && s == 0)) {
-                T dx, dy, dz;
-                pair_vector<T, MINIMG>(pc, xi, yi, zi, xj, yj, zj, T(0), T(0), T(0), dx, dy, dz);
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < pc.rc2) {
-                    const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
-                    T B[3], U[3], oml[3];
-                    screened<T, 3>(pc, r, rinv, rinv2, B, U);
-                    thole_oml<T, 3>(pc.thole_a * r2 * r * ti * tj, oml);
-                    const bool ex = (mask >> jl) & 1u;
-                    const T R1 = B[0] - (ex ? U[0] : oml[0] * U[0]);
-                    const T R2 = B[1] - (ex ? U[1] : oml[1] * U[1]);
-                    const T R3 = B[2] - (ex ? U[2] : oml[2] * U[2]);
-                    // field at i from site j
-                    T dR = djx * dx + djy * dy + djz * dz;
-                    T Qx = pxx * dx + pxy * dy + pxz * dz;
-                    T Qy = pxy * dx + pyy * dy + pyz * dz;
-                    T Qz = pxz * dx + pyz * dy + pzz * dz;
-                    T RQR = Qx * dx + Qy * dy + Qz * dz;
-                    T fac = qj * R1 + dR * R2 + RQR * R3 * T(1.0 / 3.0);
-                    const T q2 = T(2.0 / 3.0) * R2;
-                    fx += fac * dx - R1 * djx - q2 * Qx;
-                    fy += fac * dy - R1 * djy - q2 * Qy;
-                    fz += fac * dz - R1 * djz - q2 * Qz;
-                    if (!diag) {
-                        // field at j from site i (R -> -R)
-                        dR = dix * dx + diy * dy + diz * dz;
-                        Qx = qxx * dx + qxy * dy + qxz * dz;
-                        Qy = qxy * dx + qyy * dy + qyz * dz;
-                        Qz = qxz * dx + qyz * dy + qzz * dz;
-                        RQR = Qx * dx + Qy * dy + Qz * dz;
-                        fac = qi * R1 - dR * R2 + RQR * R3 * T(1.0 / 3.0);
-                        gx += -fac * dx - R1 * dix + q2 * Qx;
-                        gy += -fac * dy - R1 * diy + q2 * Qy;
-                        gz += -fac * dz - R1 * diz + q2 * Qz;
-                    }
-                }
+            S.pos[32 + lane] = cpos[cs];
+            T4 m, c, d;
+            m.x = m.y = m.z = m.w = T(0);
+            c = m;
+            d = m;
+            if (sj >= 0) {
+                const T4 a = posq[sj], b = dipd[sj];
+                c = quad0[sj];
+                d = quad1[sj];
+                m.x = a.w; m.y = b.x; m.z = b.y; m.w = b.z;
             }
-            const int src = (lane + 1) & 31;
-            xj = shfl1(xj, src); yj = shfl1(yj, src); zj = shfl1(zj, src); qj = shfl1(qj, src);
-            djx = shfl1(djx, src); djy = shfl1(djy, src); djz = shfl1(djz, src); tj = shfl1(tj, src);
-            pxx = shfl1(pxx, src); pxy = shfl1(pxy, src); pxz = shfl1(pxz, src);
-            pyy = shfl1(pyy, src); pyz = shfl1(pyz, src); pzz = shfl1(pzz, src);
-            gx = shfl1(gx, src); gy = shfl1(gy, src); gz = shfl1(gz, src);
+            S.qd[32 + lane] = m;
+            S.qa[32 + lane] = c;
+            S.qb[0][32 + lane] = d.x;
+            S.qb[1][32 + lane] = d.y;
+            ex = wa.chunk_flag[it.y] ? wa.chunk_mask[cs] : 0u;
         }
-        ax += (double)fx; ay += (double)fy; az += (double)fz;
-        if (!diag && sj >= 0) flush3(acc, n_pad, sj, (double)gx, (double)gy, (double)gz);
+        S.ex[lane] = ex;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            S.acc[c][lane] = T(0);
+            S.acc[c][32 + lane] = T(0);
+        }
+        const int total = build_side_queue(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
+                                           S.queue);
+        __syncwarp();
+        const int per = (total + 31) >> 5;
+        const int e0 = lane * per, e1 = min(total, e0 + per);
+        int cur = -1;
+        T4 self;
+        self.x = self.y = self.z = self.w = T(0);
+        T f0 = 0, f1 = 0, f2 = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int q = S.queue[e];
+            const int tg = q >> 5, sl = q & 31;
+            if (tg != cur) {
+                if (cur >= 0) {
+                    atomicAdd(&S.acc[0][cur], f0);
+                    atomicAdd(&S.acc[1][cur], f1);
+                    atomicAdd(&S.acc[2][cur], f2);
+                }
+                f0 = f1 = f2 = T(0);
+                cur = tg;
+                self = S.pos[tg];
+            }
+            const int src = tg < 32 ? 32 + sl : sl;
+            const bool exb = tg < 32 ? (S.ex[tg] >> sl) & 1u : (S.ex[sl] >> (tg - 32)) & 1u;
+            const T4 o = S.pos[src], m = S.qd[src], qa = S.qa[src];
+            const T qyz = S.qb[0][src], qzz = S.qb[1][src];
+            T dx, dy, dz;
+            pair_vector<T, MINIMG>(pc, self.x, self.y, self.z, o.x, o.y, o.z, T(0), T(0), T(0), dx, dy, dz);
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+            T B[3], U[3], oml[3];
+            screened<T, 3>(pc, r, rinv, rinv2, B, U);
+            thole_oml<T, 3>(pc.thole_a * r2 * r * self.w * o.w, oml);
+            const T R1 = B[0] - (exb ? U[0] : oml[0] * U[0]);
+            const T R2 = B[1] - (exb ? U[1] : oml[1] * U[1]);
+            const T R3 = B[2] - (exb ? U[2] : oml[2] * U[2]);
+            // field at the target of the source's (q, d, Q), R = x_target - x_source
+            const T dR = m.y * dx + m.z * dy + m.w * dz;
+            const T Qx = qa.x * dx + qa.y * dy + qa.z * dz;
+            const T Qy = qa.y * dx + qa.w * dy + qyz * dz;
+            const T Qz = qa.z * dx + qyz * dy + qzz * dz;
+            const T RQR = Qx * dx + Qy * dy + Qz * dz;
+            const T fac = m.x * R1 + dR * R2 + RQR * R3 * T(1.0 / 3.0);
+            const T q2 = T(2.0 / 3.0) * R2;
+            f0 += fac * dx - R1 * m.y - q2 * Qx;
+            f1 += fac * dy - R1 * m.z - q2 * Qy;
+            f2 += fac * dz - R1 * m.w - q2 * Qz;
+        }
+        if (cur >= 0) {
+            atomicAdd(&S.acc[0][cur], f0);
+            atomicAdd(&S.acc[1][cur], f1);
+            atomicAdd(&S.acc[2][cur], f2);
+        }
+        __syncwarp();
+        ax += (double)S.acc[0][lane];
+        ay += (double)S.acc[1][lane];
+        az += (double)S.acc[2][lane];
+        if (diag) {
+            ax += (double)S.acc[0][32 + lane];
+            ay += (double)S.acc[1][32 + lane];
+            az += (double)S.acc[2][32 + lane];
+        } else if (sj >= 0) {
+            flush3(acc, n_pad, sj, (double)S.acc[0][32 + lane], (double)S.acc[1][32 + lane],
+                   (double)S.acc[2][32 + lane]);
+        }
     }
     if (curI >= 0 && curI * 32 + lane < pc.n) flush3(acc, n_pad, curI * 32 + lane, ax, ay, az);
 }
@@ -221,30 +272,9 @@ __global__ void __launch_bounds__(128) k_matvec(
             S.acc[c][lane] = T(0);
             S.acc[c][32 + lane] = T(0);
         }
-        // queue: row sides (target i-lane, source j-lane), then column sides (target 32 + j-lane)
-        unsigned row = SHORT ? wa.smask[(size_t)t * 32 + lane] : wa.pmask[(size_t)t * 32 + lane];
-        unsigned col = SHORT ? wa.smask_t[(size_t)t * 32 + lane] : wa.pmask_t[(size_t)t * 32 + lane];
-        const int nr = __popc(row), nc = __popc(col);
-        int ir = nr, ic = nc;
-        for (int off = 1; off < 32; off <<= 1) {
-            const int vr = __shfl_up_sync(0xffffffffu, ir, off);
-            const int vc = __shfl_up_sync(0xffffffffu, ic, off);
-            if (lane >= off) { ir += vr; ic += vc; }
-        }
-        const int prow = __shfl_sync(0xffffffffu, ir, 31);
-        const int total = prow + __shfl_sync(0xffffffffu, ic, 31);
-        int pos = ir - nr;
-        while (row) {
-            const int b = __ffs(row) - 1;
-            row &= row - 1u;
-            S.queue[pos++] = (unsigned short)((lane << 5) | b);
-        }
-        pos = prow + ic - nc;
-        while (col) {
-            const int b = __ffs(col) - 1;
-            col &= col - 1u;
-            S.queue[pos++] = (unsigned short)(((32 + lane) << 5) | b);
-        }
+        const int total =
+            SHORT ? build_side_queue(wa.smask[(size_t)t * 32 + lane], wa.smask_t[(size_t)t * 32 + lane], lane, S.queue)
+                  : build_side_queue(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane, S.queue);
         __syncwarp();
         const int per = (total + 31) >> 5;
         const int e0 = lane * per, e1 = min(total, e0 + per);
@@ -335,9 +365,9 @@ int perm_field_t(ap_ctx *ctx, cudaStream_t s) {
     auto kern = ctx->minimg ? k_perm_field<T, true> : k_perm_field<T, false>;
     static int grids[2] = {0, 0};
     int &grid = grids[ctx->minimg];
-    if (!grid) grid = resident_grid(ctx, kern, 256);
-    kern<<<grid, 256, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
-                              (const T4 *)ctx->quad1, ctx->acc, ctx->n_pad, pc);
+    if (!grid) grid = resident_grid(ctx, kern, 32 * pf_warps<T>());
+    kern<<<grid, 32 * pf_warps<T>(), 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd,
+                                             (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, ctx->acc, ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }

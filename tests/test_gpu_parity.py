@@ -189,3 +189,21 @@ def test_full_size_water_sampled_rows():
     eps = DEBYE * np.sqrt(np.mean(np.sum((s.alpha[rows, None] * resid) ** 2, axis=1)))
     assert eps < 1.5e-5
     c.close()
+
+
+def test_dipole_matvec_after_drift_without_rebuild(c1):
+    """Lists built at one configuration, field and dipole products at a drifted one (every
+    atom within buffer/2): the filtered chunks and pair masks follow the configuration."""
+    c = _ctx(c1, binding.AP_FP64)
+    s2 = synth.perturb(c1, 31, sigma_t=0.2, sigma_r=0.05)
+    disp = np.linalg.norm(s2.xyz - c1.xyz, axis=1)
+    assert disp.max() < 1.0
+    c.set_positions(s2.xyz)
+    c.permanent_field()
+    o = _oracle(s2)
+    assert _rel_rms(c.field.cpu().numpy(), o.permanent_field()) < 1e-9
+    v = np.random.default_rng(6).normal(size=(c1.n, 3)) * 0.1
+    out = torch.zeros((c1.n, 3), dtype=torch.float64, device="cuda")
+    c.matvec(torch.tensor(v, device="cuda"), out)
+    assert _rel_rms(out.cpu().numpy(), o.apply_T(v)) < 1e-9
+    c.close()
