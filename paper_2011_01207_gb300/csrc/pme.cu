@@ -15,6 +15,7 @@
 #include "common.cuh"
 
 #include <climits>
+#include <cstdint>
 #include <cmath>
 #include <vector>
 
@@ -88,6 +89,32 @@ __device__ __forceinline__ void make_stencil(const PmeConsts<T> &pc, T x, T y, T
     }
 }
 
+// adds v[t] to row[k[t]], t = 0..4, where k[t] = k[0] - t (mod K): the stencil's five points
+// along x. Unless the row wraps they are contiguous, and in FP32 two float2 atomics and one
+// scalar cover them (aligned to the pair boundary) instead of five scalar ones.
+template <class T>
+__device__ __forceinline__ void add_row5(T *row, const int *k, const T *v) {
+#pragma unroll
+    for (int t = 0; t < 5; ++t) atomicAdd(row + k[t], v[t]);
+}
+__device__ __forceinline__ void add_row5(float *row, const int *k, const float *v) {
+    if (k[0] >= 4) {
+        float *p0 = row + (k[0] - 4);   // point t = 4
+        if ((reinterpret_cast<uintptr_t>(p0) & 7u) == 0) {
+            atomicAdd(reinterpret_cast<float2 *>(p0), make_float2(v[4], v[3]));
+            atomicAdd(reinterpret_cast<float2 *>(p0 + 2), make_float2(v[2], v[1]));
+            atomicAdd(p0 + 4, v[0]);
+        } else {
+            atomicAdd(p0, v[4]);
+            atomicAdd(reinterpret_cast<float2 *>(p0 + 1), make_float2(v[3], v[2]));
+            atomicAdd(reinterpret_cast<float2 *>(p0 + 3), make_float2(v[1], v[0]));
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < 5; ++t) atomicAdd(row + k[t], v[t]);
+    }
+}
+
 // spread permanent multipoles (q, d, Q) ------------------------------------------------
 template <class T>
 __global__ void k_spread_multipoles(const typename V4<T>::type *__restrict__ posq,
@@ -106,19 +133,20 @@ __global__ void k_spread_multipoles(const typename V4<T>::type *__restrict__ pos
     const T Qxx = c.x * sx * sx * third, Qyy = c.w * sy * sy * third, Qzz = d.y * sz * sz * third;
     const T Qxy = c.y * sx * sy * T(2.0 / 3.0), Qxz = c.z * sx * sz * T(2.0 / 3.0), Qyz = d.x * sy * sz * T(2.0 / 3.0);
     const int Kx = pc.K[0], Ky = pc.K[1];
-#pragma unroll 1
+#pragma unroll
     for (int t3 = 0; t3 < 5; ++t3) {
         const T z0 = st.th[2][t3], z1 = st.d1[2][t3], z2 = st.d2[2][t3];
-#pragma unroll 1
+#pragma unroll
         for (int t2 = 0; t2 < 5; ++t2) {
             const T y0 = st.th[1][t2], y1 = st.d1[1][t2], y2 = st.d2[1][t2];
             const T A = q * y0 * z0 + dy * y1 * z0 + dz * y0 * z1 + Qyy * y2 * z0 + Qzz * y0 * z2 + Qyz * y1 * z1;
             const T Bc = dx * y0 * z0 + Qxy * y1 * z0 + Qxz * y0 * z1;
             const T Cc = Qxx * y0 * z0;
             T *row = grid + ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
+            T v[5];
 #pragma unroll
-            for (int t1 = 0; t1 < 5; ++t1)
-                atomicAdd(row + st.k[0][t1], st.th[0][t1] * A + st.d1[0][t1] * Bc + st.d2[0][t1] * Cc);
+            for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc + st.d2[0][t1] * Cc;
+            add_row5(row, st.k[0], v);
         }
     }
 }
@@ -135,7 +163,7 @@ __global__ void k_spread_dipoles(const typename V4<T>::type *__restrict__ posq,
     make_stencil<T, 1>(pc, a.x, a.y, a.z, st);
     const T px = b.x * pc.s[0], py = b.y * pc.s[1], pz = b.z * pc.s[2];
     const int Kx = pc.K[0], Ky = pc.K[1];
-#pragma unroll 1
+#pragma unroll
     for (int t3 = 0; t3 < 5; ++t3) {
         const T z0 = st.th[2][t3], z1 = st.d1[2][t3];
 #pragma unroll
@@ -144,8 +172,10 @@ __global__ void k_spread_dipoles(const typename V4<T>::type *__restrict__ posq,
             const T A = py * y1 * z0 + pz * y0 * z1;
             const T Bc = px * y0 * z0;
             T *row = grid + ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
+            T v[5];
 #pragma unroll
-            for (int t1 = 0; t1 < 5; ++t1) atomicAdd(row + st.k[0][t1], st.th[0][t1] * A + st.d1[0][t1] * Bc);
+            for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc;
+            add_row5(row, st.k[0], v);
         }
     }
 }
@@ -171,7 +201,7 @@ __global__ void k_gather_field(const typename V4<T>::type *__restrict__ posq, co
     make_stencil<T, 1>(pc, a.x, a.y, a.z, st);
     const int Kx = pc.K[0], Ky = pc.K[1];
     T gx = 0, gy = 0, gz = 0;
-#pragma unroll 1
+#pragma unroll
     for (int t3 = 0; t3 < 5; ++t3) {
         const T z0 = st.th[2][t3], z1 = st.d1[2][t3];
 #pragma unroll
@@ -210,10 +240,10 @@ __global__ void k_gather_derivs(const typename V4<T>::type *__restrict__ posq, c
     T D[20];
 #pragma unroll
     for (int c = 0; c < 20; ++c) D[c] = 0;
-#pragma unroll 1
+#pragma unroll
     for (int t3 = 0; t3 < 5; ++t3) {
         const T z[4] = {st.th[2][t3], st.d1[2][t3], st.d2[2][t3], st.d3[2][t3]};
-#pragma unroll 1
+#pragma unroll
         for (int t2 = 0; t2 < 5; ++t2) {
             const T y[4] = {st.th[1][t2], st.d1[1][t2], st.d2[1][t2], st.d3[1][t2]};
             const T *row = phi + ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
