@@ -7,25 +7,26 @@
 
 namespace {
 
-__device__ __forceinline__ double mi(double v, double L) { return v - L * rint(v / L); }
+// FP64 division and sqrt are slow on this part: minimum image with 1/L, normalisation with rsqrt
+__device__ __forceinline__ double mi(double v, double L, double iL) { return v - L * rint(v * iL); }
 
 __device__ __forceinline__ void unit3(double *v) {
-    double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    v[0] /= n; v[1] /= n; v[2] /= n;
+    const double in = rsqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] *= in; v[1] *= in; v[2] *= in;
 }
 
 // columns of R are the local x, y, z axes in global coordinates
 __device__ void frame_matrix(const double *__restrict__ xyz, int i, int type, int za, int xa, double3 L,
-                             double R[3][3], double *fv) {
+                             double3 iL, double R[3][3], double *fv) {
     for (int a = 0; a < 6; ++a) fv[a] = 0.0;
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) R[a][b] = (a == b) ? 1.0 : 0.0;
     if (type != AP_FRAME_Z_THEN_X && type != AP_FRAME_BISECTOR) return;
-    const double Ls[3] = {L.x, L.y, L.z};
+    const double Ls[3] = {L.x, L.y, L.z}, iLs[3] = {iL.x, iL.y, iL.z};
     double vz[3], vx[3], z[3], x[3];
     for (int a = 0; a < 3; ++a) {
-        vz[a] = mi(xyz[3 * za + a] - xyz[3 * i + a], Ls[a]);
-        vx[a] = mi(xyz[3 * xa + a] - xyz[3 * i + a], Ls[a]);
+        vz[a] = mi(xyz[3 * za + a] - xyz[3 * i + a], Ls[a], iLs[a]);
+        vx[a] = mi(xyz[3 * xa + a] - xyz[3 * i + a], Ls[a], iLs[a]);
         fv[a] = vz[a];
         fv[3 + a] = vx[a];
     }
@@ -54,7 +55,7 @@ __device__ void frame_matrix(const double *__restrict__ xyz, int i, int type, in
 template <class T>
 __global__ void k_load(const double *__restrict__ xyz, const double *__restrict__ mpole,
                        const int *__restrict__ frame, const double *__restrict__ alpha,
-                       const int *__restrict__ iperm, const float4 *__restrict__ bcenter, int n, double3 L,
+                       const int *__restrict__ iperm, const float4 *__restrict__ bcenter, int n, double3 L, double3 iL,
                        typename V4<T>::type *__restrict__ posq, typename V4<T>::type *__restrict__ dipd,
                        typename V4<T>::type *__restrict__ quad0, typename V4<T>::type *__restrict__ quad1,
                        double *__restrict__ alpha_s, double *__restrict__ rot, double *__restrict__ mpl,
@@ -64,9 +65,9 @@ __global__ void k_load(const double *__restrict__ xyz, const double *__restrict_
     const int s = iperm[i];
     const float4 c = bcenter[s >> 5];
     double p[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
-    const double Ls[3] = {L.x, L.y, L.z};
+    const double Ls[3] = {L.x, L.y, L.z}, iLs[3] = {iL.x, iL.y, iL.z};
     const double cc[3] = {c.x, c.y, c.z};
-    for (int a = 0; a < 3; ++a) p[a] -= Ls[a] * rint((p[a] - cc[a]) / Ls[a]);   // image nearest the block
+    for (int a = 0; a < 3; ++a) p[a] -= Ls[a] * rint((p[a] - cc[a]) * iLs[a]);   // image nearest the block
     int type = frame[3 * i];
     const int za = frame[3 * i + 1], xa = frame[3 * i + 2];
     bool frame_ok = true;
@@ -77,7 +78,7 @@ __global__ void k_load(const double *__restrict__ xyz, const double *__restrict_
     }
     if (!frame_ok) type = AP_FRAME_NONE;   // never index with a bad frame atom; reported below
     double R[3][3];
-    frame_matrix(xyz, i, type, za, xa, L, R, fvec + 6 * s);
+    frame_matrix(xyz, i, type, za, xa, L, iL, R, fvec + 6 * s);
     const double *m = mpole + 10 * i;
     double dl[3] = {m[1], m[2], m[3]};
     double Ql[3][3] = {{m[4], m[5], m[6]}, {m[5], m[7], m[8]}, {m[6], m[8], m[9]}};
@@ -95,7 +96,7 @@ __global__ void k_load(const double *__restrict__ xyz, const double *__restrict_
     T4 v;
     v.x = (T)p[0]; v.y = (T)p[1]; v.z = (T)p[2]; v.w = (T)m[0];
     posq[s] = v;
-    v.x = (T)dg[0]; v.y = (T)dg[1]; v.z = (T)dg[2]; v.w = (T)(al > 0.0 ? 1.0 / sqrt(al) : 1e4);
+    v.x = (T)dg[0]; v.y = (T)dg[1]; v.z = (T)dg[2]; v.w = (T)(al > 0.0 ? rsqrt(al) : 1e4);
     dipd[s] = v;
     v.x = (T)Qg[0][0]; v.y = (T)Qg[0][1]; v.z = (T)Qg[0][2]; v.w = (T)Qg[1][1];
     quad0[s] = v;
@@ -162,10 +163,11 @@ int load_t(ap_ctx *ctx, const double *d_xyz, const double *d_mpole, const int *d
     typedef typename V4<T>::type T4;
     const ap_params &P = ctx->prm;
     double3 L = make_double3(P.box[0], P.box[1], P.box[2]);
+    double3 iL = make_double3(1.0 / P.box[0], 1.0 / P.box[1], 1.0 / P.box[2]);
     int *bad = (int *)ctx->red;   // scratch int at the start of the reduction buffer
     AP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), ctx->s0));
     k_load<T><<<ap_grid_for(ctx->n, 128), 128, 0, ctx->s0>>>(
-        d_xyz, d_mpole, d_frame, d_alpha, ctx->iperm, ctx->bcenter, ctx->n, L, (T4 *)ctx->posq, (T4 *)ctx->dipd,
+        d_xyz, d_mpole, d_frame, d_alpha, ctx->iperm, ctx->bcenter, ctx->n, L, iL, (T4 *)ctx->posq, (T4 *)ctx->dipd,
         (T4 *)ctx->quad0, (T4 *)ctx->quad1, ctx->alpha, ctx->rot, ctx->mpl, ctx->frame_s, ctx->fvec, bad);
     if (ctx->n_pad > ctx->n)
         k_pad<T><<<1, 32, 0, ctx->s0>>>(ctx->n, ctx->n_pad, (T4 *)ctx->posq, (T4 *)ctx->dipd, (T4 *)ctx->quad0,

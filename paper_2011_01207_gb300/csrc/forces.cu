@@ -281,12 +281,12 @@ __global__ void k_recip_forces(const double *__restrict__ D, const double *__res
     for (int k = 0; k < 3; ++k) {
         double g = 0.0;
         for (int l = 0; l < 3; ++l) g += m[l] * (Hu[k][l] + HM[k][l]) + dd[l] * Hu[k][l];
-        g += q * gu[k] + QT[k] / 3.0;
+        g += q * gu[k] + QT[k] * (1.0 / 3.0);
         frc[k * n_pad + s] -= f * g;
         gdip[k * n_pad + s] += f * gu[k] - f * self_coef * m[k];
     }
     const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-    for (int k = 0; k < 6; ++k) gquad[k * n_pad + s] += f / 3.0 * Hu[ia[k]][ib[k]];
+    for (int k = 0; k < 6; ++k) gquad[k * n_pad + s] += f * (1.0 / 3.0) * Hu[ia[k]][ib[k]];
 }
 
 __device__ __forceinline__ double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
@@ -338,39 +338,40 @@ __global__ void k_frame_forces(const double *__restrict__ gdip, const double *__
         const double vxz = dot3(vx, za);
         double w[3];
         for (int a = 0; a < 3; ++a) w[a] = vx[a] - vxz * za[a];
-        const double nw = sqrt(dot3(w, w)), nz = sqrt(dot3(vz, vz));
+        // reciprocal norms with rsqrt: FP64 division and sqrt are slow on this part
+        const double inw = rsqrt(dot3(w, w)), inz = rsqrt(dot3(vz, vz));
         const double gxx = dot3(gx, xa);
         double gw[3];
-        for (int a = 0; a < 3; ++a) gw[a] = (gx[a] - gxx * xa[a]) / nw;
+        for (int a = 0; a < 3; ++a) gw[a] = (gx[a] - gxx * xa[a]) * inw;
         const double gwz = dot3(gw, za);
         for (int a = 0; a < 3; ++a) {
             g_vx[a] = gw[a] - gwz * za[a];
             gz[a] = gz[a] - gwz * vx[a] - vxz * gw[a];
         }
         const double gzz = dot3(gz, za);
-        for (int a = 0; a < 3; ++a) g_vz[a] = (gz[a] - gzz * za[a]) / nz;
+        for (int a = 0; a < 3; ++a) g_vz[a] = (gz[a] - gzz * za[a]) * inz;
     } else {
-        const double n1 = sqrt(dot3(vz, vz)), n2 = sqrt(dot3(vx, vx));
+        const double in1 = rsqrt(dot3(vz, vz)), in2 = rsqrt(dot3(vx, vx));
         double u1[3], u2[3], sv[3], w[3];
-        for (int a = 0; a < 3; ++a) { u1[a] = vz[a] / n1; u2[a] = vx[a] / n2; sv[a] = u1[a] + u2[a]; }
+        for (int a = 0; a < 3; ++a) { u1[a] = vz[a] * in1; u2[a] = vx[a] * in2; sv[a] = u1[a] + u2[a]; }
         const double u2z = dot3(u2, za);
         for (int a = 0; a < 3; ++a) w[a] = u2[a] - u2z * za[a];
-        const double nw = sqrt(dot3(w, w)), ns = sqrt(dot3(sv, sv));
+        const double inw = rsqrt(dot3(w, w)), ins = rsqrt(dot3(sv, sv));
         const double gxx = dot3(gx, xa);
         double gw[3], gu2[3], gs[3];
-        for (int a = 0; a < 3; ++a) gw[a] = (gx[a] - gxx * xa[a]) / nw;
+        for (int a = 0; a < 3; ++a) gw[a] = (gx[a] - gxx * xa[a]) * inw;
         const double gwz = dot3(gw, za);
         for (int a = 0; a < 3; ++a) {
             gu2[a] = gw[a] - gwz * za[a];
             gz[a] = gz[a] - gwz * u2[a] - u2z * gw[a];
         }
         const double gzz = dot3(gz, za);
-        for (int a = 0; a < 3; ++a) gs[a] = (gz[a] - gzz * za[a]) / ns;
+        for (int a = 0; a < 3; ++a) gs[a] = (gz[a] - gzz * za[a]) * ins;
         for (int a = 0; a < 3; ++a) gu2[a] += gs[a];
         const double a1 = dot3(gs, u1), a2 = dot3(gu2, u2);
         for (int a = 0; a < 3; ++a) {
-            g_vz[a] = (gs[a] - a1 * u1[a]) / n1;
-            g_vx[a] = (gu2[a] - a2 * u2[a]) / n2;
+            g_vz[a] = (gs[a] - a1 * u1[a]) * in1;
+            g_vx[a] = (gu2[a] - a2 * u2[a]) * in2;
         }
     }
     for (int a = 0; a < 3; ++a) {

@@ -200,7 +200,8 @@ __global__ void k_features(const double *__restrict__ E, const double *__restric
     if (s >= n) return;
     const double *R = rot + 9 * s;
     auto loc = [&](const double *F, int slot, double *o) {
-        const double e[3] = {F[slot] / MLP_E_SCALE, F[n_pad + slot] / MLP_E_SCALE, F[2 * n_pad + slot] / MLP_E_SCALE};
+        const double e[3] = {F[slot] * (1.0 / MLP_E_SCALE), F[n_pad + slot] * (1.0 / MLP_E_SCALE),
+                             F[2 * n_pad + slot] * (1.0 / MLP_E_SCALE)};
         for (int b = 0; b < 3; ++b) o[b] = R[0 * 3 + b] * e[0] + R[1 * 3 + b] * e[1] + R[2 * 3 + b] * e[2];
     };
     double f[16];
