@@ -40,6 +40,17 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # source: vector 6, r^2 5, rsqrt/r/r^-2 3, screening with erfc/exp 32, B1/B2 and U1/U2 10,
 # Thole 8, R1/R2 4, two field updates 36; FMA = 2)
 FLOPS_PER_PAIR_MATVEC = 104
+# algorithmic FP32 work per in-range pair of the other pair kernels, counted from their source
+# (FMA = 2, MUFU = 1; the radial terms once per pair): permanent field with quadrupoles (radial
+# terms to R_3, both fields) and the real-space forces (radial terms to R_4, both multipole
+# gradients, the dipole-dipole term, dU/dd and dU/dQ of both atoms)
+FLOPS_PER_PAIR_FIELD = 174
+FLOPS_PER_PAIR_FORCES = 467
+MLP_FLOPS_PER_ATOM = 2 * (16 * 128 + 128 * 128 + 128 * 3)
+# bytes per slot of one PCG iteration's vector kernels: direction (r, alpha, p in/out),
+# q = A p (p, diagonal, real and reciprocal fields, q out, accumulator clear), update
+# (p, q, alpha, mu and r in/out)
+PCG_VECTOR_BYTES_PER_SLOT = 64 + 108 + 144
 WORKLOAD = "water_96000_atoms_98.7A_grid100_rc7+2_mixed_pcg1e-5"
 
 
@@ -66,6 +77,50 @@ def _peaks():
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def _bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured burst"
+    return 1900.0, "fallback"
+
+
+def kernel_rooflines(kern, per_launch_counts, n, n_pad, npairs, grid):
+    """Each timed kernel against its bound: FP32 ALU (pair kernels), HBM (spread, gather,
+    convolution, PCG vectors; algorithmic bytes) or BF16 tensor (MLP)."""
+    hbm, hbm_kind = _peaks()
+    bf16, bf16_kind = _bf16_peak()
+    k3 = grid[0] * grid[1] * grid[2]
+    kc = grid[1] * grid[2] * (grid[0] // 2 + 1)
+    work = {
+        "real_matvec": ("alu", npairs * FLOPS_PER_PAIR_MATVEC),
+        "real_field": ("alu", npairs * FLOPS_PER_PAIR_FIELD),
+        "pair_forces": ("alu", npairs * FLOPS_PER_PAIR_FORCES),
+        "spread_dipoles": ("hbm", n * 32 + k3 * 4),
+        "gather_field": ("hbm", k3 * 4 + n * 28),
+        "convolve": ("hbm", 2 * kc * 8 + kc * 4),
+        "spread_multipoles": ("hbm", n * 64 + k3 * 4),
+        "pcg_vectors": ("hbm", n_pad * PCG_VECTOR_BYTES_PER_SLOT),
+        "mlp_forward": ("tensor", n * MLP_FLOPS_PER_ATOM),
+    }
+    out = {}
+    for name, (bound, w) in work.items():
+        if name not in kern:
+            continue
+        sec = kern[name] * 1e-3
+        if bound == "hbm":
+            ach, peak, unit, kind = w / sec / 1e9, hbm, "GB/s", hbm_kind
+        elif bound == "alu":
+            ach, peak, unit, kind = w / sec / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s", "derived"
+        else:
+            ach, peak, unit, kind = w / sec / 1e12, bf16, "TFLOP/s", bf16_kind
+        out[name] = {"bound": bound, "launch_us": round(kern[name] * 1e3, 2),
+                     "launches_per_step": per_launch_counts.get(name, 1), "work_per_launch": int(w),
+                     "achieved": round(ach, 3), "peak": round(peak, 2), "unit": unit, "peak_kind": kind,
+                     "frac": round(ach / peak, 4)}
+    return out
 
 
 class Clocks:
@@ -253,6 +308,17 @@ def run_ours(args):
     kern = {k: binding.ap_time_kernel(ctx.ctx, k, 30) for k in
             ("real_matvec", "spread_dipoles", "gather_field", "convolve", "real_field", "spread_multipoles",
              "pair_forces")}
+    kern["pcg_vectors"] = binding.ap_time_kernel(ctx.ctx, "pcg_vectors", 30)
+    feat_t = torch.randn((s.n, 16), dtype=torch.float32, device=dev)
+    y_t = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
+    binding.ap_mlp_forward(trainer.packed, feat_t, y_t)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(30):
+        binding.ap_mlp_forward(trainer.packed, feat_t, y_t)
+    ev1.record(stream)
+    ev1.synchronize()
+    kern["mlp_forward"] = ev0.elapsed_time(ev1) / 30
     per_step = {"real_matvec": kern["real_matvec"] * (it_mean + 1),
                 "spread_dipoles": kern["spread_dipoles"] * (it_mean + 1),
                 "gather_field": kern["gather_field"] * (it_mean + 1),
@@ -267,8 +333,10 @@ def run_ours(args):
                 "traffic": captured_traffic(), "traffic_unit": "bytes per launch (ncu, cold caches)", "flop_per_launch": flop, "pairs_in_cutoff": npairs,
                 "launch_ms": round(kern["real_matvec"], 4),
                 "peak_note": "FP32 FMA peak from 152 SMs x 128 lanes x 2 x 2070 MHz",
-                "spread_dipoles_gbs": round((s.n * 32 + GRID[0] * GRID[1] * GRID[2] * 4) / (kern["spread_dipoles"] * 1e-3) / 1e9, 1),
                 "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind}
+    counts = {"real_matvec": it_mean + 1, "spread_dipoles": it_mean + 2, "gather_field": it_mean + 1,
+              "convolve": it_mean + 3, "pcg_vectors": it_mean}
+    kernels = kernel_rooflines(kern, counts, s.n, (s.n + 31) // 32 * 32, npairs, GRID)
     nb, nt, ne = ctx.stats()
     result = {
         "metric": METRIC, "value": round(ms, 4), "unit": "ms/step", "n_gpus": world, "steps": args.steps,
@@ -291,6 +359,7 @@ def run_ours(args):
         "kernel_ms": {k: round(v, 4) for k, v in kern.items()},
         "kernel_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
         "roofline": roofline,
+        "kernels": kernels,
         "clocks": clk,
         "wall_s_timed_region": round(t_wall, 3),
     }

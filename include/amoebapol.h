@@ -160,6 +160,9 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 #define AP_KERNEL_SPREAD_MULTIPOLES 5   /* a3: spread of the permanent multipoles */
 #define AP_KERNEL_PAIR_FORCES       6   /* a9: real-space polarization forces and torque sources,
                                            at the dipoles of the last energy/force call */
+#define AP_KERNEL_PCG_VECTORS       7   /* a7: one iteration's vector kernels (direction, q = A p
+                                           with p.q, update with r.z and |z|^2); advances the last
+                                           solve's state, so solve again before using its result */
 int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
 
 /* Batched replicas: many independent systems of uneven size advanced by one CUDA-graph

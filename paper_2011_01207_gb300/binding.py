@@ -26,7 +26,8 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "ap_mlp_features", "ap_learned_guess", "ap_mlp_gradient", "ap_mlp_train_step",
            "ap_batch_create", "ap_batch_capture", "ap_batch_launch", "ap_batch_destroy", "ap_autotune")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
-           "spread_multipoles": 5, "pair_forces": 6}
+           "spread_multipoles": 5, "pair_forces": 6,
+           "pcg_vectors": 7}
 
 
 class ApParams(ctypes.Structure):

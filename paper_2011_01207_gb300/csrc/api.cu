@@ -15,6 +15,7 @@ int ap_fail(ap_ctx *c, int code, const std::string &msg) {
 int dipole_field_apply(ap_ctx *ctx, const double *d_v, double *d_out);
 int pme_stage_launch(ap_ctx *ctx, int stage, cudaStream_t s);
 int pair_forces_launch(ap_ctx *ctx, cudaStream_t s);
+int pcg_vectors_launch(ap_ctx *ctx, cudaStream_t s);
 
 namespace {
 
@@ -26,13 +27,13 @@ int dalloc(ap_ctx *ctx, P **p, size_t bytes) {
 }
 
 void free_all(ap_ctx *c) {
-    void *ptrs[] = {c->perm, c->iperm, c->bcenter, c->tiles, c->tshift, c->tile_excl, c->excl_mask, c->cell_count,
+    void *ptrs[] = {c->perm, c->iperm, c->bcenter, c->tiles, c->tshift, c->tshift_lo, c->tile_excl, c->excl_mask, c->cell_count,
                     c->tmp_int, c->excl_off, c->excl_atoms, c->posq, c->dipd, c->quad0, c->quad1, c->alpha,
                     c->E, c->acc, c->rec, c->rot, c->mpl, c->frame_s, c->fvec, c->mu, c->r, c->qv, c->p, c->st,
                     c->grid, c->cgrid, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf,
                     c->tile_off, c->chunk_j, c->chunk_pos, c->chunk_src, c->chunk_mask, c->chunk_flag, c->nchunk,
                     c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y, c->smask, c->smask_t, c->e1s,
-                    c->dg};
+                    c->dg, c->stb, c->stw};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -75,6 +76,8 @@ int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
     if ((r = dalloc(ctx, &ctx->nchunk, sizeof(int) * nb))) return r;
     if ((r = dalloc(ctx, &ctx->n_work, sizeof(int) * 4))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->posq, 4 * es * np))) return r;
+    if ((r = dalloc(ctx, &ctx->stb, sizeof(int4) * np))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->stw, 4 * es * np))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->dipd, 4 * es * np))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->quad0, 4 * es * np))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->quad1, 4 * es * np))) return r;
@@ -255,6 +258,7 @@ int ap_time_kernel(ap_ctx *ctx, int which, int reps, double *h_ms) {
         case AP_KERNEL_GATHER_FIELD: rc = pme_stage_launch(ctx, 2, ctx->s0); break;
         case AP_KERNEL_SPREAD_MULTIPOLES: rc = pme_stage_launch(ctx, 3, ctx->s0); break;
         case AP_KERNEL_PAIR_FORCES: rc = pair_forces_launch(ctx, ctx->s0); break;
+        case AP_KERNEL_PCG_VECTORS: rc = pcg_vectors_launch(ctx, ctx->s0); break;
         default: rc = ap_fail(ctx, AP_ERR_ARG, "unknown kernel id");
         }
         if (rc) { cudaEventDestroy(a); cudaEventDestroy(b); return rc; }

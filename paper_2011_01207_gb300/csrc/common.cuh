@@ -66,7 +66,9 @@ struct ap_ctx {
     int *iperm = nullptr;     // [n] atom -> slot
     float4 *bcenter = nullptr;   // [n_blocks] block centre (x,y,z) at the last build
     int2 *tiles = nullptr;       // [cap_tiles] block pairs (I <= J), sorted by I then J
-    float4 *tshift = nullptr;    // [cap_tiles] periodic shift added to x_i - x_j
+    float4 *tshift = nullptr;    // [cap_tiles] origin of block J relative to block I's, periodic image
+                                 // included (c_J - c_I + L k), as hi + lo float pairs with tshift_lo
+    float4 *tshift_lo = nullptr; // [cap_tiles]
     int *tile_excl = nullptr;    // [cap_tiles] exclusion-mask slot or -1
     unsigned *excl_mask = nullptr;  // [cap_excl][32]
     int n_tiles = 0, cap_tiles = 0, n_excl_tiles = 0, cap_excl = 0;
@@ -93,8 +95,13 @@ struct ap_ctx {
     int *tmp_int = nullptr; int cap_tmp = 0;
     int *excl_off = nullptr, *excl_atoms = nullptr; int cap_excl_atoms = 0;   // copy of the CSR
 
-    // configuration (sorted slots; element type T = float or double)
-    void *posq = nullptr;     // T4: x, y, z, q
+    // configuration (sorted slots; element type T = float or double). Positions are stored
+    // relative to the origin of the slot's block (its centre at the list build, bcenter):
+    // small numbers, so FP32 keeps ~1e-6 A at any box size; pair kernels see differences
+    // only, and the chunk positions are formed relative to block I's origin in FP64.
+    void *posq = nullptr;     // T4: x, y, z (relative to the block origin), q
+    int4 *stb = nullptr;      // [n_pad] smooth-PME stencil origin floor(K x / L) mod K per dimension
+    void *stw = nullptr;      // T4 [n_pad] its fractional part K x / L - floor(K x / L), from FP64
     void *dipd = nullptr;     // T4: dx, dy, dz, alpha^-1/2 (Thole)
     void *quad0 = nullptr;    // T4: Qxx, Qxy, Qxz, Qyy
     void *quad1 = nullptr;    // T4: Qyz, Qzz, alpha, 0

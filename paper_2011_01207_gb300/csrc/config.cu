@@ -59,7 +59,8 @@ __global__ void k_load(const double *__restrict__ xyz, const double *__restrict_
                        typename V4<T>::type *__restrict__ posq, typename V4<T>::type *__restrict__ dipd,
                        typename V4<T>::type *__restrict__ quad0, typename V4<T>::type *__restrict__ quad1,
                        double *__restrict__ alpha_s, double *__restrict__ rot, double *__restrict__ mpl,
-                       int *__restrict__ frame_s, double *__restrict__ fvec, int *__restrict__ bad) {
+                       int *__restrict__ frame_s, double *__restrict__ fvec, int *__restrict__ bad, int3 K,
+                       double3 sK, int4 *__restrict__ stb, typename V4<T>::type *__restrict__ stw) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int s = iperm[i];
@@ -94,8 +95,26 @@ __global__ void k_load(const double *__restrict__ xyz, const double *__restrict_
     if (!ok || !frame_ok) atomicExch(bad, 1);
     typedef typename V4<T>::type T4;
     T4 v;
-    v.x = (T)p[0]; v.y = (T)p[1]; v.z = (T)p[2]; v.w = (T)m[0];
+    v.x = (T)(p[0] - cc[0]); v.y = (T)(p[1] - cc[1]); v.z = (T)(p[2] - cc[2]); v.w = (T)m[0];
     posq[s] = v;
+    // smooth-PME stencil from the FP64 position: u = K x / L, origin floor(u) mod K, fraction
+    {
+        const int Ks[3] = {K.x, K.y, K.z};
+        const double sk[3] = {sK.x, sK.y, sK.z};
+        int ib[3];
+        double w[3];
+        for (int a = 0; a < 3; ++a) {
+            const double u = p[a] * sk[a];
+            const double b = floor(u);
+            w[a] = u - b;
+            long long k = (long long)b % Ks[a];
+            if (k < 0) k += Ks[a];
+            ib[a] = (k >= 0 && k < Ks[a]) ? (int)k : 0;
+        }
+        stb[s] = make_int4(ib[0], ib[1], ib[2], 0);
+        v.x = (T)w[0]; v.y = (T)w[1]; v.z = (T)w[2]; v.w = (T)0;
+        stw[s] = v;
+    }
     v.x = (T)dg[0]; v.y = (T)dg[1]; v.z = (T)dg[2]; v.w = (T)(al > 0.0 ? rsqrt(al) : 1e4);
     dipd[s] = v;
     v.x = (T)Qg[0][0]; v.y = (T)Qg[0][1]; v.z = (T)Qg[0][2]; v.w = (T)Qg[1][1];
@@ -168,7 +187,9 @@ int load_t(ap_ctx *ctx, const double *d_xyz, const double *d_mpole, const int *d
     AP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), ctx->s0));
     k_load<T><<<ap_grid_for(ctx->n, 128), 128, 0, ctx->s0>>>(
         d_xyz, d_mpole, d_frame, d_alpha, ctx->iperm, ctx->bcenter, ctx->n, L, iL, (T4 *)ctx->posq, (T4 *)ctx->dipd,
-        (T4 *)ctx->quad0, (T4 *)ctx->quad1, ctx->alpha, ctx->rot, ctx->mpl, ctx->frame_s, ctx->fvec, bad);
+        (T4 *)ctx->quad0, (T4 *)ctx->quad1, ctx->alpha, ctx->rot, ctx->mpl, ctx->frame_s, ctx->fvec, bad,
+        make_int3(ctx->K[0], ctx->K[1], ctx->K[2]),
+        make_double3(ctx->K[0] / P.box[0], ctx->K[1] / P.box[1], ctx->K[2] / P.box[2]), ctx->stb, (T4 *)ctx->stw);
     if (ctx->n_pad > ctx->n)
         k_pad<T><<<1, 32, 0, ctx->s0>>>(ctx->n, ctx->n_pad, (T4 *)ctx->posq, (T4 *)ctx->dipd, (T4 *)ctx->quad0,
                                         (T4 *)ctx->quad1, ctx->alpha, ctx->frame_s);

@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(256) k_filter(
     const int2 *__restrict__ tiles, const int *__restrict__ tile_off, const float4 *__restrict__ tshift,
     const int *__restrict__ tile_excl, const unsigned *__restrict__ excl_mask,
     const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd, int nb,
-    T rc2, T Lx, T Ly, T Lz, int *__restrict__ chunk_j, typename V4<T>::type *__restrict__ chunk_pos,
+    T rc2, T Lx, T Ly, T Lz, const float4 *__restrict__ tshift_lo, int *__restrict__ chunk_j,
+    typename V4<T>::type *__restrict__ chunk_pos,
     int *__restrict__ chunk_src, unsigned *__restrict__ chunk_mask, int *__restrict__ chunk_flag,
     int *__restrict__ nchunk) {
     typedef typename V4<T>::type T4;
@@ -47,15 +48,15 @@ __global__ void __launch_bounds__(256) k_filter(
         if (J == I) continue;
         const int sj = J * 32 + lane;
         T4 q = posq[sj];
-        T x = q.x, y = q.y, z = q.z;
+        // positions are relative to their block's origin: move j's to block I's origin and
+        // periodic image with the tile's offset, kept as a float pair (hi + lo) so that the
+        // result (a few A) has full FP32 precision at any box size
+        const float4 oh = tshift[t], ol = tshift_lo[t];
+        T x = (q.x + (T)ol.x) + (T)oh.x, y = (q.y + (T)ol.y) + (T)oh.y, z = (q.z + (T)ol.z) + (T)oh.z;
         if (MINIMG) {
             x -= Lx * rint((x - cx) / Lx);
             y -= Ly * rint((y - cy) / Ly);
             z -= Lz * rint((z - cz) / Lz);
-        } else {
-            const float4 sh = tshift[t];
-            // pairs use x_i - x_j + shift: store x_j - shift, the image of j next to I
-            x -= (T)sh.x; y -= (T)sh.y; z -= (T)sh.z;
         }
         const T gx = max(T(0), max(lo[0] - x, x - hi[0]));
         const T gy = max(T(0), max(lo[1] - y, y - hi[1]));
@@ -198,7 +199,8 @@ int filter_t(ap_ctx *ctx, cudaStream_t s) {
     auto kern = ctx->minimg ? k_filter<T, true> : k_filter<T, false>;
     kern<<<ap_grid_for((long)nb * 32, 256), 256, 0, s>>>(
         ctx->tiles, ctx->tile_off, ctx->tshift, ctx->tile_excl, ctx->excl_mask, (const T4 *)ctx->posq,
-        (const T4 *)ctx->dipd, nb, rc2, (T)P.box[0], (T)P.box[1], (T)P.box[2], ctx->chunk_j, (T4 *)ctx->chunk_pos,
+        (const T4 *)ctx->dipd, nb, rc2, (T)P.box[0], (T)P.box[1], (T)P.box[2], ctx->tshift_lo, ctx->chunk_j,
+        (T4 *)ctx->chunk_pos,
         ctx->chunk_src, ctx->chunk_mask, ctx->chunk_flag, ctx->nchunk);
     k_worklist<<<1, 1024, 0, s>>>(ctx->nchunk, ctx->tile_off, nb, ctx->work, ctx->n_work);
     AP_CUDA(cudaMemsetAsync(ctx->n_work + 1, 0, sizeof(int), s));

@@ -148,7 +148,8 @@ __device__ __forceinline__ bool blocks_near(float4 ci, float4 hi, float4 cj, flo
 // one warp per block I: count (fill == nullptr) or write its partners J >= I
 __global__ void k_tiles(const float4 *__restrict__ center, const float4 *__restrict__ half, int nb,
                         float3 L, float r2, int *__restrict__ count, const int *__restrict__ off,
-                        int2 *__restrict__ tiles, float4 *__restrict__ tshift) {
+                        int2 *__restrict__ tiles, float4 *__restrict__ tshift, float4 *__restrict__ tshift_lo,
+                        double3 Ld) {
     int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (I >= nb) return;
@@ -164,10 +165,14 @@ __global__ void k_tiles(const float4 *__restrict__ center, const float4 *__restr
             int k = pos + __popc(m & ((1u << lane) - 1u));
             tiles[k] = make_int2(I, J);
             float4 cj = center[J];
-            float sx = -L.x * rintf((ci.x - cj.x) / L.x);
-            float sy = -L.y * rintf((ci.y - cj.y) / L.y);
-            float sz = -L.z * rintf((ci.z - cj.z) / L.z);
-            tshift[k] = make_float4(sx, sy, sz, 0.f);
+            // origin of J's image next to I, relative to I's origin: c_J - c_I + L k in FP64,
+            // split into float hi + lo (the centres are the blocks' position origins)
+            const double ox = (double)cj.x - (double)ci.x + Ld.x * rintf((ci.x - cj.x) / L.x);
+            const double oy = (double)cj.y - (double)ci.y + Ld.y * rintf((ci.y - cj.y) / L.y);
+            const double oz = (double)cj.z - (double)ci.z + Ld.z * rintf((ci.z - cj.z) / L.z);
+            const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
+            tshift[k] = make_float4(hx, hy, hz, 0.f);
+            tshift_lo[k] = make_float4((float)(ox - hx), (float)(oy - hy), (float)(oz - hz), 0.f);
         }
         pos += __popc(m);
         cnt += __popc(m);
@@ -275,7 +280,7 @@ int nb_build(ap_ctx *ctx, const double *d_xyz, const int *d_off, const int *d_at
     int *bcount = key;                 // reuse: key no longer needed
     int *boff = key + nb + 1;
     k_tiles<<<ap_grid_for((long)nb * 32, T), T, 0, s>>>(ctx->bcenter, half, nb, L, rl * rl, bcount, nullptr,
-                                                      nullptr, nullptr);
+                                                      nullptr, nullptr, nullptr, make_double3(P.box[0], P.box[1], P.box[2]));
     int *d_total = boff + nb + 1;
     k_scan_single<<<1, 1024, 0, s>>>(bcount, boff, nb, d_total);
     int ntiles = 0;
@@ -288,11 +293,14 @@ int nb_build(ap_ctx *ctx, const double *d_xyz, const int *d_off, const int *d_at
 
     if ((r = grow(ctx, &ctx->tiles, &ctx->cap_tiles, ntiles, sizeof(int2)))) return r;
     if (ctx->tshift) cudaFree(ctx->tshift);
+    if (ctx->tshift_lo) cudaFree(ctx->tshift_lo);
     if (ctx->tile_excl) cudaFree(ctx->tile_excl);
     AP_CUDA(cudaMalloc((void **)&ctx->tshift, sizeof(float4) * ctx->cap_tiles));
+    AP_CUDA(cudaMalloc((void **)&ctx->tshift_lo, sizeof(float4) * ctx->cap_tiles));
     AP_CUDA(cudaMalloc((void **)&ctx->tile_excl, sizeof(int) * ctx->cap_tiles));
     k_tiles<<<ap_grid_for((long)nb * 32, T), T, 0, s>>>(ctx->bcenter, half, nb, L, rl * rl, nullptr, boff,
-                                                      ctx->tiles, ctx->tshift);
+                                                      ctx->tiles, ctx->tshift, ctx->tshift_lo,
+                                                      make_double3(P.box[0], P.box[1], P.box[2]));
     ctx->n_tiles = ntiles;
     // keep the per-block tile offsets at the head of tmp_int for the exclusion pass
     int *tile_off = boff;

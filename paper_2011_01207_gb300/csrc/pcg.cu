@@ -445,6 +445,30 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
 
 }  // namespace
 
+// one iteration's vector work (direction, q = A p with its p.q reduction, update with its
+// r.z / z.z reduction) on `s`, for timing; it advances the last solve's state
+int pcg_vectors_launch(ap_ctx *ctx, cudaStream_t s) {
+    const int nb = ap_grid_for(ctx->n_pad, NT);
+    double *part_pq = ctx->red_part, *part_rz = ctx->red_part + nb;
+    if (ctx->prec == AP_FP64) {
+        typedef V4<double>::type T4;
+        k_direction<double><<<nb, NT, 0, s>>>(ctx->r, ctx->alpha, ctx->n_pad, (T4 *)ctx->p, ctx->st);
+        k_apply<double><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->dg, ctx->acc, (const double *)ctx->rec, ctx->n_pad,
+                                          ctx->qv, part_pq, ctx->st);
+        k_update<double><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
+                                           part_rz, ctx->n, 0, 0);
+    } else {
+        typedef V4<float>::type T4;
+        k_direction<float><<<nb, NT, 0, s>>>(ctx->r, ctx->alpha, ctx->n_pad, (T4 *)ctx->p, ctx->st);
+        k_apply<float><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->dg, ctx->acc, (const float *)ctx->rec, ctx->n_pad,
+                                         ctx->qv, part_pq, ctx->st);
+        k_update<float><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
+                                          part_rz, ctx->n, 0, 0);
+    }
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
 int pcg_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double *d_mu, ap_solve_info *info) {
     return ctx->prec == AP_FP64 ? solve_t<double>(ctx, d_guess, tol, max_iter, d_mu, info)
                                 : solve_t<float>(ctx, d_guess, tol, max_iter, d_mu, info);

@@ -69,23 +69,22 @@ struct PmeConsts {
     int n;
 };
 
+// stencil of one atom from its origin floor(u) mod K and fraction u - floor(u), u = K x / L
+// (formed in FP64 when the configuration is loaded)
 template <class T, int NDER>
-__device__ __forceinline__ void make_stencil(const PmeConsts<T> &pc, T x, T y, T z, Stencil<T> &st) {
-    T xyz[3] = {x, y, z};
+__device__ __forceinline__ void make_stencil(const PmeConsts<T> &pc, int4 ib, typename V4<T>::type w,
+                                             Stencil<T> &st) {
+    const int ibs[3] = {ib.x, ib.y, ib.z};
+    const T ws[3] = {w.x, w.y, w.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        T u = xyz[d] * pc.s[d];
-        T b = floor(u);
-        T w = u - b;
-        int K = pc.K[d];
-        int ib = (int)b % K;
-        if (ib < 0) ib += K;
+        const int K = pc.K[d];
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
-            int k = ib - t;
+            const int k = ibs[d] - t;
             st.k[d][t] = k < 0 ? k + K : k;
         }
-        bspline5<T, NDER>(w, st.th[d], st.d1[d], st.d2[d], st.d3[d]);
+        bspline5<T, NDER>(ws[d], st.th[d], st.d1[d], st.d2[d], st.d3[d]);
     }
 }
 
@@ -121,12 +120,13 @@ __global__ void k_spread_multipoles(const typename V4<T>::type *__restrict__ pos
                                     const typename V4<T>::type *__restrict__ dipd,
                                     const typename V4<T>::type *__restrict__ quad0,
                                     const typename V4<T>::type *__restrict__ quad1, T *__restrict__ grid,
-                                    PmeConsts<T> pc) {
+                                    PmeConsts<T> pc, const int4 *__restrict__ stb,
+                                    const typename V4<T>::type *__restrict__ stw) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pc.n) return;
     typename V4<T>::type a = posq[i], b = dipd[i], c = quad0[i], d = quad1[i];
     Stencil<T> st;
-    make_stencil<T, 2>(pc, a.x, a.y, a.z, st);
+    make_stencil<T, 2>(pc, stb[i], stw[i], st);
     const T sx = pc.s[0], sy = pc.s[1], sz = pc.s[2];
     const T q = a.w, dx = b.x * sx, dy = b.y * sy, dz = b.z * sz;
     const T third = T(1.0 / 3.0);
@@ -153,14 +153,14 @@ __global__ void k_spread_multipoles(const typename V4<T>::type *__restrict__ pos
 
 // spread induced dipoles p --------------------------------------------------------------
 template <class T>
-__global__ void k_spread_dipoles(const typename V4<T>::type *__restrict__ posq,
+__global__ void k_spread_dipoles(const int4 *__restrict__ stb, const typename V4<T>::type *__restrict__ stw,
                                  const typename V4<T>::type *__restrict__ pv, T *__restrict__ grid,
                                  PmeConsts<T> pc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pc.n) return;
-    typename V4<T>::type a = posq[i], b = pv[i];
+    typename V4<T>::type b = pv[i];
     Stencil<T> st;
-    make_stencil<T, 1>(pc, a.x, a.y, a.z, st);
+    make_stencil<T, 1>(pc, stb[i], stw[i], st);
     const T px = b.x * pc.s[0], py = b.y * pc.s[1], pz = b.z * pc.s[2];
     const int Kx = pc.K[0], Ky = pc.K[1];
 #pragma unroll
@@ -192,13 +192,12 @@ __global__ void k_convolve(typename FftTypes<T>::cplx *__restrict__ c, const T *
 
 // gather the field -grad(phi) at every atom ---------------------------------------------
 template <class T>
-__global__ void k_gather_field(const typename V4<T>::type *__restrict__ posq, const T *__restrict__ phi,
-                               T *__restrict__ out, int n_pad, PmeConsts<T> pc) {
+__global__ void k_gather_field(const int4 *__restrict__ stb, const typename V4<T>::type *__restrict__ stw,
+                               const T *__restrict__ phi, T *__restrict__ out, int n_pad, PmeConsts<T> pc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pc.n) return;
-    typename V4<T>::type a = posq[i];
     Stencil<T> st;
-    make_stencil<T, 1>(pc, a.x, a.y, a.z, st);
+    make_stencil<T, 1>(pc, stb[i], stw[i], st);
     const int Kx = pc.K[0], Ky = pc.K[1];
     T gx = 0, gy = 0, gz = 0;
 #pragma unroll
@@ -229,13 +228,13 @@ __global__ void k_gather_field(const typename V4<T>::type *__restrict__ posq, co
 // component order: [0] phi; [1..3] x y z; [4..9] xx yy zz xy xz yz;
 // [10..19] xxx yyy zzz xxy xxz xyy yyz xzz yzz xyz
 template <class T>
-__global__ void k_gather_derivs(const typename V4<T>::type *__restrict__ posq, const T *__restrict__ phi,
-                                double *__restrict__ out, int n_pad, int ncomp, PmeConsts<T> pc) {
+__global__ void k_gather_derivs(const int4 *__restrict__ stb, const typename V4<T>::type *__restrict__ stw,
+                                const T *__restrict__ phi, double *__restrict__ out, int n_pad, int ncomp,
+                                PmeConsts<T> pc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pc.n) return;
-    typename V4<T>::type a = posq[i];
     Stencil<T> st;
-    make_stencil<T, 3>(pc, a.x, a.y, a.z, st);
+    make_stencil<T, 3>(pc, stb[i], stw[i], st);
     const int Kx = pc.K[0], Ky = pc.K[1];
     T D[20];
 #pragma unroll
@@ -380,11 +379,11 @@ int multipole_field_t(ap_ctx *ctx, cudaStream_t s) {
     AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
     k_spread_multipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(
         (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0, (const T4 *)ctx->quad1,
-        (T *)ctx->grid, pc);
+        (T *)ctx->grid, pc, ctx->stb, (const T4 *)ctx->stw);
     AP_CUDA(cudaGetLastError());
     int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid2, s);
     if (r) return r;
-    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid2,
+    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid2,
                                                               (T *)ctx->rec, ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
@@ -395,12 +394,12 @@ int dipole_field_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
     AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
-    k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T4 *)p,
+    k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T4 *)p,
                                                                 (T *)ctx->grid, pc);
     AP_CUDA(cudaGetLastError());
     int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
     if (r) return r;
-    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid,
+    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid,
                                                               (T *)ctx->rec, ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
@@ -413,14 +412,14 @@ int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
     AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
-    k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T4 *)mu4,
+    k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T4 *)mu4,
                                                                 (T *)ctx->grid, pc);
     AP_CUDA(cudaGetLastError());
     int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
     if (r) return r;
-    k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid,
+    k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid,
                                                                gbuf, ctx->n_pad, 20, pc);
-    k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid2,
+    k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid2,
                                                                gbuf + (size_t)20 * ctx->n_pad, ctx->n_pad, 10, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
@@ -433,7 +432,7 @@ int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
     PmeConsts<T> pc = pme_consts<T>(ctx);
     switch (stage) {
     case 0:
-        k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->p,
+        k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T4 *)ctx->p,
                                                                     (T *)ctx->grid, pc);
         break;
     case 1:
@@ -441,13 +440,13 @@ int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
                                                                          ctx->ncgrid);
         break;
     case 2:
-        k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>((const T4 *)ctx->posq, (const T *)ctx->grid,
+        k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid,
                                                                   (T *)ctx->rec, ctx->n_pad, pc);
         break;
     case 3:
         k_spread_multipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(
             (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0, (const T4 *)ctx->quad1,
-            (T *)ctx->grid, pc);
+            (T *)ctx->grid, pc, ctx->stb, (const T4 *)ctx->stw);
         break;
     default:
         return ap_fail(ctx, AP_ERR_ARG, "unknown PME stage");
