@@ -138,7 +138,7 @@ class Clocks:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -239,14 +239,29 @@ def run_ours(args):
     mu0 = torch.zeros((s.n, 3), dtype=torch.float64, device=dev)
     del feat, tgt
 
+    hist = []   # converged dipoles of the two previous steps (extrapolated guess)
+
     def step(k, xyz, use_learned):
+        """use_learned: True (MLP), False (alpha E), "zero" or "extrapolated" (2 mu_{t-1} -
+        mu_{t-2}, alpha E until two previous steps exist)."""
         if k % REBUILD == 0:
             binding.build_neighbour_blocks(ctx.ctx, xyz, ctx.excl_off, ctx.excl_atoms, ctx.n_excl)
         binding.permanent_field(ctx.ctx, xyz, ctx.mpole, ctx.frame, ctx.alpha, None)
-        if use_learned:
+        guess = None
+        if use_learned is True:
             binding.ap_learned_guess(ctx.ctx, trainer.packed, mu0)
-        binding.induced_dipoles_pcg(ctx.ctx, mu0 if use_learned else None, TOL, 200, ctx.mu, want_info=False)
+            guess = mu0
+        elif use_learned == "zero":
+            mu0.zero_()
+            guess = mu0
+        elif use_learned == "extrapolated" and len(hist) == 2:
+            torch.sub(hist[1] * 2.0, hist[0], out=mu0)
+            guess = mu0
+        binding.induced_dipoles_pcg(ctx.ctx, guess, TOL, 200, ctx.mu, want_info=False)
         binding.polarization_energy_forces(ctx.ctx, ctx.mu, ctx.energy, ctx.forces)
+        if use_learned == "extrapolated":
+            hist.append(ctx.mu.clone())
+            del hist[:-2]
 
     def timed(use_learned, tag):
         it_, ts = [], []
@@ -275,6 +290,9 @@ def run_ours(args):
     times, iters = timed(True, "timed_steps")
     t_wall = time.perf_counter() - t_wall
     times_plain, iters_plain = timed(False, "timed_steps_plain")
+    times_zero, iters_zero = timed("zero", "timed_steps_zero")
+    hist.clear()
+    times_ext, iters_ext = timed("extrapolated", "timed_steps_extrapolated")
     clk = clocks.stop()
     ms = float(np.mean(times))
     ms_plain = float(np.mean(times_plain))
@@ -346,6 +364,13 @@ def run_ours(args):
                    "pcg_iters_mean": it_mean, "pcg_iters": [int(min(iters)), int(max(iters))],
                    "plain_guess": {"ms_per_step": round(ms_plain, 4), "pcg_iters_mean": float(np.mean(iters_plain)),
                                    "guess": "alpha*E"},
+                   "other_guesses": {
+                       "zero": {"ms_per_step": round(float(np.mean(times_zero)), 4),
+                                "pcg_iters_mean": float(np.mean(iters_zero))},
+                       "extrapolated": {"ms_per_step": round(float(np.mean(times_ext)), 4),
+                                        "pcg_iters_mean": float(np.mean(iters_ext)),
+                                        "guess": "2 mu(t-1) - mu(t-2) from the previous steps' solves "
+                                                 "(torch elementwise op inside the timed step)"}},
                    "learned_training": {"pairs": int(TRAIN_CONFIGS * s.n), "adam_steps": TRAIN_STEPS,
                                         "batch": TRAIN_BATCH, "loss_first": round(float(tr_loss[0]), 5),
                                         "loss_last": round(float(np.mean(tr_loss[-20:])), 5),
@@ -592,6 +617,68 @@ def run_reference(args):
     }))
 
 
+def run_precision(args):
+    """Error of every output against the FP64 oracle, in FP64 and in the mixed precision the
+    benchmark runs: 648-atom water box (full), 23,558-atom solvated chain (full) and the
+    96,000-atom box (200 sampled rows). Dipoles are solved to the stated tolerance and
+    compared with the oracle's solution at 1e-10 D; energy and forces both at the GPU's own
+    dipoles (what a user gets) and at the oracle's dipoles (the kernels alone)."""
+    import torch
+    from paper_2011_01207_gb300 import binding, build as _build, synth
+    from oracle import Oracle, Params, model
+    _build.build_library()
+    debye = 4.80321
+
+    def rel_rms(a, b):
+        return float(np.sqrt(np.mean((a - b) ** 2) / np.mean(b ** 2)))
+
+    cases = [("water_648_atoms_18.64A_grid24", lambda: synth.water_box(216, 18.64, 1001), (24, 24, 24), 1e-6,
+              [("fp64", binding.AP_FP64), ("mixed", binding.AP_MIXED)]),
+             ("chain_23558_atoms_62.2A_grid64", lambda: synth.solvated_chain(2489, 7023, 62.2, 1003), (64, 64, 64), 1e-5,
+              [("mixed", binding.AP_MIXED)])]
+    out = {}
+    for name, make, grid, tol, precs in cases:
+        s = make()
+        o = Oracle(s, Params(beta=BETA, grid=grid, cutoff=CUTOFF))
+        E_o = o.permanent_field()
+        mu_star, _ = o.pcg(E_o, tol=1e-10)
+        e_star, F_star = o.energy(mu_star, E_o), o.forces(mu_star)
+        for tag, prec in precs:
+            c = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=grid, precision=prec)
+            c.build()
+            c.permanent_field()
+            info = c.solve(tol=tol, max_iter=200)
+            mu = c.mu.cpu().numpy()
+            dmu = debye * np.linalg.norm(mu - mu_star, axis=1)
+            e, f = c.energy_forces(c.mu)
+            e_own, f_own = float(e.cpu()[0]), f.cpu().numpy()
+            e, f = c.energy_forces(torch.tensor(mu_star, device=c.mu.device))
+            e_fix, f_fix = float(e.cpu()[0]), f.cpu().numpy()
+            out[f"{name}/{tag}"] = {
+                "atoms": s.n, "pcg_tol_debye": tol, "iterations": info.iterations,
+                "field_rel_rms": rel_rms(c.field.cpu().numpy(), E_o),
+                "dipole_rms_debye": float(np.sqrt(np.mean(dmu ** 2))), "dipole_max_debye": float(dmu.max()),
+                "true_residual_debye": float(o.residual_eps(E_o - o.apply_A(mu))),
+                "energy_rel": abs(e_own - e_star) / abs(e_star), "energy_rel_same_dipoles": abs(e_fix - e_star) / abs(e_star),
+                "forces_rel_rms": rel_rms(f_own, F_star), "forces_rel_rms_same_dipoles": rel_rms(f_fix, F_star)}
+            c.close()
+    s = make_system()
+    c = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=GRID, precision=binding.AP_MIXED)
+    c.build()
+    c.permanent_field()
+    info = c.solve(tol=TOL, max_iter=200)
+    rows = np.random.default_rng(9).choice(s.n, 200, replace=False)
+    mu = c.mu.cpu().numpy()
+    E_r, Tmu = model.row_fields(s, Params(beta=BETA, grid=GRID, cutoff=CUTOFF), rows, mu)
+    resid = E_r - (mu[rows] / s.alpha[rows, None] - Tmu)
+    out["water_96000_atoms_98.7A_grid100/mixed (200 sampled rows)"] = {
+        "atoms": s.n, "pcg_tol_debye": TOL, "iterations": info.iterations,
+        "field_rel_rms": rel_rms(c.field.cpu().numpy()[rows], E_r),
+        "true_residual_debye": float(debye * np.sqrt(np.mean(np.sum((s.alpha[rows, None] * resid) ** 2, axis=1))))}
+    c.close()
+    print(json.dumps({"metric": "errors against the FP64 oracle", "impl": "ours", "cases": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -599,8 +686,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
-    ap.add_argument("--workload", default="water96k", choices=["water96k", "replicas64"],
-                    help="water96k: the 96,000-atom box (default); replicas64: 64 uneven replicas in one graph")
+    ap.add_argument("--workload", default="water96k", choices=["water96k", "replicas64", "precision"],
+                    help="water96k: the 96,000-atom box (default); replicas64: 64 uneven replicas in one graph; "
+                         "precision: errors of every output against the FP64 oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -608,6 +696,8 @@ def main():
         run_reference(args)
     elif args.workload == "replicas64":
         run_replicas(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 
