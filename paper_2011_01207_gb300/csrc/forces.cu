@@ -49,7 +49,7 @@ __device__ __forceinline__ void mu_dot_field_grad(T q, const T *d, const T *Q /*
     for (int a = 0; a < 3; ++a) out[a] = cR * R[a] + cmu * mu[a] + cd * d[a] + cQm * Qm[a] + cQR * QR[a];
 }
 
-// One warp per work item, pair-side queue as in the real-space field kernels: every
+// One warp per work item, pair sides walked in place as in the real-space field kernels: every
 // in-range pair gives the side (target t, source s) for both atoms, and with
 // R = x_t - x_s the same expressions give t's force and t's dU/dd, dU/dQ. Per side the
 // kernel accumulates, without the constant factors,
@@ -67,7 +67,8 @@ struct FoSmem {
     T qb[2][64];                    // Qyz, Qzz
     T acc[12][64];                  // per-target sums of the item
     unsigned ex[32];                // exclusion words: lane i, bit j
-    unsigned short queue[2048];
+    unsigned words[64];             // pair bits: rows of the i atoms, then columns of the j atoms
+    int pre[64];                    // inclusive prefix counts of the words' bits
 };
 
 template <class T>
@@ -156,11 +157,11 @@ __global__ void __launch_bounds__(128) k_pair_forces(
             S.acc[k][lane] = T(0);
             S.acc[k][32 + lane] = T(0);
         }
-        const int total = build_side_queue(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
-                                           S.queue);
+        const int total = side_words(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
+                                     S.words, S.pre);
         __syncwarp();
-        const int per = (total + 31) >> 5;
-        const int e0 = lane * per, e1 = min(total, e0 + per);
+        SideSlice slice;
+        slice.begin(S.words, S.pre, total, lane);
         int cur = -1;
         T4 self, sm, sa, smu;
         T syz = 0, szz = 0;
@@ -169,9 +170,10 @@ __global__ void __launch_bounds__(128) k_pair_forces(
         T f[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) f[k] = T(0);
-        for (int e = e0; e < e1; ++e) {
-            const int q = S.queue[e];
-            const int tg = q >> 5, sl = q & 31;
+        while (slice.left > 0) {
+            int tg, src;
+            slice.next(S.words, tg, src);
+            const int sl = src & 31;   // the source's lane within its half
             if (tg != cur) {
                 if (cur >= 0) {
 #pragma unroll
@@ -187,7 +189,6 @@ __global__ void __launch_bounds__(128) k_pair_forces(
                 syz = S.qb[0][tg];
                 szz = S.qb[1][tg];
             }
-            const int src = tg < 32 ? 32 + sl : sl;
             const bool exb = tg < 32 ? (S.ex[tg] >> sl) & 1u : (S.ex[sl] >> (tg - 32)) & 1u;
             const T4 o = S.pos[src], om = S.qd[src], oa = S.qa[src], ou = S.mu[src];
             const T oyz = S.qb[0][src], ozz = S.qb[1][src];

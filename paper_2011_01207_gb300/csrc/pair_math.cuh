@@ -68,32 +68,56 @@ __device__ __forceinline__ void thole_oml(T s, T *oml) {
     if (NMAX > 3) oml[3] = (T(1) + s + s * s * (T(18.0 / 35.0) + T(9.0 / 35.0) * s)) * e;
 }
 
-// Pair-side queue of one 32 x 32 work item (one warp). `row` is lane i's word of in-range
-// bits over the item's j atoms, `col` lane j's word over the i atoms (the transpose). Each
-// in-range pair gives two sides, written as (target << 5) | source-lane and sorted by target:
-// the row sides (target i, source j) first, then the column sides (target 32 + j, source i).
-// Returns the number of entries (at most 2048); every lane gets the same value.
-__device__ __forceinline__ int build_side_queue(unsigned row, unsigned col, int lane, unsigned short *queue) {
-    const int nr = __popc(row), nc = __popc(col);
-    int ir = nr, ic = nc;
+// Pair sides of one 32 x 32 work item, walked in place (one warp). Word w < 32 is row i = w
+// (bits: the item's j atoms in range of i), word 32 + j the column of j (bits: the i atoms);
+// the target of a side in word w is atom w of the item's 64 (i atoms first) and its source
+// atom b + 32 or b for bit b of a row or column word. In word order the sides are sorted by
+// target. SideSlice::begin() places lane `lane` at the start of its equal contiguous share
+// of the `total` sides; next() then yields them one by one.
+struct SideSlice {
+    int w;         // current word
+    unsigned m;    // its bits not yet taken
+    int left;      // sides left in this lane's share
+
+    // words[64] and pre[64] (inclusive prefix counts of the words' bits) in shared memory
+    __device__ __forceinline__ void begin(const unsigned *words, const int *pre, int total, int lane) {
+        const int per = (total + 31) >> 5;
+        const int e0 = min(total, lane * per);
+        left = min(total, e0 + per) - e0;
+        // first word whose inclusive prefix exceeds e0
+        int lo = 0, hi = 63;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (pre[mid] > e0) hi = mid; else lo = mid + 1;
+        }
+        w = lo;
+        int k = e0 - (w ? pre[w - 1] : 0);   // sides of word w before e0
+        m = left > 0 ? words[w] : 0u;
+        for (; k > 0; --k) m &= m - 1u;
+    }
+    // next side: target word, source bit; advances over empty words
+    __device__ __forceinline__ void next(const unsigned *words, int &target, int &source) {
+        while (m == 0u) m = words[++w];
+        const int b = __ffs(m) - 1;
+        m &= m - 1u;
+        --left;
+        target = w;
+        source = w < 32 ? b + 32 : b;
+    }
+};
+
+// words[lane] = row, words[32 + lane] = col; pre = inclusive prefix counts; returns the total
+__device__ __forceinline__ int side_words(unsigned row, unsigned col, int lane, unsigned *words, int *pre) {
+    int ir = __popc(row), ic = __popc(col);
     for (int off = 1; off < 32; off <<= 1) {
         const int vr = __shfl_up_sync(0xffffffffu, ir, off);
         const int vc = __shfl_up_sync(0xffffffffu, ic, off);
         if (lane >= off) { ir += vr; ic += vc; }
     }
     const int prow = __shfl_sync(0xffffffffu, ir, 31);
-    const int total = prow + __shfl_sync(0xffffffffu, ic, 31);
-    int pos = ir - nr;
-    while (row) {
-        const int b = __ffs(row) - 1;
-        row &= row - 1u;
-        queue[pos++] = (unsigned short)((lane << 5) | b);
-    }
-    pos = prow + ic - nc;
-    while (col) {
-        const int b = __ffs(col) - 1;
-        col &= col - 1u;
-        queue[pos++] = (unsigned short)(((32 + lane) << 5) | b);
-    }
-    return total;
+    words[lane] = row;
+    words[32 + lane] = col;
+    pre[lane] = ir;
+    pre[32 + lane] = prow + ic;
+    return prow + __shfl_sync(0xffffffffu, ic, 31);
 }

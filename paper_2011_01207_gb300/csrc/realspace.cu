@@ -5,9 +5,10 @@
 // A work item is block I against one filtered 32-atom chunk of its partner blocks (or
 // against itself). The in-range pairs of every item are known as 32-bit masks (row and
 // transposed) from the per-configuration filter. A warp stages the item's 64 atoms in
-// shared memory and turns the masks into a queue of pair sides (target, source) sorted by
-// target; each lane then takes an equal contiguous slice, so no lane evaluates an
-// out-of-range pair and the work per lane is even whatever the pair distribution. Pair
+// shared memory; the masks' bits are its pair sides (target, source), which in word order
+// are sorted by target; each lane walks an equal contiguous share of them in place, so no
+// lane evaluates an out-of-range pair and the work per lane is even whatever the pair
+// distribution. Pair
 // arithmetic is in T (FP32 in the mixed mode); sums per target are kept in T within an
 // item (registers, then a shared per-target slot), and in FP64 across items: block I's in
 // registers while consecutive items share I, the chunk atoms' with FP64 atomics.
@@ -49,7 +50,7 @@ __device__ __forceinline__ void flush3(double *acc, int n_pad, int slot, double 
 
 // ---------------------------------------------------------------------------------------
 // a2: permanent multipole field, E_i += E(R; q_j, d_j, Q_j) and E_j += E(-R; q_i, d_i, Q_i).
-// Same pair-side queue as the matvec below: every in-range pair gives the side "field at
+// Same pair sides as the matvec below: every in-range pair gives the side "field at
 // the target from the source's multipole" for both atoms, and with R = x_target - x_source
 // one expression serves both sides. The exclusion bit of the pair (sigma = 0 in R_n) is
 // looked up in the item's 32-word mask.
@@ -61,7 +62,8 @@ struct PfSmem {
     T qb[2][64];                    // Qyz, Qzz
     T acc[3][64];                   // per-target sums of the item
     unsigned ex[32];                // exclusion words: lane i, bit j
-    unsigned short queue[2048];
+    unsigned words[64];             // pair bits: rows of the i atoms, then columns of the j atoms
+    int pre[64];                    // inclusive prefix counts of the words' bits
 };
 
 template <class T>
@@ -138,18 +140,19 @@ __global__ void __launch_bounds__(128) k_perm_field(
             S.acc[c][lane] = T(0);
             S.acc[c][32 + lane] = T(0);
         }
-        const int total = build_side_queue(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
-                                           S.queue);
+        const int total = side_words(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
+                                     S.words, S.pre);
         __syncwarp();
-        const int per = (total + 31) >> 5;
-        const int e0 = lane * per, e1 = min(total, e0 + per);
+        SideSlice slice;
+        slice.begin(S.words, S.pre, total, lane);
         int cur = -1;
         T4 self;
         self.x = self.y = self.z = self.w = T(0);
         T f0 = 0, f1 = 0, f2 = 0;
-        for (int e = e0; e < e1; ++e) {
-            const int q = S.queue[e];
-            const int tg = q >> 5, sl = q & 31;
+        while (slice.left > 0) {
+            int tg, src;
+            slice.next(S.words, tg, src);
+            const int sl = src & 31;   // the source's lane within its half
             if (tg != cur) {
                 if (cur >= 0) {
                     atomicAdd(&S.acc[0][cur], f0);
@@ -160,7 +163,6 @@ __global__ void __launch_bounds__(128) k_perm_field(
                 cur = tg;
                 self = S.pos[tg];
             }
-            const int src = tg < 32 ? 32 + sl : sl;
             const bool exb = tg < 32 ? (S.ex[tg] >> sl) & 1u : (S.ex[sl] >> (tg - 32)) & 1u;
             const T4 o = S.pos[src], m = S.qd[src], qa = S.qa[src];
             const T qyz = S.qb[0][src], qzz = S.qb[1][src];
@@ -211,10 +213,10 @@ __global__ void __launch_bounds__(128) k_perm_field(
 // a5: dipole-field matrix-vector product, E_i += -R1 p_j + R2 (p_j.R) R (and i <-> j).
 // Positions are fixed during a solve, so the in-range pairs of every work item and their
 // transposed bit matrix were found once per configuration. Per item, a warp stages the
-// 32 i-atoms and 32 j-atoms in shared memory and writes a queue of "pair sides"
-// (target atom, source atom): the row bits give the field at each i-atom, the column bits
-// the field at each j-atom. The queue is sorted by target, and each lane takes an equal
-// contiguous slice of it, accumulating in registers while the target stays the same and
+// 32 i-atoms and 32 j-atoms in shared memory; the "pair sides" (target atom, source atom)
+// are the row bits (field at each i-atom) and the column bits (field at each j-atom). In
+// word order they are sorted by target, and each lane walks an equal contiguous share of
+// them in place (SideSlice), accumulating in registers while the target stays the same and
 // adding to a shared per-target sum only when it changes (a few times per lane per item).
 // So every lane evaluates one in-range pair side per step, whatever the pair distribution;
 // the field expression is even in R, so one code path serves both sides.
@@ -223,7 +225,8 @@ struct MvSmem {
     typename V4<T>::type pos[64];    // x, y, z, Thole factor: [0,32) block I, [32,64) the item's j atoms
     typename V4<T>::type p[64];      // dipoles of the same atoms
     T acc[3][64];                    // per-target sums of the item
-    unsigned short queue[2048];      // (target << 5) | source-lane, sorted by target
+    unsigned words[64];              // pair bits: rows of the i atoms, then columns of the j atoms
+    int pre[64];                     // inclusive prefix counts of the words' bits
 };
 
 template <class T, bool MINIMG, bool SHORT = false>
@@ -273,18 +276,18 @@ __global__ void __launch_bounds__(128) k_matvec(
             S.acc[c][32 + lane] = T(0);
         }
         const int total =
-            SHORT ? build_side_queue(wa.smask[(size_t)t * 32 + lane], wa.smask_t[(size_t)t * 32 + lane], lane, S.queue)
-                  : build_side_queue(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane, S.queue);
+            SHORT ? side_words(wa.smask[(size_t)t * 32 + lane], wa.smask_t[(size_t)t * 32 + lane], lane, S.words, S.pre)
+                  : side_words(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane, S.words, S.pre);
         __syncwarp();
-        const int per = (total + 31) >> 5;
-        const int e0 = lane * per, e1 = min(total, e0 + per);
+        SideSlice sl;
+        sl.begin(S.words, S.pre, total, lane);
         int cur = -1;
         T4 self;
         self.x = self.y = self.z = self.w = T(0);
         T f0 = 0, f1 = 0, f2 = 0;
-        for (int e = e0; e < e1; ++e) {
-            const int q = S.queue[e];
-            const int tg = q >> 5;
+        while (sl.left > 0) {
+            int tg, src;
+            sl.next(S.words, tg, src);
             if (tg != cur) {
                 if (cur >= 0) {
                     atomicAdd(&S.acc[0][cur], f0);
@@ -295,7 +298,6 @@ __global__ void __launch_bounds__(128) k_matvec(
                 cur = tg;
                 self = S.pos[tg];
             }
-            const int src = (q & 31) + (tg < 32 ? 32 : 0);   // a row side's source is a j atom
             const T4 other = S.pos[src], po = S.p[src];
             T dx, dy, dz;
             pair_vector<T, MINIMG>(pc, self.x, self.y, self.z, other.x, other.y, other.z, T(0), T(0), T(0), dx, dy, dz);
