@@ -90,7 +90,7 @@ int ap_batch_capture(ap_batch *b, const ap_batch_step *steps) {
         return rc;
     }
     if (e != cudaSuccess) return ap_fail(nullptr, AP_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&b->exec, g, 0);
+    e = cudaGraphInstantiate(&b->exec, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return ap_fail(nullptr, AP_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
     return AP_OK;

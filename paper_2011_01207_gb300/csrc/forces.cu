@@ -459,12 +459,17 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
     AP_CUDA(cudaMemsetAsync(ctx->red + 8, 0, sizeof(double), s));
     // energy
     k_energy<<<ap_grid_for(n_pad, 256), 256, 0, s>>>(ctx->mu_s, ctx->E, n_pad, -0.5 * f, ctx->red + 8);
-    // real space
-    int rc = pair_forces_t<T>(ctx, s);
+    // reciprocal-space potential derivatives on the second stream, concurrent with the
+    // real-space pair forces (they write only gbuf and the grid); joined before the kernels
+    // that update the force arrays per atom
+    AP_CUDA(cudaEventRecord(ctx->ev_fork, s));
+    AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
+    int rc = pme_forces_derivs(ctx, ctx->p, ctx->gbuf, ctx->s1);
     if (rc) return rc;
-    // reciprocal space
-    rc = pme_forces_derivs(ctx, ctx->p, ctx->gbuf, s);
+    rc = pair_forces_t<T>(ctx, s);
     if (rc) return rc;
+    AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));
+    AP_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     k_recip_forces<T><<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gbuf, ctx->mu_s, (const T4 *)ctx->posq,
                                                          (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
                                                          (const T4 *)ctx->quad1, n, n_pad, f, self_coef, ctx->frc,

@@ -349,7 +349,7 @@ int build_graph(ap_ctx *ctx) {
         return AP_OK;      // fall back to the host loop
     }
     cudaGraphExec_t ex = nullptr;
-    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    if (cudaGraphInstantiate(&ex, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
         cudaGetLastError();
         cudaGraphDestroy(g);
         return AP_OK;
