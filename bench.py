@@ -241,7 +241,7 @@ def run_ours(args):
 
     hist = []   # converged dipoles of the two previous steps (extrapolated guess)
 
-    def step(k, xyz, use_learned):
+    def step(k, xyz, use_learned, ctx=ctx):
         """use_learned: True (MLP), False (alpha E), "zero" or "extrapolated" (2 mu_{t-1} -
         mu_{t-2}, alpha E until two previous steps exist)."""
         if k % REBUILD == 0:
@@ -263,10 +263,10 @@ def run_ours(args):
             hist.append(ctx.mu.clone())
             del hist[:-2]
 
-    def timed(use_learned, tag):
+    def timed(use_learned, tag, c=ctx):
         it_, ts = [], []
         for k in range(args.warmup):
-            step(k, pos[k], use_learned)
+            step(k, pos[k], use_learned, c)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -275,11 +275,11 @@ def run_ours(args):
             flush.fill_(k & 0xff)                                    # untimed: evict the L2
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(k, pos[k], use_learned)
+            step(k, pos[k], use_learned, c)
             b.record(stream)
             b.synchronize()
             ts.append(a.elapsed_time(b))
-            it_.append(binding.ap_solve_info_last(ctx.ctx).iterations)
+            it_.append(binding.ap_solve_info_last(c.ctx).iterations)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         return ts, it_
@@ -293,6 +293,13 @@ def run_ours(args):
     times_zero, iters_zero = timed("zero", "timed_steps_zero")
     hist.clear()
     times_ext, iters_ext = timed("extrapolated", "timed_steps_extrapolated")
+    # the same steps in the fixed-point accumulation mode (AP_FIXED), learned guess
+    ctx_fx = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=GRID, precision=binding.AP_FIXED,
+                             device=dev)
+    times_fx, iters_fx = timed(True, "timed_steps_fixed", ctx_fx)
+    kern_fx = {k: round(binding.ap_time_kernel(ctx_fx.ctx, k, 20), 4) for k in
+               ("real_matvec", "spread_dipoles", "real_field", "pair_forces", "spread_multipoles")}
+    ctx_fx.close()
     clk = clocks.stop()
     ms = float(np.mean(times))
     ms_plain = float(np.mean(times_plain))
@@ -364,6 +371,10 @@ def run_ours(args):
                    "pcg_iters_mean": it_mean, "pcg_iters": [int(min(iters)), int(max(iters))],
                    "plain_guess": {"ms_per_step": round(ms_plain, 4), "pcg_iters_mean": float(np.mean(iters_plain)),
                                    "guess": "alpha*E"},
+                   "fixed_point": {"ms_per_step": round(float(np.mean(times_fx)), 4),
+                                   "pcg_iters_mean": float(np.mean(iters_fx)), "guess": "learned",
+                                   "accumulation": "64-bit fixed point (AP_FIXED), bitwise reproducible",
+                                   "kernel_ms": kern_fx},
                    "other_guesses": {
                        "zero": {"ms_per_step": round(float(np.mean(times_zero)), 4),
                                 "pcg_iters_mean": float(np.mean(iters_zero))},
@@ -633,9 +644,9 @@ def run_precision(args):
         return float(np.sqrt(np.mean((a - b) ** 2) / np.mean(b ** 2)))
 
     cases = [("water_648_atoms_18.64A_grid24", lambda: synth.water_box(216, 18.64, 1001), (24, 24, 24), 1e-6,
-              [("fp64", binding.AP_FP64), ("mixed", binding.AP_MIXED)]),
+              [("fp64", binding.AP_FP64), ("mixed", binding.AP_MIXED), ("fixed", binding.AP_FIXED)]),
              ("chain_23558_atoms_62.2A_grid64", lambda: synth.solvated_chain(2489, 7023, 62.2, 1003), (64, 64, 64), 1e-5,
-              [("mixed", binding.AP_MIXED)])]
+              [("mixed", binding.AP_MIXED), ("fixed", binding.AP_FIXED)])]
     out = {}
     for name, make, grid, tol, precs in cases:
         s = make()

@@ -41,6 +41,12 @@ extern "C" {
 
 #define AP_MIXED  0   /* FP32 pair/PME arithmetic, FP64 accumulation and PCG reductions */
 #define AP_FP64   1   /* FP64 everywhere (reference-grade, slow on GB300) */
+#define AP_FIXED  2   /* FP32 pair/PME arithmetic as AP_MIXED, but fields, forces, torque terms and
+                         the PME grid are accumulated in 64-bit fixed point (34 fractional bits;
+                         the energy 30), as the paper's fixed-point mode (Sec. 2.4): integer sums
+                         do not depend on the order of the additions, so every output is bitwise
+                         reproducible from run to run and for any launch shape. Magnitudes must
+                         stay below 2^29 in the units of the output (kcal/mol/A, e/A^2). */
 
 #define AP_FRAME_NONE      0   /* multipoles given in the global frame */
 #define AP_FRAME_Z_THEN_X  1   /* z toward the z-atom, x from the x-atom orthogonalised */
@@ -57,7 +63,7 @@ typedef struct {
     int    grid[3];       /* PME grid K_x, K_y, K_z (even, >= 2*pme_order) */
     int    pme_order;     /* B-spline order; must be 5 (the paper's default, Sec. 1.2.2) */
     double thole_a;       /* Thole damping parameter a (AMOEBA: 0.39) */
-    int    precision;     /* AP_MIXED or AP_FP64 */
+    int    precision;     /* AP_MIXED, AP_FP64 or AP_FIXED */
 } ap_params;
 
 typedef struct {

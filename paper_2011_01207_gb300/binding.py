@@ -14,7 +14,7 @@ import numpy as np
 from .build import LIB
 
 AP_OK, AP_NOT_CONVERGED = 0, 1
-AP_MIXED, AP_FP64 = 0, 1
+AP_MIXED, AP_FP64, AP_FIXED = 0, 1, 2
 _ERRORS = {-1: "AP_ERR_ARG", -2: "AP_ERR_CUDA", -3: "AP_ERR_CAPACITY", -4: "AP_ERR_NONFINITE",
            -5: "AP_ERR_TIMEOUT", -6: "AP_ERR_STATE"}
 

@@ -33,7 +33,7 @@ void free_all(ap_ctx *c) {
                     c->grid, c->cgrid, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf,
                     c->tile_off, c->chunk_j, c->chunk_pos, c->chunk_src, c->chunk_mask, c->chunk_flag, c->nchunk,
                     c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y, c->smask, c->smask_t, c->e1s,
-                    c->dg, c->stb, c->stw};
+                    c->dg, c->stb, c->stw, c->grid_fx};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -49,7 +49,8 @@ void free_all(ap_ctx *c) {
 
 int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
     ctx->prm = *P;
-    ctx->prec = P->precision;
+    ctx->fixed = P->precision == AP_FIXED ? 1 : 0;
+    ctx->prec = ctx->fixed ? AP_MIXED : P->precision;   // the arithmetic of AP_FIXED is the mixed mode's
     ctx->n = P->n_atoms;
     ctx->n_blocks = (P->n_atoms + 31) / 32;
     ctx->n_pad = ctx->n_blocks * 32;
@@ -127,7 +128,8 @@ int ap_create(ap_ctx **out, const ap_params *P, void *stream) {
     *out = nullptr;
     if (!P) return ap_fail(nullptr, AP_ERR_ARG, "params is NULL");
     if (P->n_atoms <= 0) return ap_fail(nullptr, AP_ERR_ARG, "n_atoms must be > 0");
-    if (P->precision != AP_MIXED && P->precision != AP_FP64) return ap_fail(nullptr, AP_ERR_ARG, "unknown precision");
+    if (P->precision != AP_MIXED && P->precision != AP_FP64 && P->precision != AP_FIXED)
+        return ap_fail(nullptr, AP_ERR_ARG, "unknown precision");
     if (P->pme_order != 5) return ap_fail(nullptr, AP_ERR_ARG, "pme_order must be 5");
     if (!(P->cutoff > 0) || !(P->buffer >= 0) || !(P->ewald_beta > 0) || !(P->thole_a >= 0))
         return ap_fail(nullptr, AP_ERR_ARG, "cutoff, buffer, ewald_beta and thole_a must be positive");

@@ -50,9 +50,22 @@ struct PcgState {
     int guard;         // iterations started by the graph loop (hard bound on the WHILE node)
 };
 
+// 64-bit fixed point (two's complement in unsigned long long so that atomicAdd applies):
+// fields, forces and torque terms with 34 fractional bits, the energy with 30 (paper Sec. 2.4)
+#define AP_FX_BITS 34
+#define AP_FX_EBITS 30
+__host__ __device__ __forceinline__ long long ap_to_fx(double v) { return llrint(v * 17179869184.0); }   // 2^34
+__device__ __forceinline__ long long ap_to_fx(float v) { return llrintf(v * 17179869184.0f); }
+__host__ __device__ __forceinline__ double ap_from_fx(long long a) { return (double)a * (1.0 / 17179869184.0); }
+// value k of an accumulator array that holds FP64 numbers or (fixed != 0) fixed-point integers
+__device__ __forceinline__ double acc_value(const double *acc, size_t k, int fixed) {
+    return fixed ? ap_from_fx(reinterpret_cast<const long long *>(acc)[k]) : acc[k];
+}
+
 struct ap_ctx {
     ap_params prm;
-    int prec = AP_MIXED;
+    int prec = AP_MIXED;      // arithmetic: AP_MIXED (FP32 pairs/PME) or AP_FP64
+    int fixed = 0;            // 1: 64-bit fixed-point accumulation (AP_FIXED)
     int n = 0, n_pad = 0, n_blocks = 0;
     cudaStream_t s0 = nullptr;          // caller's stream
     cudaStream_t s1 = nullptr;          // internal stream (reciprocal branch)
@@ -130,6 +143,7 @@ struct ap_ctx {
     void *cgrid = nullptr;    // complex [Kz][Ky][Kx/2+1]
     void *green = nullptr;    // T [Kz][Ky][Kx/2+1]  B(m) C(m)
     void *grid2 = nullptr;    // second real grid (potential of the permanent multipoles, kept for forces)
+    long long *grid_fx = nullptr;   // AP_FIXED: the spread's fixed-point grid (kept cleared)
     cufftHandle plan_r2c = 0, plan_c2r = 0;
 
     // forces

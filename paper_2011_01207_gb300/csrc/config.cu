@@ -155,7 +155,7 @@ __global__ void k_pad(int n, int n_pad, typename V4<T>::type *posq, typename V4<
 template <class T>
 __global__ void k_field_finish(const double *__restrict__ acc, const T *__restrict__ rec,
                                const typename V4<T>::type *__restrict__ dipd, double self_coef, int n, int n_pad,
-                               double *__restrict__ E, const int *__restrict__ iperm, double *__restrict__ out) {
+                               double *__restrict__ E, const int *__restrict__ iperm, double *__restrict__ out, int fixed) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_pad) return;
     if (s >= n) {
@@ -164,7 +164,8 @@ __global__ void k_field_finish(const double *__restrict__ acc, const T *__restri
     }
     typename V4<T>::type d = dipd[s];
     double dd[3] = {(double)d.x, (double)d.y, (double)d.z};
-    for (int c = 0; c < 3; ++c) E[c * n_pad + s] = acc[c * n_pad + s] + (double)rec[c * n_pad + s] + self_coef * dd[c];
+    for (int c = 0; c < 3; ++c)
+        E[c * n_pad + s] = acc_value(acc, (size_t)c * n_pad + s, fixed) + (double)rec[c * n_pad + s] + self_coef * dd[c];
 }
 
 __global__ void k_unsort3(const double *__restrict__ src, int n_pad, const int *__restrict__ iperm, int n,
@@ -202,7 +203,8 @@ int finish_t(ap_ctx *ctx, double *out) {
     typedef typename V4<T>::type T4;
     double self_coef = 4.0 * std::pow(ctx->prm.ewald_beta, 3) / (3.0 * AP_SQRT_PI);
     k_field_finish<T><<<ap_grid_for(ctx->n_pad, 256), 256, 0, ctx->s0>>>(
-        ctx->acc, (const T *)ctx->rec, (const T4 *)ctx->dipd, self_coef, ctx->n, ctx->n_pad, ctx->E, ctx->iperm, out);
+        ctx->acc, (const T *)ctx->rec, (const T4 *)ctx->dipd, self_coef, ctx->n, ctx->n_pad, ctx->E, ctx->iperm, out,
+        ctx->fixed);
     if (out) k_unsort3<<<ap_grid_for(ctx->n, 256), 256, 0, ctx->s0>>>(ctx->E, ctx->n_pad, ctx->iperm, ctx->n, out);
     AP_CUDA(cudaGetLastError());
     return AP_OK;

@@ -14,16 +14,33 @@
 #include "pair_math.cuh"
 
 #include <cmath>
+#include <type_traits>
 
 void unsort3(ap_ctx *ctx, const double *src, double *out, cudaStream_t s);
 int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s);
 
 namespace {
 
-__device__ __forceinline__ void flush12(double *frc, double *gdip, double *gquad, int n_pad, int s, const double *a) {
-    for (int c = 0; c < 3; ++c) atomicAdd(frc + c * n_pad + s, a[c]);
-    for (int c = 0; c < 3; ++c) atomicAdd(gdip + c * n_pad + s, a[3 + c]);
-    for (int c = 0; c < 6; ++c) atomicAdd(gquad + c * n_pad + s, a[6 + c]);
+template <class R>
+__device__ __forceinline__ void add_to(double *p, R v) {
+    if constexpr (std::is_integral<R>::value)   // fixed point
+        atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+    else
+        atomicAdd(p, (double)v);
+}
+template <class R>
+__device__ __forceinline__ void flush12(double *frc, double *gdip, double *gquad, int n_pad, int s, const R *a) {
+    for (int c = 0; c < 3; ++c) add_to(frc + c * n_pad + s, a[c]);
+    for (int c = 0; c < 3; ++c) add_to(gdip + c * n_pad + s, a[3 + c]);
+    for (int c = 0; c < 6; ++c) add_to(gquad + c * n_pad + s, a[6 + c]);
+}
+// FP64 value v added to slot k of an array of FP64 numbers or (fixed) fixed-point integers,
+// by the only thread that updates that slot
+__device__ __forceinline__ void add_plain(double *arr, size_t k, double v, int fixed) {
+    if (fixed)
+        reinterpret_cast<long long *>(arr)[k] += ap_to_fx(v);
+    else
+        arr[k] += v;
 }
 
 // out_a = sum_b mu_b dE_b/dR_a for the field E(R) of a multipole (q, d, Q) at the origin
@@ -58,14 +75,14 @@ __device__ __forceinline__ void mu_dot_field_grad(T q, const T *d, const T *Q /*
 //   dU/dQ_t / (-f/3) += R_2 sym(mu_s R) - R_3 (mu_s.R) R R
 // so the pair's force is evaluated once per side (twice per pair) in exchange for lanes
 // that only ever see in-range pairs.
-template <class T>
+template <class T, class A>
 struct FoSmem {
     typename V4<T>::type pos[64];   // x, y, z, Thole factor: [0,32) block I, [32,64) the item's j atoms
     typename V4<T>::type qd[64];    // charge, dipole
     typename V4<T>::type qa[64];    // Qxx, Qxy, Qxz, Qyy
     typename V4<T>::type mu[64];    // induced dipole
     T qb[2][64];                    // Qyz, Qzz
-    T acc[12][64];                  // per-target sums of the item
+    A acc[12][64];                  // per-target sums of the item
     unsigned ex[32];                // exclusion words: lane i, bit j
     unsigned words[64];             // pair bits: rows of the i atoms, then columns of the j atoms
     int pre[64];                    // inclusive prefix counts of the words' bits
@@ -74,7 +91,7 @@ struct FoSmem {
 template <class T>
 constexpr int fo_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
-template <class T, bool MINIMG>
+template <class T, bool MINIMG, bool FX>
 __global__ void __launch_bounds__(128) k_pair_forces(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq,
     const typename V4<T>::type *__restrict__ dipd, const typename V4<T>::type *__restrict__ quad0,
@@ -82,8 +99,9 @@ __global__ void __launch_bounds__(128) k_pair_forces(
     double *__restrict__ frc, double *__restrict__ gdip, double *__restrict__ gquad, int n_pad, PairConsts<T> pc,
     double fconst) {
     typedef typename V4<T>::type T4;
-    __shared__ FoSmem<T> smem[fo_warps<T>()];
-    FoSmem<T> &S = smem[threadIdx.x >> 5];
+    typedef PairAcc<T, FX> PA;
+    __shared__ FoSmem<T, typename PA::shared_t> smem[fo_warps<T>()];
+    FoSmem<T, typename PA::shared_t> &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
@@ -92,17 +110,22 @@ __global__ void __launch_bounds__(128) k_pair_forces(
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     const double sc[12] = {fconst, fconst, fconst, -fconst, -fconst, -fconst, -fconst / 3, -fconst / 3,
                            -fconst / 3, -fconst / 3, -fconst / 3, -fconst / 3};
-    int curI = -1;
-    double ai[12];
+    // FP64 mode: per-item sums are unscaled and scaled in FP64; fixed point: scaled in T
+    // before the conversion, so that the integers hold the final quantities
+    T scf[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) ai[k] = 0.0;
+    for (int k = 0; k < 12; ++k) scf[k] = FX ? (T)sc[k] : T(1);
+    int curI = -1;
+    typename PA::reg_t ai[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ai[k] = 0;
     for (long t = t0; t < t1; ++t) {
         const int2 it = wa.work[t];
         __syncwarp();
         if (it.x != curI) {
             if (curI >= 0 && curI * 32 + lane < pc.n) flush12(frc, gdip, gquad, n_pad, curI * 32 + lane, ai);
 #pragma unroll
-            for (int k = 0; k < 12; ++k) ai[k] = 0.0;
+            for (int k = 0; k < 12; ++k) ai[k] = 0;
             curI = it.x;
             const int si = curI * 32 + lane;
             const T4 a = posq[si], b = dipd[si], c = quad0[si], d = quad1[si];
@@ -154,8 +177,8 @@ __global__ void __launch_bounds__(128) k_pair_forces(
         S.ex[lane] = ex;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            S.acc[k][lane] = T(0);
-            S.acc[k][32 + lane] = T(0);
+            S.acc[k][lane] = 0;
+            S.acc[k][32 + lane] = 0;
         }
         const int total = side_words(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
                                      S.words, S.pre);
@@ -177,7 +200,7 @@ __global__ void __launch_bounds__(128) k_pair_forces(
             if (tg != cur) {
                 if (cur >= 0) {
 #pragma unroll
-                    for (int k = 0; k < 12; ++k) atomicAdd(&S.acc[k][cur], f[k]);
+                    for (int k = 0; k < 12; ++k) PA::shared_add(&S.acc[k][cur], f[k] * scf[k]);
                 }
 #pragma unroll
                 for (int k = 0; k < 12; ++k) f[k] = T(0);
@@ -232,18 +255,20 @@ __global__ void __launch_bounds__(128) k_pair_forces(
         }
         if (cur >= 0) {
 #pragma unroll
-            for (int k = 0; k < 12; ++k) atomicAdd(&S.acc[k][cur], f[k]);
+            for (int k = 0; k < 12; ++k) PA::shared_add(&S.acc[k][cur], f[k] * scf[k]);
         }
         __syncwarp();
 #pragma unroll
-        for (int k = 0; k < 12; ++k) ai[k] += sc[k] * (double)S.acc[k][lane];
+        for (int k = 0; k < 12; ++k) ai[k] += FX ? PA::to_reg(S.acc[k][lane]) : sc[k] * PA::to_reg(S.acc[k][lane]);
         if (diag) {
 #pragma unroll
-            for (int k = 0; k < 12; ++k) ai[k] += sc[k] * (double)S.acc[k][32 + lane];
+            for (int k = 0; k < 12; ++k)
+                ai[k] += FX ? PA::to_reg(S.acc[k][32 + lane]) : sc[k] * PA::to_reg(S.acc[k][32 + lane]);
         } else if (sj >= 0) {
-            double aj[12];
+            typename PA::reg_t aj[12];
 #pragma unroll
-            for (int k = 0; k < 12; ++k) aj[k] = sc[k] * (double)S.acc[k][32 + lane];
+            for (int k = 0; k < 12; ++k)
+                aj[k] = FX ? PA::to_reg(S.acc[k][32 + lane]) : sc[k] * PA::to_reg(S.acc[k][32 + lane]);
             flush12(frc, gdip, gquad, n_pad, sj, aj);
         }
     }
@@ -259,7 +284,7 @@ __global__ void k_recip_forces(const double *__restrict__ D, const double *__res
                                const typename V4<T>::type *__restrict__ quad0,
                                const typename V4<T>::type *__restrict__ quad1, int n, int n_pad, double f,
                                double self_coef, double *__restrict__ frc, double *__restrict__ gdip,
-                               double *__restrict__ gquad) {
+                               double *__restrict__ gquad, int fixed) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     auto Du = [&](int c) { return D[(size_t)c * n_pad + s]; };
@@ -283,11 +308,11 @@ __global__ void k_recip_forces(const double *__restrict__ D, const double *__res
         double g = 0.0;
         for (int l = 0; l < 3; ++l) g += m[l] * (Hu[k][l] + HM[k][l]) + dd[l] * Hu[k][l];
         g += q * gu[k] + QT[k] * (1.0 / 3.0);
-        frc[k * n_pad + s] -= f * g;
-        gdip[k * n_pad + s] += f * gu[k] - f * self_coef * m[k];
+        add_plain(frc, (size_t)k * n_pad + s, -f * g, fixed);
+        add_plain(gdip, (size_t)k * n_pad + s, f * gu[k] - f * self_coef * m[k], fixed);
     }
     const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-    for (int k = 0; k < 6; ++k) gquad[k * n_pad + s] += f * (1.0 / 3.0) * Hu[ia[k]][ib[k]];
+    for (int k = 0; k < 6; ++k) add_plain(gquad, (size_t)k * n_pad + s, f * (1.0 / 3.0) * Hu[ia[k]][ib[k]], fixed);
 }
 
 __device__ __forceinline__ double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
@@ -301,7 +326,7 @@ __device__ __forceinline__ void cross3(const double *a, const double *b, double 
 __global__ void k_frame_forces(const double *__restrict__ gdip, const double *__restrict__ gquad,
                                const double *__restrict__ rot, const double *__restrict__ mpl,
                                const double *__restrict__ fvec, const int *__restrict__ frame_s, int n, int n_pad,
-                               double *__restrict__ frc) {
+                               double *__restrict__ frc, int fixed) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int type = frame_s[3 * s];
@@ -313,9 +338,10 @@ __global__ void k_frame_forces(const double *__restrict__ gdip, const double *__
     const double *m = mpl + 10 * s;
     const double dl[3] = {m[1], m[2], m[3]};
     const double Ql[3][3] = {{m[4], m[5], m[6]}, {m[5], m[7], m[8]}, {m[6], m[8], m[9]}};
-    const double Gd[3] = {gdip[s], gdip[n_pad + s], gdip[2 * n_pad + s]};
-    const double g6[6] = {gquad[s], gquad[n_pad + s], gquad[2 * n_pad + s], gquad[3 * n_pad + s],
-                          gquad[4 * n_pad + s], gquad[5 * n_pad + s]};
+    const double Gd[3] = {acc_value(gdip, s, fixed), acc_value(gdip, (size_t)n_pad + s, fixed),
+                          acc_value(gdip, (size_t)2 * n_pad + s, fixed)};
+    double g6[6];
+    for (int k = 0; k < 6; ++k) g6[k] = acc_value(gquad, (size_t)k * n_pad + s, fixed);
     const double GQ[3][3] = {{g6[0], g6[1], g6[2]}, {g6[1], g6[3], g6[4]}, {g6[2], g6[4], g6[5]}};
     double RQ[3][3], dR[3][3];
     for (int a = 0; a < 3; ++a)
@@ -376,9 +402,16 @@ __global__ void k_frame_forces(const double *__restrict__ gdip, const double *__
         }
     }
     for (int a = 0; a < 3; ++a) {
-        atomicAdd(frc + a * n_pad + zs, -g_vz[a]);
-        atomicAdd(frc + a * n_pad + xs, -g_vx[a]);
-        atomicAdd(frc + a * n_pad + s, g_vz[a] + g_vx[a]);
+        if (fixed) {
+            unsigned long long *fx = reinterpret_cast<unsigned long long *>(frc);
+            atomicAdd(fx + a * n_pad + zs, (unsigned long long)ap_to_fx(-g_vz[a]));
+            atomicAdd(fx + a * n_pad + xs, (unsigned long long)ap_to_fx(-g_vx[a]));
+            atomicAdd(fx + a * n_pad + s, (unsigned long long)ap_to_fx(g_vz[a] + g_vx[a]));
+        } else {
+            atomicAdd(frc + a * n_pad + zs, -g_vz[a]);
+            atomicAdd(frc + a * n_pad + xs, -g_vx[a]);
+            atomicAdd(frc + a * n_pad + s, g_vz[a] + g_vx[a]);
+        }
     }
 }
 
@@ -399,7 +432,7 @@ __global__ void k_mu_load(const double *__restrict__ mu_in, const int *__restric
 }
 
 __global__ void k_energy(const double *__restrict__ mu, const double *__restrict__ E, int n_pad, double scale,
-                         double *__restrict__ out) {
+                         double *__restrict__ out, int fixed) {
     __shared__ double sm[8];
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
@@ -411,8 +444,25 @@ __global__ void k_energy(const double *__restrict__ mu, const double *__restrict
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
-        atomicAdd(out, scale * t);
+        if (fixed)   // energy in fixed point with 30 fractional bits: order-independent sum
+            atomicAdd(reinterpret_cast<unsigned long long *>(out), (unsigned long long)llrint(scale * t * 1073741824.0));
+        else
+            atomicAdd(out, scale * t);
     }
+}
+
+// fixed-point energy (30 fractional bits) -> FP64
+__global__ void k_energy_out(const double *__restrict__ e, double *__restrict__ out) {
+    *out = (double)*reinterpret_cast<const long long *>(e) * (1.0 / 1073741824.0);
+}
+
+// force accumulators in fixed point, sorted slots -> FP64, caller order
+__global__ void k_unsort3_fx(const double *__restrict__ src, int n_pad, const int *__restrict__ iperm, int n,
+                             double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = iperm[i];
+    for (int c = 0; c < 3; ++c) out[3 * i + c] = acc_value(src, (size_t)c * n_pad + s, 1);
 }
 
 // the real-space force kernel over the current work items with the dipoles in ctx->p,
@@ -430,9 +480,10 @@ int pair_forces_t(ap_ctx *ctx, cudaStream_t s) {
     pc.rc2 = (T)(P.cutoff * P.cutoff);
     for (int dd = 0; dd < 3; ++dd) { pc.L[dd] = (T)P.box[dd]; pc.iL[dd] = (T)(1.0 / P.box[dd]); }
     pc.n = ctx->n;
-    auto kern = ctx->minimg ? k_pair_forces<T, true> : k_pair_forces<T, false>;
-    static int grids[2] = {0, 0};
-    int &grid = grids[ctx->minimg];
+    auto kern = ctx->fixed ? (ctx->minimg ? k_pair_forces<T, true, true> : k_pair_forces<T, false, true>)
+                           : (ctx->minimg ? k_pair_forces<T, true, false> : k_pair_forces<T, false, false>);
+    static int grids[4] = {0, 0, 0, 0};
+    int &grid = grids[ctx->minimg + 2 * ctx->fixed];
     if (!grid) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * fo_warps<T>(), 0);
@@ -458,7 +509,7 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
     AP_CUDA(cudaMemsetAsync(ctx->gquad, 0, sizeof(double) * 6 * n_pad, s));
     AP_CUDA(cudaMemsetAsync(ctx->red + 8, 0, sizeof(double), s));
     // energy
-    k_energy<<<ap_grid_for(n_pad, 256), 256, 0, s>>>(ctx->mu_s, ctx->E, n_pad, -0.5 * f, ctx->red + 8);
+    k_energy<<<ap_grid_for(n_pad, 256), 256, 0, s>>>(ctx->mu_s, ctx->E, n_pad, -0.5 * f, ctx->red + 8, ctx->fixed);
     // reciprocal-space potential derivatives on the second stream, concurrent with the
     // real-space pair forces (they write only gbuf and the grid); joined before the kernels
     // that update the force arrays per atom
@@ -473,12 +524,17 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
     k_recip_forces<T><<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gbuf, ctx->mu_s, (const T4 *)ctx->posq,
                                                          (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
                                                          (const T4 *)ctx->quad1, n, n_pad, f, self_coef, ctx->frc,
-                                                         ctx->gdip, ctx->gquad);
+                                                         ctx->gdip, ctx->gquad, ctx->fixed);
     k_frame_forces<<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gdip, ctx->gquad, ctx->rot, ctx->mpl, ctx->fvec,
-                                                       ctx->frame_s, n, n_pad, ctx->frc);
+                                                       ctx->frame_s, n, n_pad, ctx->frc, ctx->fixed);
     AP_CUDA(cudaGetLastError());
-    unsort3(ctx, ctx->frc, d_forces, s);
-    AP_CUDA(cudaMemcpyAsync(d_energy, ctx->red + 8, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (ctx->fixed) {
+        k_unsort3_fx<<<ap_grid_for(n, 256), 256, 0, s>>>(ctx->frc, n_pad, ctx->iperm, n, d_forces);
+        k_energy_out<<<1, 1, 0, s>>>(ctx->red + 8, d_energy);
+    } else {
+        unsort3(ctx, ctx->frc, d_forces, s);
+        AP_CUDA(cudaMemcpyAsync(d_energy, ctx->red + 8, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }

@@ -195,22 +195,23 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const unsigned char *__rest
 // (3 + 3), |e_i|, |e1_i|, alpha_i, frame kind (0 global, 0.5 Z-then-X, 1 bisector)
 __global__ void k_features(const double *__restrict__ E, const double *__restrict__ E1, const double *__restrict__ rot,
                            const double *__restrict__ alpha, const int *__restrict__ frame_s, int n, int n_pad,
-                           float *__restrict__ feat) {
+                           float *__restrict__ feat, int e1_fixed) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const double *R = rot + 9 * s;
-    auto loc = [&](const double *F, int slot, double *o) {
-        const double e[3] = {F[slot] * (1.0 / MLP_E_SCALE), F[n_pad + slot] * (1.0 / MLP_E_SCALE),
-                             F[2 * n_pad + slot] * (1.0 / MLP_E_SCALE)};
+    auto loc = [&](const double *F, int slot, double *o, int fx) {
+        const double e[3] = {acc_value(F, slot, fx) * (1.0 / MLP_E_SCALE),
+                             acc_value(F, (size_t)n_pad + slot, fx) * (1.0 / MLP_E_SCALE),
+                             acc_value(F, (size_t)2 * n_pad + slot, fx) * (1.0 / MLP_E_SCALE)};
         for (int b = 0; b < 3; ++b) o[b] = R[0 * 3 + b] * e[0] + R[1 * 3 + b] * e[1] + R[2 * 3 + b] * e[2];
     };
     double f[16];
-    loc(E, s, f);
-    loc(E1, s, f + 3);
+    loc(E, s, f, 0);
+    loc(E1, s, f + 3, e1_fixed);
     const int type = frame_s[3 * s];
     if (type != AP_FRAME_NONE) {
-        loc(E, frame_s[3 * s + 1], f + 6);
-        loc(E, frame_s[3 * s + 2], f + 9);
+        loc(E, frame_s[3 * s + 1], f + 6, 0);
+        loc(E, frame_s[3 * s + 2], f + 9, 0);
     } else {
         for (int k = 6; k < 12; ++k) f[k] = 0.0;
     }
@@ -523,7 +524,7 @@ int features_slots(ap_ctx *ctx) {
     int r = short_matvec_launch(ctx, ctx->p, ctx->e1s, st);
     if (r) return r;
     k_features<<<ap_grid_for(n, 128), 128, 0, st>>>(ctx->E, ctx->e1s, ctx->rot, ctx->alpha, ctx->frame_s, n, ctx->n_pad,
-                                                   ctx->mlp_feat);
+                                                   ctx->mlp_feat, ctx->fixed);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }

@@ -8,6 +8,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 __device__ __forceinline__ float ap_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double ap_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float ap_exp(float x) { return expf(x); }
@@ -121,3 +123,31 @@ __device__ __forceinline__ int side_words(unsigned row, unsigned col, int lane, 
     pre[32 + lane] = prow + ic;
     return prow + __shfl_sync(0xffffffffu, ic, 31);
 }
+
+// Accumulation of the pair kernels' FP32 partial sums. FX = false: per-target sums of an item
+// in T with shared-memory atomics, running sums across items in FP64 registers, FP64 atomics
+// to the global accumulators. FX = true (AP_FIXED): the same in 64-bit fixed point (integer
+// additions, so the totals do not depend on their order); the global accumulators then hold
+// fixed-point integers in the same 8-byte slots.
+template <class T, bool FX>
+struct PairAcc;
+template <class T>
+struct PairAcc<T, false> {
+    typedef T shared_t;
+    typedef double reg_t;
+    static __device__ __forceinline__ void shared_add(shared_t *p, T v) { atomicAdd(p, v); }
+    static __device__ __forceinline__ reg_t to_reg(shared_t v) { return (double)v; }
+    static __device__ __forceinline__ void global_add(double *p, reg_t v) { atomicAdd(p, v); }
+};
+template <class T>
+struct PairAcc<T, true> {
+    typedef unsigned long long shared_t;
+    typedef long long reg_t;
+    static __device__ __forceinline__ void shared_add(shared_t *p, T v) {
+        atomicAdd(p, (unsigned long long)ap_to_fx(v));
+    }
+    static __device__ __forceinline__ reg_t to_reg(shared_t v) { return (long long)v; }
+    static __device__ __forceinline__ void global_add(double *p, reg_t v) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+    }
+};

@@ -79,14 +79,14 @@ __global__ void k_init_residual(const double *__restrict__ E, const double *__re
                                 const double *__restrict__ mu, double *__restrict__ acc,
                                 const T *__restrict__ rec, const double *__restrict__ dg, int n_pad,
                                 double *__restrict__ r, typename V4<T>::type *__restrict__ p,
-                                double *__restrict__ part) {
+                                double *__restrict__ part, int fixed) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double rz = 0.0, zz = 0.0;
     if (s < n_pad) {
         const double a = alpha[s], d = dg[s];
         for (int c = 0; c < 3; ++c) {
             const int k = c * n_pad + s;
-            double Amu = a > 0.0 ? mu[k] * d - acc[k] - (double)rec[k] : 0.0;
+            double Amu = a > 0.0 ? mu[k] * d - acc_value(acc, k, fixed) - (double)rec[k] : 0.0;
             double rr = a > 0.0 ? E[k] - Amu : 0.0;
             r[k] = rr;
             acc[k] = 0.0;
@@ -202,7 +202,7 @@ __global__ void k_direction(const double *__restrict__ r, const double *__restri
 template <class T>
 __global__ void k_apply(const typename V4<T>::type *__restrict__ p, const double *__restrict__ dg,
                         double *__restrict__ acc, const T *__restrict__ rec, int n_pad, double *__restrict__ q,
-                        double *__restrict__ part, PcgState *st) {
+                        double *__restrict__ part, PcgState *st, int fixed) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double pq = 0.0, dummy = 0.0;
     if (s < n_pad) {
@@ -211,7 +211,7 @@ __global__ void k_apply(const typename V4<T>::type *__restrict__ p, const double
         const double pv[3] = {(double)v.x, (double)v.y, (double)v.z};
         for (int c = 0; c < 3; ++c) {
             const int k = c * n_pad + s;
-            const double qq = pv[c] * d - acc[k] - (double)rec[k];
+            const double qq = pv[c] * d - acc_value(acc, k, fixed) - (double)rec[k];
             q[k] = qq;
             acc[k] = 0.0;
             pq += pv[c] * qq;
@@ -294,7 +294,7 @@ int enqueue_iteration(ap_ctx *ctx, cudaGraphConditionalHandle h, int use_cond, c
     if (rc) return rc;
     double *part_pq = ctx->red_part, *part_rz = ctx->red_part + nb;
     k_apply<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->dg, ctx->acc, (const T *)ctx->rec, ctx->n_pad, ctx->qv,
-                                     part_pq, ctx->st);
+                                     part_pq, ctx->st, ctx->fixed);
     k_update<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
                                       part_rz, ctx->n, h, use_cond);
     AP_CUDA(cudaGetLastError());
@@ -373,7 +373,7 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
     int rc = matvec_into<T>(ctx, ctx->p);
     if (rc) return rc;
     k_init_residual<T><<<nb, NT, 0, s>>>(ctx->E, ctx->alpha, ctx->mu, ctx->acc, (const T *)ctx->rec, ctx->dg,
-                                          ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->red_part);
+                                          ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->red_part, ctx->fixed);
     k_init_finish<<<1, NT, 0, s>>>(ctx->st, ctx->red_part, nb, ctx->n, tol, max_iter);
     AP_CUDA(cudaGetLastError());
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -454,14 +454,14 @@ int pcg_vectors_launch(ap_ctx *ctx, cudaStream_t s) {
         typedef V4<double>::type T4;
         k_direction<double><<<nb, NT, 0, s>>>(ctx->r, ctx->alpha, ctx->n_pad, (T4 *)ctx->p, ctx->st);
         k_apply<double><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->dg, ctx->acc, (const double *)ctx->rec, ctx->n_pad,
-                                          ctx->qv, part_pq, ctx->st);
+                                          ctx->qv, part_pq, ctx->st, ctx->fixed);
         k_update<double><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
                                            part_rz, ctx->n, 0, 0);
     } else {
         typedef V4<float>::type T4;
         k_direction<float><<<nb, NT, 0, s>>>(ctx->r, ctx->alpha, ctx->n_pad, (T4 *)ctx->p, ctx->st);
         k_apply<float><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->dg, ctx->acc, (const float *)ctx->rec, ctx->n_pad,
-                                         ctx->qv, part_pq, ctx->st);
+                                         ctx->qv, part_pq, ctx->st, ctx->fixed);
         k_update<float><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
                                           part_rz, ctx->n, 0, 0);
     }
@@ -491,12 +491,13 @@ __global__ void k_load_vec(const double *__restrict__ v, const int *__restrict__
 
 template <class T>
 __global__ void k_tp_out(const typename V4<T>::type *__restrict__ p, const double *__restrict__ acc,
-                         const T *__restrict__ rec, double self_coef, int n_pad, double *__restrict__ out) {
+                         const T *__restrict__ rec, double self_coef, int n_pad, double *__restrict__ out, int fixed) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_pad) return;
     typename V4<T>::type v = p[s];
     const double pv[3] = {(double)v.x, (double)v.y, (double)v.z};
-    for (int c = 0; c < 3; ++c) out[c * n_pad + s] = acc[c * n_pad + s] + (double)rec[c * n_pad + s] + self_coef * pv[c];
+    for (int c = 0; c < 3; ++c)
+        out[c * n_pad + s] = acc_value(acc, (size_t)c * n_pad + s, fixed) + (double)rec[c * n_pad + s] + self_coef * pv[c];
 }
 
 template <class T>
@@ -508,7 +509,7 @@ int apply_t(ap_ctx *ctx, const double *d_v, double *d_out) {
     int rc = matvec_into<T>(ctx, ctx->p);
     if (rc) return rc;
     k_tp_out<T><<<nb, NT, 0, ctx->s0>>>((const T4 *)ctx->p, ctx->acc, (const T *)ctx->rec, self_coef(ctx),
-                                         ctx->n_pad, ctx->qv);
+                                         ctx->n_pad, ctx->qv, ctx->fixed);
     unsort3(ctx, ctx->qv, d_out, ctx->s0);
     AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
     AP_CUDA(cudaGetLastError());

@@ -115,11 +115,23 @@ __device__ __forceinline__ void add_row5(float *row, const int *k, const float *
 }
 
 // spread permanent multipoles (q, d, Q) ------------------------------------------------
-template <class T>
+// adds the stencil row v[0..4] to the grid (FX: the fixed-point grid, one 64-bit atomic per point)
+template <class T, bool FX>
+__device__ __forceinline__ void grid_row5(void *grid, size_t row, const int *k, const T *v) {
+    if constexpr (FX) {
+        unsigned long long *g = reinterpret_cast<unsigned long long *>(grid) + row;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) atomicAdd(g + k[t], (unsigned long long)ap_to_fx(v[t]));
+    } else {
+        add_row5(reinterpret_cast<T *>(grid) + row, k, v);
+    }
+}
+
+template <class T, bool FX>
 __global__ void k_spread_multipoles(const typename V4<T>::type *__restrict__ posq,
                                     const typename V4<T>::type *__restrict__ dipd,
                                     const typename V4<T>::type *__restrict__ quad0,
-                                    const typename V4<T>::type *__restrict__ quad1, T *__restrict__ grid,
+                                    const typename V4<T>::type *__restrict__ quad1, void *__restrict__ grid,
                                     PmeConsts<T> pc, const int4 *__restrict__ stb,
                                     const typename V4<T>::type *__restrict__ stw) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -142,19 +154,19 @@ __global__ void k_spread_multipoles(const typename V4<T>::type *__restrict__ pos
             const T A = q * y0 * z0 + dy * y1 * z0 + dz * y0 * z1 + Qyy * y2 * z0 + Qzz * y0 * z2 + Qyz * y1 * z1;
             const T Bc = dx * y0 * z0 + Qxy * y1 * z0 + Qxz * y0 * z1;
             const T Cc = Qxx * y0 * z0;
-            T *row = grid + ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
+            const size_t row = ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
             T v[5];
 #pragma unroll
             for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc + st.d2[0][t1] * Cc;
-            add_row5(row, st.k[0], v);
+            grid_row5<T, FX>(grid, row, st.k[0], v);
         }
     }
 }
 
 // spread induced dipoles p --------------------------------------------------------------
-template <class T>
+template <class T, bool FX>
 __global__ void k_spread_dipoles(const int4 *__restrict__ stb, const typename V4<T>::type *__restrict__ stw,
-                                 const typename V4<T>::type *__restrict__ pv, T *__restrict__ grid,
+                                 const typename V4<T>::type *__restrict__ pv, void *__restrict__ grid,
                                  PmeConsts<T> pc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pc.n) return;
@@ -171,13 +183,22 @@ __global__ void k_spread_dipoles(const int4 *__restrict__ stb, const typename V4
             const T y0 = st.th[1][t2], y1 = st.d1[1][t2];
             const T A = py * y1 * z0 + pz * y0 * z1;
             const T Bc = px * y0 * z0;
-            T *row = grid + ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
+            const size_t row = ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
             T v[5];
 #pragma unroll
             for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc;
-            add_row5(row, st.k[0], v);
+            grid_row5<T, FX>(grid, row, st.k[0], v);
         }
     }
+}
+
+// fixed-point grid -> T grid for the FFT; clears the fixed-point grid for its next use
+template <class T>
+__global__ void k_grid_from_fx(long long *__restrict__ gfx, T *__restrict__ grid, size_t m) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    grid[i] = (T)ap_from_fx(gfx[i]);
+    gfx[i] = 0;
 }
 
 // k-space product with B(m) C(m) ----------------------------------------------------------
@@ -348,6 +369,10 @@ int init_t(ap_ctx *ctx) {
     bool dbl = sizeof(T) == 8;
     AP_CUFFT(cufftPlan3d(&ctx->plan_r2c, Kz, Ky, Kx, dbl ? CUFFT_D2Z : CUFFT_R2C));
     AP_CUFFT(cufftPlan3d(&ctx->plan_c2r, Kz, Ky, Kx, dbl ? CUFFT_Z2D : CUFFT_C2R));
+    if (ctx->fixed) {
+        AP_CUDA(cudaMalloc((void **)&ctx->grid_fx, sizeof(long long) * ctx->ngrid));
+        AP_CUDA(cudaMemset(ctx->grid_fx, 0, sizeof(long long) * ctx->ngrid));
+    }
     return AP_OK;
 }
 
@@ -372,19 +397,44 @@ int fft_roundtrip(ap_ctx *ctx, T *in, T *out, cudaStream_t s) {
     return AP_OK;
 }
 
+// spread into ctx->grid: the induced dipoles `src` (multi = false) or the permanent
+// multipoles (multi = true). Mixed/FP64 modes: FP32/T atomics on a cleared grid. AP_FIXED:
+// 64-bit fixed-point atomics on ctx->grid_fx (kept cleared), then converted into the grid.
+template <class T>
+int spread_t(ap_ctx *ctx, const void *src, bool multi, cudaStream_t s) {
+    typedef typename V4<T>::type T4;
+    PmeConsts<T> pc = pme_consts<T>(ctx);
+    const bool fx = ctx->fixed != 0;
+    void *g = fx ? (void *)ctx->grid_fx : ctx->grid;
+    if (!fx) AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
+    if (multi) {
+        auto kern = fx ? k_spread_multipoles<T, true> : k_spread_multipoles<T, false>;
+        kern<<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->dipd,
+                                                       (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, g, pc,
+                                                       ctx->stb, (const T4 *)ctx->stw);
+    } else {
+        auto kern = fx ? k_spread_dipoles<T, true> : k_spread_dipoles<T, false>;
+        kern<<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
+            ctx->stb, (const T4 *)ctx->stw, (const T4 *)src, g, pc);
+    }
+    AP_CUDA(cudaGetLastError());
+    if (fx) {
+        k_grid_from_fx<T><<<ap_grid_for((long)ctx->ngrid, 256), 256, 0, s>>>(ctx->grid_fx, (T *)ctx->grid, ctx->ngrid);
+        AP_CUDA(cudaGetLastError());
+    }
+    return AP_OK;
+}
+
 template <class T>
 int multipole_field_t(ap_ctx *ctx, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
-    AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
-    k_spread_multipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(
-        (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0, (const T4 *)ctx->quad1,
-        (T *)ctx->grid, pc, ctx->stb, (const T4 *)ctx->stw);
-    AP_CUDA(cudaGetLastError());
-    int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid2, s);
+    int r = spread_t<T>(ctx, nullptr, true, s);
     if (r) return r;
-    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid2,
-                                                              (T *)ctx->rec, ctx->n_pad, pc);
+    r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid2, s);
+    if (r) return r;
+    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
+        ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid2, (T *)ctx->rec, ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -393,14 +443,12 @@ template <class T>
 int dipole_field_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
-    AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
-    k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T4 *)p,
-                                                                (T *)ctx->grid, pc);
-    AP_CUDA(cudaGetLastError());
-    int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
+    int r = spread_t<T>(ctx, p, false, s);
     if (r) return r;
-    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid,
-                                                              (T *)ctx->rec, ctx->n_pad, pc);
+    r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
+    if (r) return r;
+    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
+        ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid, (T *)ctx->rec, ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -411,11 +459,9 @@ template <class T>
 int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
-    AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
-    k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T4 *)mu4,
-                                                                (T *)ctx->grid, pc);
-    AP_CUDA(cudaGetLastError());
-    int r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
+    int r = spread_t<T>(ctx, mu4, false, s);
+    if (r) return r;
+    r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
     if (r) return r;
     k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid,
                                                                gbuf, ctx->n_pad, 20, pc);
@@ -425,6 +471,7 @@ int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
     return AP_OK;
 }
 
+// one stage alone, for timing (the spreads include the fixed-point conversion in AP_FIXED)
 template <class T>
 int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
     typedef typename V4<T>::type T4;
@@ -432,22 +479,17 @@ int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
     PmeConsts<T> pc = pme_consts<T>(ctx);
     switch (stage) {
     case 0:
-        k_spread_dipoles<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T4 *)ctx->p,
-                                                                    (T *)ctx->grid, pc);
-        break;
+        return spread_t<T>(ctx, ctx->p, false, s);
     case 1:
         k_convolve<T><<<ap_grid_for((long)ctx->ncgrid, 256), 256, 0, s>>>((C *)ctx->cgrid, (const T *)ctx->green,
                                                                          ctx->ncgrid);
         break;
     case 2:
-        k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid,
-                                                                  (T *)ctx->rec, ctx->n_pad, pc);
+        k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
+            ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid, (T *)ctx->rec, ctx->n_pad, pc);
         break;
     case 3:
-        k_spread_multipoles<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(
-            (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)ctx->quad0, (const T4 *)ctx->quad1,
-            (T *)ctx->grid, pc, ctx->stb, (const T4 *)ctx->stw);
-        break;
+        return spread_t<T>(ctx, nullptr, true, s);
     default:
         return ap_fail(ctx, AP_ERR_ARG, "unknown PME stage");
     }

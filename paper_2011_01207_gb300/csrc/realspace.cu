@@ -37,10 +37,12 @@ __device__ __forceinline__ void pair_vector(const PairConsts<T> &pc, T xi, T yi,
     }
 }
 
-__device__ __forceinline__ void flush3(double *acc, int n_pad, int slot, double a, double b, double c) {
-    atomicAdd(acc + slot, a);
-    atomicAdd(acc + n_pad + slot, b);
-    atomicAdd(acc + 2 * n_pad + slot, c);
+template <class PA>
+__device__ __forceinline__ void flush3(double *acc, int n_pad, int slot, typename PA::reg_t a, typename PA::reg_t b,
+                                       typename PA::reg_t c) {
+    PA::global_add(acc + slot, a);
+    PA::global_add(acc + n_pad + slot, b);
+    PA::global_add(acc + 2 * n_pad + slot, c);
 }
 
 // Work items come from the per-configuration filter: (I, -1) is block I against itself,
@@ -54,13 +56,13 @@ __device__ __forceinline__ void flush3(double *acc, int n_pad, int slot, double 
 // the target from the source's multipole" for both atoms, and with R = x_target - x_source
 // one expression serves both sides. The exclusion bit of the pair (sigma = 0 in R_n) is
 // looked up in the item's 32-word mask.
-template <class T>
+template <class T, class A>
 struct PfSmem {
     typename V4<T>::type pos[64];   // x, y, z, Thole factor: [0,32) block I, [32,64) the item's j atoms
     typename V4<T>::type qd[64];    // charge, dipole
     typename V4<T>::type qa[64];    // Qxx, Qxy, Qxz, Qyy
     T qb[2][64];                    // Qyz, Qzz
-    T acc[3][64];                   // per-target sums of the item
+    A acc[3][64];                   // per-target sums of the item
     unsigned ex[32];                // exclusion words: lane i, bit j
     unsigned words[64];             // pair bits: rows of the i atoms, then columns of the j atoms
     int pre[64];                    // inclusive prefix counts of the words' bits
@@ -69,14 +71,15 @@ struct PfSmem {
 template <class T>
 __host__ __device__ constexpr int pf_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
-template <class T, bool MINIMG>
+template <class T, bool MINIMG, bool FX>
 __global__ void __launch_bounds__(128) k_perm_field(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
     const typename V4<T>::type *__restrict__ quad0, const typename V4<T>::type *__restrict__ quad1,
     double *__restrict__ acc, int n_pad, PairConsts<T> pc) {
     typedef typename V4<T>::type T4;
-    __shared__ PfSmem<T> smem[pf_warps<T>()];
-    PfSmem<T> &S = smem[threadIdx.x >> 5];
+    typedef PairAcc<T, FX> PA;
+    __shared__ PfSmem<T, typename PA::shared_t> smem[pf_warps<T>()];
+    PfSmem<T, typename PA::shared_t> &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
@@ -84,12 +87,12 @@ __global__ void __launch_bounds__(128) k_perm_field(
     const long t0 = nitems * gw / nw, t1 = nitems * (gw + 1) / nw;
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
-    double ax = 0, ay = 0, az = 0;
+    typename PA::reg_t ax = 0, ay = 0, az = 0;
     for (long t = t0; t < t1; ++t) {
         const int2 it = wa.work[t];
         __syncwarp();
         if (it.x != curI) {
-            if (curI >= 0 && curI * 32 + lane < pc.n) flush3(acc, n_pad, curI * 32 + lane, ax, ay, az);
+            if (curI >= 0 && curI * 32 + lane < pc.n) flush3<PA>(acc, n_pad, curI * 32 + lane, ax, ay, az);
             ax = ay = az = 0;
             curI = it.x;
             const int si = curI * 32 + lane;
@@ -137,8 +140,8 @@ __global__ void __launch_bounds__(128) k_perm_field(
         S.ex[lane] = ex;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            S.acc[c][lane] = T(0);
-            S.acc[c][32 + lane] = T(0);
+            S.acc[c][lane] = 0;
+            S.acc[c][32 + lane] = 0;
         }
         const int total = side_words(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
                                      S.words, S.pre);
@@ -155,9 +158,9 @@ __global__ void __launch_bounds__(128) k_perm_field(
             const int sl = src & 31;   // the source's lane within its half
             if (tg != cur) {
                 if (cur >= 0) {
-                    atomicAdd(&S.acc[0][cur], f0);
-                    atomicAdd(&S.acc[1][cur], f1);
-                    atomicAdd(&S.acc[2][cur], f2);
+                    PA::shared_add(&S.acc[0][cur], f0);
+                    PA::shared_add(&S.acc[1][cur], f1);
+                    PA::shared_add(&S.acc[2][cur], f2);
                 }
                 f0 = f1 = f2 = T(0);
                 cur = tg;
@@ -189,24 +192,24 @@ __global__ void __launch_bounds__(128) k_perm_field(
             f2 += fac * dz - R1 * m.w - q2 * Qz;
         }
         if (cur >= 0) {
-            atomicAdd(&S.acc[0][cur], f0);
-            atomicAdd(&S.acc[1][cur], f1);
-            atomicAdd(&S.acc[2][cur], f2);
+            PA::shared_add(&S.acc[0][cur], f0);
+            PA::shared_add(&S.acc[1][cur], f1);
+            PA::shared_add(&S.acc[2][cur], f2);
         }
         __syncwarp();
-        ax += (double)S.acc[0][lane];
-        ay += (double)S.acc[1][lane];
-        az += (double)S.acc[2][lane];
+        ax += PA::to_reg(S.acc[0][lane]);
+        ay += PA::to_reg(S.acc[1][lane]);
+        az += PA::to_reg(S.acc[2][lane]);
         if (diag) {
-            ax += (double)S.acc[0][32 + lane];
-            ay += (double)S.acc[1][32 + lane];
-            az += (double)S.acc[2][32 + lane];
+            ax += PA::to_reg(S.acc[0][32 + lane]);
+            ay += PA::to_reg(S.acc[1][32 + lane]);
+            az += PA::to_reg(S.acc[2][32 + lane]);
         } else if (sj >= 0) {
-            flush3(acc, n_pad, sj, (double)S.acc[0][32 + lane], (double)S.acc[1][32 + lane],
-                   (double)S.acc[2][32 + lane]);
+            flush3<PA>(acc, n_pad, sj, PA::to_reg(S.acc[0][32 + lane]), PA::to_reg(S.acc[1][32 + lane]),
+                   PA::to_reg(S.acc[2][32 + lane]));
         }
     }
-    if (curI >= 0 && curI * 32 + lane < pc.n) flush3(acc, n_pad, curI * 32 + lane, ax, ay, az);
+    if (curI >= 0 && curI * 32 + lane < pc.n) flush3<PA>(acc, n_pad, curI * 32 + lane, ax, ay, az);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -220,22 +223,23 @@ __global__ void __launch_bounds__(128) k_perm_field(
 // adding to a shared per-target sum only when it changes (a few times per lane per item).
 // So every lane evaluates one in-range pair side per step, whatever the pair distribution;
 // the field expression is even in R, so one code path serves both sides.
-template <class T>
+template <class T, class A>
 struct MvSmem {
     typename V4<T>::type pos[64];    // x, y, z, Thole factor: [0,32) block I, [32,64) the item's j atoms
     typename V4<T>::type p[64];      // dipoles of the same atoms
-    T acc[3][64];                    // per-target sums of the item
+    A acc[3][64];                    // per-target sums of the item
     unsigned words[64];              // pair bits: rows of the i atoms, then columns of the j atoms
     int pre[64];                     // inclusive prefix counts of the words' bits
 };
 
-template <class T, bool MINIMG, bool SHORT = false>
+template <class T, bool MINIMG, bool SHORT, bool FX>
 __global__ void __launch_bounds__(128) k_matvec(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
     const typename V4<T>::type *__restrict__ pv, double *__restrict__ acc, int n_pad, PairConsts<T> pc) {
     typedef typename V4<T>::type T4;
-    __shared__ MvSmem<T> smem[4];
-    MvSmem<T> &S = smem[threadIdx.x >> 5];
+    typedef PairAcc<T, FX> PA;
+    __shared__ MvSmem<T, typename PA::shared_t> smem[4];
+    MvSmem<T, typename PA::shared_t> &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
@@ -243,12 +247,12 @@ __global__ void __launch_bounds__(128) k_matvec(
     const long t0 = nitems * gw / nw, t1 = nitems * (gw + 1) / nw;
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
-    double ax = 0, ay = 0, az = 0;
+    typename PA::reg_t ax = 0, ay = 0, az = 0;
     for (long t = t0; t < t1; ++t) {
         const int2 it = wa.work[t];
         __syncwarp();   // every lane is done with the previous item's staging
         if (it.x != curI) {
-            if (curI >= 0 && curI * 32 + lane < pc.n) flush3(acc, n_pad, curI * 32 + lane, ax, ay, az);
+            if (curI >= 0 && curI * 32 + lane < pc.n) flush3<PA>(acc, n_pad, curI * 32 + lane, ax, ay, az);
             ax = ay = az = 0;
             curI = it.x;
             const int si = curI * 32 + lane;
@@ -272,8 +276,8 @@ __global__ void __launch_bounds__(128) k_matvec(
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            S.acc[c][lane] = T(0);
-            S.acc[c][32 + lane] = T(0);
+            S.acc[c][lane] = 0;
+            S.acc[c][32 + lane] = 0;
         }
         const int total =
             SHORT ? side_words(wa.smask[(size_t)t * 32 + lane], wa.smask_t[(size_t)t * 32 + lane], lane, S.words, S.pre)
@@ -290,9 +294,9 @@ __global__ void __launch_bounds__(128) k_matvec(
             sl.next(S.words, tg, src);
             if (tg != cur) {
                 if (cur >= 0) {
-                    atomicAdd(&S.acc[0][cur], f0);
-                    atomicAdd(&S.acc[1][cur], f1);
-                    atomicAdd(&S.acc[2][cur], f2);
+                    PA::shared_add(&S.acc[0][cur], f0);
+                    PA::shared_add(&S.acc[1][cur], f1);
+                    PA::shared_add(&S.acc[2][cur], f2);
                 }
                 f0 = f1 = f2 = T(0);
                 cur = tg;
@@ -314,24 +318,24 @@ __global__ void __launch_bounds__(128) k_matvec(
             f2 += pr * dz - R1 * po.z;
         }
         if (cur >= 0) {
-            atomicAdd(&S.acc[0][cur], f0);
-            atomicAdd(&S.acc[1][cur], f1);
-            atomicAdd(&S.acc[2][cur], f2);
+            PA::shared_add(&S.acc[0][cur], f0);
+            PA::shared_add(&S.acc[1][cur], f1);
+            PA::shared_add(&S.acc[2][cur], f2);
         }
         __syncwarp();
-        ax += (double)S.acc[0][lane];
-        ay += (double)S.acc[1][lane];
-        az += (double)S.acc[2][lane];
+        ax += PA::to_reg(S.acc[0][lane]);
+        ay += PA::to_reg(S.acc[1][lane]);
+        az += PA::to_reg(S.acc[2][lane]);
         if (diag) {
-            ax += (double)S.acc[0][32 + lane];
-            ay += (double)S.acc[1][32 + lane];
-            az += (double)S.acc[2][32 + lane];
+            ax += PA::to_reg(S.acc[0][32 + lane]);
+            ay += PA::to_reg(S.acc[1][32 + lane]);
+            az += PA::to_reg(S.acc[2][32 + lane]);
         } else if (sj >= 0) {
-            flush3(acc, n_pad, sj, (double)S.acc[0][32 + lane], (double)S.acc[1][32 + lane],
-                   (double)S.acc[2][32 + lane]);
+            flush3<PA>(acc, n_pad, sj, PA::to_reg(S.acc[0][32 + lane]), PA::to_reg(S.acc[1][32 + lane]),
+                   PA::to_reg(S.acc[2][32 + lane]));
         }
     }
-    if (curI >= 0 && curI * 32 + lane < pc.n) flush3(acc, n_pad, curI * 32 + lane, ax, ay, az);
+    if (curI >= 0 && curI * 32 + lane < pc.n) flush3<PA>(acc, n_pad, curI * 32 + lane, ax, ay, az);
 }
 
 template <class T>
@@ -364,9 +368,10 @@ template <class T>
 int perm_field_t(ap_ctx *ctx, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PairConsts<T> pc = make_consts<T>(ctx);
-    auto kern = ctx->minimg ? k_perm_field<T, true> : k_perm_field<T, false>;
-    static int grids[2] = {0, 0};
-    int &grid = grids[ctx->minimg];
+    auto kern = ctx->fixed ? (ctx->minimg ? k_perm_field<T, true, true> : k_perm_field<T, false, true>)
+                           : (ctx->minimg ? k_perm_field<T, true, false> : k_perm_field<T, false, false>);
+    static int grids[4] = {0, 0, 0, 0};
+    int &grid = grids[ctx->minimg + 2 * ctx->fixed];
     if (!grid) grid = resident_grid(ctx, kern, 32 * pf_warps<T>());
     kern<<<grid, 32 * pf_warps<T>(), 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd,
                                              (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, ctx->acc, ctx->n_pad, pc);
@@ -378,9 +383,10 @@ template <class T>
 int matvec_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PairConsts<T> pc = make_consts<T>(ctx);
-    auto kern = ctx->minimg ? k_matvec<T, true> : k_matvec<T, false>;
-    static int grids[2] = {0, 0};
-    int &g0 = grids[ctx->minimg];
+    auto kern = ctx->fixed ? (ctx->minimg ? k_matvec<T, true, false, true> : k_matvec<T, false, false, true>)
+                           : (ctx->minimg ? k_matvec<T, true, false, false> : k_matvec<T, false, false, false>);
+    static int grids[4] = {0, 0, 0, 0};
+    int &g0 = grids[ctx->minimg + 2 * ctx->fixed];
     if (!g0) g0 = resident_grid(ctx, kern, 128);
     const int grid = std::max(ctx->sm_count, g0 / std::max(1, ctx->tune_mv_div));
     kern<<<grid, 128, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)p, ctx->acc,
@@ -393,9 +399,10 @@ template <class T>
 int short_t(ap_ctx *ctx, const void *p, double *out, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PairConsts<T> pc = make_consts<T>(ctx);
-    auto kern = ctx->minimg ? k_matvec<T, true, true> : k_matvec<T, false, true>;
-    static int grids[2] = {0, 0};
-    int &grid = grids[ctx->minimg];
+    auto kern = ctx->fixed ? (ctx->minimg ? k_matvec<T, true, true, true> : k_matvec<T, false, true, true>)
+                           : (ctx->minimg ? k_matvec<T, true, true, false> : k_matvec<T, false, true, false>);
+    static int grids[4] = {0, 0, 0, 0};
+    int &grid = grids[ctx->minimg + 2 * ctx->fixed];
     if (!grid) grid = resident_grid(ctx, kern, 128);
     kern<<<grid, 128, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)p, out,
                               ctx->n_pad, pc);
