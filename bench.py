@@ -52,6 +52,7 @@ MLP_FLOPS_PER_ATOM = 2 * (16 * 128 + 128 * 128 + 128 * 3)
 # (p, q, alpha, mu and r in/out)
 PCG_VECTOR_BYTES_PER_SLOT = 64 + 108 + 144
 WORKLOAD = "water_96000_atoms_98.7A_grid100_rc7+2_mixed_pcg1e-5"
+HEADLINE_GUESS = "learned+extrapolated"
 
 
 def captured_traffic():
@@ -199,7 +200,7 @@ def launches_per_step(iters, n, rebuild_frac, learned_guess):
     pad = 1 if n % 32 else 0
     field = 3 + 6 + pad                   # filter, worklist, pair masks, load, [pad], spread, convolve,
     #                                       gather, pair field, assemble
-    guess = 5 if learned_guess else 0     # alpha E, short-range field, features, MLP, assemble
+    guess = 6 if learned_guess else 0     # alpha E, short-range field, features, MLP, assemble, extrapolation
     solve = 1 + 4 + 2 + 1 + 7 * iters + 1  # guess, matvec(4), residual, finish, cond, 7/iter, unsort
     forces = 10
     build = 14 * rebuild_frac
@@ -239,29 +240,44 @@ def run_ours(args):
     mu0 = torch.zeros((s.n, 3), dtype=torch.float64, device=dev)
     del feat, tgt
 
-    hist = []   # converged dipoles of the two previous steps (extrapolated guess)
+    # ring buffers for the trajectory guesses: converged dipoles and learned guesses of the
+    # last three steps (written in place by the library, no copies)
+    ring_mu = [torch.zeros((s.n, 3), dtype=torch.float64, device=dev) for _ in range(3)]
+    ring_g = [torch.zeros((s.n, 3), dtype=torch.float64, device=dev) for _ in range(3)]
+    hist = {"count": 0}
 
     def step(k, xyz, use_learned, ctx=ctx):
-        """use_learned: True (MLP), False (alpha E), "zero" or "extrapolated" (2 mu_{t-1} -
-        mu_{t-2}, alpha E until two previous steps exist)."""
+        """use_learned: True (MLP), False (alpha E), "zero", "extrapolated" (2 mu(t-1) -
+        mu(t-2)) or "learned+extrapolated" (the learned guess plus the extrapolation of its
+        error over the two previous steps); the trajectory guesses fall back to alpha E or
+        the learned guess until two previous steps exist."""
         if k % REBUILD == 0:
             binding.build_neighbour_blocks(ctx.ctx, xyz, ctx.excl_off, ctx.excl_atoms, ctx.n_excl)
         binding.permanent_field(ctx.ctx, xyz, ctx.mpole, ctx.frame, ctx.alpha, None)
-        guess = None
+        guess, out = None, ctx.mu
+        ready = hist["count"] >= 2
         if use_learned is True:
             binding.ap_learned_guess(ctx.ctx, trainer.packed, mu0)
             guess = mu0
         elif use_learned == "zero":
             mu0.zero_()
             guess = mu0
-        elif use_learned == "extrapolated" and len(hist) == 2:
-            torch.sub(hist[1] * 2.0, hist[0], out=mu0)
-            guess = mu0
-        binding.induced_dipoles_pcg(ctx.ctx, guess, TOL, 200, ctx.mu, want_info=False)
-        binding.polarization_energy_forces(ctx.ctx, ctx.mu, ctx.energy, ctx.forces)
-        if use_learned == "extrapolated":
-            hist.append(ctx.mu.clone())
-            del hist[:-2]
+        elif use_learned == "extrapolated":
+            out = ring_mu[k % 3]
+            if ready:
+                binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % 3], ring_mu[(k - 2) % 3])
+                guess = mu0
+        elif use_learned == "learned+extrapolated":
+            out = ring_mu[k % 3]
+            binding.ap_learned_guess(ctx.ctx, trainer.packed, ring_g[k % 3])
+            guess = ring_g[k % 3]
+            if ready:
+                binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % 3], ring_mu[(k - 2) % 3], base=ring_g[k % 3],
+                                             base1=ring_g[(k - 1) % 3], base2=ring_g[(k - 2) % 3])
+                guess = mu0
+        binding.induced_dipoles_pcg(ctx.ctx, guess, TOL, 200, out, want_info=False)
+        binding.polarization_energy_forces(ctx.ctx, out, ctx.energy, ctx.forces)
+        hist["count"] += 1
 
     def timed(use_learned, tag, c=ctx):
         it_, ts = [], []
@@ -286,17 +302,21 @@ def run_ours(args):
 
     clocks = Clocks(local)
     clocks.start()
+    # headline: the learned guess with the trajectory extrapolation of its error
+    hist["count"] = 0
     t_wall = time.perf_counter()
-    times, iters = timed(True, "timed_steps")
+    times, iters = timed(HEADLINE_GUESS, "timed_steps")
     t_wall = time.perf_counter() - t_wall
+    times_learned, iters_learned = timed(True, "timed_steps_learned_only")
     times_plain, iters_plain = timed(False, "timed_steps_plain")
     times_zero, iters_zero = timed("zero", "timed_steps_zero")
-    hist.clear()
+    hist["count"] = 0
     times_ext, iters_ext = timed("extrapolated", "timed_steps_extrapolated")
     # the same steps in the fixed-point accumulation mode (AP_FIXED), learned guess
     ctx_fx = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=GRID, precision=binding.AP_FIXED,
                              device=dev)
-    times_fx, iters_fx = timed(True, "timed_steps_fixed", ctx_fx)
+    hist["count"] = 0
+    times_fx, iters_fx = timed(HEADLINE_GUESS, "timed_steps_fixed", ctx_fx)
     kern_fx = {k: round(binding.ap_time_kernel(ctx_fx.ctx, k, 20), 4) for k in
                ("real_matvec", "spread_dipoles", "real_field", "pair_forces", "spread_multipoles")}
     ctx_fx.close()
@@ -308,24 +328,27 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms, ms_plain = float(t[0].item()), float(t[1].item())
 
-    # end to end through the public API with host buffers: pinned positions in, forces and
-    # energy out, copies inside the timed region
-    host_pos = torch.tensor(traj[-1], dtype=torch.float64).pin_memory()
+    # end to end through the public API with host buffers: every step's positions copied in
+    # from pinned host memory, forces and energy copied out, inside the timed region; the
+    # same trajectory and guess as the headline
+    host_traj = torch.tensor(traj, dtype=torch.float64).pin_memory()
     host_f = torch.empty((s.n, 3), dtype=torch.float64).pin_memory()
     host_e = torch.empty(1, dtype=torch.float64).pin_memory()
     dev_pos = torch.empty((s.n, 3), dtype=torch.float64, device=dev)
     e2e = []
-    for k in range(args.steps):
+    hist["count"] = 0
+    for k in range(total):
         flush.fill_(k & 0xff)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        dev_pos.copy_(host_pos, non_blocking=True)
-        step(args.warmup + k, dev_pos, True)
+        dev_pos.copy_(host_traj[k], non_blocking=True)
+        step(k, dev_pos, HEADLINE_GUESS)
         host_f.copy_(ctx.forces, non_blocking=True)
         host_e.copy_(ctx.energy, non_blocking=True)
         b.record(stream)
         b.synchronize()
-        e2e.append(a.elapsed_time(b))
+        if k >= args.warmup:
+            e2e.append(a.elapsed_time(b))
     e2e_ms = float(np.mean(e2e))
 
     # dominant kernel: per-launch durations with CUDA events on the launch stream
@@ -367,12 +390,17 @@ def run_ours(args):
         "metric": METRIC, "value": round(ms, 4), "unit": "ms/step", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 pair/PME arithmetic, f64 accumulation", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "atoms": s.n, "guess": "learned (16-128-128-3 BF16 MLP)",
+        "config": {"workload": WORKLOAD, "atoms": s.n,
+                   "guess": "learned (16-128-128-3 BF16 MLP) plus the trajectory extrapolation of its error: "
+                            "learned(t) + 2 (mu - learned)(t-1) - (mu - learned)(t-2)",
                    "pcg_iters_mean": it_mean, "pcg_iters": [int(min(iters)), int(max(iters))],
                    "plain_guess": {"ms_per_step": round(ms_plain, 4), "pcg_iters_mean": float(np.mean(iters_plain)),
                                    "guess": "alpha*E"},
+                   "learned_only": {"ms_per_step": round(float(np.mean(times_learned)), 4),
+                                    "pcg_iters_mean": float(np.mean(iters_learned)),
+                                    "guess": "learned MLP alone (no history)"},
                    "fixed_point": {"ms_per_step": round(float(np.mean(times_fx)), 4),
-                                   "pcg_iters_mean": float(np.mean(iters_fx)), "guess": "learned",
+                                   "pcg_iters_mean": float(np.mean(iters_fx)), "guess": "as the headline",
                                    "accumulation": "64-bit fixed point (AP_FIXED), bitwise reproducible",
                                    "kernel_ms": kern_fx},
                    "other_guesses": {
@@ -380,8 +408,8 @@ def run_ours(args):
                                 "pcg_iters_mean": float(np.mean(iters_zero))},
                        "extrapolated": {"ms_per_step": round(float(np.mean(times_ext)), 4),
                                         "pcg_iters_mean": float(np.mean(iters_ext)),
-                                        "guess": "2 mu(t-1) - mu(t-2) from the previous steps' solves "
-                                                 "(torch elementwise op inside the timed step)"}},
+                                        "guess": "2 mu(t-1) - mu(t-2) from the previous steps' solves"},
+                       },
                    "learned_training": {"pairs": int(TRAIN_CONFIGS * s.n), "adam_steps": TRAIN_STEPS,
                                         "batch": TRAIN_BATCH, "loss_first": round(float(tr_loss[0]), 5),
                                         "loss_last": round(float(np.mean(tr_loss[-20:])), 5),

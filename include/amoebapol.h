@@ -250,6 +250,18 @@ int ap_mlp_features(ap_ctx* ctx, const double* d_mu, float* d_feat, float* d_tar
  * to pass as d_guess to induced_dipoles_pcg(). */
 int ap_learned_guess(ap_ctx* ctx, const void* d_packed, double* d_mu0);
 
+/* Initial guess from the two previous steps of a trajectory (the paper has no predictor;
+ * this is the classical extrapolation, optionally on top of a per-step base guess):
+ *   d_out = d_base + 2 (d_mu1 - d_base1) - (d_mu2 - d_base2)
+ * with d_mu1, d_mu2 the converged dipoles of steps t-1 and t-2 and d_base, d_base1, d_base2
+ * the base guesses of steps t, t-1, t-2 (e.g. ap_learned_guess() outputs). Any base pointer
+ * may be NULL for zero, so (NULL, mu1, NULL, mu2, NULL) gives 2 mu(t-1) - mu(t-2). All
+ * arrays [n][3] double, device, one common atom order; d_out may alias d_base. n >= 1.
+ * Async on `stream` (cudaStream_t, NULL = legacy default stream); AP_ERR_ARG for a NULL
+ * d_mu1, d_mu2 or d_out or n < 1, AP_ERR_CUDA if the launch fails. */
+int ap_extrapolate_guess(int n, const double* d_base, const double* d_mu1, const double* d_base1,
+                         const double* d_mu2, const double* d_base2, double* d_out, void* stream);
+
 /* Polarization energy without allocation - the paper has no counterpart; it is a
  * convenience for callers that cannot allocate device memory: code whose device memory
  * all belongs to another framework's pool, loops that forbid allocation after set-up,

@@ -24,7 +24,8 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "ap_stream", "ap_solve_info_last", "ap_time_kernel", "polarization_energy_noalloc",
            "ap_mlp_param_count", "ap_mlp_packed_bytes", "ap_mlp_pack", "ap_mlp_forward", "ap_mlp_status",
            "ap_mlp_features", "ap_learned_guess", "ap_mlp_gradient", "ap_mlp_train_step",
-           "ap_batch_create", "ap_batch_capture", "ap_batch_launch", "ap_batch_destroy", "ap_autotune")
+           "ap_batch_create", "ap_batch_capture", "ap_batch_launch", "ap_batch_destroy", "ap_autotune",
+           "ap_extrapolate_guess")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5, "pair_forces": 6,
            "pcg_vectors": 7}
@@ -78,6 +79,7 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "ap_solve_info_last": (I, [P, ctypes.POINTER(ApSolveInfo)]),
         "ap_time_kernel": (I, [P, I, I, ctypes.POINTER(D)]),
         "polarization_energy_noalloc": (I, [P, P, I, P, P]),
+        "ap_extrapolate_guess": (I, [I, P, P, P, P, P, P, P]),
         "ap_mlp_param_count": (I, []),
         "ap_mlp_packed_bytes": (I, []),
         "ap_mlp_pack": (I, [P, P, P]),
@@ -209,6 +211,17 @@ def polarization_energy_noalloc(mu, field, energy, stream=None):
         _ptr(mu, torch.float64, (n, 3), "mu"), _ptr(field, torch.float64, (n, 3), "field"), int(n),
         _ptr(energy, torch.float64, (1,), "energy"), sp)
     return _check(None, code, "polarization_energy_noalloc")
+
+
+def ap_extrapolate_guess(out, mu1, mu2, base=None, base1=None, base2=None, stream=None):
+    """out = base + 2 (mu1 - base1) - (mu2 - base2); None bases are zero (caller-order [n][3])."""
+    import torch
+    n = out.shape[0]
+    opt = lambda t, name: None if t is None else _ptr(t, torch.float64, (n, 3), name)
+    return _check(None, load().ap_extrapolate_guess(int(n), opt(base, "base"), _ptr(mu1, torch.float64, (n, 3), "mu1"),
+                                                     opt(base1, "base1"), _ptr(mu2, torch.float64, (n, 3), "mu2"),
+                                                     opt(base2, "base2"), _ptr(out, torch.float64, (n, 3), "out"),
+                                                     _stream_ptr(out, stream)), "ap_extrapolate_guess")
 
 
 def _stream_ptr(t, stream=None):
