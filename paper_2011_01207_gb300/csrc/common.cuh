@@ -95,6 +95,7 @@ struct ap_ctx {
     int *chunk_flag = nullptr;   // [cap] 1 if the chunk holds excluded pairs
     int *nchunk = nullptr;       // [n_blocks]
     int2 *work = nullptr;        // [n_blocks + cap] (I, chunk) items, chunk -1 = diagonal block
+    int *work_off = nullptr;     // [n_blocks + 1] first item of each block
     int *n_work = nullptr;       // device: [0] work items, [1] in-range pairs of the configuration
     unsigned *pmask = nullptr;   // [work][32] in-range pair bits per item (i-lane word, bit = j-lane)
     unsigned *pmask_t = nullptr; // [work][32] the transpose (j-lane word, bit = i-lane)

@@ -107,29 +107,53 @@ __global__ void __launch_bounds__(256) k_filter(
     if (lane == 0) nchunk[I] = nc;
 }
 
-// flat work list (I, -1) then (I, chunk) for every block, in block order (one CTA)
-__global__ void k_worklist(const int *__restrict__ nchunk, const int *__restrict__ tile_off, int nb,
-                           int2 *__restrict__ work, int *__restrict__ n_work) {
+// flat work list (I, -1) then (I, chunk) for every block, in block order: first the
+// offsets (exclusive scan of 1 + nchunk, one CTA), then one warp per block writes its items
+__global__ void k_work_offsets(const int *__restrict__ nchunk, int nb, int *__restrict__ off,
+                               int *__restrict__ n_work) {
     __shared__ int sums[1024];
     const int t = threadIdx.x;
     const int per = (nb + 1023) / 1024;
-    const int b = t * per, e = min(nb, b + per);
+    const int b = min(nb, t * per), e = min(nb, b + per);
     int s = 0;
     for (int k = b; k < e; ++k) s += 1 + nchunk[k];
     sums[t] = s;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        int v = t >= off ? sums[t - off] : 0;
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int v = t >= d ? sums[t - d] : 0;
         __syncthreads();
         sums[t] += v;
         __syncthreads();
     }
     int pos = sums[t] - s;
     for (int k = b; k < e; ++k) {
-        work[pos++] = make_int2(k, -1);
-        for (int c = 0; c < nchunk[k]; ++c) work[pos++] = make_int2(k, tile_off[k] + c);
+        off[k] = pos;
+        pos += 1 + nchunk[k];
     }
     if (t == 1023) *n_work = sums[1023];
+}
+
+__global__ void k_work_fill(const int *__restrict__ nchunk, const int *__restrict__ tile_off,
+                            const int *__restrict__ off, int nb, int2 *__restrict__ work) {
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (I >= nb) return;
+    const int o = off[I], nc = nchunk[I], t0 = tile_off[I];
+    if (lane == 0) work[o] = make_int2(I, -1);
+    for (int c = lane; c < nc; c += 32) work[o + 1 + c] = make_int2(I, t0 + c);
+}
+
+// transpose of a 32 x 32 bit matrix held one row per lane (bit c of lane r -> bit r of lane
+// c): five butterfly stages, each swapping the off-diagonal blocks of lanes l and l ^ j
+__device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane) {
+    const unsigned lo_masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int st = 0, j = 16; st < 5; ++st, j >>= 1) {
+        const unsigned y = __shfl_xor_sync(0xffffffffu, x, j);
+        const unsigned lo = lo_masks[st];
+        x = (lane & j) ? ((x & ~lo) | ((y >> j) & lo)) : ((x & lo) | ((y & lo) << j));
+    }
+    return x;
 }
 
 // per-item in-range pair masks at the current configuration: word (item, i-lane) has bit
@@ -170,20 +194,10 @@ __global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work,
             zj = __shfl_sync(0xffffffffu, zj, src);
         }
         pmask[(size_t)t * 32 + lane] = m;
-        // transpose: word of j-lane c has bit i-lane set for every in-range pair (i, c)
-        unsigned col = 0u;
-        for (int c = 0; c < 32; ++c) {
-            const unsigned w = __ballot_sync(0xffffffffu, (m >> c) & 1u);
-            if (lane == c) col = w;
-        }
-        pmask_t[(size_t)t * 32 + lane] = col;
+        // transposes: word of j-lane c has bit i-lane set for every pair (i, c)
+        pmask_t[(size_t)t * 32 + lane] = warp_transpose32(m, lane);
         smask[(size_t)t * 32 + lane] = ms;
-        unsigned cols = 0u;
-        for (int c = 0; c < 32; ++c) {
-            const unsigned w = __ballot_sync(0xffffffffu, (ms >> c) & 1u);
-            if (lane == c) cols = w;
-        }
-        smask_t[(size_t)t * 32 + lane] = cols;
+        smask_t[(size_t)t * 32 + lane] = warp_transpose32(ms, lane);
         int c = __popc(m);
         for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
         if (lane == 0) atomicAdd(pcount, c);
@@ -202,7 +216,8 @@ int filter_t(ap_ctx *ctx, cudaStream_t s) {
         (const T4 *)ctx->dipd, nb, rc2, (T)P.box[0], (T)P.box[1], (T)P.box[2], ctx->tshift_lo, ctx->chunk_j,
         (T4 *)ctx->chunk_pos,
         ctx->chunk_src, ctx->chunk_mask, ctx->chunk_flag, ctx->nchunk);
-    k_worklist<<<1, 1024, 0, s>>>(ctx->nchunk, ctx->tile_off, nb, ctx->work, ctx->n_work);
+    k_work_offsets<<<1, 1024, 0, s>>>(ctx->nchunk, nb, ctx->work_off, ctx->n_work);
+    k_work_fill<<<ap_grid_for((long)nb * 32, 256), 256, 0, s>>>(ctx->nchunk, ctx->tile_off, ctx->work_off, nb, ctx->work);
     AP_CUDA(cudaMemsetAsync(ctx->n_work + 1, 0, sizeof(int), s));
     const T rcm = (T)(P.cutoff * P.cutoff);
     auto km = ctx->minimg ? k_pairmask<T, true> : k_pairmask<T, false>;
@@ -234,6 +249,7 @@ int filter_alloc(ap_ctx *ctx) {
     AP_CUDA(cudaMalloc((void **)&ctx->chunk_mask, sizeof(unsigned) * 32 * cap));
     AP_CUDA(cudaMalloc((void **)&ctx->chunk_flag, sizeof(int) * cap));
     AP_CUDA(cudaMalloc((void **)&ctx->work, sizeof(int2) * (cap + ctx->n_blocks)));
+    if (!ctx->work_off) AP_CUDA(cudaMalloc((void **)&ctx->work_off, sizeof(int) * (ctx->n_blocks + 1)));
     AP_CUDA(cudaMalloc((void **)&ctx->pmask, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
     AP_CUDA(cudaMalloc((void **)&ctx->pmask_t, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
     AP_CUDA(cudaMalloc((void **)&ctx->smask, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));

@@ -92,7 +92,7 @@ template <class T>
 constexpr int fo_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
 template <class T, bool MINIMG, bool FX>
-__global__ void __launch_bounds__(128) k_pair_forces(
+__global__ void __launch_bounds__(128, 6) k_pair_forces(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq,
     const typename V4<T>::type *__restrict__ dipd, const typename V4<T>::type *__restrict__ quad0,
     const typename V4<T>::type *__restrict__ quad1, const typename V4<T>::type *__restrict__ muv,
