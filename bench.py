@@ -275,6 +275,15 @@ def run_ours(args):
                 binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % 3], ring_mu[(k - 2) % 3], base=ring_g[k % 3],
                                              base1=ring_g[(k - 1) % 3], base2=ring_g[(k - 2) % 3])
                 guess = mu0
+        elif use_learned == "learned+previous":
+            # zero-order hold of the learned guess's error: g(t) + (mu - g)(t-1)
+            out = ring_mu[k % 3]
+            binding.ap_learned_guess(ctx.ctx, trainer.packed, ring_g[k % 3])
+            guess = ring_g[k % 3]
+            if hist["count"] >= 1:
+                binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % 3], ring_mu[(k - 1) % 3], base=ring_g[k % 3],
+                                             base1=ring_g[(k - 1) % 3], base2=ring_g[(k - 1) % 3])
+                guess = mu0
         binding.induced_dipoles_pcg(ctx.ctx, guess, TOL, 200, out, want_info=False)
         binding.polarization_energy_forces(ctx.ctx, out, ctx.energy, ctx.forces)
         hist["count"] += 1
@@ -312,6 +321,8 @@ def run_ours(args):
     times_zero, iters_zero = timed("zero", "timed_steps_zero")
     hist["count"] = 0
     times_ext, iters_ext = timed("extrapolated", "timed_steps_extrapolated")
+    hist["count"] = 0
+    times_lprev, iters_lprev = timed("learned+previous", "timed_steps_learned_previous")
     # the same steps in the fixed-point accumulation mode (AP_FIXED), learned guess
     ctx_fx = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=GRID, precision=binding.AP_FIXED,
                              device=dev)
@@ -409,6 +420,9 @@ def run_ours(args):
                        "extrapolated": {"ms_per_step": round(float(np.mean(times_ext)), 4),
                                         "pcg_iters_mean": float(np.mean(iters_ext)),
                                         "guess": "2 mu(t-1) - mu(t-2) from the previous steps' solves"},
+                       "learned+previous": {"ms_per_step": round(float(np.mean(times_lprev)), 4),
+                                            "pcg_iters_mean": float(np.mean(iters_lprev)),
+                                            "guess": "learned(t) + (mu - learned)(t-1) (zero-order hold of its error)"},
                        },
                    "learned_training": {"pairs": int(TRAIN_CONFIGS * s.n), "adam_steps": TRAIN_STEPS,
                                         "batch": TRAIN_BATCH, "loss_first": round(float(tr_loss[0]), 5),
