@@ -387,7 +387,7 @@ def run_ours(args):
     hbm_peak, peak_kind = _peaks()
     flop = npairs * FLOPS_PER_PAIR_MATVEC
     achieved = flop / (kern["real_matvec"] * 1e-3) / 1e12
-    roofline = {"kernel": "real_matvec (a5 tile kernel)", "bound": "alu", "achieved": round(achieved, 3),
+    roofline = {"kernel": "real_matvec (a5 real-space pair kernel)", "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
                 "traffic": captured_traffic(), "traffic_unit": "bytes per launch (ncu, cold caches)", "flop_per_launch": flop, "pairs_in_cutoff": npairs,
                 "launch_ms": round(kern["real_matvec"], 4),

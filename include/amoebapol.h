@@ -158,8 +158,8 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
  * on the current configuration (inputs as left by the last calls), timing each launch
  * with CUDA events, and return the mean duration in ms. Overwrites scratch buffers
  * only (the stored field, dipoles and lists are untouched). Synchronizes. */
-#define AP_KERNEL_REAL_MATVEC       0   /* a5: real-space dipole-field tile kernel */
-#define AP_KERNEL_REAL_FIELD        1   /* a2: real-space permanent-field tile kernel */
+#define AP_KERNEL_REAL_MATVEC       0   /* a5: real-space dipole-field pair kernel */
+#define AP_KERNEL_REAL_FIELD        1   /* a2: real-space permanent-field pair kernel */
 #define AP_KERNEL_SPREAD_DIPOLES    2   /* a6: B-spline spread of dipoles onto the grid */
 #define AP_KERNEL_CONVOLVE          3   /* a3/a6: k-space product with B(m)C(m) */
 #define AP_KERNEL_GATHER_FIELD      4   /* a3/a6: B-spline gather of the field */

@@ -6,11 +6,13 @@
 // positions of a step are known they stay fixed for the field, every PCG matrix-vector
 // product and the forces. So at each configuration, for every block I, the atoms of its
 // partner blocks J > I that lie within r_c of I's bounding box are packed into 32-wide
-// chunks (positions pre-shifted to the periodic image next to I, padding with NaN phantoms)
-// with their exclusion bits carried over. The real-space kernels then run over
+// chunks (positions relative to block I's origin, in the periodic image next to I, padding
+// with NaN phantoms) with their exclusion bits carried over. The real-space kernels then
+// run over
 //   work = [(I, diagonal block), (I, chunk 0), (I, chunk 1), ...] for every I,
 // which keeps only ~1/4 of the candidate pairs of the block-pair tiles while preserving the
-// 32 x 32 warp tile and the shuffle rotation.
+// 32 x 32 warp tile. The in-range pair bits of every item (and their transposes) are found
+// here too, once per configuration.
 #include "common.cuh"
 
 #include <algorithm>
