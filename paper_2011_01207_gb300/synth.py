@@ -203,38 +203,49 @@ def _random_walk_chain(rng, n, box, radius, bond=1.53, angle_deg=111.0, dmin=2.2
         return True
 
     pts = np.zeros((n, 3))
-    pts[0] = center + rng.normal(size=3)
-    add(0, pts[0])
-    if n > 1:
-        d = rng.normal(size=3)
-        pts[1] = pts[0] + bond * d / np.linalg.norm(d)
-        add(1, pts[1])
-    i = 2
-    fails = 0
-    while i < n:
-        b1 = pts[i - 1] - pts[i - 2]
-        b1 /= np.linalg.norm(b1)
-        ok = False
-        for _ in range(60):
-            perp = rng.normal(size=3)
-            perp -= perp.dot(b1) * b1
-            perp /= np.linalg.norm(perp)
-            cand = pts[i - 1] + bond * (np.cos(np.pi - ang) * b1 + np.sin(np.pi - ang) * perp)
-            if np.linalg.norm(cand - center) > radius:
-                continue
-            if clear(cand, i):
-                ok = True
-                break
-        if ok:
-            pts[i] = cand
-            add(i, cand)
-            i += 1
-            fails = 0
-        else:
-            fails += 1
-            i = max(2, i - 1 - min(fails, 20))   # backtrack
-            remove_from(i)
-    return pts
+    # a walk trapped in a dense globule can backtrack for a very long time: after 40 n
+    # placement rounds it restarts from a new first bond, and gives up after 5 restarts
+    for restart in range(6):
+        if restart:
+            cells.clear()
+            for j in range(n):
+                keys[j] = None
+        pts[0] = center + rng.normal(size=3)
+        add(0, pts[0])
+        if n > 1:
+            d = rng.normal(size=3)
+            pts[1] = pts[0] + bond * d / np.linalg.norm(d)
+            add(1, pts[1])
+        i = 2
+        fails = 0
+        rounds = 0
+        while i < n and rounds < 40 * n:
+            rounds += 1
+            b1 = pts[i - 1] - pts[i - 2]
+            b1 /= np.linalg.norm(b1)
+            ok = False
+            for _ in range(60):
+                perp = rng.normal(size=3)
+                perp -= perp.dot(b1) * b1
+                perp /= np.linalg.norm(perp)
+                cand = pts[i - 1] + bond * (np.cos(np.pi - ang) * b1 + np.sin(np.pi - ang) * perp)
+                if np.linalg.norm(cand - center) > radius:
+                    continue
+                if clear(cand, i):
+                    ok = True
+                    break
+            if ok:
+                pts[i] = cand
+                add(i, cand)
+                i += 1
+                fails = 0
+            else:
+                fails += 1
+                i = max(2, i - 1 - min(fails, 20))   # backtrack
+                remove_from(i)
+        if i >= n:
+            return pts
+    raise RuntimeError(f"self-avoiding walk of {n} atoms did not finish; lower globule_density or dmin")
 
 
 def solvated_chain(n_chain: int, n_water: int, box_len: float, seed: int,
