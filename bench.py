@@ -512,6 +512,10 @@ def run_replicas(args):
     torch.cuda.synchronize()
     batch = binding.Batch(ctxs)
     batch.capture(tol=TOL, max_iter=200, packed=trainer.packed)
+    # the headline guess of the single-box benchmark: learned plus the extrapolation of its
+    # error over the two previous batch steps (history kept inside the graph)
+    batch_h = binding.Batch(ctxs)
+    batch_h.capture(tol=TOL, max_iter=200, packed=trainer.packed, history=True)
     main = torch.cuda.Stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
@@ -546,27 +550,32 @@ def run_replicas(args):
 
     clocks = Clocks(0)
     clocks.start()
+    ms_hist = timed(lambda: batch_h.launch(main))
+    iters_hist = [binding.ap_solve_info_last(c.ctx).iterations for c in ctxs]
     ms_graph = timed(lambda: batch.launch(main))
     clk = clocks.stop()
     iters = [binding.ap_solve_info_last(c.ctx).iterations for c in ctxs]
     ms_seq = timed(one_by_one)
     atoms = int(sum(s.n for s, _ in reps))
     print(json.dumps({
-        "metric": METRIC, "value": round(ms_graph, 4), "unit": "ms per batch step (64 replicas)", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_graph, 4), "higher_is_better": False,
+        "metric": METRIC, "value": round(ms_hist, 4), "unit": "ms per batch step (64 replicas)", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_hist, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair/PME arithmetic, f64 accumulation",
         "data": "synthetic",
         "config": {"workload": "replicas_64_water_sizes_648-24000_mixed_learned_pcg1e-5",
                    "replicas": len(reps), "atoms_total": atoms, "sizes": [int(s.n) for s, _ in reps],
-                   "grids": [int(g[0]) for _, g in reps], "pcg_iters": iters,
-                   "one_by_one_ms_per_batch_step": round(ms_seq, 4),
-                   "graph_speedup": round(ms_seq / ms_graph, 3),
+                   "grids": [int(g[0]) for _, g in reps], "pcg_iters": iters_hist,
+                   "guess": "learned plus the extrapolation of its error over the two previous batch steps",
+                   "learned_only": {"ms_per_batch_step": round(ms_graph, 4), "pcg_iters": iters,
+                                    "one_by_one_ms_per_batch_step": round(ms_seq, 4),
+                                    "graph_speedup": round(ms_seq / ms_graph, 3)},
                    "autotuned_shapes": tuned, "generation_s": round(t_gen, 1),
-                   "atom_steps_per_s": round(atoms / (ms_graph * 1e-3), 1),
+                   "atom_steps_per_s": round(atoms / (ms_hist * 1e-3), 1),
                    "l2": "flushed between timed steps (256 MB write)"},
         "clocks": clk,
     }))
     batch.close()
+    batch_h.close()
     for c in ctxs:
         c.close()
 

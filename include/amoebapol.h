@@ -194,6 +194,13 @@ typedef struct {
     double*       d_mu;          /* [n][3] output dipoles */
     double*       d_energy;      /* [1] output energy, or NULL to skip energy and forces */
     double*       d_forces;      /* [n][3] output forces, or NULL */
+    double*       d_hist;        /* [5][n][3] scratch for the trajectory guess, or NULL: with the
+                                    learned guess, each launch starts from the learned guess plus
+                                    the linear extrapolation of its error over the two previous
+                                    launches (ap_extrapolate_guess with base = learned guess;
+                                    the learned guess alone until two launches exist). Holds the
+                                    last two dipoles, the last two learned guesses and the guess;
+                                    ap_batch_capture() starts a new trajectory. */
 } ap_batch_step;
 int ap_batch_create(ap_batch** out, ap_ctx* const* ctxs, int n_ctx);
 int ap_batch_capture(ap_batch* b, const ap_batch_step* steps);

@@ -46,7 +46,7 @@ class ApBatchStep(ctypes.Structure):
     _fields_ = [("d_xyz", ctypes.c_void_p), ("d_mpole", ctypes.c_void_p), ("d_frame", ctypes.c_void_p),
                 ("d_alpha", ctypes.c_void_p), ("d_mlp_packed", ctypes.c_void_p), ("d_mu0", ctypes.c_void_p),
                 ("tol_debye", ctypes.c_double), ("max_iter", ctypes.c_int), ("d_mu", ctypes.c_void_p),
-                ("d_energy", ctypes.c_void_p), ("d_forces", ctypes.c_void_p)]
+                ("d_energy", ctypes.c_void_p), ("d_forces", ctypes.c_void_p), ("d_hist", ctypes.c_void_p)]
 
 
 class ApError(RuntimeError):
@@ -312,7 +312,7 @@ class Batch:
         _check(None, load().ap_batch_create(ctypes.byref(self.ptr), arr, len(self.contexts)), "ap_batch_create")
         self._keep = []
 
-    def capture(self, tol=1e-5, max_iter=200, packed=None, forces=True):
+    def capture(self, tol=1e-5, max_iter=200, packed=None, forces=True, history=False):
         steps = (ApBatchStep * len(self.contexts))()
         self._keep = []
         for k, c in enumerate(self.contexts):
@@ -323,6 +323,10 @@ class Batch:
                 mu0 = c.torch.zeros((c.n, 3), dtype=c.torch.float64, device=c.device)
                 self._keep.append(mu0)
                 st.d_mlp_packed, st.d_mu0 = packed.data_ptr(), mu0.data_ptr()
+                if history:
+                    hist = c.torch.zeros((5, c.n, 3), dtype=c.torch.float64, device=c.device)
+                    self._keep.append(hist)
+                    st.d_hist = hist.data_ptr()
             st.tol_debye, st.max_iter = float(tol), int(max_iter)
             st.d_mu = c.mu.data_ptr()
             if forces:

@@ -33,7 +33,8 @@ void free_all(ap_ctx *c) {
                     c->grid, c->cgrid, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf,
                     c->tile_off, c->chunk_j, c->chunk_pos, c->chunk_src, c->chunk_mask, c->chunk_flag, c->nchunk,
                     c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y, c->smask, c->smask_t, c->e1s,
-                    c->dg, c->stb, c->stw, c->grid_fx, c->work_off};
+                    c->dg, c->stb, c->stw, c->grid_fx, c->work_off,
+                    c->hist_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -94,6 +95,7 @@ int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
     if ((r = dalloc(ctx, &ctx->r, sizeof(double) * 3 * np))) return r;
     if ((r = dalloc(ctx, &ctx->qv, sizeof(double) * 3 * np))) return r;
     if ((r = dalloc(ctx, &ctx->dg, sizeof(double) * np))) return r;
+    if ((r = dalloc(ctx, &ctx->hist_count, sizeof(int)))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->p, 4 * es * np))) return r;
     if ((r = dalloc(ctx, &ctx->st, sizeof(PcgState)))) return r;
     if ((r = dalloc(ctx, &ctx->red_part, sizeof(double) * 3 * ((np + 255) / 256 + 1)))) return r;

@@ -132,6 +132,7 @@ struct ap_ctx {
     // PCG
     double *mu = nullptr, *r = nullptr, *qv = nullptr;   // [3][n_pad]
     double *dg = nullptr;     // [n_pad] diagonal of A: 1/alpha - self coefficient (0 for padding)
+    int *hist_count = nullptr;   // device: steps held by a batch step's trajectory history
     void *p = nullptr;        // T4 [n_pad] search direction
     PcgState *st = nullptr;   // device
     double *red_part = nullptr;   // [3 * ceil(n_pad/256)] per-block partial sums of the PCG dots

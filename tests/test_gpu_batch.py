@@ -79,3 +79,44 @@ def test_batch_graph_matches_standalone_and_relaunches():
     b.close()
     for _, c in reps:
         c.close()
+
+
+def test_batch_history_guess():
+    """With d_hist, each launch starts from the learned guess plus the linear extrapolation
+    of its error over the two previous launches (the learned guess alone before that), and
+    still converges to the standalone solution."""
+    from paper_2011_01207_gb300 import learned
+    reps = _replicas()
+    tr = learned.Trainer(seed=3)            # untrained weights: any guess is a valid start
+    for s, c in reps:
+        with torch.cuda.stream(c.stream):
+            c.permanent_field(out=False)
+    torch.cuda.synchronize()
+    b = binding.Batch([c for _, c in reps])
+    b.capture(tol=1e-6, max_iter=200, packed=tr.packed, history=True)
+    g_buf = [t for t in b._keep if t.dim() == 2]     # learned guesses, one per replica
+    h_buf = [t for t in b._keep if t.dim() == 3]     # [5][n][3] histories
+    main = torch.cuda.Stream()
+    cur = [s for s, _ in reps]
+    past = [[] for _ in reps]                       # (mu, g) per earlier launch
+    for step in range(4):
+        for k, (s, c) in enumerate(reps):
+            cur[k] = synth.perturb(cur[k], 70 + 10 * step + k)
+            c.set_positions(cur[k].xyz)
+        torch.cuda.synchronize()
+        b.launch(main)
+        torch.cuda.synchronize()
+        for k, (s, c) in enumerate(reps):
+            g, used, mu = g_buf[k].clone(), h_buf[k][4].clone(), c.mu.clone()
+            if step < 2:
+                assert torch.equal(used, g)
+            else:
+                (m1, g1), (m2, g2) = past[k][-1], past[k][-2]
+                want = g + 2.0 * (m1 - g1) - (m2 - g2)
+                assert (used - want).abs().max().item() < 1e-12
+            past[k].append((mu, g))
+            ref = _standalone(c)                    # same configuration, guess alpha E
+            assert 4.80321 * (mu - ref[1]).abs().max().item() < 1e-4
+    b.close()
+    for _, c in reps:
+        c.close()
