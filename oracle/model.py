@@ -129,6 +129,47 @@ class Oracle:
             rz = rz_new
         return mu, {"iters": it, "eps": eps, "history": hist, "converged": eps <= tol}
 
+    def jacobi_diis(self, E, guess=None, tol=1e-6, depth=6, maxiter=500):
+        """Jacobi iteration accelerated by DIIS (one of the solvers the paper's method builds
+        on, Lipparini 2014): the Jacobi map g(x) = alpha (E + T x) (the splitting
+        A = alpha^-1 - T) with Pulay's direct inversion in the iterative subspace over the
+        last `depth` steps.
+
+        Step k: y_k = g(x_k) and e_k = y_k - x_k, which equals alpha r_k with r_k = E - A x_k,
+        so the convergence measure is the PCG's (Debye RMS of alpha r); stop when it is
+        <= tol and return x_k. Otherwise take c minimising |sum_i c_i e_i| over the window
+        subject to sum_i c_i = 1 (the bordered normal equations of B_ij = e_i . e_j) and set
+        x_{k+1} = sum_i c_i y_i. depth = 1 is plain Jacobi. Returns (mu, info dict) with
+        "iters" the number of steps taken (each costs one application of T after the first)."""
+        a = self.alpha[:, None]
+        x = a * E if guess is None else np.array(guess, np.float64).reshape(self.n, 3)
+        ys, es = [], []
+        hist = []
+        it = 0
+        while True:
+            y = a * (E + self.apply_T(x))
+            e = y - x
+            eps = DEBYE * np.sqrt(np.sum(e * e) / self.n)
+            hist.append(eps)
+            if eps <= tol or it >= maxiter:
+                break
+            ys.append(y)
+            es.append(e)
+            ys, es = ys[-depth:], es[-depth:]
+            m = len(es)
+            B = np.empty((m + 1, m + 1))
+            for i in range(m):
+                for j in range(m):
+                    B[i, j] = np.sum(es[i] * es[j])
+            B[:m, m] = B[m, :m] = -1.0
+            B[m, m] = 0.0
+            rhs = np.zeros(m + 1)
+            rhs[m] = -1.0
+            c = np.linalg.solve(B, rhs)[:m]
+            x = sum(ci * yi for ci, yi in zip(c, ys))
+            it += 1
+        return x, {"iters": it, "eps": eps, "history": hist, "converged": eps <= tol}
+
     def dense_A(self):
         """A as a dense 3N x 3N matrix, column by column (tiny systems only)."""
         m = 3 * self.n
