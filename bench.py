@@ -53,6 +53,7 @@ MLP_FLOPS_PER_ATOM = 2 * (16 * 128 + 128 * 128 + 128 * 3)
 PCG_VECTOR_BYTES_PER_SLOT = 64 + 108 + 144
 WORKLOAD = "water_96000_atoms_98.7A_grid100_rc7+2_mixed_pcg1e-5"
 HEADLINE_GUESS = "learned+extrapolated"
+DIIS_DEPTH = 6          # window of the Jacobi/DIIS solver timed beside the PCG
 
 
 def captured_traffic():
@@ -246,7 +247,7 @@ def run_ours(args):
     ring_g = [torch.zeros((s.n, 3), dtype=torch.float64, device=dev) for _ in range(3)]
     hist = {"count": 0}
 
-    def step(k, xyz, use_learned, ctx=ctx):
+    def step(k, xyz, use_learned, ctx=ctx, solver="pcg"):
         """use_learned: True (MLP), False (alpha E), "zero", "extrapolated" (2 mu(t-1) -
         mu(t-2)) or "learned+extrapolated" (the learned guess plus the extrapolation of its
         error over the two previous steps); the trajectory guesses fall back to alpha E or
@@ -284,14 +285,17 @@ def run_ours(args):
                 binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % 3], ring_mu[(k - 1) % 3], base=ring_g[k % 3],
                                              base1=ring_g[(k - 1) % 3], base2=ring_g[(k - 1) % 3])
                 guess = mu0
-        binding.induced_dipoles_pcg(ctx.ctx, guess, TOL, 200, out, want_info=False)
+        if solver == "diis":
+            binding.induced_dipoles_diis(ctx.ctx, guess, TOL, 200, DIIS_DEPTH, out, want_info=False)
+        else:
+            binding.induced_dipoles_pcg(ctx.ctx, guess, TOL, 200, out, want_info=False)
         binding.polarization_energy_forces(ctx.ctx, out, ctx.energy, ctx.forces)
         hist["count"] += 1
 
-    def timed(use_learned, tag, c=ctx):
+    def timed(use_learned, tag, c=ctx, solver="pcg"):
         it_, ts = [], []
         for k in range(args.warmup):
-            step(k, pos[k], use_learned, c)
+            step(k, pos[k], use_learned, c, solver)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -300,7 +304,7 @@ def run_ours(args):
             flush.fill_(k & 0xff)                                    # untimed: evict the L2
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(k, pos[k], use_learned, c)
+            step(k, pos[k], use_learned, c, solver)
             b.record(stream)
             b.synchronize()
             ts.append(a.elapsed_time(b))
@@ -323,6 +327,9 @@ def run_ours(args):
     times_ext, iters_ext = timed("extrapolated", "timed_steps_extrapolated")
     hist["count"] = 0
     times_lprev, iters_lprev = timed("learned+previous", "timed_steps_learned_previous")
+    # the same steps with the Jacobi/DIIS solver in place of the PCG
+    hist["count"] = 0
+    times_diis, iters_diis = timed(HEADLINE_GUESS, "timed_steps_diis", solver="diis")
     # the same steps in the fixed-point accumulation mode (AP_FIXED), learned guess
     ctx_fx = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=GRID, precision=binding.AP_FIXED,
                              device=dev)
@@ -414,6 +421,12 @@ def run_ours(args):
                                    "pcg_iters_mean": float(np.mean(iters_fx)), "guess": "as the headline",
                                    "accumulation": "64-bit fixed point (AP_FIXED), bitwise reproducible",
                                    "kernel_ms": kern_fx},
+                   "other_solvers": {
+                       "jacobi_diis": {"ms_per_step": round(float(np.mean(times_diis)), 4),
+                                       "updates_mean": float(np.mean(iters_diis)), "depth": DIIS_DEPTH,
+                                       "t_applications_mean": float(np.mean(iters_diis)) + 1,
+                                       "guess": "as the headline"},
+                       "pcg": {"t_applications_mean": it_mean + 1}},
                    "other_guesses": {
                        "zero": {"ms_per_step": round(float(np.mean(times_zero)), 4),
                                 "pcg_iters_mean": float(np.mean(iters_zero))},

@@ -67,7 +67,8 @@ typedef struct {
 } ap_params;
 
 typedef struct {
-    int    iterations;    /* PCG iterations performed (matrix-vector products after the initial residual) */
+    int    iterations;    /* PCG iterations performed (matrix-vector products after the initial residual),
+                             or DIIS updates taken */
     int    status;        /* AP_OK or AP_NOT_CONVERGED */
     double eps_debye;     /* final RMS of alpha_i r_i in Debye (the convergence measure) */
     double eps_initial;   /* the same measure for the initial guess */
@@ -129,6 +130,30 @@ int permanent_field(ap_ctx* ctx, const double* d_xyz, const double* d_mpole,
 int induced_dipoles_pcg(ap_ctx* ctx, const double* d_guess, double tol_debye, int max_iter,
                         double* d_mu, ap_solve_info* h_info);
 
+/* Longest DIIS window induced_dipoles_diis accepts. */
+#define AP_DIIS_MAX_DEPTH 8
+
+/* f3 - Jacobi iteration with DIIS extrapolation, an alternative solver of the same system
+ * A mu = E (Sec. 1.3; A = alpha^-1 - T as for the PCG). Step k forms the Jacobi update
+ * y_k = alpha (E + T x_k) and its error e_k = y_k - x_k = alpha r_k, stops when
+ * eps = 4.80321 sqrt(sum |e_k|^2 / n) <= tol_debye (the PCG's measure) and returns x_k;
+ * otherwise x_{k+1} = sum_i c_i y_i over the last `depth` steps, c minimising
+ * |sum_i c_i e_i| subject to sum_i c_i = 1 (Pulay's DIIS). Where the window's bordered
+ * system is singular the oldest entries are dropped until it is not (one entry: a plain
+ * Jacobi step). depth = 1 is plain Jacobi iteration.
+ *   d_guess   [n][3] double initial dipoles, or NULL for x_0 = alpha E.
+ *   tol_debye convergence threshold, Debye (> 0).
+ *   max_iter  limit on the extrapolated updates (>= 1); at most max_iter + 1 applications of T.
+ *   depth     DIIS window, 1 .. AP_DIIS_MAX_DEPTH.
+ *   d_mu      [n][3] double output dipoles, e*A.
+ *   h_info    optional host struct (iterations = updates taken); when non-NULL the call
+ *             synchronizes.
+ * The first call allocates 2 * depth vectors of 3 * n doubles (kept by the context and grown
+ * when a later call asks for a longer window); the call cannot be captured into a graph.
+ * Returns AP_NOT_CONVERGED (> 0) when max_iter was reached (reported only with h_info). */
+int induced_dipoles_diis(ap_ctx* ctx, const double* d_guess, double tol_debye, int max_iter,
+                         int depth, double* d_mu, ap_solve_info* h_info);
+
 /* a9 - Polarization energy and forces at fixed dipoles (variational):
  * E_pol = -(f/2) sum_i mu_i . E_i with f = 332.063713, and F = -dE_pol/dx including the
  * reciprocal-space terms and the forces on frame atoms from multipole rotation.
@@ -150,8 +175,8 @@ int ap_list_stats(const ap_ctx* ctx, int* h_blocks, int* h_tiles, int* h_excl_ti
 /* The stream the context enqueues on (cudaStream_t). */
 void* ap_stream(const ap_ctx* ctx);
 
-/* Iterations and residuals of the most recent induced_dipoles_pcg() on this context.
- * Synchronizes the context's stream. */
+/* Iterations and residuals of the most recent induced_dipoles_pcg() or
+ * induced_dipoles_diis() on this context. Synchronizes the context's stream. */
 int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 
 /* Benchmark support: launch one kernel of the path `reps` times on the context's stream

@@ -25,7 +25,7 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "ap_mlp_param_count", "ap_mlp_packed_bytes", "ap_mlp_pack", "ap_mlp_forward", "ap_mlp_status",
            "ap_mlp_features", "ap_learned_guess", "ap_mlp_gradient", "ap_mlp_train_step",
            "ap_batch_create", "ap_batch_capture", "ap_batch_launch", "ap_batch_destroy", "ap_autotune",
-           "ap_extrapolate_guess")
+           "ap_extrapolate_guess", "induced_dipoles_diis")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5, "pair_forces": 6,
            "pcg_vectors": 7}
@@ -72,6 +72,7 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "build_neighbour_blocks": (I, [P, P, P, P, I]),
         "permanent_field": (I, [P, P, P, P, P, P]),
         "induced_dipoles_pcg": (I, [P, P, D, I, P, ctypes.POINTER(ApSolveInfo)]),
+        "induced_dipoles_diis": (I, [P, P, D, I, I, P, ctypes.POINTER(ApSolveInfo)]),
         "polarization_energy_forces": (I, [P, P, P, P]),
         "dipole_field_matvec": (I, [P, P, P]),
         "ap_list_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -165,6 +166,17 @@ def induced_dipoles_pcg(ctx, guess, tol_debye: float, max_iter: int, mu, want_in
         ctx, _ptr(guess, torch.float64, (n, 3), "guess", allow_none=True), float(tol_debye), int(max_iter),
         _ptr(mu, torch.float64, (n, 3), "mu"), ctypes.byref(info) if want_info else None)
     _check(ctx, code, "induced_dipoles_pcg")
+    return info if want_info else None
+
+
+def induced_dipoles_diis(ctx, guess, tol_debye: float, max_iter: int, depth: int, mu, want_info: bool = True):
+    import torch
+    n = mu.shape[0]
+    info = ApSolveInfo()
+    code = load().induced_dipoles_diis(
+        ctx, _ptr(guess, torch.float64, (n, 3), "guess", allow_none=True), float(tol_debye), int(max_iter),
+        int(depth), _ptr(mu, torch.float64, (n, 3), "mu"), ctypes.byref(info) if want_info else None)
+    _check(ctx, code, "induced_dipoles_diis")
     return info if want_info else None
 
 
@@ -406,6 +418,9 @@ class Context:
 
     def solve(self, tol=1e-5, max_iter=200, guess=None, want_info=True):
         return induced_dipoles_pcg(self.ctx, guess, tol, max_iter, self.mu, want_info)
+
+    def solve_diis(self, tol=1e-5, max_iter=200, depth=6, guess=None, want_info=True):
+        return induced_dipoles_diis(self.ctx, guess, tol, max_iter, depth, self.mu, want_info)
 
     def energy_forces(self, mu=None):
         polarization_energy_forces(self.ctx, self.mu if mu is None else mu, self.energy, self.forces)

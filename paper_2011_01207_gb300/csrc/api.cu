@@ -37,6 +37,7 @@ void free_all(ap_ctx *c) {
                     c->hist_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    diis_release(c);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->plan_r2c) cufftDestroy(c->plan_r2c);
     if (c->plan_c2r) cufftDestroy(c->plan_c2r);
@@ -202,7 +203,20 @@ int induced_dipoles_pcg(ap_ctx *ctx, const double *d_guess, double tol_debye, in
     if (!d_mu) return ap_fail(ctx, AP_ERR_ARG, "d_mu is NULL");
     if (!(tol_debye > 0) || max_iter < 1) return ap_fail(ctx, AP_ERR_ARG, "tol_debye must be > 0 and max_iter >= 1");
     if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
+    ctx->last_solver = 0;
     return pcg_solve(ctx, d_guess, tol_debye, max_iter, d_mu, h_info);
+}
+
+int induced_dipoles_diis(ap_ctx *ctx, const double *d_guess, double tol_debye, int max_iter, int depth,
+                         double *d_mu, ap_solve_info *h_info) {
+    if (!ctx) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!d_mu) return ap_fail(ctx, AP_ERR_ARG, "d_mu is NULL");
+    if (!(tol_debye > 0) || max_iter < 1) return ap_fail(ctx, AP_ERR_ARG, "tol_debye must be > 0 and max_iter >= 1");
+    if (depth < 1 || depth > AP_DIIS_MAX_DEPTH) return ap_fail(ctx, AP_ERR_ARG, "depth must be in 1 .. AP_DIIS_MAX_DEPTH");
+    if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
+    ctx->last_solver = 1;
+    return diis_solve(ctx, d_guess, tol_debye, max_iter, depth, d_mu, h_info);
 }
 
 int polarization_energy_forces(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
@@ -234,6 +248,10 @@ void *ap_stream(const ap_ctx *ctx) { return ctx ? (void *)ctx->s0 : nullptr; }
 int ap_solve_info_last(ap_ctx *ctx, ap_solve_info *h_info) {
     if (!ctx || !h_info) return AP_ERR_ARG;
     ctx->err.clear();
+    if (ctx->last_solver == 1) {
+        const int rc = diis_info(ctx, h_info);
+        return rc < 0 ? rc : AP_OK;
+    }
     AP_CUDA(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, ctx->s0));
     AP_CUDA(cudaStreamSynchronize(ctx->s0));
     h_info->iterations = ctx->st_host->iter;

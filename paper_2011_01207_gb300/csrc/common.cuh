@@ -161,6 +161,15 @@ struct ap_ctx {
     // launch shapes chosen by ap_autotune (0 = default)
     int tune_mv_div = 1;      // matvec grid = resident CTAs / tune_mv_div
     int tune_pme_threads = 128;
+    // Jacobi/DIIS solver (allocated by its first call)
+    void *diis_st = nullptr;         // device state: window matrix, coefficients, convergence
+    void *diis_st_host = nullptr;    // pinned mirror
+    double *diis_y = nullptr;        // [depth][3][n_pad] ring of Jacobi updates y_k
+    double *diis_e = nullptr;        // [depth][3][n_pad] ring of their errors e_k
+    double *diis_part = nullptr;     // [AP_DIIS_MAX_DEPTH][blocks] partial dots
+    int diis_cap = 0;                // window length the rings hold
+    int last_solver = 0;             // 0: the last solve was the PCG, 1: Jacobi/DIIS
+    cudaGraphExec_t diis_exec = nullptr;
     // graph of the solve loop
     cudaGraphExec_t solve_exec = nullptr;
     int graph_ok = 0;         // 1 when the conditional-while graph is usable
@@ -237,3 +246,7 @@ int field_finish(ap_ctx *ctx, double *d_field_out);
 int pcg_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double *d_mu,
               ap_solve_info *info);
 int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces);
+int diis_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, int depth, double *d_mu,
+               ap_solve_info *info);
+void diis_release(ap_ctx *ctx);
+int diis_info(ap_ctx *ctx, ap_solve_info *info);   // state of the last DIIS solve; synchronizes

@@ -445,6 +445,13 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
 
 }  // namespace
 
+// T applied to ctx->p (real space on `main`, reciprocal on `aux`, joined into `main`), into
+// ctx->acc and ctx->rec; for other solvers of the same system
+int dipole_operator_into(ap_ctx *ctx, cudaStream_t main, cudaStream_t aux) {
+    return ctx->prec == AP_FP64 ? matvec_into<double>(ctx, ctx->p, main, aux)
+                                : matvec_into<float>(ctx, ctx->p, main, aux);
+}
+
 // one iteration's vector work (direction, q = A p with its p.q reduction, update with its
 // r.z / z.z reduction) on `s`, for timing; it advances the last solve's state
 int pcg_vectors_launch(ap_ctx *ctx, cudaStream_t s) {
