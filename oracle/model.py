@@ -13,7 +13,10 @@ Readings where the paper is silent:
     mutual scale 1 for every pair;
   * PCG: M^-1 = diag(alpha); convergence measure eps = 4.80321 sqrt(sum_i |alpha_i r_i|^2 / N)
     (Debye RMS of the preconditioned residual); stop when eps <= tol;
-  * E_pol = -(f/2) sum_i mu_i . E_i ; forces are -dE_pol/dx at fixed mu (variational).
+  * E_pol = -(f/2) sum_i mu_i . E_i ; forces are -dE_pol/dx at fixed mu (variational);
+  * two dipole sets (AMOEBA's d and p, the three scale factors of Sec. 2.3): E_d and E_p
+    use the direct and the polarization scale factors of the listed pairs, T uses scale 1;
+    mu_d = A^-1 E_d, mu_p = A^-1 E_p; E_pol = -(f/2) sum_i mu_d,i . E_p,i.
 Modes: 'spme' (the GPU's method), 'exact' (classical Ewald k-sum), 'open' (isolated
 cluster: beta = 0, no reciprocal or self terms, all pairs).
 """
@@ -45,7 +48,9 @@ class Params:
 class Oracle:
     """FP64 reference for one configuration of a System-like object."""
 
-    def __init__(self, sysobj, params: Params, xyz=None):
+    def __init__(self, sysobj, params: Params, xyz=None, dp=None):
+        """dp = (pairs [M,2], scales [M,2]): AMOEBA's direct (d) and polarization (p) scale
+        factors of the listed pairs (others 1), for the two-dipole-set methods (*_dp)."""
         self.s = sysobj
         self.p = params
         self.xyz = np.asarray(sysobj.xyz if xyz is None else xyz, np.float64)
@@ -65,6 +70,11 @@ class Oracle:
                 self.I, self.J, self.R = pairs.pairs_min_image(self.xyz, self.box, params.cutoff)
             self.sigma = pairs.scale_of_pairs(self.I, self.J, sysobj.excl, self.n, self.R, self.box)
         self.beta = 0.0 if params.mode == "open" else params.beta
+        if dp is not None:
+            tp, tv = np.asarray(dp[0]), np.asarray(dp[1], np.float64)
+            img = (None, None) if params.mode == "open" else (self.R, self.box)
+            self.sigma_d = pairs.scales_from_table(self.I, self.J, tp, tv[:, 0], self.n, *img)
+            self.sigma_p = pairs.scales_from_table(self.I, self.J, tp, tv[:, 1], self.n, *img)
 
     # ---- reciprocal part -------------------------------------------------------------
     def recip(self, q, dip, quad, order):
@@ -170,6 +180,95 @@ class Oracle:
             it += 1
         return x, {"iters": it, "eps": eps, "history": hist, "converged": eps <= tol}
 
+    # ---- AMOEBA's two induced-dipole sets (d and p) ----------------------------------
+    def permanent_field_dp(self):
+        """(E_d, E_p): the permanent field with the direct and the polarization scale
+        factors in real space; the reciprocal and self parts are unscaled and shared."""
+        rec = -self.recip(self.q, self.dip, self.quad, 1)[1] + self.p.self_coef * self.dip
+        out = []
+        for sig in (self.sigma_d, self.sigma_p):
+            E = realspace.real_field(self.n, self.I, self.J, self.R, sig, self.q, self.dip,
+                                     self.quad, self.alpha, self.beta, self.p.thole_a)
+            out.append(E + rec)
+        return out[0], out[1]
+
+    def pcg_dp(self, E_d, E_p, guess_d=None, guess_p=None, tol=1e-6, maxiter=500):
+        """A mu_d = E_d and A mu_p = E_p by two diagonal-preconditioned CG recurrences run
+        in lockstep (one iteration updates both) until the larger of the two convergence
+        measures is <= tol. A recurrence whose r.z is exactly zero is left as it is.
+        Returns (mu_d, mu_p, info) with info["iters"], info["eps"] = the larger measure,
+        and info["eps_d"], info["eps_p"]."""
+        a = self.alpha[:, None]
+        mus, rs, ps, rzs = [], [], [], []
+        for E, g in ((E_d, guess_d), (E_p, guess_p)):
+            mu = a * E if g is None else np.array(g, np.float64).reshape(self.n, 3)
+            r = E - self.apply_A(mu)
+            mus.append(mu)
+            rs.append(r)
+            ps.append(a * r)
+            rzs.append(np.sum(r * a * r))
+        epsk = [self.residual_eps(r) for r in rs]
+        it = 0
+        while max(epsk) > tol and it < maxiter:
+            for k in range(2):
+                if rzs[k] == 0.0:
+                    continue
+                qv = self.apply_A(ps[k])
+                gamma = rzs[k] / np.sum(ps[k] * qv)
+                mus[k] = mus[k] + gamma * ps[k]
+                rs[k] = rs[k] - gamma * qv
+            it += 1
+            epsk = [self.residual_eps(r) for r in rs]
+            if max(epsk) <= tol:
+                break
+            for k in range(2):
+                if rzs[k] == 0.0:
+                    continue
+                z = a * rs[k]
+                rz_new = np.sum(rs[k] * z)
+                ps[k] = z + (rz_new / rzs[k]) * ps[k]
+                rzs[k] = rz_new
+        return mus[0], mus[1], {"iters": it, "eps": max(epsk), "eps_d": epsk[0], "eps_p": epsk[1],
+                                "converged": max(epsk) <= tol}
+
+    @staticmethod
+    def energy_dp(mu_d, E_p):
+        """E_pol = -(f/2) sum_i mu_d,i . E_p,i (d-set dipoles in the p-scaled field)."""
+        return -0.5 * F_COUL * float(np.sum(mu_d * E_p))
+
+    def forces_dp(self, mu_d, mu_p):
+        """-dE_pol/dx of E_pol = -(f/2) mu_d . E_p with mu_d = A^-1 E_d and mu_p = A^-1 E_p
+        (converged): -(f/2) [mu_p . dE_d + mu_d . dE_p + mu_p . dT mu_d], including the
+        multipole frames' rotation. Reciprocal part, with mu_s = (mu_d + mu_p)/2 and phi_X
+        the reciprocal potential of sources X:
+            U_rec = f mu_s . grad phi_M + (f/2) mu_p . grad phi_{mu_d}
+        whose gradient is f [H(phi_M) mu_s + q grad phi_s + H(phi_s) d + D3(phi_s):Q/3]
+        + (f/2) [H(phi_d) mu_p + H(phi_p) mu_d]."""
+        f = F_COUL
+        mu_d = np.asarray(mu_d, np.float64).reshape(self.n, 3)
+        mu_p = np.asarray(mu_p, np.float64).reshape(self.n, 3)
+        grad, g_dip, g_quad = realspace.real_forces_dp(
+            self.n, self.I, self.J, self.R, self.sigma_d, self.sigma_p, self.q, self.dip, self.quad,
+            self.alpha, mu_d, mu_p, self.beta, self.p.thole_a, f)
+        if self.p.mode != "open":
+            zq, zQ = np.zeros(self.n), np.zeros((self.n, 3, 3))
+            mu_s = 0.5 * (mu_d + mu_p)
+            phM = self.recip(self.q, self.dip, self.quad, 2)
+            phS = self.recip(zq, mu_s, zQ, 3)
+            phD = self.recip(zq, mu_d, zQ, 2)
+            phP = self.recip(zq, mu_p, zQ, 2)
+            grad += f * (np.einsum("nab,nb->na", phM[2], mu_s)
+                         + self.q[:, None] * phS[1]
+                         + np.einsum("nab,nb->na", phS[2], self.dip)
+                         + np.einsum("nabc,nbc->na", phS[3], self.quad) / 3.0)
+            grad += 0.5 * f * (np.einsum("nab,nb->na", phD[2], mu_p) + np.einsum("nab,nb->na", phP[2], mu_d))
+            g_dip += f * phS[1]
+            g_quad += (f / 3.0) * phS[2]
+            g_dip += -f * self.p.self_coef * mu_s
+        grad += frames.frame_gradient(self.xyz, self.box, self.s.frame, self.s.dip, self.s.quad,
+                                      g_dip, g_quad)
+        return -grad
+
     def dense_A(self):
         """A as a dense 3N x 3N matrix, column by column (tiny systems only)."""
         m = 3 * self.n
@@ -227,6 +326,15 @@ def solve_energy(sysobj, params, xyz=None, tol=1e-11):
     E = o.permanent_field()
     mu, _ = o.pcg(E, tol=tol, maxiter=2000)
     return o.energy(mu, E)
+
+
+def solve_energy_dp(sysobj, params, dp, xyz=None, tol=1e-11):
+    """E_pol = -(f/2) mu_d . E_p with both dipole sets converged tightly (finite-difference
+    checks of forces_dp)."""
+    o = Oracle(sysobj, params, xyz, dp=dp)
+    E_d, E_p = o.permanent_field_dp()
+    mu_d, _, _ = o.pcg_dp(E_d, E_p, tol=tol, maxiter=2000)
+    return o.energy_dp(mu_d, E_p)
 
 
 def row_fields(sysobj, params, rows, vec=None):

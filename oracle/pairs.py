@@ -83,3 +83,27 @@ def scale_of_pairs(I, J, excl, n, R=None, box=None):
         mi = R - box * np.round(R / box)
         hit &= np.all(np.abs(mi - R) < 1e-9, axis=1)
     return np.where(hit, 0.0, 1.0)
+
+
+def scales_from_table(I, J, table_pairs, table_values, n, R=None, box=None):
+    """Per-pair scale factor looked up in a table of unordered pairs (i, j) with values;
+    pairs not in the table get 1. With R and box given, only the minimum image of a listed
+    pair takes the table value (as in scale_of_pairs)."""
+    out = np.ones(len(I))
+    if len(table_pairs) == 0:
+        return out
+    a = np.minimum(table_pairs[:, 0], table_pairs[:, 1]).astype(np.int64)
+    b = np.maximum(table_pairs[:, 0], table_pairs[:, 1]).astype(np.int64)
+    keys = a * n + b
+    order = np.argsort(keys)
+    keys, vals = keys[order], np.asarray(table_values, np.float64)[order]
+    lo = np.minimum(I, J).astype(np.int64)
+    hi = np.maximum(I, J).astype(np.int64)
+    k = lo * n + hi
+    pos = np.clip(np.searchsorted(keys, k), 0, len(keys) - 1)
+    hit = keys[pos] == k
+    if R is not None:
+        mi = R - box * np.round(R / box)
+        hit &= np.all(np.abs(mi - R) < 1e-9, axis=1)
+    out[hit] = vals[pos[hit]]
+    return out

@@ -109,3 +109,55 @@ def real_forces(n, I, J, R, sigma, q, dip, quad, alpha, mu, beta, thole_a, fcons
                         + (Rd[2] * mir / 3.0)[:, None, None] * np.einsum("pa,pb->pab", Rs, Rs))
         np.add.at(g_quad, Jj, gq)
     return grad, g_dip, g_quad
+
+
+def real_forces_dp(n, I, J, R, sigma_d, sigma_p, q, dip, quad, alpha, mu_d, mu_p, beta, thole_a, fconst):
+    """Real-space part of the polarization gradient with AMOEBA's two induced-dipole sets:
+    mu_d induced by the direct field (pair scale sigma_d), mu_p by the polarization field
+    (sigma_p), mutual scale 1. Each ordered pair (I, J) carries
+        U_IJ = -(f/2) [mu_p,I . E(R; M_J, sigma_d) + mu_d,I . E(R; M_J, sigma_p)]
+               -(f/2) mu_p,I . T(R) mu_d,J,
+    whose sum over ordered pairs is the position-dependent real-space part of
+    -(f/2) mu_d . E_p at fixed dipoles, with the response of mu_d folded in through mu_p
+    (A symmetric). With sigma_d = sigma_p and mu_d = mu_p it is real_forces' U_IJ.
+    Returns (dU/dx, dU/d(global dipole), dU/d(global quadrupole))."""
+    grad = np.zeros((n, 3))
+    g_dip = np.zeros((n, 3))
+    g_quad = np.zeros((n, 3, 3))
+    h = 0.5 * fconst
+    for s in _chunks(len(I)):
+        Rs = R[s]
+        r = np.linalg.norm(Rs, axis=1)
+        Ii, Jj = I[s], J[s]
+        Rd = damped_r(r, beta, alpha[Ii], alpha[Jj], thole_a, sigma_d[s], nmax=4)
+        Rp = damped_r(r, beta, alpha[Ii], alpha[Jj], thole_a, sigma_p[s], nmax=4)
+        Ru = damped_r(r, beta, alpha[Ii], alpha[Jj], thole_a, 1.0, nmax=3)
+        pI, dI = mu_p[Ii], mu_d[Ii]
+        dJ = mu_d[Jj]
+        Gd = multipole_field_gradient(Rs, Rd, q[Jj], dip[Jj], quad[Jj])
+        Gp = multipole_field_gradient(Rs, Rp, q[Jj], dip[Jj], quad[Jj])
+        gR = -h * (np.einsum("pab,pb->pa", Gd, pI) + np.einsum("pab,pb->pa", Gp, dI))
+        # mutual: gradient of mu_p,I . T mu_d,J
+        pd = np.einsum("pa,pa->p", pI, dJ)
+        pr = np.einsum("pa,pa->p", pI, Rs)
+        dr = np.einsum("pa,pa->p", dJ, Rs)
+        dT = ((Ru[1] * pd - Ru[2] * pr * dr)[:, None] * Rs
+              + Ru[1][:, None] * (pI * dr[:, None] + dJ * pr[:, None]))
+        gR += -h * dT
+        np.add.at(grad, Ii, gR)
+        np.add.at(grad, Jj, -gR)
+        # dependence on the source multipole J: d(mu . E)/d d_J = -R1 mu + R2 (mu.R) R,
+        # d(mu . E)/d Q_J = -(R2/3) sym(mu R^T) + (R3/3)(mu.R) R R^T
+        dIr = np.einsum("pa,pa->p", dI, Rs)
+        gd = (-Rd[0][:, None] * pI + (Rd[1] * pr)[:, None] * Rs
+              - Rp[0][:, None] * dI + (Rp[1] * dIr)[:, None] * Rs)
+        np.add.at(g_dip, Jj, -h * gd)
+        RR = np.einsum("pa,pb->pab", Rs, Rs)
+        symp = np.einsum("pa,pb->pab", pI, Rs)
+        symp = symp + np.swapaxes(symp, 1, 2)
+        symd = np.einsum("pa,pb->pab", dI, Rs)
+        symd = symd + np.swapaxes(symd, 1, 2)
+        gq = (-(Rd[1] / 3.0)[:, None, None] * symp + (Rd[2] * pr / 3.0)[:, None, None] * RR
+              - (Rp[1] / 3.0)[:, None, None] * symd + (Rp[2] * dIr / 3.0)[:, None, None] * RR)
+        np.add.at(g_quad, Jj, -h * gq)
+    return grad, g_dip, g_quad

@@ -341,3 +341,77 @@ def replica_sizes(n_rep: int, lo: int, hi: int, seed: int):
     """Seeded replica sizes (atoms, rounded down to whole waters) uniform in [lo, hi]."""
     rng = np.random.default_rng(seed)
     return (rng.integers(lo, hi + 1, n_rep) // 3 * 3).astype(np.int64)
+
+
+# AMOEBA's scale factors of the two induced-dipole sets (force-field inputs, not part of
+# the method's arithmetic): the direct field (d) is scaled by 0 between atoms of the same
+# polarization group; the polarization field (p) by 0 for 1-2 and 1-3 pairs and by 1/2 for
+# 1-4 pairs inside one group; every other pair, and the mutual field, by 1.
+D_SCALE_SAME_GROUP = 0.0
+P_SCALE_12_13 = 0.0
+P_SCALE_14_SAME_GROUP = 0.5
+
+
+def polarization_groups(sys: System, seed: int, lo: int = 3, hi: int = 6) -> np.ndarray:
+    """Group index per atom: every water is one group; the chain (consecutive atoms of
+    molecule 0 that are not rigid) is cut into consecutive runs of U[lo, hi] atoms."""
+    rng = np.random.default_rng(seed)
+    rigid = sys.rigid if sys.rigid is not None else np.zeros(sys.n, np.int32)
+    chain = np.nonzero(rigid == 0)[0]
+    grp = np.empty(sys.n, np.int64)
+    g, k = 0, 0
+    while k < len(chain):
+        m = int(rng.integers(lo, hi + 1))
+        grp[chain[k:k + m]] = g
+        g += 1
+        k += m
+    water = np.nonzero(rigid == 1)[0]
+    if len(water):
+        grp[water] = g + (sys.mol[water] - sys.mol[water].min())
+    return grp
+
+
+def dp_scales(sys: System, groups: np.ndarray):
+    """Pairs whose d or p scale differs from 1, with (d, p) scales: (pairs [M,2] int32 with
+    i < j, scales [M,2] float64). Bonds: chain atoms k, k+1 and water O-H; 1-3 and 1-4
+    pairs follow along the chain, and H-H inside a water."""
+    rigid = sys.rigid if sys.rigid is not None else np.zeros(sys.n, np.int32)
+    chain = np.nonzero(rigid == 0)[0]
+    table = {}
+
+    def put(i, j, d, p):
+        a, b = (int(i), int(j)) if i < j else (int(j), int(i))
+        table[(a, b)] = (d, p)
+
+    for sep in (1, 2, 3):
+        for a, b in zip(chain[:-sep], chain[sep:]):
+            same = groups[a] == groups[b]
+            d = D_SCALE_SAME_GROUP if same else 1.0
+            p = P_SCALE_12_13 if sep < 3 else (P_SCALE_14_SAME_GROUP if same else 1.0)
+            if (d, p) != (1.0, 1.0):
+                put(a, b, d, p)
+    # same-group chain pairs beyond 1-4: d scaled only
+    for g in np.unique(groups[chain]) if len(chain) else ():
+        mem = chain[groups[chain] == g]
+        for x in range(len(mem)):
+            for y in range(x + 1, len(mem)):
+                if (min(mem[x], mem[y]), max(mem[x], mem[y])) not in table:
+                    put(mem[x], mem[y], D_SCALE_SAME_GROUP, 1.0)
+    # waters: O-H (1-2) and H-H (1-3), one group each
+    for a, b in sys.excl:
+        if rigid[a] == 1 and rigid[b] == 1:
+            put(a, b, D_SCALE_SAME_GROUP, P_SCALE_12_13)
+    keys = sorted(table)
+    pairs = np.array(keys, np.int32).reshape(-1, 2)
+    scales = np.array([table[k] for k in keys], np.float64).reshape(-1, 2)
+    return pairs, scales
+
+
+def dp_system(sys: System, seed: int, lo: int = 3, hi: int = 6):
+    """(system, pairs, scales) for the two-dipole-set path: a copy of `sys` whose exclusion
+    list is the set of scaled pairs (the pairs the pair kernels leave to the scaled-pair
+    corrections), and the d/p scale table from dp_scales."""
+    pairs, scales = dp_scales(sys, polarization_groups(sys, seed, lo, hi))
+    out = sys.copy()
+    out.excl = pairs.copy()
+    return out, pairs, scales
