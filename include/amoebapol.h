@@ -154,6 +154,44 @@ int induced_dipoles_pcg(ap_ctx* ctx, const double* d_guess, double tol_debye, in
 int induced_dipoles_diis(ap_ctx* ctx, const double* d_guess, double tol_debye, int max_iter,
                          int depth, double* d_mu, ap_solve_info* h_info);
 
+/* f1 - AMOEBA's two induced-dipole sets. The polarization interactions carry three scale
+ * factors (Sec. 2.3): one for the direct field that induces the d dipoles, one for the field
+ * that induces the p dipoles, and one (1 here) for the mutual field. The d and p fields are
+ *   E_d = E_c + sum_listed sigma_d F,  E_p = E_c + sum_listed sigma_p F,
+ * where E_c is permanent_field()'s field with every excluded pair left out of real space
+ * and F is a listed pair's Thole-damped Coulomb field (radial functions lambda_{2n+1} U_n);
+ * mu_d = A^-1 E_d, mu_p = A^-1 E_p, and E_pol = -(f/2) sum_i mu_d,i . E_p,i.
+ *
+ * set_scaled_pairs: the listed pairs and their scales, kept by the context (copied).
+ *   d_pairs   [n_pairs][2] int atom indices (caller order), i != j, each pair once.
+ *   d_scales  [n_pairs][2] double (sigma_d, sigma_p).
+ *   Every listed pair must also be in the exclusion lists given to build_neighbour_blocks
+ *   (so that E_c leaves it out); listed pairs farther apart than the cutoff contribute
+ *   nothing, as every pair beyond it. Synchronizes; AP_ERR_ARG for an index out of range,
+ *   i == j or a non-finite scale. The first call allocates the two-set buffers (about
+ *   40 doubles per atom). */
+int set_scaled_pairs(ap_ctx* ctx, int n_pairs, const int* d_pairs, const double* d_scales);
+
+/* f1 - E_d and E_p of a configuration: runs permanent_field() (E_c, kept for the forces),
+ * then the listed-pair terms. d_field_d, d_field_p: [n][3] double outputs, or NULL. */
+int permanent_field_dp(ap_ctx* ctx, const double* d_xyz, const double* d_mpole, const int* d_frame,
+                       const double* d_alpha, double* d_field_d, double* d_field_p);
+
+/* f1 - Both dipole sets by two diagonal-preconditioned CG recurrences in lockstep: every
+ * iteration applies T to both search directions (the pair tensor of every pair evaluated
+ * once for both) and the loop stops when the larger of the two convergence measures
+ * (4.80321 sqrt(sum |alpha_i r_i|^2 / n), Debye) is <= tol_debye. Guesses: [n][3] double
+ * or NULL (alpha E_d, alpha E_p). Outputs d_mu_d, d_mu_p [n][3] double. h_info as for
+ * induced_dipoles_pcg (eps fields hold the larger measure); not capturable into a graph. */
+int induced_dipoles_pcg_dp(ap_ctx* ctx, const double* d_guess_d, const double* d_guess_p, double tol_debye,
+                           int max_iter, double* d_mu_d, double* d_mu_p, ap_solve_info* h_info);
+
+/* f1 - E_pol = -(f/2) sum mu_d . E_p and F = -dE_pol/dx for converged mu_d, mu_p:
+ * -(f/2) [mu_p . dE_d + mu_d . dE_p + mu_p . dT mu_d], with the frame (torque) terms.
+ *   d_energy [1] double, kcal/mol; d_forces [n][3] double, kcal/mol/A (overwritten). */
+int polarization_energy_forces_dp(ap_ctx* ctx, const double* d_mu_d, const double* d_mu_p,
+                                  double* d_energy, double* d_forces);
+
 /* a9 - Polarization energy and forces at fixed dipoles (variational):
  * E_pol = -(f/2) sum_i mu_i . E_i with f = 332.063713, and F = -dE_pol/dx including the
  * reciprocal-space terms and the forces on frame atoms from multipole rotation.
@@ -175,8 +213,9 @@ int ap_list_stats(const ap_ctx* ctx, int* h_blocks, int* h_tiles, int* h_excl_ti
 /* The stream the context enqueues on (cudaStream_t). */
 void* ap_stream(const ap_ctx* ctx);
 
-/* Iterations and residuals of the most recent induced_dipoles_pcg() or
- * induced_dipoles_diis() on this context. Synchronizes the context's stream. */
+/* Iterations and residuals of the most recent induced_dipoles_pcg(),
+ * induced_dipoles_diis() or induced_dipoles_pcg_dp() on this context. Synchronizes the
+ * context's stream. */
 int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 
 /* Benchmark support: launch one kernel of the path `reps` times on the context's stream

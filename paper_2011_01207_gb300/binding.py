@@ -25,7 +25,8 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "ap_mlp_param_count", "ap_mlp_packed_bytes", "ap_mlp_pack", "ap_mlp_forward", "ap_mlp_status",
            "ap_mlp_features", "ap_learned_guess", "ap_mlp_gradient", "ap_mlp_train_step",
            "ap_batch_create", "ap_batch_capture", "ap_batch_launch", "ap_batch_destroy", "ap_autotune",
-           "ap_extrapolate_guess", "induced_dipoles_diis")
+           "ap_extrapolate_guess", "induced_dipoles_diis", "set_scaled_pairs", "permanent_field_dp",
+           "induced_dipoles_pcg_dp", "polarization_energy_forces_dp")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5, "pair_forces": 6,
            "pcg_vectors": 7}
@@ -73,6 +74,10 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "permanent_field": (I, [P, P, P, P, P, P]),
         "induced_dipoles_pcg": (I, [P, P, D, I, P, ctypes.POINTER(ApSolveInfo)]),
         "induced_dipoles_diis": (I, [P, P, D, I, I, P, ctypes.POINTER(ApSolveInfo)]),
+        "set_scaled_pairs": (I, [P, I, P, P]),
+        "permanent_field_dp": (I, [P, P, P, P, P, P, P]),
+        "induced_dipoles_pcg_dp": (I, [P, P, P, D, I, P, P, ctypes.POINTER(ApSolveInfo)]),
+        "polarization_energy_forces_dp": (I, [P, P, P, P, P]),
         "polarization_energy_forces": (I, [P, P, P, P]),
         "dipole_field_matvec": (I, [P, P, P]),
         "ap_list_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -178,6 +183,48 @@ def induced_dipoles_diis(ctx, guess, tol_debye: float, max_iter: int, depth: int
         int(depth), _ptr(mu, torch.float64, (n, 3), "mu"), ctypes.byref(info) if want_info else None)
     _check(ctx, code, "induced_dipoles_diis")
     return info if want_info else None
+
+
+def set_scaled_pairs(ctx, pairs, scales):
+    """pairs: int32 [m, 2] CUDA tensor (caller atom indices); scales: float64 [m, 2] (d, p)."""
+    import torch
+    m = int(pairs.shape[0])
+    return _check(ctx, load().set_scaled_pairs(
+        ctx, m, _ptr(pairs, torch.int32, (m, 2), "pairs", allow_none=m == 0),
+        _ptr(scales, torch.float64, (m, 2), "scales", allow_none=m == 0)), "set_scaled_pairs")
+
+
+def permanent_field_dp(ctx, xyz, mpole, frame, alpha, field_d=None, field_p=None):
+    import torch
+    n = xyz.shape[0]
+    return _check(ctx, load().permanent_field_dp(
+        ctx, _ptr(xyz, torch.float64, (n, 3), "xyz"), _ptr(mpole, torch.float64, (n, 10), "mpole"),
+        _ptr(frame, torch.int32, (n, 3), "frame"), _ptr(alpha, torch.float64, (n,), "alpha"),
+        _ptr(field_d, torch.float64, (n, 3), "field_d", allow_none=True),
+        _ptr(field_p, torch.float64, (n, 3), "field_p", allow_none=True)), "permanent_field_dp")
+
+
+def induced_dipoles_pcg_dp(ctx, guess_d, guess_p, tol_debye: float, max_iter: int, mu_d, mu_p,
+                           want_info: bool = True):
+    import torch
+    n = mu_d.shape[0]
+    info = ApSolveInfo()
+    code = load().induced_dipoles_pcg_dp(
+        ctx, _ptr(guess_d, torch.float64, (n, 3), "guess_d", allow_none=True),
+        _ptr(guess_p, torch.float64, (n, 3), "guess_p", allow_none=True), float(tol_debye), int(max_iter),
+        _ptr(mu_d, torch.float64, (n, 3), "mu_d"), _ptr(mu_p, torch.float64, (n, 3), "mu_p"),
+        ctypes.byref(info) if want_info else None)
+    _check(ctx, code, "induced_dipoles_pcg_dp")
+    return info if want_info else None
+
+
+def polarization_energy_forces_dp(ctx, mu_d, mu_p, energy, forces):
+    import torch
+    n = mu_d.shape[0]
+    return _check(ctx, load().polarization_energy_forces_dp(
+        ctx, _ptr(mu_d, torch.float64, (n, 3), "mu_d"), _ptr(mu_p, torch.float64, (n, 3), "mu_p"),
+        _ptr(energy, torch.float64, (1,), "energy"), _ptr(forces, torch.float64, (n, 3), "forces")),
+        "polarization_energy_forces_dp")
 
 
 def polarization_energy_forces(ctx, mu, energy, forces):
@@ -421,6 +468,27 @@ class Context:
 
     def solve_diis(self, tol=1e-5, max_iter=200, depth=6, guess=None, want_info=True):
         return induced_dipoles_diis(self.ctx, guess, tol, max_iter, depth, self.mu, want_info)
+
+    # AMOEBA's two dipole sets: the context's exclusion list must hold every listed pair
+    def set_scaled_pairs(self, pairs, scales):
+        t = self.torch
+        self.dp_pairs = t.tensor(np.ascontiguousarray(pairs, np.int32).reshape(-1, 2), device=self.device)
+        self.dp_scales = t.tensor(np.ascontiguousarray(scales, np.float64).reshape(-1, 2), device=self.device)
+        z = lambda: t.zeros((self.n, 3), dtype=t.float64, device=self.device)
+        self.field_d, self.field_p, self.mu_d, self.mu_p = z(), z(), z(), z()
+        return set_scaled_pairs(self.ctx, self.dp_pairs, self.dp_scales)
+
+    def permanent_field_dp(self, out=True):
+        return permanent_field_dp(self.ctx, self.xyz, self.mpole, self.frame, self.alpha,
+                                  self.field_d if out else None, self.field_p if out else None)
+
+    def solve_dp(self, tol=1e-5, max_iter=200, guess_d=None, guess_p=None, want_info=True):
+        return induced_dipoles_pcg_dp(self.ctx, guess_d, guess_p, tol, max_iter, self.mu_d, self.mu_p, want_info)
+
+    def energy_forces_dp(self, mu_d=None, mu_p=None):
+        polarization_energy_forces_dp(self.ctx, self.mu_d if mu_d is None else mu_d,
+                                      self.mu_p if mu_p is None else mu_p, self.energy, self.forces)
+        return self.energy, self.forces
 
     def energy_forces(self, mu=None):
         polarization_energy_forces(self.ctx, self.mu if mu is None else mu, self.energy, self.forces)

@@ -38,6 +38,7 @@ void free_all(ap_ctx *c) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     diis_release(c);
+    dp_release(c);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->plan_r2c) cufftDestroy(c->plan_r2c);
     if (c->plan_c2r) cufftDestroy(c->plan_c2r);
@@ -219,6 +220,41 @@ int induced_dipoles_diis(ap_ctx *ctx, const double *d_guess, double tol_debye, i
     return diis_solve(ctx, d_guess, tol_debye, max_iter, depth, d_mu, h_info);
 }
 
+int set_scaled_pairs(ap_ctx *ctx, int n_pairs, const int *d_pairs, const double *d_scales) {
+    if (!ctx) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (n_pairs < 0 || (n_pairs > 0 && (!d_pairs || !d_scales)))
+        return ap_fail(ctx, AP_ERR_ARG, "n_pairs < 0 or a null pointer with n_pairs > 0");
+    return dp_set_pairs(ctx, n_pairs, d_pairs, d_scales);
+}
+
+int permanent_field_dp(ap_ctx *ctx, const double *d_xyz, const double *d_mpole, const int *d_frame,
+                       const double *d_alpha, double *d_field_d, double *d_field_p) {
+    if (!ctx) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->dp) return ap_fail(ctx, AP_ERR_STATE, "set_scaled_pairs() must come first");
+    int r = permanent_field(ctx, d_xyz, d_mpole, d_frame, d_alpha, nullptr);
+    if (r) return r;
+    return dp_fields(ctx, d_field_d, d_field_p);
+}
+
+int induced_dipoles_pcg_dp(ap_ctx *ctx, const double *d_guess_d, const double *d_guess_p, double tol_debye,
+                           int max_iter, double *d_mu_d, double *d_mu_p, ap_solve_info *h_info) {
+    if (!ctx) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!d_mu_d || !d_mu_p) return ap_fail(ctx, AP_ERR_ARG, "d_mu_d or d_mu_p is NULL");
+    if (!(tol_debye > 0) || max_iter < 1) return ap_fail(ctx, AP_ERR_ARG, "tol_debye must be > 0 and max_iter >= 1");
+    return dp_solve(ctx, d_guess_d, d_guess_p, tol_debye, max_iter, d_mu_d, d_mu_p, h_info);
+}
+
+int polarization_energy_forces_dp(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d_energy,
+                                  double *d_forces) {
+    if (!ctx) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!d_mu_d || !d_mu_p || !d_energy || !d_forces) return ap_fail(ctx, AP_ERR_ARG, "null pointer");
+    return dp_forces(ctx, d_mu_d, d_mu_p, d_energy, d_forces);
+}
+
 int polarization_energy_forces(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
     if (!ctx) return AP_ERR_ARG;
     ctx->err.clear();
@@ -248,6 +284,7 @@ void *ap_stream(const ap_ctx *ctx) { return ctx ? (void *)ctx->s0 : nullptr; }
 int ap_solve_info_last(ap_ctx *ctx, ap_solve_info *h_info) {
     if (!ctx || !h_info) return AP_ERR_ARG;
     ctx->err.clear();
+    if (ctx->last_solver == 2) return dp_info(ctx, h_info);
     if (ctx->last_solver == 1) {
         const int rc = diis_info(ctx, h_info);
         return rc < 0 ? rc : AP_OK;

@@ -168,7 +168,8 @@ struct ap_ctx {
     double *diis_e = nullptr;        // [depth][3][n_pad] ring of their errors e_k
     double *diis_part = nullptr;     // [AP_DIIS_MAX_DEPTH][blocks] partial dots
     int diis_cap = 0;                // window length the rings hold
-    int last_solver = 0;             // 0: the last solve was the PCG, 1: Jacobi/DIIS
+    int last_solver = 0;             // the last solve: 0 PCG, 1 Jacobi/DIIS, 2 the two-set PCG
+    void *dp = nullptr;              // buffers of the two-dipole-set path (allocated on first use)
     cudaGraphExec_t diis_exec = nullptr;
     // graph of the solve loop
     cudaGraphExec_t solve_exec = nullptr;
@@ -242,11 +243,23 @@ int real_forces_launch(ap_ctx *ctx, cudaStream_t s);
 int pme_init(ap_ctx *ctx);
 int pme_multipole_field(ap_ctx *ctx, cudaStream_t s);              // permanent: grid2 keeps phi_M
 int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s);  // T_rec p -> rec
+int pme_dipole_field_into(ap_ctx *ctx, const void *p, void *rec_out, cudaStream_t s);   // T_rec p -> rec_out
+int real_matvec2_launch(ap_ctx *ctx, const void *p0, const void *p1, double *acc0, double *acc1,
+                        cudaStream_t s);   // T_real on two dipole sets
 int field_finish(ap_ctx *ctx, double *d_field_out);
 int pcg_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double *d_mu,
               ap_solve_info *info);
 int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces);
+int forces_run_ex(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces,
+                  int (*extra)(ap_ctx *, cudaStream_t));   // extra terms before the frame chain rule
 int diis_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, int depth, double *d_mu,
                ap_solve_info *info);
 void diis_release(ap_ctx *ctx);
 int diis_info(ap_ctx *ctx, ap_solve_info *info);   // state of the last DIIS solve; synchronizes
+int dp_set_pairs(ap_ctx *ctx, int n_pairs, const int *d_pairs, const double *d_scales);
+int dp_fields(ap_ctx *ctx, double *d_field_d, double *d_field_p);
+int dp_solve(ap_ctx *ctx, const double *gd, const double *gp, double tol, int max_iter, double *d_mu_d,
+             double *d_mu_p, ap_solve_info *info);
+int dp_forces(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d_energy, double *d_forces);
+int dp_info(ap_ctx *ctx, ap_solve_info *info);
+void dp_release(ap_ctx *ctx);

@@ -496,8 +496,11 @@ int pair_forces_t(ap_ctx *ctx, cudaStream_t s) {
     return AP_OK;
 }
 
+// `extra`, if given, runs on the force stream after the pair and reciprocal terms and before
+// the frame chain rule: it may add to ctx->frc, ctx->gdip and ctx->gquad
 template <class T>
-int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
+int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces,
+             int (*extra)(ap_ctx *, cudaStream_t)) {
     typedef typename V4<T>::type T4;
     cudaStream_t s = ctx->s0;
     const int n = ctx->n, n_pad = ctx->n_pad;
@@ -525,6 +528,8 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
                                                          (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
                                                          (const T4 *)ctx->quad1, n, n_pad, f, self_coef, ctx->frc,
                                                          ctx->gdip, ctx->gquad, ctx->fixed);
+    AP_CUDA(cudaGetLastError());
+    if (extra && (rc = extra(ctx, s))) return rc;
     k_frame_forces<<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gdip, ctx->gquad, ctx->rot, ctx->mpl, ctx->fvec,
                                                        ctx->frame_s, n, n_pad, ctx->frc, ctx->fixed);
     AP_CUDA(cudaGetLastError());
@@ -546,6 +551,12 @@ int pair_forces_launch(ap_ctx *ctx, cudaStream_t s) {
 }
 
 int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
-    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, d_mu, d_energy, d_forces)
-                                : forces_t<float>(ctx, d_mu, d_energy, d_forces);
+    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, d_mu, d_energy, d_forces, nullptr)
+                                : forces_t<float>(ctx, d_mu, d_energy, d_forces, nullptr);
+}
+
+int forces_run_ex(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces,
+                  int (*extra)(ap_ctx *, cudaStream_t)) {
+    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, d_mu, d_energy, d_forces, extra)
+                                : forces_t<float>(ctx, d_mu, d_energy, d_forces, extra);
 }

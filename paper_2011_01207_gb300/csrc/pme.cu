@@ -440,7 +440,7 @@ int multipole_field_t(ap_ctx *ctx, cudaStream_t s) {
 }
 
 template <class T>
-int dipole_field_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
+int dipole_field_t(ap_ctx *ctx, const void *p, void *rec_out, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
     int r = spread_t<T>(ctx, p, false, s);
@@ -448,7 +448,7 @@ int dipole_field_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
     r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
     if (r) return r;
     k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
-        ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid, (T *)ctx->rec, ctx->n_pad, pc);
+        ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid, (T *)rec_out, ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -510,7 +510,12 @@ int pme_multipole_field(ap_ctx *ctx, cudaStream_t s) {
 }
 
 int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s) {
-    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, s) : dipole_field_t<float>(ctx, p, s);
+    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, ctx->rec, s) : dipole_field_t<float>(ctx, p, ctx->rec, s);
+}
+
+int pme_dipole_field_into(ap_ctx *ctx, const void *p, void *rec_out, cudaStream_t s) {
+    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, rec_out, s)
+                                : dipole_field_t<float>(ctx, p, rec_out, s);
 }
 
 int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {

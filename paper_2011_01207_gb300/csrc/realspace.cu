@@ -338,6 +338,137 @@ __global__ void __launch_bounds__(128) k_matvec(
     if (curI >= 0 && curI * 32 + lane < pc.n) flush3<PA>(acc, n_pad, curI * 32 + lane, ax, ay, az);
 }
 
+// f1: the same product for two dipole sets at once (AMOEBA's d and p dipoles share the
+// operator): the pair tensor (R1, R2) of every pair side is evaluated once and applied to
+// both sources, so the radial work - most of the kernel - is paid once for two vectors.
+template <class T, class A>
+struct Mv2Smem {
+    typename V4<T>::type pos[64];
+    typename V4<T>::type p[2][64];   // the two dipole sets of the item's atoms
+    A acc[6][64];                    // per-target sums: set 0 x y z, set 1 x y z
+    unsigned words[64];
+    int pre[64];
+};
+
+template <class T, bool MINIMG, bool FX>
+__global__ void __launch_bounds__(128) k_matvec2(
+    WorkArgs wa, const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
+    const typename V4<T>::type *__restrict__ pv0, const typename V4<T>::type *__restrict__ pv1,
+    double *__restrict__ acc0, double *__restrict__ acc1, int n_pad, PairConsts<T> pc) {
+    typedef typename V4<T>::type T4;
+    typedef PairAcc<T, FX> PA;
+    __shared__ Mv2Smem<T, typename PA::shared_t> smem[4];
+    Mv2Smem<T, typename PA::shared_t> &S = smem[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long nw = ((long)gridDim.x * blockDim.x) >> 5;
+    const long nitems = *wa.n_work;
+    const long t0 = nitems * gw / nw, t1 = nitems * (gw + 1) / nw;
+    const T4 *cpos = (const T4 *)wa.chunk_pos;
+    int curI = -1;
+    typename PA::reg_t a[6] = {0, 0, 0, 0, 0, 0};
+    for (long t = t0; t < t1; ++t) {
+        const int2 it = wa.work[t];
+        __syncwarp();
+        if (it.x != curI) {
+            if (curI >= 0 && curI * 32 + lane < pc.n) {
+                flush3<PA>(acc0, n_pad, curI * 32 + lane, a[0], a[1], a[2]);
+                flush3<PA>(acc1, n_pad, curI * 32 + lane, a[3], a[4], a[5]);
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) a[c] = 0;
+            curI = it.x;
+            const int si = curI * 32 + lane;
+            T4 q = posq[si];
+            q.w = dipd[si].w;
+            S.pos[lane] = q;
+            S.p[0][lane] = pv0[si];
+            S.p[1][lane] = pv1[si];
+        }
+        const bool diag = it.y < 0;
+        int sj = -1;
+        if (diag) {
+            S.pos[32 + lane] = S.pos[lane];
+            S.p[0][32 + lane] = S.p[0][lane];
+            S.p[1][32 + lane] = S.p[1][lane];
+        } else {
+            const size_t cs = (size_t)it.y * 32 + lane;
+            sj = wa.chunk_j[cs];
+            S.pos[32 + lane] = cpos[cs];
+            T4 z;
+            z.x = z.y = z.z = z.w = T(0);
+            S.p[0][32 + lane] = sj >= 0 ? pv0[sj] : z;
+            S.p[1][32 + lane] = sj >= 0 ? pv1[sj] : z;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            S.acc[c][lane] = 0;
+            S.acc[c][32 + lane] = 0;
+        }
+        const int total = side_words(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
+                                     S.words, S.pre);
+        __syncwarp();
+        SideSlice sl;
+        sl.begin(S.words, S.pre, total, lane);
+        int cur = -1;
+        T4 self;
+        self.x = self.y = self.z = self.w = T(0);
+        T f[6] = {0, 0, 0, 0, 0, 0};
+        while (sl.left > 0) {
+            int tg, src;
+            sl.next(S.words, tg, src);
+            if (tg != cur) {
+                if (cur >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) PA::shared_add(&S.acc[c][cur], f[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < 6; ++c) f[c] = T(0);
+                cur = tg;
+                self = S.pos[tg];
+            }
+            const T4 other = S.pos[src], po = S.p[0][src], pq = S.p[1][src];
+            T dx, dy, dz;
+            pair_vector<T, MINIMG>(pc, self.x, self.y, self.z, other.x, other.y, other.z, T(0), T(0), T(0), dx, dy, dz);
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+            T B[2], U[2], oml[2];
+            screened<T, 2>(pc, r, rinv, rinv2, B, U);
+            thole_oml<T, 2>(pc.thole_a * r2 * r * self.w * other.w, oml);
+            const T R1 = B[0] - oml[0] * U[0];
+            const T R2 = B[1] - oml[1] * U[1];
+            const T pr0 = (po.x * dx + po.y * dy + po.z * dz) * R2;
+            const T pr1 = (pq.x * dx + pq.y * dy + pq.z * dz) * R2;
+            f[0] += pr0 * dx - R1 * po.x;
+            f[1] += pr0 * dy - R1 * po.y;
+            f[2] += pr0 * dz - R1 * po.z;
+            f[3] += pr1 * dx - R1 * pq.x;
+            f[4] += pr1 * dy - R1 * pq.y;
+            f[5] += pr1 * dz - R1 * pq.z;
+        }
+        if (cur >= 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) PA::shared_add(&S.acc[c][cur], f[c]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a[c] += PA::to_reg(S.acc[c][lane]);
+        if (diag) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) a[c] += PA::to_reg(S.acc[c][32 + lane]);
+        } else if (sj >= 0) {
+            flush3<PA>(acc0, n_pad, sj, PA::to_reg(S.acc[0][32 + lane]), PA::to_reg(S.acc[1][32 + lane]),
+                       PA::to_reg(S.acc[2][32 + lane]));
+            flush3<PA>(acc1, n_pad, sj, PA::to_reg(S.acc[3][32 + lane]), PA::to_reg(S.acc[4][32 + lane]),
+                       PA::to_reg(S.acc[5][32 + lane]));
+        }
+    }
+    if (curI >= 0 && curI * 32 + lane < pc.n) {
+        flush3<PA>(acc0, n_pad, curI * 32 + lane, a[0], a[1], a[2]);
+        flush3<PA>(acc1, n_pad, curI * 32 + lane, a[3], a[4], a[5]);
+    }
+}
+
 template <class T>
 PairConsts<T> make_consts(const ap_ctx *ctx) {
     PairConsts<T> pc;
@@ -396,6 +527,21 @@ int matvec_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
 }
 
 template <class T>
+int matvec2_t(ap_ctx *ctx, const void *p0, const void *p1, double *acc0, double *acc1, cudaStream_t s) {
+    typedef typename V4<T>::type T4;
+    PairConsts<T> pc = make_consts<T>(ctx);
+    auto kern = ctx->fixed ? (ctx->minimg ? k_matvec2<T, true, true> : k_matvec2<T, false, true>)
+                           : (ctx->minimg ? k_matvec2<T, true, false> : k_matvec2<T, false, false>);
+    static int grids[4] = {0, 0, 0, 0};
+    int &grid = grids[ctx->minimg + 2 * ctx->fixed];
+    if (!grid) grid = resident_grid(ctx, kern, 128);
+    kern<<<grid, 128, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)p0,
+                              (const T4 *)p1, acc0, acc1, ctx->n_pad, pc);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+template <class T>
 int short_t(ap_ctx *ctx, const void *p, double *out, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PairConsts<T> pc = make_consts<T>(ctx);
@@ -422,4 +568,9 @@ int real_field_launch(ap_ctx *ctx, cudaStream_t s) {
 
 int real_matvec_launch(ap_ctx *ctx, const void *p, cudaStream_t s) {
     return ctx->prec == AP_FP64 ? matvec_t<double>(ctx, p, s) : matvec_t<float>(ctx, p, s);
+}
+
+int real_matvec2_launch(ap_ctx *ctx, const void *p0, const void *p1, double *acc0, double *acc1, cudaStream_t s) {
+    return ctx->prec == AP_FP64 ? matvec2_t<double>(ctx, p0, p1, acc0, acc1, s)
+                                : matvec2_t<float>(ctx, p0, p1, acc0, acc1, s);
 }
