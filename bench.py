@@ -737,6 +737,34 @@ def run_precision(args):
                 "energy_rel": abs(e_own - e_star) / abs(e_star), "energy_rel_same_dipoles": abs(e_fix - e_star) / abs(e_star),
                 "forces_rel_rms": rel_rms(f_own, F_star), "forces_rel_rms_same_dipoles": rel_rms(f_fix, F_star)}
             c.close()
+    # AMOEBA's two dipole sets on the same chain, cut into polarization groups
+    s, pairs, scales = synth.dp_system(synth.solvated_chain(2489, 7023, 62.2, 1003), 1009)
+    o = Oracle(s, Params(beta=BETA, grid=(64, 64, 64), cutoff=CUTOFF), dp=(pairs, scales))
+    Ed_o, Ep_o = o.permanent_field_dp()
+    mud_star, mup_star, _ = o.pcg_dp(Ed_o, Ep_o, tol=1e-10)
+    e_star, F_star = o.energy_dp(mud_star, Ep_o), o.forces_dp(mud_star, mup_star)
+    for tag, prec in (("mixed", binding.AP_MIXED), ("fixed", binding.AP_FIXED)):
+        c = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=(64, 64, 64), precision=prec)
+        c.build()
+        c.set_scaled_pairs(pairs, scales)
+        c.permanent_field_dp()
+        info = c.solve_dp(tol=1e-5, max_iter=200)
+        mud, mup = c.mu_d.cpu().numpy(), c.mu_p.cpu().numpy()
+        dmu = debye * np.linalg.norm(np.concatenate([mud - mud_star, mup - mup_star]), axis=1)
+        e, f = c.energy_forces_dp()
+        e_own, f_own = float(e.cpu()[0]), f.cpu().numpy()
+        e, f = c.energy_forces_dp(torch.tensor(mud_star, device=c.mu.device), torch.tensor(mup_star, device=c.mu.device))
+        e_fix, f_fix = float(e.cpu()[0]), f.cpu().numpy()
+        out[f"chain_23558_atoms_62.2A_grid64_two_sets/{tag}"] = {
+            "atoms": s.n, "pcg_tol_debye": 1e-5, "iterations": info.iterations,
+            "field_d_rel_rms": rel_rms(c.field_d.cpu().numpy(), Ed_o),
+            "field_p_rel_rms": rel_rms(c.field_p.cpu().numpy(), Ep_o),
+            "dipole_rms_debye": float(np.sqrt(np.mean(dmu ** 2))), "dipole_max_debye": float(dmu.max()),
+            "true_residual_debye": max(float(o.residual_eps(Ed_o - o.apply_A(mud))),
+                                       float(o.residual_eps(Ep_o - o.apply_A(mup)))),
+            "energy_rel": abs(e_own - e_star) / abs(e_star), "energy_rel_same_dipoles": abs(e_fix - e_star) / abs(e_star),
+            "forces_rel_rms": rel_rms(f_own, F_star), "forces_rel_rms_same_dipoles": rel_rms(f_fix, F_star)}
+        c.close()
     s = make_system()
     c = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=GRID, precision=binding.AP_MIXED)
     c.build()
@@ -754,6 +782,76 @@ def run_precision(args):
     print(json.dumps({"metric": "errors against the FP64 oracle", "impl": "ours", "cases": out}))
 
 
+def run_two_sets(args):
+    """AMOEBA's two induced-dipole sets (d and p) on the 23,558-atom solvated chain cut into
+    polarization groups: one step = permanent_field_dp + induced_dipoles_pcg_dp (alpha E_d,
+    alpha E_p guesses, lockstep to 1e-5 D) + polarization_energy_forces_dp, against the
+    single-set step on the same configurations and lists. Also the two-set real-space pair
+    kernel against two launches of the single-set one."""
+    import torch
+    from paper_2011_01207_gb300 import binding, build as _build, synth
+    _build.build_library()
+    dev = torch.device("cuda", 0)
+    s0 = synth.solvated_chain(2489, 7023, 62.2, 1003)
+    s, pairs, scales = synth.dp_system(s0, 1009)
+    grid = (64, 64, 64)
+    total = args.warmup + args.steps
+    pos = torch.tensor(trajectory(s, total), device=dev)
+    ctx = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=grid, precision=binding.AP_MIXED,
+                          device=dev)
+    ctx.set_scaled_pairs(pairs, scales)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k, two):
+        xyz = pos[k]
+        if k % REBUILD == 0:
+            binding.build_neighbour_blocks(ctx.ctx, xyz, ctx.excl_off, ctx.excl_atoms, ctx.n_excl)
+        if two:
+            binding.permanent_field_dp(ctx.ctx, xyz, ctx.mpole, ctx.frame, ctx.alpha)
+            binding.induced_dipoles_pcg_dp(ctx.ctx, None, None, TOL, 200, ctx.mu_d, ctx.mu_p, want_info=False)
+            binding.polarization_energy_forces_dp(ctx.ctx, ctx.mu_d, ctx.mu_p, ctx.energy, ctx.forces)
+        else:
+            binding.permanent_field(ctx.ctx, xyz, ctx.mpole, ctx.frame, ctx.alpha, None)
+            binding.induced_dipoles_pcg(ctx.ctx, None, TOL, 200, ctx.mu, want_info=False)
+            binding.polarization_energy_forces(ctx.ctx, ctx.mu, ctx.energy, ctx.forces)
+
+    def timed(two):
+        ts, its = [], []
+        for k in range(args.warmup):
+            step(k, two)
+        for k in range(args.warmup, total):
+            flush.fill_(k & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(k, two)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+            its.append(binding.ap_solve_info_last(ctx.ctx).iterations)
+        return float(np.mean(ts)), float(np.mean(its))
+
+    clocks = Clocks(0)
+    clocks.start()
+    ms2, it2 = timed(True)
+    ms1, it1 = timed(False)
+    clk = clocks.stop()
+    kern = {k: round(binding.ap_time_kernel(ctx.ctx, k, 30), 4) for k in ("real_matvec", "real_matvec2")}
+    ctx.close()
+    print(json.dumps({
+        "metric": "two-set (d/p) polarization step ms, lockstep PCG at 1e-5 D", "impl": "ours",
+        "value": round(ms2, 4), "unit": "ms/step", "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "dtype": "f32 pair/PME arithmetic, f64 accumulation", "data": "synthetic",
+        "config": {"workload": "chain_23558_atoms_62.2A_grid64_two_sets", "atoms": s.n, "listed_pairs": int(len(pairs)),
+                   "iters_mean": it2, "guess": "alpha E_d, alpha E_p",
+                   "single_set": {"ms_per_step": round(ms1, 4), "pcg_iters_mean": it1,
+                                  "note": "same configurations and lists, one dipole set"},
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "kernel_ms": kern,
+        "matvec2_vs_two_matvecs": round(kern["real_matvec2"] / (2 * kern["real_matvec"]), 4),
+        "clocks": clk}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -761,9 +859,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
-    ap.add_argument("--workload", default="water96k", choices=["water96k", "replicas64", "precision"],
+    ap.add_argument("--workload", default="water96k", choices=["water96k", "replicas64", "precision", "two_sets"],
                     help="water96k: the 96,000-atom box (default); replicas64: 64 uneven replicas in one graph; "
-                         "precision: errors of every output against the FP64 oracle")
+                         "precision: errors of every output against the FP64 oracle; two_sets: AMOEBA's d/p "
+                         "dipole sets on the 23,558-atom solvated chain")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -773,6 +872,8 @@ def main():
         run_replicas(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "two_sets":
+        run_two_sets(args)
     else:
         run_ours(args)
 

@@ -233,6 +233,8 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 #define AP_KERNEL_PCG_VECTORS       7   /* a7: one iteration's vector kernels (direction, q = A p
                                            with p.q, update with r.z and |z|^2); advances the last
                                            solve's state, so solve again before using its result */
+#define AP_KERNEL_REAL_MATVEC2      8   /* f1: the two-set real-space product on the last two-set
+                                          search directions (needs set_scaled_pairs) */
 int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
 
 /* Batched replicas: many independent systems of uneven size advanced by one CUDA-graph

@@ -29,7 +29,7 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "induced_dipoles_pcg_dp", "polarization_energy_forces_dp")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5, "pair_forces": 6,
-           "pcg_vectors": 7}
+           "pcg_vectors": 7, "real_matvec2": 8}
 
 
 class ApParams(ctypes.Structure):

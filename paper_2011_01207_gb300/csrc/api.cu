@@ -318,6 +318,7 @@ int ap_time_kernel(ap_ctx *ctx, int which, int reps, double *h_ms) {
         case AP_KERNEL_SPREAD_MULTIPOLES: rc = pme_stage_launch(ctx, 3, ctx->s0); break;
         case AP_KERNEL_PAIR_FORCES: rc = pair_forces_launch(ctx, ctx->s0); break;
         case AP_KERNEL_PCG_VECTORS: rc = pcg_vectors_launch(ctx, ctx->s0); break;
+        case AP_KERNEL_REAL_MATVEC2: rc = dp_matvec2_launch(ctx, ctx->s0, 0); break;
         default: rc = ap_fail(ctx, AP_ERR_ARG, "unknown kernel id");
         }
         if (rc) { cudaEventDestroy(a); cudaEventDestroy(b); return rc; }
@@ -331,6 +332,10 @@ int ap_time_kernel(ap_ctx *ctx, int which, int reps, double *h_ms) {
     cudaEventDestroy(b);
     // the timed launches accumulated into scratch buffers: clear them for the next call
     AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+    if (which == AP_KERNEL_REAL_MATVEC2) {
+        const int rc = dp_matvec2_launch(ctx, ctx->s0, 1);
+        if (rc) return rc;
+    }
     if (which == AP_KERNEL_PAIR_FORCES) {
         AP_CUDA(cudaMemsetAsync(ctx->frc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
         AP_CUDA(cudaMemsetAsync(ctx->gdip, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));

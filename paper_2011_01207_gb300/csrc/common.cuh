@@ -262,4 +262,5 @@ int dp_solve(ap_ctx *ctx, const double *gd, const double *gp, double tol, int ma
              double *d_mu_p, ap_solve_info *info);
 int dp_forces(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d_energy, double *d_forces);
 int dp_info(ap_ctx *ctx, ap_solve_info *info);
+int dp_matvec2_launch(ap_ctx *ctx, cudaStream_t s, int clear);
 void dp_release(ap_ctx *ctx);

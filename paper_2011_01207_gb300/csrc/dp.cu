@@ -855,6 +855,20 @@ int dp_forces(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d
     return AP_OK;
 }
 
+// the two-set real-space product on the current directions alone (timing), or (clear) a
+// reset of the second accumulator afterwards
+int dp_matvec2_launch(ap_ctx *ctx, cudaStream_t s, int clear) {
+    if (!ctx->dp) return ap_fail(ctx, AP_ERR_STATE, "set_scaled_pairs() must come first");
+    DpBuffers *B = dpb(ctx);
+    if (clear) {
+        AP_CUDA(cudaMemsetAsync(B->acc2, 0, sizeof(double) * 3 * ctx->n_pad, s));
+        return AP_OK;
+    }
+    const size_t t4 = (ctx->prec == AP_FP64 ? sizeof(double) : sizeof(float)) * 4;
+    const char *p0 = (const char *)B->p2;
+    return real_matvec2_launch(ctx, p0, p0 + t4 * ctx->n_pad, ctx->acc, B->acc2, s);
+}
+
 int dp_info(ap_ctx *ctx, ap_solve_info *info) {
     if (!ctx->dp) return ap_fail(ctx, AP_ERR_STATE, "no two-set solve on this context");
     DpBuffers *B = dpb(ctx);
