@@ -97,6 +97,7 @@ struct ap_ctx {
     int2 *work = nullptr;        // [n_blocks + cap] (I, chunk) items, chunk -1 = diagonal block
     int *work_off = nullptr;     // [n_blocks + 1] first item of each block
     int *n_work = nullptr;       // device: [0] work items, [1] in-range pairs of the configuration
+    int *item_start = nullptr;   // [work + 1] exclusive prefix of the items' in-range pair counts
     unsigned *pmask = nullptr;   // [work][32] in-range pair bits per item (i-lane word, bit = j-lane)
     unsigned *pmask_t = nullptr; // [work][32] the transpose (j-lane word, bit = i-lane)
     unsigned *smask = nullptr;   // [work][32] pairs closer than AP_SHORT_RANGE (learned-guess feature)
@@ -192,6 +193,7 @@ struct WorkArgs {
     const unsigned *pmask_t;
     const unsigned *smask;
     const unsigned *smask_t;
+    const int *item_start;     // exclusive prefix of in-range pairs per item; [n_work] = total
 };
 
 inline WorkArgs work_args(const ap_ctx *ctx) {
@@ -209,6 +211,7 @@ inline WorkArgs work_args(const ap_ctx *ctx) {
     w.pmask_t = ctx->pmask_t;
     w.smask = ctx->smask;
     w.smask_t = ctx->smask_t;
+    w.item_start = ctx->item_start;
     return w;
 }
 

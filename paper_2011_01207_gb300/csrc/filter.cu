@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work,
                                                   const typename V4<T>::type *__restrict__ chunk_pos, T rc2, T Lx,
                                                   T Ly, T Lz, unsigned *__restrict__ pmask,
                                                   unsigned *__restrict__ pmask_t, T rs2, unsigned *__restrict__ smask,
-                                                  unsigned *__restrict__ smask_t, int *__restrict__ pcount) {
+                                                  unsigned *__restrict__ smask_t, int *__restrict__ pcount,
+                                                  int *__restrict__ item_cnt) {
     typedef typename V4<T>::type T4;
     const int lane = threadIdx.x & 31;
     const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -202,8 +203,45 @@ __global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work,
         smask_t[(size_t)t * 32 + lane] = warp_transpose32(ms, lane);
         int c = __popc(m);
         for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-        if (lane == 0) atomicAdd(pcount, c);
+        if (lane == 0) {
+            atomicAdd(pcount, c);
+            item_cnt[t] = c;
+        }
     }
+}
+
+// in place: per-item pair counts -> exclusive prefix, total at [n_work] (one block)
+__global__ void __launch_bounds__(1024) k_item_scan(int *__restrict__ a, const int *__restrict__ n_work) {
+    __shared__ int wsum[32];
+    const int n = *n_work;
+    const int per = (n + 1023) / 1024;
+    const int b0 = min(n, (int)threadIdx.x * per), b1 = min(n, b0 + per);
+    int s = 0;
+    for (int k = b0; k < b1; ++k) s += a[k];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = s;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int v = wsum[lane];
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += y;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int excl = x - s + (w ? wsum[w - 1] : 0);
+    for (int k = b0; k < b1; ++k) {
+        const int c = a[k];
+        a[k] = excl;
+        excl += c;
+    }
+    if (threadIdx.x == 1023) a[n] = wsum[31];
 }
 
 template <class T>
@@ -225,7 +263,9 @@ int filter_t(ap_ctx *ctx, cudaStream_t s) {
     auto km = ctx->minimg ? k_pairmask<T, true> : k_pairmask<T, false>;
     km<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->work, ctx->n_work, (const T4 *)ctx->posq, (const T4 *)ctx->chunk_pos, rcm,
                                          (T)P.box[0], (T)P.box[1], (T)P.box[2], ctx->pmask, ctx->pmask_t,
-                                         (T)(AP_SHORT_RANGE * AP_SHORT_RANGE), ctx->smask, ctx->smask_t, ctx->n_work + 1);
+                                         (T)(AP_SHORT_RANGE * AP_SHORT_RANGE), ctx->smask, ctx->smask_t, ctx->n_work + 1,
+                                         ctx->item_start);
+    k_item_scan<<<1, 1024, 0, s>>>(ctx->item_start, ctx->n_work);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -241,7 +281,7 @@ int filter_alloc(ap_ctx *ctx) {
     const long cap = ctx->cap_tiles;
     if (cap <= ctx->cap_chunks) return AP_OK;
     void *ptrs[] = {ctx->chunk_j, ctx->chunk_pos, ctx->chunk_src, ctx->chunk_mask, ctx->chunk_flag, ctx->work,
-                    ctx->pmask, ctx->pmask_t, ctx->smask, ctx->smask_t};
+                    ctx->pmask, ctx->pmask_t, ctx->smask, ctx->smask_t, ctx->item_start};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     const size_t es = ctx->prec == AP_FP64 ? 8 : 4;
@@ -251,6 +291,7 @@ int filter_alloc(ap_ctx *ctx) {
     AP_CUDA(cudaMalloc((void **)&ctx->chunk_mask, sizeof(unsigned) * 32 * cap));
     AP_CUDA(cudaMalloc((void **)&ctx->chunk_flag, sizeof(int) * cap));
     AP_CUDA(cudaMalloc((void **)&ctx->work, sizeof(int2) * (cap + ctx->n_blocks)));
+    AP_CUDA(cudaMalloc((void **)&ctx->item_start, sizeof(int) * (cap + ctx->n_blocks + 1)));
     if (!ctx->work_off) AP_CUDA(cudaMalloc((void **)&ctx->work_off, sizeof(int) * (ctx->n_blocks + 1)));
     AP_CUDA(cudaMalloc((void **)&ctx->pmask, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
     AP_CUDA(cudaMalloc((void **)&ctx->pmask_t, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));

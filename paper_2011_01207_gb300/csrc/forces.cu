@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(128, 6) k_pair_forces(
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
-    const long nitems = *wa.n_work;
-    const long t0 = nitems * gw / nw, t1 = nitems * (gw + 1) / nw;
+    long t0, t1;
+    work_range(wa, gw, nw, t0, t1);
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     const double sc[12] = {fconst, fconst, fconst, -fconst, -fconst, -fconst, -fconst / 3, -fconst / 3,
                            -fconst / 3, -fconst / 3, -fconst / 3, -fconst / 3};

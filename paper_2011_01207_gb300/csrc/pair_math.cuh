@@ -70,6 +70,27 @@ __device__ __forceinline__ void thole_oml(T s, T *oml) {
     if (NMAX > 3) oml[3] = (T(1) + s + s * s * (T(18.0 / 35.0) + T(9.0 / 35.0) * s)) * e;
 }
 
+// Items [t0, t1) of warp gw of nw: consecutive items holding an equal share of the in-range
+// pairs (by the items' exclusive prefix counts), so that warps get equal work whatever the
+// pair density of their items; item order (grouped by block I) is kept.
+__device__ __forceinline__ void work_range(const WorkArgs &wa, long gw, long nw, long &t0, long &t1) {
+    const long nitems = *wa.n_work;
+    const long total = wa.item_start[nitems];
+    const long a = total * gw / nw, b = total * (gw + 1) / nw;
+    long lo = 0, hi = nitems;   // first item whose start >= a
+    while (lo < hi) {
+        const long mid = (lo + hi) >> 1;
+        if (wa.item_start[mid] < a) lo = mid + 1; else hi = mid;
+    }
+    t0 = lo;
+    hi = nitems;                // first item whose start >= b
+    while (lo < hi) {
+        const long mid = (lo + hi) >> 1;
+        if (wa.item_start[mid] < b) lo = mid + 1; else hi = mid;
+    }
+    t1 = gw == nw - 1 ? nitems : lo;
+}
+
 // Pair sides of one 32 x 32 work item, walked in place (one warp). Word w < 32 is row i = w
 // (bits: the item's j atoms in range of i), word 32 + j the column of j (bits: the i atoms);
 // the target of a side in word w is atom w of the item's 64 (i atoms first) and its source

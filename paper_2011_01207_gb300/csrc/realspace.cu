@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(128) k_perm_field(
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
-    const long nitems = *wa.n_work;
-    const long t0 = nitems * gw / nw, t1 = nitems * (gw + 1) / nw;
+    long t0, t1;
+    work_range(wa, gw, nw, t0, t1);
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
     typename PA::reg_t ax = 0, ay = 0, az = 0;
@@ -243,8 +243,8 @@ __global__ void __launch_bounds__(128) k_matvec(
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
-    const long nitems = *wa.n_work;
-    const long t0 = nitems * gw / nw, t1 = nitems * (gw + 1) / nw;
+    long t0, t1;
+    work_range(wa, gw, nw, t0, t1);
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
     typename PA::reg_t ax = 0, ay = 0, az = 0;
@@ -362,8 +362,8 @@ __global__ void __launch_bounds__(128) k_matvec2(
     const int lane = threadIdx.x & 31;
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
-    const long nitems = *wa.n_work;
-    const long t0 = nitems * gw / nw, t1 = nitems * (gw + 1) / nw;
+    long t0, t1;
+    work_range(wa, gw, nw, t0, t1);
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
     typename PA::reg_t a[6] = {0, 0, 0, 0, 0, 0};
