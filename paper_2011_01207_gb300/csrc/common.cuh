@@ -97,7 +97,7 @@ struct ap_ctx {
     int2 *work = nullptr;        // [n_blocks + cap] (I, chunk) items, chunk -1 = diagonal block
     int *work_off = nullptr;     // [n_blocks + 1] first item of each block
     int *n_work = nullptr;       // device: [0] work items, [1] in-range pairs of the configuration
-    int *item_start = nullptr;   // [work + 1] exclusive prefix of the items' in-range pair counts
+    int *item_start = nullptr;   // [work + 1] exclusive prefix of the items' weights (pairs + staging cost)
     unsigned *pmask = nullptr;   // [work][32] in-range pair bits per item (i-lane word, bit = j-lane)
     unsigned *pmask_t = nullptr; // [work][32] the transpose (j-lane word, bit = i-lane)
     unsigned *smask = nullptr;   // [work][32] pairs closer than AP_SHORT_RANGE (learned-guess feature)
@@ -193,7 +193,7 @@ struct WorkArgs {
     const unsigned *pmask_t;
     const unsigned *smask;
     const unsigned *smask_t;
-    const int *item_start;     // exclusive prefix of in-range pairs per item; [n_work] = total
+    const int *item_start;     // exclusive prefix of the item weights; [n_work] = total
 };
 
 inline WorkArgs work_args(const ap_ctx *ctx) {

@@ -70,9 +70,10 @@ __device__ __forceinline__ void thole_oml(T s, T *oml) {
     if (NMAX > 3) oml[3] = (T(1) + s + s * s * (T(18.0 / 35.0) + T(9.0 / 35.0) * s)) * e;
 }
 
-// Items [t0, t1) of warp gw of nw: consecutive items holding an equal share of the in-range
-// pairs (by the items' exclusive prefix counts), so that warps get equal work whatever the
-// pair density of their items; item order (grouped by block I) is kept.
+// Items [t0, t1) of warp gw of nw: consecutive items holding an equal share of the total
+// item weight (in-range pairs plus a fixed staging cost per item, as exclusive prefix sums),
+// so that warps get equal work whatever the pair density of their items; item order
+// (grouped by block I) is kept.
 __device__ __forceinline__ void work_range(const WorkArgs &wa, long gw, long nw, long &t0, long &t1) {
     const long nitems = *wa.n_work;
     const long total = wa.item_start[nitems];
