@@ -255,6 +255,8 @@ int pcg_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, doub
 int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces);
 int forces_run_ex(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces,
                   int (*extra)(ap_ctx *, cudaStream_t));   // extra terms before the frame chain rule
+int mutual_forces_run(ap_ctx *ctx, const double *d_mu, void *const *mz, double *gd, double *gq,
+                      double *d_forces);   // forces of -(f/2) mu.T mu alone (mz: zeroed multipoles)
 int diis_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, int depth, double *d_mu,
                ap_solve_info *info);
 void diis_release(ap_ctx *ctx);

@@ -18,11 +18,12 @@
 // measure is <= tol.
 //
 // Forces (-dE_pol/dx with mu_d's response folded in through mu_p, A symmetric):
-//   F = F_1(mu_s) - [F_1(delta) + F_1(-delta)] / 2 + F_listed,
+//   F = F_1(mu_s) - F_T(delta) + F_listed,
 // with mu_s = (mu_d + mu_p)/2, delta = (mu_d - mu_p)/2, F_1(mu) the single-set force of
-// -f mu . E_c - (f/2) mu . T mu (whose +/- pair isolates the mutual term -(f/2) delta T delta),
-// and F_listed the gradient of -(f/2) sum_listed (sigma_d mu_p,I + sigma_p mu_d,I) . F_lambda
-// including its multipole-orientation (frame) terms.
+// -f mu . E_c - (f/2) mu . T mu, F_T(delta) the force of the mutual term -(f/2) delta . T delta
+// alone (the single-set path with the permanent multipoles zeroed), and F_listed the
+// gradient of -(f/2) sum_listed (sigma_d mu_p,I + sigma_p mu_d,I) . F_lambda including its
+// multipole-orientation (frame) terms.
 #include "common.cuh"
 
 #include <cmath>
@@ -50,7 +51,9 @@ struct DpBuffers {
     double *part = nullptr;       // [4][blocks] partial sums
     DpState *st = nullptr, *st_host = nullptr;
     double *mus = nullptr;        // [2][3][n_pad] mu_d, mu_p in slot order (force terms)
-    double *cbuf = nullptr;       // [5][n][3] caller order: mu_s, delta, -delta, F_1(delta), F_1(-delta)
+    double *cbuf = nullptr;       // [3][n][3] caller order: mu_s, delta, mutual forces of delta
+    void *mz = nullptr;           // T4 [4][n_pad]: posq, dipd, quad0, quad1 with the multipoles zeroed
+    double *gsc = nullptr;        // [9][n_pad] scratch multipole derivatives of the mutual pass
     double *e_scr = nullptr;      // [2] energy scratch
     int *flag = nullptr;          // [1] validation flag
     cudaGraphExec_t exec = nullptr;
@@ -611,7 +614,26 @@ __global__ void k_dp_split(const double *__restrict__ md, const double *__restri
     const double a = md[k], b = mp[k];
     cbuf[k] = 0.5 * (a + b);
     cbuf[n3 + k] = 0.5 * (a - b);
-    cbuf[2 * n3 + k] = -0.5 * (a - b);
+}
+
+// copies of the configuration arrays with the permanent multipoles zeroed: positions, Thole
+// factors and polarizabilities kept
+template <class T>
+__global__ void k_zero_multipoles(const typename V4<T>::type *__restrict__ posq,
+                                  const typename V4<T>::type *__restrict__ dipd,
+                                  const typename V4<T>::type *__restrict__ quad1, int n_pad,
+                                  typename V4<T>::type *__restrict__ mz) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    typename V4<T>::type a = posq[s], b = dipd[s], d = quad1[s], z;
+    a.w = T(0);
+    b.x = b.y = b.z = T(0);
+    z.x = z.y = z.z = z.w = T(0);
+    d.x = d.y = d.w = T(0);
+    mz[s] = a;
+    mz[(size_t)n_pad + s] = b;
+    mz[(size_t)2 * n_pad + s] = z;
+    mz[(size_t)3 * n_pad + s] = d;
 }
 
 // both sets into slot order (the listed-pair force kernel reads them by slot)
@@ -642,12 +664,11 @@ __global__ void k_dp_energy(const double *__restrict__ mus, const double *__rest
     if (threadIdx.x == 0) *out = scale * tot[0];
 }
 
-// F = F_1(mu_s) - (F_1(delta) + F_1(-delta)) / 2, in caller order
-__global__ void k_dp_force_combine(const double *__restrict__ fa, const double *__restrict__ fb, int n3,
-                                   double *__restrict__ out) {
+// F = F_1(mu_s) - F_T(delta), in caller order
+__global__ void k_dp_force_combine(const double *__restrict__ ft, int n3, double *__restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n3) return;
-    out[k] -= 0.5 * (fa[k] + fb[k]);
+    out[k] -= ft[k];
 }
 
 // gradient of -(f/2) sum over listed ordered pairs (I, J) of w . F_lambda(R; M_J) with
@@ -782,7 +803,9 @@ int reserve(ap_ctx *ctx) {
     if ((r = dmalloc(ctx, &B->st, sizeof(DpState)))) return r;
     AP_CUDA(cudaMallocHost((void **)&B->st_host, sizeof(DpState)));
     if ((r = dmalloc(ctx, &B->mus, sizeof(double) * 6 * np))) return r;
-    if ((r = dmalloc(ctx, &B->cbuf, sizeof(double) * 15 * n))) return r;
+    if ((r = dmalloc(ctx, &B->cbuf, sizeof(double) * 9 * n))) return r;
+    if ((r = dmalloc(ctx, (char **)&B->mz, 4 * tsz * 4 * np))) return r;
+    if ((r = dmalloc(ctx, &B->gsc, sizeof(double) * 9 * np))) return r;
     if ((r = dmalloc(ctx, &B->e_scr, sizeof(double) * 2 + sizeof(unsigned int)))) return r;
     if ((r = dmalloc(ctx, &B->flag, sizeof(int)))) return r;
     return AP_OK;
@@ -838,19 +861,29 @@ int dp_forces(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d
     DpBuffers *B = dpb(ctx);
     cudaStream_t s = ctx->s0;
     const int n3 = 3 * ctx->n;
-    double *mu_s = B->cbuf, *dl = B->cbuf + n3, *ndl = B->cbuf + 2 * n3, *fa = B->cbuf + 3 * n3,
-           *fb = B->cbuf + 4 * n3;
+    double *mu_s = B->cbuf, *dl = B->cbuf + n3, *ft = B->cbuf + 2 * n3;
     k_dp_split<<<ap_grid_for(n3, 256), 256, 0, s>>>(d_mu_d, d_mu_p, n3, B->cbuf);
     k_dp_slots<<<ap_grid_for(ctx->n_pad, 256), 256, 0, s>>>(d_mu_d, d_mu_p, ctx->perm, ctx->n, ctx->n_pad, B->mus);
     const int nb = ap_grid_for(ctx->n_pad, NT);
     k_dp_energy<<<nb, NT, 0, s>>>(B->mus, B->E2, ctx->n_pad, -0.5 * AP_COULOMB, B->part,
                                   (unsigned int *)(B->e_scr + 2), d_energy);
     AP_CUDA(cudaGetLastError());
+    const size_t t4 = (ctx->prec == AP_FP64 ? sizeof(double) : sizeof(float)) * 4;
+    void *mz[4];
+    for (int k = 0; k < 4; ++k) mz[k] = (char *)B->mz + t4 * ctx->n_pad * k;
+    if (ctx->prec == AP_FP64)
+        k_zero_multipoles<double><<<ap_grid_for(ctx->n_pad, 256), 256, 0, s>>>(
+            (const V4<double>::type *)ctx->posq, (const V4<double>::type *)ctx->dipd,
+            (const V4<double>::type *)ctx->quad1, ctx->n_pad, (V4<double>::type *)B->mz);
+    else
+        k_zero_multipoles<float><<<ap_grid_for(ctx->n_pad, 256), 256, 0, s>>>(
+            (const V4<float>::type *)ctx->posq, (const V4<float>::type *)ctx->dipd,
+            (const V4<float>::type *)ctx->quad1, ctx->n_pad, (V4<float>::type *)B->mz);
+    AP_CUDA(cudaGetLastError());
     int r;
-    if ((r = forces_run(ctx, dl, B->e_scr, fa))) return r;
-    if ((r = forces_run(ctx, ndl, B->e_scr, fb))) return r;
+    if ((r = mutual_forces_run(ctx, dl, mz, B->gsc, B->gsc + (size_t)3 * ctx->n_pad, ft))) return r;
     if ((r = forces_run_ex(ctx, mu_s, B->e_scr, d_forces, listed_forces))) return r;
-    k_dp_force_combine<<<ap_grid_for(n3, 256), 256, 0, s>>>(fa, fb, n3, d_forces);
+    k_dp_force_combine<<<ap_grid_for(n3, 256), 256, 0, s>>>(ft, n3, d_forces);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -887,7 +920,7 @@ void dp_release(ap_ctx *ctx) {
     if (!B) return;
     if (B->exec) cudaGraphExecDestroy(B->exec);
     void *ptrs[] = {B->pairs, B->scales, B->E2, B->corr, B->mu2, B->r2, B->q2, B->p2, B->acc2, B->rec2, B->part,
-                    B->st, B->mus, B->cbuf, B->e_scr, B->flag};
+                    B->st, B->mus, B->cbuf, B->e_scr, B->flag, B->mz, B->gsc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (B->st_host) cudaFreeHost(B->st_host);

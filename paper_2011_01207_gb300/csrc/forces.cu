@@ -18,6 +18,7 @@
 
 void unsort3(ap_ctx *ctx, const double *src, double *out, cudaStream_t s);
 int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s);
+int pme_forces_derivs_mu(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s);
 
 namespace {
 
@@ -465,10 +466,11 @@ __global__ void k_unsort3_fx(const double *__restrict__ src, int n_pad, const in
     for (int c = 0; c < 3; ++c) out[3 * i + c] = acc_value(src, (size_t)c * n_pad + s, 1);
 }
 
-// the real-space force kernel over the current work items with the dipoles in ctx->p,
-// accumulating into ctx->frc, ctx->gdip and ctx->gquad
+// the real-space force kernel over the current work items with the dipoles in ctx->p and
+// the multipoles (posq q, dipd, quad0, quad1) given, accumulating into frc, gdip and gquad
 template <class T>
-int pair_forces_t(ap_ctx *ctx, cudaStream_t s) {
+int pair_forces_t(ap_ctx *ctx, cudaStream_t s, const void *posq, const void *dipd, const void *quad0,
+                  const void *quad1, double *frc, double *gdip, double *gquad) {
     typedef typename V4<T>::type T4;
     PairConsts<T> pc;
     const ap_params &P = ctx->prm;
@@ -489,9 +491,9 @@ int pair_forces_t(ap_ctx *ctx, cudaStream_t s) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * fo_warps<T>(), 0);
         grid = std::max(1, per_sm) * ctx->sm_count;
     }
-    kern<<<grid, 32 * fo_warps<T>(), 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd,
-                                            (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, (const T4 *)ctx->p,
-                                            ctx->frc, ctx->gdip, ctx->gquad, ctx->n_pad, pc, AP_COULOMB);
+    kern<<<grid, 32 * fo_warps<T>(), 0, s>>>(work_args(ctx), (const T4 *)posq, (const T4 *)dipd,
+                                            (const T4 *)quad0, (const T4 *)quad1, (const T4 *)ctx->p,
+                                            frc, gdip, gquad, ctx->n_pad, pc, AP_COULOMB);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -520,7 +522,7 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
     AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
     int rc = pme_forces_derivs(ctx, ctx->p, ctx->gbuf, ctx->s1);
     if (rc) return rc;
-    rc = pair_forces_t<T>(ctx, s);
+    rc = pair_forces_t<T>(ctx, s, ctx->posq, ctx->dipd, ctx->quad0, ctx->quad1, ctx->frc, ctx->gdip, ctx->gquad);
     if (rc) return rc;
     AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));
     AP_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
@@ -544,10 +546,55 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
     return AP_OK;
 }
 
+// forces of the mutual term alone, -(f/2) mu . T mu, for caller-order dipoles d_mu: the
+// single-set force path with the permanent multipoles replaced by zeros (mz: posq, dipd,
+// quad0, quad1 with q, d and Q zero, positions and Thole factors kept) and without the
+// permanent potential's reciprocal part or the frame chain rule. gd, gq: scratch for the
+// dipole and quadrupole derivatives the kernels also write (not used).
+template <class T>
+int mutual_forces_t(ap_ctx *ctx, const double *d_mu, void *const *mz, double *gd, double *gq, double *d_forces) {
+    typedef typename V4<T>::type T4;
+    cudaStream_t s = ctx->s0;
+    const int n = ctx->n, n_pad = ctx->n_pad;
+    const double f = AP_COULOMB;
+    const double self_coef = 4.0 * std::pow(ctx->prm.ewald_beta, 3) / (3.0 * AP_SQRT_PI);
+    k_mu_load<T><<<ap_grid_for(n_pad, 256), 256, 0, s>>>(d_mu, ctx->perm, n, n_pad, ctx->mu_s, (T4 *)ctx->p);
+    AP_CUDA(cudaMemsetAsync(ctx->frc, 0, sizeof(double) * 3 * n_pad, s));
+    AP_CUDA(cudaMemsetAsync(gd, 0, sizeof(double) * 3 * n_pad, s));
+    AP_CUDA(cudaMemsetAsync(gq, 0, sizeof(double) * 6 * n_pad, s));
+    AP_CUDA(cudaEventRecord(ctx->ev_fork, s));
+    AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
+    int rc = pme_forces_derivs_mu(ctx, ctx->p, ctx->gbuf, ctx->s1);
+    if (rc) return rc;
+    rc = pair_forces_t<T>(ctx, s, mz[0], mz[1], mz[2], mz[3], ctx->frc, gd, gq);
+    if (rc) return rc;
+    AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));
+    AP_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+    k_recip_forces<T><<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gbuf, ctx->mu_s, (const T4 *)mz[0], (const T4 *)mz[1],
+                                                         (const T4 *)mz[2], (const T4 *)mz[3], n, n_pad, f, self_coef,
+                                                         ctx->frc, gd, gq, ctx->fixed);
+    AP_CUDA(cudaGetLastError());
+    if (ctx->fixed)
+        k_unsort3_fx<<<ap_grid_for(n, 256), 256, 0, s>>>(ctx->frc, n_pad, ctx->iperm, n, d_forces);
+    else
+        unsort3(ctx, ctx->frc, d_forces, s);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
 }  // namespace
 
 int pair_forces_launch(ap_ctx *ctx, cudaStream_t s) {
-    return ctx->prec == AP_FP64 ? pair_forces_t<double>(ctx, s) : pair_forces_t<float>(ctx, s);
+    return ctx->prec == AP_FP64
+               ? pair_forces_t<double>(ctx, s, ctx->posq, ctx->dipd, ctx->quad0, ctx->quad1, ctx->frc, ctx->gdip,
+                                       ctx->gquad)
+               : pair_forces_t<float>(ctx, s, ctx->posq, ctx->dipd, ctx->quad0, ctx->quad1, ctx->frc, ctx->gdip,
+                                      ctx->gquad);
+}
+
+int mutual_forces_run(ap_ctx *ctx, const double *d_mu, void *const *mz, double *gd, double *gq, double *d_forces) {
+    return ctx->prec == AP_FP64 ? mutual_forces_t<double>(ctx, d_mu, mz, gd, gq, d_forces)
+                                : mutual_forces_t<float>(ctx, d_mu, mz, gd, gq, d_forces);
 }
 
 int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {

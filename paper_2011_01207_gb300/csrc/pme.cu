@@ -456,7 +456,7 @@ int dipole_field_t(ap_ctx *ctx, const void *p, void *rec_out, cudaStream_t s) {
 // forces: phi_mu derivatives (20 comps, into gbuf[0..19]) and phi_M second derivatives
 // (components 4..9, into gbuf[20..25]); the spread of mu uses ctx->p as scratch.
 template <class T>
-int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
+int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, int with_M, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
     int r = spread_t<T>(ctx, mu4, false, s);
@@ -465,8 +465,12 @@ int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
     if (r) return r;
     k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid,
                                                                gbuf, ctx->n_pad, 20, pc);
-    k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid2,
-                                                               gbuf + (size_t)20 * ctx->n_pad, ctx->n_pad, 10, pc);
+    if (with_M)
+        k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(ctx->stb, (const T4 *)ctx->stw,
+                                                                   (const T *)ctx->grid2,
+                                                                   gbuf + (size_t)20 * ctx->n_pad, ctx->n_pad, 10, pc);
+    else
+        AP_CUDA(cudaMemsetAsync(gbuf + (size_t)20 * ctx->n_pad, 0, sizeof(double) * 10 * ctx->n_pad, s));
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -519,5 +523,10 @@ int pme_dipole_field_into(ap_ctx *ctx, const void *p, void *rec_out, cudaStream_
 }
 
 int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
-    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, mu4, gbuf, s) : forces_t<float>(ctx, mu4, gbuf, s);
+    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, mu4, gbuf, 1, s) : forces_t<float>(ctx, mu4, gbuf, 1, s);
+}
+
+// the dipoles' potential derivatives only (the permanent multipoles' part left zero)
+int pme_forces_derivs_mu(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
+    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, mu4, gbuf, 0, s) : forces_t<float>(ctx, mu4, gbuf, 0, s);
 }
