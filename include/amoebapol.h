@@ -273,10 +273,13 @@ int ap_batch_capture(ap_batch* b, const ap_batch_step* steps);
 int ap_batch_launch(ap_batch* b, void* stream);
 void ap_batch_destroy(ap_batch* b);
 
-/* Launch-shape autotuner: times the real-space matvec with 1, 1/2 and 1/4 of the
- * resident grid and the PME spread+gather with 64, 128 and 256 threads per block on the
- * current configuration, and keeps the fastest for this context. h_choice[2] (optional)
- * receives the grid divisor and the thread count. Synchronizes. */
+/* Launch-shape autotuner: times whole PCG solves (four iterations from alpha E, each one
+ * graph launch, so the real-space matvec runs concurrently with the PME branch as in any
+ * solve) for every combination of the matvec grid (1, 1/2 and 1/4 of the resident grid)
+ * and the PME spread/gather block size (64, 128 and 256 threads) on the current
+ * configuration, and keeps the fastest for this context. Overwrites the state of the last
+ * solve (ap_solve_info_last). h_choice[2] (optional) receives the grid divisor and the
+ * thread count. Synchronizes. */
 int ap_autotune(ap_ctx* ctx, int reps, int* h_choice);
 
 /* a8 - Learned initial guess. The paper has no learned component; any PCG start is

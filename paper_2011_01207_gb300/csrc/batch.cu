@@ -15,6 +15,7 @@ int ap_learned_guess(ap_ctx *ctx, const void *d_packed, double *d_mu0);
 int hist_guess_launch(ap_ctx *ctx, const double *g, const double *h, double *out, cudaStream_t s);
 int hist_push_launch(ap_ctx *ctx, const double *g, const double *mu, double *h, cudaStream_t s);
 int pme_stage_launch(ap_ctx *ctx, int stage, cudaStream_t s);
+int dipole_operator_into(ap_ctx *ctx, cudaStream_t main, cudaStream_t aux);
 
 struct ap_batch {
     std::vector<ap_ctx *> ctxs;
@@ -147,32 +148,42 @@ int ap_autotune(ap_ctx *ctx, int reps, int *h_choice) {
         }
         return best;
     };
-    // real-space matvec: resident grid / {1, 2, 4}
+    // whole PCG solves (four iterations from alpha E, as one graph launch each) for every
+    // combination of the real-space matvec grid (1, 1/2 and 1/4 of the resident grid) and
+    // the PME spread/gather block size (64, 128 and 256 threads): what counts is the
+    // matvec running concurrently with the reciprocal branch inside the solve, and the
+    // matvec's grid decides how much room the PME kernels find on the SMs
+    auto forget = [&] {
+        if (ctx->solve_exec) cudaGraphExecDestroy(ctx->solve_exec);
+        ctx->solve_exec = nullptr;
+        ctx->graph_ok = 0;
+        ctx->graph_tried = 0;
+    };
     const int divs[3] = {1, 2, 4};
-    float best = 1e30f;
-    int best_div = 1;
-    for (int d : divs) {
-        ctx->tune_mv_div = d;
-        float t = time_it([&] { real_matvec_launch(ctx, ctx->p, ctx->s0); });
-        if (t < best) { best = t; best_div = d; }
-    }
-    ctx->tune_mv_div = best_div;
-    // PME spread + gather: threads per block {64, 128, 256}
     const int thr[3] = {64, 128, 256};
-    best = 1e30f;
-    int best_thr = 128;
-    for (int th : thr) {
-        ctx->tune_pme_threads = th;
-        float t = time_it([&] {
-            pme_stage_launch(ctx, 0, ctx->s0);
-            pme_stage_launch(ctx, 2, ctx->s0);
-        });
-        if (t < best) { best = t; best_thr = th; }
-    }
+    float best = 1e30f;
+    int best_div = 1, best_thr = 128;
+    for (int d : divs)
+        for (int th : thr) {
+            ctx->tune_mv_div = d;
+            ctx->tune_pme_threads = th;
+            forget();
+            int rc = pcg_solve(ctx, nullptr, 1e-300, 4, ctx->frc, nullptr);   // captures the loop
+            if (rc < 0) return rc;
+            float t = time_it([&] { pcg_solve(ctx, nullptr, 1e-300, 4, ctx->frc, nullptr); });
+            if (t < best) { best = t; best_div = d; best_thr = th; }
+        }
+    ctx->tune_mv_div = best_div;
     ctx->tune_pme_threads = best_thr;
+    // the solve graphs captured the old launch shapes: capture again at the next solve
+    forget();
+    if (ctx->diis_exec) cudaGraphExecDestroy(ctx->diis_exec);
+    ctx->diis_exec = nullptr;
+    dp_forget_graph(ctx);
     cudaEventDestroy(a);
     cudaEventDestroy(z);
     AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+    AP_CUDA(cudaMemsetAsync(ctx->frc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
     AP_CUDA(cudaStreamSynchronize(ctx->s0));
     AP_CUDA(cudaGetLastError());
     if (h_choice) {

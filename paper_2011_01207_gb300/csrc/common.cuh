@@ -246,7 +246,16 @@ int real_forces_launch(ap_ctx *ctx, cudaStream_t s);
 int pme_init(ap_ctx *ctx);
 int pme_multipole_field(ap_ctx *ctx, cudaStream_t s);              // permanent: grid2 keeps phi_M
 int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s);  // T_rec p -> rec
-int pme_dipole_field_into(ap_ctx *ctx, const void *p, void *rec_out, cudaStream_t s);   // T_rec p -> rec_out
+// a set of PME work grids and cuFFT plans (the context owns one; others allow concurrent passes)
+struct PmeBufs {
+    void *grid = nullptr, *cgrid = nullptr;
+    long long *grid_fx = nullptr;
+    cufftHandle r2c = 0, c2r = 0;
+};
+int pme_bufs_create(ap_ctx *ctx, PmeBufs *b);
+void pme_bufs_destroy(PmeBufs *b);
+// T_rec p -> rec_out, on the given grids (NULL: the context's own)
+int pme_dipole_field_into(ap_ctx *ctx, const void *p, void *rec_out, const PmeBufs *bufs, cudaStream_t s);
 int real_matvec2_launch(ap_ctx *ctx, const void *p0, const void *p1, double *acc0, double *acc1,
                         cudaStream_t s);   // T_real on two dipole sets
 int field_finish(ap_ctx *ctx, double *d_field_out);
@@ -269,3 +278,4 @@ int dp_forces(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d
 int dp_info(ap_ctx *ctx, ap_solve_info *info);
 int dp_matvec2_launch(ap_ctx *ctx, cudaStream_t s, int clear);
 void dp_release(ap_ctx *ctx);
+void dp_forget_graph(ap_ctx *ctx);   // drop the captured two-set solve loop (launch shapes changed)

@@ -56,6 +56,9 @@ struct DpBuffers {
     double *gsc = nullptr;        // [9][n_pad] scratch multipole derivatives of the mutual pass
     double *e_scr = nullptr;      // [2] energy scratch
     int *flag = nullptr;          // [1] validation flag
+    PmeBufs pme2;                 // grids and plans of the second set's PME pass
+    cudaStream_t s_rec2 = nullptr;  // its stream, concurrent with the first set's PME pass
+    cudaEvent_t ev_join2 = nullptr;
     cudaGraphExec_t exec = nullptr;
     int exec_tried = 0;
     int field_valid = 0;
@@ -462,7 +465,7 @@ DpVecs vecs_of(ap_ctx *ctx) {
 }
 
 // T applied to both directions: real space (two-set kernel) on `main`, the two PME passes
-// on `aux`, joined into `main`
+// on `aux` and on the second set's own stream with its own grids, all joined into `main`
 template <class T>
 int matvec2(ap_ctx *ctx, cudaStream_t main, cudaStream_t aux) {
     typedef typename V4<T>::type T4;
@@ -470,14 +473,17 @@ int matvec2(ap_ctx *ctx, cudaStream_t main, cudaStream_t aux) {
     const T4 *p0 = (const T4 *)B->p2, *p1 = p0 + ctx->n_pad;
     AP_CUDA(cudaEventRecord(ctx->ev_fork, main));
     AP_CUDA(cudaStreamWaitEvent(aux, ctx->ev_fork, 0));
-    int rc = pme_dipole_field_into(ctx, p0, ctx->rec, aux);
+    AP_CUDA(cudaStreamWaitEvent(B->s_rec2, ctx->ev_fork, 0));
+    int rc = pme_dipole_field_into(ctx, p0, ctx->rec, nullptr, aux);
     if (rc) return rc;
-    rc = pme_dipole_field_into(ctx, p1, B->rec2, aux);
+    rc = pme_dipole_field_into(ctx, p1, B->rec2, &B->pme2, B->s_rec2);
     if (rc) return rc;
     rc = real_matvec2_launch(ctx, p0, p1, ctx->acc, B->acc2, main);
     if (rc) return rc;
     AP_CUDA(cudaEventRecord(ctx->ev_join, aux));
+    AP_CUDA(cudaEventRecord(B->ev_join2, B->s_rec2));
     AP_CUDA(cudaStreamWaitEvent(main, ctx->ev_join, 0));
+    AP_CUDA(cudaStreamWaitEvent(main, B->ev_join2, 0));
     return AP_OK;
 }
 
@@ -808,6 +814,11 @@ int reserve(ap_ctx *ctx) {
     if ((r = dmalloc(ctx, &B->gsc, sizeof(double) * 9 * np))) return r;
     if ((r = dmalloc(ctx, &B->e_scr, sizeof(double) * 2 + sizeof(unsigned int)))) return r;
     if ((r = dmalloc(ctx, &B->flag, sizeof(int)))) return r;
+    if ((r = pme_bufs_create(ctx, &B->pme2))) return r;
+    int lo = 0, hi = 0;
+    AP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    AP_CUDA(cudaStreamCreateWithPriority(&B->s_rec2, cudaStreamNonBlocking, hi));
+    AP_CUDA(cudaEventCreateWithFlags(&B->ev_join2, cudaEventDisableTiming));
     return AP_OK;
 }
 
@@ -915,6 +926,14 @@ int dp_info(ap_ctx *ctx, ap_solve_info *info) {
     return AP_OK;
 }
 
+void dp_forget_graph(ap_ctx *ctx) {
+    DpBuffers *B = dpb(ctx);
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+    B->exec_tried = 0;
+}
+
 void dp_release(ap_ctx *ctx) {
     DpBuffers *B = dpb(ctx);
     if (!B) return;
@@ -924,6 +943,9 @@ void dp_release(ap_ctx *ctx) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (B->st_host) cudaFreeHost(B->st_host);
+    pme_bufs_destroy(&B->pme2);
+    if (B->s_rec2) cudaStreamDestroy(B->s_rec2);
+    if (B->ev_join2) cudaEventDestroy(B->ev_join2);
     delete B;
     ctx->dp = nullptr;
 }

@@ -376,23 +376,34 @@ int init_t(ap_ctx *ctx) {
     return AP_OK;
 }
 
+// the context's own grids and plans as a PmeBufs view
+PmeBufs own_bufs(ap_ctx *ctx) {
+    PmeBufs b;
+    b.grid = ctx->grid;
+    b.cgrid = ctx->cgrid;
+    b.grid_fx = ctx->grid_fx;
+    b.r2c = ctx->plan_r2c;
+    b.c2r = ctx->plan_c2r;
+    return b;
+}
+
 template <class T>
-int fft_roundtrip(ap_ctx *ctx, T *in, T *out, cudaStream_t s) {
+int fft_roundtrip(ap_ctx *ctx, const PmeBufs &b, T *in, T *out, cudaStream_t s) {
     typedef typename FftTypes<T>::cplx C;
-    AP_CUFFT(cufftSetStream(ctx->plan_r2c, s));
-    AP_CUFFT(cufftSetStream(ctx->plan_c2r, s));
+    AP_CUFFT(cufftSetStream(b.r2c, s));
+    AP_CUFFT(cufftSetStream(b.c2r, s));
     if (sizeof(T) == 8) {
-        AP_CUFFT(cufftExecD2Z(ctx->plan_r2c, (cufftDoubleReal *)in, (cufftDoubleComplex *)ctx->cgrid));
+        AP_CUFFT(cufftExecD2Z(b.r2c, (cufftDoubleReal *)in, (cufftDoubleComplex *)b.cgrid));
     } else {
-        AP_CUFFT(cufftExecR2C(ctx->plan_r2c, (cufftReal *)in, (cufftComplex *)ctx->cgrid));
+        AP_CUFFT(cufftExecR2C(b.r2c, (cufftReal *)in, (cufftComplex *)b.cgrid));
     }
-    k_convolve<T><<<ap_grid_for((long)ctx->ncgrid, 256), 256, 0, s>>>((C *)ctx->cgrid, (const T *)ctx->green,
+    k_convolve<T><<<ap_grid_for((long)ctx->ncgrid, 256), 256, 0, s>>>((C *)b.cgrid, (const T *)ctx->green,
                                                                      ctx->ncgrid);
     AP_CUDA(cudaGetLastError());
     if (sizeof(T) == 8) {
-        AP_CUFFT(cufftExecZ2D(ctx->plan_c2r, (cufftDoubleComplex *)ctx->cgrid, (cufftDoubleReal *)out));
+        AP_CUFFT(cufftExecZ2D(b.c2r, (cufftDoubleComplex *)b.cgrid, (cufftDoubleReal *)out));
     } else {
-        AP_CUFFT(cufftExecC2R(ctx->plan_c2r, (cufftComplex *)ctx->cgrid, (cufftReal *)out));
+        AP_CUFFT(cufftExecC2R(b.c2r, (cufftComplex *)b.cgrid, (cufftReal *)out));
     }
     return AP_OK;
 }
@@ -401,12 +412,12 @@ int fft_roundtrip(ap_ctx *ctx, T *in, T *out, cudaStream_t s) {
 // multipoles (multi = true). Mixed/FP64 modes: FP32/T atomics on a cleared grid. AP_FIXED:
 // 64-bit fixed-point atomics on ctx->grid_fx (kept cleared), then converted into the grid.
 template <class T>
-int spread_t(ap_ctx *ctx, const void *src, bool multi, cudaStream_t s) {
+int spread_t(ap_ctx *ctx, const PmeBufs &bf, const void *src, bool multi, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
     const bool fx = ctx->fixed != 0;
-    void *g = fx ? (void *)ctx->grid_fx : ctx->grid;
-    if (!fx) AP_CUDA(cudaMemsetAsync(ctx->grid, 0, sizeof(T) * ctx->ngrid, s));
+    void *g = fx ? (void *)bf.grid_fx : bf.grid;
+    if (!fx) AP_CUDA(cudaMemsetAsync(bf.grid, 0, sizeof(T) * ctx->ngrid, s));
     if (multi) {
         auto kern = fx ? k_spread_multipoles<T, true> : k_spread_multipoles<T, false>;
         kern<<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->dipd,
@@ -419,7 +430,7 @@ int spread_t(ap_ctx *ctx, const void *src, bool multi, cudaStream_t s) {
     }
     AP_CUDA(cudaGetLastError());
     if (fx) {
-        k_grid_from_fx<T><<<ap_grid_for((long)ctx->ngrid, 256), 256, 0, s>>>(ctx->grid_fx, (T *)ctx->grid, ctx->ngrid);
+        k_grid_from_fx<T><<<ap_grid_for((long)ctx->ngrid, 256), 256, 0, s>>>(bf.grid_fx, (T *)bf.grid, ctx->ngrid);
         AP_CUDA(cudaGetLastError());
     }
     return AP_OK;
@@ -429,9 +440,10 @@ template <class T>
 int multipole_field_t(ap_ctx *ctx, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
-    int r = spread_t<T>(ctx, nullptr, true, s);
+    const PmeBufs bf = own_bufs(ctx);
+    int r = spread_t<T>(ctx, bf, nullptr, true, s);
     if (r) return r;
-    r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid2, s);
+    r = fft_roundtrip<T>(ctx, bf, (T *)ctx->grid, (T *)ctx->grid2, s);
     if (r) return r;
     k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
         ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid2, (T *)ctx->rec, ctx->n_pad, pc);
@@ -440,15 +452,15 @@ int multipole_field_t(ap_ctx *ctx, cudaStream_t s) {
 }
 
 template <class T>
-int dipole_field_t(ap_ctx *ctx, const void *p, void *rec_out, cudaStream_t s) {
+int dipole_field_t(ap_ctx *ctx, const void *p, void *rec_out, const PmeBufs &bf, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
-    int r = spread_t<T>(ctx, p, false, s);
+    int r = spread_t<T>(ctx, bf, p, false, s);
     if (r) return r;
-    r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
+    r = fft_roundtrip<T>(ctx, bf, (T *)bf.grid, (T *)bf.grid, s);
     if (r) return r;
     k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
-        ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid, (T *)rec_out, ctx->n_pad, pc);
+        ctx->stb, (const T4 *)ctx->stw, (const T *)bf.grid, (T *)rec_out, ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -459,9 +471,10 @@ template <class T>
 int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, int with_M, cudaStream_t s) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
-    int r = spread_t<T>(ctx, mu4, false, s);
+    const PmeBufs bf = own_bufs(ctx);
+    int r = spread_t<T>(ctx, bf, mu4, false, s);
     if (r) return r;
-    r = fft_roundtrip<T>(ctx, (T *)ctx->grid, (T *)ctx->grid, s);
+    r = fft_roundtrip<T>(ctx, bf, (T *)ctx->grid, (T *)ctx->grid, s);
     if (r) return r;
     k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid,
                                                                gbuf, ctx->n_pad, 20, pc);
@@ -483,7 +496,7 @@ int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
     PmeConsts<T> pc = pme_consts<T>(ctx);
     switch (stage) {
     case 0:
-        return spread_t<T>(ctx, ctx->p, false, s);
+        return spread_t<T>(ctx, own_bufs(ctx), ctx->p, false, s);
     case 1:
         k_convolve<T><<<ap_grid_for((long)ctx->ncgrid, 256), 256, 0, s>>>((C *)ctx->cgrid, (const T *)ctx->green,
                                                                          ctx->ncgrid);
@@ -493,7 +506,7 @@ int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
             ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid, (T *)ctx->rec, ctx->n_pad, pc);
         break;
     case 3:
-        return spread_t<T>(ctx, nullptr, true, s);
+        return spread_t<T>(ctx, own_bufs(ctx), nullptr, true, s);
     default:
         return ap_fail(ctx, AP_ERR_ARG, "unknown PME stage");
     }
@@ -514,12 +527,39 @@ int pme_multipole_field(ap_ctx *ctx, cudaStream_t s) {
 }
 
 int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s) {
-    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, ctx->rec, s) : dipole_field_t<float>(ctx, p, ctx->rec, s);
+    const PmeBufs bf = own_bufs(ctx);
+    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, ctx->rec, bf, s)
+                                : dipole_field_t<float>(ctx, p, ctx->rec, bf, s);
 }
 
-int pme_dipole_field_into(ap_ctx *ctx, const void *p, void *rec_out, cudaStream_t s) {
-    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, rec_out, s)
-                                : dipole_field_t<float>(ctx, p, rec_out, s);
+int pme_dipole_field_into(ap_ctx *ctx, const void *p, void *rec_out, const PmeBufs *bufs, cudaStream_t s) {
+    const PmeBufs bf = bufs ? *bufs : own_bufs(ctx);
+    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, rec_out, bf, s)
+                                : dipole_field_t<float>(ctx, p, rec_out, bf, s);
+}
+
+// a second set of grids and cuFFT plans of the context's sizes (for concurrent passes)
+int pme_bufs_create(ap_ctx *ctx, PmeBufs *b) {
+    const bool dbl = ctx->prec == AP_FP64;
+    const size_t es = dbl ? sizeof(double) : sizeof(float);
+    AP_CUDA(cudaMalloc(&b->grid, es * ctx->ngrid));
+    AP_CUDA(cudaMalloc(&b->cgrid, 2 * es * ctx->ncgrid));
+    if (ctx->fixed) {
+        AP_CUDA(cudaMalloc((void **)&b->grid_fx, sizeof(long long) * ctx->ngrid));
+        AP_CUDA(cudaMemset(b->grid_fx, 0, sizeof(long long) * ctx->ngrid));
+    }
+    AP_CUFFT(cufftPlan3d(&b->r2c, ctx->K[2], ctx->K[1], ctx->K[0], dbl ? CUFFT_D2Z : CUFFT_R2C));
+    AP_CUFFT(cufftPlan3d(&b->c2r, ctx->K[2], ctx->K[1], ctx->K[0], dbl ? CUFFT_Z2D : CUFFT_C2R));
+    return AP_OK;
+}
+
+void pme_bufs_destroy(PmeBufs *b) {
+    if (b->grid) cudaFree(b->grid);
+    if (b->cgrid) cudaFree(b->cgrid);
+    if (b->grid_fx) cudaFree(b->grid_fx);
+    if (b->r2c) cufftDestroy(b->r2c);
+    if (b->c2r) cufftDestroy(b->c2r);
+    *b = PmeBufs();
 }
 
 int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
