@@ -89,20 +89,34 @@ __device__ __forceinline__ void make_stencil(const PmeConsts<T> &pc, int4 ib, ty
 }
 
 // adds v[t] to row[k[t]], t = 0..4, where k[t] = k[0] - t (mod K): the stencil's five points
-// along x. Unless the row wraps they are contiguous, and in FP32 two float2 atomics and one
-// scalar cover them (aligned to the pair boundary) instead of five scalar ones.
+// along x. Unless the row wraps they are contiguous, and in FP32 they take two vector atomics
+// (float4 and float2 are native on sm_90 and later) for three of the four alignments of the
+// first point to a 16-byte boundary and three for the fourth, instead of five scalar ones; a
+// float4 may also cover the point after the stencil (adding zero) when that point is still
+// inside the row of Kx points.
 template <class T>
-__device__ __forceinline__ void add_row5(T *row, const int *k, const T *v) {
+__device__ __forceinline__ void add_row5(T *row, const int *k, const T *v, int) {
 #pragma unroll
     for (int t = 0; t < 5; ++t) atomicAdd(row + k[t], v[t]);
 }
-__device__ __forceinline__ void add_row5(float *row, const int *k, const float *v) {
+__device__ __forceinline__ void add_row5(float *row, const int *k, const float *v, int Kx) {
     if (k[0] >= 4) {
-        float *p0 = row + (k[0] - 4);   // point t = 4
-        if ((reinterpret_cast<uintptr_t>(p0) & 7u) == 0) {
-            atomicAdd(reinterpret_cast<float2 *>(p0), make_float2(v[4], v[3]));
-            atomicAdd(reinterpret_cast<float2 *>(p0 + 2), make_float2(v[2], v[1]));
+        float *p0 = row + (k[0] - 4);   // point t = 4; p0[j] takes v[4 - j]
+        const unsigned mis = (unsigned)(reinterpret_cast<uintptr_t>(p0) & 15u) >> 2;
+        if (mis == 0) {
+            atomicAdd(reinterpret_cast<float4 *>(p0), make_float4(v[4], v[3], v[2], v[1]));
             atomicAdd(p0 + 4, v[0]);
+        } else if (mis == 3) {
+            atomicAdd(p0, v[4]);
+            atomicAdd(reinterpret_cast<float4 *>(p0 + 1), make_float4(v[3], v[2], v[1], v[0]));
+        } else if (mis == 2) {
+            atomicAdd(reinterpret_cast<float2 *>(p0), make_float2(v[4], v[3]));
+            if (k[0] + 1 < Kx) {
+                atomicAdd(reinterpret_cast<float4 *>(p0 + 2), make_float4(v[2], v[1], v[0], 0.0f));
+            } else {
+                atomicAdd(reinterpret_cast<float2 *>(p0 + 2), make_float2(v[2], v[1]));
+                atomicAdd(p0 + 4, v[0]);
+            }
         } else {
             atomicAdd(p0, v[4]);
             atomicAdd(reinterpret_cast<float2 *>(p0 + 1), make_float2(v[3], v[2]));
@@ -117,13 +131,13 @@ __device__ __forceinline__ void add_row5(float *row, const int *k, const float *
 // spread permanent multipoles (q, d, Q) ------------------------------------------------
 // adds the stencil row v[0..4] to the grid (FX: the fixed-point grid, one 64-bit atomic per point)
 template <class T, bool FX>
-__device__ __forceinline__ void grid_row5(void *grid, size_t row, const int *k, const T *v) {
+__device__ __forceinline__ void grid_row5(void *grid, size_t row, const int *k, const T *v, int Kx) {
     if constexpr (FX) {
         unsigned long long *g = reinterpret_cast<unsigned long long *>(grid) + row;
 #pragma unroll
         for (int t = 0; t < 5; ++t) atomicAdd(g + k[t], (unsigned long long)ap_to_fx(v[t]));
     } else {
-        add_row5(reinterpret_cast<T *>(grid) + row, k, v);
+        add_row5(reinterpret_cast<T *>(grid) + row, k, v, Kx);
     }
 }
 
@@ -158,7 +172,7 @@ __global__ void k_spread_multipoles(const typename V4<T>::type *__restrict__ pos
             T v[5];
 #pragma unroll
             for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc + st.d2[0][t1] * Cc;
-            grid_row5<T, FX>(grid, row, st.k[0], v);
+            grid_row5<T, FX>(grid, row, st.k[0], v, Kx);
         }
     }
 }
@@ -187,7 +201,7 @@ __global__ void k_spread_dipoles(const int4 *__restrict__ stb, const typename V4
             T v[5];
 #pragma unroll
             for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc;
-            grid_row5<T, FX>(grid, row, st.k[0], v);
+            grid_row5<T, FX>(grid, row, st.k[0], v, Kx);
         }
     }
 }
