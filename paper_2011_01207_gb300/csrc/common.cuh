@@ -98,6 +98,7 @@ struct ap_ctx {
     int *work_off = nullptr;     // [n_blocks + 1] first item of each block
     int *n_work = nullptr;       // device: [0] work items, [1] in-range pairs of the configuration
     int *item_start = nullptr;   // [work + 1] exclusive prefix of the items' weights (pairs + staging cost)
+    int *scan_tmp = nullptr;     // chunk sums of that prefix
     unsigned *pmask = nullptr;   // [work][32] in-range pair bits per item (i-lane word, bit = j-lane)
     unsigned *pmask_t = nullptr; // [work][32] the transpose (j-lane word, bit = i-lane)
     unsigned *smask = nullptr;   // [work][32] pairs closer than AP_SHORT_RANGE (learned-guess feature)

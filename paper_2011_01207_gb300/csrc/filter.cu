@@ -216,38 +216,108 @@ __global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work,
     }
 }
 
-// in place: per-item pair counts -> exclusive prefix, total at [n_work] (one block)
-__global__ void __launch_bounds__(1024) k_item_scan(int *__restrict__ a, const int *__restrict__ n_work) {
+// per-item weights -> exclusive prefix in place, total at [n_work]: chunk sums, a one-block
+// scan of the chunk sums, then each chunk's own scan plus its offset (all coalesced)
+constexpr int SCAN_T = 256, SCAN_PER = 8, SCAN_CHUNK = SCAN_T * SCAN_PER;
+
+__device__ __forceinline__ int block_excl_scan(int x, int &total) {
+    __shared__ int wsum[SCAN_T / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int v = x;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += y;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    int base = 0;
+    total = 0;
+    for (int q = 0; q < SCAN_T / 32; ++q) {
+        if (q < w) base += wsum[q];
+        total += wsum[q];
+    }
+    __syncthreads();
+    return base + v - x;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_chunks(const int *__restrict__ a, const int *__restrict__ n_work,
+                                                        int *__restrict__ csum) {
+    const int n = *n_work;
+    const int c0 = blockIdx.x * SCAN_CHUNK;
+    if (c0 >= n) return;   // whole block: uniform
+    int s = 0;
+#pragma unroll
+    for (int r = 0; r < SCAN_PER; ++r) {
+        const int k = c0 + r * SCAN_T + threadIdx.x;
+        s += k < n ? a[k] : 0;
+    }
+    int total;
+    block_excl_scan(s, total);
+    if (threadIdx.x == 0) csum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int *__restrict__ csum, const int *__restrict__ n_work) {
     __shared__ int wsum[32];
     const int n = *n_work;
-    const int per = (n + 1023) / 1024;
-    const int b0 = min(n, (int)threadIdx.x * per), b1 = min(n, b0 + per);
-    int s = 0;
-    for (int k = b0; k < b1; ++k) s += a[k];
+    const int nc = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = s;
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
-    }
-    if (lane == 31) wsum[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int v = wsum[lane];
+    int carry = 0;
+    for (int c0 = 0; c0 < nc; c0 += 1024) {
+        const int k = c0 + threadIdx.x;
+        const int x = k < nc ? csum[k] : 0;
+        int v = x;
         for (int off = 1; off < 32; off <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, v, off);
             if (lane >= off) v += y;
         }
-        wsum[lane] = v;
+        if (lane == 31) wsum[w] = v;
+        __syncthreads();
+        int base = 0, total = 0;
+        for (int q = 0; q < 32; ++q) {
+            if (q < w) base += wsum[q];
+            total += wsum[q];
+        }
+        if (k < nc) csum[k] = carry + base + v - x;
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) csum[nc] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(int *__restrict__ a, const int *__restrict__ n_work,
+                                                       const int *__restrict__ csum) {
+    const int n = *n_work;
+    const int c0 = blockIdx.x * SCAN_CHUNK;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a[n] = csum[(n + SCAN_CHUNK - 1) / SCAN_CHUNK];
+    if (c0 >= n) return;
+    // thread t owns SCAN_PER consecutive items; loads are staged through shared memory so
+    // that global accesses stay coalesced
+    __shared__ int tile[SCAN_CHUNK];
+#pragma unroll
+    for (int r = 0; r < SCAN_PER; ++r) {
+        const int k = c0 + r * SCAN_T + threadIdx.x;
+        tile[r * SCAN_T + threadIdx.x] = k < n ? a[k] : 0;
     }
     __syncthreads();
-    int excl = x - s + (w ? wsum[w - 1] : 0);
-    for (int k = b0; k < b1; ++k) {
-        const int c = a[k];
-        a[k] = excl;
-        excl += c;
+    int v[SCAN_PER], s = 0;
+#pragma unroll
+    for (int r = 0; r < SCAN_PER; ++r) {
+        v[r] = tile[threadIdx.x * SCAN_PER + r];
+        s += v[r];
     }
-    if (threadIdx.x == 1023) a[n] = wsum[31];
+    int total;
+    int e = block_excl_scan(s, total) + csum[blockIdx.x];
+#pragma unroll
+    for (int r = 0; r < SCAN_PER; ++r) {
+        tile[threadIdx.x * SCAN_PER + r] = e;
+        e += v[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < SCAN_PER; ++r) {
+        const int k = c0 + r * SCAN_T + threadIdx.x;
+        if (k < n) a[k] = tile[r * SCAN_T + threadIdx.x];
+    }
 }
 
 template <class T>
@@ -271,7 +341,10 @@ int filter_t(ap_ctx *ctx, cudaStream_t s) {
                                          (T)P.box[0], (T)P.box[1], (T)P.box[2], ctx->pmask, ctx->pmask_t,
                                          (T)(AP_SHORT_RANGE * AP_SHORT_RANGE), ctx->smask, ctx->smask_t, ctx->n_work + 1,
                                          ctx->item_start, ITEM_WEIGHT);
-    k_item_scan<<<1, 1024, 0, s>>>(ctx->item_start, ctx->n_work);
+    const int nchunks = (int)((ctx->cap_chunks + (long)nb + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    k_scan_chunks<<<nchunks, SCAN_T, 0, s>>>(ctx->item_start, ctx->n_work, ctx->scan_tmp);
+    k_scan_top<<<1, 1024, 0, s>>>(ctx->scan_tmp, ctx->n_work);
+    k_scan_apply<<<nchunks, SCAN_T, 0, s>>>(ctx->item_start, ctx->n_work, ctx->scan_tmp);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -287,7 +360,7 @@ int filter_alloc(ap_ctx *ctx) {
     const long cap = ctx->cap_tiles;
     if (cap <= ctx->cap_chunks) return AP_OK;
     void *ptrs[] = {ctx->chunk_j, ctx->chunk_pos, ctx->chunk_src, ctx->chunk_mask, ctx->chunk_flag, ctx->work,
-                    ctx->pmask, ctx->pmask_t, ctx->smask, ctx->smask_t, ctx->item_start};
+                    ctx->pmask, ctx->pmask_t, ctx->smask, ctx->smask_t, ctx->item_start, ctx->scan_tmp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     const size_t es = ctx->prec == AP_FP64 ? 8 : 4;
@@ -298,6 +371,7 @@ int filter_alloc(ap_ctx *ctx) {
     AP_CUDA(cudaMalloc((void **)&ctx->chunk_flag, sizeof(int) * cap));
     AP_CUDA(cudaMalloc((void **)&ctx->work, sizeof(int2) * (cap + ctx->n_blocks)));
     AP_CUDA(cudaMalloc((void **)&ctx->item_start, sizeof(int) * (cap + ctx->n_blocks + 1)));
+    AP_CUDA(cudaMalloc((void **)&ctx->scan_tmp, sizeof(int) * ((cap + ctx->n_blocks) / SCAN_CHUNK + 2)));
     if (!ctx->work_off) AP_CUDA(cudaMalloc((void **)&ctx->work_off, sizeof(int) * (ctx->n_blocks + 1)));
     AP_CUDA(cudaMalloc((void **)&ctx->pmask, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
     AP_CUDA(cudaMalloc((void **)&ctx->pmask_t, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
