@@ -10,41 +10,49 @@ namespace {
 // FP64 division and sqrt are slow on this part: minimum image with 1/L, normalisation with rsqrt
 __device__ __forceinline__ double mi(double v, double L, double iL) { return v - L * rint(v * iL); }
 
-__device__ __forceinline__ void unit3(double *v) {
-    const double in = rsqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+template <class C>
+__device__ __forceinline__ void unit3(C *v) {
+    const C in = rsq(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     v[0] *= in; v[1] *= in; v[2] *= in;
 }
 
-// columns of R are the local x, y, z axes in global coordinates
+// columns of R are the local x, y, z axes in global coordinates; the minimum-image
+// vectors to the frame atoms (kept in fv) in FP64, the axes in C
+template <class C>
 __device__ void frame_matrix(const double *__restrict__ xyz, int i, int type, int za, int xa, double3 L,
-                             double3 iL, double R[3][3], double *fv) {
+                             double3 iL, C R[3][3], double *fv) {
     for (int a = 0; a < 6; ++a) fv[a] = 0.0;
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) R[a][b] = (a == b) ? 1.0 : 0.0;
+        for (int b = 0; b < 3; ++b) R[a][b] = (a == b) ? C(1) : C(0);
     if (type != AP_FRAME_Z_THEN_X && type != AP_FRAME_BISECTOR) return;
     const double Ls[3] = {L.x, L.y, L.z}, iLs[3] = {iL.x, iL.y, iL.z};
-    double vz[3], vx[3], z[3], x[3];
+    C vz[3], vx[3], z[3], x[3];
     for (int a = 0; a < 3; ++a) {
-        vz[a] = mi(xyz[3 * za + a] - xyz[3 * i + a], Ls[a], iLs[a]);
-        vx[a] = mi(xyz[3 * xa + a] - xyz[3 * i + a], Ls[a], iLs[a]);
-        fv[a] = vz[a];
-        fv[3 + a] = vx[a];
+        const double dz = mi(xyz[3 * za + a] - xyz[3 * i + a], Ls[a], iLs[a]);
+        const double dx = mi(xyz[3 * xa + a] - xyz[3 * i + a], Ls[a], iLs[a]);
+        fv[a] = dz;
+        fv[3 + a] = dx;
+        vz[a] = (C)dz;
+        vx[a] = (C)dx;
     }
     if (type == AP_FRAME_Z_THEN_X) {
         for (int a = 0; a < 3; ++a) z[a] = vz[a];
         unit3(z);
-        double d = vx[0] * z[0] + vx[1] * z[1] + vx[2] * z[2];
+        C d = vx[0] * z[0] + vx[1] * z[1] + vx[2] * z[2];
         for (int a = 0; a < 3; ++a) x[a] = vx[a] - d * z[a];
     } else {
         unit3(vz);
         unit3(vx);
         for (int a = 0; a < 3; ++a) z[a] = vz[a] + vx[a];
         unit3(z);
-        double d = vx[0] * z[0] + vx[1] * z[1] + vx[2] * z[2];
+        C d = vx[0] * z[0] + vx[1] * z[1] + vx[2] * z[2];
         for (int a = 0; a < 3; ++a) x[a] = vx[a] - d * z[a];
     }
     unit3(x);
-    double y[3] = {z[1] * x[2] - z[2] * x[1], z[2] * x[0] - z[0] * x[2], z[0] * x[1] - z[1] * x[0]};
+    C y[3] = {z[1] * x[2] - z[2] * x[1], z[2] * x[0] - z[0] * x[2], z[0] * x[1] - z[1] * x[0]};
     for (int a = 0; a < 3; ++a) {
         R[a][0] = x[a];
         R[a][1] = y[a];
@@ -78,12 +86,16 @@ __global__ void k_load(const double *__restrict__ xyz, const double *__restrict_
         frame_ok = type == AP_FRAME_NONE;
     }
     if (!frame_ok) type = AP_FRAME_NONE;   // never index with a bad frame atom; reported below
-    double R[3][3];
-    frame_matrix(xyz, i, type, za, xa, L, iL, R, fvec + 6 * s);
+    // frames and rotations in the pair arithmetic's type (FP32 in the mixed and fixed modes:
+    // FP64 is a small fraction of the FP32 rate on this part, and the rotated multipoles are
+    // stored in that type anyway)
+    typedef T C;
+    C R[3][3];
+    frame_matrix<C>(xyz, i, type, za, xa, L, iL, R, fvec + 6 * s);
     const double *m = mpole + 10 * i;
-    double dl[3] = {m[1], m[2], m[3]};
-    double Ql[3][3] = {{m[4], m[5], m[6]}, {m[5], m[7], m[8]}, {m[6], m[8], m[9]}};
-    double dg[3], Qg[3][3], tmp[3][3];
+    const C dl[3] = {(C)m[1], (C)m[2], (C)m[3]};
+    const C Ql[3][3] = {{(C)m[4], (C)m[5], (C)m[6]}, {(C)m[5], (C)m[7], (C)m[8]}, {(C)m[6], (C)m[8], (C)m[9]}};
+    C dg[3], Qg[3][3], tmp[3][3];
     for (int a = 0; a < 3; ++a) dg[a] = R[a][0] * dl[0] + R[a][1] * dl[1] + R[a][2] * dl[2];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) tmp[a][b] = R[a][0] * Ql[0][b] + R[a][1] * Ql[1][b] + R[a][2] * Ql[2][b];

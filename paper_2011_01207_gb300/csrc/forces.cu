@@ -288,42 +288,48 @@ __global__ void k_recip_forces(const double *__restrict__ D, const double *__res
                                double *__restrict__ gquad, int fixed) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    auto Du = [&](int c) { return D[(size_t)c * n_pad + s]; };
-    auto DM = [&](int c) { return D[(size_t)(20 + c) * n_pad + s]; };
-    const double m[3] = {mu[s], mu[n_pad + s], mu[2 * n_pad + s]};
+    typedef T C;   // FP32 in the mixed and fixed modes (FP64 is slow on this part), FP64 in AP_FP64
+    auto Du = [&](int c) { return (C)D[(size_t)c * n_pad + s]; };
+    auto DM = [&](int c) { return (C)D[(size_t)(20 + c) * n_pad + s]; };
+    const C m[3] = {(C)mu[s], (C)mu[n_pad + s], (C)mu[2 * n_pad + s]};
     typename V4<T>::type a = posq[s], b = dipd[s], c = quad0[s], d = quad1[s];
-    const double q = a.w, dd[3] = {b.x, b.y, b.z};
-    const double Qxx = c.x, Qxy = c.y, Qxz = c.z, Qyy = c.w, Qyz = d.x, Qzz = d.y;
+    const C q = a.w, dd[3] = {b.x, b.y, b.z};
+    const C Qxx = c.x, Qxy = c.y, Qxz = c.z, Qyy = c.w, Qyz = d.x, Qzz = d.y;
     // symmetric Hessians: index (xx yy zz xy xz yz) -> 4..9
-    double Hu[3][3] = {{Du(4), Du(7), Du(8)}, {Du(7), Du(5), Du(9)}, {Du(8), Du(9), Du(6)}};
-    double HM[3][3] = {{DM(4), DM(7), DM(8)}, {DM(7), DM(5), DM(9)}, {DM(8), DM(9), DM(6)}};
-    const double gu[3] = {Du(1), Du(2), Du(3)};
+    C Hu[3][3] = {{Du(4), Du(7), Du(8)}, {Du(7), Du(5), Du(9)}, {Du(8), Du(9), Du(6)}};
+    C HM[3][3] = {{DM(4), DM(7), DM(8)}, {DM(7), DM(5), DM(9)}, {DM(8), DM(9), DM(6)}};
+    const C gu[3] = {Du(1), Du(2), Du(3)};
     // sum_bc Q_bc T_abc with T the third derivatives of phi_mu
-    const double Txxx = Du(10), Tyyy = Du(11), Tzzz = Du(12), Txxy = Du(13), Txxz = Du(14), Txyy = Du(15),
+    const C Txxx = Du(10), Tyyy = Du(11), Tzzz = Du(12), Txxy = Du(13), Txxz = Du(14), Txyy = Du(15),
                  Tyyz = Du(16), Txzz = Du(17), Tyzz = Du(18), Txyz = Du(19);
-    const double QT[3] = {
+    const C QT[3] = {
         Qxx * Txxx + Qyy * Txyy + Qzz * Txzz + 2 * (Qxy * Txxy + Qxz * Txxz + Qyz * Txyz),
         Qxx * Txxy + Qyy * Tyyy + Qzz * Tyzz + 2 * (Qxy * Txyy + Qxz * Txyz + Qyz * Tyyz),
         Qxx * Txxz + Qyy * Tyyz + Qzz * Tzzz + 2 * (Qxy * Txyz + Qxz * Txzz + Qyz * Tyzz)};
     for (int k = 0; k < 3; ++k) {
-        double g = 0.0;
+        C g = 0;
         for (int l = 0; l < 3; ++l) g += m[l] * (Hu[k][l] + HM[k][l]) + dd[l] * Hu[k][l];
-        g += q * gu[k] + QT[k] * (1.0 / 3.0);
-        add_plain(frc, (size_t)k * n_pad + s, -f * g, fixed);
-        add_plain(gdip, (size_t)k * n_pad + s, f * gu[k] - f * self_coef * m[k], fixed);
+        g += q * gu[k] + QT[k] * C(1.0 / 3.0);
+        add_plain(frc, (size_t)k * n_pad + s, -f * (double)g, fixed);
+        add_plain(gdip, (size_t)k * n_pad + s, f * (double)gu[k] - f * self_coef * (double)m[k], fixed);
     }
     const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-    for (int k = 0; k < 6; ++k) add_plain(gquad, (size_t)k * n_pad + s, f * (1.0 / 3.0) * Hu[ia[k]][ib[k]], fixed);
+    for (int k = 0; k < 6; ++k) add_plain(gquad, (size_t)k * n_pad + s, f * (1.0 / 3.0) * (double)Hu[ia[k]][ib[k]], fixed);
 }
 
-__device__ __forceinline__ double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
-__device__ __forceinline__ void cross3(const double *a, const double *b, double *o) {
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+template <class C>
+__device__ __forceinline__ C dot3(const C *a, const C *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+template <class C>
+__device__ __forceinline__ void cross3(const C *a, const C *b, C *o) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
 // frame chain rule: dU/dR = G_d d_l^T + 2 G_Q R Q_l, then through the axis construction
+template <class C>
 __global__ void k_frame_forces(const double *__restrict__ gdip, const double *__restrict__ gquad,
                                const double *__restrict__ rot, const double *__restrict__ mpl,
                                const double *__restrict__ fvec, const int *__restrict__ frame_s, int n, int n_pad,
@@ -333,70 +339,71 @@ __global__ void k_frame_forces(const double *__restrict__ gdip, const double *__
     const int type = frame_s[3 * s];
     if (type != AP_FRAME_Z_THEN_X && type != AP_FRAME_BISECTOR) return;
     const int zs = frame_s[3 * s + 1], xs = frame_s[3 * s + 2];
-    double R[3][3];
+    C R[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) R[a][b] = rot[9 * s + 3 * a + b];
     const double *m = mpl + 10 * s;
-    const double dl[3] = {m[1], m[2], m[3]};
-    const double Ql[3][3] = {{m[4], m[5], m[6]}, {m[5], m[7], m[8]}, {m[6], m[8], m[9]}};
-    const double Gd[3] = {acc_value(gdip, s, fixed), acc_value(gdip, (size_t)n_pad + s, fixed),
-                          acc_value(gdip, (size_t)2 * n_pad + s, fixed)};
-    double g6[6];
-    for (int k = 0; k < 6; ++k) g6[k] = acc_value(gquad, (size_t)k * n_pad + s, fixed);
-    const double GQ[3][3] = {{g6[0], g6[1], g6[2]}, {g6[1], g6[3], g6[4]}, {g6[2], g6[4], g6[5]}};
-    double RQ[3][3], dR[3][3];
+    const C dl[3] = {(C)m[1], (C)m[2], (C)m[3]};
+    const C Ql[3][3] = {{(C)m[4], (C)m[5], (C)m[6]}, {(C)m[5], (C)m[7], (C)m[8]}, {(C)m[6], (C)m[8], (C)m[9]}};
+    const C Gd[3] = {(C)acc_value(gdip, s, fixed), (C)acc_value(gdip, (size_t)n_pad + s, fixed),
+                     (C)acc_value(gdip, (size_t)2 * n_pad + s, fixed)};
+    C g6[6];
+    for (int k = 0; k < 6; ++k) g6[k] = (C)acc_value(gquad, (size_t)k * n_pad + s, fixed);
+    const C GQ[3][3] = {{g6[0], g6[1], g6[2]}, {g6[1], g6[3], g6[4]}, {g6[2], g6[4], g6[5]}};
+    C RQ[3][3], dR[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) RQ[a][b] = R[a][0] * Ql[0][b] + R[a][1] * Ql[1][b] + R[a][2] * Ql[2][b];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b)
-            dR[a][b] = Gd[a] * dl[b] + 2.0 * (GQ[a][0] * RQ[0][b] + GQ[a][1] * RQ[1][b] + GQ[a][2] * RQ[2][b]);
-    double gx[3], gy[3], gz[3], xa[3], za[3];
+            dR[a][b] = Gd[a] * dl[b] + C(2) * (GQ[a][0] * RQ[0][b] + GQ[a][1] * RQ[1][b] + GQ[a][2] * RQ[2][b]);
+    C gx[3], gy[3], gz[3], xa[3], za[3];
     for (int a = 0; a < 3; ++a) {
         gx[a] = dR[a][0]; gy[a] = dR[a][1]; gz[a] = dR[a][2];
         xa[a] = R[a][0]; za[a] = R[a][2];
     }
-    double t[3];
+    C t[3];
     cross3(gy, za, t);
     for (int a = 0; a < 3; ++a) gx[a] += t[a];
     cross3(xa, gy, t);
     for (int a = 0; a < 3; ++a) gz[a] += t[a];
-    const double *vz = fvec + 6 * s, *vx = fvec + 6 * s + 3;
-    double g_vz[3], g_vx[3];
+    const C vz[3] = {(C)fvec[6 * s], (C)fvec[6 * s + 1], (C)fvec[6 * s + 2]};
+    const C vx[3] = {(C)fvec[6 * s + 3], (C)fvec[6 * s + 4], (C)fvec[6 * s + 5]};
+    C g_vz[3], g_vx[3];
     if (type == AP_FRAME_Z_THEN_X) {
-        const double vxz = dot3(vx, za);
-        double w[3];
+        const C vxz = dot3(vx, za);
+        C w[3];
         for (int a = 0; a < 3; ++a) w[a] = vx[a] - vxz * za[a];
         // reciprocal norms with rsqrt: FP64 division and sqrt are slow on this part
-        const double inw = rsqrt(dot3(w, w)), inz = rsqrt(dot3(vz, vz));
-        const double gxx = dot3(gx, xa);
-        double gw[3];
+        const C inw = rsq(dot3(w, w)), inz = rsq(dot3(vz, vz));
+        const C gxx = dot3(gx, xa);
+        C gw[3];
         for (int a = 0; a < 3; ++a) gw[a] = (gx[a] - gxx * xa[a]) * inw;
-        const double gwz = dot3(gw, za);
+        const C gwz = dot3(gw, za);
         for (int a = 0; a < 3; ++a) {
             g_vx[a] = gw[a] - gwz * za[a];
             gz[a] = gz[a] - gwz * vx[a] - vxz * gw[a];
         }
-        const double gzz = dot3(gz, za);
+        const C gzz = dot3(gz, za);
         for (int a = 0; a < 3; ++a) g_vz[a] = (gz[a] - gzz * za[a]) * inz;
     } else {
-        const double in1 = rsqrt(dot3(vz, vz)), in2 = rsqrt(dot3(vx, vx));
-        double u1[3], u2[3], sv[3], w[3];
+        const C in1 = rsq(dot3(vz, vz)), in2 = rsq(dot3(vx, vx));
+        C u1[3], u2[3], sv[3], w[3];
         for (int a = 0; a < 3; ++a) { u1[a] = vz[a] * in1; u2[a] = vx[a] * in2; sv[a] = u1[a] + u2[a]; }
-        const double u2z = dot3(u2, za);
+        const C u2z = dot3(u2, za);
         for (int a = 0; a < 3; ++a) w[a] = u2[a] - u2z * za[a];
-        const double inw = rsqrt(dot3(w, w)), ins = rsqrt(dot3(sv, sv));
-        const double gxx = dot3(gx, xa);
-        double gw[3], gu2[3], gs[3];
+        const C inw = rsq(dot3(w, w)), ins = rsq(dot3(sv, sv));
+        const C gxx = dot3(gx, xa);
+        C gw[3], gu2[3], gs[3];
         for (int a = 0; a < 3; ++a) gw[a] = (gx[a] - gxx * xa[a]) * inw;
-        const double gwz = dot3(gw, za);
+        const C gwz = dot3(gw, za);
         for (int a = 0; a < 3; ++a) {
             gu2[a] = gw[a] - gwz * za[a];
             gz[a] = gz[a] - gwz * u2[a] - u2z * gw[a];
         }
-        const double gzz = dot3(gz, za);
+        const C gzz = dot3(gz, za);
         for (int a = 0; a < 3; ++a) gs[a] = (gz[a] - gzz * za[a]) * ins;
         for (int a = 0; a < 3; ++a) gu2[a] += gs[a];
-        const double a1 = dot3(gs, u1), a2 = dot3(gu2, u2);
+        const C a1 = dot3(gs, u1), a2 = dot3(gu2, u2);
         for (int a = 0; a < 3; ++a) {
             g_vz[a] = (gs[a] - a1 * u1[a]) * in1;
             g_vx[a] = (gu2[a] - a2 * u2[a]) * in2;
@@ -405,13 +412,13 @@ __global__ void k_frame_forces(const double *__restrict__ gdip, const double *__
     for (int a = 0; a < 3; ++a) {
         if (fixed) {
             unsigned long long *fx = reinterpret_cast<unsigned long long *>(frc);
-            atomicAdd(fx + a * n_pad + zs, (unsigned long long)ap_to_fx(-g_vz[a]));
-            atomicAdd(fx + a * n_pad + xs, (unsigned long long)ap_to_fx(-g_vx[a]));
-            atomicAdd(fx + a * n_pad + s, (unsigned long long)ap_to_fx(g_vz[a] + g_vx[a]));
+            atomicAdd(fx + a * n_pad + zs, (unsigned long long)ap_to_fx(-(double)g_vz[a]));
+            atomicAdd(fx + a * n_pad + xs, (unsigned long long)ap_to_fx(-(double)g_vx[a]));
+            atomicAdd(fx + a * n_pad + s, (unsigned long long)ap_to_fx((double)g_vz[a] + (double)g_vx[a]));
         } else {
-            atomicAdd(frc + a * n_pad + zs, -g_vz[a]);
-            atomicAdd(frc + a * n_pad + xs, -g_vx[a]);
-            atomicAdd(frc + a * n_pad + s, g_vz[a] + g_vx[a]);
+            atomicAdd(frc + a * n_pad + zs, -(double)g_vz[a]);
+            atomicAdd(frc + a * n_pad + xs, -(double)g_vx[a]);
+            atomicAdd(frc + a * n_pad + s, (double)g_vz[a] + (double)g_vx[a]);
         }
     }
 }
@@ -532,7 +539,7 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
                                                          ctx->gdip, ctx->gquad, ctx->fixed);
     AP_CUDA(cudaGetLastError());
     if (extra && (rc = extra(ctx, s))) return rc;
-    k_frame_forces<<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gdip, ctx->gquad, ctx->rot, ctx->mpl, ctx->fvec,
+    k_frame_forces<T><<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gdip, ctx->gquad, ctx->rot, ctx->mpl, ctx->fvec,
                                                        ctx->frame_s, n, n_pad, ctx->frc, ctx->fixed);
     AP_CUDA(cudaGetLastError());
     if (ctx->fixed) {
