@@ -44,38 +44,65 @@ __global__ void __launch_bounds__(256) k_filter(
         }
     const T cx = T(0.5) * (lo[0] + hi[0]), cy = T(0.5) * (lo[1] + hi[1]), cz = T(0.5) * (lo[2] + hi[2]);
     const int base = tile_off[I];
+    const int t_end = tile_off[I + 1];
     int count = 0;
-    for (int t = base; t < tile_off[I + 1]; ++t) {
-        const int J = tiles[t].y;
-        if (J == I) continue;
-        const int sj = J * 32 + lane;
-        T4 q = posq[sj];
-        // positions are relative to their block's origin: move j's to block I's origin and
-        // periodic image with the tile's offset, kept as a float pair (hi + lo) so that the
-        // result (a few A) has full FP32 precision at any box size
-        const float4 oh = tshift[t], ol = tshift_lo[t];
-        T x = (q.x + (T)ol.x) + (T)oh.x, y = (q.y + (T)ol.y) + (T)oh.y, z = (q.z + (T)ol.z) + (T)oh.z;
-        if (MINIMG) {
-            x -= Lx * rint((x - cx) / Lx);
-            y -= Ly * rint((y - cy) / Ly);
-            z -= Lz * rint((z - cz) / Lz);
+    // four tiles per round: their loads are issued together (one warp walks all of block I's
+    // tiles, so latency, not bandwidth, bounds this loop), then the selections are packed in
+    // tile order
+    constexpr int U = 4;
+    for (int t0 = base; t0 < t_end; t0 += U) {
+        int Jv[U], ev[U];
+        T4 qv[U];
+        float4 ohv[U], olv[U];
+        T wv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u;
+            Jv[u] = -1;
+            if (t < t_end) {
+                Jv[u] = tiles[t].y;
+                const int sj = Jv[u] * 32 + lane;
+                qv[u] = posq[sj];
+                wv[u] = dipd[sj].w;
+                ohv[u] = tshift[t];
+                olv[u] = tshift_lo[t];
+                ev[u] = tile_excl[t];
+            }
         }
-        const T gx = max(T(0), max(lo[0] - x, x - hi[0]));
-        const T gy = max(T(0), max(lo[1] - y, y - hi[1]));
-        const T gz = max(T(0), max(lo[2] - z, z - hi[2]));
-        const bool sel = isfinite((float)x) && (gx * gx + gy * gy + gz * gz < rc2);
-        const unsigned m = __ballot_sync(0xffffffffu, sel);
-        if (sel) {
-            const int k = count + __popc(m & ((1u << lane) - 1u));
-            const int e = tile_excl[t];
-            const size_t slot = (size_t)(base + (k >> 5)) * 32 + (k & 31);
-            chunk_j[slot] = sj;
-            T4 v;
-            v.x = x; v.y = y; v.z = z; v.w = dipd[sj].w;
-            chunk_pos[slot] = v;
-            chunk_src[slot] = e >= 0 ? (e << 5) | lane : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u;
+            const int J = Jv[u];
+            if (J < 0 || J == I) continue;   // uniform over the warp
+            const int sj = J * 32 + lane;
+            const T4 q = qv[u];
+            // positions are relative to their block's origin: move j's to block I's origin and
+            // periodic image with the tile's offset, kept as a float pair (hi + lo) so that the
+            // result (a few A) has full FP32 precision at any box size
+            const float4 oh = ohv[u], ol = olv[u];
+            T x = (q.x + (T)ol.x) + (T)oh.x, y = (q.y + (T)ol.y) + (T)oh.y, z = (q.z + (T)ol.z) + (T)oh.z;
+            if (MINIMG) {
+                x -= Lx * rint((x - cx) / Lx);
+                y -= Ly * rint((y - cy) / Ly);
+                z -= Lz * rint((z - cz) / Lz);
+            }
+            const T gx = max(T(0), max(lo[0] - x, x - hi[0]));
+            const T gy = max(T(0), max(lo[1] - y, y - hi[1]));
+            const T gz = max(T(0), max(lo[2] - z, z - hi[2]));
+            const bool sel = isfinite((float)x) && (gx * gx + gy * gy + gz * gz < rc2);
+            const unsigned m = __ballot_sync(0xffffffffu, sel);
+            if (sel) {
+                const int k = count + __popc(m & ((1u << lane) - 1u));
+                const int e = ev[u];
+                const size_t slot = (size_t)(base + (k >> 5)) * 32 + (k & 31);
+                chunk_j[slot] = sj;
+                T4 v;
+                v.x = x; v.y = y; v.z = z; v.w = wv[u];
+                chunk_pos[slot] = v;
+                chunk_src[slot] = e >= 0 ? (e << 5) | lane : -1;
+            }
+            count += __popc(m);
         }
-        count += __popc(m);
     }
     const int nc = (count + 31) >> 5;
     // phantom padding of the last chunk
