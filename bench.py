@@ -199,8 +199,8 @@ def pairs_within(xyz, box, rc):
 def launches_per_step(iters, n, rebuild_frac, learned_guess):
     """Kernels of this library launched by one step (cuFFT's own kernels not counted)."""
     pad = 1 if n % 32 else 0
-    field = 3 + 6 + pad                   # filter, worklist, pair masks, load, [pad], spread, convolve,
-    #                                       gather, pair field, assemble
+    field = 8 + pad + 5                   # load, filter, work offsets, work fill, pair masks, 3 prefix
+    #                                       scans, [pad]; spread, convolve, gather, pair field, assemble
     guess = 6 if learned_guess else 0     # alpha E, short-range field, features, MLP, assemble, extrapolation
     solve = 1 + 4 + 2 + 1 + 7 * iters + 1  # guess, matvec(4), residual, finish, cond, 7/iter, unsort
     forces = 10
