@@ -72,7 +72,7 @@ template <class T>
 __host__ __device__ constexpr int pf_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
 template <class T, bool MINIMG, bool FX>
-__global__ void __launch_bounds__(128) k_perm_field(
+__global__ void __launch_bounds__(128, 8) k_perm_field(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
     const typename V4<T>::type *__restrict__ quad0, const typename V4<T>::type *__restrict__ quad1,
     double *__restrict__ acc, int n_pad, PairConsts<T> pc) {
@@ -233,7 +233,7 @@ struct MvSmem {
 };
 
 template <class T, bool MINIMG, bool SHORT, bool FX>
-__global__ void __launch_bounds__(128) k_matvec(
+__global__ void __launch_bounds__(128, 12) k_matvec(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
     const typename V4<T>::type *__restrict__ pv, double *__restrict__ acc, int n_pad, PairConsts<T> pc) {
     typedef typename V4<T>::type T4;
