@@ -172,3 +172,21 @@ def test_window_growth_and_argument_errors(c1, oracle_c1):
     with pytest.raises(binding.ApError):
         c.solve_diis(tol=0.0, max_iter=10, depth=4)
     c.close()
+
+
+@pytest.mark.parametrize("n_mol,box,cutoff,buffer,grid", [
+    (1, 11.0, 4.0, 1.5, (8, 8, 8)),        # one molecule: a single, mostly padded block
+    (11, 12.0, 4.5, 1.5, (12, 10, 8)),     # 33 atoms: one full block and a 1-atom tail
+])
+def test_small_and_ragged(n_mol, box, cutoff, buffer, grid):
+    s = synth.water_box(n_mol, box, 77 + n_mol, dmin_inter=1.6)
+    c = binding.Context(s, cutoff=cutoff, buffer=buffer, beta=0.5446, grid=grid, precision=binding.AP_FP64)
+    c.build()
+    c.permanent_field()
+    o = Oracle(s, Params(beta=0.5446, grid=grid, cutoff=cutoff))
+    E = o.permanent_field()
+    info = c.solve_diis(tol=1e-8, max_iter=200, depth=5)
+    mu_o, info_o = o.jacobi_diis(E, tol=1e-8, depth=5)
+    assert info.iterations == info_o["iters"]
+    assert _rel_max(c.mu.cpu().numpy(), mu_o) < 1e-7
+    c.close()

@@ -167,3 +167,44 @@ def test_state_and_argument_errors(chain):
     info = c.solve_dp(tol=1e-12, max_iter=3)
     assert info.status == binding.AP_NOT_CONVERGED and info.iterations == 3
     c.close()
+
+
+def test_no_listed_pairs_gives_two_copies_of_the_single_set(chain):
+    """With an empty table both fields are the single-set field of the context's exclusion
+    list, so the lockstep solve returns that solve twice."""
+    s, pairs, scales = chain
+    c = _ctx(s, np.zeros((0, 2), np.int32), np.zeros((0, 2)), binding.AP_FP64)
+    c.permanent_field()
+    E = c.field.cpu().numpy()
+    assert _rel_max(c.field_d.cpu().numpy(), E) < 1e-14 and _rel_max(c.field_p.cpu().numpy(), E) < 1e-14
+    c.permanent_field_dp()
+    info = c.solve_dp(tol=1e-7, max_iter=100)
+    info1 = c.solve(tol=1e-7, max_iter=100)
+    assert info.iterations == info1.iterations
+    mu = c.mu.cpu().numpy()
+    assert _rel_max(c.mu_d.cpu().numpy(), mu) < 1e-12 and _rel_max(c.mu_p.cpu().numpy(), mu) < 1e-12
+    c.close()
+
+
+@pytest.mark.parametrize("n_chain,n_water,box,grid", [(7, 4, 12.0, (12, 12, 12)), (13, 8, 14.0, (16, 14, 12))])
+def test_small_and_ragged_chains(n_chain, n_water, box, grid):
+    """A few dozen atoms (one or two blocks with a ragged tail), non-cubic grid: FP64 fields,
+    iterations, dipoles, energy and forces against the oracle."""
+    s0 = synth.solvated_chain(n_chain, n_water, box, 300 + n_chain)
+    s, pairs, scales = synth.dp_system(s0, 11, 3, 5)
+    o = Oracle(s, Params(beta=0.5446, grid=grid, cutoff=5.0), dp=(pairs, scales))
+    E_d, E_p = o.permanent_field_dp()
+    c = binding.Context(s, cutoff=5.0, buffer=1.0, beta=0.5446, grid=grid, precision=binding.AP_FP64)
+    c.build()
+    c.set_scaled_pairs(pairs, scales)
+    c.permanent_field_dp()
+    assert _rel_rms(c.field_d.cpu().numpy(), E_d) < 1e-9 and _rel_rms(c.field_p.cpu().numpy(), E_p) < 1e-9
+    info = c.solve_dp(tol=1e-8, max_iter=200)
+    mu_d, mu_p, info_o = o.pcg_dp(E_d, E_p, tol=1e-8)
+    assert info.iterations == info_o["iters"]
+    assert _rel_max(c.mu_d.cpu().numpy(), mu_d) < 1e-7 and _rel_max(c.mu_p.cpu().numpy(), mu_p) < 1e-7
+    e, f = c.energy_forces_dp()
+    gd, gp = c.mu_d.cpu().numpy(), c.mu_p.cpu().numpy()
+    assert abs(float(e.cpu()[0]) - o.energy_dp(gd, E_p)) < 1e-9 * abs(o.energy_dp(gd, E_p))
+    assert _rel_rms(f.cpu().numpy(), o.forces_dp(gd, gp)) < 1e-8
+    c.close()
