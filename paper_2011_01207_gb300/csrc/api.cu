@@ -183,11 +183,13 @@ int permanent_field(ap_ctx *ctx, const double *d_xyz, const double *d_mpole, con
     if (!ctx->lists_valid) return ap_fail(ctx, AP_ERR_STATE, "build_neighbour_blocks() must come first");
     int r = cfg_load(ctx, d_xyz, d_mpole, d_frame, d_alpha);
     if (r) return r;
-    if ((r = filter_launch(ctx, ctx->s0))) return r;
-    AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
+    // the reciprocal branch needs only the loaded configuration: it runs on the second
+    // stream while the list filter, the pair masks and the real-space field run here
     AP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->s0));
     AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
     if ((r = pme_multipole_field(ctx, ctx->s1))) return r;
+    if ((r = filter_launch(ctx, ctx->s0))) return r;
+    AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
     if ((r = real_field_launch(ctx, ctx->s0))) return r;
     AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));
     AP_CUDA(cudaStreamWaitEvent(ctx->s0, ctx->ev_join, 0));
