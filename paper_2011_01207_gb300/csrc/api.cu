@@ -183,12 +183,18 @@ int permanent_field(ap_ctx *ctx, const double *d_xyz, const double *d_mpole, con
     if (!ctx->lists_valid) return ap_fail(ctx, AP_ERR_STATE, "build_neighbour_blocks() must come first");
     int r = cfg_load(ctx, d_xyz, d_mpole, d_frame, d_alpha);
     if (r) return r;
-    // the reciprocal branch needs only the loaded configuration: it runs on the second
-    // stream while the list filter, the pair masks and the real-space field run here
+    // the reciprocal branch needs only the loaded configuration. Run directly, it starts
+    // on the second stream while the list filter and the pair masks run here (one system
+    // leaves the GPU room for both); captured into a batch graph, where many replicas
+    // already fill the GPU, it starts after them (measured faster both ways)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    AP_CUDA(cudaStreamIsCapturing(ctx->s0, &cap));
+    const bool early = cap == cudaStreamCaptureStatusNone;
+    if (!early && (r = filter_launch(ctx, ctx->s0))) return r;
     AP_CUDA(cudaEventRecord(ctx->ev_fork, ctx->s0));
     AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
     if ((r = pme_multipole_field(ctx, ctx->s1))) return r;
-    if ((r = filter_launch(ctx, ctx->s0))) return r;
+    if (early && (r = filter_launch(ctx, ctx->s0))) return r;
     AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, ctx->s0));
     if ((r = real_field_launch(ctx, ctx->s0))) return r;
     AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));
