@@ -126,7 +126,12 @@ int permanent_field(ap_ctx* ctx, const double* d_xyz, const double* d_mpole,
  *   h_info    optional host struct filled with the iteration count and residuals;
  *             when non-NULL the call synchronizes.
  * Returns AP_NOT_CONVERGED (> 0) when max_iter was reached (d_mu holds the last iterate;
- * reported only when h_info is non-NULL). */
+ * reported only when h_info is non-NULL).
+ * The iteration loop runs as one CUDA graph with a conditional WHILE node (captured on the
+ * first call); with the environment variable AP_SOLVE_GRAPH=0 the same kernels are launched
+ * one by one with a host-side status read per iteration instead (for profilers that cannot
+ * attribute kernels inside conditional graphs). The same holds for induced_dipoles_diis and
+ * induced_dipoles_pcg_dp. */
 int induced_dipoles_pcg(ap_ctx* ctx, const double* d_guess, double tol_debye, int max_iter,
                         double* d_mu, ap_solve_info* h_info);
 
