@@ -56,6 +56,18 @@ HEADLINE_GUESS = "learned+extrapolated"
 DIIS_DEPTH = 6          # window of the Jacobi/DIIS solver timed beside the PCG
 
 
+def max_over_ranks(values, device=None):
+    """Element-wise maximum over all ranks of a torch.distributed job (the slowest rank's
+    time sets a weak-scaling step); the values themselves without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def captured_traffic():
     """DRAM bytes per launch of the real-space matvec from the committed ncu capture, if the
     kernel's sources are unchanged since (else None)."""
@@ -341,10 +353,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = float(np.mean(times))
     ms_plain = float(np.mean(times_plain))
-    if world > 1:
-        t = torch.tensor([ms, ms_plain], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_plain = float(t[0].item()), float(t[1].item())
+    ms, ms_plain = max_over_ranks([ms, ms_plain], dev)
 
     # end to end through the public API with host buffers: every step's positions copied in
     # from pinned host memory, forces and energy copied out, inside the timed region; the
@@ -367,7 +376,7 @@ def run_ours(args):
         b.synchronize()
         if k >= args.warmup:
             e2e.append(a.elapsed_time(b))
-    e2e_ms = float(np.mean(e2e))
+    e2e_ms = max_over_ranks([float(np.mean(e2e))], dev)[0]
 
     # dominant kernel: per-launch durations with CUDA events on the launch stream
     it_mean = float(np.mean(iters))
