@@ -193,19 +193,23 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const unsigned char *__rest
 // features in slot order (e = field / E_SCALE): e_i in the atom's frame (3), the short-range
 // first-order induced field e1_i in the same frame (3), e at the z- and x-atoms in i's frame
 // (3 + 3), |e_i|, |e1_i|, alpha_i, frame kind (0 global, 0.5 Z-then-X, 1 bisector)
+// C: the arithmetic type (FP32 in the mixed and fixed modes - the features are FP32 inputs
+// of a BF16 network, and FP64 is slow on this part - FP64 in AP_FP64)
+template <class C>
 __global__ void k_features(const double *__restrict__ E, const double *__restrict__ E1, const double *__restrict__ rot,
                            const double *__restrict__ alpha, const int *__restrict__ frame_s, int n, int n_pad,
                            float *__restrict__ feat, int e1_fixed) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const double *R = rot + 9 * s;
-    auto loc = [&](const double *F, int slot, double *o, int fx) {
-        const double e[3] = {acc_value(F, slot, fx) * (1.0 / MLP_E_SCALE),
-                             acc_value(F, (size_t)n_pad + slot, fx) * (1.0 / MLP_E_SCALE),
-                             acc_value(F, (size_t)2 * n_pad + slot, fx) * (1.0 / MLP_E_SCALE)};
+    C R[9];
+    for (int k = 0; k < 9; ++k) R[k] = (C)rot[9 * s + k];
+    auto loc = [&](const double *F, int slot, C *o, int fx) {
+        const C e[3] = {(C)(acc_value(F, slot, fx) * (1.0 / MLP_E_SCALE)),
+                        (C)(acc_value(F, (size_t)n_pad + slot, fx) * (1.0 / MLP_E_SCALE)),
+                        (C)(acc_value(F, (size_t)2 * n_pad + slot, fx) * (1.0 / MLP_E_SCALE))};
         for (int b = 0; b < 3; ++b) o[b] = R[0 * 3 + b] * e[0] + R[1 * 3 + b] * e[1] + R[2 * 3 + b] * e[2];
     };
-    double f[16];
+    C f[16];
     loc(E, s, f, 0);
     loc(E1, s, f + 3, e1_fixed);
     const int type = frame_s[3 * s];
@@ -213,12 +217,12 @@ __global__ void k_features(const double *__restrict__ E, const double *__restric
         loc(E, frame_s[3 * s + 1], f + 6, 0);
         loc(E, frame_s[3 * s + 2], f + 9, 0);
     } else {
-        for (int k = 6; k < 12; ++k) f[k] = 0.0;
+        for (int k = 6; k < 12; ++k) f[k] = C(0);
     }
     f[12] = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
     f[13] = sqrt(f[3] * f[3] + f[4] * f[4] + f[5] * f[5]);
-    f[14] = alpha[s];
-    f[15] = type == AP_FRAME_BISECTOR ? 1.0 : (type == AP_FRAME_Z_THEN_X ? 0.5 : 0.0);
+    f[14] = (C)alpha[s];
+    f[15] = type == AP_FRAME_BISECTOR ? C(1) : (type == AP_FRAME_Z_THEN_X ? C(0.5) : C(0));
     for (int k = 0; k < 16; ++k) feat[(size_t)s * 16 + k] = (float)f[k];
 }
 
@@ -523,8 +527,12 @@ int features_slots(ap_ctx *ctx) {
     AP_CUDA(cudaMemsetAsync(ctx->e1s, 0, sizeof(double) * 3 * ctx->n_pad, st));
     int r = short_matvec_launch(ctx, ctx->p, ctx->e1s, st);
     if (r) return r;
-    k_features<<<ap_grid_for(n, 128), 128, 0, st>>>(ctx->E, ctx->e1s, ctx->rot, ctx->alpha, ctx->frame_s, n, ctx->n_pad,
-                                                   ctx->mlp_feat, ctx->fixed);
+    if (ctx->prec == AP_FP64)
+        k_features<double><<<ap_grid_for(n, 128), 128, 0, st>>>(ctx->E, ctx->e1s, ctx->rot, ctx->alpha, ctx->frame_s, n,
+                                                                ctx->n_pad, ctx->mlp_feat, ctx->fixed);
+    else
+        k_features<float><<<ap_grid_for(n, 128), 128, 0, st>>>(ctx->E, ctx->e1s, ctx->rot, ctx->alpha, ctx->frame_s, n,
+                                                               ctx->n_pad, ctx->mlp_feat, ctx->fixed);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
