@@ -174,7 +174,7 @@ int induced_dipoles_diis(ap_ctx* ctx, const double* d_guess, double tol_debye, i
  *   (so that E_c leaves it out); listed pairs farther apart than the cutoff contribute
  *   nothing, as every pair beyond it. Synchronizes; AP_ERR_ARG for an index out of range,
  *   i == j or a non-finite scale. The first call allocates the two-set buffers (about
- *   40 doubles per atom). */
+ *   70 doubles per atom, and a second PME grid pair with its own cuFFT plans). */
 int set_scaled_pairs(ap_ctx* ctx, int n_pairs, const int* d_pairs, const double* d_scales);
 
 /* f1 - E_d and E_p of a configuration: runs permanent_field() (E_c, kept for the forces),
