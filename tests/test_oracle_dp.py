@@ -136,3 +136,27 @@ def test_lockstep_pcg_matches_dense_solves(chain_dp):
     assert info["eps"] == max(info["eps_d"], info["eps_p"]) <= 1e-11
     np.testing.assert_allclose(mu_d.ravel(), np.linalg.solve(A, E_d.ravel()), rtol=0, atol=1e-10)
     np.testing.assert_allclose(mu_p.ravel(), np.linalg.solve(A, E_p.ravel()), rtol=0, atol=1e-10)
+
+
+def test_scale_table_follows_its_definition():
+    """Every chain pair's (d, p) scales against the rule written out pair by pair: d = 0
+    inside a polarization group; p = 0 at bond separation 1 or 2, 1/2 at separation 3
+    inside a group, 1 otherwise; waters: both 0 inside a molecule. Pairs absent from the
+    table must have (1, 1)."""
+    s = synth.solvated_chain(14, 3, 14.0, 77)
+    pairs, scales = synth.dp_scales(s, synth.polarization_groups(s, 4, 3, 6))
+    table = {(int(a), int(b)): tuple(v) for (a, b), v in zip(pairs, scales)}
+    g = synth.polarization_groups(s, 4, 3, 6)
+    chain = [i for i in range(s.n) if s.rigid[i] == 0]
+    for x in range(s.n):
+        for y in range(x + 1, s.n):
+            if x in chain and y in chain:
+                sep = abs(chain.index(x) - chain.index(y))
+                same = g[x] == g[y]
+                d = 0.0 if same else 1.0
+                p = 0.0 if sep <= 2 else (0.5 if sep == 3 and same else 1.0)
+            elif s.mol[x] == s.mol[y] and s.rigid[x] == 1:
+                d, p = 0.0, 0.0
+            else:
+                d, p = 1.0, 1.0
+            assert table.get((x, y), (1.0, 1.0)) == (d, p), (x, y)
