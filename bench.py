@@ -5,12 +5,14 @@ to 1e-5 D RMS).
 One step = one pass of the whole hot path on a new synthetic configuration: neighbour
 blocks (rebuilt every REBUILD steps, amortised), permanent field (real + PME + self), the
 guess, the PCG solve, and the polarization energy and forces. The reported value uses the
-learned guess (the network is trained in the untimed set-up on ~10^6 pairs from converged
-solves of separate configurations); the same steps with the plain guess alpha E are timed
-alongside. Inputs (every step's
-positions) are resident on the device before timing; the L2 is flushed between timed
-steps (the working set, ~60 MB, fits the 129 MB L2). `--impl reference` times the FP64
-oracle on the host cores on a bounded sample of the same workload.
+learned guess plus the extrapolation of its error over the two previous steps (the network
+is trained in the untimed set-up on ~10^6 pairs from converged solves of separate
+configurations); the same steps with the learned guess alone, the plain guess alpha E and
+other guesses, the Jacobi/DIIS solver and the fixed-point mode are timed alongside. Inputs
+(every step's positions) are resident on the device before timing; the L2 is flushed
+between timed steps (the working set, ~60 MB, fits the 129 MB L2). `--impl reference`
+times the FP64 oracle on the host cores on a bounded sample of the same workload. Other
+workloads: `--workload two_sets | replicas64 | precision`.
 
 Prints one JSON line (rank 0).
 """
