@@ -216,7 +216,7 @@ def launches_per_step(iters, n, rebuild_frac, learned_guess):
     field = 8 + pad + 5                   # load, filter, work offsets, work fill, pair masks, 3 prefix
     #                                       scans, [pad]; spread, convolve, gather, pair field, assemble
     guess = 6 if learned_guess else 0     # alpha E, short-range field, features, MLP, assemble, extrapolation
-    solve = 1 + 4 + 2 + 1 + 7 * iters + 1  # guess, matvec(4), residual, finish, cond, 7/iter, unsort
+    solve = 1 + 4 + 1 + 1 + 7 * iters + 1  # guess, matvec(4), residual (+ state), cond, 7/iter, unsort
     forces = 10
     build = 14 * rebuild_frac
     return field + guess + solve + forces + build

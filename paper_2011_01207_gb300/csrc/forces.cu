@@ -516,19 +516,19 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
     const double f = AP_COULOMB;
     const double self_coef = 4.0 * std::pow(ctx->prm.ewald_beta, 3) / (3.0 * AP_SQRT_PI);
     k_mu_load<T><<<ap_grid_for(n_pad, 256), 256, 0, s>>>(d_mu, ctx->perm, n, n_pad, ctx->mu_s, (T4 *)ctx->p);
+    // reciprocal-space potential derivatives on the second stream, concurrent with the
+    // energy and the real-space pair forces (they write only gbuf and the grid); joined
+    // before the kernels that update the force arrays per atom
+    AP_CUDA(cudaEventRecord(ctx->ev_fork, s));
+    AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
+    int rc = pme_forces_derivs(ctx, ctx->p, ctx->gbuf, ctx->s1);
+    if (rc) return rc;
     AP_CUDA(cudaMemsetAsync(ctx->frc, 0, sizeof(double) * 3 * n_pad, s));
     AP_CUDA(cudaMemsetAsync(ctx->gdip, 0, sizeof(double) * 3 * n_pad, s));
     AP_CUDA(cudaMemsetAsync(ctx->gquad, 0, sizeof(double) * 6 * n_pad, s));
     AP_CUDA(cudaMemsetAsync(ctx->red + 8, 0, sizeof(double), s));
     // energy
     k_energy<<<ap_grid_for(n_pad, 256), 256, 0, s>>>(ctx->mu_s, ctx->E, n_pad, -0.5 * f, ctx->red + 8, ctx->fixed);
-    // reciprocal-space potential derivatives on the second stream, concurrent with the
-    // real-space pair forces (they write only gbuf and the grid); joined before the kernels
-    // that update the force arrays per atom
-    AP_CUDA(cudaEventRecord(ctx->ev_fork, s));
-    AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
-    int rc = pme_forces_derivs(ctx, ctx->p, ctx->gbuf, ctx->s1);
-    if (rc) return rc;
     rc = pair_forces_t<T>(ctx, s, ctx->posq, ctx->dipd, ctx->quad0, ctx->quad1, ctx->frc, ctx->gdip, ctx->gquad);
     if (rc) return rc;
     AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));

@@ -73,37 +73,6 @@ __global__ void k_init_guess(const double *__restrict__ guess, const double *__r
     p[s] = v;
 }
 
-// r_0 = E - A mu_0, partial sums of r.z and z.z; clears acc and p
-template <class T>
-__global__ void k_init_residual(const double *__restrict__ E, const double *__restrict__ alpha,
-                                const double *__restrict__ mu, double *__restrict__ acc,
-                                const T *__restrict__ rec, const double *__restrict__ dg, int n_pad,
-                                double *__restrict__ r, typename V4<T>::type *__restrict__ p,
-                                double *__restrict__ part, int fixed) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    double rz = 0.0, zz = 0.0;
-    if (s < n_pad) {
-        const double a = alpha[s], d = dg[s];
-        for (int c = 0; c < 3; ++c) {
-            const int k = c * n_pad + s;
-            double Amu = a > 0.0 ? mu[k] * d - acc_value(acc, k, fixed) - (double)rec[k] : 0.0;
-            double rr = a > 0.0 ? E[k] - Amu : 0.0;
-            r[k] = rr;
-            acc[k] = 0.0;
-            rz += rr * a * rr;
-            zz += a * rr * a * rr;
-        }
-        typename V4<T>::type v;
-        v.x = v.y = v.z = v.w = (T)0;
-        p[s] = v;
-    }
-    block_sum2<NT>(rz, zz);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = rz;
-        part[gridDim.x + blockIdx.x] = zz;
-    }
-}
-
 // sum of nparts partials (one block of NT threads, fixed order: deterministic)
 __device__ __forceinline__ void sum_partials2(const double *part, int nparts, double &a, double &b) {
     a = 0.0;
@@ -113,28 +82,6 @@ __device__ __forceinline__ void sum_partials2(const double *part, int nparts, do
         b += __ldcg(part + nparts + k);
     }
     block_sum2<NT>(a, b);
-}
-
-__global__ void k_init_finish(PcgState *st, const double *__restrict__ part, int nparts, int n, double tol,
-                              int max_iter) {
-    double rz, zz;
-    sum_partials2(part, nparts, rz, zz);
-    if (threadIdx.x != 0) return;
-    double eps = AP_DEBYE * sqrt(zz / n);
-    st->rz = rz;
-    st->eps = eps;
-    st->eps0 = eps;
-    st->tol = tol;
-    st->iter = 0;
-    st->max_iter = max_iter;
-    st->beta = 0.0;
-    st->gamma = 0.0;
-    st->nonfinite = !isfinite(eps);
-    st->done = (eps <= tol) || st->nonfinite;
-    st->status = AP_OK;
-    st->pq = st->rz_new = st->zz = 0.0;
-    st->blocks_done = 0;
-    st->guard = 0;
 }
 
 __global__ void k_set_cond(cudaGraphConditionalHandle h, const PcgState *st) {
@@ -181,6 +128,57 @@ __device__ __forceinline__ bool last_block(unsigned int *counter) {
     }
     __syncthreads();
     return last;
+}
+
+// r_0 = E - A mu_0, partial sums of r.z and z.z; clears acc and p. The last block sums the
+// partials in a fixed order and sets the initial state (eps_0, the stop decision).
+template <class T>
+__global__ void k_init_residual(const double *__restrict__ E, const double *__restrict__ alpha,
+                                const double *__restrict__ mu, double *__restrict__ acc,
+                                const T *__restrict__ rec, const double *__restrict__ dg, int n_pad,
+                                double *__restrict__ r, typename V4<T>::type *__restrict__ p,
+                                double *__restrict__ part, int fixed, PcgState *st, int n, double tol,
+                                int max_iter) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double rz = 0.0, zz = 0.0;
+    if (s < n_pad) {
+        const double a = alpha[s], d = dg[s];
+        for (int c = 0; c < 3; ++c) {
+            const int k = c * n_pad + s;
+            double Amu = a > 0.0 ? mu[k] * d - acc_value(acc, k, fixed) - (double)rec[k] : 0.0;
+            double rr = a > 0.0 ? E[k] - Amu : 0.0;
+            r[k] = rr;
+            acc[k] = 0.0;
+            rz += rr * a * rr;
+            zz += a * rr * a * rr;
+        }
+        typename V4<T>::type v;
+        v.x = v.y = v.z = v.w = (T)0;
+        p[s] = v;
+    }
+    block_sum2<NT>(rz, zz);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = rz;
+        part[gridDim.x + blockIdx.x] = zz;
+    }
+    if (!last_block(&st->blocks_done)) return;
+    double rzt, zzt;
+    sum_partials2(part, gridDim.x, rzt, zzt);
+    if (threadIdx.x != 0) return;
+    const double eps = AP_DEBYE * sqrt(zzt / n);
+    st->rz = rzt;
+    st->eps = eps;
+    st->eps0 = eps;
+    st->tol = tol;
+    st->iter = 0;
+    st->max_iter = max_iter;
+    st->beta = 0.0;
+    st->gamma = 0.0;
+    st->nonfinite = !isfinite(eps);
+    st->done = (eps <= tol) || st->nonfinite;
+    st->status = AP_OK;
+    st->pq = st->rz_new = st->zz = 0.0;
+    st->guard = 0;
 }
 
 // p = alpha r + beta p
@@ -373,8 +371,8 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
     int rc = matvec_into<T>(ctx, ctx->p);
     if (rc) return rc;
     k_init_residual<T><<<nb, NT, 0, s>>>(ctx->E, ctx->alpha, ctx->mu, ctx->acc, (const T *)ctx->rec, ctx->dg,
-                                          ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->red_part, ctx->fixed);
-    k_init_finish<<<1, NT, 0, s>>>(ctx->st, ctx->red_part, nb, ctx->n, tol, max_iter);
+                                          ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->red_part, ctx->fixed, ctx->st,
+                                          ctx->n, tol, max_iter);
     AP_CUDA(cudaGetLastError());
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     AP_CUDA(cudaStreamIsCapturing(s, &cap));
