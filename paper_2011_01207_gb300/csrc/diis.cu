@@ -346,11 +346,22 @@ int build_diis_graph(ap_ctx *ctx) {
 
 // rings for `depth` steps, partial sums and state; drops a graph made for smaller rings
 int diis_reserve(ap_ctx *ctx, int depth) {
-    if (!ctx->diis_st) {
-        AP_CUDA(cudaMalloc(&ctx->diis_st, sizeof(DiisState)));
-        AP_CUDA(cudaMallocHost(&ctx->diis_st_host, sizeof(DiisState)));
+    if (!ctx->diis_st || !ctx->diis_st_host || !ctx->diis_part) {
+        // state, its pinned mirror and the partial sums together, or none
         const int nb = ap_grid_for(ctx->n_pad, NT);
-        AP_CUDA(cudaMalloc((void **)&ctx->diis_part, sizeof(double) * AP_DIIS_MAX_DEPTH * nb));
+        cudaError_t e = cudaSuccess;
+        if (!ctx->diis_st) e = cudaMalloc(&ctx->diis_st, sizeof(DiisState));
+        if (e == cudaSuccess && !ctx->diis_st_host) e = cudaMallocHost(&ctx->diis_st_host, sizeof(DiisState));
+        if (e == cudaSuccess && !ctx->diis_part)
+            e = cudaMalloc((void **)&ctx->diis_part, sizeof(double) * AP_DIIS_MAX_DEPTH * nb);
+        if (e != cudaSuccess) {
+            if (ctx->diis_st) cudaFree(ctx->diis_st);
+            if (ctx->diis_st_host) cudaFreeHost(ctx->diis_st_host);
+            if (ctx->diis_part) cudaFree(ctx->diis_part);
+            ctx->diis_st = ctx->diis_st_host = nullptr;
+            ctx->diis_part = nullptr;
+            return ap_fail(ctx, AP_ERR_CUDA, std::string("DIIS state allocation: ") + cudaGetErrorString(e));
+        }
     }
     if (depth > ctx->diis_cap) {
         if (ctx->diis_exec) cudaGraphExecDestroy(ctx->diis_exec);
@@ -358,9 +369,16 @@ int diis_reserve(ap_ctx *ctx, int depth) {
         if (ctx->diis_y) cudaFree(ctx->diis_y);
         if (ctx->diis_e) cudaFree(ctx->diis_e);
         ctx->diis_y = ctx->diis_e = nullptr;
+        ctx->diis_cap = 0;
         const size_t bytes = sizeof(double) * 3 * (size_t)ctx->n_pad * depth;
-        AP_CUDA(cudaMalloc((void **)&ctx->diis_y, bytes));
-        AP_CUDA(cudaMalloc((void **)&ctx->diis_e, bytes));
+        cudaError_t e = cudaMalloc((void **)&ctx->diis_y, bytes);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->diis_e, bytes);
+        if (e != cudaSuccess) {
+            if (ctx->diis_y) cudaFree(ctx->diis_y);
+            ctx->diis_y = nullptr;
+            ctx->diis_e = nullptr;
+            return ap_fail(ctx, AP_ERR_CUDA, std::string("DIIS ring allocation: ") + cudaGetErrorString(e));
+        }
         ctx->diis_cap = depth;
     }
     return AP_OK;

@@ -30,6 +30,7 @@
 #include <cstdlib>
 
 void unsort3(ap_ctx *ctx, const double *src, double *out, cudaStream_t s);
+void dp_release_impl(ap_ctx *ctx);
 
 struct DpState {
     double rz[2], pq[2], gamma[2], beta[2], eps[2], eps0[2];
@@ -789,8 +790,17 @@ int dmalloc(ap_ctx *ctx, P **p, size_t bytes) {
     return AP_OK;
 }
 
+int reserve_all(ap_ctx *ctx);
+
+// all two-set buffers, or none (a failed allocation releases what was taken)
 int reserve(ap_ctx *ctx) {
     if (ctx->dp) return AP_OK;
+    const int r = reserve_all(ctx);
+    if (r) dp_release_impl(ctx);
+    return r;
+}
+
+int reserve_all(ap_ctx *ctx) {
     DpBuffers *B = new DpBuffers();
     ctx->dp = B;
     const size_t np = ctx->n_pad, n = ctx->n;
@@ -828,6 +838,8 @@ int dp_set_pairs(ap_ctx *ctx, int n_pairs, const int *d_pairs, const double *d_s
     int r = reserve(ctx);
     if (r) return r;
     DpBuffers *B = dpb(ctx);
+    B->n_pairs = 0;   // no table until this one is copied and checked
+    B->field_valid = 0;
     if (n_pairs > B->cap_pairs) {
         if (B->pairs) cudaFree(B->pairs);
         if (B->scales) cudaFree(B->scales);
@@ -838,8 +850,6 @@ int dp_set_pairs(ap_ctx *ctx, int n_pairs, const int *d_pairs, const double *d_s
         AP_CUDA(cudaMalloc((void **)&B->scales, sizeof(double2) * n_pairs));
         B->cap_pairs = n_pairs;
     }
-    B->n_pairs = 0;
-    B->field_valid = 0;
     if (n_pairs == 0) return AP_OK;
     AP_CUDA(cudaMemsetAsync(B->flag, 0, sizeof(int), ctx->s0));
     k_pairs_check<<<ap_grid_for(n_pairs, 256), 256, 0, ctx->s0>>>(d_pairs, d_scales, n_pairs, ctx->n, B->pairs,
@@ -934,7 +944,9 @@ void dp_forget_graph(ap_ctx *ctx) {
     B->exec_tried = 0;
 }
 
-void dp_release(ap_ctx *ctx) {
+void dp_release(ap_ctx *ctx) { dp_release_impl(ctx); }
+
+void dp_release_impl(ap_ctx *ctx) {
     DpBuffers *B = dpb(ctx);
     if (!B) return;
     if (B->exec) cudaGraphExecDestroy(B->exec);
