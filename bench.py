@@ -54,7 +54,7 @@ MLP_FLOPS_PER_ATOM = 2 * (16 * 128 + 128 * 128 + 128 * 3)
 # (p, q, alpha, mu and r in/out)
 PCG_VECTOR_BYTES_PER_SLOT = 64 + 108 + 144
 WORKLOAD = "water_96000_atoms_98.7A_grid100_rc7+2_mixed_pcg1e-5"
-HEADLINE_GUESS = "learned+extrapolated"
+HEADLINE_GUESS = "learned+adaptive"
 DIIS_DEPTH = 6          # window of the Jacobi/DIIS solver timed beside the PCG
 
 
@@ -215,7 +215,7 @@ def launches_per_step(iters, n, rebuild_frac, learned_guess):
     pad = 1 if n % 32 else 0
     field = 8 + pad + 5                   # load, filter, work offsets, work fill, pair masks, 3 prefix
     #                                       scans, [pad]; spread, convolve, gather, pair field, assemble
-    guess = 6 if learned_guess else 0     # alpha E, short-range field, features, MLP, assemble, extrapolation
+    guess = 7 if learned_guess else 0     # alpha E, short-range field, features, MLP, assemble, adaptive (2)
     solve = 1 + 4 + 1 + 1 + 7 * iters + 1  # guess, matvec(4), residual (+ state), cond, 7/iter, unsort
     forces = 10
     build = 14 * rebuild_frac
@@ -256,16 +256,21 @@ def run_ours(args):
     del feat, tgt
 
     # ring buffers for the trajectory guesses: converged dipoles and learned guesses of the
-    # last three steps (written in place by the library, no copies)
-    ring_mu = [torch.zeros((s.n, 3), dtype=torch.float64, device=dev) for _ in range(3)]
-    ring_g = [torch.zeros((s.n, 3), dtype=torch.float64, device=dev) for _ in range(3)]
+    # current and the last three steps (written in place by the library, no copies)
+    RING = 4
+    ring_mu = [torch.zeros((s.n, 3), dtype=torch.float64, device=dev) for _ in range(RING)]
+    ring_g = [torch.zeros((s.n, 3), dtype=torch.float64, device=dev) for _ in range(RING)]
+    scratch = torch.zeros(binding.AP_ADAPTIVE_SCRATCH, dtype=torch.float64, device=dev)
     hist = {"count": 0}
 
     def step(k, xyz, use_learned, ctx=ctx, solver="pcg"):
         """use_learned: True (MLP), False (alpha E), "zero", "extrapolated" (2 mu(t-1) -
-        mu(t-2)) or "learned+extrapolated" (the learned guess plus the extrapolation of its
-        error over the two previous steps); the trajectory guesses fall back to alpha E or
-        the learned guess until two previous steps exist."""
+        mu(t-2)), "learned+extrapolated" (the learned guess plus the linear extrapolation
+        of its error over the two previous steps), "learned+previous" (plus its previous
+        error) or "learned+adaptive" (plus its error extrapolated with the least-squares
+        coefficient of the three previous steps, ap_adaptive_guess; the previous error
+        while fewer steps exist); the trajectory guesses fall back to alpha E or the learned
+        guess until enough previous steps exist."""
         if k % REBUILD == 0:
             binding.build_neighbour_blocks(ctx.ctx, xyz, ctx.excl_off, ctx.excl_atoms, ctx.n_excl)
         binding.permanent_field(ctx.ctx, xyz, ctx.mpole, ctx.frame, ctx.alpha, None)
@@ -278,26 +283,39 @@ def run_ours(args):
             mu0.zero_()
             guess = mu0
         elif use_learned == "extrapolated":
-            out = ring_mu[k % 3]
+            out = ring_mu[k % RING]
             if ready:
-                binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % 3], ring_mu[(k - 2) % 3])
+                binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % RING], ring_mu[(k - 2) % RING])
                 guess = mu0
         elif use_learned == "learned+extrapolated":
-            out = ring_mu[k % 3]
-            binding.ap_learned_guess(ctx.ctx, trainer.packed, ring_g[k % 3])
-            guess = ring_g[k % 3]
+            out = ring_mu[k % RING]
+            binding.ap_learned_guess(ctx.ctx, trainer.packed, ring_g[k % RING])
+            guess = ring_g[k % RING]
             if ready:
-                binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % 3], ring_mu[(k - 2) % 3], base=ring_g[k % 3],
-                                             base1=ring_g[(k - 1) % 3], base2=ring_g[(k - 2) % 3])
+                binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % RING], ring_mu[(k - 2) % RING], base=ring_g[k % RING],
+                                             base1=ring_g[(k - 1) % RING], base2=ring_g[(k - 2) % RING])
+                guess = mu0
+        elif use_learned == "learned+adaptive":
+            out = ring_mu[k % RING]
+            g = ring_g[k % RING]
+            binding.ap_learned_guess(ctx.ctx, trainer.packed, g)
+            guess = g
+            m1, m2, m3 = (ring_mu[(k - j) % RING] for j in (1, 2, 3))
+            g1, g2, g3 = (ring_g[(k - j) % RING] for j in (1, 2, 3))
+            if hist["count"] >= 3:
+                binding.ap_adaptive_guess(mu0, m1, m2, m3, scratch, base=g, base1=g1, base2=g2, base3=g3)
+                guess = mu0
+            elif hist["count"] >= 1:
+                binding.ap_extrapolate_guess(mu0, m1, m1, base=g, base1=g1, base2=g1)
                 guess = mu0
         elif use_learned == "learned+previous":
             # zero-order hold of the learned guess's error: g(t) + (mu - g)(t-1)
-            out = ring_mu[k % 3]
-            binding.ap_learned_guess(ctx.ctx, trainer.packed, ring_g[k % 3])
-            guess = ring_g[k % 3]
+            out = ring_mu[k % RING]
+            binding.ap_learned_guess(ctx.ctx, trainer.packed, ring_g[k % RING])
+            guess = ring_g[k % RING]
             if hist["count"] >= 1:
-                binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % 3], ring_mu[(k - 1) % 3], base=ring_g[k % 3],
-                                             base1=ring_g[(k - 1) % 3], base2=ring_g[(k - 1) % 3])
+                binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % RING], ring_mu[(k - 1) % RING], base=ring_g[k % RING],
+                                             base1=ring_g[(k - 1) % RING], base2=ring_g[(k - 1) % RING])
                 guess = mu0
         if solver == "diis":
             binding.induced_dipoles_diis(ctx.ctx, guess, TOL, 200, DIIS_DEPTH, out, want_info=False)
@@ -341,6 +359,8 @@ def run_ours(args):
     times_ext, iters_ext = timed("extrapolated", "timed_steps_extrapolated")
     hist["count"] = 0
     times_lprev, iters_lprev = timed("learned+previous", "timed_steps_learned_previous")
+    hist["count"] = 0
+    times_lext, iters_lext = timed("learned+extrapolated", "timed_steps_learned_extrapolated")
     # the same steps with the Jacobi/DIIS solver in place of the PCG
     hist["count"] = 0
     times_diis, iters_diis = timed(HEADLINE_GUESS, "timed_steps_diis", solver="diis")
@@ -420,8 +440,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 pair/PME arithmetic, f64 accumulation", "data": "synthetic",
         "config": {"workload": WORKLOAD, "atoms": s.n,
-                   "guess": "learned (16-128-128-3 BF16 MLP) plus the trajectory extrapolation of its error: "
-                            "learned(t) + 2 (mu - learned)(t-1) - (mu - learned)(t-2)",
+                   "guess": "learned (16-128-128-3 BF16 MLP) plus the adaptive extrapolation of its error: "
+                            "learned(t) + e1 + c (e1 - e2), e = mu - learned at t-1, t-2, c the least-squares "
+                            "coefficient of the three previous steps (ap_adaptive_guess)",
                    "pcg_iters_mean": it_mean, "pcg_iters": [int(min(iters)), int(max(iters))],
                    "plain_guess": {"ms_per_step": round(ms_plain, 4), "pcg_iters_mean": float(np.mean(iters_plain)),
                                    "guess": "alpha*E"},
@@ -441,6 +462,9 @@ def run_ours(args):
                    "other_guesses": {
                        "zero": {"ms_per_step": round(float(np.mean(times_zero)), 4),
                                 "pcg_iters_mean": float(np.mean(iters_zero))},
+                       "learned+extrapolated": {"ms_per_step": round(float(np.mean(times_lext)), 4),
+                                                "pcg_iters_mean": float(np.mean(iters_lext)),
+                                                "guess": "learned(t) + 2 (mu - learned)(t-1) - (mu - learned)(t-2)"},
                        "extrapolated": {"ms_per_step": round(float(np.mean(times_ext)), 4),
                                         "pcg_iters_mean": float(np.mean(iters_ext)),
                                         "guess": "2 mu(t-1) - mu(t-2) from the previous steps' solves"},

@@ -343,6 +343,22 @@ int ap_learned_guess(ap_ctx* ctx, const void* d_packed, double* d_mu0);
 int ap_extrapolate_guess(int n, const double* d_base, const double* d_mu1, const double* d_base1,
                          const double* d_mu2, const double* d_base2, double* d_out, void* stream);
 
+/* Adaptive trajectory guess: a least-squares predictor on the error of a per-step base
+ * guess over the three previous steps (the paper has none):
+ *   e_k = d_mu_k - d_base_k, k = 1, 2, 3 (1 = the previous step; NULL bases are zero),
+ *   c = (e1 - e2).(e2 - e3) / |e2 - e3|^2 clamped to [0, 1] (0 when e2 = e3),
+ *   d_out = d_base + e1 + c (e1 - e2).
+ * c is the coefficient that best predicted the previous step's change of e from the change
+ * before it: about 0 (hold the last error) for uncorrelated, random-walk motion, about 1
+ * (linear extrapolation) for steady motion. All arrays [n][3] double, caller order, device
+ * memory; c is computed and used on the device (no synchronization, deterministic).
+ *   d_scratch  device memory of AP_ADAPTIVE_SCRATCH doubles, zeroed before its first use;
+ *              the call leaves it ready for the next (scratch[0] holds the last c). */
+#define AP_ADAPTIVE_SCRATCH 520
+int ap_adaptive_guess(int n, const double* d_base, const double* d_mu1, const double* d_base1,
+                      const double* d_mu2, const double* d_base2, const double* d_mu3,
+                      const double* d_base3, double* d_out, double* d_scratch, void* stream);
+
 /* Polarization energy without allocation - the paper has no counterpart; it is a
  * convenience for callers that cannot allocate device memory: code whose device memory
  * all belongs to another framework's pool, loops that forbid allocation after set-up,

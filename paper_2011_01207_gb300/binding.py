@@ -26,7 +26,7 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "ap_mlp_features", "ap_learned_guess", "ap_mlp_gradient", "ap_mlp_train_step",
            "ap_batch_create", "ap_batch_capture", "ap_batch_launch", "ap_batch_destroy", "ap_autotune",
            "ap_extrapolate_guess", "induced_dipoles_diis", "set_scaled_pairs", "permanent_field_dp",
-           "induced_dipoles_pcg_dp", "polarization_energy_forces_dp")
+           "induced_dipoles_pcg_dp", "polarization_energy_forces_dp", "ap_adaptive_guess")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5, "pair_forces": 6,
            "pcg_vectors": 7, "real_matvec2": 8}
@@ -74,6 +74,7 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "permanent_field": (I, [P, P, P, P, P, P]),
         "induced_dipoles_pcg": (I, [P, P, D, I, P, ctypes.POINTER(ApSolveInfo)]),
         "induced_dipoles_diis": (I, [P, P, D, I, I, P, ctypes.POINTER(ApSolveInfo)]),
+        "ap_adaptive_guess": (I, [I, P, P, P, P, P, P, P, P, P, P]),
         "set_scaled_pairs": (I, [P, I, P, P]),
         "permanent_field_dp": (I, [P, P, P, P, P, P, P]),
         "induced_dipoles_pcg_dp": (I, [P, P, P, D, I, P, P, ctypes.POINTER(ApSolveInfo)]),
@@ -281,6 +282,24 @@ def ap_extrapolate_guess(out, mu1, mu2, base=None, base1=None, base2=None, strea
                                                      opt(base1, "base1"), _ptr(mu2, torch.float64, (n, 3), "mu2"),
                                                      opt(base2, "base2"), _ptr(out, torch.float64, (n, 3), "out"),
                                                      _stream_ptr(out, stream)), "ap_extrapolate_guess")
+
+
+AP_ADAPTIVE_SCRATCH = 520
+
+
+def ap_adaptive_guess(out, mu1, mu2, mu3, scratch, base=None, base1=None, base2=None, base3=None, stream=None):
+    """out = base + e1 + c (e1 - e2), e_k = mu_k - base_k, c the clamped least-squares
+    coefficient from the three previous steps; scratch: zeroed float64 CUDA tensor of
+    AP_ADAPTIVE_SCRATCH entries (scratch[0] holds c afterwards)."""
+    import torch
+    n = out.shape[0]
+    opt = lambda t, name: None if t is None else _ptr(t, torch.float64, (n, 3), name)
+    return _check(None, load().ap_adaptive_guess(
+        int(n), opt(base, "base"), _ptr(mu1, torch.float64, (n, 3), "mu1"), opt(base1, "base1"),
+        _ptr(mu2, torch.float64, (n, 3), "mu2"), opt(base2, "base2"), _ptr(mu3, torch.float64, (n, 3), "mu3"),
+        opt(base3, "base3"), _ptr(out, torch.float64, (n, 3), "out"),
+        _ptr(scratch, torch.float64, (AP_ADAPTIVE_SCRATCH,), "scratch"), _stream_ptr(out, stream)),
+        "ap_adaptive_guess")
 
 
 def _stream_ptr(t, stream=None):

@@ -1,5 +1,7 @@
-// Trajectory extrapolation of the initial guess (classical predictor beside the learned
-// guess): out = base + 2 (mu1 - base1) - (mu2 - base2), element by element.
+// Trajectory extrapolation of the initial guess (classical predictors beside the learned
+// guess): out = base + 2 (mu1 - base1) - (mu2 - base2), element by element; and the
+// adaptive form out = base + e1 + c (e1 - e2), e_k = mu_k - base_k, with c the
+// least-squares fit of the previous step's change of e from the one before.
 #include "common.cuh"
 
 namespace {
@@ -35,6 +37,72 @@ __global__ void k_hist_push(long m, const double *__restrict__ g, const double *
     if (i == 0) *count = min(*count + 1, 2);
 }
 
+// adaptive extrapolation: c = (e1 - e2).(e2 - e3) / |e2 - e3|^2 (clamped to [0, 1]) from block
+// partials over a grid-stride loop; the last block (ticket counter in the scratch) sums them
+// in a fixed order and stores c in scratch[0]
+constexpr int AD_BLOCKS = 256, AD_THREADS = 256;
+
+__global__ void __launch_bounds__(AD_THREADS) k_adaptive_coef(long m, const double *__restrict__ mu1,
+                                                              const double *__restrict__ b1,
+                                                              const double *__restrict__ mu2,
+                                                              const double *__restrict__ b2,
+                                                              const double *__restrict__ mu3,
+                                                              const double *__restrict__ b3,
+                                                              double *__restrict__ scratch) {
+    __shared__ double sa[AD_THREADS / 32], sb[AD_THREADS / 32];
+    __shared__ bool last;
+    double num = 0.0, den = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long)gridDim.x * blockDim.x) {
+        const double e1 = mu1[i] - (b1 ? b1[i] : 0.0), e2 = mu2[i] - (b2 ? b2[i] : 0.0),
+                     e3 = mu3[i] - (b3 ? b3[i] : 0.0);
+        const double d12 = e1 - e2, d23 = e2 - e3;
+        num += d12 * d23;
+        den += d23 * d23;
+    }
+    for (int off = 16; off; off >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, off);
+        den += __shfl_xor_sync(0xffffffffu, den, off);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sa[w] = num; sb[w] = den; }
+    __syncthreads();
+    double *part = scratch + 2;   // [2][AD_BLOCKS]
+    unsigned int *counter = reinterpret_cast<unsigned int *>(scratch + 1);
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < AD_THREADS / 32; ++q) { a += sa[q]; b += sb[q]; }
+        part[blockIdx.x] = a;
+        part[AD_BLOCKS + blockIdx.x] = b;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(counter, 1u);
+        last = ticket == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) {
+        a += __ldcg(part + k);
+        b += __ldcg(part + AD_BLOCKS + k);
+    }
+    double c = b > 0.0 ? a / b : 0.0;
+    c = isfinite(c) ? fmin(1.0, fmax(0.0, c)) : 0.0;
+    scratch[0] = c;
+    *counter = 0u;
+}
+
+// out = base + e1 + c (e1 - e2)
+__global__ void k_adaptive_apply(long m, const double *__restrict__ base, const double *__restrict__ mu1,
+                                 const double *__restrict__ b1, const double *__restrict__ mu2,
+                                 const double *__restrict__ b2, const double *__restrict__ scratch,
+                                 double *__restrict__ out) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const double c = scratch[0];
+    const double e1 = mu1[i] - (b1 ? b1[i] : 0.0), e2 = mu2[i] - (b2 ? b2[i] : 0.0);
+    out[i] = (base ? base[i] : 0.0) + e1 + c * (e1 - e2);
+}
+
 }  // namespace
 
 int hist_guess_launch(ap_ctx *ctx, const double *g, const double *h, double *out, cudaStream_t s) {
@@ -55,5 +123,17 @@ extern "C" int ap_extrapolate_guess(int n, const double *d_base, const double *d
     const long m = 3L * n;
     k_extrapolate<<<(unsigned)((m + 255) / 256), 256, 0, (cudaStream_t)stream>>>(m, d_base, d_mu1, d_base1, d_mu2,
                                                                                  d_base2, d_out);
+    return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
+extern "C" int ap_adaptive_guess(int n, const double *d_base, const double *d_mu1, const double *d_base1,
+                                 const double *d_mu2, const double *d_base2, const double *d_mu3,
+                                 const double *d_base3, double *d_out, double *d_scratch, void *stream) {
+    if (n < 1 || !d_mu1 || !d_mu2 || !d_mu3 || !d_out || !d_scratch) return AP_ERR_ARG;
+    const long m = 3L * n;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_adaptive_coef<<<AD_BLOCKS, AD_THREADS, 0, st>>>(m, d_mu1, d_base1, d_mu2, d_base2, d_mu3, d_base3, d_scratch);
+    k_adaptive_apply<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, d_base, d_mu1, d_base1, d_mu2, d_base2, d_scratch,
+                                                                  d_out);
     return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }

@@ -56,3 +56,30 @@ def test_extrapolated_guess_saves_iterations():
         mus.append(mu_plain)
     assert np.mean(extrap) < np.mean(plain[2:])
     c.close()
+
+
+def test_adaptive_guess_definition():
+    """ap_adaptive_guess against its definition written out in NumPy, and its limits: steady
+    motion gives c = 1 (linear extrapolation), a reversal clamps c to 0 (hold)."""
+    rng = np.random.default_rng(3)
+    n = 1003
+    a = {k: rng.normal(size=(n, 3)) for k in ("b", "m1", "b1", "m2", "b2", "m3", "b3")}
+    t = {k: torch.tensor(v, device="cuda") for k, v in a.items()}
+    out = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    scratch = torch.zeros(binding.AP_ADAPTIVE_SCRATCH, dtype=torch.float64, device="cuda")
+    binding.ap_adaptive_guess(out, t["m1"], t["m2"], t["m3"], scratch, base=t["b"], base1=t["b1"], base2=t["b2"],
+                              base3=t["b3"])
+    e1, e2, e3 = a["m1"] - a["b1"], a["m2"] - a["b2"], a["m3"] - a["b3"]
+    c = float(np.clip(np.sum((e1 - e2) * (e2 - e3)) / np.sum((e2 - e3) ** 2), 0.0, 1.0))
+    assert abs(scratch[0].item() - c) < 1e-13
+    np.testing.assert_allclose(out.cpu().numpy(), a["b"] + e1 + c * (e1 - e2), rtol=0, atol=1e-12)
+    # steady motion: mu_k = x + (4 - k) v -> c = 1, out = 2 mu1 - mu2
+    x, v = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    m = [torch.tensor(x + (4 - k) * v, device="cuda") for k in (1, 2, 3)]
+    binding.ap_adaptive_guess(out, m[0], m[1], m[2], scratch)
+    assert abs(scratch[0].item() - 1.0) < 1e-12
+    np.testing.assert_allclose(out.cpu().numpy(), x + 4 * v, rtol=0, atol=1e-12)
+    # reversal: mu3 = mu1 -> (e1 - e2) = -(e2 - e3), c = -1 clamped to 0: hold mu1
+    binding.ap_adaptive_guess(out, m[0], m[1], m[0], scratch)
+    assert scratch[0].item() == 0.0
+    assert np.array_equal(out.cpu().numpy(), m[0].cpu().numpy())
