@@ -272,6 +272,14 @@ typedef struct {
                                     the learned guess alone until two launches exist). Holds the
                                     last two dipoles, the last two learned guesses and the guess;
                                     ap_batch_capture() starts a new trajectory. */
+    double*       d_hist_lsq;    /* 7 * n * 3 + AP_ADAPTIVE_SCRATCH doubles, zeroed, or NULL: with
+                                    the learned guess, each launch starts from the learned guess
+                                    plus the adaptive extrapolation of its error over the three
+                                    previous launches (ap_adaptive_guess with base = learned
+                                    guess; the learned guess alone at the first launch, its
+                                    previous error held at the second and third). Holds the last
+                                    three dipoles, the last three learned guesses, the guess and
+                                    the reduction scratch; takes precedence over d_hist. */
 } ap_batch_step;
 int ap_batch_create(ap_batch** out, ap_ctx* const* ctxs, int n_ctx);
 int ap_batch_capture(ap_batch* b, const ap_batch_step* steps);

@@ -47,7 +47,8 @@ class ApBatchStep(ctypes.Structure):
     _fields_ = [("d_xyz", ctypes.c_void_p), ("d_mpole", ctypes.c_void_p), ("d_frame", ctypes.c_void_p),
                 ("d_alpha", ctypes.c_void_p), ("d_mlp_packed", ctypes.c_void_p), ("d_mu0", ctypes.c_void_p),
                 ("tol_debye", ctypes.c_double), ("max_iter", ctypes.c_int), ("d_mu", ctypes.c_void_p),
-                ("d_energy", ctypes.c_void_p), ("d_forces", ctypes.c_void_p), ("d_hist", ctypes.c_void_p)]
+                ("d_energy", ctypes.c_void_p), ("d_forces", ctypes.c_void_p), ("d_hist", ctypes.c_void_p),
+                ("d_hist_lsq", ctypes.c_void_p)]
 
 
 class ApError(RuntimeError):
@@ -401,7 +402,11 @@ class Batch:
                 mu0 = c.torch.zeros((c.n, 3), dtype=c.torch.float64, device=c.device)
                 self._keep.append(mu0)
                 st.d_mlp_packed, st.d_mu0 = packed.data_ptr(), mu0.data_ptr()
-                if history:
+                if history == "adaptive":
+                    hist = c.torch.zeros(7 * c.n * 3 + AP_ADAPTIVE_SCRATCH, dtype=c.torch.float64, device=c.device)
+                    self._keep.append(hist)
+                    st.d_hist_lsq = hist.data_ptr()
+                elif history:
                     hist = c.torch.zeros((5, c.n, 3), dtype=c.torch.float64, device=c.device)
                     self._keep.append(hist)
                     st.d_hist = hist.data_ptr()

@@ -14,6 +14,8 @@
 int ap_learned_guess(ap_ctx *ctx, const void *d_packed, double *d_mu0);
 int hist_guess_launch(ap_ctx *ctx, const double *g, const double *h, double *out, cudaStream_t s);
 int hist_push_launch(ap_ctx *ctx, const double *g, const double *mu, double *h, cudaStream_t s);
+int hist_adaptive_launch(ap_ctx *ctx, const double *g, double *h, double *out, cudaStream_t s);
+int hist_push3_launch(ap_ctx *ctx, const double *g, const double *mu, double *h, cudaStream_t s);
 int pme_stage_launch(ap_ctx *ctx, int stage, cudaStream_t s);
 int dipole_operator_into(ap_ctx *ctx, cudaStream_t main, cudaStream_t aux);
 
@@ -31,20 +33,28 @@ int capture_one(ap_ctx *c, const ap_batch_step &st) {
     int r = permanent_field(c, st.d_xyz, st.d_mpole, st.d_frame, st.d_alpha, nullptr);
     if (r) return r;
     const double *guess = nullptr;
-    if (st.d_hist && !st.d_mlp_packed) return ap_fail(c, AP_ERR_ARG, "the trajectory guess needs the learned guess");
+    if ((st.d_hist || st.d_hist_lsq) && !st.d_mlp_packed)
+        return ap_fail(c, AP_ERR_ARG, "the trajectory guess needs the learned guess");
     if (st.d_mlp_packed) {
         if (!st.d_mu0) return ap_fail(c, AP_ERR_ARG, "learned guess needs d_mu0 scratch");
         if ((r = ap_learned_guess(c, st.d_mlp_packed, st.d_mu0))) return r;
         guess = st.d_mu0;
     }
     double *hist_out = st.d_hist ? st.d_hist + 12L * c->n : nullptr;   // slot 5 of [5][n][3]
-    if (st.d_hist) {
+    if (st.d_hist_lsq) {
+        double *out = st.d_hist_lsq + 18L * c->n;                        // the guess, after six vectors
+        if ((r = hist_adaptive_launch(c, st.d_mu0, st.d_hist_lsq, out, c->s0))) return ap_fail(c, r, "history guess");
+        guess = out;
+    } else if (st.d_hist) {
         if ((r = hist_guess_launch(c, st.d_mu0, st.d_hist, hist_out, c->s0))) return ap_fail(c, r, "history guess");
         guess = hist_out;
     }
     if ((r = induced_dipoles_pcg(c, guess, st.tol_debye, st.max_iter, st.d_mu, nullptr)) < 0) return r;
-    if (st.d_hist)
+    if (st.d_hist_lsq) {
+        if ((r = hist_push3_launch(c, st.d_mu0, st.d_mu, st.d_hist_lsq, c->s0))) return ap_fail(c, r, "history push");
+    } else if (st.d_hist) {
         if ((r = hist_push_launch(c, st.d_mu0, st.d_mu, st.d_hist, c->s0))) return ap_fail(c, r, "history push");
+    }
     if (st.d_energy && st.d_forces)
         if ((r = polarization_energy_forces(c, st.d_mu, st.d_energy, st.d_forces))) return r;
     return AP_OK;

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(AD_THREADS) k_adaptive_coef(long m, const doub
                                                               const double *__restrict__ b2,
                                                               const double *__restrict__ mu3,
                                                               const double *__restrict__ b3,
-                                                              double *__restrict__ scratch) {
+                                                              double *__restrict__ scratch,
+                                                              const int *__restrict__ count) {
     __shared__ double sa[AD_THREADS / 32], sb[AD_THREADS / 32];
     __shared__ bool last;
     double num = 0.0, den = 0.0;
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(AD_THREADS) k_adaptive_coef(long m, const doub
     }
     double c = b > 0.0 ? a / b : 0.0;
     c = isfinite(c) ? fmin(1.0, fmax(0.0, c)) : 0.0;
+    if (count && *count < 3) c = 0.0;   // history too short: hold the last error
     scratch[0] = c;
     *counter = 0u;
 }
@@ -95,15 +97,51 @@ __global__ void __launch_bounds__(AD_THREADS) k_adaptive_coef(long m, const doub
 __global__ void k_adaptive_apply(long m, const double *__restrict__ base, const double *__restrict__ mu1,
                                  const double *__restrict__ b1, const double *__restrict__ mu2,
                                  const double *__restrict__ b2, const double *__restrict__ scratch,
-                                 double *__restrict__ out) {
+                                 double *__restrict__ out, const int *__restrict__ count) {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
+    if (count && *count == 0) {   // no history yet: the base guess alone
+        out[i] = base ? base[i] : 0.0;
+        return;
+    }
     const double c = scratch[0];
     const double e1 = mu1[i] - (b1 ? b1[i] : 0.0), e2 = mu2[i] - (b2 ? b2[i] : 0.0);
     out[i] = (base ? base[i] : 0.0) + e1 + c * (e1 - e2);
 }
 
+// three-level history h = [mu1, mu2, mu3, g1, g2, g3] (m entries each): shift by one step
+__global__ void k_hist_push3(long m, const double *__restrict__ g, const double *__restrict__ mu,
+                             double *__restrict__ h, int *__restrict__ count) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) {
+        h[2 * m + i] = h[m + i];
+        h[m + i] = h[i];
+        h[i] = mu[i];
+        h[5 * m + i] = h[4 * m + i];
+        h[4 * m + i] = h[3 * m + i];
+        h[3 * m + i] = g[i];
+    }
+    if (i == 0) *count = min(*count + 1, 3);
+}
+
 }  // namespace
+
+// adaptive guess from the three-level history (layout of ap_batch_step.d_hist_lsq)
+int hist_adaptive_launch(ap_ctx *ctx, const double *g, double *h, double *out, cudaStream_t s) {
+    const long m = 3L * ctx->n;
+    double *scratch = h + 7 * m;
+    k_adaptive_coef<<<AD_BLOCKS, AD_THREADS, 0, s>>>(m, h, h + 3 * m, h + m, h + 4 * m, h + 2 * m, h + 5 * m, scratch,
+                                                     ctx->hist_count);
+    k_adaptive_apply<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, g, h, h + 3 * m, h + m, h + 4 * m, scratch, out,
+                                                                 ctx->hist_count);
+    return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
+int hist_push3_launch(ap_ctx *ctx, const double *g, const double *mu, double *h, cudaStream_t s) {
+    const long m = 3L * ctx->n;
+    k_hist_push3<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, g, mu, h, ctx->hist_count);
+    return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
 
 int hist_guess_launch(ap_ctx *ctx, const double *g, const double *h, double *out, cudaStream_t s) {
     const long m = 3L * ctx->n;
@@ -132,8 +170,9 @@ extern "C" int ap_adaptive_guess(int n, const double *d_base, const double *d_mu
     if (n < 1 || !d_mu1 || !d_mu2 || !d_mu3 || !d_out || !d_scratch) return AP_ERR_ARG;
     const long m = 3L * n;
     cudaStream_t st = (cudaStream_t)stream;
-    k_adaptive_coef<<<AD_BLOCKS, AD_THREADS, 0, st>>>(m, d_mu1, d_base1, d_mu2, d_base2, d_mu3, d_base3, d_scratch);
+    k_adaptive_coef<<<AD_BLOCKS, AD_THREADS, 0, st>>>(m, d_mu1, d_base1, d_mu2, d_base2, d_mu3, d_base3, d_scratch,
+                                                      nullptr);
     k_adaptive_apply<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, d_base, d_mu1, d_base1, d_mu2, d_base2, d_scratch,
-                                                                  d_out);
+                                                                  d_out, nullptr);
     return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }

@@ -120,3 +120,52 @@ def test_batch_history_guess():
     b.close()
     for _, c in reps:
         c.close()
+
+
+def test_batch_adaptive_history_guess():
+    """With d_hist_lsq, launch 0 starts from the learned guess, launches 1-2 hold its
+    previous error, later launches extrapolate it with the least-squares coefficient of the
+    three previous launches (ap_adaptive_guess's definition); every launch still converges
+    to the standalone solution."""
+    from paper_2011_01207_gb300 import learned
+    reps = _replicas()
+    tr = learned.Trainer(seed=3)
+    for s, c in reps:
+        with torch.cuda.stream(c.stream):
+            c.permanent_field(out=False)
+    torch.cuda.synchronize()
+    b = binding.Batch([c for _, c in reps])
+    b.capture(tol=1e-6, max_iter=200, packed=tr.packed, history="adaptive")
+    g_buf = [t for t in b._keep if t.dim() == 2]     # learned guesses, one per replica
+    h_buf = [t for t in b._keep if t.dim() == 1]     # flat histories
+    main = torch.cuda.Stream()
+    cur = [s for s, _ in reps]
+    past = [[] for _ in reps]
+    for step in range(5):
+        for k, (s, c) in enumerate(reps):
+            cur[k] = synth.perturb(cur[k], 90 + 10 * step + k)
+            c.set_positions(cur[k].xyz)
+        torch.cuda.synchronize()
+        b.launch(main)
+        torch.cuda.synchronize()
+        for k, (s, c) in enumerate(reps):
+            n3 = 3 * c.n
+            g, used, mu = g_buf[k].clone(), h_buf[k][6 * n3:7 * n3].view(c.n, 3).clone(), c.mu.clone()
+            if step == 0:
+                assert torch.equal(used, g)
+            elif step < 3:
+                m1, g1 = past[k][-1]
+                assert (used - (g + (m1 - g1))).abs().max().item() < 1e-12
+            else:
+                (m1, g1), (m2, g2), (m3, g3) = past[k][-1], past[k][-2], past[k][-3]
+                e1, e2, e3 = m1 - g1, m2 - g2, m3 - g3
+                cc = float(((e1 - e2) * (e2 - e3)).sum() / ((e2 - e3) ** 2).sum())
+                cc = min(1.0, max(0.0, cc))
+                want = g + e1 + cc * (e1 - e2)
+                assert (used - want).abs().max().item() < 1e-9
+            past[k].append((mu, g))
+            ref = _standalone(c)
+            assert 4.80321 * (mu - ref[1]).abs().max().item() < 1e-4
+    b.close()
+    for _, c in reps:
+        c.close()
