@@ -12,9 +12,10 @@ benchmark may import it. The CUDA library never calls it, and it shares no code 
 the library: both take the same arrays from the seeded input generators.
 
 Modules: radial (screened and damped radial functions), frames (local frames and their
-derivatives), pairs (pair enumeration), realspace (pair sums), ewald (exact reciprocal
-k-sum), spme (smooth PME), model (field, operator, PCG, energy, forces), mlp (the
-learned-guess network in FP64).
+derivatives), pairs (pair enumeration and scale tables), realspace (pair sums, single and
+two-dipole-set forces), ewald (exact reciprocal k-sum), spme (smooth PME), model (field,
+operator, PCG, Jacobi/DIIS, energy, forces, and AMOEBA's two dipole sets: d/p fields,
+lockstep PCG, energy and forces), mlp (the learned-guess network in FP64).
 """
 from . import radial, frames, pairs, realspace, ewald, spme, model, mlp  # noqa: F401
 from .model import Params, Oracle  # noqa: F401
