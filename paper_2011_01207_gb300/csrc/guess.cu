@@ -41,6 +41,7 @@ __global__ void k_hist_push(long m, const double *__restrict__ g, const double *
 // partials over a grid-stride loop; the last block (ticket counter in the scratch) sums them
 // in a fixed order and stores c in scratch[0]
 constexpr int AD_BLOCKS = 256, AD_THREADS = 256;
+static_assert(AD_BLOCKS <= AD_THREADS, "the last block loads one partial per thread");
 
 __global__ void __launch_bounds__(AD_THREADS) k_adaptive_coef(long m, const double *__restrict__ mu1,
                                                               const double *__restrict__ b1,
@@ -79,13 +80,21 @@ __global__ void __launch_bounds__(AD_THREADS) k_adaptive_coef(long m, const doub
         last = ticket == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
+    // last block: thread k loads partial k (gridDim.x <= AD_THREADS), then the same fixed
+    // warp-and-block tree as above, so the result does not depend on block order
     __threadfence();
-    double a = 0.0, b = 0.0;
-    for (int k = 0; k < (int)gridDim.x; ++k) {
-        a += __ldcg(part + k);
-        b += __ldcg(part + AD_BLOCKS + k);
+    num = threadIdx.x < gridDim.x ? __ldcg(part + threadIdx.x) : 0.0;
+    den = threadIdx.x < gridDim.x ? __ldcg(part + AD_BLOCKS + threadIdx.x) : 0.0;
+    for (int off = 16; off; off >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, off);
+        den += __shfl_xor_sync(0xffffffffu, den, off);
     }
+    if (l == 0) { sa[w] = num; sb[w] = den; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < AD_THREADS / 32; ++q) { a += sa[q]; b += sb[q]; }
     double c = b > 0.0 ? a / b : 0.0;
     c = isfinite(c) ? fmin(1.0, fmax(0.0, c)) : 0.0;
     if (count && *count < 3) c = 0.0;   // history too short: hold the last error
