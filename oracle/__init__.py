@@ -14,8 +14,8 @@ the library: both take the same arrays from the seeded input generators.
 Modules: radial (screened and damped radial functions), frames (local frames and their
 derivatives), pairs (pair enumeration and scale tables), realspace (pair sums, single and
 two-dipole-set forces), ewald (exact reciprocal k-sum), spme (smooth PME), model (field,
-operator, PCG, Jacobi/DIIS, energy, forces, and AMOEBA's two dipole sets: d/p fields,
-lockstep PCG, energy and forces), mlp (the learned-guess network in FP64).
+operator, PCG, Jacobi/DIIS, energy, forces, virial, and AMOEBA's two dipole sets: d/p
+fields, lockstep PCG, energy, forces and virial), mlp (the learned-guess network in FP64).
 """
 from . import radial, frames, pairs, realspace, ewald, spme, model, mlp  # noqa: F401
 from .model import Params, Oracle  # noqa: F401

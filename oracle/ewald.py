@@ -50,3 +50,32 @@ def recip_derivs(xyz, box, beta, q, dip, quad, order, chunk=1500):
         if order >= 3:
             out[3] += np.real(np.einsum("ma,mb,mc,mn->nabc", 1j * tp * mt, 1j * tp * mt, 1j * tp * mt, Z))
     return out
+
+
+def strain_sum(xyz, box, beta, src_a, src_b, chunk=1500):
+    """sum_{m != 0} C(m) Re[S_a(m) conj S_b(m)] K(m) [3,3] for two source sets
+    src = (q [N], dip [N,3], quad [N,3,3]), with
+        K(m)_ab = -delta_ab + 2 (1/|m|^2 + pi^2/beta^2) m_a m_b,
+    the logarithmic derivative of C(m) under the homogeneous deformation x -> (I + e) x
+    (V -> V det(I + e), m -> (I + e)^-T m; the phases m.x_j do not change). It is the
+    structure-factor share of the strain derivative of sum_m C Re[S_a conj S_b]."""
+    xyz = np.asarray(xyz, np.float64)
+    box = np.asarray(box, np.float64)
+    vol = float(np.prod(box))
+    ms = kvectors(box, beta)
+    tp = 2.0 * np.pi
+    out = np.zeros((3, 3))
+    for s in range(0, len(ms), chunk):
+        mt = ms[s:s + chunk] / box
+        m2 = np.einsum("ma,ma->m", mt, mt)
+        C = np.exp(-np.pi ** 2 * m2 / beta ** 2) / (np.pi * vol * m2)
+        ph = np.exp(-1j * tp * (mt @ xyz.T))                     # [M, N]
+        S = []
+        for q, dip, quad in (src_a, src_b):
+            fac = (q[None, :] - 1j * tp * (mt @ dip.T)
+                   - (4.0 * np.pi ** 2 / 3.0) * np.einsum("ma,nab,mb->mn", mt, quad, mt))
+            S.append(np.sum(fac * ph, axis=1))
+        w = C * np.real(S[0] * np.conj(S[1]))
+        out += -np.sum(w) * np.eye(3)
+        out += 2.0 * np.einsum("m,ma,mb->ab", w * (1.0 / m2 + np.pi ** 2 / beta ** 2), mt, mt)
+    return out

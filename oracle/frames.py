@@ -66,16 +66,15 @@ def rotate_multipoles(xyz, box, frame, dip_local, quad_local):
     return dip, quad, rot
 
 
-def frame_gradient(xyz, box, frame, dip_local, quad_local, g_dip, g_quad):
-    """dU/dx [N,3] from dU/d(global dipole) [N,3] and dU/d(global quadrupole) [N,3,3]
-    (symmetric), by the chain rule through the frame construction."""
-    n = xyz.shape[0]
+def _frame_vector_gradients(xyz, box, frame, dip_local, quad_local, g_dip, g_quad):
+    """dU/dv_z and dU/dv_x of every framed atom from dU/d(global dipole) [N,3] and
+    dU/d(global quadrupole) [N,3,3] (symmetric), by the chain rule through the frame
+    construction. Yields (atoms, z atoms, x atoms, dU/dv_z, dU/dv_x, v_z, v_x) per kind."""
     rot = frame_matrices(xyz, box, frame)
     ql = quad6_to_mat(quad_local)
     g_quad = 0.5 * (g_quad + np.swapaxes(g_quad, 1, 2))
     # dU/dR = G_d d_l^T + 2 G_Q R Q_l
     g_rot = np.einsum("na,nb->nab", g_dip, dip_local) + 2.0 * np.einsum("nab,nbc,ncd->nad", g_quad, rot, ql)
-    out = np.zeros((n, 3))
     ftype, fz, fx = frame[:, 0], frame[:, 1], frame[:, 2]
 
     def dot(a, b):
@@ -112,7 +111,28 @@ def frame_gradient(xyz, box, frame, dip_local, quad_local, g_dip, g_quad):
             g_u2 = g_u2 + g_s
             g_vz = (g_u1 - dot(g_u1, u1) * u1) / n1
             g_vx = (g_u2 - dot(g_u2, u2) * u2) / n2
-        np.add.at(out, fz[idx], g_vz)
-        np.add.at(out, fx[idx], g_vx)
+        yield idx, fz[idx], fx[idx], g_vz, g_vx, vz, vx
+
+
+def frame_gradient(xyz, box, frame, dip_local, quad_local, g_dip, g_quad):
+    """dU/dx [N,3] from dU/d(global dipole) [N,3] and dU/d(global quadrupole) [N,3,3]
+    (symmetric), by the chain rule through the frame construction: v_z = x_Z - x_i and
+    v_x = x_X - x_i, so x_Z and x_X receive dU/dv and atom i minus their sum."""
+    out = np.zeros((xyz.shape[0], 3))
+    for idx, iz, ix, g_vz, g_vx, _, _ in _frame_vector_gradients(xyz, box, frame, dip_local, quad_local,
+                                                                   g_dip, g_quad):
+        np.add.at(out, iz, g_vz)
+        np.add.at(out, ix, g_vx)
         np.add.at(out, idx, -(g_vz + g_vx))
     return out
+
+
+def frame_virial(xyz, box, frame, dip_local, quad_local, g_dip, g_quad):
+    """The frames' share of dU/d(strain) [3,3]: a homogeneous deformation x -> (I + e) x
+    maps each frame vector v to (I + e) v, so it contributes sum (dU/dv)_a v_b over the
+    frame vectors of every atom (U's dependence on the global multipoles only)."""
+    V = np.zeros((3, 3))
+    for _, _, _, g_vz, g_vx, vz, vx in _frame_vector_gradients(xyz, box, frame, dip_local, quad_local,
+                                                                 g_dip, g_quad):
+        V += np.einsum("na,nb->ab", g_vz, vz) + np.einsum("na,nb->ab", g_vx, vx)
+    return V

@@ -14,6 +14,9 @@ Readings where the paper is silent:
   * PCG: M^-1 = diag(alpha); convergence measure eps = 4.80321 sqrt(sum_i |alpha_i r_i|^2 / N)
     (Debye RMS of the preconditioned residual); stop when eps <= tol;
   * E_pol = -(f/2) sum_i mu_i . E_i ; forces are -dE_pol/dx at fixed mu (variational);
+  * virial V_ab = dE_pol/de_ab under x -> (I + e) x of positions and box (local-frame
+    multipoles carried by the deformed frames, mu re-solved), in kcal/mol; the sign is
+    that of the strain derivative, so the pressure tensor's share is -V / volume;
   * two dipole sets (AMOEBA's d and p, the three scale factors of Sec. 2.3): E_d and E_p
     use the direct and the polarization scale factors of the listed pairs, T uses scale 1;
     mu_d = A^-1 E_d, mu_p = A^-1 E_p; E_pol = -(f/2) sum_i mu_d,i . E_p,i.
@@ -306,6 +309,77 @@ class Oracle:
         grad += frames.frame_gradient(self.xyz, self.box, self.s.frame, self.s.dip, self.s.quad,
                                       g_dip, g_quad)
         return -grad
+
+    # ---- virial ----------------------------------------------------------------------
+    def recip_strain(self, src_a, src_b):
+        """Structure-factor share of the strain derivative of the bilinear reciprocal energy
+        of two source sets (ewald.strain_sum / spme.strain_sum)."""
+        p = self.p
+        if p.mode == "exact":
+            return ewald.strain_sum(self.xyz, self.box, p.beta, src_a, src_b)
+        return spme.strain_sum(self.xyz, self.box, p.beta, p.grid, p.order, src_a, src_b)
+
+    def virial(self, mu):
+        """V_ab = dE_pol/de_ab [3,3] (kcal/mol) under the homogeneous deformation
+        x -> (I + e) x of positions and box, with the local-frame multipoles carried by the
+        deformed frames and mu re-solved; because E_pol is stationary in mu this is the
+        derivative of U = -f mu.E - (f/2) mu.T mu at fixed mu (global components):
+          real space: sum over ordered pairs of (dU/dR)_a R_b;
+          frames:     sum over frame vectors of (dU/dv)_a v_b;
+          reciprocal: U_rec = f [B(mu, M) + B(mu, mu)/2], B(X, Y) = sum_m C Re[S_X conj S_Y];
+                      the change of C (volume, |m|) gives the structure-factor sums, and the
+                      change of m in the dipole and quadrupole factors of S gives
+                      -f sum_j [dphi_{M+mu}/dx_a mu_j,b + dphi_mu/dx_a d_j,b
+                                + (2/3) (H(phi_mu) Q_j)_ab];
+          self terms: no dependence at fixed global components.
+        The pressure tensor's polarization share is -V / volume."""
+        f = F_COUL
+        mu = np.asarray(mu, np.float64).reshape(self.n, 3)
+        _, g_dip, g_quad, V = realspace.real_forces(
+            self.n, self.I, self.J, self.R, self.sigma, self.q, self.dip, self.quad, self.alpha,
+            mu, self.beta, self.p.thole_a, f, virial=True)
+        if self.p.mode != "open":
+            zq, zQ = np.zeros(self.n), np.zeros((self.n, 3, 3))
+            M, U = (self.q, self.dip, self.quad), (zq, mu, zQ)
+            phM = self.recip(*M, 1)
+            phU = self.recip(*U, 2)
+            g_dip += f * phU[1]
+            g_quad += (f / 3.0) * phU[2]
+            g_dip += -f * self.p.self_coef * mu
+            V += f * (self.recip_strain(U, M) + 0.5 * self.recip_strain(U, U))
+            V -= f * (np.einsum("ja,jb->ab", phM[1] + phU[1], mu) + np.einsum("ja,jb->ab", phU[1], self.dip)
+                      + (2.0 / 3.0) * np.einsum("jac,jcb->ab", phU[2], self.quad))
+        V += frames.frame_virial(self.xyz, self.box, self.s.frame, self.s.dip, self.s.quad, g_dip, g_quad)
+        return V
+
+    def virial_dp(self, mu_d, mu_p):
+        """dE_pol/de [3,3] of E_pol = -(f/2) mu_d . E_p with both dipole sets converged,
+        term by term as in `virial`: real space from real_forces_dp, reciprocal from
+        U_rec = f [B(mu_s, M) + B(mu_p, mu_d)/2] with mu_s = (mu_d + mu_p)/2, frames from
+        the same multipole derivatives as forces_dp."""
+        f = F_COUL
+        mu_d = np.asarray(mu_d, np.float64).reshape(self.n, 3)
+        mu_p = np.asarray(mu_p, np.float64).reshape(self.n, 3)
+        _, g_dip, g_quad, V = realspace.real_forces_dp(
+            self.n, self.I, self.J, self.R, self.sigma_d, self.sigma_p, self.q, self.dip, self.quad,
+            self.alpha, mu_d, mu_p, self.beta, self.p.thole_a, f, virial=True)
+        if self.p.mode != "open":
+            zq, zQ = np.zeros(self.n), np.zeros((self.n, 3, 3))
+            mu_s = 0.5 * (mu_d + mu_p)
+            M, S, D, P = (self.q, self.dip, self.quad), (zq, mu_s, zQ), (zq, mu_d, zQ), (zq, mu_p, zQ)
+            phM = self.recip(*M, 1)
+            phS = self.recip(*S, 2)
+            phD = self.recip(*D, 1)
+            phP = self.recip(*P, 1)
+            g_dip += f * phS[1]
+            g_quad += (f / 3.0) * phS[2]
+            g_dip += -f * self.p.self_coef * mu_s
+            V += f * (self.recip_strain(S, M) + 0.5 * self.recip_strain(P, D))
+            V -= f * (np.einsum("ja,jb->ab", phM[1], mu_s) + np.einsum("ja,jb->ab", phS[1], self.dip)
+                      + (2.0 / 3.0) * np.einsum("jac,jcb->ab", phS[2], self.quad))
+            V -= 0.5 * f * (np.einsum("ja,jb->ab", phD[1], mu_p) + np.einsum("ja,jb->ab", phP[1], mu_d))
+        V += frames.frame_virial(self.xyz, self.box, self.s.frame, self.s.dip, self.s.quad, g_dip, g_quad)
+        return V
 
     def charge_potential(self):
         """Electrostatic potential at each site from all charges (Madelung checks)."""

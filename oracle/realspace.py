@@ -70,18 +70,22 @@ def real_dipole_field(n, I, J, R, p, alpha, beta, thole_a):
     return E
 
 
-def real_forces(n, I, J, R, sigma, q, dip, quad, alpha, mu, beta, thole_a, fconst):
+def real_forces(n, I, J, R, sigma, q, dip, quad, alpha, mu, beta, thole_a, fconst, virial=False):
     """Real-space part of the polarization gradient at fixed induced dipoles mu.
 
     Each ordered pair (I, J) carries
         U_IJ = -f mu_I . E(R; multipole J) - (f/2) mu_I . T(R) mu_J,
     whose sum over ordered pairs is the position-dependent real-space energy.
     Returns (dU/dx [n,3] from the pair distances, dU/d(global dipole) [n,3],
-    dU/d(global quadrupole) [n,3,3]) - the last two feed the frame chain rule.
+    dU/d(global quadrupole) [n,3,3]) - the last two feed the frame chain rule - and, with
+    virial=True, the pairs' share of dU/d(strain) [3,3]: a homogeneous deformation
+    x -> (I + e) x maps every pair vector R (images included) to (I + e) R, so it is
+    sum over ordered pairs of (dU_IJ/dR)_a R_b at fixed global multipoles.
     """
     grad = np.zeros((n, 3))
     g_dip = np.zeros((n, 3))
     g_quad = np.zeros((n, 3, 3))
+    V = np.zeros((3, 3))
     for s in _chunks(len(I)):
         Rs = R[s]
         r = np.linalg.norm(Rs, axis=1)
@@ -101,6 +105,7 @@ def real_forces(n, I, J, R, sigma, q, dip, quad, alpha, mu, beta, thole_a, fcons
         gR += -0.5 * fconst * dT
         np.add.at(grad, Ii, gR)
         np.add.at(grad, Jj, -gR)
+        V += np.einsum("pa,pb->ab", gR, Rs)
         # dependence on the source multipole J (global components)
         np.add.at(g_dip, Jj, -fconst * (-Rd[0][:, None] * mi + (Rd[1] * mir)[:, None] * Rs))
         sym = np.einsum("pa,pb->pab", mi, Rs)
@@ -108,10 +113,11 @@ def real_forces(n, I, J, R, sigma, q, dip, quad, alpha, mu, beta, thole_a, fcons
         gq = -fconst * (-(Rd[1] / 3.0)[:, None, None] * sym
                         + (Rd[2] * mir / 3.0)[:, None, None] * np.einsum("pa,pb->pab", Rs, Rs))
         np.add.at(g_quad, Jj, gq)
-    return grad, g_dip, g_quad
+    return (grad, g_dip, g_quad, V) if virial else (grad, g_dip, g_quad)
 
 
-def real_forces_dp(n, I, J, R, sigma_d, sigma_p, q, dip, quad, alpha, mu_d, mu_p, beta, thole_a, fconst):
+def real_forces_dp(n, I, J, R, sigma_d, sigma_p, q, dip, quad, alpha, mu_d, mu_p, beta, thole_a, fconst,
+                   virial=False):
     """Real-space part of the polarization gradient with AMOEBA's two induced-dipole sets:
     mu_d induced by the direct field (pair scale sigma_d), mu_p by the polarization field
     (sigma_p), mutual scale 1. Each ordered pair (I, J) carries
@@ -120,10 +126,12 @@ def real_forces_dp(n, I, J, R, sigma_d, sigma_p, q, dip, quad, alpha, mu_d, mu_p
     whose sum over ordered pairs is the position-dependent real-space part of
     -(f/2) mu_d . E_p at fixed dipoles, with the response of mu_d folded in through mu_p
     (A symmetric). With sigma_d = sigma_p and mu_d = mu_p it is real_forces' U_IJ.
-    Returns (dU/dx, dU/d(global dipole), dU/d(global quadrupole))."""
+    Returns (dU/dx, dU/d(global dipole), dU/d(global quadrupole)) and, with virial=True,
+    the pairs' share of dU/d(strain) as in real_forces."""
     grad = np.zeros((n, 3))
     g_dip = np.zeros((n, 3))
     g_quad = np.zeros((n, 3, 3))
+    V = np.zeros((3, 3))
     h = 0.5 * fconst
     for s in _chunks(len(I)):
         Rs = R[s]
@@ -146,6 +154,7 @@ def real_forces_dp(n, I, J, R, sigma_d, sigma_p, q, dip, quad, alpha, mu_d, mu_p
         gR += -h * dT
         np.add.at(grad, Ii, gR)
         np.add.at(grad, Jj, -gR)
+        V += np.einsum("pa,pb->ab", gR, Rs)
         # dependence on the source multipole J: d(mu . E)/d d_J = -R1 mu + R2 (mu.R) R,
         # d(mu . E)/d Q_J = -(R2/3) sym(mu R^T) + (R3/3)(mu.R) R R^T
         dIr = np.einsum("pa,pa->p", dI, Rs)
@@ -160,4 +169,4 @@ def real_forces_dp(n, I, J, R, sigma_d, sigma_p, q, dip, quad, alpha, mu_d, mu_p
         gq = (-(Rd[1] / 3.0)[:, None, None] * symp + (Rd[2] * pr / 3.0)[:, None, None] * RR
               - (Rp[1] / 3.0)[:, None, None] * symd + (Rp[2] * dIr / 3.0)[:, None, None] * RR)
         np.add.at(g_quad, Jj, -h * gq)
-    return grad, g_dip, g_quad
+    return (grad, g_dip, g_quad, V) if virial else (grad, g_dip, g_quad)

@@ -150,3 +150,23 @@ def recip_derivs(xyz, box, beta, K, order, q, dip, quad, max_order):
     grid = spread(xyz, box, K, order, q, dip, quad)
     phi = convolve(grid, box, K, order, beta)
     return gather(phi, xyz, box, K, order, max_order)
+
+
+def strain_sum(xyz, box, beta, K, order, src_a, src_b):
+    """sum_m B(m) C(m) Re[F_a(m) conj F_b(m)] K(m) [3,3], F = DFT of the spread grid of
+    each source set src = (q, dip, quad), K(m)_ab = -delta_ab + 2 (1/|m|^2 + pi^2/beta^2)
+    m_a m_b: the smooth-PME counterpart of `ewald.strain_sum`. The B-spline moduli B(m)
+    depend on the integer index only and the grid follows the fractional coordinates, so
+    a homogeneous deformation changes only the volume and the Cartesian m."""
+    K = np.asarray(K)
+    box = np.asarray(box, np.float64)
+    Fa = np.fft.fftn(spread(xyz, box, K, order, *src_a))
+    Fb = np.fft.fftn(spread(xyz, box, K, order, *src_b))
+    w = influence(box, K, order, beta) * np.real(Fa * np.conj(Fb))
+    ms = [np.where(np.arange(k) < (k + 1) // 2, np.arange(k), np.arange(k) - k) / L for k, L in zip(K, box)]
+    m = np.stack(np.meshgrid(*ms, indexing="ij"), -1)
+    m2 = np.einsum("xyza,xyza->xyz", m, m)
+    m2[0, 0, 0] = 1.0                                    # w is zero there
+    out = -np.sum(w) * np.eye(3)
+    out += 2.0 * np.einsum("xyz,xyza,xyzb->ab", w * (1.0 / m2 + np.pi ** 2 / beta ** 2), m, m)
+    return out
