@@ -156,7 +156,8 @@ class Clocks:
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
-        self.path = tempfile.mktemp(suffix=".csv")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
         self.proc = None
         self.index = index
 

@@ -14,7 +14,6 @@ multipole order fails one of these."""
 import numpy as np
 
 from oracle import Oracle, Params, radial, spme
-from paper_2011_01207_gb300 import synth
 
 
 def _damped_multipole_field(R, q, d, Q, ai, aj, a=0.39):
