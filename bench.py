@@ -172,6 +172,8 @@ class Clocks:
 
     def stop(self):
         if self.proc is None:
+            if os.path.exists(self.path):
+                os.unlink(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:

@@ -111,3 +111,11 @@ def test_trajectory_is_seeded():
     a, b = bench.trajectory(s, 4), bench.trajectory(s, 4)
     assert a.shape == (4, s.n, 3) and np.array_equal(a, b)
     assert np.array_equal(a[0], s.xyz) and not np.array_equal(a[1], a[0])
+
+
+def test_clock_sampler_without_nvidia_smi_leaves_no_file():
+    c = bench.Clocks(0)
+    c.proc = None
+    assert os.path.exists(c.path)
+    got = c.stop()
+    assert got["sm_mhz"] is None and not os.path.exists(c.path)
