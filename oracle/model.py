@@ -23,7 +23,7 @@ Readings where the paper is silent:
 Modes: 'spme' (the GPU's method), 'exact' (classical Ewald k-sum), 'open' (isolated
 cluster: beta = 0, no reciprocal or self terms, all pairs).
 """
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -418,7 +418,6 @@ def row_fields(sysobj, params, rows, vec=None):
     reciprocal part from one full smooth-PME evaluation gathered at the rows, plus the
     self terms. For spot checks of large systems, where pairs of every atom would not fit.
     """
-    from .radial import damped_r
     xyz = np.asarray(sysobj.xyz, np.float64)
     box = np.asarray(sysobj.box, np.float64)
     n = xyz.shape[0]

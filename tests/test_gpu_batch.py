@@ -5,7 +5,6 @@ relaunch picks up new positions written into the captured buffers.
 Mixed precision accumulates the PME grid with FP32 atomics, whose order varies from run
 to run, so "equal" means: same iteration count, dipoles within a tenth of the solve
 tolerance (in Debye), energy to 1e-7 and forces to 1e-5 relative."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

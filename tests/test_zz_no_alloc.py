@@ -4,7 +4,6 @@ set-up, or they hold no library context). Its scratch is a fixed array inside th
 library; two calls in a row on different systems must each match the energy that the
 context-based entry point polarization_energy_forces() returns, so nothing of the first
 call leaks into the second. Collected last on purpose."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
