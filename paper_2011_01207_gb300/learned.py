@@ -106,8 +106,15 @@ class Trainer:
         with open(path, "rb") as fh:
             if fh.read(8) != MAGIC:
                 raise ValueError("not an MLP checkpoint")
-            size, step = struct.unpack("<qq", fh.read(16))
+            head = fh.read(16)
+            if len(head) != 16:
+                raise ValueError("truncated MLP checkpoint")
+            size, step = struct.unpack("<qq", head)
+            if size <= 0 or step < 0:
+                raise ValueError("corrupt MLP checkpoint header")
             arrs = [np.frombuffer(fh.read(4 * size), np.float32) for _ in range(3)]
+            if any(a.size != size for a in arrs) or fh.read(1):
+                raise ValueError("MLP checkpoint size does not match its header")
         tr = cls(device=device, params=arrs[0])
         tr.m.copy_(tr.torch.tensor(arrs[1], device=device))
         tr.v.copy_(tr.torch.tensor(arrs[2], device=device))

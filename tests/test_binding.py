@@ -1,9 +1,11 @@
 """Host-side checks of the Python binding that run without a GPU: argument marshalling
-rejects host tensors, wrong dtypes and wrong shapes before any library call, and the
-constants mirror the public header."""
+rejects host tensors, wrong dtypes and wrong shapes before any library call, the
+constants mirror the public header, and learned-guess checkpoints are validated before
+any device work."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -41,3 +43,31 @@ def test_batch_step_layout_matches_the_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"([A-Za-z_][A-Za-z0-9_]*)\s*;", body)
     assert fields == [name for name, _ in binding.ApBatchStep._fields_]
+
+
+def test_checkpoint_header_is_checked_before_any_device_work(tmp_path):
+    import struct
+    from paper_2011_01207_gb300 import learned
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"NOTMAGIC" + b"\0" * 16)
+    with pytest.raises(ValueError, match="not an MLP checkpoint"):
+        learned.Trainer.load(str(bad), device="cpu")
+    short = tmp_path / "short.ckpt"
+    short.write_bytes(learned.MAGIC + struct.pack("<qq", 10, 3) + b"\0" * (4 * 25))
+    with pytest.raises(ValueError, match="does not match"):
+        learned.Trainer.load(str(short), device="cpu")
+    long_ = tmp_path / "long.ckpt"
+    long_.write_bytes(learned.MAGIC + struct.pack("<qq", 10, 3) + b"\0" * (4 * 31))
+    with pytest.raises(ValueError, match="does not match"):
+        learned.Trainer.load(str(long_), device="cpu")
+    head = tmp_path / "head.ckpt"
+    head.write_bytes(learned.MAGIC + b"\0" * 5)
+    with pytest.raises(ValueError, match="truncated"):
+        learned.Trainer.load(str(head), device="cpu")
+
+
+def test_initial_parameters_fit_the_network_shape():
+    from paper_2011_01207_gb300 import learned
+    p = learned.init_params(3)
+    assert p.dtype == np.float32 and p.size == 16 * 128 + 128 + 128 * 128 + 128 + 128 * 3 + 3
+    assert np.array_equal(p, learned.init_params(3)) and not np.array_equal(p, learned.init_params(4))
