@@ -140,7 +140,14 @@ class Oracle:
             rz_new = np.sum(r * z)
             p = z + (rz_new / rz) * p
             rz = rz_new
-        return mu, {"iters": it, "eps": eps, "history": hist, "converged": eps <= tol}
+        return mu, {"iters": it, "eps": eps, "history": hist, "converged": eps <= tol,
+                    "eps_field": self.field_residual_debye(E, mu)}
+
+    def field_residual_debye(self, E, mu):
+        """The other reading of the threshold: 4.80321 sqrt(sum_i |r_i|^2 / N) with the true
+        residual r = E - A mu (a field, unweighted by alpha), as Tinker logs it."""
+        r = E - self.apply_A(mu)
+        return DEBYE * float(np.sqrt(np.sum(r * r) / self.n))
 
     def jacobi_diis(self, E, guess=None, tol=1e-6, depth=6, maxiter=500):
         """Jacobi iteration accelerated by DIIS (one of the solvers the paper's method builds

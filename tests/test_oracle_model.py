@@ -164,3 +164,20 @@ def test_row_fields_match_full_oracle():
     Er, Tv = model.row_fields(s, p, rows, v)
     np.testing.assert_allclose(Er, o.permanent_field()[rows], rtol=0, atol=1e-12)
     np.testing.assert_allclose(Tv, o.apply_T(v)[rows], rtol=0, atol=1e-12)
+
+
+def test_two_readings_of_the_threshold():
+    """The alpha-weighted measure (the stopping rule) and the unweighted field residual
+    differ per atom by the factor 1/alpha_i, so their ratio lies in [1/max alpha,
+    1/min alpha]; and the PCG's recursive residual is the true one, so the field reading
+    of a tightly converged solve is tiny too."""
+    from paper_2011_01207_gb300 import synth
+    s = synth.water_box(27, 9.3, 11)
+    o = Oracle(s, Params(beta=0.5446, cutoff=4.5, grid=(12, 12, 12)))
+    E = o.permanent_field()
+    for tol in (1e-3, 1e-5, 1e-10):
+        mu, info = o.pcg(E, tol=tol)
+        ea = o.residual_eps(E - o.apply_A(mu))
+        ratio = info["eps_field"] / ea
+        assert 1 / s.alpha.max() - 1e-9 <= ratio <= 1 / s.alpha.min() + 1e-9
+        assert info["eps_field"] < 3 * tol / s.alpha.min()
