@@ -327,7 +327,10 @@ class Oracle:
         return spme.strain_sum(self.xyz, self.box, p.beta, p.grid, p.order, src_a, src_b)
 
     def virial(self, mu):
-        """V_ab = dE_pol/de_ab [3,3] (kcal/mol) under the homogeneous deformation
+        """The virial that the paper's real-space pair loop updates with the energy and the
+        forces (Sec. 1.2.1) and accumulates in double precision (Sec. 2.2); the paper
+        prints no formula, so it is written here from its definition:
+        V_ab = dE_pol/de_ab [3,3] (kcal/mol) under the homogeneous deformation
         x -> (I + e) x of positions and box, with the local-frame multipoles carried by the
         deformed frames and mu re-solved; because E_pol is stationary in mu this is the
         derivative of U = -f mu.E - (f/2) mu.T mu at fixed mu (global components):
