@@ -113,7 +113,7 @@ def _bf16_peak():
     return 1900.0, "fallback"
 
 
-def kernel_rooflines(kern, per_launch_counts, n, n_pad, npairs, grid):
+def kernel_rooflines(kern, per_launch_counts, n, n_pad, npairs, grid, fp32_peak=None):
     """Each timed kernel against its bound: FP32 ALU (pair kernels), HBM (spread, gather,
     convolution, PCG vectors; algorithmic bytes) or BF16 tensor (MLP)."""
     hbm, hbm_kind = _peaks()
@@ -139,7 +139,8 @@ def kernel_rooflines(kern, per_launch_counts, n, n_pad, npairs, grid):
         if bound == "hbm":
             ach, peak, unit, kind = w / sec / 1e9, hbm, "GB/s", hbm_kind
         elif bound == "alu":
-            ach, peak, unit, kind = w / sec / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s", "derived"
+            ach, unit = w / sec / 1e12, "TFLOP/s"
+            peak, kind = (fp32_peak, "measured (ap_fp32_peak)") if fp32_peak else (FP32_PEAK_TFLOPS, "derived")
         else:
             ach, peak, unit, kind = w / sec / 1e12, bf16, "TFLOP/s", bf16_kind
         out[name] = {"bound": bound, "launch_us": round(kern[name] * 1e3, 2),
@@ -904,6 +905,47 @@ def run_two_sets(args):
         "clocks": clk}))
 
 
+KERNEL_WORKLOADS = {
+    96000: (32000, 98.7, (100, 100, 100), 1002, "water_96000_atoms_98.7A_grid100_rc7+2_mixed"),
+    1065000: (355000, 221.6, (224, 224, 224), 1004, "water_1065000_atoms_221.6A_grid224_rc7+2_mixed"),
+}
+
+
+def run_kernels(args):
+    """Every kernel of the path timed alone (CUDA events on its launch stream, warm L2, one
+    configuration after one solve from alpha E and one force call), each against its own
+    roofline, with the FP32 peak measured on the device. Small enough to run under ncu."""
+    import torch
+    from paper_2011_01207_gb300 import binding, build as _build, synth
+    _build.build_library()
+    dev = torch.device("cuda", 0)
+    nmol, box, grid, seed, name = KERNEL_WORKLOADS[args.atoms]
+    s = synth.water_box(nmol, box, seed)
+    ctx = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=grid, precision=binding.AP_MIXED,
+                          device=dev)
+    ctx.build()
+    ctx.permanent_field()
+    info = ctx.solve(tol=TOL, max_iter=200)
+    ctx.energy_forces()
+    torch.cuda.synchronize()
+    reps = max(1, args.reps)
+    kern = {k: binding.ap_time_kernel(ctx.ctx, k, reps) for k in
+            ("real_matvec", "spread_dipoles", "gather_field", "convolve", "real_field", "spread_multipoles",
+             "pair_forces")}
+    ctx.solve(tol=TOL, max_iter=200)
+    kern["pcg_vectors"] = binding.ap_time_kernel(ctx.ctx, "pcg_vectors", reps)
+    fp32, sms = binding.ap_fp32_peak(max(3, reps))
+    npairs = pairs_within(s.xyz, s.box, CUTOFF)
+    counts = {"real_matvec": info.iterations + 1, "spread_dipoles": info.iterations + 2,
+              "gather_field": info.iterations + 1, "convolve": info.iterations + 3, "pcg_vectors": info.iterations}
+    kernels = kernel_rooflines(kern, counts, s.n, (s.n + 31) // 32 * 32, npairs, grid, fp32_peak=fp32)
+    ctx.close()
+    print(json.dumps({"metric": "per-kernel launch time and roofline fraction", "impl": "ours", "workload": name,
+                      "atoms": s.n, "pairs_in_cutoff": npairs, "pcg_iters_plain": info.iterations,
+                      "fp32_peak_tflops_measured": round(fp32, 2), "sm_count": sms, "reps": reps,
+                      "kernels": kernels}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -911,7 +953,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
-    ap.add_argument("--workload", default="water96k", choices=["water96k", "replicas64", "precision", "two_sets"],
+    ap.add_argument("--atoms", type=int, default=96000, choices=sorted(KERNEL_WORKLOADS),
+                    help="--workload kernels: the 96,000- or the 1,065,000-atom water box")
+    ap.add_argument("--reps", type=int, default=20, help="--workload kernels: timed launches per kernel")
+    ap.add_argument("--workload", default="water96k",
+                    choices=["water96k", "replicas64", "precision", "two_sets", "kernels"],
                     help="water96k: the 96,000-atom box (default); replicas64: 64 uneven replicas in one graph; "
                          "precision: errors of every output against the FP64 oracle; two_sets: AMOEBA's d/p "
                          "dipole sets on the 23,558-atom solvated chain")
@@ -926,6 +972,8 @@ def main():
         run_precision(args)
     elif args.workload == "two_sets":
         run_two_sets(args)
+    elif args.workload == "kernels":
+        run_kernels(args)
     else:
         run_ours(args)
 

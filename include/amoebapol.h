@@ -34,7 +34,7 @@ extern "C" {
 #define AP_NOT_CONVERGED    1   /* warning: max_iter reached, output holds the last iterate */
 #define AP_ERR_ARG         -1   /* null pointer, bad size, box smaller than 2*(cutoff+buffer) ... */
 #define AP_ERR_CUDA        -2   /* a CUDA / cuFFT call failed (message in ap_last_error) */
-#define AP_ERR_CAPACITY    -3   /* a fixed-size internal list overflowed */
+/* -3 is unused: every internal list grows to fit (build_neighbour_blocks reallocates) */
 #define AP_ERR_NONFINITE   -4   /* NaN or Inf found in an input or a reduction */
 #define AP_ERR_TIMEOUT     -5   /* a bounded device wait expired */
 #define AP_ERR_STATE       -6   /* calls made out of order (e.g. solve before field) */
@@ -69,7 +69,8 @@ typedef struct {
 typedef struct {
     int    iterations;    /* PCG iterations performed (matrix-vector products after the initial residual),
                              or DIIS updates taken */
-    int    status;        /* AP_OK or AP_NOT_CONVERGED */
+    int    status;        /* AP_OK, AP_NOT_CONVERGED, or AP_ERR_NONFINITE when a reduction of the
+                             solve produced NaN or Inf (the solve then stops) */
     double eps_debye;     /* final RMS of alpha_i r_i in Debye (the convergence measure) */
     double eps_initial;   /* the same measure for the initial guess */
 } ap_solve_info;
@@ -219,8 +220,10 @@ int ap_list_stats(const ap_ctx* ctx, int* h_blocks, int* h_tiles, int* h_excl_ti
 void* ap_stream(const ap_ctx* ctx);
 
 /* Iterations and residuals of the most recent induced_dipoles_pcg(),
- * induced_dipoles_diis() or induced_dipoles_pcg_dp() on this context. Synchronizes the
- * context's stream. */
+ * induced_dipoles_diis() or induced_dipoles_pcg_dp() on this context, including solves
+ * launched inside a batch graph. Synchronizes the context's stream. Returns
+ * AP_ERR_NONFINITE (h_info still filled, status AP_ERR_NONFINITE) when a reduction of that
+ * solve produced NaN or Inf, e.g. from a non-finite input, and AP_OK otherwise. */
 int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 
 /* Benchmark support: launch one kernel of the path `reps` times on the context's stream
@@ -241,6 +244,21 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 #define AP_KERNEL_REAL_MATVEC2      8   /* f1: the two-set real-space product on the last two-set
                                           search directions (needs set_scaled_pairs) */
 int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
+
+/* Diagnostics: the FP32 fused multiply-add rate of the current device, measured. The pair
+ * kernels (a2, a5, a9) are bound by plain FP32 ALU work, not by a contraction, so their
+ * roofline denominator is this rate, SMs x FP32 lanes x 2 flops x clock. A kernel with 8
+ * independent FMA chains per thread runs on a grid of (resident CTAs per SM) x (the SM count
+ * queried from the device); the best of `reps` launches timed with CUDA events gives
+ * *h_tflops (TFLOP/s, FMA = 2 flops) and *h_sm_count the SM count. Allocates 4 bytes and a
+ * stream of its own; synchronizes. Errors through ap_last_error(NULL). */
+int ap_fp32_peak(int reps, double *h_tflops, int *h_sm_count);
+
+/* Diagnostics: erfc as the FP32 pair kernels evaluate it (the rational approximation of
+ * Abramowitz & Stegun 7.1.26 times e^{-x^2} from the kernels' fast exponential) in d_approx,
+ * and CUDA's erfcf in d_lib, for the n arguments d_x (x >= 0; device arrays of floats). Async
+ * on `stream`; AP_ERR_ARG for a null pointer or n < 1. */
+int ap_eval_erfc(const float *d_x, int n, float *d_approx, float *d_lib, void *stream);
 
 /* Batched replicas: many independent systems of uneven size advanced by one CUDA-graph
  * launch (the paper runs independent trajectories as separate jobs; here they share the
@@ -380,7 +398,9 @@ int ap_adaptive_guess(int n, const double* d_base, const double* d_mu1, const do
  * Allocates nothing and calls no allocating routine: its scratch is a 32 KB array of
  * block partial sums that every GPU loading the library holds until the process exits.
  * The first call on each device looks up that array's device address (with the
- * device current); make that first call before any stream capture. All calls share
+ * device current); make that first call before any stream capture. The address is kept
+ * for the rest of the process: after cudaDeviceReset() on a device the array is reloaded
+ * elsewhere, so do not call this entry point on that device again. All calls share
  * the array and it keeps the last call's partials, so calls whose kernels overlap on the
  * GPU (e.g. on two streams at once) race and must be serialised by the caller.
  * Errors are described by ap_last_error(NULL). Returns once the work is enqueued. */

@@ -15,7 +15,8 @@ from .build import LIB
 
 AP_OK, AP_NOT_CONVERGED = 0, 1
 AP_MIXED, AP_FP64, AP_FIXED = 0, 1, 2
-_ERRORS = {-1: "AP_ERR_ARG", -2: "AP_ERR_CUDA", -3: "AP_ERR_CAPACITY", -4: "AP_ERR_NONFINITE",
+AP_ERR_NONFINITE = -4
+_ERRORS = {-1: "AP_ERR_ARG", -2: "AP_ERR_CUDA", -4: "AP_ERR_NONFINITE",
            -5: "AP_ERR_TIMEOUT", -6: "AP_ERR_STATE"}
 
 # every symbol the public header declares
@@ -26,7 +27,8 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "ap_mlp_features", "ap_learned_guess", "ap_mlp_gradient", "ap_mlp_train_step",
            "ap_batch_create", "ap_batch_capture", "ap_batch_launch", "ap_batch_destroy", "ap_autotune",
            "ap_extrapolate_guess", "induced_dipoles_diis", "set_scaled_pairs", "permanent_field_dp",
-           "induced_dipoles_pcg_dp", "polarization_energy_forces_dp", "ap_adaptive_guess")
+           "induced_dipoles_pcg_dp", "polarization_energy_forces_dp", "ap_adaptive_guess", "ap_fp32_peak",
+           "ap_eval_erfc")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5, "pair_forces": 6,
            "pcg_vectors": 7, "real_matvec2": 8}
@@ -52,7 +54,11 @@ class ApBatchStep(ctypes.Structure):
 
 
 class ApError(RuntimeError):
-    pass
+    """A failed call; `code` is the library's AP_ERR_* value (0 for a marshalling error)."""
+
+    def __init__(self, msg, code=0):
+        super().__init__(msg)
+        self.code = code
 
 
 _lib = None
@@ -102,6 +108,8 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "ap_batch_launch": (I, [P, P]),
         "ap_batch_destroy": (None, [P]),
         "ap_autotune": (I, [P, I, ctypes.POINTER(I)]),
+        "ap_fp32_peak": (I, [I, ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "ap_eval_erfc": (I, [P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -131,7 +139,7 @@ def _ptr(t, dtype=None, shape=None, name="tensor", allow_none=False):
 def _check(ctx, code, what):
     if code < 0:
         msg = load().ap_last_error(ctx).decode(errors="replace")
-        raise ApError(f"{what} failed: {_ERRORS.get(code, code)}: {msg}")
+        raise ApError(f"{what} failed: {_ERRORS.get(code, code)}: {msg}", code)
     return code
 
 
@@ -267,10 +275,15 @@ def polarization_energy_noalloc(mu, field, energy, stream=None):
     """Context-free energy (no device allocation); `stream` is a torch stream or None."""
     import torch
     n = mu.shape[0]
-    sp = ctypes.c_void_p((stream or torch.cuda.current_stream(mu.device)).cuda_stream)
-    code = load().polarization_energy_noalloc(
-        _ptr(mu, torch.float64, (n, 3), "mu"), _ptr(field, torch.float64, (n, 3), "field"), int(n),
-        _ptr(energy, torch.float64, (1,), "energy"), sp)
+    for t, name in ((field, "field"), (energy, "energy")):
+        if isinstance(t, torch.Tensor) and t.device != mu.device:
+            raise ApError(f"{name} is on {t.device}, mu on {mu.device}: all three must be on one device")
+    # the library launches on the current device with that device's scratch array
+    with torch.cuda.device(mu.device):
+        sp = ctypes.c_void_p((stream or torch.cuda.current_stream(mu.device)).cuda_stream)
+        code = load().polarization_energy_noalloc(
+            _ptr(mu, torch.float64, (n, 3), "mu"), _ptr(field, torch.float64, (n, 3), "field"), int(n),
+            _ptr(energy, torch.float64, (1,), "energy"), sp)
     return _check(None, code, "polarization_energy_noalloc")
 
 
@@ -373,6 +386,21 @@ def ap_learned_guess(ctx, packed, mu0):
     n = mu0.shape[0]
     _check(ctx, load().ap_learned_guess(ctx, _ptr(packed, torch.uint8, (ap_mlp_packed_bytes(),), "packed"),
                                         _ptr(mu0, torch.float64, (n, 3), "mu0")), "ap_learned_guess")
+
+
+def ap_fp32_peak(reps=10):
+    """(TFLOP/s, SM count): the device's FP32 FMA rate measured by the library's microbenchmark."""
+    tf, sms = ctypes.c_double(), ctypes.c_int()
+    _check(None, load().ap_fp32_peak(int(reps), ctypes.byref(tf), ctypes.byref(sms)), "ap_fp32_peak")
+    return tf.value, sms.value
+
+
+def ap_eval_erfc(x, approx, lib, stream=None):
+    """approx = erfc as the FP32 pair kernels form it, lib = CUDA's erfcf, at x (float32 CUDA)."""
+    import torch
+    n = x.shape[0]
+    _check(None, load().ap_eval_erfc(_ptr(x, torch.float32, (n,), "x"), int(n), _ptr(approx, torch.float32, (n,), "approx"),
+                                     _ptr(lib, torch.float32, (n,), "lib"), _stream_ptr(x, stream)), "ap_eval_erfc")
 
 
 def ap_autotune(ctx, reps=5):

@@ -303,6 +303,7 @@ int ap_solve_info_last(ap_ctx *ctx, ap_solve_info *h_info) {
     h_info->eps_debye = ctx->st_host->eps;
     h_info->eps_initial = ctx->st_host->eps0;
     h_info->status = ctx->st_host->status;
+    if (ctx->st_host->nonfinite) return ap_fail(ctx, AP_ERR_NONFINITE, "non-finite value in the PCG reductions");
     return AP_OK;
 }
 

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(NT) k_diis_step(const double *__restrict__ x, 
     if (!isfinite(eps)) {
         st->nonfinite = 1;
         st->done = 1;
-        st->status = AP_OK;
+        st->status = AP_ERR_NONFINITE;
     } else if (eps <= st->tol) {
         st->done = 1;
         st->status = AP_OK;

@@ -338,6 +338,7 @@ __global__ void k_dp_init_residual(const double *__restrict__ E2, const double *
         if (!isfinite(st->eps[k])) st->nonfinite = 1;
     }
     st->done = (fmax(st->eps[0], st->eps[1]) <= tol) || st->nonfinite;
+    if (st->nonfinite) st->status = AP_ERR_NONFINITE;
 }
 
 __global__ void k_dp_set_cond(cudaGraphConditionalHandle h, const DpState *st) {
@@ -445,7 +446,7 @@ __global__ void k_dp_update(const typename V4<T>::type *__restrict__ p2, const d
     if (bad) st->nonfinite = 1;
     if (fmax(st->eps[0], st->eps[1]) <= st->tol || bad) {
         st->done = 1;
-        st->status = AP_OK;
+        st->status = bad ? AP_ERR_NONFINITE : AP_OK;
     } else if (st->iter >= st->max_iter) {
         st->done = 1;
         st->status = AP_NOT_CONVERGED;
@@ -933,6 +934,7 @@ int dp_info(ap_ctx *ctx, ap_solve_info *info) {
     info->eps_debye = fmax(h->eps[0], h->eps[1]);
     info->eps_initial = fmax(h->eps0[0], h->eps0[1]);
     info->status = h->status;
+    if (h->nonfinite) return ap_fail(ctx, AP_ERR_NONFINITE, "non-finite value in the PCG reductions");
     return AP_OK;
 }
 

@@ -54,7 +54,9 @@ __global__ void k_energy_final(const double *__restrict__ partials, int nparts, 
 std::mutex g_mtx;
 double *g_dev_ptr[256] = {nullptr};
 
-// device address of the scratch array on the current device, looked up once per device
+// device address of the scratch array on the current device, looked up once per device and
+// kept for the process (a cudaDeviceReset() would reload the module elsewhere: the header
+// tells callers not to use this entry point on a device after resetting it)
 int scratch_address(int dev, double **out) {
     std::lock_guard<std::mutex> lock(g_mtx);
     if (dev < 0 || dev >= 256) return ap_fail(nullptr, AP_ERR_ARG, "device ordinal out of range");

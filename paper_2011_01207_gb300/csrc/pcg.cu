@@ -102,7 +102,7 @@ __device__ void finish_iteration(PcgState *st, double rzn, double zzt, int n, cu
     if (bad) st->nonfinite = 1;
     if (eps <= st->tol || bad) {
         st->done = 1;
-        st->status = AP_OK;
+        st->status = bad ? AP_ERR_NONFINITE : AP_OK;
     } else if (st->iter >= st->max_iter) {
         st->done = 1;
         st->status = AP_NOT_CONVERGED;
@@ -176,7 +176,7 @@ __global__ void k_init_residual(const double *__restrict__ E, const double *__re
     st->gamma = 0.0;
     st->nonfinite = !isfinite(eps);
     st->done = (eps <= tol) || st->nonfinite;
-    st->status = AP_OK;
+    st->status = st->nonfinite ? AP_ERR_NONFINITE : AP_OK;
     st->pq = st->rz_new = st->zz = 0.0;
     st->guard = 0;
 }

@@ -1,11 +1,14 @@
-"""GPU parity at the full sizes of the solvated-chain box (23,558 atoms, 62.2 A, grid 64)
-and the large water box (1,065,000 atoms, 221.6 A, grid 224), in the mixed precision the
-benchmark runs (FP32 pair and PME arithmetic, FP64 accumulation), through the C-ABI.
+"""GPU parity at the full sizes of the benchmark's water box (96,000 atoms, 98.7 A, grid
+100), the solvated-chain box (23,558 atoms, 62.2 A, grid 64) and the large water box
+(1,065,000 atoms, 221.6 A, grid 224), in the mixed precision the benchmark runs (FP32 pair
+and PME arithmetic, FP64 accumulation), through the C-ABI and in the benchmark's launch
+configuration (7 A + 2 A lists, tile shifts, list filtering, graph solve).
 
-The chain box is checked atom by atom against the FP64 oracle: permanent field, the true
-residual and the error of the solved dipoles, the energy and the forces at those dipoles.
-At a million atoms the oracle evaluates sampled rows: the permanent field and the true
-residual of the solved dipoles at 200 atoms."""
+The 96,000- and 23,558-atom boxes are checked atom by atom against the full FP64 oracle:
+permanent field, the true residual of the solved dipoles (and at 23,558 atoms their
+distance to the oracle's solution), the energy and every force at those dipoles. At a
+million atoms the oracle evaluates sampled rows: the permanent field and the true residual
+of the solved dipoles at 200 atoms."""
 import numpy as np
 import pytest
 
@@ -28,6 +31,29 @@ def _built():
     build.build_library()
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
+
+
+def test_water_96000_atoms_full():
+    s = synth.water_box(32000, 98.7, 1002)
+    grid = (100, 100, 100)
+    c = binding.Context(s, cutoff=7.0, buffer=2.0, beta=0.5446, grid=grid, precision=binding.AP_MIXED)
+    c.build()
+    c.permanent_field()
+    tol = 1e-5
+    info = c.solve(tol=tol, max_iter=100)
+    assert info.status == 0 and info.eps_debye <= tol
+    e, f = c.energy_forces(c.mu)
+    torch.cuda.synchronize()
+    o = Oracle(s, Params(beta=0.5446, grid=grid, cutoff=7.0))
+    E = o.permanent_field()
+    assert _rel_rms(c.field.cpu().numpy(), E) < 1e-5
+    mu = c.mu.cpu().numpy()
+    assert o.residual_eps(E - o.apply_A(mu)) < 1.5 * tol
+    e_o = o.energy(mu, E)
+    assert abs(float(e.cpu()[0]) - e_o) < 1e-5 * abs(e_o)
+    F_o = o.forces(mu)
+    assert _rel_rms(f.cpu().numpy(), F_o) < 1e-4
+    c.close()
 
 
 def test_solvated_chain_23558_atoms():
