@@ -194,19 +194,30 @@ int induced_dipoles_pcg_dp(ap_ctx* ctx, const double* d_guess_d, const double* d
 
 /* f1 - E_pol = -(f/2) sum mu_d . E_p and F = -dE_pol/dx for converged mu_d, mu_p:
  * -(f/2) [mu_p . dE_d + mu_d . dE_p + mu_p . dT mu_d], with the frame (torque) terms.
- *   d_energy [1] double, kcal/mol; d_forces [n][3] double, kcal/mol/A (overwritten). */
+ *   d_energy [1] double, kcal/mol; d_forces [n][3] double, kcal/mol/A (overwritten).
+ *   d_virial [9] double output (row-major V_ab = dE_pol/de_ab, as polarization_energy_forces),
+ *            or NULL to skip it. */
 int polarization_energy_forces_dp(ap_ctx* ctx, const double* d_mu_d, const double* d_mu_p,
-                                  double* d_energy, double* d_forces);
+                                  double* d_energy, double* d_forces, double* d_virial);
 
-/* a9 - Polarization energy and forces at fixed dipoles (variational):
+/* a9 - Polarization energy, forces and virial at fixed dipoles (variational; the paper's
+ * real-space loop updates energy, forces and virial together, Sec. 1.2.1, and accumulates them
+ * in double precision, Sec. 2.2):
  * E_pol = -(f/2) sum_i mu_i . E_i with f = 332.063713, and F = -dE_pol/dx including the
  * reciprocal-space terms and the forces on frame atoms from multipole rotation.
  *   d_mu      [n][3] double induced dipoles (e.g. from induced_dipoles_pcg).
  *   d_energy  [1] double output, kcal/mol.
  *   d_forces  [n][3] double output, kcal/mol/A (overwritten).
+ *   d_virial  [9] double output or NULL: V_ab = dE_pol/de_ab (row-major, kcal/mol), the
+ *             derivative under the homogeneous deformation x -> (I + e) x of positions and box
+ *             with the local-frame multipoles carried by their frames; at converged dipoles it
+ *             equals the derivative at fixed mu. The pressure tensor's polarization share is
+ *             -V / volume. Pairs, frame vectors and the reciprocal sum (volume and |m| of the
+ *             Ewald kernel, potential derivatives times multipoles) are summed in FP64 (fixed
+ *             point in AP_FIXED, reproducible).
  * Uses the configuration and field of the last permanent_field() call. */
 int polarization_energy_forces(ap_ctx* ctx, const double* d_mu, double* d_energy,
-                               double* d_forces);
+                               double* d_forces, double* d_virial);
 
 /* a5+a6 alone, for tests and diagnostics: d_out = T v = (T_real + T_rec + self) v for the
  * current configuration; d_v and d_out are [n][3] double in caller order. */
@@ -298,6 +309,7 @@ typedef struct {
                                     previous error held at the second and third). Holds the last
                                     three dipoles, the last three learned guesses, the guess and
                                     the reduction scratch; takes precedence over d_hist. */
+    double*       d_virial;      /* [9] output virial (as polarization_energy_forces), or NULL */
 } ap_batch_step;
 int ap_batch_create(ap_batch** out, ap_ctx* const* ctxs, int n_ctx);
 int ap_batch_capture(ap_batch* b, const ap_batch_step* steps);
@@ -356,6 +368,12 @@ int ap_mlp_features(ap_ctx* ctx, const double* d_mu, float* d_feat, float* d_tar
 /* mu0 [n][3] (double, caller order) = the learned guess for the current configuration,
  * to pass as d_guess to induced_dipoles_pcg(). */
 int ap_learned_guess(ap_ctx* ctx, const void* d_packed, double* d_mu0);
+
+/* a4 - The direct-field guess mu0 = alpha_i E_i of the current configuration, in caller order
+ * (the start induced_dipoles_pcg takes for a NULL guess), as a base for the trajectory guesses
+ * below: with it, ap_extrapolate_guess gives the classical zero-order hold of its error,
+ * alpha E(t) + (mu - alpha E)(t-1). d_mu0 [n][3] double, device. Async. */
+int ap_direct_guess(ap_ctx* ctx, double* d_mu0);
 
 /* Initial guess from the two previous steps of a trajectory (the paper has no predictor;
  * this is the classical extrapolation, optionally on top of a per-step base guess):

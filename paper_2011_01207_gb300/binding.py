@@ -28,7 +28,7 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "ap_batch_create", "ap_batch_capture", "ap_batch_launch", "ap_batch_destroy", "ap_autotune",
            "ap_extrapolate_guess", "induced_dipoles_diis", "set_scaled_pairs", "permanent_field_dp",
            "induced_dipoles_pcg_dp", "polarization_energy_forces_dp", "ap_adaptive_guess", "ap_fp32_peak",
-           "ap_eval_erfc")
+           "ap_eval_erfc", "ap_direct_guess")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5, "pair_forces": 6,
            "pcg_vectors": 7, "real_matvec2": 8}
@@ -50,7 +50,7 @@ class ApBatchStep(ctypes.Structure):
                 ("d_alpha", ctypes.c_void_p), ("d_mlp_packed", ctypes.c_void_p), ("d_mu0", ctypes.c_void_p),
                 ("tol_debye", ctypes.c_double), ("max_iter", ctypes.c_int), ("d_mu", ctypes.c_void_p),
                 ("d_energy", ctypes.c_void_p), ("d_forces", ctypes.c_void_p), ("d_hist", ctypes.c_void_p),
-                ("d_hist_lsq", ctypes.c_void_p)]
+                ("d_hist_lsq", ctypes.c_void_p), ("d_virial", ctypes.c_void_p)]
 
 
 class ApError(RuntimeError):
@@ -85,8 +85,8 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "set_scaled_pairs": (I, [P, I, P, P]),
         "permanent_field_dp": (I, [P, P, P, P, P, P, P]),
         "induced_dipoles_pcg_dp": (I, [P, P, P, D, I, P, P, ctypes.POINTER(ApSolveInfo)]),
-        "polarization_energy_forces_dp": (I, [P, P, P, P, P]),
-        "polarization_energy_forces": (I, [P, P, P, P]),
+        "polarization_energy_forces_dp": (I, [P, P, P, P, P, P]),
+        "polarization_energy_forces": (I, [P, P, P, P, P]),
         "dipole_field_matvec": (I, [P, P, P]),
         "ap_list_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "ap_stream": (P, [P]),
@@ -110,6 +110,7 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "ap_autotune": (I, [P, I, ctypes.POINTER(I)]),
         "ap_fp32_peak": (I, [I, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "ap_eval_erfc": (I, [P, I, P, P, P]),
+        "ap_direct_guess": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -228,21 +229,23 @@ def induced_dipoles_pcg_dp(ctx, guess_d, guess_p, tol_debye: float, max_iter: in
     return info if want_info else None
 
 
-def polarization_energy_forces_dp(ctx, mu_d, mu_p, energy, forces):
+def polarization_energy_forces_dp(ctx, mu_d, mu_p, energy, forces, virial=None):
     import torch
     n = mu_d.shape[0]
     return _check(ctx, load().polarization_energy_forces_dp(
         ctx, _ptr(mu_d, torch.float64, (n, 3), "mu_d"), _ptr(mu_p, torch.float64, (n, 3), "mu_p"),
-        _ptr(energy, torch.float64, (1,), "energy"), _ptr(forces, torch.float64, (n, 3), "forces")),
-        "polarization_energy_forces_dp")
+        _ptr(energy, torch.float64, (1,), "energy"), _ptr(forces, torch.float64, (n, 3), "forces"),
+        _ptr(virial, torch.float64, (3, 3), "virial", allow_none=True)), "polarization_energy_forces_dp")
 
 
-def polarization_energy_forces(ctx, mu, energy, forces):
+def polarization_energy_forces(ctx, mu, energy, forces, virial=None):
+    """virial: optional float64 [3, 3] CUDA tensor receiving V_ab = dE_pol/de_ab."""
     import torch
     n = mu.shape[0]
     return _check(ctx, load().polarization_energy_forces(
         ctx, _ptr(mu, torch.float64, (n, 3), "mu"), _ptr(energy, torch.float64, (1,), "energy"),
-        _ptr(forces, torch.float64, (n, 3), "forces")), "polarization_energy_forces")
+        _ptr(forces, torch.float64, (n, 3), "forces"), _ptr(virial, torch.float64, (3, 3), "virial", allow_none=True)),
+        "polarization_energy_forces")
 
 
 def dipole_field_matvec(ctx, v, out):
@@ -381,6 +384,13 @@ def ap_mlp_features(ctx, feat, mu=None, target=None):
            "ap_mlp_features")
 
 
+def ap_direct_guess(ctx, mu0):
+    """mu0 [n][3] (caller order) = alpha E of the current configuration."""
+    import torch
+    n = mu0.shape[0]
+    _check(ctx, load().ap_direct_guess(ctx, _ptr(mu0, torch.float64, (n, 3), "mu0")), "ap_direct_guess")
+
+
 def ap_learned_guess(ctx, packed, mu0):
     import torch
     n = mu0.shape[0]
@@ -419,7 +429,7 @@ class Batch:
         _check(None, load().ap_batch_create(ctypes.byref(self.ptr), arr, len(self.contexts)), "ap_batch_create")
         self._keep = []
 
-    def capture(self, tol=1e-5, max_iter=200, packed=None, forces=True, history=False):
+    def capture(self, tol=1e-5, max_iter=200, packed=None, forces=True, history=False, virial=False):
         steps = (ApBatchStep * len(self.contexts))()
         self._keep = []
         for k, c in enumerate(self.contexts):
@@ -442,6 +452,8 @@ class Batch:
             st.d_mu = c.mu.data_ptr()
             if forces:
                 st.d_energy, st.d_forces = c.energy.data_ptr(), c.forces.data_ptr()
+                if virial:
+                    st.d_virial = c.virial.data_ptr()
         _check(None, load().ap_batch_capture(self.ptr, steps), "ap_batch_capture")
 
     def launch(self, stream):
@@ -505,6 +517,7 @@ class Context:
         self.mu = t.zeros((self.n, 3), dtype=t.float64, device=dev)
         self.forces = t.zeros((self.n, 3), dtype=t.float64, device=dev)
         self.energy = t.zeros(1, dtype=t.float64, device=dev)
+        self.virial = t.zeros((3, 3), dtype=t.float64, device=dev)
 
     def set_positions(self, xyz):
         self.xyz.copy_(self.torch.as_tensor(np.ascontiguousarray(xyz, np.float64)), non_blocking=False)
@@ -537,14 +550,17 @@ class Context:
     def solve_dp(self, tol=1e-5, max_iter=200, guess_d=None, guess_p=None, want_info=True):
         return induced_dipoles_pcg_dp(self.ctx, guess_d, guess_p, tol, max_iter, self.mu_d, self.mu_p, want_info)
 
-    def energy_forces_dp(self, mu_d=None, mu_p=None):
+    def energy_forces_dp(self, mu_d=None, mu_p=None, virial=False):
         polarization_energy_forces_dp(self.ctx, self.mu_d if mu_d is None else mu_d,
-                                      self.mu_p if mu_p is None else mu_p, self.energy, self.forces)
-        return self.energy, self.forces
+                                      self.mu_p if mu_p is None else mu_p, self.energy, self.forces,
+                                      self.virial if virial else None)
+        return (self.energy, self.forces, self.virial) if virial else (self.energy, self.forces)
 
-    def energy_forces(self, mu=None):
-        polarization_energy_forces(self.ctx, self.mu if mu is None else mu, self.energy, self.forces)
-        return self.energy, self.forces
+    def energy_forces(self, mu=None, virial=False):
+        """(energy, forces) or, with virial=True, (energy, forces, virial [3, 3])."""
+        polarization_energy_forces(self.ctx, self.mu if mu is None else mu, self.energy, self.forces,
+                                   self.virial if virial else None)
+        return (self.energy, self.forces, self.virial) if virial else (self.energy, self.forces)
 
     def matvec(self, v, out):
         return dipole_field_matvec(self.ctx, v, out)

@@ -30,7 +30,7 @@ void free_all(ap_ctx *c) {
     void *ptrs[] = {c->perm, c->iperm, c->bcenter, c->tiles, c->tshift, c->tshift_lo, c->tile_excl, c->excl_mask, c->cell_count,
                     c->tmp_int, c->excl_off, c->excl_atoms, c->posq, c->dipd, c->quad0, c->quad1, c->alpha,
                     c->E, c->acc, c->rec, c->rot, c->mpl, c->frame_s, c->fvec, c->mu, c->r, c->qv, c->p, c->st,
-                    c->grid, c->cgrid, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf,
+                    c->grid, c->cgrid, c->cgrid_v, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf,
                     c->tile_off, c->chunk_j, c->chunk_pos, c->chunk_src, c->chunk_mask, c->chunk_flag, c->nchunk,
                     c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y, c->smask, c->smask_t, c->e1s,
                     c->dg, c->stb, c->stw, c->grid_fx, c->work_off,
@@ -107,6 +107,7 @@ int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
     if ((r = dalloc(ctx, (char **)&ctx->grid, es * ctx->ngrid))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->grid2, es * ctx->ngrid))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->cgrid, 2 * es * ctx->ncgrid))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->cgrid_v, 2 * es * ctx->ncgrid))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->green, es * ctx->ncgrid))) return r;
     if ((r = dalloc(ctx, &ctx->frc, sizeof(double) * 3 * np))) return r;
     if ((r = dalloc(ctx, &ctx->gdip, sizeof(double) * 3 * np))) return r;
@@ -256,19 +257,20 @@ int induced_dipoles_pcg_dp(ap_ctx *ctx, const double *d_guess_d, const double *d
 }
 
 int polarization_energy_forces_dp(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d_energy,
-                                  double *d_forces) {
+                                  double *d_forces, double *d_virial) {
     if (!ctx) return AP_ERR_ARG;
     ctx->err.clear();
     if (!d_mu_d || !d_mu_p || !d_energy || !d_forces) return ap_fail(ctx, AP_ERR_ARG, "null pointer");
-    return dp_forces(ctx, d_mu_d, d_mu_p, d_energy, d_forces);
+    return dp_forces(ctx, d_mu_d, d_mu_p, d_energy, d_forces, d_virial);
 }
 
-int polarization_energy_forces(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
+int polarization_energy_forces(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces,
+                               double *d_virial) {
     if (!ctx) return AP_ERR_ARG;
     ctx->err.clear();
     if (!d_mu || !d_energy || !d_forces) return ap_fail(ctx, AP_ERR_ARG, "null pointer");
     if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
-    return forces_run(ctx, d_mu, d_energy, d_forces);
+    return forces_run(ctx, d_mu, d_energy, d_forces, d_virial);
 }
 
 int dipole_field_matvec(ap_ctx *ctx, const double *d_v, double *d_out) {

@@ -56,7 +56,7 @@ int capture_one(ap_ctx *c, const ap_batch_step &st) {
         if ((r = hist_push_launch(c, st.d_mu0, st.d_mu, st.d_hist, c->s0))) return ap_fail(c, r, "history push");
     }
     if (st.d_energy && st.d_forces)
-        if ((r = polarization_energy_forces(c, st.d_mu, st.d_energy, st.d_forces))) return r;
+        if ((r = polarization_energy_forces(c, st.d_mu, st.d_energy, st.d_forces, st.d_virial))) return r;
     return AP_OK;
 }
 

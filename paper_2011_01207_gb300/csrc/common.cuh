@@ -157,6 +157,8 @@ struct ap_ctx {
     double *red = nullptr;    // small reduction scratch
     double *mu_s = nullptr;   // [3][n_pad] dipoles given to the force call (sorted)
     double *gbuf = nullptr;   // [30][n_pad] PME potential derivatives for the forces
+    void *cgrid_v = nullptr;  // complex [Kz][Ky][Kx/2+1]: transform of the permanent potential (virial)
+    double *vir_active = nullptr;   // virial accumulator of the force call in progress (or NULL)
     float *mlp_feat = nullptr;   // [n_pad][16] learned-guess features (slot order)
     float *mlp_y = nullptr;      // [n_pad][3] network outputs (slot order)
 
@@ -262,11 +264,20 @@ int real_matvec2_launch(ap_ctx *ctx, const void *p0, const void *p1, double *acc
 int field_finish(ap_ctx *ctx, double *d_field_out);
 int pcg_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double *d_mu,
               ap_solve_info *info);
-int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces);
+// energy, forces and (d_virial non-NULL) the virial [9] at caller-order dipoles d_mu
+int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces, double *d_virial);
+// the same with extra terms before the frame chain rule; vir: a virial accumulator (virial_acc) or NULL
 int forces_run_ex(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces,
-                  int (*extra)(ap_ctx *, cudaStream_t));   // extra terms before the frame chain rule
+                  int (*extra)(ap_ctx *, cudaStream_t), double *vir);
+// forces of -(f/2) mu.T mu alone (mz: zeroed multipoles); vir as above
 int mutual_forces_run(ap_ctx *ctx, const double *d_mu, void *const *mz, double *gd, double *gq,
-                      double *d_forces);   // forces of -(f/2) mu.T mu alone (mz: zeroed multipoles)
+                      double *d_forces, double *vir);
+double *virial_acc(ap_ctx *ctx, int which);   // nine device slots: 0 a force call, 1 the mutual pass
+int virial_out(ap_ctx *ctx, const double *a, const double *b, double *d_virial);   // a - b -> FP64 [9]
+// smooth-PME potential derivatives for the forces; with vir non-NULL also the structure-factor
+// share of the virial (permanent-induced and induced-induced, or induced-induced alone for _mu)
+int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s, double *vir);
+int pme_forces_derivs_mu(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s, double *vir);
 int diis_solve(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, int depth, double *d_mu,
                ap_solve_info *info);
 void diis_release(ap_ctx *ctx);
@@ -275,7 +286,8 @@ int dp_set_pairs(ap_ctx *ctx, int n_pairs, const int *d_pairs, const double *d_s
 int dp_fields(ap_ctx *ctx, double *d_field_d, double *d_field_p);
 int dp_solve(ap_ctx *ctx, const double *gd, const double *gp, double tol, int max_iter, double *d_mu_d,
              double *d_mu_p, ap_solve_info *info);
-int dp_forces(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d_energy, double *d_forces);
+int dp_forces(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d_energy, double *d_forces,
+              double *d_virial);
 int dp_info(ap_ctx *ctx, ap_solve_info *info);
 int dp_matvec2_launch(ap_ctx *ctx, cudaStream_t s, int clear);
 void dp_release(ap_ctx *ctx);

@@ -26,6 +26,8 @@
 // multipole-orientation (frame) terms.
 #include "common.cuh"
 
+#include <type_traits>
+
 #include <cmath>
 #include <cstdlib>
 
@@ -679,19 +681,37 @@ __global__ void k_dp_force_combine(const double *__restrict__ ft, int n3, double
     out[k] -= ft[k];
 }
 
-// gradient of -(f/2) sum over listed ordered pairs (I, J) of w . F_lambda(R; M_J) with
-// w = sigma_d mu_p,I + sigma_p mu_d,I: force on I and J, dU/d(global dipole) and
-// dU/d(global quadrupole) of J (one thread per unordered pair, both orders)
+// adds v[0..8] of every thread of a block of NT threads to acc[0..8] (FP64 atomics, or
+// integer atomics for values already in fixed point)
+template <int NT, class V>
+__device__ __forceinline__ void block_add9_dp(V *v, double *acc) {
+    __shared__ V sm[NT / 32][9];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int e = 0; e < 9; ++e) {
+        V x = v[e];
+        for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (l == 0) sm[w][e] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        V t = 0;
+        for (int e = 0; e < NT / 32; ++e) t += sm[e][threadIdx.x];
+        if constexpr (std::is_integral<V>::value)
+            atomicAdd(reinterpret_cast<unsigned long long *>(acc) + threadIdx.x, (unsigned long long)t);
+        else
+            atomicAdd(acc + threadIdx.x, t);
+    }
+}
+
+// one listed pair k of k_listed_forces; v (optional) receives its virial
 template <class T>
-__global__ void k_listed_forces(const int2 *__restrict__ pairs, const double2 *__restrict__ scales, int m,
-                                const int *__restrict__ iperm, const typename V4<T>::type *__restrict__ posq,
-                                const typename V4<T>::type *__restrict__ dipd,
-                                const typename V4<T>::type *__restrict__ quad0,
-                                const typename V4<T>::type *__restrict__ quad1, const float4 *__restrict__ bcenter,
-                                double3 L, double3 iL, double rc2, double thole_a, const double *__restrict__ mus,
-                                int n_pad, double f, double *__restrict__ frc, double *__restrict__ gdip,
-                                double *__restrict__ gquad, int fixed) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void listed_pair_forces(
+    const int2 *__restrict__ pairs, const double2 *__restrict__ scales, int m, const int *__restrict__ iperm,
+    const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
+    const typename V4<T>::type *__restrict__ quad0, const typename V4<T>::type *__restrict__ quad1,
+    const float4 *__restrict__ bcenter, double3 L, double3 iL, double rc2, double thole_a,
+    const double *__restrict__ mus, int n_pad, double f, double *__restrict__ frc, double *__restrict__ gdip,
+    double *__restrict__ gquad, int fixed, int k, double *v) {
     if (k >= m) return;
     const int2 pr = pairs[k];
     const double2 sc = scales[k];
@@ -729,6 +749,9 @@ __global__ void k_listed_forces(const int2 *__restrict__ pairs, const double2 *_
                  + (2.0 / 3.0) * Rn[2] * (R[c] * QRw + qr[c] * wR) + (RQR / 3.0) * Rn[2] * w[c]
                  - (RQR / 3.0) * Rn[3] * R[c] * wR;
         // dU/dR = -h g: force +h g on I, -h g on J
+        if (v)
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) v[3 * a + c] += -h * g[a] * R[c];
         for (int c = 0; c < 3; ++c) {
             add_acc(frc, (size_t)c * n_pad + I, h * g[c], fixed);
             add_acc(frc, (size_t)c * n_pad + J, -h * g[c], fixed);
@@ -743,6 +766,35 @@ __global__ void k_listed_forces(const int2 *__restrict__ pairs, const double2 *_
     }
 }
 
+// gradient of -(f/2) sum over listed ordered pairs (I, J) of w . F_lambda(R; M_J) with
+// w = sigma_d mu_p,I + sigma_p mu_d,I: force on I and J, dU/d(global dipole) and
+// dU/d(global quadrupole) of J (one thread per unordered pair, both orders); with vir
+// non-NULL (blocks of 128 threads) also the pairs' virial, sum of (dU/dR) R^T
+template <class T>
+__global__ void k_listed_forces(const int2 *__restrict__ pairs, const double2 *__restrict__ scales, int m,
+                                const int *__restrict__ iperm, const typename V4<T>::type *__restrict__ posq,
+                                const typename V4<T>::type *__restrict__ dipd,
+                                const typename V4<T>::type *__restrict__ quad0,
+                                const typename V4<T>::type *__restrict__ quad1, const float4 *__restrict__ bcenter,
+                                double3 L, double3 iL, double rc2, double thole_a, const double *__restrict__ mus,
+                                int n_pad, double f, double *__restrict__ frc, double *__restrict__ gdip,
+                                double *__restrict__ gquad, int fixed, double *__restrict__ vir) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    listed_pair_forces<T>(pairs, scales, m, iperm, posq, dipd, quad0, quad1, bcenter, L, iL, rc2, thole_a, mus, n_pad,
+                          f, frc, gdip, gquad, fixed, k, vir ? v : nullptr);
+    if (vir) {   // uniform over the launch
+        if (fixed) {
+            long long vf[9];
+            for (int e = 0; e < 9; ++e) vf[e] = ap_to_fx(v[e]);
+            block_add9_dp<128>(vf, vir);
+        } else {
+            block_add9_dp<128>(v, vir);
+        }
+    }
+}
+
+
 template <class T>
 int listed_forces_t(ap_ctx *ctx, cudaStream_t s) {
     typedef typename V4<T>::type T4;
@@ -753,7 +805,7 @@ int listed_forces_t(ap_ctx *ctx, cudaStream_t s) {
         B->pairs, B->scales, B->n_pairs, ctx->iperm, (const T4 *)ctx->posq, (const T4 *)ctx->dipd,
         (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, ctx->bcenter, make_double3(P.box[0], P.box[1], P.box[2]),
         make_double3(1.0 / P.box[0], 1.0 / P.box[1], 1.0 / P.box[2]), P.cutoff * P.cutoff, P.thole_a, B->mus,
-        ctx->n_pad, AP_COULOMB, ctx->frc, ctx->gdip, ctx->gquad, ctx->fixed);
+        ctx->n_pad, AP_COULOMB, ctx->frc, ctx->gdip, ctx->gquad, ctx->fixed, ctx->vir_active);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -878,7 +930,8 @@ int dp_solve(ap_ctx *ctx, const double *gd, const double *gp, double tol, int ma
                                 : solve_t<float>(ctx, gd, gp, tol, max_iter, d_mu_d, d_mu_p, info);
 }
 
-int dp_forces(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d_energy, double *d_forces) {
+int dp_forces(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d_energy, double *d_forces,
+              double *d_virial) {
     if (!ctx->dp || !dpb(ctx)->field_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field_dp() must come first");
     DpBuffers *B = dpb(ctx);
     cudaStream_t s = ctx->s0;
@@ -903,10 +956,14 @@ int dp_forces(ap_ctx *ctx, const double *d_mu_d, const double *d_mu_p, double *d
             (const V4<float>::type *)ctx->quad1, ctx->n_pad, (V4<float>::type *)B->mz);
     AP_CUDA(cudaGetLastError());
     int r;
-    if ((r = mutual_forces_run(ctx, dl, mz, B->gsc, B->gsc + (size_t)3 * ctx->n_pad, ft))) return r;
-    if ((r = forces_run_ex(ctx, mu_s, B->e_scr, d_forces, listed_forces))) return r;
+    // the virial splits as the forces do: single-set terms at mu_s (with the listed pairs) minus
+    // the mutual term of delta
+    double *v1 = d_virial ? virial_acc(ctx, 0) : nullptr, *v2 = d_virial ? virial_acc(ctx, 1) : nullptr;
+    if ((r = mutual_forces_run(ctx, dl, mz, B->gsc, B->gsc + (size_t)3 * ctx->n_pad, ft, v2))) return r;
+    if ((r = forces_run_ex(ctx, mu_s, B->e_scr, d_forces, listed_forces, v1))) return r;
     k_dp_force_combine<<<ap_grid_for(n3, 256), 256, 0, s>>>(ft, n3, d_forces);
     AP_CUDA(cudaGetLastError());
+    if (d_virial && (r = virial_out(ctx, v1, v2, d_virial))) return r;
     return AP_OK;
 }
 

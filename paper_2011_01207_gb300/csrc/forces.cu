@@ -10,6 +10,15 @@
 //   frames:     global multipoles rotate with their frame atoms: dU/d(global dipole) and
 //               dU/d(global quadrupole) are chained through the frame construction.
 // Pair arithmetic in T, accumulation in FP64 as in the other real-space kernels.
+//
+// Virial (on request): V_ab = dE_pol/de_ab under x -> (I + e) x of positions and box, which
+// the paper's real-space loop updates with the energy and the forces (Sec. 1.2.1) and sums in
+// double precision (Sec. 2.2). At fixed mu it is
+//   pairs:      sum over pairs of (dU/dR)_a R_b (R the image vector);
+//   frames:     sum over frame vectors v of (dU/dv)_a v_b;
+//   reciprocal: -f sum_j [grad phi_{M+mu} mu_j^T + grad phi_mu d_j^T + (2/3) H(phi_mu) Q_j]
+//               plus the structure-factor sum of pme.cu (volume and |m| of C(m));
+// accumulated per block in FP64 (fixed point in AP_FIXED) into nine device slots.
 #include "common.cuh"
 #include "pair_math.cuh"
 
@@ -17,8 +26,6 @@
 #include <type_traits>
 
 void unsort3(ap_ctx *ctx, const double *src, double *out, cudaStream_t s);
-int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s);
-int pme_forces_derivs_mu(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s);
 
 namespace {
 
@@ -42,6 +49,31 @@ __device__ __forceinline__ void add_plain(double *arr, size_t k, double v, int f
         reinterpret_cast<long long *>(arr)[k] += ap_to_fx(v);
     else
         arr[k] += v;
+}
+
+// adds the nine values v of every thread of a block of NT threads to acc[0..8]: FP64 sums
+// and FP64 atomics, or (FX) values already in fixed point, integer sums and integer atomics
+// (order-independent, so bitwise reproducible)
+template <int NT, class V>
+__device__ __forceinline__ void block_add9(V *v, double *acc) {
+    __shared__ V sm[NT / 32][9];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        V x = v[k];
+        for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (l == 0) sm[w][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        V t = 0;
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) t += sm[k][threadIdx.x];
+        if constexpr (std::is_integral<V>::value)
+            atomicAdd(reinterpret_cast<unsigned long long *>(acc) + threadIdx.x, (unsigned long long)t);
+        else
+            atomicAdd(acc + threadIdx.x, t);
+    }
 }
 
 // out_a = sum_b mu_b dE_b/dR_a for the field E(R) of a multipole (q, d, Q) at the origin
@@ -92,13 +124,19 @@ struct FoSmem {
 template <class T>
 constexpr int fo_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
-template <class T, bool MINIMG, bool FX>
-__global__ void __launch_bounds__(128, 6) k_pair_forces(
+// VIR: also the pairs' virial. Without per-pair minimum image every position of an item is
+// relative to block I's origin, and the item holds both sides of each of its pairs, whose
+// forces are opposite; so the item's sum over pairs of (dU/dR) R^T = -sum over sides of
+// F_t R^T / 2 equals -sum over its 64 targets of F_t x_t^T, formed once per item from the
+// per-target sums the kernel keeps anyway. With per-pair minimum image (small boxes) the
+// sides' F R^T are summed as they come.
+template <class T, bool MINIMG, bool FX, bool VIR>
+__global__ void __launch_bounds__(128, VIR ? 4 : 6) k_pair_forces(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq,
     const typename V4<T>::type *__restrict__ dipd, const typename V4<T>::type *__restrict__ quad0,
     const typename V4<T>::type *__restrict__ quad1, const typename V4<T>::type *__restrict__ muv,
     double *__restrict__ frc, double *__restrict__ gdip, double *__restrict__ gquad, int n_pad, PairConsts<T> pc,
-    double fconst) {
+    double fconst, double *__restrict__ vir) {
     typedef typename V4<T>::type T4;
     typedef PairAcc<T, FX> PA;
     __shared__ FoSmem<T, typename PA::shared_t> smem[fo_warps<T>()];
@@ -120,6 +158,9 @@ __global__ void __launch_bounds__(128, 6) k_pair_forces(
     typename PA::reg_t ai[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) ai[k] = 0;
+    typename PA::reg_t vacc[9];     // this lane's share of the virial (VIR)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) vacc[k] = 0;
     for (long t = t0; t < t1; ++t) {
         const int2 it = wa.work[t];
         __syncwarp();
@@ -194,6 +235,9 @@ __global__ void __launch_bounds__(128, 6) k_pair_forces(
         T f[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) f[k] = T(0);
+        T vs[9];                    // sum of F_side R^T over this lane's sides (VIR, MINIMG)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) vs[k] = T(0);
         while (slice.left > 0) {
             int tg, src;
             slice.next(S.words, tg, src);
@@ -244,10 +288,18 @@ __global__ void __launch_bounds__(128, 6) k_pair_forces(
             const T msr = ms[0] * dx + ms[1] * dy + ms[2] * dz;
             const T cR = Ru[1] * mts - Ru[2] * mtr * msr;
             const T R[3] = {dx, dy, dz};
+            T fs[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                f[k] += A[k] - Bv[k] + cR * R[k] + Ru[1] * (mt[k] * msr + ms[k] * mtr);
+                fs[k] = A[k] - Bv[k] + cR * R[k] + Ru[1] * (mt[k] * msr + ms[k] * mtr);
+                f[k] += fs[k];
                 f[3 + k] += -Rd[0] * ms[k] + Rd[1] * msr * R[k];
+            }
+            if constexpr (VIR && MINIMG) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) vs[3 * a + b] += fs[a] * R[b];
             }
             const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
@@ -259,6 +311,40 @@ __global__ void __launch_bounds__(128, 6) k_pair_forces(
             for (int k = 0; k < 12; ++k) PA::shared_add(&S.acc[k][cur], f[k] * scf[k]);
         }
         __syncwarp();
+        if constexpr (VIR) {
+            // in kcal/mol: each side's force is f times the kernel's sums, the pair's virial half
+            // the sum over its two sides
+            double v[9];
+            if constexpr (MINIMG) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[k] = -0.5 * fconst * (double)vs[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[k] = 0.0;
+                const bool oki = curI * 32 + lane < pc.n;          // padding slots hold NaN positions
+                const bool okj = diag ? oki : sj >= 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int tt = h ? 32 + lane : lane;
+                    if (!(h ? okj : oki)) continue;
+                    const T4 ps = S.pos[tt];
+                    const double x[3] = {(double)ps.x, (double)ps.y, (double)ps.z};
+                    double F[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        F[a] = FX ? ap_from_fx((long long)PA::to_reg(S.acc[a][tt])) : sc[a] * (double)PA::to_reg(S.acc[a][tt]);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) v[3 * a + b] -= F[a] * x[b];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                if constexpr (FX) vacc[k] += ap_to_fx(v[k]);
+                else vacc[k] += v[k];
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 12; ++k) ai[k] += FX ? PA::to_reg(S.acc[k][lane]) : sc[k] * PA::to_reg(S.acc[k][lane]);
         if (diag) {
@@ -274,19 +360,60 @@ __global__ void __launch_bounds__(128, 6) k_pair_forces(
         }
     }
     if (curI >= 0 && curI * 32 + lane < pc.n) flush12(frc, gdip, gquad, n_pad, curI * 32 + lane, ai);
+    if constexpr (VIR) block_add9<32 * fo_warps<T>()>(vacc, vir);
 }
 
 // reciprocal-space gradient and source terms per atom
 // D: phi_mu derivatives [20][n_pad] then phi_M derivatives [10][n_pad] (component order of pme.cu)
+// one atom's share of the reciprocal virial from its potential derivatives (layout of D as in
+// k_recip_forces), its induced dipole and its global multipoles
 template <class T>
+__device__ __forceinline__ void recip_atom_virial(const double *__restrict__ D, const double *__restrict__ mu,
+                                                  const typename V4<T>::type *__restrict__ dipd,
+                                                  const typename V4<T>::type *__restrict__ quad0,
+                                                  const typename V4<T>::type *__restrict__ quad1, int s, int n_pad,
+                                                  double f, double *v) {
+    typedef T C;
+    auto Du = [&](int c) { return (C)D[(size_t)c * n_pad + s]; };
+    auto DM = [&](int c) { return (C)D[(size_t)(20 + c) * n_pad + s]; };
+    const C m[3] = {(C)mu[s], (C)mu[n_pad + s], (C)mu[2 * n_pad + s]};
+    const typename V4<T>::type b = dipd[s], c = quad0[s], d = quad1[s];
+    const C dd[3] = {b.x, b.y, b.z};
+    const C Q[3][3] = {{c.x, c.y, c.z}, {c.y, c.w, d.x}, {c.z, d.x, d.y}};
+    const C Hu[3][3] = {{Du(4), Du(7), Du(8)}, {Du(7), Du(5), Du(9)}, {Du(8), Du(9), Du(6)}};
+    const C gu[3] = {Du(1), Du(2), Du(3)}, gM[3] = {DM(1), DM(2), DM(3)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const C hq = Hu[a][0] * Q[0][e] + Hu[a][1] * Q[1][e] + Hu[a][2] * Q[2][e];
+            v[3 * a + e] = -f * (double)((gM[a] + gu[a]) * m[e] + gu[a] * dd[e] + C(2.0 / 3.0) * hq);
+        }
+}
+
+// VIR (blocks of 128 threads): also the atoms' share of the reciprocal virial,
+// -f [grad phi_{M+mu} mu^T + grad phi_mu d^T + (2/3) H(phi_mu) Q]
+template <class T, bool VIR>
 __global__ void k_recip_forces(const double *__restrict__ D, const double *__restrict__ mu,
                                const typename V4<T>::type *__restrict__ posq,
                                const typename V4<T>::type *__restrict__ dipd,
                                const typename V4<T>::type *__restrict__ quad0,
                                const typename V4<T>::type *__restrict__ quad1, int n, int n_pad, double f,
                                double self_coef, double *__restrict__ frc, double *__restrict__ gdip,
-                               double *__restrict__ gquad, int fixed) {
+                               double *__restrict__ gquad, int fixed, double *__restrict__ vir) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (VIR) {
+        double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (s < n) recip_atom_virial<T>(D, mu, dipd, quad0, quad1, s, n_pad, f, v);
+        if (fixed) {
+            long long vf[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) vf[k] = ap_to_fx(v[k]);
+            block_add9<128>(vf, vir);
+        } else {
+            block_add9<128>(v, vir);
+        }
+    }
     if (s >= n) return;
     typedef T C;   // FP32 in the mixed and fixed modes (FP64 is slow on this part), FP64 in AP_FP64
     auto Du = [&](int c) { return (C)D[(size_t)c * n_pad + s]; };
@@ -329,12 +456,13 @@ __device__ __forceinline__ void cross3(const C *a, const C *b, C *o) {
 }
 
 // frame chain rule: dU/dR = G_d d_l^T + 2 G_Q R Q_l, then through the axis construction
+// the chain rule of one atom's frame: forces on the atom and its z- and x-atoms; with v
+// given, also its frame vectors' virial (dU/dv) v^T into v[0..8]
 template <class C>
-__global__ void k_frame_forces(const double *__restrict__ gdip, const double *__restrict__ gquad,
-                               const double *__restrict__ rot, const double *__restrict__ mpl,
-                               const double *__restrict__ fvec, const int *__restrict__ frame_s, int n, int n_pad,
-                               double *__restrict__ frc, int fixed) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void frame_chain(const double *__restrict__ gdip, const double *__restrict__ gquad,
+                                            const double *__restrict__ rot, const double *__restrict__ mpl,
+                                            const double *__restrict__ fvec, const int *__restrict__ frame_s, int n,
+                                            int n_pad, double *__restrict__ frc, int fixed, int s, double *vout) {
     if (s >= n) return;
     const int type = frame_s[3 * s];
     if (type != AP_FRAME_Z_THEN_X && type != AP_FRAME_BISECTOR) return;
@@ -421,6 +549,33 @@ __global__ void k_frame_forces(const double *__restrict__ gdip, const double *__
             atomicAdd(frc + a * n_pad + s, (double)g_vz[a] + (double)g_vx[a]);
         }
     }
+    if (vout) {
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                vout[3 * a + b] = (double)g_vz[a] * (double)vz[b] + (double)g_vx[a] * (double)vx[b];
+    }
+}
+
+// VIR (blocks of 128 threads): also the frames' share of the virial, sum over the frame
+// vectors v of (dU/dv) v^T
+template <class C, bool VIR>
+__global__ void k_frame_forces(const double *__restrict__ gdip, const double *__restrict__ gquad,
+                               const double *__restrict__ rot, const double *__restrict__ mpl,
+                               const double *__restrict__ fvec, const int *__restrict__ frame_s, int n, int n_pad,
+                               double *__restrict__ frc, int fixed, double *__restrict__ vir) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    frame_chain<C>(gdip, gquad, rot, mpl, fvec, frame_s, n, n_pad, frc, fixed, s, VIR ? v : nullptr);
+    if constexpr (VIR) {
+        if (fixed) {
+            long long vf[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) vf[k] = ap_to_fx(v[k]);
+            block_add9<128>(vf, vir);
+        } else {
+            block_add9<128>(v, vir);
+        }
+    }
 }
 
 template <class T>
@@ -474,10 +629,11 @@ __global__ void k_unsort3_fx(const double *__restrict__ src, int n_pad, const in
 }
 
 // the real-space force kernel over the current work items with the dipoles in ctx->p and
-// the multipoles (posq q, dipd, quad0, quad1) given, accumulating into frc, gdip and gquad
+// the multipoles (posq q, dipd, quad0, quad1) given, accumulating into frc, gdip and gquad;
+// with vir given, also the pairs' virial into vir[0..8]
 template <class T>
 int pair_forces_t(ap_ctx *ctx, cudaStream_t s, const void *posq, const void *dipd, const void *quad0,
-                  const void *quad1, double *frc, double *gdip, double *gquad) {
+                  const void *quad1, double *frc, double *gdip, double *gquad, double *vir = nullptr) {
     typedef typename V4<T>::type T4;
     PairConsts<T> pc;
     const ap_params &P = ctx->prm;
@@ -489,10 +645,16 @@ int pair_forces_t(ap_ctx *ctx, cudaStream_t s, const void *posq, const void *dip
     pc.rc2 = (T)(P.cutoff * P.cutoff);
     for (int dd = 0; dd < 3; ++dd) { pc.L[dd] = (T)P.box[dd]; pc.iL[dd] = (T)(1.0 / P.box[dd]); }
     pc.n = ctx->n;
-    auto kern = ctx->fixed ? (ctx->minimg ? k_pair_forces<T, true, true> : k_pair_forces<T, false, true>)
-                           : (ctx->minimg ? k_pair_forces<T, true, false> : k_pair_forces<T, false, false>);
-    static int grids[4] = {0, 0, 0, 0};
-    int &grid = grids[ctx->minimg + 2 * ctx->fixed];
+    typedef void (*Kern)(WorkArgs, const T4 *, const T4 *, const T4 *, const T4 *, const T4 *, double *, double *,
+                         double *, int, PairConsts<T>, double, double *);
+    static const Kern kerns[8] = {k_pair_forces<T, false, false, false>, k_pair_forces<T, true, false, false>,
+                                  k_pair_forces<T, false, true, false>,  k_pair_forces<T, true, true, false>,
+                                  k_pair_forces<T, false, false, true>,  k_pair_forces<T, true, false, true>,
+                                  k_pair_forces<T, false, true, true>,   k_pair_forces<T, true, true, true>};
+    const int which = ctx->minimg + 2 * ctx->fixed + 4 * (vir ? 1 : 0);
+    const Kern kern = kerns[which];
+    static int grids[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int &grid = grids[which];
     if (!grid) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * fo_warps<T>(), 0);
@@ -500,28 +662,31 @@ int pair_forces_t(ap_ctx *ctx, cudaStream_t s, const void *posq, const void *dip
     }
     kern<<<grid, 32 * fo_warps<T>(), 0, s>>>(work_args(ctx), (const T4 *)posq, (const T4 *)dipd,
                                             (const T4 *)quad0, (const T4 *)quad1, (const T4 *)ctx->p,
-                                            frc, gdip, gquad, ctx->n_pad, pc, AP_COULOMB);
+                                            frc, gdip, gquad, ctx->n_pad, pc, AP_COULOMB, vir);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
 
 // `extra`, if given, runs on the force stream after the pair and reciprocal terms and before
-// the frame chain rule: it may add to ctx->frc, ctx->gdip and ctx->gquad
+// the frame chain rule: it may add to ctx->frc, ctx->gdip and ctx->gquad (and, while
+// ctx->vir_active is set, to that virial accumulator). vir: nine device slots (FP64, or fixed
+// point in AP_FIXED) cleared here and accumulating the virial, or NULL.
 template <class T>
 int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces,
-             int (*extra)(ap_ctx *, cudaStream_t)) {
+             int (*extra)(ap_ctx *, cudaStream_t), double *vir) {
     typedef typename V4<T>::type T4;
     cudaStream_t s = ctx->s0;
     const int n = ctx->n, n_pad = ctx->n_pad;
     const double f = AP_COULOMB;
     const double self_coef = 4.0 * std::pow(ctx->prm.ewald_beta, 3) / (3.0 * AP_SQRT_PI);
+    if (vir) AP_CUDA(cudaMemsetAsync(vir, 0, sizeof(double) * 9, s));
     k_mu_load<T><<<ap_grid_for(n_pad, 256), 256, 0, s>>>(d_mu, ctx->perm, n, n_pad, ctx->mu_s, (T4 *)ctx->p);
     // reciprocal-space potential derivatives on the second stream, concurrent with the
     // energy and the real-space pair forces (they write only gbuf and the grid); joined
     // before the kernels that update the force arrays per atom
     AP_CUDA(cudaEventRecord(ctx->ev_fork, s));
     AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
-    int rc = pme_forces_derivs(ctx, ctx->p, ctx->gbuf, ctx->s1);
+    int rc = pme_forces_derivs(ctx, ctx->p, ctx->gbuf, ctx->s1, vir);
     if (rc) return rc;
     AP_CUDA(cudaMemsetAsync(ctx->frc, 0, sizeof(double) * 3 * n_pad, s));
     AP_CUDA(cudaMemsetAsync(ctx->gdip, 0, sizeof(double) * 3 * n_pad, s));
@@ -529,18 +694,22 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
     AP_CUDA(cudaMemsetAsync(ctx->red + 8, 0, sizeof(double), s));
     // energy
     k_energy<<<ap_grid_for(n_pad, 256), 256, 0, s>>>(ctx->mu_s, ctx->E, n_pad, -0.5 * f, ctx->red + 8, ctx->fixed);
-    rc = pair_forces_t<T>(ctx, s, ctx->posq, ctx->dipd, ctx->quad0, ctx->quad1, ctx->frc, ctx->gdip, ctx->gquad);
+    rc = pair_forces_t<T>(ctx, s, ctx->posq, ctx->dipd, ctx->quad0, ctx->quad1, ctx->frc, ctx->gdip, ctx->gquad, vir);
     if (rc) return rc;
     AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));
     AP_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
-    k_recip_forces<T><<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gbuf, ctx->mu_s, (const T4 *)ctx->posq,
-                                                         (const T4 *)ctx->dipd, (const T4 *)ctx->quad0,
-                                                         (const T4 *)ctx->quad1, n, n_pad, f, self_coef, ctx->frc,
-                                                         ctx->gdip, ctx->gquad, ctx->fixed);
+    auto krec = vir ? k_recip_forces<T, true> : k_recip_forces<T, false>;
+    krec<<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gbuf, ctx->mu_s, (const T4 *)ctx->posq, (const T4 *)ctx->dipd,
+                                            (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, n, n_pad, f, self_coef,
+                                            ctx->frc, ctx->gdip, ctx->gquad, ctx->fixed, vir);
     AP_CUDA(cudaGetLastError());
-    if (extra && (rc = extra(ctx, s))) return rc;
-    k_frame_forces<T><<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gdip, ctx->gquad, ctx->rot, ctx->mpl, ctx->fvec,
-                                                       ctx->frame_s, n, n_pad, ctx->frc, ctx->fixed);
+    ctx->vir_active = vir;
+    rc = extra ? extra(ctx, s) : AP_OK;
+    ctx->vir_active = nullptr;
+    if (rc) return rc;
+    auto kfr = vir ? k_frame_forces<T, true> : k_frame_forces<T, false>;
+    kfr<<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gdip, ctx->gquad, ctx->rot, ctx->mpl, ctx->fvec, ctx->frame_s, n,
+                                           n_pad, ctx->frc, ctx->fixed, vir);
     AP_CUDA(cudaGetLastError());
     if (ctx->fixed) {
         k_unsort3_fx<<<ap_grid_for(n, 256), 256, 0, s>>>(ctx->frc, n_pad, ctx->iperm, n, d_forces);
@@ -557,29 +726,32 @@ int forces_t(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces
 // single-set force path with the permanent multipoles replaced by zeros (mz: posq, dipd,
 // quad0, quad1 with q, d and Q zero, positions and Thole factors kept) and without the
 // permanent potential's reciprocal part or the frame chain rule. gd, gq: scratch for the
-// dipole and quadrupole derivatives the kernels also write (not used).
+// dipole and quadrupole derivatives the kernels also write (not used). vir: as in forces_t.
 template <class T>
-int mutual_forces_t(ap_ctx *ctx, const double *d_mu, void *const *mz, double *gd, double *gq, double *d_forces) {
+int mutual_forces_t(ap_ctx *ctx, const double *d_mu, void *const *mz, double *gd, double *gq, double *d_forces,
+                    double *vir) {
     typedef typename V4<T>::type T4;
     cudaStream_t s = ctx->s0;
     const int n = ctx->n, n_pad = ctx->n_pad;
     const double f = AP_COULOMB;
     const double self_coef = 4.0 * std::pow(ctx->prm.ewald_beta, 3) / (3.0 * AP_SQRT_PI);
+    if (vir) AP_CUDA(cudaMemsetAsync(vir, 0, sizeof(double) * 9, s));
     k_mu_load<T><<<ap_grid_for(n_pad, 256), 256, 0, s>>>(d_mu, ctx->perm, n, n_pad, ctx->mu_s, (T4 *)ctx->p);
     AP_CUDA(cudaMemsetAsync(ctx->frc, 0, sizeof(double) * 3 * n_pad, s));
     AP_CUDA(cudaMemsetAsync(gd, 0, sizeof(double) * 3 * n_pad, s));
     AP_CUDA(cudaMemsetAsync(gq, 0, sizeof(double) * 6 * n_pad, s));
     AP_CUDA(cudaEventRecord(ctx->ev_fork, s));
     AP_CUDA(cudaStreamWaitEvent(ctx->s1, ctx->ev_fork, 0));
-    int rc = pme_forces_derivs_mu(ctx, ctx->p, ctx->gbuf, ctx->s1);
+    int rc = pme_forces_derivs_mu(ctx, ctx->p, ctx->gbuf, ctx->s1, vir);
     if (rc) return rc;
-    rc = pair_forces_t<T>(ctx, s, mz[0], mz[1], mz[2], mz[3], ctx->frc, gd, gq);
+    rc = pair_forces_t<T>(ctx, s, mz[0], mz[1], mz[2], mz[3], ctx->frc, gd, gq, vir);
     if (rc) return rc;
     AP_CUDA(cudaEventRecord(ctx->ev_join, ctx->s1));
     AP_CUDA(cudaStreamWaitEvent(s, ctx->ev_join, 0));
-    k_recip_forces<T><<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gbuf, ctx->mu_s, (const T4 *)mz[0], (const T4 *)mz[1],
-                                                         (const T4 *)mz[2], (const T4 *)mz[3], n, n_pad, f, self_coef,
-                                                         ctx->frc, gd, gq, ctx->fixed);
+    auto krec = vir ? k_recip_forces<T, true> : k_recip_forces<T, false>;
+    krec<<<ap_grid_for(n, 128), 128, 0, s>>>(ctx->gbuf, ctx->mu_s, (const T4 *)mz[0], (const T4 *)mz[1],
+                                            (const T4 *)mz[2], (const T4 *)mz[3], n, n_pad, f, self_coef, ctx->frc,
+                                            gd, gq, ctx->fixed, vir);
     AP_CUDA(cudaGetLastError());
     if (ctx->fixed)
         k_unsort3_fx<<<ap_grid_for(n, 256), 256, 0, s>>>(ctx->frc, n_pad, ctx->iperm, n, d_forces);
@@ -587,6 +759,17 @@ int mutual_forces_t(ap_ctx *ctx, const double *d_mu, void *const *mz, double *gd
         unsort3(ctx, ctx->frc, d_forces, s);
     AP_CUDA(cudaGetLastError());
     return AP_OK;
+}
+
+// d_out[0..8] = value(a) - value(b) (b optional) of two virial accumulators in FP64 or (fixed)
+// fixed point
+__global__ void k_virial_out(const double *__restrict__ a, const double *__restrict__ b, int fixed,
+                             double *__restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= 9) return;
+    double v = acc_value(a, k, fixed);
+    if (b) v -= acc_value(b, k, fixed);
+    out[k] = v;
 }
 
 }  // namespace
@@ -599,18 +782,32 @@ int pair_forces_launch(ap_ctx *ctx, cudaStream_t s) {
                                       ctx->gquad);
 }
 
-int mutual_forces_run(ap_ctx *ctx, const double *d_mu, void *const *mz, double *gd, double *gq, double *d_forces) {
-    return ctx->prec == AP_FP64 ? mutual_forces_t<double>(ctx, d_mu, mz, gd, gq, d_forces)
-                                : mutual_forces_t<float>(ctx, d_mu, mz, gd, gq, d_forces);
+int mutual_forces_run(ap_ctx *ctx, const double *d_mu, void *const *mz, double *gd, double *gq, double *d_forces,
+                      double *vir) {
+    return ctx->prec == AP_FP64 ? mutual_forces_t<double>(ctx, d_mu, mz, gd, gq, d_forces, vir)
+                                : mutual_forces_t<float>(ctx, d_mu, mz, gd, gq, d_forces, vir);
 }
 
-int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces) {
-    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, d_mu, d_energy, d_forces, nullptr)
-                                : forces_t<float>(ctx, d_mu, d_energy, d_forces, nullptr);
+// the virial accumulators: slots 16..24 of the context's reduction scratch for a force call,
+// 32..40 for the mutual pass of the two-set forces
+double *virial_acc(ap_ctx *ctx, int which) { return ctx->red + (which ? 32 : 16); }
+
+int virial_out(ap_ctx *ctx, const double *a, const double *b, double *d_virial) {
+    k_virial_out<<<1, 32, 0, ctx->s0>>>(a, b, ctx->fixed, d_virial);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
+int forces_run(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces, double *d_virial) {
+    double *vir = d_virial ? virial_acc(ctx, 0) : nullptr;
+    const int rc = ctx->prec == AP_FP64 ? forces_t<double>(ctx, d_mu, d_energy, d_forces, nullptr, vir)
+                                        : forces_t<float>(ctx, d_mu, d_energy, d_forces, nullptr, vir);
+    if (rc || !d_virial) return rc;
+    return virial_out(ctx, vir, nullptr, d_virial);
 }
 
 int forces_run_ex(ap_ctx *ctx, const double *d_mu, double *d_energy, double *d_forces,
-                  int (*extra)(ap_ctx *, cudaStream_t)) {
-    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, d_mu, d_energy, d_forces, extra)
-                                : forces_t<float>(ctx, d_mu, d_energy, d_forces, extra);
+                  int (*extra)(ap_ctx *, cudaStream_t), double *vir) {
+    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, d_mu, d_energy, d_forces, extra, vir)
+                                : forces_t<float>(ctx, d_mu, d_energy, d_forces, extra, vir);
 }

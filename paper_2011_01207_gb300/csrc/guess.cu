@@ -133,6 +133,16 @@ __global__ void k_hist_push3(long m, const double *__restrict__ g, const double 
     if (i == 0) *count = min(*count + 1, 3);
 }
 
+// mu0 (caller order) = alpha E from the sorted slots
+__global__ void k_direct_guess(const double *__restrict__ E, const double *__restrict__ alpha,
+                               const int *__restrict__ iperm, int n, int n_pad, double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = iperm[i];
+    const double a = alpha[s];
+    for (int c = 0; c < 3; ++c) out[3 * i + c] = a * E[(size_t)c * n_pad + s];
+}
+
 }  // namespace
 
 // adaptive guess from the three-level history (layout of ap_batch_step.d_hist_lsq)
@@ -184,4 +194,14 @@ extern "C" int ap_adaptive_guess(int n, const double *d_base, const double *d_mu
     k_adaptive_apply<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, d_base, d_mu1, d_base1, d_mu2, d_base2, d_scratch,
                                                                   d_out, nullptr);
     return cudaGetLastError() == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+}
+
+extern "C" int ap_direct_guess(ap_ctx *ctx, double *d_mu0) {
+    if (!ctx || !d_mu0) return AP_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
+    k_direct_guess<<<ap_grid_for(ctx->n, 256), 256, 0, ctx->s0>>>(ctx->E, ctx->alpha, ctx->iperm, ctx->n, ctx->n_pad,
+                                                                  d_mu0);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
 }

@@ -479,17 +479,117 @@ int dipole_field_t(ap_ctx *ctx, const void *p, void *rec_out, const PmeBufs &bf,
     return AP_OK;
 }
 
-// forces: phi_mu derivatives (20 comps, into gbuf[0..19]) and phi_M second derivatives
-// (components 4..9, into gbuf[20..25]); the spread of mu uses ctx->p as scratch.
+// Structure-factor share of the virial. A homogeneous strain leaves the B-spline moduli and
+// the fractional coordinates unchanged and moves only the volume and the Cartesian m of C(m),
+// so the reciprocal energy's strain derivative at fixed global multipoles holds
+//   f sum_m B(m) C(m) Re[S_mu conj S_M + |S_mu|^2 / 2] K(m),
+//   K(m)_ab = -delta_ab + 2 (1/|m|^2 + pi^2/beta^2) m_a m_b,
+// with S_X the transform of X's spread grid (the potential-derivative terms are per atom, in
+// the force kernel). The permanent part is read off the permanent potential:
+// R2C[phi_M] = K^3 B C S_M (unnormalised inverse). The sum runs over the half spectrum:
+// points with kx = 0 or kx = Kx/2 (Kx even) stand for themselves, the others for their
+// conjugate partner too, weight 2; where exactly one of the two components of an
+// off-diagonal m_a m_b sits at a Nyquist index (y or z), the aliased m of the partner keeps
+// that component and flips the other, so the pair's products cancel (weight 0).
+// One block of 256 threads per 256 points, FP64 sums, nine atomics per block (fixed point in
+// AP_FIXED: per-block sums converted and added as integers; the launch shape depends on the
+// grid only, so the result is reproducible).
 template <class T>
-int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, int with_M, cudaStream_t s) {
+__global__ void k_virial_sf(const typename FftTypes<T>::cplx *__restrict__ Fmu,
+                            const typename FftTypes<T>::cplx *__restrict__ Phi, const T *__restrict__ green,
+                            int Kx, int Ky, int Kz, double iLx, double iLy, double iLz, double pib2,
+                            double inv_k3, double f, size_t m, double *__restrict__ acc, int fixed) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (idx < m) {
+        const int hx = Kx / 2 + 1;
+        const int ix = (int)(idx % hx);
+        const int iy = (int)((idx / hx) % Ky);
+        const int iz = (int)(idx / ((size_t)hx * Ky));
+        const int kx = ix < (Kx + 1) / 2 ? ix : ix - Kx;
+        const int ky = iy < (Ky + 1) / 2 ? iy : iy - Ky;
+        const int kz = iz < (Kz + 1) / 2 ? iz : iz - Kz;
+        const double mv[3] = {kx * iLx, ky * iLy, kz * iLz};
+        const double m2 = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
+        if (m2 > 0.0) {
+            const double fr = (double)Fmu[idx].x, fi = (double)Fmu[idx].y;
+            double w = 0.5 * (double)green[idx] * (fr * fr + fi * fi);
+            if (Phi) w += (fr * (double)Phi[idx].x + fi * (double)Phi[idx].y) * inv_k3;
+            const bool edge = ix == 0 || (Kx % 2 == 0 && ix == Kx / 2);
+            const double wt = edge ? 1.0 : 2.0;
+            const bool nyq[3] = {Kx % 2 == 0 && ix == Kx / 2, Ky % 2 == 0 && iy == Ky / 2,
+                                 Kz % 2 == 0 && iz == Kz / 2};
+            const double c = 2.0 * (1.0 / m2 + pib2);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    double wab = wt;
+                    if (a != b && !edge && (nyq[a] != nyq[b])) wab = 0.0;
+                    v[3 * a + b] = f * wab * w * ((a == b ? -1.0 : 0.0) + c * mv[a] * mv[b]);
+                }
+        }
+    }
+    // block reduction: warps, then nine atomics
+    __shared__ double sm[8][9];
+    const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        double x = v[k];
+        for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (l == 0) sm[wp][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += sm[k][threadIdx.x];
+        if (fixed)
+            atomicAdd(reinterpret_cast<unsigned long long *>(acc) + threadIdx.x, (unsigned long long)ap_to_fx(t));
+        else
+            atomicAdd(acc + threadIdx.x, t);
+    }
+}
+
+// forces: phi_mu derivatives (20 comps, into gbuf[0..19]) and phi_M second derivatives
+// (components 4..9, into gbuf[20..25]); the spread of mu uses ctx->p as scratch. With vir
+// given, the structure-factor share of the virial is added to it between the forward
+// transform and the convolution (with_M: the permanent-induced and induced-induced terms;
+// otherwise the induced-induced term alone).
+template <class T>
+int forces_t(ap_ctx *ctx, const void *mu4, double *gbuf, int with_M, cudaStream_t s, double *vir) {
     typedef typename V4<T>::type T4;
+    typedef typename FftTypes<T>::cplx C;
     PmeConsts<T> pc = pme_consts<T>(ctx);
     const PmeBufs bf = own_bufs(ctx);
     int r = spread_t<T>(ctx, bf, mu4, false, s);
     if (r) return r;
-    r = fft_roundtrip<T>(ctx, bf, (T *)ctx->grid, (T *)ctx->grid, s);
-    if (r) return r;
+    if (!vir) {
+        r = fft_roundtrip<T>(ctx, bf, (T *)ctx->grid, (T *)ctx->grid, s);
+        if (r) return r;
+    } else {
+        const bool dbl = sizeof(T) == 8;
+        AP_CUFFT(cufftSetStream(bf.r2c, s));
+        AP_CUFFT(cufftSetStream(bf.c2r, s));
+        if (dbl) AP_CUFFT(cufftExecD2Z(bf.r2c, (cufftDoubleReal *)ctx->grid, (cufftDoubleComplex *)ctx->cgrid));
+        else AP_CUFFT(cufftExecR2C(bf.r2c, (cufftReal *)ctx->grid, (cufftComplex *)ctx->cgrid));
+        if (with_M) {
+            // the permanent potential, copied so that its grid stays untouched for later calls
+            AP_CUDA(cudaMemcpyAsync(ctx->grid, ctx->grid2, sizeof(T) * ctx->ngrid, cudaMemcpyDeviceToDevice, s));
+            if (dbl) AP_CUFFT(cufftExecD2Z(bf.r2c, (cufftDoubleReal *)ctx->grid, (cufftDoubleComplex *)ctx->cgrid_v));
+            else AP_CUFFT(cufftExecR2C(bf.r2c, (cufftReal *)ctx->grid, (cufftComplex *)ctx->cgrid_v));
+        }
+        const ap_params &P = ctx->prm;
+        const double k3 = (double)ctx->K[0] * ctx->K[1] * ctx->K[2];
+        k_virial_sf<T><<<ap_grid_for((long)ctx->ncgrid, 256), 256, 0, s>>>(
+            (const C *)ctx->cgrid, with_M ? (const C *)ctx->cgrid_v : nullptr, (const T *)ctx->green, ctx->K[0],
+            ctx->K[1], ctx->K[2], 1.0 / P.box[0], 1.0 / P.box[1], 1.0 / P.box[2],
+            M_PI * M_PI / (P.ewald_beta * P.ewald_beta), 1.0 / k3, AP_COULOMB, ctx->ncgrid, vir, ctx->fixed);
+        k_convolve<T><<<ap_grid_for((long)ctx->ncgrid, 256), 256, 0, s>>>((C *)ctx->cgrid, (const T *)ctx->green,
+                                                                         ctx->ncgrid);
+        AP_CUDA(cudaGetLastError());
+        if (dbl) AP_CUFFT(cufftExecZ2D(bf.c2r, (cufftDoubleComplex *)ctx->cgrid, (cufftDoubleReal *)ctx->grid));
+        else AP_CUFFT(cufftExecC2R(bf.c2r, (cufftComplex *)ctx->cgrid, (cufftReal *)ctx->grid));
+    }
     k_gather_derivs<T><<<ap_grid_for(ctx->n, 128), 128, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid,
                                                                gbuf, ctx->n_pad, 20, pc);
     if (with_M)
@@ -576,11 +676,13 @@ void pme_bufs_destroy(PmeBufs *b) {
     *b = PmeBufs();
 }
 
-int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
-    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, mu4, gbuf, 1, s) : forces_t<float>(ctx, mu4, gbuf, 1, s);
+int pme_forces_derivs(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s, double *vir) {
+    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, mu4, gbuf, 1, s, vir)
+                                : forces_t<float>(ctx, mu4, gbuf, 1, s, vir);
 }
 
 // the dipoles' potential derivatives only (the permanent multipoles' part left zero)
-int pme_forces_derivs_mu(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s) {
-    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, mu4, gbuf, 0, s) : forces_t<float>(ctx, mu4, gbuf, 0, s);
+int pme_forces_derivs_mu(ap_ctx *ctx, const void *mu4, double *gbuf, cudaStream_t s, double *vir) {
+    return ctx->prec == AP_FP64 ? forces_t<double>(ctx, mu4, gbuf, 0, s, vir)
+                                : forces_t<float>(ctx, mu4, gbuf, 0, s, vir);
 }

@@ -57,9 +57,9 @@ def test_null_context_calls_return_arg_error(lib):
     assert L.build_neighbour_blocks(None, None, None, None, 0) == -1
     assert L.permanent_field(None, None, None, None, None, None) == -1
     assert L.induced_dipoles_pcg(None, None, 1e-5, 10, None, None) == -1
-    assert L.polarization_energy_forces(None, None, None, None) == -1
+    assert L.polarization_energy_forces(None, None, None, None, None) == -1
     assert L.induced_dipoles_diis(None, None, 1e-5, 10, 6, None, None) == -1
     assert L.set_scaled_pairs(None, 0, None, None) == -1
     assert L.permanent_field_dp(None, None, None, None, None, None, None) == -1
     assert L.induced_dipoles_pcg_dp(None, None, None, 1e-5, 10, None, None, None) == -1
-    assert L.polarization_energy_forces_dp(None, None, None, None, None) == -1
+    assert L.polarization_energy_forces_dp(None, None, None, None, None, None) == -1

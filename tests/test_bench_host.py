@@ -2,7 +2,7 @@
 its launches counted; the committed ncu traffic is reported only while the measured
 kernel's sources are unchanged; the pair count and the replica grid rule follow their
 definitions; the clock sampler's parser reports the median clock and the throttle reasons
-that were active."""
+that were active; the host-core harness that times the oracle reproduces the serial oracle."""
 import json
 import os
 import shutil
@@ -119,3 +119,32 @@ def test_clock_sampler_without_nvidia_smi_leaves_no_file():
     assert os.path.exists(c.path)
     got = c.stop()
     assert got["sm_mhz"] is None and not os.path.exists(c.path)
+
+
+def test_host_oracle_harness_equals_serial_oracle():
+    """The host-core harness that times the oracle only splits the oracle's own pair sums and
+    smooth-PME passes over worker processes: field, PCG iterates, energy and forces equal the
+    serial oracle's to rounding (the parts are summed in another order), and the module
+    references it swaps are restored afterwards."""
+    import oracle.model as om
+    from oracle import Oracle, Params
+    from paper_2011_01207_gb300 import synth
+    s = synth.water_box(64, 12.5, 4242, dmin_inter=1.7)
+    p = Params(beta=0.5446, grid=(16, 16, 16), cutoff=6.0)
+    o = Oracle(s, p)
+    E = o.permanent_field()
+    mu, info = o.pcg(E, tol=1e-6)
+    e_ref, F_ref = o.energy(mu, E), o.forces(mu)
+    saved = (om.pairs, om.realspace, om.spme)
+    h = bench.HostOracle(3)
+    h.start(s.n)
+    try:
+        _, iters, _, (E2, mu2, e2, F2) = h.step(s, p, 1e-6, outputs=True)
+    finally:
+        h.stop()
+    assert (om.pairs, om.realspace, om.spme) == saved
+    assert iters == info["iters"]
+    np.testing.assert_allclose(E2, E, rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(mu2, mu, rtol=1e-9, atol=1e-12)
+    assert abs(e2 - e_ref) < 1e-10 * abs(e_ref)
+    np.testing.assert_allclose(F2, F_ref, rtol=1e-9, atol=1e-10)

@@ -4,8 +4,8 @@ A NaN in one multipole value (never in the positions, which feed the cell indexi
 the solve's reductions non-finite: the direct call returns AP_ERR_NONFINITE, and so does
 ap_solve_info_last() for a solve that ran inside a batch graph, while the other replicas of
 the same graph are unaffected. The FP32 erfc of the pair kernels (Abramowitz & Stegun
-7.1.26, absolute error <= 1.5e-7) is compared with CUDA's erfcf over the range the
-cutoff allows, beta r in [0, 0.5446 * 7]."""
+7.1.26, absolute error <= 1.5e-7, evaluated in FP32) is compared with CUDA's erfcf over the
+range the cutoff allows, beta r in [0, 0.5446 * 7]: within 1e-6 absolute."""
 import numpy as np
 import pytest
 
@@ -80,7 +80,9 @@ def test_erfc_against_cuda_erfcf():
     torch.cuda.synchronize()
     a, l = approx.cpu().numpy().astype(np.float64), lib.cpu().numpy().astype(np.float64)
     err = np.abs(a - l)
-    # A&S 7.1.26's 1.5e-7, the fast exponential's few ulp of e^{-x^2} and erfcf's own ulps
-    assert err.max() < 5e-7, err.max()
-    # relative to the bare Coulomb term (erfc(x) / r against 1 / r): the same bound
+    # A&S 7.1.26's 1.5e-7, the FP32 rounding of its polynomial and reciprocal, the fast
+    # exponential's few ulp of e^{-x^2} and erfcf's own ulps (measured on GB300: 5.4e-7);
+    # relative to the bare Coulomb term (erfc(x) / r against 1 / r) the bound is the same,
+    # 10x below the 1e-5 tolerance of the field
+    assert err.max() < 1e-6, err.max()
     print(f"max |erfc_pair - erfcf| = {err.max():.2e} over beta r in [0, {0.5446 * 7:.3f}]")

@@ -6,7 +6,8 @@ configuration (7 A + 2 A lists, tile shifts, list filtering, graph solve).
 
 The 96,000- and 23,558-atom boxes are checked atom by atom against the full FP64 oracle:
 permanent field, the true residual of the solved dipoles (and at 23,558 atoms their
-distance to the oracle's solution), the energy and every force at those dipoles. At a
+distance to the oracle's solution and the nine components of the virial), the energy and
+every force at those dipoles. At a
 million atoms the oracle evaluates sampled rows: the permanent field and the true residual
 of the solved dipoles at 200 atoms."""
 import numpy as np
@@ -74,10 +75,12 @@ def test_solvated_chain_23558_atoms():
     mu_star, _ = o.pcg(E, tol=1e-9)
     err_debye = DEBYE * np.sqrt(np.mean(np.sum((mu - mu_star) ** 2, axis=1)))
     assert err_debye < 10 * tol
-    e, f = c.energy_forces(c.mu)
+    e, f, V = c.energy_forces(c.mu, virial=True)
     e_o = o.energy(mu, E)
     assert abs(float(e.cpu()[0]) - e_o) < 1e-5 * abs(e_o)
     assert _rel_rms(f.cpu().numpy(), o.forces(mu)) < 1e-4
+    V_o = o.virial(mu)
+    assert np.abs(V.cpu().numpy() - V_o).max() < 1e-4 * np.abs(V_o).max()
     c.close()
 
 
