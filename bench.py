@@ -19,6 +19,7 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import os
 import subprocess
@@ -249,7 +250,7 @@ def launches_per_step(iters, n, rebuild_frac, guess_launches):
 # on 96,000-atom boxes (the features are local, so it transfers).
 STEP_WORKLOADS = {
     "water96k": {"name": WORKLOAD, "system": ("water", N_MOL, BOX, SEED), "grid": GRID,
-                 "train": [("water", N_MOL, BOX, sd) for sd in (1102, 1202, 1302, 1402)], "train_grid": GRID,
+                 "train": [("water", N_MOL, BOX, 1002 + 100 * k) for k in range(1, 9)], "train_grid": GRID,
                  "per_box": 3, "all_guesses": True},
     "chain23k": {"name": "chain_23558_atoms_62.2A_grid64_rc7+2_mixed_pcg1e-5",
                  "system": ("chain", 2489, 7023, 62.2, 1003), "grid": (64, 64, 64),
@@ -257,7 +258,7 @@ STEP_WORKLOADS = {
                  "train_grid": (64, 64, 64), "per_box": 8, "all_guesses": False},
     "water1m": {"name": "water_1065000_atoms_221.6A_grid224_rc7+2_mixed_pcg1e-5",
                 "system": ("water", 355000, 221.6, 1004), "grid": (224, 224, 224),
-                "train": [("water", N_MOL, BOX, sd) for sd in (1102, 1202, 1302, 1402)], "train_grid": GRID,
+                "train": [("water", N_MOL, BOX, 1002 + 100 * k) for k in range(1, 9)], "train_grid": GRID,
                 "per_box": 3, "all_guesses": False},
 }
 
@@ -402,6 +403,8 @@ def run_ours(args):
         binding.polarization_energy_forces(ctx.ctx, out, ctx.energy, ctx.forces)
         hist["count"] += 1
 
+    eps0 = {}       # initial residual (Debye) of every timed step, per guess
+
     def timed(use_learned, tag, c=ctx, solver="pcg"):
         hist["count"] = 0
         it_, ts = [], []
@@ -419,7 +422,9 @@ def run_ours(args):
             b.record(stream)
             b.synchronize()
             ts.append(a.elapsed_time(b))
-            it_.append(binding.ap_solve_info_last(c.ctx).iterations)
+            inf = binding.ap_solve_info_last(c.ctx)
+            it_.append(inf.iterations)
+            eps0[tag] = eps0.get(tag, []) + [inf.eps_initial]
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         return ts, it_
@@ -524,7 +529,13 @@ def run_ours(args):
     cmp = {"plain_ms_per_step": round(ms_plain, 4), "plain_pcg_iters": float(np.mean(iters_plain)),
            "learned_only_ms_per_step": round(ms_learned, 4), "learned_only_pcg_iters": float(np.mean(iters_learned)),
            "classical_hold_ms_per_step": round(ms_hold, 4), "classical_hold_pcg_iters": float(np.mean(iters_hold)),
-           "headline_pcg_iters": it_mean}
+           "headline_pcg_iters": it_mean,
+           # the initial residual of each guess (Debye RMS of alpha r0): the guess quality itself,
+           # which the whole-number iteration counts show only in steps
+           "headline_eps0_debye": float(f"{np.mean(eps0['timed_steps']):.4e}"),
+           "plain_eps0_debye": float(f"{np.mean(eps0['timed_steps_plain']):.4e}"),
+           "learned_only_eps0_debye": float(f"{np.mean(eps0['timed_steps_learned_only']):.4e}"),
+           "classical_hold_eps0_debye": float(f"{np.mean(eps0['timed_steps_classical_hold']):.4e}")}
     config = {"workload": wl["name"], "atoms": s.n, "guess": GUESS_TEXT[HEADLINE_GUESS],
               "pcg_iters_mean": it_mean, "pcg_iters": [int(min(iters)), int(max(iters))], **cmp,
               "classical_hold_guess": "alpha E(t) + (mu - alpha E)(t-1) (ap_direct_guess + ap_extrapolate_guess)",
@@ -571,9 +582,23 @@ def run_ours(args):
         "clocks": clk,
         "wall_s_timed_region": round(t_wall, 3),
     }
-    ctx.close()
     if rank == 0 and not args.no_cpu and args.workload == "water96k":
-        result["cpu_baseline"] = cpu_baseline(s)
+        # the library's outputs at the first configuration (plain guess, the benchmark's
+        # tolerance), for its errors against the oracle there
+        ctx.set_positions(traj[0])
+        ctx.build()
+        ctx.permanent_field()
+        ctx.solve(tol=TOL, max_iter=200)
+        e_g, f_g, v_g = ctx.energy_forces(virial=True)
+        gpu_out = (ctx.field.cpu().numpy(), ctx.mu.cpu().numpy(), float(e_g.item()), f_g.cpu().numpy(),
+                   v_g.cpu().numpy())
+        ctx.close()
+        base, errors = cpu_baseline(s, gpu_out)
+        result["cpu_baseline"] = base
+        if errors:
+            config.update({k: float(f"{v:.3e}") for k, v in errors.items()})
+    else:
+        ctx.close()
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -581,15 +606,23 @@ def run_ours(args):
 
 
 def make_replicas(n_rep=64, lo=648, hi=24000, seed=1005):
-    """Seeded replica water boxes with sizes uniform in [lo, hi] atoms at liquid density;
-    PME grid = the smallest even 7-smooth K >= L / 1 A."""
+    """Seeded replicas with sizes uniform in [lo, hi] atoms, alternating water boxes (even
+    index) and solvated chains (odd index: a random-walk chain of a tenth of the atoms in
+    water, at the 23,558-atom chain box's density); PME grid = the smallest even 7-smooth
+    K >= L / 1 A."""
     from paper_2011_01207_gb300 import synth
     sizes = synth.replica_sizes(n_rep, lo, hi, seed)
     out = []
     for k, n in enumerate(sizes):
-        nmol = int(n) // 3
-        L = synth.water_cfg(nmol)
-        s = synth.water_box(nmol, L, seed + 10 * k)
+        if k % 2 == 0:
+            nmol = int(n) // 3
+            L = synth.water_cfg(nmol)
+            s = synth.water_box(nmol, L, seed + 10 * k)
+        else:
+            nc = max(30, int(n) // 10)
+            nw = (int(n) - nc) // 3
+            L = ((nc + 3 * nw) / 0.0979) ** (1.0 / 3.0)
+            s = synth.solvated_chain(nc, nw, L, seed + 10 * k)
         K = next(k2 for k2 in range(int(np.ceil(L)), 4 * int(np.ceil(L)) + 8) if k2 % 2 == 0 and _smooth7(k2))
         out.append((s, (K, K, K)))
     return out
@@ -692,7 +725,7 @@ def run_replicas(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_hist, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair/PME arithmetic, f64 accumulation",
         "data": "synthetic",
-        "config": {"workload": "replicas_64_water_sizes_648-24000_mixed_learned_pcg1e-5",
+        "config": {"workload": "replicas_64_water_and_chain_sizes_648-24000_mixed_learned_pcg1e-5",
                    "replicas": len(reps), "atoms_total": atoms, "sizes": [int(s.n) for s, _ in reps],
                    "grids": [int(g[0]) for _, g in reps], "pcg_iters": iters_hist,
                    "guess": "learned plus the adaptive (least-squares) extrapolation of its error over the three previous batch steps",
@@ -752,8 +785,9 @@ def _oracle_worker(conn, lo, hi):
                 conn.send(("ok", realspace.real_field(st["n"], st["I"], st["J"], st["R"], st["sigma"], *msg[1:])))
             elif cmd == "real_dipole_field":
                 conn.send(("ok", realspace.real_dipole_field(st["n"], st["I"], st["J"], st["R"], *msg[1:])))
-            elif cmd == "real_forces":
-                conn.send(("ok", realspace.real_forces(st["n"], st["I"], st["J"], st["R"], st["sigma"], *msg[1:])))
+            elif cmd == "real_forces":              # the last argument is the virial flag
+                conn.send(("ok", realspace.real_forces(st["n"], st["I"], st["J"], st["R"], st["sigma"], *msg[1:-1],
+                                                       virial=msg[-1])))
             elif cmd == "spread":                   # this worker's atoms only
                 K, order, q, dip, quad = msg[1:]
                 conn.send(("ok", spme.spread(st["xyz"][lo:hi], st["box"], K, order, q, dip, quad)))
@@ -807,15 +841,16 @@ class HostOracle:
             pr.join(timeout=10)
         self.workers = []
 
-    def step(self, s, params, tol, outputs=False):
-        """One full oracle step for system s; returns (ms, iterations, seconds per stage) and,
-        with outputs=True, also (field, dipoles, energy, forces)."""
+    @contextlib.contextmanager
+    def installed(self):
+        """While active, the oracle model's pair enumeration, real-space sums and smooth-PME
+        passes go to the workers (the workers own the pairs); everything else is unchanged."""
         import oracle.model as om
-        from oracle import Oracle
-
         host = self
+        saved = (om.pairs, om.realspace, om.spme)
+        spme_mod = saved[2]
 
-        class _Pairs:                                # the workers own the pairs
+        class _Pairs:
             def pairs_min_image(self, xyz, box, rc):
                 e = np.zeros(0, np.int64)
                 return e, e, np.zeros((0, 3))
@@ -830,26 +865,37 @@ class HostOracle:
             def real_dipole_field(self, n, I, J, R, *args):
                 return sum(host.call("real_dipole_field", *args))
 
-            def real_forces(self, n, I, J, R, sigma, *args, **kw):
-                parts = host.call("real_forces", *args)
+            def real_forces(self, n, I, J, R, sigma, *args, virial=False):
+                parts = host.call("real_forces", *args, virial)
                 return tuple(sum(p[k] for p in parts) for k in range(len(parts[0])))
 
-        saved = (om.pairs, om.realspace, om.spme)
-        convolve = saved[2].convolve
-
         class _Spme:
+            strain_sum = staticmethod(spme_mod.strain_sum)
+
             def recip_derivs(self, xyz, box, beta, K, order, q, dip, quad, max_order):
                 grid = sum(host.call("spread", K, order, q, dip, quad, sliced=(3, 4, 5)))
-                phi = convolve(grid, box, K, order, beta)
+                phi = spme_mod.convolve(grid, box, K, order, beta)
                 parts = host.call("gather", phi, K, order, max_order)
                 return [np.concatenate([p[d] for p in parts]) for d in range(max_order + 1)]
 
         om.pairs, om.realspace, om.spme = _Pairs(), _Real(), _Spme()
         try:
+            yield
+        finally:
+            om.pairs, om.realspace, om.spme = saved
+
+    def _setup(self, s, params):
+        self.call("setup", np.asarray(s.xyz, np.float64), np.asarray(s.box, np.float64), params.cutoff,
+                  np.asarray(s.excl), s.n)
+
+    def step(self, s, params, tol, outputs=False):
+        """One full oracle step for system s; returns (ms, iterations, seconds per stage) and,
+        with outputs=True, also (field, dipoles, energy, forces)."""
+        from oracle import Oracle
+        with self.installed():
             t = {}
             t0 = time.perf_counter()
-            self.call("setup", np.asarray(s.xyz, np.float64), np.asarray(s.box, np.float64), params.cutoff,
-                      np.asarray(s.excl), s.n)
+            self._setup(s, params)
             o = Oracle(s, params)
             t["pairs_and_frames"] = time.perf_counter() - t0
             t1 = time.perf_counter()
@@ -863,10 +909,19 @@ class HostOracle:
             F = o.forces(mu)
             t["energy_forces"] = time.perf_counter() - t1
             total = time.perf_counter() - t0
-        finally:
-            om.pairs, om.realspace, om.spme = saved
         res = (total * 1e3, info["iters"], {k: round(v, 3) for k, v in t.items()})
         return res + ((E, mu, energy, F),) if outputs else res
+
+    def at_dipoles(self, s, params, mu):
+        """The oracle's permanent field, and at the given dipoles the true residual (Debye),
+        energy, forces and virial."""
+        from oracle import Oracle
+        with self.installed():
+            self._setup(s, params)
+            o = Oracle(s, params)
+            E = o.permanent_field()
+            resid = o.residual_eps(E - o.apply_A(mu))
+            return E, resid, o.energy(mu, E), o.forces(mu), o.virial(mu)
 
 
 def host_cores():
@@ -887,18 +942,28 @@ def cpu_model():
     return "unknown"
 
 
-def cpu_baseline(s):
+def cpu_baseline(s, gpu=None):
     """The oracle as it stands, timed on this host: one full step of the 96,000-atom workload
     on every host core (measured, not scaled), and one full step of the 648-atom box on one
-    core and on every core."""
+    core. With gpu = (field, dipoles, energy, forces, virial) of the library at s (dipoles
+    solved to the benchmark's tolerance), also the library's errors against the oracle there:
+    field, the true residual of its dipoles, and energy, forces and virial at its dipoles."""
     from oracle import Params
     from paper_2011_01207_gb300 import synth
     cores = host_cores()
     p = Params(beta=BETA, grid=GRID, cutoff=CUTOFF)
     h = HostOracle(cores)
     h.start(s.n)
+    errors = None
     try:
         ms, iters, stages = h.step(s, p, TOL)
+        if gpu is not None:
+            E_g, mu_g, e_g, F_g, V_g = gpu
+            E_o, resid, e_o, F_o, V_o = h.at_dipoles(s, p, mu_g)
+            rel = lambda a, b: float(np.sqrt(np.mean((a - b) ** 2) / np.mean(b ** 2)))
+            errors = {"err_field_rel_rms": rel(E_g, E_o), "err_true_residual_debye": float(resid),
+                      "err_energy_rel": abs(e_g - e_o) / abs(e_o), "err_forces_rel_rms": rel(F_g, F_o),
+                      "err_virial_rel_max": float(np.abs(V_g - V_o).max() / np.abs(V_o).max())}
     finally:
         h.stop()
     small = synth.water_box(216, 18.64, 1001)
@@ -911,12 +976,13 @@ def cpu_baseline(s):
     o.energy(mu, E)
     o.forces(mu)
     ms1 = (time.perf_counter() - t0) * 1e3
-    return {"value": round(ms, 1), "unit": "ms/step", "cores": cores, "kind": "oracle",
-            "sample": f"one full oracle step of the 96,000-atom workload (pairs, frames, permanent field, PCG "
-                      f"from alpha E to {TOL} D: {iters} iterations, energy, forces), its pair sums and "
-                      f"smooth-PME passes split over {cores} host processes, measured once",
-            "cpu": cpu_model(), "stages_s": stages, "oracle_pcg_iters": iters,
-            "single_thread_648_atoms_ms_per_step": round(ms1, 1)}
+    out = {"value": round(ms, 1), "unit": "ms/step", "cores": cores, "kind": "oracle",
+           "sample": f"one full oracle step of the 96,000-atom workload (pairs, frames, permanent field, PCG "
+                     f"from alpha E to {TOL} D: {iters} iterations, energy, forces), its pair sums and "
+                     f"smooth-PME passes split over {cores} host processes, measured once",
+           "cpu": cpu_model(), "stages_s": stages, "oracle_pcg_iters": iters,
+           "single_thread_648_atoms_ms_per_step": round(ms1, 1)}
+    return out, errors
 
 
 def run_reference(args):

@@ -140,8 +140,15 @@ def test_host_oracle_harness_equals_serial_oracle():
     h.start(s.n)
     try:
         _, iters, _, (E2, mu2, e2, F2) = h.step(s, p, 1e-6, outputs=True)
+        E3, resid, e3, F3, V3 = h.at_dipoles(s, p, mu)
     finally:
         h.stop()
+    np.testing.assert_allclose(E3, E, rtol=1e-11, atol=1e-13)
+    assert abs(resid - o.residual_eps(E - o.apply_A(mu))) < 1e-12
+    assert abs(e3 - e_ref) < 1e-12 * abs(e_ref)
+    np.testing.assert_allclose(F3, F_ref, rtol=1e-10, atol=1e-11)
+    V = o.virial(mu)
+    np.testing.assert_allclose(V3, V, rtol=1e-9, atol=1e-10 * np.abs(V).max())
     assert (om.pairs, om.realspace, om.spme) == saved
     assert iters == info["iters"]
     np.testing.assert_allclose(E2, E, rtol=1e-11, atol=1e-13)

@@ -1,14 +1,18 @@
 """Batched replicas in one CUDA graph: every replica's step (field, solve with its WHILE
-loop, energy and forces) as a parallel branch; results equal the standalone calls, and a
-relaunch picks up new positions written into the captured buffers.
+loop, energy, forces and virial) as a parallel branch. Each replica's results are checked
+against the FP64 oracle (a water box, a solvated chain with global frames and exclusions,
+and a larger water box); they also equal the standalone calls, and a relaunch picks up new
+positions written into the captured buffers.
 
 Mixed precision accumulates the PME grid with FP32 atomics, whose order varies from run
 to run, so "equal" means: same iteration count, dipoles within a tenth of the solve
 tolerance (in Debye), energy to 1e-7 and forces to 1e-5 relative."""
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import Oracle, Params
 from paper_2011_01207_gb300 import binding, synth
 
 pytestmark = pytest.mark.gpu
@@ -167,4 +171,44 @@ def test_batch_adaptive_history_guess():
             assert 4.80321 * (mu - ref[1]).abs().max().item() < 1e-4
     b.close()
     for _, c in reps:
+        c.close()
+
+
+def test_batch_graph_against_oracle():
+    """One graph launch over the three replicas in the mixed precision: each replica's
+    dipoles reach the tolerance in the oracle's true residual, and its energy, forces and
+    virial at those dipoles match the oracle's at the stated tolerances (1e-5, 1e-4, 1e-4)."""
+    systems = [(synth.water_box(216, 18.64, 1001), (24, 24, 24)),
+               (synth.solvated_chain(60, 180, 26.0, 1103), (32, 32, 32)),
+               (synth.water_box(1000, 31.1, 3001), (40, 40, 40))]
+    reps = []
+    for s, g in systems:
+        c = binding.Context(s, cutoff=7.0, buffer=2.0, beta=0.5446, grid=g, precision=binding.AP_MIXED,
+                            stream=torch.cuda.Stream())
+        c.build()
+        with torch.cuda.stream(c.stream):
+            c.permanent_field(out=False)
+        reps.append((s, g, c))
+    torch.cuda.synchronize()
+    tol = 1e-5
+    b = binding.Batch([c for _, _, c in reps])
+    b.capture(tol=tol, max_iter=200, virial=True)
+    b.launch(torch.cuda.Stream())
+    torch.cuda.synchronize()
+    for s, g, c in reps:
+        info = binding.ap_solve_info_last(c.ctx)
+        assert info.status == 0 and info.eps_debye <= tol
+        o = Oracle(s, Params(beta=0.5446, grid=g, cutoff=7.0))
+        E = o.permanent_field()
+        mu = c.mu.cpu().numpy()
+        assert o.residual_eps(E - o.apply_A(mu)) < 1.5 * tol
+        e_o = o.energy(mu, E)
+        assert abs(c.energy.item() - e_o) < 1e-5 * abs(e_o)
+        F_o = o.forces(mu)
+        F = c.forces.cpu().numpy()
+        assert np.sqrt(np.mean((F - F_o) ** 2) / np.mean(F_o ** 2)) < 1e-4
+        V_o = o.virial(mu)
+        assert np.abs(c.virial.cpu().numpy() - V_o).max() < 1e-4 * np.abs(V_o).max()
+    b.close()
+    for _, _, c in reps:
         c.close()
