@@ -2,17 +2,21 @@
 98.7 A cube, PME grid 100^3, order 5, cutoff 7 A + 2 A list buffer, mixed precision, PCG
 to 1e-5 D RMS).
 
-One step = one pass of the whole hot path on a new synthetic configuration: neighbour
-blocks (rebuilt every REBUILD steps, amortised), permanent field (real + PME + self), the
-guess, the PCG solve, and the polarization energy and forces. The reported value uses the
-learned guess plus the extrapolation of its error over the two previous steps (the network
-is trained in the untimed set-up on ~10^6 pairs from converged solves of separate
-configurations); the same steps with the learned guess alone, the plain guess alpha E and
-other guesses, the Jacobi/DIIS solver and the fixed-point mode are timed alongside. Inputs
-(every step's positions) are resident on the device before timing; the L2 is flushed
-between timed steps (the working set, ~60 MB, fits the 129 MB L2). `--impl reference`
-times the FP64 oracle on the host cores on a bounded sample of the same workload. Other
-workloads: `--workload two_sets | replicas64 | precision`.
+One step = one pass of the whole hot path on a new configuration: neighbour blocks (rebuilt
+every REBUILD steps, amortised), permanent field (real + PME + self), the guess, the PCG
+solve, and the polarization energy and forces. The configurations are consecutive 2 fs
+steps of a real trajectory, made in the untimed set-up by the library's rigid-water
+integrator (--trajectory walk: the synthetic random walk instead). The reported value uses
+the learned guess plus the adaptive (least-squares) extrapolation of its error over the
+previous steps; the network is trained in the untimed set-up on ~2.3e6 solver-generated
+pairs from water boxes of eight other seeds (the timed box is held out). The same steps
+with the learned guess alone, the plain guess alpha E, the classical hold and the
+classical adaptive predictor (alpha E in place of the network), other guesses, the
+Jacobi/DIIS solver and the fixed-point mode are timed alongside. Inputs (every step's
+positions) are resident on the device before timing; the L2 is flushed between timed
+steps (the working set, ~60 MB, fits the 129 MB L2). `--impl reference` times the FP64
+oracle on the host cores, full steps of the same workload. Other workloads:
+`--workload chain23k | water1m | two_sets | replicas64 | precision | kernels`.
 
 Prints one JSON line (rank 0).
 """
@@ -55,7 +59,7 @@ MLP_FLOPS_PER_ATOM = 2 * (16 * 128 + 128 * 128 + 128 * 3)
 # (p, q, alpha, mu and r in/out)
 PCG_VECTOR_BYTES_PER_SLOT = 64 + 108 + 144
 WORKLOAD = "water_96000_atoms_98.7A_grid100_rc7+2_mixed_pcg1e-5"
-HEADLINE_GUESS = "learned+previous"
+HEADLINE_GUESS = "learned+adaptive"
 GUESS_TEXT = {
     "learned+previous": "learned (16-128-128-3 BF16 MLP) plus its previous error: learned(t) + (mu - learned)(t-1) "
                         "(zero-order hold of the error, ap_extrapolate_guess)",
@@ -65,7 +69,8 @@ GUESS_TEXT = {
 }
 # kernels of this library one guess launches: the learned guess (alpha E, short-range field,
 # features, MLP, assemble) plus the predictor of its error
-GUESS_LAUNCHES = {"learned+previous": 6, "learned+adaptive": 7, "learned+extrapolated": 6, "direct+previous": 2}
+GUESS_LAUNCHES = {"learned+previous": 6, "learned+adaptive": 7, "learned+extrapolated": 6, "direct+previous": 2,
+                  "direct+adaptive": 3}
 DIIS_DEPTH = 6          # window of the Jacobi/DIIS solver timed beside the PCG
 
 
@@ -226,6 +231,31 @@ def trajectory(s, steps, seed=TRAJ_SEED, sigma_t=0.005, sigma_r=0.01):
     return np.stack(out)
 
 
+MD_DT, MD_EQUIL, MD_T = 2.0, 300, 300.0    # fs, equilibration steps, K
+
+
+def md_trajectory(s, steps, dev, grid, seed=TRAJ_SEED):
+    """Positions of `steps` consecutive 2 fs steps of a real trajectory of the water box s: the
+    library's rigid-water velocity Verlet (SHAKE/RATTLE) under its polarization forces and an
+    O-O Lennard-Jones term, started from seeded 300 K velocities and equilibrated for
+    MD_EQUIL steps with a weak Berendsen coupling (tau 50 fs, then 200 fs while recording)."""
+    from paper_2011_01207_gb300 import binding, dynamics, synth
+    c = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=grid, precision=binding.AP_MIXED,
+                        device=dev)
+    dyn = dynamics.RigidWaterMD(c, s, dt=MD_DT, rebuild_every=10, tol=TOL)
+    dyn.start(synth.water_velocities(s, MD_T, seed))
+    for _ in range(MD_EQUIL):
+        dyn.step(target_temperature=MD_T, tau_fs=50.0)
+    out = [c.xyz.cpu().numpy().copy()]
+    for _ in range(1, steps):
+        dyn.step(target_temperature=MD_T, tau_fs=200.0)
+        out.append(c.xyz.cpu().numpy().copy())
+    dyn.check()
+    info = {"dt_fs": MD_DT, "equilibration_steps": MD_EQUIL, "temperature_K": round(dyn.temperature(), 1)}
+    c.close()
+    return np.stack(out), info
+
+
 def pairs_within(xyz, box, rc):
     from scipy.spatial import cKDTree
     w = np.mod(xyz, box)
@@ -272,17 +302,18 @@ def make_system_spec(spec):
 
 def train_learned_guess(wl, dev):
     """Solver-generated (feature, dipole) pairs from the workload's training systems (other
-    seeds than the timed one; lists rebuilt at every configuration), then Adam on the GPU
-    kernels. Returns (trainer, losses, pairs, seconds)."""
+    seeds than the timed one; configurations from large random moves, lists rebuilt at
+    each), then Adam on the GPU kernels. Returns (trainer, losses, pairs, seconds)."""
     import torch
     from paper_2011_01207_gb300 import binding, learned
     t0 = time.perf_counter()
     feats, tgts = [], []
     for k, spec in enumerate(wl["train"]):
         ts = make_system_spec(spec)
+        confs = trajectory(ts, wl["per_box"], seed=TRAIN_SEED + 100 * k, sigma_t=0.05, sigma_r=0.1)
         c = binding.Context(ts, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=wl["train_grid"],
                             precision=binding.AP_MIXED, device=dev)
-        for xyz in trajectory(ts, wl["per_box"], seed=TRAIN_SEED + 100 * k, sigma_t=0.05, sigma_r=0.1):
+        for xyz in confs:
             c.set_positions(xyz)
             c.build()
             f, t = learned.collect(c, [xyz], tol=1e-8)
@@ -317,7 +348,13 @@ def run_ours(args):
     grid = wl["grid"]
     s = make_system_spec(wl["system"])
     total = args.warmup + args.steps
-    traj = trajectory(s, total)
+    use_md = args.trajectory == "md" and wl["system"][0] == "water"
+    if use_md:
+        traj, traj_info = md_trajectory(s, total, dev, grid)
+        s = s.copy()
+        s.xyz = traj[0].copy()
+    else:
+        traj, traj_info = trajectory(s, total), {"kind": "random walk"}
     pos = torch.tensor(traj, device=dev)                       # [steps, N, 3], resident before timing
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -340,7 +377,9 @@ def run_ours(args):
     def step(k, xyz, use_learned, ctx=ctx, solver="pcg"):
         """use_learned: True (MLP), False (alpha E), "zero", "extrapolated" (2 mu(t-1) -
         mu(t-2)), "direct+previous" (alpha E plus its previous error, the classical hold:
-        alpha E(t) + (mu - alpha E)(t-1)), "learned+extrapolated" (the learned guess plus the
+        alpha E(t) + (mu - alpha E)(t-1)), "direct+adaptive" (alpha E plus the adaptive
+        extrapolation of its error, the classical counterpart of the headline),
+        "learned+extrapolated" (the learned guess plus the
         linear extrapolation of its error over the two previous steps), "learned+previous"
         (plus its previous error) or "learned+adaptive" (plus its error extrapolated with the
         least-squares coefficient of the three previous steps, ap_adaptive_guess; the previous
@@ -370,10 +409,13 @@ def run_ours(args):
                 binding.ap_extrapolate_guess(mu0, ring_mu[(k - 1) % RING], ring_mu[(k - 2) % RING], base=ring_g[k % RING],
                                              base1=ring_g[(k - 1) % RING], base2=ring_g[(k - 2) % RING])
                 guess = mu0
-        elif use_learned == "learned+adaptive":
+        elif use_learned in ("learned+adaptive", "direct+adaptive"):
             out = ring_mu[k % RING]
             g = ring_g[k % RING]
-            binding.ap_learned_guess(ctx.ctx, trainer.packed, g)
+            if use_learned == "learned+adaptive":
+                binding.ap_learned_guess(ctx.ctx, trainer.packed, g)
+            else:
+                binding.ap_direct_guess(ctx.ctx, g)
             guess = g
             m1, m2, m3 = (ring_mu[(k - j) % RING] for j in (1, 2, 3))
             g1, g2, g3 = (ring_g[(k - j) % RING] for j in (1, 2, 3))
@@ -405,11 +447,12 @@ def run_ours(args):
 
     eps0 = {}       # initial residual (Debye) of every timed step, per guess
 
-    def timed(use_learned, tag, c=ctx, solver="pcg"):
+    def timed(use_learned, tag, c=ctx, solver="pcg", positions=None):
+        pos_ = pos if positions is None else positions
         hist["count"] = 0
         it_, ts = [], []
         for k in range(args.warmup):
-            step(k, pos[k], use_learned, c, solver)
+            step(k, pos_[k], use_learned, c, solver)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -418,7 +461,7 @@ def run_ours(args):
             flush.fill_(k & 0xff)                                    # untimed: evict the L2
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(k, pos[k], use_learned, c, solver)
+            step(k, pos_[k], use_learned, c, solver)
             b.record(stream)
             b.synchronize()
             ts.append(a.elapsed_time(b))
@@ -438,11 +481,13 @@ def run_ours(args):
     times_learned, iters_learned = timed(True, "timed_steps_learned_only")
     times_plain, iters_plain = timed(False, "timed_steps_plain")
     times_hold, iters_hold = timed("direct+previous", "timed_steps_classical_hold")
+    times_cad, iters_cad = timed("direct+adaptive", "timed_steps_classical_adaptive")
     others = {}
     if wl["all_guesses"]:
+        others["learned+previous"] = timed("learned+previous", "timed_steps_learned_previous")
         others["zero"] = timed("zero", "timed_steps_zero")
         others["extrapolated"] = timed("extrapolated", "timed_steps_extrapolated")
-        others["learned+adaptive"] = timed("learned+adaptive", "timed_steps_learned_adaptive")
+
         others["learned+extrapolated"] = timed("learned+extrapolated", "timed_steps_learned_extrapolated")
         # the same steps with the Jacobi/DIIS solver in place of the PCG
         others["diis"] = timed(HEADLINE_GUESS, "timed_steps_diis", solver="diis")
@@ -453,12 +498,27 @@ def run_ours(args):
         kern_fx = {k: round(binding.ap_time_kernel(ctx_fx.ctx, k, 20), 4) for k in
                    ("real_matvec", "spread_dipoles", "real_field", "pair_forces", "spread_multipoles")}
         ctx_fx.close()
+    walk = {}
+    if use_md:
+        # the same two guesses along the synthetic random walk of the same box (the workload of
+        # earlier measurements), for comparison
+        pos_walk = torch.tensor(trajectory(s, total), device=dev)
+        ctx.xyz.copy_(pos_walk[0])
+        ctx.build()
+        tw, iw = timed(HEADLINE_GUESS, "timed_steps_walk", positions=pos_walk)
+        twp, iwp = timed(False, "timed_steps_walk_plain", positions=pos_walk)
+        walk = {"walk_ms_per_step": round(float(np.mean(tw)), 4), "walk_pcg_iters": float(np.mean(iw)),
+                "walk_plain_ms_per_step": round(float(np.mean(twp)), 4), "walk_plain_pcg_iters": float(np.mean(iwp))}
+        del pos_walk
+        ctx.xyz.copy_(pos[0])
+        ctx.build()
     clk = clocks.stop()
     ms = float(np.mean(times))
     ms_plain = float(np.mean(times_plain))
     ms_learned = float(np.mean(times_learned))
     ms_hold = float(np.mean(times_hold))
-    ms, ms_plain, ms_learned, ms_hold = max_over_ranks([ms, ms_plain, ms_learned, ms_hold], dev)
+    ms_cad = float(np.mean(times_cad))
+    ms, ms_plain, ms_learned, ms_hold, ms_cad = max_over_ranks([ms, ms_plain, ms_learned, ms_hold, ms_cad], dev)
 
     # end to end through the public API with host buffers: every step's positions copied in
     # from pinned host memory, forces and energy copied out, inside the timed region; the
@@ -529,18 +589,28 @@ def run_ours(args):
     cmp = {"plain_ms_per_step": round(ms_plain, 4), "plain_pcg_iters": float(np.mean(iters_plain)),
            "learned_only_ms_per_step": round(ms_learned, 4), "learned_only_pcg_iters": float(np.mean(iters_learned)),
            "classical_hold_ms_per_step": round(ms_hold, 4), "classical_hold_pcg_iters": float(np.mean(iters_hold)),
+           "classical_adaptive_ms_per_step": round(ms_cad, 4),
+           "classical_adaptive_pcg_iters": float(np.mean(iters_cad)),
            "headline_pcg_iters": it_mean,
            # the initial residual of each guess (Debye RMS of alpha r0): the guess quality itself,
            # which the whole-number iteration counts show only in steps
            "headline_eps0_debye": float(f"{np.mean(eps0['timed_steps']):.4e}"),
            "plain_eps0_debye": float(f"{np.mean(eps0['timed_steps_plain']):.4e}"),
            "learned_only_eps0_debye": float(f"{np.mean(eps0['timed_steps_learned_only']):.4e}"),
-           "classical_hold_eps0_debye": float(f"{np.mean(eps0['timed_steps_classical_hold']):.4e}")}
+           "classical_hold_eps0_debye": float(f"{np.mean(eps0['timed_steps_classical_hold']):.4e}"),
+           "classical_adaptive_eps0_debye": float(f"{np.mean(eps0['timed_steps_classical_adaptive']):.4e}")}
     config = {"workload": wl["name"], "atoms": s.n, "guess": GUESS_TEXT[HEADLINE_GUESS],
               "pcg_iters_mean": it_mean, "pcg_iters": [int(min(iters)), int(max(iters))], **cmp,
               "classical_hold_guess": "alpha E(t) + (mu - alpha E)(t-1) (ap_direct_guess + ap_extrapolate_guess)",
-              "learned_train_boxes": len(wl["train"]), "learned_train_pairs": n_train,
+              "classical_adaptive_guess": "alpha E(t) + the adaptive extrapolation of (mu - alpha E) over the three "
+                                          "previous steps (ap_direct_guess + ap_adaptive_guess): the headline's "
+                                          "predictor without the network",
+              **walk, "learned_train_boxes": len(wl["train"]), "learned_train_pairs": n_train,
               "learned_held_out": "the timed box's seed is not among the training boxes' seeds",
+              "trajectory": ("rigid-water MD, 2 fs steps (ap_md_kick_drift / ap_md_kick, polarization + O-O "
+                             "Lennard-Jones forces, Berendsen 300 K)") if use_md else
+                            "random walk (rigid moves ~N(0, 0.005 A), ~N(0, 0.01 rad) per step)",
+              "trajectory_temperature_K": traj_info.get("temperature_K"),
               "rebuild_every": REBUILD, "l2": "flushed between timed steps (256 MB write)", "blocks": nb, "tiles": nt,
               "excl_tiles": ne, "replicas": world, "parallelism": "replicas" if world > 1 else "1 GPU",
               "learned_training": {"pairs": n_train, "adam_steps": TRAIN_STEPS, "batch": TRAIN_BATCH,
@@ -548,12 +618,18 @@ def run_ours(args):
                                    "loss_last": round(float(np.mean(tr_loss[-20:])), 5), "seconds": round(t_train, 2)}}
     if others:
         og = {}
+        tags = {"zero": "timed_steps_zero", "extrapolated": "timed_steps_extrapolated",
+                "learned+previous": "timed_steps_learned_previous",
+                "learned+extrapolated": "timed_steps_learned_extrapolated"}
         for key, txt in (("zero", "zero"), ("extrapolated", "2 mu(t-1) - mu(t-2) from the previous steps' solves"),
-                         ("learned+adaptive", GUESS_TEXT["learned+adaptive"]),
+                         ("learned+previous", GUESS_TEXT["learned+previous"]),
                          ("learned+extrapolated", GUESS_TEXT["learned+extrapolated"])):
             ts_, it_ = others[key]
             og[key] = {"ms_per_step": round(float(np.mean(ts_)), 4), "pcg_iters_mean": float(np.mean(it_)),
-                       "guess": txt}
+                       "eps0_debye": float(f"{np.mean(eps0[tags[key]]):.4e}"), "guess": txt}
+        for key, name in (("extrapolated", "extrapolated"), ("learned+previous", "learned_previous")):
+            config[f"{name}_ms_per_step"] = og[key]["ms_per_step"]
+            config[f"{name}_pcg_iters"] = og[key]["pcg_iters_mean"]
         config["other_guesses"] = og
         ts_, it_ = others["diis"]
         config["other_solvers"] = {"jacobi_diis": {"ms_per_step": round(float(np.mean(ts_)), 4),
@@ -1031,13 +1107,15 @@ def run_reference(args):
 
 def run_precision(args):
     """Error of every output against the FP64 oracle, in FP64 and in the mixed precision the
-    benchmark runs: 648-atom water box (full), 23,558-atom solvated chain (full) and the
-    96,000-atom box (200 sampled rows). Dipoles are solved to the stated tolerance and
+    benchmark runs: 648-atom water box, 23,558-atom solvated chain and the 96,000-atom box,
+    every atom. Dipoles are solved to the stated tolerance and
     compared with the oracle's solution at 1e-10 D; energy and forces both at the GPU's own
-    dipoles (what a user gets) and at the oracle's dipoles (the kernels alone)."""
+    dipoles (what a user gets) and at the oracle's dipoles (the kernels alone), the virial at
+    the oracle's dipoles. The 96,000-atom box is compared in full (the oracle on all host
+    cores) at the GPU's dipoles."""
     import torch
     from paper_2011_01207_gb300 import binding, build as _build, synth
-    from oracle import Oracle, Params, model
+    from oracle import Oracle, Params
     _build.build_library()
     debye = 4.80321
 
@@ -1054,7 +1132,7 @@ def run_precision(args):
         o = Oracle(s, Params(beta=BETA, grid=grid, cutoff=CUTOFF))
         E_o = o.permanent_field()
         mu_star, _ = o.pcg(E_o, tol=1e-10)
-        e_star, F_star = o.energy(mu_star, E_o), o.forces(mu_star)
+        e_star, F_star, V_star = o.energy(mu_star, E_o), o.forces(mu_star), o.virial(mu_star)
         for tag, prec in precs:
             c = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=grid, precision=prec)
             c.build()
@@ -1064,9 +1142,10 @@ def run_precision(args):
             dmu = debye * np.linalg.norm(mu - mu_star, axis=1)
             e, f = c.energy_forces(c.mu)
             e_own, f_own = float(e.cpu()[0]), f.cpu().numpy()
-            e, f = c.energy_forces(torch.tensor(mu_star, device=c.mu.device))
-            e_fix, f_fix = float(e.cpu()[0]), f.cpu().numpy()
+            e, f, V = c.energy_forces(torch.tensor(mu_star, device=c.mu.device), virial=True)
+            e_fix, f_fix, V_fix = float(e.cpu()[0]), f.cpu().numpy(), V.cpu().numpy()
             out[f"{name}/{tag}"] = {
+                "virial_rel_max_same_dipoles": float(np.abs(V_fix - V_star).max() / np.abs(V_star).max()),
                 "atoms": s.n, "pcg_tol_debye": tol, "iterations": info.iterations,
                 "field_rel_rms": rel_rms(c.field.cpu().numpy(), E_o),
                 "dipole_rms_debye": float(np.sqrt(np.mean(dmu ** 2))), "dipole_max_debye": float(dmu.max()),
@@ -1102,20 +1181,28 @@ def run_precision(args):
             "energy_rel": abs(e_own - e_star) / abs(e_star), "energy_rel_same_dipoles": abs(e_fix - e_star) / abs(e_star),
             "forces_rel_rms": rel_rms(f_own, F_star), "forces_rel_rms_same_dipoles": rel_rms(f_fix, F_star)}
         c.close()
+    # the 96,000-atom box: the full oracle on all host cores (field, and at the GPU's dipoles the
+    # true residual, energy, forces and virial)
     s = make_system()
     c = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=GRID, precision=binding.AP_MIXED)
     c.build()
     c.permanent_field()
     info = c.solve(tol=TOL, max_iter=200)
-    rows = np.random.default_rng(9).choice(s.n, 200, replace=False)
-    mu = c.mu.cpu().numpy()
-    E_r, Tmu = model.row_fields(s, Params(beta=BETA, grid=GRID, cutoff=CUTOFF), rows, mu)
-    resid = E_r - (mu[rows] / s.alpha[rows, None] - Tmu)
-    out["water_96000_atoms_98.7A_grid100/mixed (200 sampled rows)"] = {
-        "atoms": s.n, "pcg_tol_debye": TOL, "iterations": info.iterations,
-        "field_rel_rms": rel_rms(c.field.cpu().numpy()[rows], E_r),
-        "true_residual_debye": float(debye * np.sqrt(np.mean(np.sum((s.alpha[rows, None] * resid) ** 2, axis=1))))}
+    e, f, V = c.energy_forces(c.mu, virial=True)
+    E_g, mu_g, e_g, F_g, V_g = (c.field.cpu().numpy(), c.mu.cpu().numpy(), float(e.item()), f.cpu().numpy(),
+                                V.cpu().numpy())
     c.close()
+    h = HostOracle(host_cores())
+    h.start(s.n)
+    try:
+        E_o, resid, e_o, F_o, V_o = h.at_dipoles(s, Params(beta=BETA, grid=GRID, cutoff=CUTOFF), mu_g)
+    finally:
+        h.stop()
+    out["water_96000_atoms_98.7A_grid100/mixed"] = {
+        "atoms": s.n, "pcg_tol_debye": TOL, "iterations": info.iterations, "field_rel_rms": rel_rms(E_g, E_o),
+        "true_residual_debye": float(resid), "energy_rel_same_dipoles": abs(e_g - e_o) / abs(e_o),
+        "forces_rel_rms_same_dipoles": rel_rms(F_g, F_o),
+        "virial_rel_max_same_dipoles": float(np.abs(V_g - V_o).max() / np.abs(V_o).max())}
     print(json.dumps({"metric": "errors against the FP64 oracle", "impl": "ours", "cases": out}))
 
 
@@ -1245,6 +1332,9 @@ def main():
     ap.add_argument("--atoms", type=int, default=96000, choices=sorted(KERNEL_WORKLOADS),
                     help="--workload kernels: the 96,000- or the 1,065,000-atom water box")
     ap.add_argument("--reps", type=int, default=20, help="--workload kernels: timed launches per kernel")
+    ap.add_argument("--trajectory", default="md", choices=["md", "walk"],
+                    help="steps of the water workloads: a real rigid-water MD trajectory (default) or the "
+                         "synthetic random walk; the chain workload always walks")
     ap.add_argument("--workload", default="water96k",
                     choices=["water96k", "chain23k", "water1m", "replicas64", "precision", "two_sets", "kernels"],
                     help="water96k: the 96,000-atom box (default); replicas64: 64 uneven replicas in one graph; "

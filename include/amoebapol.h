@@ -256,6 +256,42 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
                                           search directions (needs set_scaled_pairs) */
 int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
 
+/* f3 - A minimal rigid-water integrator, for real trajectories of the path (an MD step is one
+ * call of an integrator that moves positions and velocities under the forces, paper Sec. 1.1;
+ * velocity Verlet is the paper's default, Sec. 2.5-2.6; its benchmarks step at 2 fs,
+ * Sec. 2.7). Velocity Verlet in the kick-drift-kick form for rigid three-site molecules: the
+ * distances atom0-atom1, atom0-atom2 and atom1-atom2 of every molecule are held by SHAKE after
+ * the drift and by RATTLE on the velocities after the second kick (sweeps until the relative
+ * violation is below 1e-12, at most 1000). Units: A, fs, amu, kcal/mol/A. One thread per
+ * molecule, FP64, async on `stream`; every atom must belong to one molecule.
+ *   d_mol      [n_mol][3] int atom indices of each molecule (water: O, H, H).
+ *   h_lengths  [3] host doubles: the three constrained distances (water: O-H, O-H, H-H).
+ *   d_mass     [n] double masses, amu.
+ *   d_forces   [n][3] double total forces at the current positions, kcal/mol/A.
+ *   d_status   device int or NULL: bit 0 set if SHAKE, bit 1 if RATTLE did not converge for a
+ *              molecule (the caller clears it).
+ * ap_md_kick_drift: v += dt/2 F/m, x += dt v, SHAKE, and v = the constrained displacement / dt.
+ * ap_md_kick: v += dt/2 F/m with the forces at the new positions, RATTLE, then v *= lambda
+ * (> 0: 1 keeps the energy; a Berendsen thermostat, paper Sec. 2.6, passes
+ * sqrt(1 + dt/tau (T0/T - 1))); d_kinetic (device double or NULL) receives the kinetic energy
+ * after the scale, kcal/mol. Errors through ap_last_error(NULL). */
+int ap_md_kick_drift(int n_mol, const int *d_mol, const double *h_lengths, const double *d_mass, double dt_fs,
+                     const double *d_forces, double *d_xyz, double *d_vel, int *d_status, void *stream);
+int ap_md_kick(int n_mol, const int *d_mol, const double *h_lengths, const double *d_mass, double dt_fs,
+               const double *d_forces, const double *d_xyz, double *d_vel, double lambda, double *d_kinetic,
+               int *d_status, void *stream);
+
+/* f3 - The van der Waals term of the minimal trajectories: Lennard-Jones between atoms i and j,
+ * V = 4 eps_ij [(s_ij/r)^12 - (s_ij/r)^6] with eps_ij = sqrt(eps_i eps_j), s_ij = (s_i + s_j)/2,
+ * force-shifted at the context's real-space cutoff rc (V(r) - V(rc) + (r - rc) F(rc), so energy
+ * and force vanish there), over every non-excluded pair of the current configuration (the one
+ * of the last permanent_field()). The polarization energy alone is attractive; this supplies
+ * the repulsion that keeps a liquid from collapsing.
+ *   d_lj      [n][2] double (eps kcal/mol, sigma A) in caller order; eps = 0 leaves an atom out.
+ *   d_energy  [1] double output, kcal/mol (overwritten).
+ *   d_forces  [n][3] double, caller order: the Lennard-Jones forces are ADDED to it. */
+int ap_lj_forces(ap_ctx *ctx, const double *d_lj, double *d_energy, double *d_forces);
+
 /* Diagnostics: the FP32 fused multiply-add rate of the current device, measured. The pair
  * kernels (a2, a5, a9) are bound by plain FP32 ALU work, not by a contraction, so their
  * roofline denominator is this rate, SMs x FP32 lanes x 2 flops x clock. A kernel with 8

@@ -28,7 +28,7 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "ap_batch_create", "ap_batch_capture", "ap_batch_launch", "ap_batch_destroy", "ap_autotune",
            "ap_extrapolate_guess", "induced_dipoles_diis", "set_scaled_pairs", "permanent_field_dp",
            "induced_dipoles_pcg_dp", "polarization_energy_forces_dp", "ap_adaptive_guess", "ap_fp32_peak",
-           "ap_eval_erfc", "ap_direct_guess")
+           "ap_eval_erfc", "ap_direct_guess", "ap_md_kick_drift", "ap_md_kick", "ap_lj_forces")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5, "pair_forces": 6,
            "pcg_vectors": 7, "real_matvec2": 8}
@@ -111,6 +111,9 @@ def load(path: str = LIB) -> ctypes.CDLL:
         "ap_fp32_peak": (I, [I, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "ap_eval_erfc": (I, [P, I, P, P, P]),
         "ap_direct_guess": (I, [P, P]),
+        "ap_md_kick_drift": (I, [I, P, ctypes.POINTER(D), P, D, P, P, P, P, P]),
+        "ap_md_kick": (I, [I, P, ctypes.POINTER(D), P, D, P, P, P, D, P, P, P]),
+        "ap_lj_forces": (I, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -382,6 +385,48 @@ def ap_mlp_features(ctx, feat, mu=None, target=None):
                                        _ptr(feat, torch.float32, (n, 16), "feat"),
                                        _ptr(target, torch.float32, (n, 3), "target", allow_none=True)),
            "ap_mlp_features")
+
+
+def _lengths(h):
+    arr = (ctypes.c_double * 3)(*[float(x) for x in h])
+    return arr
+
+
+def ap_md_kick_drift(mol, lengths, mass, dt, forces, xyz, vel, status=None, stream=None):
+    """First half of a rigid-water velocity-Verlet step (positions and velocities in place)."""
+    import torch
+    n = xyz.shape[0]
+    nm = mol.shape[0]
+    _check(None, load().ap_md_kick_drift(int(nm), _ptr(mol, torch.int32, (nm, 3), "mol"), _lengths(lengths),
+                                         _ptr(mass, torch.float64, (n,), "mass"), float(dt),
+                                         _ptr(forces, torch.float64, (n, 3), "forces"),
+                                         _ptr(xyz, torch.float64, (n, 3), "xyz"), _ptr(vel, torch.float64, (n, 3), "vel"),
+                                         _ptr(status, torch.int32, (1,), "status", allow_none=True),
+                                         _stream_ptr(xyz, stream)), "ap_md_kick_drift")
+
+
+def ap_md_kick(mol, lengths, mass, dt, forces, xyz, vel, kinetic=None, status=None, stream=None, scale=1.0):
+    """Second half of the step (velocities in place, then scaled by `scale`); kinetic:
+    optional [1] float64 output."""
+    import torch
+    n = xyz.shape[0]
+    nm = mol.shape[0]
+    _check(None, load().ap_md_kick(int(nm), _ptr(mol, torch.int32, (nm, 3), "mol"), _lengths(lengths),
+                                   _ptr(mass, torch.float64, (n,), "mass"), float(dt),
+                                   _ptr(forces, torch.float64, (n, 3), "forces"),
+                                   _ptr(xyz, torch.float64, (n, 3), "xyz"), _ptr(vel, torch.float64, (n, 3), "vel"),
+                                   float(scale), _ptr(kinetic, torch.float64, (1,), "kinetic", allow_none=True),
+                                   _ptr(status, torch.int32, (1,), "status", allow_none=True),
+                                   _stream_ptr(xyz, stream)), "ap_md_kick")
+
+
+def ap_lj_forces(ctx, lj, energy, forces):
+    """Force-shifted Lennard-Jones of the current configuration: energy [1] written, forces
+    [n][3] added to."""
+    import torch
+    n = forces.shape[0]
+    _check(ctx, load().ap_lj_forces(ctx, _ptr(lj, torch.float64, (n, 2), "lj"), _ptr(energy, torch.float64, (1,), "energy"),
+                                    _ptr(forces, torch.float64, (n, 3), "forces")), "ap_lj_forces")
 
 
 def ap_direct_guess(ctx, mu0):

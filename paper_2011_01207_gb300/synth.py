@@ -332,6 +332,20 @@ def perturb(sys: System, seed: int, sigma_t: float = 0.005, sigma_r: float = 0.0
     return out
 
 
+def water_velocities(sys: System, temperature: float, seed: int) -> np.ndarray:
+    """Seeded initial velocities (A/fs) for an MD run of a water-only system: every atom
+    ~N(0, kB T / m) per axis (O 15.999, H 1.008 amu; kB = 0.0019872041 kcal/mol/K and
+    1 kcal/mol/amu = 4.184e-4 A^2/fs^2), the total momentum removed. The integrator projects
+    them onto the rigid-water constraints itself."""
+    rng = np.random.default_rng(seed)
+    m = np.full(sys.n, 1.008)
+    m[0::3] = 15.999
+    sd = np.sqrt(0.0019872041 * temperature * 4.184e-4 / m)
+    v = rng.normal(size=(sys.n, 3)) * sd[:, None]
+    v -= (m[:, None] * v).sum(axis=0) / m.sum()
+    return v
+
+
 def water_cfg(n_mol: int) -> float:
     """Cubic edge (A) for n_mol waters at 0.0333 molecules/A^3 (the configs' density)."""
     return (n_mol / 0.03334) ** (1.0 / 3.0)
