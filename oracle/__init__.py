@@ -15,7 +15,9 @@ Modules: radial (screened and damped radial functions), frames (local frames and
 derivatives), pairs (pair enumeration and scale tables), realspace (pair sums, single and
 two-dipole-set forces), ewald (exact reciprocal k-sum), spme (smooth PME), model (field,
 operator, PCG, Jacobi/DIIS, energy, forces, virial, and AMOEBA's two dipole sets: d/p
-fields, lockstep PCG, energy, forces and virial), mlp (the learned-guess network in FP64).
+fields, lockstep PCG, energy, forces and virial), mlp (the learned-guess network in FP64),
+md (the minimal rigid-water integrator: velocity Verlet with SHAKE/RATTLE and a
+force-shifted oxygen Lennard-Jones term).
 """
-from . import radial, frames, pairs, realspace, ewald, spme, model, mlp  # noqa: F401
+from . import radial, frames, pairs, realspace, ewald, spme, model, mlp, md  # noqa: F401
 from .model import Params, Oracle  # noqa: F401
