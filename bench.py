@@ -364,6 +364,10 @@ def run_ours(args):
     ctx = binding.Context(s, cutoff=CUTOFF, buffer=BUFFER, beta=BETA, grid=grid, precision=binding.AP_MIXED,
                           device=dev)
     ctx.build()
+    tuned = None
+    if not args.no_autotune:
+        ctx.permanent_field(out=False)
+        tuned = binding.ap_autotune(ctx.ctx, 3)   # launch shapes, untimed set-up
     mu0 = torch.zeros((s.n, 3), dtype=torch.float64, device=dev)
 
     # ring buffers for the trajectory guesses: converged dipoles and base guesses of the
@@ -612,6 +616,8 @@ def run_ours(args):
                             "random walk (rigid moves ~N(0, 0.005 A), ~N(0, 0.01 rad) per step)",
               "trajectory_temperature_K": traj_info.get("temperature_K"),
               "rebuild_every": REBUILD, "l2": "flushed between timed steps (256 MB write)", "blocks": nb, "tiles": nt,
+              "launch_shapes": ({"matvec_ctas_per_sm": tuned[0], "pme_threads": tuned[1], "by": "ap_autotune"}
+                                if tuned else {"matvec_ctas_per_sm": 0, "pme_threads": 128, "by": "defaults"}),
               "excl_tiles": ne, "replicas": world, "parallelism": "replicas" if world > 1 else "1 GPU",
               "learned_training": {"pairs": n_train, "adam_steps": TRAIN_STEPS, "batch": TRAIN_BATCH,
                                    "loss_first": round(float(tr_loss[0]), 5),
@@ -1272,7 +1278,7 @@ def run_two_sets(args):
         "higher_is_better": False, "dtype": "f32 pair/PME arithmetic, f64 accumulation", "data": "synthetic",
         "config": {"workload": "chain_23558_atoms_62.2A_grid64_two_sets", "atoms": s.n, "listed_pairs": int(len(pairs)),
                    "iters_mean": it2, "guess": "alpha E_d, alpha E_p",
-                   "autotune": {"matvec_grid_divisor": tuned[0], "pme_threads": tuned[1]},
+                   "autotune": {"matvec_ctas_per_sm": tuned[0], "pme_threads": tuned[1]},
                    "single_set": {"ms_per_step": round(ms1, 4), "pcg_iters_mean": it1,
                                   "note": "same configurations and lists, one dipole set"},
                    "l2": "flushed between timed steps (256 MB write)"},
@@ -1329,6 +1335,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (resident matvec grid, 128-thread PME kernels)")
     ap.add_argument("--atoms", type=int, default=96000, choices=sorted(KERNEL_WORKLOADS),
                     help="--workload kernels: the 96,000- or the 1,065,000-atom water box")
     ap.add_argument("--reps", type=int, default=20, help="--workload kernels: timed launches per kernel")

@@ -354,11 +354,11 @@ void ap_batch_destroy(ap_batch* b);
 
 /* Launch-shape autotuner: times whole PCG solves (four iterations from alpha E, each one
  * graph launch, so the real-space matvec runs concurrently with the PME branch as in any
- * solve) for every combination of the matvec grid (1, 1/2 and 1/4 of the resident grid)
- * and the PME spread/gather block size (64, 128 and 256 threads) on the current
+ * solve) for every combination of the matvec's CTAs per SM (as many as fit, 11, 10, 9, 8,
+ * 6 and 3) and the PME spread/gather block size (64, 128 and 256 threads) on the current
  * configuration, and keeps the fastest for this context. Overwrites the state of the last
- * solve (ap_solve_info_last). h_choice[2] (optional) receives the grid divisor and the
- * thread count. Synchronizes. */
+ * solve (ap_solve_info_last). h_choice[2] (optional) receives the matvec CTAs per SM (0 =
+ * as many as fit) and the thread count. Synchronizes. */
 int ap_autotune(ap_ctx* ctx, int reps, int* h_choice);
 
 /* a8 - Learned initial guess. The paper has no learned component; any PCG start is

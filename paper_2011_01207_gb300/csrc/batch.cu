@@ -159,31 +159,32 @@ int ap_autotune(ap_ctx *ctx, int reps, int *h_choice) {
         return best;
     };
     // whole PCG solves (four iterations from alpha E, as one graph launch each) for every
-    // combination of the real-space matvec grid (1, 1/2 and 1/4 of the resident grid) and
-    // the PME spread/gather block size (64, 128 and 256 threads): what counts is the
-    // matvec running concurrently with the reciprocal branch inside the solve, and the
-    // matvec's grid decides how much room the PME kernels find on the SMs
+    // combination of the real-space matvec's CTAs per SM (as many as fit, then 11, 10, 9,
+    // 8, 6 and 3) and the PME spread/gather block size (64, 128 and 256 threads): what
+    // counts is the matvec running concurrently with the reciprocal branch inside the
+    // solve, and the matvec's grid decides how much room the PME kernels find on the SMs
+    // (a resident grid fills every SM's registers)
     auto forget = [&] {
         if (ctx->solve_exec) cudaGraphExecDestroy(ctx->solve_exec);
         ctx->solve_exec = nullptr;
         ctx->graph_ok = 0;
         ctx->graph_tried = 0;
     };
-    const int divs[3] = {1, 2, 4};
+    const int per_sm[7] = {0, 11, 10, 9, 8, 6, 3};
     const int thr[3] = {64, 128, 256};
     float best = 1e30f;
-    int best_div = 1, best_thr = 128;
-    for (int d : divs)
+    int best_per_sm = 0, best_thr = 128;
+    for (int d : per_sm)
         for (int th : thr) {
-            ctx->tune_mv_div = d;
+            ctx->tune_mv_per_sm = d;
             ctx->tune_pme_threads = th;
             forget();
             int rc = pcg_solve(ctx, nullptr, 1e-300, 4, ctx->frc, nullptr);   // captures the loop
             if (rc < 0) return rc;
             float t = time_it([&] { pcg_solve(ctx, nullptr, 1e-300, 4, ctx->frc, nullptr); });
-            if (t < best) { best = t; best_div = d; best_thr = th; }
+            if (t < best) { best = t; best_per_sm = d; best_thr = th; }
         }
-    ctx->tune_mv_div = best_div;
+    ctx->tune_mv_per_sm = best_per_sm;
     ctx->tune_pme_threads = best_thr;
     // the solve graphs captured the old launch shapes: capture again at the next solve
     forget();
@@ -197,7 +198,7 @@ int ap_autotune(ap_ctx *ctx, int reps, int *h_choice) {
     AP_CUDA(cudaStreamSynchronize(ctx->s0));
     AP_CUDA(cudaGetLastError());
     if (h_choice) {
-        h_choice[0] = best_div;
+        h_choice[0] = best_per_sm;
         h_choice[1] = best_thr;
     }
     return AP_OK;

@@ -163,7 +163,7 @@ struct ap_ctx {
     float *mlp_y = nullptr;      // [n_pad][3] network outputs (slot order)
 
     // launch shapes chosen by ap_autotune (0 = default)
-    int tune_mv_div = 1;      // matvec grid = resident CTAs / tune_mv_div
+    int tune_mv_per_sm = 0;   // matvec CTAs per SM (0: as many as fit, the resident grid)
     int tune_pme_threads = 128;
     // Jacobi/DIIS solver (allocated by its first call)
     void *diis_st = nullptr;         // device state: window matrix, coefficients, convergence

@@ -519,7 +519,7 @@ int matvec_t(ap_ctx *ctx, const void *p, cudaStream_t s) {
     static int grids[4] = {0, 0, 0, 0};
     int &g0 = grids[ctx->minimg + 2 * ctx->fixed];
     if (!g0) g0 = resident_grid(ctx, kern, 128);
-    const int grid = std::max(ctx->sm_count, g0 / std::max(1, ctx->tune_mv_div));
+    const int grid = ctx->tune_mv_per_sm > 0 ? std::min(g0, ctx->tune_mv_per_sm * ctx->sm_count) : g0;
     kern<<<grid, 128, 0, s>>>(work_args(ctx), (const T4 *)ctx->posq, (const T4 *)ctx->dipd, (const T4 *)p, ctx->acc,
                               ctx->n_pad, pc);
     AP_CUDA(cudaGetLastError());
