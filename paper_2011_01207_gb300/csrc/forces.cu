@@ -243,9 +243,9 @@ __global__ void __launch_bounds__(128, VIR ? 4 : 6) k_pair_forces(
             slice.next(S.words, tg, src);
             const int sl = src & 31;   // the source's lane within its half
             if (tg != cur) {
-                if (cur >= 0) {
+                if (cur >= 0) {   // the only lane that leaves this target: a plain store
 #pragma unroll
-                    for (int k = 0; k < 12; ++k) PA::shared_add(&S.acc[k][cur], f[k] * scf[k]);
+                    for (int k = 0; k < 12; ++k) PA::shared_put(&S.acc[k][cur], f[k] * scf[k]);
                 }
 #pragma unroll
                 for (int k = 0; k < 12; ++k) f[k] = T(0);
@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(128, VIR ? 4 : 6) k_pair_forces(
             for (int k = 0; k < 6; ++k)
                 f[6 + k] += Rd[1] * (ms[ia[k]] * R[ib[k]] + R[ia[k]] * ms[ib[k]]) - Rd[2] * msr * R[ia[k]] * R[ib[k]];
         }
+        __syncwarp();   // the plain stores land before the last targets are added
         if (cur >= 0) {
 #pragma unroll
             for (int k = 0; k < 12; ++k) PA::shared_add(&S.acc[k][cur], f[k] * scf[k]);

@@ -158,6 +158,7 @@ struct PairAcc<T, false> {
     typedef T shared_t;
     typedef double reg_t;
     static __device__ __forceinline__ void shared_add(shared_t *p, T v) { atomicAdd(p, v); }
+    static __device__ __forceinline__ void shared_put(shared_t *p, T v) { *p = v; }
     static __device__ __forceinline__ reg_t to_reg(shared_t v) { return (double)v; }
     static __device__ __forceinline__ void global_add(double *p, reg_t v) { atomicAdd(p, v); }
 };
@@ -168,6 +169,7 @@ struct PairAcc<T, true> {
     static __device__ __forceinline__ void shared_add(shared_t *p, T v) {
         atomicAdd(p, (unsigned long long)ap_to_fx(v));
     }
+    static __device__ __forceinline__ void shared_put(shared_t *p, T v) { *p = (unsigned long long)ap_to_fx(v); }
     static __device__ __forceinline__ reg_t to_reg(shared_t v) { return (long long)v; }
     static __device__ __forceinline__ void global_add(double *p, reg_t v) {
         atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);

@@ -148,6 +148,10 @@ __global__ void __launch_bounds__(128, 8) k_perm_field(
         __syncwarp();
         SideSlice slice;
         slice.begin(S.words, S.pre, total, lane);
+        // A lane that moves on from a target is the only lane that ever leaves it (the
+        // shares are contiguous runs of the target-sorted sides; any other lane with sides
+        // of that target holds it as its last one): a plain store, and the last target of
+        // every lane is added atomically after the walk.
         int cur = -1;
         T4 self;
         self.x = self.y = self.z = self.w = T(0);
@@ -158,9 +162,9 @@ __global__ void __launch_bounds__(128, 8) k_perm_field(
             const int sl = src & 31;   // the source's lane within its half
             if (tg != cur) {
                 if (cur >= 0) {
-                    PA::shared_add(&S.acc[0][cur], f0);
-                    PA::shared_add(&S.acc[1][cur], f1);
-                    PA::shared_add(&S.acc[2][cur], f2);
+                    PA::shared_put(&S.acc[0][cur], f0);
+                    PA::shared_put(&S.acc[1][cur], f1);
+                    PA::shared_put(&S.acc[2][cur], f2);
                 }
                 f0 = f1 = f2 = T(0);
                 cur = tg;
@@ -191,6 +195,7 @@ __global__ void __launch_bounds__(128, 8) k_perm_field(
             f1 += fac * dy - R1 * m.z - q2 * Qy;
             f2 += fac * dz - R1 * m.w - q2 * Qz;
         }
+        __syncwarp();   // the plain stores land before the last targets are added
         if (cur >= 0) {
             PA::shared_add(&S.acc[0][cur], f0);
             PA::shared_add(&S.acc[1][cur], f1);
@@ -285,6 +290,10 @@ __global__ void __launch_bounds__(128, 12) k_matvec(
         __syncwarp();
         SideSlice sl;
         sl.begin(S.words, S.pre, total, lane);
+        // A lane's share is a contiguous run of the target-sorted sides, so a lane that
+        // moves on from a target is the only lane that ever leaves it: any other lane with
+        // sides of that target holds it as its last one. Leaving takes a plain store; the
+        // last target of every lane is added atomically after the walk.
         int cur = -1;
         T4 self;
         self.x = self.y = self.z = self.w = T(0);
@@ -294,9 +303,9 @@ __global__ void __launch_bounds__(128, 12) k_matvec(
             sl.next(S.words, tg, src);
             if (tg != cur) {
                 if (cur >= 0) {
-                    PA::shared_add(&S.acc[0][cur], f0);
-                    PA::shared_add(&S.acc[1][cur], f1);
-                    PA::shared_add(&S.acc[2][cur], f2);
+                    PA::shared_put(&S.acc[0][cur], f0);
+                    PA::shared_put(&S.acc[1][cur], f1);
+                    PA::shared_put(&S.acc[2][cur], f2);
                 }
                 f0 = f1 = f2 = T(0);
                 cur = tg;
@@ -317,6 +326,7 @@ __global__ void __launch_bounds__(128, 12) k_matvec(
             f1 += pr * dy - R1 * po.y;
             f2 += pr * dz - R1 * po.z;
         }
+        __syncwarp();   // the plain stores land before the last targets are added
         if (cur >= 0) {
             PA::shared_add(&S.acc[0][cur], f0);
             PA::shared_add(&S.acc[1][cur], f1);
@@ -410,6 +420,7 @@ __global__ void __launch_bounds__(128) k_matvec2(
         __syncwarp();
         SideSlice sl;
         sl.begin(S.words, S.pre, total, lane);
+        // as in k_matvec: plain stores on leaving a target, atomics for the last one
         int cur = -1;
         T4 self;
         self.x = self.y = self.z = self.w = T(0);
@@ -420,7 +431,7 @@ __global__ void __launch_bounds__(128) k_matvec2(
             if (tg != cur) {
                 if (cur >= 0) {
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) PA::shared_add(&S.acc[c][cur], f[c]);
+                    for (int c = 0; c < 6; ++c) PA::shared_put(&S.acc[c][cur], f[c]);
                 }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) f[c] = T(0);
@@ -446,6 +457,7 @@ __global__ void __launch_bounds__(128) k_matvec2(
             f[4] += pr1 * dy - R1 * pq.y;
             f[5] += pr1 * dz - R1 * pq.z;
         }
+        __syncwarp();   // the plain stores land before the last targets are added
         if (cur >= 0) {
 #pragma unroll
             for (int c = 0; c < 6; ++c) PA::shared_add(&S.acc[c][cur], f[c]);
