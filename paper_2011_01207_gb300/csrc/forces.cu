@@ -29,18 +29,21 @@ void unsort3(ap_ctx *ctx, const double *src, double *out, cudaStream_t s);
 
 namespace {
 
-template <class R>
-__device__ __forceinline__ void add_to(double *p, R v) {
-    if constexpr (std::is_integral<R>::value)   // fixed point
-        atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
-    else
-        atomicAdd(p, (double)v);
+// the twelve running sums of block I's atom s (force, dU/dd, dU/dQ) to the accumulators
+template <class PA>
+__device__ __forceinline__ void flush12(double *frc, double *gdip, double *gquad, int n_pad, int s,
+                                        const typename PA::run_t *a) {
+    for (int c = 0; c < 3; ++c) PA::run_flush(frc + c * n_pad + s, a[c]);
+    for (int c = 0; c < 3; ++c) PA::run_flush(gdip + c * n_pad + s, a[3 + c]);
+    for (int c = 0; c < 6; ++c) PA::run_flush(gquad + c * n_pad + s, a[6 + c]);
 }
-template <class R>
-__device__ __forceinline__ void flush12(double *frc, double *gdip, double *gquad, int n_pad, int s, const R *a) {
-    for (int c = 0; c < 3; ++c) add_to(frc + c * n_pad + s, a[c]);
-    for (int c = 0; c < 3; ++c) add_to(gdip + c * n_pad + s, a[3 + c]);
-    for (int c = 0; c < 6; ++c) add_to(gquad + c * n_pad + s, a[6 + c]);
+// one item's twelve sums of a chunk atom s (already scaled)
+template <class PA>
+__device__ __forceinline__ void flush12_item(double *frc, double *gdip, double *gquad, int n_pad, int s,
+                                             const typename PA::shared_t *a) {
+    for (int c = 0; c < 3; ++c) PA::item_flush(frc + c * n_pad + s, a[c]);
+    for (int c = 0; c < 3; ++c) PA::item_flush(gdip + c * n_pad + s, a[3 + c]);
+    for (int c = 0; c < 6; ++c) PA::item_flush(gquad + c * n_pad + s, a[6 + c]);
 }
 // FP64 value v added to slot k of an array of FP64 numbers or (fixed) fixed-point integers,
 // by the only thread that updates that slot
@@ -149,25 +152,28 @@ __global__ void __launch_bounds__(128, VIR ? 4 : 6) k_pair_forces(
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     const double sc[12] = {fconst, fconst, fconst, -fconst, -fconst, -fconst, -fconst / 3, -fconst / 3,
                            -fconst / 3, -fconst / 3, -fconst / 3, -fconst / 3};
-    // FP64 mode: per-item sums are unscaled and scaled in FP64; fixed point: scaled in T
-    // before the conversion, so that the integers hold the final quantities
+    // FP64 mode: per-item sums are unscaled and scaled in FP64; mixed and fixed point: scaled
+    // in T as they enter the item's sums (so that no FP64 multiply runs per item, and the
+    // fixed-point integers hold the final quantities)
+    constexpr bool PRESCALE = FX || sizeof(T) == 4;
     T scf[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) scf[k] = FX ? (T)sc[k] : T(1);
+    for (int k = 0; k < 12; ++k) scf[k] = PRESCALE ? (T)sc[k] : T(1);
     int curI = -1;
-    typename PA::reg_t ai[12];
+    typename PA::run_t ai[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) ai[k] = 0;
-    typename PA::reg_t vacc[9];     // this lane's share of the virial (VIR)
+    for (int k = 0; k < 12; ++k) PA::run_zero(ai[k]);
+    typedef typename std::conditional<FX, long long, double>::type vacc_t;
+    vacc_t vacc[9];                 // this lane's share of the virial (VIR)
 #pragma unroll
     for (int k = 0; k < 9; ++k) vacc[k] = 0;
     for (long t = t0; t < t1; ++t) {
         const int2 it = wa.work[t];
         __syncwarp();
         if (it.x != curI) {
-            if (curI >= 0 && curI * 32 + lane < pc.n) flush12(frc, gdip, gquad, n_pad, curI * 32 + lane, ai);
+            if (curI >= 0 && curI * 32 + lane < pc.n) flush12<PA>(frc, gdip, gquad, n_pad, curI * 32 + lane, ai);
 #pragma unroll
-            for (int k = 0; k < 12; ++k) ai[k] = 0;
+            for (int k = 0; k < 12; ++k) PA::run_zero(ai[k]);
             curI = it.x;
             const int si = curI * 32 + lane;
             const T4 a = posq[si], b = dipd[si], c = quad0[si], d = quad1[si];
@@ -333,7 +339,8 @@ __global__ void __launch_bounds__(128, VIR ? 4 : 6) k_pair_forces(
                     double F[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
-                        F[a] = FX ? ap_from_fx((long long)PA::to_reg(S.acc[a][tt])) : sc[a] * (double)PA::to_reg(S.acc[a][tt]);
+                        F[a] = FX ? ap_from_fx((long long)S.acc[a][tt])
+                                  : (PRESCALE ? 1.0 : sc[a]) * (double)S.acc[a][tt];
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -346,21 +353,26 @@ __global__ void __launch_bounds__(128, VIR ? 4 : 6) k_pair_forces(
                 else vacc[k] += v[k];
             }
         }
+        typename PA::shared_t ti[12], tj[12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) ai[k] += FX ? PA::to_reg(S.acc[k][lane]) : sc[k] * PA::to_reg(S.acc[k][lane]);
+        for (int k = 0; k < 12; ++k) {
+            ti[k] = S.acc[k][lane];
+            tj[k] = S.acc[k][32 + lane];
+            if constexpr (!PRESCALE) {
+                ti[k] *= sc[k];
+                tj[k] *= sc[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) PA::run_add(ai[k], ti[k]);
         if (diag) {
 #pragma unroll
-            for (int k = 0; k < 12; ++k)
-                ai[k] += FX ? PA::to_reg(S.acc[k][32 + lane]) : sc[k] * PA::to_reg(S.acc[k][32 + lane]);
+            for (int k = 0; k < 12; ++k) PA::run_add(ai[k], tj[k]);
         } else if (sj >= 0) {
-            typename PA::reg_t aj[12];
-#pragma unroll
-            for (int k = 0; k < 12; ++k)
-                aj[k] = FX ? PA::to_reg(S.acc[k][32 + lane]) : sc[k] * PA::to_reg(S.acc[k][32 + lane]);
-            flush12(frc, gdip, gquad, n_pad, sj, aj);
+            flush12_item<PA>(frc, gdip, gquad, n_pad, sj, tj);
         }
     }
-    if (curI >= 0 && curI * 32 + lane < pc.n) flush12(frc, gdip, gquad, n_pad, curI * 32 + lane, ai);
+    if (curI >= 0 && curI * 32 + lane < pc.n) flush12<PA>(frc, gdip, gquad, n_pad, curI * 32 + lane, ai);
     if constexpr (VIR) block_add9<32 * fo_warps<T>()>(vacc, vir);
 }
 

@@ -146,32 +146,82 @@ __device__ __forceinline__ int side_words(unsigned row, unsigned col, int lane, 
     return prow + __shfl_sync(0xffffffffu, ic, 31);
 }
 
-// Accumulation of the pair kernels' FP32 partial sums. FX = false: per-target sums of an item
-// in T with shared-memory atomics, running sums across items in FP64 registers, FP64 atomics
-// to the global accumulators. FX = true (AP_FIXED): the same in 64-bit fixed point (integer
-// additions, so the totals do not depend on their order); the global accumulators then hold
-// fixed-point integers in the same 8-byte slots.
+// Exact FP32 -> FP64 conversion with integer operations only (FP64 instructions issue at a
+// small fraction of the FP32 rate on this part): the sign, the exponent rebased from 127 to
+// 1023 and the 23 mantissa bits moved to the top of the 52. Zero and subnormal inputs
+// (below 1.2e-38) give a signed zero; infinities and NaNs keep their class.
+__device__ __forceinline__ double f2d_exact(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu, s = u & 0x80000000u, m = u & 0x7fffffu;
+    unsigned hi = s | ((e + 896u) << 20) | (m >> 3);
+    hi = e == 0u ? s : hi;
+    hi = e == 0xffu ? (s | 0x7ff00000u | (m >> 3)) : hi;
+    const unsigned lo = e == 0u ? 0u : (m << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// Compensated FP32 sum hi + lo: each addition is Knuth's TwoSum (the rounding error of
+// hi + x, recovered exactly in FP32, is added to lo), so the pair carries ~48 bits.
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ void f2_add(F2 &a, float x) {
+    const float t = a.hi + x;
+    const float z = t - a.hi;
+    a.lo += (a.hi - (t - z)) + (x - z);
+    a.hi = t;
+}
+
+// Accumulation of the pair kernels' partial sums. Per-target sums of an item are kept in
+// shared memory (shared_t; plain stores by a target's only leaving lane, atomics for the
+// last targets), running sums across items in registers (run_t), and both are added to the
+// global FP64 accumulators with FP64 atomics:
+//   FP64 mode: everything in FP64;
+//   mixed mode: items in FP32, running sums in a compensated FP32 pair, converted to FP64
+//     exactly once per flush, so the per-item path issues no FP64 instruction;
+//   FX = true (AP_FIXED): 64-bit fixed point throughout (integer additions, so the totals do
+//     not depend on their order); the global accumulators then hold fixed-point integers
+//     in the same 8-byte slots.
 template <class T, bool FX>
 struct PairAcc;
-template <class T>
-struct PairAcc<T, false> {
-    typedef T shared_t;
-    typedef double reg_t;
-    static __device__ __forceinline__ void shared_add(shared_t *p, T v) { atomicAdd(p, v); }
-    static __device__ __forceinline__ void shared_put(shared_t *p, T v) { *p = v; }
-    static __device__ __forceinline__ reg_t to_reg(shared_t v) { return (double)v; }
-    static __device__ __forceinline__ void global_add(double *p, reg_t v) { atomicAdd(p, v); }
+template <>
+struct PairAcc<double, false> {
+    typedef double shared_t;
+    typedef double run_t;
+    static __device__ __forceinline__ void shared_add(shared_t *p, double v) { atomicAdd(p, v); }
+    static __device__ __forceinline__ void shared_put(shared_t *p, double v) { *p = v; }
+    static __device__ __forceinline__ void run_zero(run_t &r) { r = 0.0; }
+    static __device__ __forceinline__ void run_add(run_t &r, shared_t v) { r += v; }
+    static __device__ __forceinline__ void run_flush(double *p, const run_t &r) { atomicAdd(p, r); }
+    static __device__ __forceinline__ void item_flush(double *p, shared_t v) { atomicAdd(p, v); }
+};
+template <>
+struct PairAcc<float, false> {
+    typedef float shared_t;
+    typedef F2 run_t;
+    static __device__ __forceinline__ void shared_add(shared_t *p, float v) { atomicAdd(p, v); }
+    static __device__ __forceinline__ void shared_put(shared_t *p, float v) { *p = v; }
+    static __device__ __forceinline__ void run_zero(run_t &r) { r.hi = r.lo = 0.f; }
+    static __device__ __forceinline__ void run_add(run_t &r, shared_t v) { f2_add(r, v); }
+    static __device__ __forceinline__ void run_flush(double *p, const run_t &r) {
+        atomicAdd(p, f2d_exact(r.hi) + f2d_exact(r.lo));
+    }
+    static __device__ __forceinline__ void item_flush(double *p, shared_t v) { atomicAdd(p, f2d_exact(v)); }
 };
 template <class T>
 struct PairAcc<T, true> {
     typedef unsigned long long shared_t;
-    typedef long long reg_t;
+    typedef long long run_t;
     static __device__ __forceinline__ void shared_add(shared_t *p, T v) {
         atomicAdd(p, (unsigned long long)ap_to_fx(v));
     }
     static __device__ __forceinline__ void shared_put(shared_t *p, T v) { *p = (unsigned long long)ap_to_fx(v); }
-    static __device__ __forceinline__ reg_t to_reg(shared_t v) { return (long long)v; }
-    static __device__ __forceinline__ void global_add(double *p, reg_t v) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+    static __device__ __forceinline__ void run_zero(run_t &r) { r = 0; }
+    static __device__ __forceinline__ void run_add(run_t &r, shared_t v) { r += (long long)v; }
+    static __device__ __forceinline__ void run_flush(double *p, const run_t &r) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)r);
+    }
+    static __device__ __forceinline__ void item_flush(double *p, shared_t v) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(p), v);
     }
 };

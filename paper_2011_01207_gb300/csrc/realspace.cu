@@ -37,12 +37,20 @@ __device__ __forceinline__ void pair_vector(const PairConsts<T> &pc, T xi, T yi,
     }
 }
 
+// running sums of block I's atom `slot` (three components) to the global accumulators
 template <class PA>
-__device__ __forceinline__ void flush3(double *acc, int n_pad, int slot, typename PA::reg_t a, typename PA::reg_t b,
-                                       typename PA::reg_t c) {
-    PA::global_add(acc + slot, a);
-    PA::global_add(acc + n_pad + slot, b);
-    PA::global_add(acc + 2 * n_pad + slot, c);
+__device__ __forceinline__ void flush3(double *acc, int n_pad, int slot, const typename PA::run_t &a,
+                                       const typename PA::run_t &b, const typename PA::run_t &c) {
+    PA::run_flush(acc + slot, a);
+    PA::run_flush(acc + n_pad + slot, b);
+    PA::run_flush(acc + 2 * n_pad + slot, c);
+}
+// one item's sums of a chunk atom: components c0, c0 + 1, c0 + 2 of the item's target 32 + lane
+template <class PA, class S>
+__device__ __forceinline__ void flush3_item(double *acc, int n_pad, int slot, const S &sm, int c0, int lane) {
+    PA::item_flush(acc + slot, sm.acc[c0][32 + lane]);
+    PA::item_flush(acc + n_pad + slot, sm.acc[c0 + 1][32 + lane]);
+    PA::item_flush(acc + 2 * n_pad + slot, sm.acc[c0 + 2][32 + lane]);
 }
 
 // Work items come from the per-configuration filter: (I, -1) is block I against itself,
@@ -87,13 +95,18 @@ __global__ void __launch_bounds__(128, 8) k_perm_field(
     work_range(wa, gw, nw, t0, t1);
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
-    typename PA::reg_t ax = 0, ay = 0, az = 0;
+    typename PA::run_t ax, ay, az;
+    PA::run_zero(ax);
+    PA::run_zero(ay);
+    PA::run_zero(az);
     for (long t = t0; t < t1; ++t) {
         const int2 it = wa.work[t];
         __syncwarp();
         if (it.x != curI) {
             if (curI >= 0 && curI * 32 + lane < pc.n) flush3<PA>(acc, n_pad, curI * 32 + lane, ax, ay, az);
-            ax = ay = az = 0;
+            PA::run_zero(ax);
+            PA::run_zero(ay);
+            PA::run_zero(az);
             curI = it.x;
             const int si = curI * 32 + lane;
             const T4 a = posq[si], b = dipd[si], c = quad0[si], d = quad1[si];
@@ -202,16 +215,15 @@ __global__ void __launch_bounds__(128, 8) k_perm_field(
             PA::shared_add(&S.acc[2][cur], f2);
         }
         __syncwarp();
-        ax += PA::to_reg(S.acc[0][lane]);
-        ay += PA::to_reg(S.acc[1][lane]);
-        az += PA::to_reg(S.acc[2][lane]);
+        PA::run_add(ax, S.acc[0][lane]);
+        PA::run_add(ay, S.acc[1][lane]);
+        PA::run_add(az, S.acc[2][lane]);
         if (diag) {
-            ax += PA::to_reg(S.acc[0][32 + lane]);
-            ay += PA::to_reg(S.acc[1][32 + lane]);
-            az += PA::to_reg(S.acc[2][32 + lane]);
+            PA::run_add(ax, S.acc[0][32 + lane]);
+            PA::run_add(ay, S.acc[1][32 + lane]);
+            PA::run_add(az, S.acc[2][32 + lane]);
         } else if (sj >= 0) {
-            flush3<PA>(acc, n_pad, sj, PA::to_reg(S.acc[0][32 + lane]), PA::to_reg(S.acc[1][32 + lane]),
-                   PA::to_reg(S.acc[2][32 + lane]));
+            flush3_item<PA>(acc, n_pad, sj, S, 0, lane);
         }
     }
     if (curI >= 0 && curI * 32 + lane < pc.n) flush3<PA>(acc, n_pad, curI * 32 + lane, ax, ay, az);
@@ -252,13 +264,18 @@ __global__ void __launch_bounds__(128, 12) k_matvec(
     work_range(wa, gw, nw, t0, t1);
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
-    typename PA::reg_t ax = 0, ay = 0, az = 0;
+    typename PA::run_t ax, ay, az;
+    PA::run_zero(ax);
+    PA::run_zero(ay);
+    PA::run_zero(az);
     for (long t = t0; t < t1; ++t) {
         const int2 it = wa.work[t];
         __syncwarp();   // every lane is done with the previous item's staging
         if (it.x != curI) {
             if (curI >= 0 && curI * 32 + lane < pc.n) flush3<PA>(acc, n_pad, curI * 32 + lane, ax, ay, az);
-            ax = ay = az = 0;
+            PA::run_zero(ax);
+            PA::run_zero(ay);
+            PA::run_zero(az);
             curI = it.x;
             const int si = curI * 32 + lane;
             T4 a = posq[si];
@@ -333,16 +350,15 @@ __global__ void __launch_bounds__(128, 12) k_matvec(
             PA::shared_add(&S.acc[2][cur], f2);
         }
         __syncwarp();
-        ax += PA::to_reg(S.acc[0][lane]);
-        ay += PA::to_reg(S.acc[1][lane]);
-        az += PA::to_reg(S.acc[2][lane]);
+        PA::run_add(ax, S.acc[0][lane]);
+        PA::run_add(ay, S.acc[1][lane]);
+        PA::run_add(az, S.acc[2][lane]);
         if (diag) {
-            ax += PA::to_reg(S.acc[0][32 + lane]);
-            ay += PA::to_reg(S.acc[1][32 + lane]);
-            az += PA::to_reg(S.acc[2][32 + lane]);
+            PA::run_add(ax, S.acc[0][32 + lane]);
+            PA::run_add(ay, S.acc[1][32 + lane]);
+            PA::run_add(az, S.acc[2][32 + lane]);
         } else if (sj >= 0) {
-            flush3<PA>(acc, n_pad, sj, PA::to_reg(S.acc[0][32 + lane]), PA::to_reg(S.acc[1][32 + lane]),
-                   PA::to_reg(S.acc[2][32 + lane]));
+            flush3_item<PA>(acc, n_pad, sj, S, 0, lane);
         }
     }
     if (curI >= 0 && curI * 32 + lane < pc.n) flush3<PA>(acc, n_pad, curI * 32 + lane, ax, ay, az);
@@ -376,7 +392,9 @@ __global__ void __launch_bounds__(128) k_matvec2(
     work_range(wa, gw, nw, t0, t1);
     const T4 *cpos = (const T4 *)wa.chunk_pos;
     int curI = -1;
-    typename PA::reg_t a[6] = {0, 0, 0, 0, 0, 0};
+    typename PA::run_t a[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) PA::run_zero(a[c]);
     for (long t = t0; t < t1; ++t) {
         const int2 it = wa.work[t];
         __syncwarp();
@@ -386,7 +404,7 @@ __global__ void __launch_bounds__(128) k_matvec2(
                 flush3<PA>(acc1, n_pad, curI * 32 + lane, a[3], a[4], a[5]);
             }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) a[c] = 0;
+            for (int c = 0; c < 6; ++c) PA::run_zero(a[c]);
             curI = it.x;
             const int si = curI * 32 + lane;
             T4 q = posq[si];
@@ -464,15 +482,13 @@ __global__ void __launch_bounds__(128) k_matvec2(
         }
         __syncwarp();
 #pragma unroll
-        for (int c = 0; c < 6; ++c) a[c] += PA::to_reg(S.acc[c][lane]);
+        for (int c = 0; c < 6; ++c) PA::run_add(a[c], S.acc[c][lane]);
         if (diag) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) a[c] += PA::to_reg(S.acc[c][32 + lane]);
+            for (int c = 0; c < 6; ++c) PA::run_add(a[c], S.acc[c][32 + lane]);
         } else if (sj >= 0) {
-            flush3<PA>(acc0, n_pad, sj, PA::to_reg(S.acc[0][32 + lane]), PA::to_reg(S.acc[1][32 + lane]),
-                       PA::to_reg(S.acc[2][32 + lane]));
-            flush3<PA>(acc1, n_pad, sj, PA::to_reg(S.acc[3][32 + lane]), PA::to_reg(S.acc[4][32 + lane]),
-                       PA::to_reg(S.acc[5][32 + lane]));
+            flush3_item<PA>(acc0, n_pad, sj, S, 0, lane);
+            flush3_item<PA>(acc1, n_pad, sj, S, 3, lane);
         }
     }
     if (curI >= 0 && curI * 32 + lane < pc.n) {
