@@ -70,26 +70,45 @@ __device__ __forceinline__ void thole_oml(T s, T *oml) {
     if (NMAX > 3) oml[3] = (T(1) + s + s * s * (T(18.0 / 35.0) + T(9.0 / 35.0) * s)) * e;
 }
 
+// First index i in [lo, hi] with start[i] >= a, for a nondecreasing start[] with
+// start[hi] >= a and start[i] < a for every i < lo; the 32 lanes of a warp search together,
+// each round testing 32 evenly spaced entries of the interval (one load per lane) and
+// keeping the 1/32 of it where the answer lies, so the dependent loads number
+// log32(hi - lo) + 1 instead of log2(hi - lo).
+__device__ __forceinline__ long warp_lower_bound(const int *__restrict__ start, long lo, long hi, long a, int lane) {
+    while (hi - lo > 32) {
+        const long step = (hi - lo + 31) >> 5;                       // sample j at lo + (j + 1) step
+        const long idx = min(lo + (long)(lane + 1) * step, hi);      // lane 31's sample is hi itself
+        const unsigned ge = __ballot_sync(0xffffffffu, start[idx] >= a);
+        const int k = __ffs(ge) - 1;                                 // first sample at or above a
+        const long nhi = min(lo + (long)(k + 1) * step, hi);
+        if (k > 0) lo += (long)k * step + 1;                         // sample k - 1 was below a
+        hi = nhi;
+    }
+    const long idx = lo + lane;
+    const unsigned ge = __ballot_sync(0xffffffffu, idx < hi && start[idx] >= a);
+    return ge ? lo + __ffs(ge) - 1 : hi;
+}
+
 // Items [t0, t1) of warp gw of nw: consecutive items holding an equal share of the total
 // item weight (in-range pairs plus a fixed staging cost per item, as exclusive prefix sums),
 // so that warps get equal work whatever the pair density of their items; item order
-// (grouped by block I) is kept.
+// (grouped by block I) is kept. Called by all 32 lanes of the warp together; the end is
+// looked for first among the 32 items from t0, where it nearly always is.
 __device__ __forceinline__ void work_range(const WorkArgs &wa, long gw, long nw, long &t0, long &t1) {
+    const int lane = threadIdx.x & 31;
     const long nitems = *wa.n_work;
     const long total = wa.item_start[nitems];
     const long a = total * gw / nw, b = total * (gw + 1) / nw;
-    long lo = 0, hi = nitems;   // first item whose start >= a
-    while (lo < hi) {
-        const long mid = (lo + hi) >> 1;
-        if (wa.item_start[mid] < a) lo = mid + 1; else hi = mid;
+    t0 = warp_lower_bound(wa.item_start, 0, nitems, a, lane);
+    if (gw == nw - 1) {
+        t1 = nitems;
+        return;
     }
-    t0 = lo;
-    hi = nitems;                // first item whose start >= b
-    while (lo < hi) {
-        const long mid = (lo + hi) >> 1;
-        if (wa.item_start[mid] < b) lo = mid + 1; else hi = mid;
-    }
-    t1 = gw == nw - 1 ? nitems : lo;
+    const long idx = t0 + lane;
+    const unsigned ge = __ballot_sync(0xffffffffu, idx < nitems && wa.item_start[idx] >= b);
+    if (ge) t1 = t0 + __ffs(ge) - 1;
+    else t1 = t0 + 32 >= nitems ? nitems : warp_lower_bound(wa.item_start, t0 + 32, nitems, b, lane);
 }
 
 // Pair sides of one 32 x 32 work item, walked in place (one warp). Word w < 32 is row i = w
