@@ -5,13 +5,14 @@
 // The block-pair lists are built with cutoff + buffer and reused for many steps; once the
 // positions of a step are known they stay fixed for the field, every PCG matrix-vector
 // product and the forces. So at each configuration, for every block I, the atoms of its
-// partner blocks J > I that lie within r_c of I's bounding box are packed into 32-wide
+// partner blocks J > I that lie within r_c of some atom of I (preselected by I's bounding
+// box) are packed into 32-wide
 // chunks (positions relative to block I's origin, in the periodic image next to I, padding
 // with NaN phantoms) with their exclusion bits carried over. The real-space kernels then
 // run over
 //   work = [(I, diagonal block), (I, chunk 0), (I, chunk 1), ...] for every I,
-// which keeps only ~1/4 of the candidate pairs of the block-pair tiles while preserving the
-// 32 x 32 warp tile. The in-range pair bits of every item (and their transposes) are found
+// which keeps only a fraction of the candidate pairs of the block-pair tiles while
+// preserving the 32 x 32 warp tile. The in-range pair bits of every item (and their transposes) are found
 // here too, once per configuration.
 #include "common.cuh"
 
@@ -89,7 +90,27 @@ __global__ void __launch_bounds__(256) k_filter(
             const T gx = max(T(0), max(lo[0] - x, x - hi[0]));
             const T gy = max(T(0), max(lo[1] - y, y - hi[1]));
             const T gz = max(T(0), max(lo[2] - z, z - hi[2]));
-            const bool sel = isfinite((float)x) && (gx * gx + gy * gy + gz * gz < rc2);
+            bool sel = isfinite((float)x) && (gx * gx + gy * gy + gz * gz < rc2);
+            // the box test only preselects; the paper's criterion is r_c of some atom of the
+            // group (about half the box's candidates in water), tested against block I's 32
+            // atoms (padding slots hold NaN and never pass); rc2 carries a 1e-5 margin over
+            // the pair masks' r_c^2, so no pair within r_c is dropped by rounding
+            if (__any_sync(0xffffffffu, sel)) {
+                bool near = false;
+#pragma unroll 8
+                for (int il = 0; il < 32; ++il) {
+                    T dx = x - __shfl_sync(0xffffffffu, pi.x, il);
+                    T dy = y - __shfl_sync(0xffffffffu, pi.y, il);
+                    T dz = z - __shfl_sync(0xffffffffu, pi.z, il);
+                    if (MINIMG) {
+                        dx -= Lx * rint(dx / Lx);
+                        dy -= Ly * rint(dy / Ly);
+                        dz -= Lz * rint(dz / Lz);
+                    }
+                    near |= dx * dx + dy * dy + dz * dz < rc2;
+                }
+                sel = sel && near;
+            }
             const unsigned m = __ballot_sync(0xffffffffu, sel);
             if (sel) {
                 const int k = count + __popc(m & ((1u << lane) - 1u));
