@@ -32,7 +32,7 @@ void free_all(ap_ctx *c) {
                     c->E, c->acc, c->rec, c->rot, c->mpl, c->frame_s, c->fvec, c->mu, c->r, c->qv, c->p, c->st,
                     c->grid, c->cgrid, c->cgrid_v, c->green, c->grid2, c->frc, c->gdip, c->gquad, c->red, c->mu_s, c->gbuf,
                     c->tile_off, c->chunk_j, c->chunk_pos, c->chunk_src, c->chunk_mask, c->chunk_flag, c->nchunk,
-                    c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y, c->smask, c->smask_t, c->e1s,
+                    c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y, c->smask, c->smask_t, c->pstart, c->sstart, c->e1s,
                     c->dg, c->stb, c->stw, c->grid_fx, c->work_off,
                     c->hist_count, c->item_start, c->scan_tmp};
     for (void *p : ptrs)

@@ -103,6 +103,8 @@ struct ap_ctx {
     unsigned *pmask_t = nullptr; // [work][32] the transpose (j-lane word, bit = i-lane)
     unsigned *smask = nullptr;   // [work][32] pairs closer than AP_SHORT_RANGE (learned-guess feature)
     unsigned *smask_t = nullptr; // its transpose
+    unsigned *pstart = nullptr;  // [work][32] each lane's start in the item's pair sides (side_start)
+    unsigned *sstart = nullptr;  // the same for the short-range sides
     double *e1s = nullptr;       // [3][n_pad] short-range first-order induced field (feature)
     int cap_chunks = 0;
     int lists_valid = 0;
@@ -196,6 +198,8 @@ struct WorkArgs {
     const unsigned *pmask_t;
     const unsigned *smask;
     const unsigned *smask_t;
+    const unsigned *pstart;    // per (item, lane): packed start of the lane's share of the sides
+    const unsigned *sstart;
     const int *item_start;     // exclusive prefix of the item weights; [n_work] = total
 };
 
@@ -214,6 +218,8 @@ inline WorkArgs work_args(const ap_ctx *ctx) {
     w.pmask_t = ctx->pmask_t;
     w.smask = ctx->smask;
     w.smask_t = ctx->smask_t;
+    w.pstart = ctx->pstart;
+    w.sstart = ctx->sstart;
     w.item_start = ctx->item_start;
     return w;
 }

@@ -15,6 +15,7 @@
 // preserving the 32 x 32 warp tile. The in-range pair bits of every item (and their transposes) are found
 // here too, once per configuration.
 #include "common.cuh"
+#include "pair_math.cuh"
 
 #include <algorithm>
 
@@ -220,7 +221,8 @@ __global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work,
                                                   const typename V4<T>::type *__restrict__ chunk_pos, T rc2, T Lx,
                                                   T Ly, T Lz, unsigned *__restrict__ pmask,
                                                   unsigned *__restrict__ pmask_t, T rs2, unsigned *__restrict__ smask,
-                                                  unsigned *__restrict__ smask_t, int *__restrict__ pcount,
+                                                  unsigned *__restrict__ smask_t, unsigned *__restrict__ pstart,
+                                                  unsigned *__restrict__ sstart, int *__restrict__ pcount,
                                                   int *__restrict__ item_cnt, int item_weight) {
     typedef typename V4<T>::type T4;
     const int lane = threadIdx.x & 31;
@@ -252,9 +254,13 @@ __global__ void __launch_bounds__(256) k_pairmask(const int2 *__restrict__ work,
         }
         pmask[(size_t)t * 32 + lane] = m;
         // transposes: word of j-lane c has bit i-lane set for every pair (i, c)
-        pmask_t[(size_t)t * 32 + lane] = warp_transpose32(m, lane);
+        const unsigned mt = warp_transpose32(m, lane), mst = warp_transpose32(ms, lane);
+        pmask_t[(size_t)t * 32 + lane] = mt;
         smask[(size_t)t * 32 + lane] = ms;
-        smask_t[(size_t)t * 32 + lane] = warp_transpose32(ms, lane);
+        smask_t[(size_t)t * 32 + lane] = mst;
+        // where each lane's share of the sides starts, for every pair kernel of this configuration
+        pstart[(size_t)t * 32 + lane] = side_start(m, mt, lane);
+        sstart[(size_t)t * 32 + lane] = side_start(ms, mst, lane);
         int c = __popc(m);
         for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
         if (lane == 0) {
@@ -387,7 +393,8 @@ int filter_t(ap_ctx *ctx, cudaStream_t s) {
     auto km = ctx->minimg ? k_pairmask<T, true> : k_pairmask<T, false>;
     km<<<ctx->sm_count * 8, 256, 0, s>>>(ctx->work, ctx->n_work, (const T4 *)ctx->posq, (const T4 *)ctx->chunk_pos, rcm,
                                          (T)P.box[0], (T)P.box[1], (T)P.box[2], ctx->pmask, ctx->pmask_t,
-                                         (T)(AP_SHORT_RANGE * AP_SHORT_RANGE), ctx->smask, ctx->smask_t, ctx->n_work + 1,
+                                         (T)(AP_SHORT_RANGE * AP_SHORT_RANGE), ctx->smask, ctx->smask_t, ctx->pstart,
+                                         ctx->sstart, ctx->n_work + 1,
                                          ctx->item_start, ITEM_WEIGHT);
     const int nchunks = (int)((ctx->cap_chunks + (long)nb + SCAN_CHUNK - 1) / SCAN_CHUNK);
     k_scan_chunks<<<nchunks, SCAN_T, 0, s>>>(ctx->item_start, ctx->n_work, ctx->scan_tmp);
@@ -408,7 +415,8 @@ int filter_alloc(ap_ctx *ctx) {
     const long cap = ctx->cap_tiles;
     if (cap <= ctx->cap_chunks) return AP_OK;
     void *ptrs[] = {ctx->chunk_j, ctx->chunk_pos, ctx->chunk_src, ctx->chunk_mask, ctx->chunk_flag, ctx->work,
-                    ctx->pmask, ctx->pmask_t, ctx->smask, ctx->smask_t, ctx->item_start, ctx->scan_tmp};
+                    ctx->pmask, ctx->pmask_t, ctx->smask, ctx->smask_t, ctx->pstart, ctx->sstart, ctx->item_start,
+                    ctx->scan_tmp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     const size_t es = ctx->prec == AP_FP64 ? 8 : 4;
@@ -425,6 +433,8 @@ int filter_alloc(ap_ctx *ctx) {
     AP_CUDA(cudaMalloc((void **)&ctx->pmask_t, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
     AP_CUDA(cudaMalloc((void **)&ctx->smask, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
     AP_CUDA(cudaMalloc((void **)&ctx->smask_t, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
+    AP_CUDA(cudaMalloc((void **)&ctx->pstart, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
+    AP_CUDA(cudaMalloc((void **)&ctx->sstart, sizeof(unsigned) * 32 * (cap + ctx->n_blocks)));
     ctx->cap_chunks = (int)cap;
     return AP_OK;
 }

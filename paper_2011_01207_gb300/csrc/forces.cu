@@ -121,7 +121,6 @@ struct FoSmem {
     A acc[12][64];                  // per-target sums of the item
     unsigned ex[32];                // exclusion words: lane i, bit j
     unsigned words[64];             // pair bits: rows of the i atoms, then columns of the j atoms
-    int pre[64];                    // inclusive prefix counts of the words' bits
 };
 
 template <class T>
@@ -228,11 +227,9 @@ __global__ void __launch_bounds__(128, VIR ? 4 : 6) k_pair_forces(
             S.acc[k][lane] = 0;
             S.acc[k][32 + lane] = 0;
         }
-        const int total = side_words(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
-                                     S.words, S.pre);
-        __syncwarp();
         SideSlice slice;
-        slice.begin(S.words, S.pre, total, lane);
+        slice.load(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], wa.pstart[(size_t)t * 32 + lane],
+                 lane, S.words);
         int cur = -1;
         T4 self, sm, sa, smu;
         T syz = 0, szz = 0;

@@ -115,28 +115,65 @@ __device__ __forceinline__ void work_range(const WorkArgs &wa, long gw, long nw,
 // (bits: the item's j atoms in range of i), word 32 + j the column of j (bits: the i atoms);
 // the target of a side in word w is atom w of the item's 64 (i atoms first) and its source
 // atom b + 32 or b for bit b of a row or column word. In word order the sides are sorted by
-// target. SideSlice::begin() places lane `lane` at the start of its equal contiguous share
-// of the `total` sides; next() then yields them one by one.
+// target, and lane l owns the l-th of 32 equal contiguous shares of them.
+//
+// side_start() (run once per configuration, with the masks) finds where lane `lane`'s share
+// starts and packs it: the word (bits 0-5), the position of its first bit in that word
+// (bits 6-10) and the number of sides in the share (bits 11-31; at most 64). All 32 lanes
+// call it together, each with its row word `row` and column word `col`.
+__device__ __forceinline__ unsigned side_start(unsigned row, unsigned col, int lane) {
+    // inclusive prefix counts of the row words (low half) and of the column words (high
+    // half) in one scan: each count is at most 32 * 32, so the halves never carry
+    int v = __popc(row) | (__popc(col) << 16);
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += y;
+    }
+    const int last = __shfl_sync(0xffffffffu, v, 31);
+    const int nrow = last & 0xffff, total = nrow + (last >> 16);
+    const int per = (total + 31) >> 5;
+    const int e0 = min(total, lane * per);
+    const int left = min(total, e0 + per) - e0;
+    // inclusive prefix of word w: lane w's low half, or the rows' total plus lane (w - 32)'s
+    // high half
+    auto prefix = [&](int w) {
+        const int u = __shfl_sync(0xffffffffu, v, w & 31);
+        return w < 32 ? (u & 0xffff) : nrow + (u >> 16);
+    };
+    // first word whose inclusive prefix exceeds e0
+    int lo = 0, hi = 63;
+    for (int r = 0; r < 6; ++r) {   // 64 words: six halvings (lo == hi after the last)
+        const int mid = (lo + hi) >> 1;
+        const int pm = prefix(mid);
+        if (lo < hi) {
+            if (pm > e0) hi = mid; else lo = mid + 1;
+        }
+    }
+    const int pb = prefix(max(lo - 1, 0));   // every lane shuffles (warp-collective)
+    const int before = lo > 0 ? pb : 0;
+    const int pick = lo & 31;
+    const unsigned wr = __shfl_sync(0xffffffffu, row, pick), wc = __shfl_sync(0xffffffffu, col, pick);
+    unsigned m = lo < 32 ? wr : wc;
+    for (int k = e0 - before; k > 0; --k) m &= m - 1u;   // skip the sides before e0
+    const int pos = left > 0 ? __ffs(m) - 1 : 0;
+    const int w = left > 0 ? lo : 0;
+    return (unsigned)w | ((unsigned)pos << 6) | ((unsigned)left << 11);
+}
+
 struct SideSlice {
     int w;         // current word
     unsigned m;    // its bits not yet taken
     int left;      // sides left in this lane's share
 
-    // words[64] and pre[64] (inclusive prefix counts of the words' bits) in shared memory
-    __device__ __forceinline__ void begin(const unsigned *words, const int *pre, int total, int lane) {
-        const int per = (total + 31) >> 5;
-        const int e0 = min(total, lane * per);
-        left = min(total, e0 + per) - e0;
-        // first word whose inclusive prefix exceeds e0
-        int lo = 0, hi = 63;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (pre[mid] > e0) hi = mid; else lo = mid + 1;
-        }
-        w = lo;
-        int k = e0 - (w ? pre[w - 1] : 0);   // sides of word w before e0
-        m = left > 0 ? words[w] : 0u;
-        for (; k > 0; --k) m &= m - 1u;
+    // stages the item's 64 words (row, col: this lane's) in shared memory and places the
+    // lane at its share's start (`start` from side_start)
+    __device__ __forceinline__ void load(unsigned row, unsigned col, unsigned start, int lane, unsigned *words) {
+        words[lane] = row;
+        words[32 + lane] = col;
+        __syncwarp();
+        w = start & 63;
+        left = (int)(start >> 11);
+        m = left > 0 ? words[w] & (~0u << ((start >> 6) & 31)) : 0u;
     }
     // next side: target word, source bit; advances over empty words
     __device__ __forceinline__ void next(const unsigned *words, int &target, int &source) {
@@ -148,22 +185,6 @@ struct SideSlice {
         source = w < 32 ? b + 32 : b;
     }
 };
-
-// words[lane] = row, words[32 + lane] = col; pre = inclusive prefix counts; returns the total
-__device__ __forceinline__ int side_words(unsigned row, unsigned col, int lane, unsigned *words, int *pre) {
-    int ir = __popc(row), ic = __popc(col);
-    for (int off = 1; off < 32; off <<= 1) {
-        const int vr = __shfl_up_sync(0xffffffffu, ir, off);
-        const int vc = __shfl_up_sync(0xffffffffu, ic, off);
-        if (lane >= off) { ir += vr; ic += vc; }
-    }
-    const int prow = __shfl_sync(0xffffffffu, ir, 31);
-    words[lane] = row;
-    words[32 + lane] = col;
-    pre[lane] = ir;
-    pre[32 + lane] = prow + ic;
-    return prow + __shfl_sync(0xffffffffu, ic, 31);
-}
 
 // Exact FP32 -> FP64 conversion with integer operations only (FP64 instructions issue at a
 // small fraction of the FP32 rate on this part): the sign, the exponent rebased from 127 to

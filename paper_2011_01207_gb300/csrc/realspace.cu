@@ -73,7 +73,6 @@ struct PfSmem {
     A acc[3][64];                   // per-target sums of the item
     unsigned ex[32];                // exclusion words: lane i, bit j
     unsigned words[64];             // pair bits: rows of the i atoms, then columns of the j atoms
-    int pre[64];                    // inclusive prefix counts of the words' bits
 };
 
 template <class T>
@@ -156,11 +155,9 @@ __global__ void __launch_bounds__(128, 8) k_perm_field(
             S.acc[c][lane] = 0;
             S.acc[c][32 + lane] = 0;
         }
-        const int total = side_words(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
-                                     S.words, S.pre);
-        __syncwarp();
         SideSlice slice;
-        slice.begin(S.words, S.pre, total, lane);
+        slice.load(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], wa.pstart[(size_t)t * 32 + lane],
+                 lane, S.words);
         // A lane that moves on from a target is the only lane that ever leaves it (the
         // shares are contiguous runs of the target-sorted sides; any other lane with sides
         // of that target holds it as its last one): a plain store, and the last target of
@@ -246,7 +243,6 @@ struct MvSmem {
     typename V4<T>::type p[64];      // dipoles of the same atoms
     A acc[3][64];                    // per-target sums of the item
     unsigned words[64];              // pair bits: rows of the i atoms, then columns of the j atoms
-    int pre[64];                     // inclusive prefix counts of the words' bits
 };
 
 template <class T, bool MINIMG, bool SHORT, bool FX>
@@ -301,12 +297,10 @@ __global__ void __launch_bounds__(128, 12) k_matvec(
             S.acc[c][lane] = 0;
             S.acc[c][32 + lane] = 0;
         }
-        const int total =
-            SHORT ? side_words(wa.smask[(size_t)t * 32 + lane], wa.smask_t[(size_t)t * 32 + lane], lane, S.words, S.pre)
-                  : side_words(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane, S.words, S.pre);
-        __syncwarp();
+        const size_t wl = (size_t)t * 32 + lane;
         SideSlice sl;
-        sl.begin(S.words, S.pre, total, lane);
+        if (SHORT) sl.load(wa.smask[wl], wa.smask_t[wl], wa.sstart[wl], lane, S.words);
+        else sl.load(wa.pmask[wl], wa.pmask_t[wl], wa.pstart[wl], lane, S.words);
         // A lane's share is a contiguous run of the target-sorted sides, so a lane that
         // moves on from a target is the only lane that ever leaves it: any other lane with
         // sides of that target holds it as its last one. Leaving takes a plain store; the
@@ -373,7 +367,6 @@ struct Mv2Smem {
     typename V4<T>::type p[2][64];   // the two dipole sets of the item's atoms
     A acc[6][64];                    // per-target sums: set 0 x y z, set 1 x y z
     unsigned words[64];
-    int pre[64];
 };
 
 template <class T, bool MINIMG, bool FX>
@@ -433,11 +426,9 @@ __global__ void __launch_bounds__(128) k_matvec2(
             S.acc[c][lane] = 0;
             S.acc[c][32 + lane] = 0;
         }
-        const int total = side_words(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], lane,
-                                     S.words, S.pre);
-        __syncwarp();
         SideSlice sl;
-        sl.begin(S.words, S.pre, total, lane);
+        sl.load(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], wa.pstart[(size_t)t * 32 + lane],
+                 lane, S.words);
         // as in k_matvec: plain stores on leaving a target, atomics for the last one
         int cur = -1;
         T4 self;
