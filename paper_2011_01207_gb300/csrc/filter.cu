@@ -61,6 +61,10 @@ __global__ void __launch_bounds__(256) k_filter(
         for (int u = 0; u < U; ++u) {
             const int t = t0 + u;
             Jv[u] = -1;
+            qv[u].x = qv[u].y = qv[u].z = qv[u].w = T(0);
+            ohv[u] = olv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            wv[u] = T(0);
+            ev[u] = -1;
             if (t < t_end) {
                 Jv[u] = tiles[t].y;
                 const int sj = Jv[u] * 32 + lane;
@@ -71,12 +75,12 @@ __global__ void __launch_bounds__(256) k_filter(
                 ev[u] = tile_excl[t];
             }
         }
+        // each candidate moved to block I's origin and periodic image, and its box test
+        T xv[U], yv[U], zv[U];
+        bool sv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int t = t0 + u;
             const int J = Jv[u];
-            if (J < 0 || J == I) continue;   // uniform over the warp
-            const int sj = J * 32 + lane;
             const T4 q = qv[u];
             // positions are relative to their block's origin: move j's to block I's origin and
             // periodic image with the tile's offset, kept as a float pair (hi + lo) so that the
@@ -91,35 +95,55 @@ __global__ void __launch_bounds__(256) k_filter(
             const T gx = max(T(0), max(lo[0] - x, x - hi[0]));
             const T gy = max(T(0), max(lo[1] - y, y - hi[1]));
             const T gz = max(T(0), max(lo[2] - z, z - hi[2]));
-            bool sel = isfinite((float)x) && (gx * gx + gy * gy + gz * gz < rc2);
-            // the box test only preselects; the paper's criterion is r_c of some atom of the
-            // group (about half the box's candidates in water), tested against block I's 32
-            // atoms (padding slots hold NaN and never pass); rc2 carries a 1e-5 margin over
-            // the pair masks' r_c^2, so no pair within r_c is dropped by rounding
-            if (__any_sync(0xffffffffu, sel)) {
-                bool near = false;
-#pragma unroll 8
-                for (int il = 0; il < 32; ++il) {
-                    T dx = x - __shfl_sync(0xffffffffu, pi.x, il);
-                    T dy = y - __shfl_sync(0xffffffffu, pi.y, il);
-                    T dz = z - __shfl_sync(0xffffffffu, pi.z, il);
+            xv[u] = x;
+            yv[u] = y;
+            zv[u] = z;
+            sv[u] = J >= 0 && J != I && isfinite((float)x) && (gx * gx + gy * gy + gz * gz < rc2);
+        }
+        // The box test only preselects; the paper's criterion is r_c of some atom of the group
+        // (about half the box's candidates in water): the U candidates of each lane against
+        // block I's 32 atoms (each shuffled once per round; padding slots hold NaN and never
+        // pass). rc2 carries a 1e-5 margin over the pair masks' r_c^2, so no pair within r_c is
+        // dropped by rounding.
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) any |= sv[u];
+        if (__any_sync(0xffffffffu, any)) {
+            bool nv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) nv[u] = false;
+#pragma unroll 4
+            for (int il = 0; il < 32; ++il) {
+                const T xi = __shfl_sync(0xffffffffu, pi.x, il), yi = __shfl_sync(0xffffffffu, pi.y, il),
+                        zi = __shfl_sync(0xffffffffu, pi.z, il);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    T dx = xv[u] - xi, dy = yv[u] - yi, dz = zv[u] - zi;
                     if (MINIMG) {
                         dx -= Lx * rint(dx / Lx);
                         dy -= Ly * rint(dy / Ly);
                         dz -= Lz * rint(dz / Lz);
                     }
-                    near |= dx * dx + dy * dy + dz * dz < rc2;
+                    nv[u] |= dx * dx + dy * dy + dz * dz < rc2;
                 }
-                sel = sel && near;
             }
+#pragma unroll
+            for (int u = 0; u < U; ++u) sv[u] = sv[u] && nv[u];
+        }
+        // pack the selections in tile order
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int J = Jv[u];
+            if (J < 0 || J == I) continue;   // uniform over the warp
+            const bool sel = sv[u];
             const unsigned m = __ballot_sync(0xffffffffu, sel);
             if (sel) {
                 const int k = count + __popc(m & ((1u << lane) - 1u));
                 const int e = ev[u];
                 const size_t slot = (size_t)(base + (k >> 5)) * 32 + (k & 31);
-                chunk_j[slot] = sj;
+                chunk_j[slot] = J * 32 + lane;
                 T4 v;
-                v.x = x; v.y = y; v.z = z; v.w = wv[u];
+                v.x = xv[u]; v.y = yv[u]; v.z = zv[u]; v.w = wv[u];
                 chunk_pos[slot] = v;
                 chunk_src[slot] = e >= 0 ? (e << 5) | lane : -1;
             }
