@@ -553,6 +553,11 @@ def run_ours(args):
             ("real_matvec", "spread_dipoles", "gather_field", "convolve", "real_field", "spread_multipoles",
              "pair_forces")}
     kern["pcg_vectors"] = binding.ap_time_kernel(ctx.ctx, "pcg_vectors", 30)
+    # one application of T as inside the solve (both branches), its reciprocal branch alone
+    # and that branch's transforms: what bounds an iteration beside the vector kernels
+    operator_us = {k: round(binding.ap_time_kernel(ctx.ctx, k, 30) * 1e3, 2)
+                   for k in ("dipole_operator", "pme_dipoles", "fft_roundtrip", "real_matvec")}
+    operator_us["pcg_vectors"] = round(kern["pcg_vectors"] * 1e3, 2)
     feat_t = torch.randn((s.n, 16), dtype=torch.float32, device=dev)
     y_t = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
     binding.ap_mlp_forward(trainer.packed, feat_t, y_t)
@@ -661,6 +666,7 @@ def run_ours(args):
         "kernel_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
         "roofline": roofline,
         "kernels": kernels,
+        "operator_us": operator_us,
         "clocks": clk,
         "wall_s_timed_region": round(t_wall, 3),
     }
@@ -1316,6 +1322,8 @@ def run_kernels(args):
              "pair_forces")}
     ctx.solve(tol=TOL, max_iter=200)
     kern["pcg_vectors"] = binding.ap_time_kernel(ctx.ctx, "pcg_vectors", reps)
+    operator_us = {k: round(binding.ap_time_kernel(ctx.ctx, k, reps) * 1e3, 2)
+                   for k in ("dipole_operator", "pme_dipoles", "fft_roundtrip")}
     fp32, sms = binding.ap_fp32_peak(max(3, reps))
     npairs = pairs_within(s.xyz, s.box, CUTOFF)
     counts = {"real_matvec": info.iterations + 1, "spread_dipoles": info.iterations + 2,
@@ -1325,7 +1333,7 @@ def run_kernels(args):
     print(json.dumps({"metric": "per-kernel launch time and roofline fraction", "impl": "ours", "workload": name,
                       "atoms": s.n, "pairs_in_cutoff": npairs, "pcg_iters_plain": info.iterations,
                       "fp32_peak_tflops_measured": round(fp32, 2), "sm_count": sms, "reps": reps,
-                      "kernels": kernels}))
+                      "kernels": kernels, "operator_us": operator_us}))
 
 
 def main():

@@ -254,6 +254,13 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
                                            solve's state, so solve again before using its result */
 #define AP_KERNEL_REAL_MATVEC2      8   /* f1: the two-set real-space product on the last two-set
                                           search directions (needs set_scaled_pairs) */
+#define AP_KERNEL_FFT_ROUNDTRIP     9   /* a3/a6: the grid's forward transform (cuFFT R2C), the
+                                           k-space product and the inverse transform (C2R) */
+#define AP_KERNEL_PME_DIPOLES      10   /* a6: the whole reciprocal branch of one operator
+                                           application (grid clear, spread, transforms, gather) */
+#define AP_KERNEL_DIPOLE_OPERATOR  11   /* a5 + a6: one application of T as inside the PCG solve,
+                                           real space on the context's stream and the reciprocal
+                                           branch on its second stream, joined */
 int ap_time_kernel(ap_ctx* ctx, int which, int reps, double* h_ms);
 
 /* f3 - A minimal rigid-water integrator, for real trajectories of the path (an MD step is one

@@ -31,7 +31,7 @@ EXPORTS = ("ap_create", "ap_destroy", "ap_last_error", "build_neighbour_blocks",
            "ap_eval_erfc", "ap_direct_guess", "ap_md_kick_drift", "ap_md_kick", "ap_lj_forces")
 KERNELS = {"real_matvec": 0, "real_field": 1, "spread_dipoles": 2, "convolve": 3, "gather_field": 4,
            "spread_multipoles": 5, "pair_forces": 6,
-           "pcg_vectors": 7, "real_matvec2": 8}
+           "pcg_vectors": 7, "real_matvec2": 8, "fft_roundtrip": 9, "pme_dipoles": 10, "dipole_operator": 11}
 
 
 class ApParams(ctypes.Structure):

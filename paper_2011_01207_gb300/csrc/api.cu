@@ -330,6 +330,9 @@ int ap_time_kernel(ap_ctx *ctx, int which, int reps, double *h_ms) {
         case AP_KERNEL_PAIR_FORCES: rc = pair_forces_launch(ctx, ctx->s0); break;
         case AP_KERNEL_PCG_VECTORS: rc = pcg_vectors_launch(ctx, ctx->s0); break;
         case AP_KERNEL_REAL_MATVEC2: rc = dp_matvec2_launch(ctx, ctx->s0, 0); break;
+        case AP_KERNEL_FFT_ROUNDTRIP: rc = pme_stage_launch(ctx, 4, ctx->s0); break;
+        case AP_KERNEL_PME_DIPOLES: rc = pme_dipole_field(ctx, ctx->p, ctx->s0); break;
+        case AP_KERNEL_DIPOLE_OPERATOR: rc = dipole_operator_into(ctx, ctx->s0, ctx->s1); break;
         default: rc = ap_fail(ctx, AP_ERR_ARG, "unknown kernel id");
         }
         if (rc) { cudaEventDestroy(a); cudaEventDestroy(b); return rc; }

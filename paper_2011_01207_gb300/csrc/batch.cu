@@ -9,6 +9,7 @@
 // ap_autotune() picks launch shapes per context by timing the candidates.
 #include "common.cuh"
 
+#include <algorithm>
 #include <vector>
 
 int ap_learned_guess(ap_ctx *ctx, const void *d_packed, double *d_mu0);
@@ -159,18 +160,21 @@ int ap_autotune(ap_ctx *ctx, int reps, int *h_choice) {
         return best;
     };
     // whole PCG solves (four iterations from alpha E, as one graph launch each) for every
-    // combination of the real-space matvec's CTAs per SM (as many as fit, then 11, 10, 9,
-    // 8, 6 and 3) and the PME spread/gather block size (64, 128 and 256 threads): what
-    // counts is the matvec running concurrently with the reciprocal branch inside the
-    // solve, and the matvec's grid decides how much room the PME kernels find on the SMs
-    // (a resident grid fills every SM's registers)
+    // combination of the real-space matvec's CTAs per SM (as many as fit, r, then r - 1,
+    // r - 2, r - 3, r - 4, r - 6 and 3, those from 3 to r - 1) and the PME spread/gather
+    // block size (64, 128 and 256 threads): what counts is the matvec running concurrently
+    // with the reciprocal branch inside the solve, and the matvec's grid decides how much
+    // room the PME kernels find on the SMs (a resident grid fills every SM's registers)
     auto forget = [&] {
         if (ctx->solve_exec) cudaGraphExecDestroy(ctx->solve_exec);
         ctx->solve_exec = nullptr;
         ctx->graph_ok = 0;
         ctx->graph_tried = 0;
     };
-    const int per_sm[7] = {0, 11, 10, 9, 8, 6, 3};
+    const int r = real_matvec_resident_per_sm(ctx);
+    std::vector<int> per_sm = {0};
+    for (int d : {r - 1, r - 2, r - 3, r - 4, r - 6, 3})
+        if (d >= 3 && d < r && std::find(per_sm.begin(), per_sm.end(), d) == per_sm.end()) per_sm.push_back(d);
     const int thr[3] = {64, 128, 256};
     float best = 1e30f;
     int best_per_sm = 0, best_thr = 128;

@@ -250,11 +250,13 @@ int filter_launch(ap_ctx *ctx, cudaStream_t s);
 int filter_alloc(ap_ctx *ctx);
 int real_field_launch(ap_ctx *ctx, cudaStream_t s);
 int real_matvec_launch(ap_ctx *ctx, const void *p, cudaStream_t s);
+int real_matvec_resident_per_sm(ap_ctx *ctx);
 int short_matvec_launch(ap_ctx *ctx, const void *p, double *out, cudaStream_t s);
 int real_forces_launch(ap_ctx *ctx, cudaStream_t s);
 int pme_init(ap_ctx *ctx);
 int pme_multipole_field(ap_ctx *ctx, cudaStream_t s);              // permanent: grid2 keeps phi_M
 int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s);  // T_rec p -> rec
+int dipole_operator_into(ap_ctx *ctx, cudaStream_t main, cudaStream_t aux);   // T p, both branches
 // a set of PME work grids and cuFFT plans (the context owns one; others allow concurrent passes)
 struct PmeBufs {
     void *grid = nullptr, *cgrid = nullptr;

@@ -44,6 +44,84 @@ __device__ __forceinline__ double erfc_e2(double x, double) { return erfc(x); }
 __device__ __forceinline__ float ap_fexp(float x) { return __expf(x); }
 __device__ __forceinline__ double ap_fexp(double x) { return exp(x); }
 
+// Packed FP32 pairs: the f32x2 add/sub/mul/fma instructions of sm_100 and later do two FP32
+// operations in one issue slot. The pair kernels are issue-bound, so two pair sides
+// evaluated side by side in the two halves of each register pair take about half the
+// issue slots of their radial arithmetic. The special-function unit has no packed form:
+// 2^x and 1/x are the PTX approximations applied to each half.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 ex2_2(float2 a) { return make_float2(ex2_approx(a.x), ex2_approx(a.y)); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+__device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+
+// Constants of the packed radial terms, from PairConsts<float>: the exponents are taken to
+// base 2 (e^-y = 2^(-y log2 e)), so each exponential is one multiply and one 2^x.
+struct PairConsts2 {
+    float2 ce;        // -beta^2 log2(e): e^{-beta^2 r^2} = 2^{ce r^2}
+    float2 pb;        // A&S 7.1.26's p times beta: t = 1 / (1 + pb r)
+    float2 c1, c2;    // (2 beta^2)^n / (beta sqrt(pi)), n = 1, 2
+    float2 ta;        // Thole a
+    float2 nl2e;      // -log2(e)
+};
+__host__ __device__ inline PairConsts2 make_consts2(const PairConsts<float> &pc) {
+    const float l2e = 1.4426950408889634f;
+    PairConsts2 k;
+    k.ce = make_float2(-pc.beta * pc.beta * l2e, -pc.beta * pc.beta * l2e);
+    k.pb = make_float2(0.3275911f * pc.beta, 0.3275911f * pc.beta);
+    k.c1 = make_float2(pc.c[1], pc.c[1]);
+    k.c2 = make_float2(pc.c[2], pc.c[2]);
+    k.ta = make_float2(pc.thole_a, pc.thole_a);
+    k.nl2e = make_float2(-l2e, -l2e);
+    return k;
+}
+
+// R_1, R_2 of the dipole operator (sigma = 1) for two pair sides at once, from r^2 and the
+// sides' Thole factor products ww = w_target w_source: the same terms as screened<float, 2>
+// and thole_oml<float, 2>, with erfc from A&S 7.1.26.
+__device__ __forceinline__ void radial12_x2(const PairConsts2 &k, float2 r2, float2 ww, float2 &R1, float2 &R2) {
+    const float2 rinv = rsqrt2(r2);
+    const float2 r = mul2(r2, rinv), rinv2 = mul2(rinv, rinv);
+    const float2 e2 = ex2_2(mul2(r2, k.ce));
+    const float2 t = rcp2(fma2(k.pb, r, splat2(1.0f)));
+    const float2 poly = mul2(t, fma2(t, fma2(t, fma2(t, fma2(t, splat2(1.061405429f), splat2(-1.453152027f)),
+                                                      splat2(1.421413741f)),
+                                             splat2(-0.284496736f)),
+                                     splat2(0.254829592f)));
+    const float2 b0 = mul2(mul2(poly, e2), rinv);
+    const float2 b1 = mul2(fma2(k.c1, e2, b0), rinv2);
+    const float2 u1 = mul2(rinv, rinv2);
+    const float2 r3 = mul2(splat2(3.0f), rinv2);
+    const float2 b2 = mul2(fma2(splat2(3.0f), b1, mul2(k.c2, e2)), rinv2);
+    const float2 u2 = mul2(u1, r3);
+    const float2 s = mul2(mul2(r2, r), mul2(ww, k.ta));
+    const float2 e = ex2_2(mul2(s, k.nl2e));
+    const float2 oml1 = fma2(s, e, e);
+    R1 = sub2(b1, mul2(e, u1));
+    R2 = sub2(b2, mul2(oml1, u2));
+}
+
 // Screened B_1..B_nmax and Coulomb U_1..U_nmax at r (rinv = 1/r, rinv2 = 1/r^2).
 template <class T, int NMAX>
 __device__ __forceinline__ void screened(const PairConsts<T> &pc, T r, T rinv, T rinv2, T *B, T *U) {

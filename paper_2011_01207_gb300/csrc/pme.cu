@@ -621,6 +621,8 @@ int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
         break;
     case 3:
         return spread_t<T>(ctx, own_bufs(ctx), nullptr, true, s);
+    case 4:
+        return fft_roundtrip<T>(ctx, own_bufs(ctx), (T *)ctx->grid, (T *)ctx->grid, s);
     default:
         return ap_fail(ctx, AP_ERR_ARG, "unknown PME stage");
     }
