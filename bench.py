@@ -127,6 +127,26 @@ def _bf16_peak():
     return 1900.0, "fallback"
 
 
+def pcg_iteration_us(ctx, reps):
+    """Time of one PCG iteration inside the solve graph: solves of exactly 4 and 12 iterations
+    (an unreachable tolerance), each one graph launch timed with CUDA events, best of `reps`;
+    (t12 - t4) / 8 in microseconds. Leaves the context's dipoles at a 12-iteration solve."""
+    import torch
+    stream = ctx.stream
+    best = {}
+    for k in (4, 12):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.solve(tol=1e-30, max_iter=k, want_info=False)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        best[k] = min(ts)
+    return (best[12] - best[4]) / 8 * 1e3
+
+
 def kernel_rooflines(kern, per_launch_counts, n, n_pad, npairs, grid, fp32_peak=None):
     """Each timed kernel against its bound: FP32 ALU (pair kernels), HBM (spread, gather,
     convolution, PCG vectors; algorithmic bytes) or BF16 tensor (MLP)."""
@@ -558,6 +578,7 @@ def run_ours(args):
     operator_us = {k: round(binding.ap_time_kernel(ctx.ctx, k, 30) * 1e3, 2)
                    for k in ("dipole_operator", "pme_dipoles", "fft_roundtrip", "real_matvec")}
     operator_us["pcg_vectors"] = round(kern["pcg_vectors"] * 1e3, 2)
+    operator_us["pcg_iteration"] = round(pcg_iteration_us(ctx, 10), 2)
     feat_t = torch.randn((s.n, 16), dtype=torch.float32, device=dev)
     y_t = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
     binding.ap_mlp_forward(trainer.packed, feat_t, y_t)
@@ -1324,6 +1345,7 @@ def run_kernels(args):
     kern["pcg_vectors"] = binding.ap_time_kernel(ctx.ctx, "pcg_vectors", reps)
     operator_us = {k: round(binding.ap_time_kernel(ctx.ctx, k, reps) * 1e3, 2)
                    for k in ("dipole_operator", "pme_dipoles", "fft_roundtrip")}
+    operator_us["pcg_iteration"] = round(pcg_iteration_us(ctx, max(3, reps)), 2)
     fp32, sms = binding.ap_fp32_peak(max(3, reps))
     npairs = pairs_within(s.xyz, s.box, CUTOFF)
     counts = {"real_matvec": info.iterations + 1, "spread_dipoles": info.iterations + 2,

@@ -239,8 +239,10 @@ int ap_solve_info_last(ap_ctx* ctx, ap_solve_info* h_info);
 
 /* Benchmark support: launch one kernel of the path `reps` times on the context's stream
  * on the current configuration (inputs as left by the last calls), timing each launch
- * with CUDA events, and return the mean duration in ms. Overwrites scratch buffers
- * only (the stored field, dipoles and lists are untouched). Synchronizes. */
+ * with CUDA events, and return the mean duration in ms. The composite ids (9-11: several
+ * kernels, library transforms, two streams) are captured once into a CUDA graph and each
+ * graph launch is timed, as they run inside the solve. Overwrites scratch buffers only
+ * (the stored field, dipoles and lists are untouched). Synchronizes. */
 #define AP_KERNEL_REAL_MATVEC       0   /* a5: real-space dipole-field pair kernel */
 #define AP_KERNEL_REAL_FIELD        1   /* a2: real-space permanent-field pair kernel */
 #define AP_KERNEL_SPREAD_DIPOLES    2   /* a6: B-spline spread of dipoles onto the grid */

@@ -313,6 +313,43 @@ int ap_time_kernel(ap_ctx *ctx, int which, int reps, double *h_ms) {
     if (!ctx || !h_ms || reps < 1) return AP_ERR_ARG;
     ctx->err.clear();
     if (!ctx->config_valid) return ap_fail(ctx, AP_ERR_STATE, "permanent_field() must come first");
+    auto launch = [&](cudaStream_t st) -> int {
+        switch (which) {
+        case AP_KERNEL_REAL_MATVEC: return real_matvec_launch(ctx, ctx->p, st);
+        case AP_KERNEL_REAL_FIELD: return real_field_launch(ctx, st);
+        case AP_KERNEL_SPREAD_DIPOLES: return pme_stage_launch(ctx, 0, st);
+        case AP_KERNEL_CONVOLVE: return pme_stage_launch(ctx, 1, st);
+        case AP_KERNEL_GATHER_FIELD: return pme_stage_launch(ctx, 2, st);
+        case AP_KERNEL_SPREAD_MULTIPOLES: return pme_stage_launch(ctx, 3, st);
+        case AP_KERNEL_PAIR_FORCES: return pair_forces_launch(ctx, st);
+        case AP_KERNEL_PCG_VECTORS: return pcg_vectors_launch(ctx, st);
+        case AP_KERNEL_REAL_MATVEC2: return dp_matvec2_launch(ctx, st, 0);
+        case AP_KERNEL_FFT_ROUNDTRIP: return pme_stage_launch(ctx, 4, st);
+        case AP_KERNEL_PME_DIPOLES: return pme_dipole_field(ctx, ctx->p, st);
+        case AP_KERNEL_DIPOLE_OPERATOR: return dipole_operator_into(ctx, st, ctx->s1);
+        default: return ap_fail(ctx, AP_ERR_ARG, "unknown kernel id");
+        }
+    };
+    // the composite ids (several kernels, library FFTs, two streams) are captured once into a
+    // CUDA graph and the graph is timed, as they run inside the solve: no host launch gaps
+    cudaGraphExec_t gx = nullptr;
+    if (which >= AP_KERNEL_FFT_ROUNDTRIP && which <= AP_KERNEL_DIPOLE_OPERATOR) {
+        cudaStream_t cs = nullptr;
+        AP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        AP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const int rc = launch(cs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ec != cudaSuccess) return ap_fail(ctx, AP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ec));
+        const cudaError_t ei = cudaGraphInstantiate(&gx, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return ap_fail(ctx, AP_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ei));
+    }
     cudaEvent_t a, b;
     AP_CUDA(cudaEventCreate(&a));
     AP_CUDA(cudaEventCreate(&b));
@@ -320,28 +357,24 @@ int ap_time_kernel(ap_ctx *ctx, int which, int reps, double *h_ms) {
     for (int r = 0; r < reps; ++r) {
         AP_CUDA(cudaEventRecord(a, ctx->s0));
         int rc = AP_OK;
-        switch (which) {
-        case AP_KERNEL_REAL_MATVEC: rc = real_matvec_launch(ctx, ctx->p, ctx->s0); break;
-        case AP_KERNEL_REAL_FIELD: rc = real_field_launch(ctx, ctx->s0); break;
-        case AP_KERNEL_SPREAD_DIPOLES: rc = pme_stage_launch(ctx, 0, ctx->s0); break;
-        case AP_KERNEL_CONVOLVE: rc = pme_stage_launch(ctx, 1, ctx->s0); break;
-        case AP_KERNEL_GATHER_FIELD: rc = pme_stage_launch(ctx, 2, ctx->s0); break;
-        case AP_KERNEL_SPREAD_MULTIPOLES: rc = pme_stage_launch(ctx, 3, ctx->s0); break;
-        case AP_KERNEL_PAIR_FORCES: rc = pair_forces_launch(ctx, ctx->s0); break;
-        case AP_KERNEL_PCG_VECTORS: rc = pcg_vectors_launch(ctx, ctx->s0); break;
-        case AP_KERNEL_REAL_MATVEC2: rc = dp_matvec2_launch(ctx, ctx->s0, 0); break;
-        case AP_KERNEL_FFT_ROUNDTRIP: rc = pme_stage_launch(ctx, 4, ctx->s0); break;
-        case AP_KERNEL_PME_DIPOLES: rc = pme_dipole_field(ctx, ctx->p, ctx->s0); break;
-        case AP_KERNEL_DIPOLE_OPERATOR: rc = dipole_operator_into(ctx, ctx->s0, ctx->s1); break;
-        default: rc = ap_fail(ctx, AP_ERR_ARG, "unknown kernel id");
+        if (gx) {
+            if (cudaGraphLaunch(gx, ctx->s0) != cudaSuccess) rc = ap_fail(ctx, AP_ERR_CUDA, "graph launch");
+        } else {
+            rc = launch(ctx->s0);
         }
-        if (rc) { cudaEventDestroy(a); cudaEventDestroy(b); return rc; }
+        if (rc) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            if (gx) cudaGraphExecDestroy(gx);
+            return rc;
+        }
         AP_CUDA(cudaEventRecord(b, ctx->s0));
         AP_CUDA(cudaEventSynchronize(b));
         float ms = 0.f;
         AP_CUDA(cudaEventElapsedTime(&ms, a, b));
         total += ms;
     }
+    if (gx) cudaGraphExecDestroy(gx);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     // the timed launches accumulated into scratch buffers: clear them for the next call

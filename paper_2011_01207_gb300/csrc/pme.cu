@@ -14,9 +14,12 @@
 // Grid layout: [z][y][x], x contiguous; complex half grid [z][y][x/2+1].
 #include "common.cuh"
 
+#include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cstdint>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -128,7 +131,7 @@ __device__ __forceinline__ void add_row5(float *row, const int *k, const float *
     }
 }
 
-// spread permanent multipoles (q, d, Q) ------------------------------------------------
+// spreads (the dipoles p, the permanent multipoles q, d, Q) ------------------------------
 // adds the stencil row v[0..4] to the grid (FX: the fixed-point grid, one 64-bit atomic per point)
 template <class T, bool FX>
 __device__ __forceinline__ void grid_row5(void *grid, size_t row, const int *k, const T *v, int Kx) {
@@ -138,71 +141,6 @@ __device__ __forceinline__ void grid_row5(void *grid, size_t row, const int *k, 
         for (int t = 0; t < 5; ++t) atomicAdd(g + k[t], (unsigned long long)ap_to_fx(v[t]));
     } else {
         add_row5(reinterpret_cast<T *>(grid) + row, k, v, Kx);
-    }
-}
-
-template <class T, bool FX>
-__global__ void k_spread_multipoles(const typename V4<T>::type *__restrict__ posq,
-                                    const typename V4<T>::type *__restrict__ dipd,
-                                    const typename V4<T>::type *__restrict__ quad0,
-                                    const typename V4<T>::type *__restrict__ quad1, void *__restrict__ grid,
-                                    PmeConsts<T> pc, const int4 *__restrict__ stb,
-                                    const typename V4<T>::type *__restrict__ stw) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= pc.n) return;
-    typename V4<T>::type a = posq[i], b = dipd[i], c = quad0[i], d = quad1[i];
-    Stencil<T> st;
-    make_stencil<T, 2>(pc, stb[i], stw[i], st);
-    const T sx = pc.s[0], sy = pc.s[1], sz = pc.s[2];
-    const T q = a.w, dx = b.x * sx, dy = b.y * sy, dz = b.z * sz;
-    const T third = T(1.0 / 3.0);
-    const T Qxx = c.x * sx * sx * third, Qyy = c.w * sy * sy * third, Qzz = d.y * sz * sz * third;
-    const T Qxy = c.y * sx * sy * T(2.0 / 3.0), Qxz = c.z * sx * sz * T(2.0 / 3.0), Qyz = d.x * sy * sz * T(2.0 / 3.0);
-    const int Kx = pc.K[0], Ky = pc.K[1];
-#pragma unroll
-    for (int t3 = 0; t3 < 5; ++t3) {
-        const T z0 = st.th[2][t3], z1 = st.d1[2][t3], z2 = st.d2[2][t3];
-#pragma unroll
-        for (int t2 = 0; t2 < 5; ++t2) {
-            const T y0 = st.th[1][t2], y1 = st.d1[1][t2], y2 = st.d2[1][t2];
-            const T A = q * y0 * z0 + dy * y1 * z0 + dz * y0 * z1 + Qyy * y2 * z0 + Qzz * y0 * z2 + Qyz * y1 * z1;
-            const T Bc = dx * y0 * z0 + Qxy * y1 * z0 + Qxz * y0 * z1;
-            const T Cc = Qxx * y0 * z0;
-            const size_t row = ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
-            T v[5];
-#pragma unroll
-            for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc + st.d2[0][t1] * Cc;
-            grid_row5<T, FX>(grid, row, st.k[0], v, Kx);
-        }
-    }
-}
-
-// spread induced dipoles p --------------------------------------------------------------
-template <class T, bool FX>
-__global__ void k_spread_dipoles(const int4 *__restrict__ stb, const typename V4<T>::type *__restrict__ stw,
-                                 const typename V4<T>::type *__restrict__ pv, void *__restrict__ grid,
-                                 PmeConsts<T> pc) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= pc.n) return;
-    typename V4<T>::type b = pv[i];
-    Stencil<T> st;
-    make_stencil<T, 1>(pc, stb[i], stw[i], st);
-    const T px = b.x * pc.s[0], py = b.y * pc.s[1], pz = b.z * pc.s[2];
-    const int Kx = pc.K[0], Ky = pc.K[1];
-#pragma unroll
-    for (int t3 = 0; t3 < 5; ++t3) {
-        const T z0 = st.th[2][t3], z1 = st.d1[2][t3];
-#pragma unroll
-        for (int t2 = 0; t2 < 5; ++t2) {
-            const T y0 = st.th[1][t2], y1 = st.d1[1][t2];
-            const T A = py * y1 * z0 + pz * y0 * z1;
-            const T Bc = px * y0 * z0;
-            const size_t row = ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
-            T v[5];
-#pragma unroll
-            for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc;
-            grid_row5<T, FX>(grid, row, st.k[0], v, Kx);
-        }
     }
 }
 
@@ -257,6 +195,121 @@ __global__ void k_gather_field(const int4 *__restrict__ stb, const typename V4<T
     out[i] = -gx * pc.s[0];
     out[n_pad + i] = -gy * pc.s[1];
     out[2 * n_pad + i] = -gz * pc.s[2];
+}
+
+// The spreads run five threads per atom (one per z-plane t3 of its stencil), a warp holding
+// six atoms in lanes 0-29, lanes 30 and 31 idle. One thread per atom left most of the GPU's
+// thread slots empty (96,000 threads for 311,296 slots) and kept too few reductions in flight
+// for the L2's atomic unit (dipole spread 42.8 -> 38.4 us per launch at 96,000 atoms). Each
+// thread forms the x and y stencils and its own plane's z weights, and covers that plane's 25
+// points.
+struct Lane5 {
+    int t3;        // this thread's z-plane of the stencil
+    long i;        // the atom
+    bool ok;       // a real atom (lanes 30, 31 and atoms past the end are not)
+};
+__device__ __forceinline__ Lane5 lane5(int n) {
+    const int lane = threadIdx.x & 31;
+    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int a = lane / 5;
+    Lane5 l;
+    l.t3 = lane - 5 * a;
+    l.i = warp * 6 + a;
+    l.ok = lane < 30 && l.i < n;
+    return l;
+}
+
+// the x and y stencils of an atom and the z weights (value and derivatives up to NDER = 1 or
+// 2) and index of plane t3
+template <class T, int NDER = 1>
+__device__ __forceinline__ void make_stencil_plane(const PmeConsts<T> &pc, int4 ib, typename V4<T>::type w, int t3,
+                                                   Stencil<T> &st, int &kz, T &z0, T &z1, T *z2 = nullptr) {
+    const int ibs[2] = {ib.x, ib.y};
+    const T ws[2] = {w.x, w.y};
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+        const int K = pc.K[d];
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            const int k = ibs[d] - t;
+            st.k[d][t] = k < 0 ? k + K : k;
+        }
+        bspline5<T, NDER>(ws[d], st.th[d], st.d1[d], st.d2[d], st.d3[d]);
+    }
+    bspline5<T, NDER>(w.z, st.th[2], st.d1[2], st.d2[2], st.d3[2]);
+    z0 = st.th[2][0];
+    z1 = st.d1[2][0];
+    T zz = NDER >= 2 ? st.d2[2][0] : T(0);
+#pragma unroll
+    for (int t = 1; t < 5; ++t)
+        if (t3 == t) {
+            z0 = st.th[2][t];
+            z1 = st.d1[2][t];
+            if (NDER >= 2) zz = st.d2[2][t];
+        }
+    if (NDER >= 2) *z2 = zz;
+    const int k = ib.z - t3;
+    kz = k < 0 ? k + pc.K[2] : k;
+}
+
+template <class T, bool FX>
+__global__ void k_spread_dipoles5(const int4 *__restrict__ stb, const typename V4<T>::type *__restrict__ stw,
+                                  const typename V4<T>::type *__restrict__ pv, void *__restrict__ grid,
+                                  PmeConsts<T> pc) {
+    const Lane5 l = lane5(pc.n);
+    if (!l.ok) return;
+    const typename V4<T>::type b = pv[l.i];
+    Stencil<T> st;
+    int kz;
+    T z0, z1;
+    make_stencil_plane<T>(pc, stb[l.i], stw[l.i], l.t3, st, kz, z0, z1);
+    const T px = b.x * pc.s[0], py = b.y * pc.s[1], pz = b.z * pc.s[2];
+    const int Kx = pc.K[0], Ky = pc.K[1];
+#pragma unroll
+    for (int t2 = 0; t2 < 5; ++t2) {
+        const T y0 = st.th[1][t2], y1 = st.d1[1][t2];
+        const T A = py * y1 * z0 + pz * y0 * z1;
+        const T Bc = px * y0 * z0;
+        const size_t row = ((size_t)kz * Ky + st.k[1][t2]) * Kx;
+        T v[5];
+#pragma unroll
+        for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc;
+        grid_row5<T, FX>(grid, row, st.k[0], v, Kx);
+    }
+}
+
+template <class T, bool FX>
+__global__ void k_spread_multipoles5(const typename V4<T>::type *__restrict__ posq,
+                                     const typename V4<T>::type *__restrict__ dipd,
+                                     const typename V4<T>::type *__restrict__ quad0,
+                                     const typename V4<T>::type *__restrict__ quad1, void *__restrict__ grid,
+                                     PmeConsts<T> pc, const int4 *__restrict__ stb,
+                                     const typename V4<T>::type *__restrict__ stw) {
+    const Lane5 l = lane5(pc.n);
+    if (!l.ok) return;
+    const typename V4<T>::type a = posq[l.i], b = dipd[l.i], c = quad0[l.i], d = quad1[l.i];
+    Stencil<T> st;
+    int kz;
+    T z0, z1, z2;
+    make_stencil_plane<T, 2>(pc, stb[l.i], stw[l.i], l.t3, st, kz, z0, z1, &z2);
+    const T sx = pc.s[0], sy = pc.s[1], sz = pc.s[2];
+    const T q = a.w, dx = b.x * sx, dy = b.y * sy, dz = b.z * sz;
+    const T third = T(1.0 / 3.0);
+    const T Qxx = c.x * sx * sx * third, Qyy = c.w * sy * sy * third, Qzz = d.y * sz * sz * third;
+    const T Qxy = c.y * sx * sy * T(2.0 / 3.0), Qxz = c.z * sx * sz * T(2.0 / 3.0), Qyz = d.x * sy * sz * T(2.0 / 3.0);
+    const int Kx = pc.K[0], Ky = pc.K[1];
+#pragma unroll
+    for (int t2 = 0; t2 < 5; ++t2) {
+        const T y0 = st.th[1][t2], y1 = st.d1[1][t2], y2 = st.d2[1][t2];
+        const T A = q * y0 * z0 + dy * y1 * z0 + dz * y0 * z1 + Qyy * y2 * z0 + Qzz * y0 * z2 + Qyz * y1 * z1;
+        const T Bc = dx * y0 * z0 + Qxy * y1 * z0 + Qxz * y0 * z1;
+        const T Cc = Qxx * y0 * z0;
+        const size_t row = ((size_t)kz * Ky + st.k[1][t2]) * Kx;
+        T v[5];
+#pragma unroll
+        for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc + st.d2[0][t1] * Cc;
+        grid_row5<T, FX>(grid, row, st.k[0], v, Kx);
+    }
 }
 
 // derivatives of phi up to third order (20 components) for the forces -------------------
@@ -401,6 +454,24 @@ PmeBufs own_bufs(ap_ctx *ctx) {
     return b;
 }
 
+// launch shape of the five-threads-per-atom kernels: ceil(n / 6) warps in blocks of
+// `threads` (a multiple of 32)
+inline int lane5_blocks(int n, int threads) {
+    const long warps = (n + 5) / 6;
+    return (int)((warps * 32 + threads - 1) / threads);
+}
+
+// the field -grad(phi) of the grid phi at every atom, into out[3][n_pad]
+template <class T>
+int gather_launch(ap_ctx *ctx, const T *phi, T *out, cudaStream_t s) {
+    typedef typename V4<T>::type T4;
+    PmeConsts<T> pc = pme_consts<T>(ctx);
+    const int th = ctx->tune_pme_threads;
+    k_gather_field<T><<<ap_grid_for(ctx->n, th), th, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, phi, out, ctx->n_pad, pc);
+    AP_CUDA(cudaGetLastError());
+    return AP_OK;
+}
+
 template <class T>
 int fft_roundtrip(ap_ctx *ctx, const PmeBufs &b, T *in, T *out, cudaStream_t s) {
     typedef typename FftTypes<T>::cplx C;
@@ -433,14 +504,14 @@ int spread_t(ap_ctx *ctx, const PmeBufs &bf, const void *src, bool multi, cudaSt
     void *g = fx ? (void *)bf.grid_fx : bf.grid;
     if (!fx) AP_CUDA(cudaMemsetAsync(bf.grid, 0, sizeof(T) * ctx->ngrid, s));
     if (multi) {
-        auto kern = fx ? k_spread_multipoles<T, true> : k_spread_multipoles<T, false>;
-        kern<<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->dipd,
-                                                       (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, g, pc,
-                                                       ctx->stb, (const T4 *)ctx->stw);
+        auto kern = fx ? k_spread_multipoles5<T, true> : k_spread_multipoles5<T, false>;
+        kern<<<lane5_blocks(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->dipd,
+                                                        (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, g, pc,
+                                                        ctx->stb, (const T4 *)ctx->stw);
     } else {
-        auto kern = fx ? k_spread_dipoles<T, true> : k_spread_dipoles<T, false>;
-        kern<<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
-            ctx->stb, (const T4 *)ctx->stw, (const T4 *)src, g, pc);
+        const int th = ctx->tune_pme_threads;
+        auto kern = fx ? k_spread_dipoles5<T, true> : k_spread_dipoles5<T, false>;
+        kern<<<lane5_blocks(ctx->n, th), th, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T4 *)src, g, pc);
     }
     AP_CUDA(cudaGetLastError());
     if (fx) {
@@ -459,10 +530,7 @@ int multipole_field_t(ap_ctx *ctx, cudaStream_t s) {
     if (r) return r;
     r = fft_roundtrip<T>(ctx, bf, (T *)ctx->grid, (T *)ctx->grid2, s);
     if (r) return r;
-    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
-        ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid2, (T *)ctx->rec, ctx->n_pad, pc);
-    AP_CUDA(cudaGetLastError());
-    return AP_OK;
+    return gather_launch<T>(ctx, (const T *)ctx->grid2, (T *)ctx->rec, s);
 }
 
 template <class T>
@@ -473,10 +541,7 @@ int dipole_field_t(ap_ctx *ctx, const void *p, void *rec_out, const PmeBufs &bf,
     if (r) return r;
     r = fft_roundtrip<T>(ctx, bf, (T *)bf.grid, (T *)bf.grid, s);
     if (r) return r;
-    k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
-        ctx->stb, (const T4 *)ctx->stw, (const T *)bf.grid, (T *)rec_out, ctx->n_pad, pc);
-    AP_CUDA(cudaGetLastError());
-    return AP_OK;
+    return gather_launch<T>(ctx, (const T *)bf.grid, (T *)rec_out, s);
 }
 
 // Structure-factor share of the virial. A homogeneous strain leaves the B-spline moduli and
@@ -616,9 +681,7 @@ int stage_t(ap_ctx *ctx, int stage, cudaStream_t s) {
                                                                          ctx->ncgrid);
         break;
     case 2:
-        k_gather_field<T><<<ap_grid_for(ctx->n, ctx->tune_pme_threads), ctx->tune_pme_threads, 0, s>>>(
-            ctx->stb, (const T4 *)ctx->stw, (const T *)ctx->grid, (T *)ctx->rec, ctx->n_pad, pc);
-        break;
+        return gather_launch<T>(ctx, (const T *)ctx->grid, (T *)ctx->rec, s);
     case 3:
         return spread_t<T>(ctx, own_bufs(ctx), nullptr, true, s);
     case 4:
