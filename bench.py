@@ -54,10 +54,11 @@ FLOPS_PER_PAIR_MATVEC = 104
 FLOPS_PER_PAIR_FIELD = 174
 FLOPS_PER_PAIR_FORCES = 467
 MLP_FLOPS_PER_ATOM = 2 * (16 * 128 + 128 * 128 + 128 * 3)
-# bytes per slot of one PCG iteration's vector kernels: direction (r, alpha, p in/out),
-# q = A p (p, diagonal, real and reciprocal fields, q out, accumulator clear), update
-# (p, q, alpha, mu and r in/out)
-PCG_VECTOR_BYTES_PER_SLOT = 64 + 108 + 144
+# bytes per slot of one PCG iteration's vector kernels in the mixed mode (FP32 vectors as one
+# float4 per slot, the diagonal and alpha as a float2): direction (r, diagonal/alpha, p in/out),
+# q = A p (p, diagonal/alpha, FP64 real-space and FP32 reciprocal fields, q out, accumulator
+# clear), update (p, q, diagonal/alpha, mu and r in/out)
+PCG_VECTOR_BYTES_PER_SLOT = 56 + 100 + 104
 WORKLOAD = "water_96000_atoms_98.7A_grid100_rc7+2_mixed_pcg1e-5"
 HEADLINE_GUESS = "learned+adaptive"
 GUESS_TEXT = {

@@ -34,7 +34,7 @@ void free_all(ap_ctx *c) {
                     c->tile_off, c->chunk_j, c->chunk_pos, c->chunk_src, c->chunk_mask, c->chunk_flag, c->nchunk,
                     c->work, c->n_work, c->red_part, c->pmask, c->pmask_t, c->mlp_feat, c->mlp_y, c->smask, c->smask_t, c->pstart, c->sstart, c->e1s,
                     c->dg, c->stb, c->stw, c->grid_fx, c->work_off,
-                    c->hist_count, c->item_start, c->scan_tmp};
+                    c->hist_count, c->item_start, c->scan_tmp, c->mu_f, c->r_f, c->q_f, c->dga_f};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     diis_release(c);
@@ -97,6 +97,10 @@ int create_impl(ap_ctx *ctx, const ap_params *P, void *stream) {
     if ((r = dalloc(ctx, &ctx->r, sizeof(double) * 3 * np))) return r;
     if ((r = dalloc(ctx, &ctx->qv, sizeof(double) * 3 * np))) return r;
     if ((r = dalloc(ctx, &ctx->dg, sizeof(double) * np))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->mu_f, sizeof(float4) * np))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->r_f, sizeof(float4) * np))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->q_f, sizeof(float4) * np))) return r;
+    if ((r = dalloc(ctx, (char **)&ctx->dga_f, sizeof(float2) * np))) return r;
     if ((r = dalloc(ctx, &ctx->hist_count, sizeof(int)))) return r;
     if ((r = dalloc(ctx, (char **)&ctx->p, 4 * es * np))) return r;
     if ((r = dalloc(ctx, &ctx->st, sizeof(PcgState)))) return r;

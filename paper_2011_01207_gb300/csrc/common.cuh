@@ -136,6 +136,9 @@ struct ap_ctx {
     // PCG
     double *mu = nullptr, *r = nullptr, *qv = nullptr;   // [3][n_pad]
     double *dg = nullptr;     // [n_pad] diagonal of A: 1/alpha - self coefficient (0 for padding)
+    // mixed and fixed-point modes: the PCG vectors in FP32, one float4 (x, y, z, unused) per slot
+    float4 *mu_f = nullptr, *r_f = nullptr, *q_f = nullptr;   // [n_pad] each
+    float2 *dga_f = nullptr;  // [n_pad] (1/alpha - self coefficient, alpha), 0 for padding
     int *hist_count = nullptr;   // device: steps held by a batch step's trajectory history
     void *p = nullptr;        // T4 [n_pad] search direction
     PcgState *st = nullptr;   // device

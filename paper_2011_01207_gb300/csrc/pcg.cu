@@ -8,16 +8,19 @@
 //          beta = (r.z)_new/(r.z)_old;  p = z + beta p
 // with A = alpha^-1 - T and T p = T_real p (blocked pair kernel) + T_rec p (PME) + self p.
 //
-// Vectors mu, r, q are FP64; the search direction p is stored in T for the pair and PME
-// kernels; dot products and norms are FP64 block reductions finished with FP64 atomics.
+// FP64 mode: vectors mu, r, q in FP64, the search direction p in T for the pair and PME
+// kernels, dot products and norms as FP64 block sums. Mixed and fixed modes: every vector in
+// FP32 with FP64-grade sums of the dot products and norms (the kernels with the _f suffix).
 // The convergence test runs on the device: the update kernel's last block decides, and
 // inside a CUDA graph it drives a conditional WHILE node, so a whole solve is one graph
 // launch with no host round trip per iteration (the paper's host-synchronous loop is what
 // made DHFR drop to 12 ns/day, Sec. 3).
 #include "common.cuh"
+#include "pair_math.cuh"
 
 #include <cmath>
 #include <cstdlib>
+#include <type_traits>
 
 void unsort3(ap_ctx *ctx, const double *src, double *out, cudaStream_t s);
 
@@ -262,6 +265,239 @@ __global__ void k_update(const typename V4<T>::type *__restrict__ p, const doubl
     if (threadIdx.x == 0) finish_iteration(st, rzn, zzt, n, h, use_cond);
 }
 
+// ---------------------------------------------------------------------------------------
+// The same iteration with the vectors in FP32 (mixed and fixed-point modes): mu, r, q and p
+// stored as float4 per slot, the diagonal and alpha as a float2, every vector operation in
+// FP32. The dot products and norms keep FP64-grade sums without FP64 arithmetic per slot:
+// each product is split exactly into its rounded value and error (fma), both summed in a
+// compensated FP32 pair (TwoSum, ~48 bits) per thread, warp and block; the block's pair is
+// converted exactly to FP64 and the last block adds the partials in FP64 in a fixed order.
+// (GB300 issues FP64 at a small fraction of its FP32 rate; the FP64 kernels above spent a
+// few microseconds per iteration on it.)
+
+// a += x y, the product carried exactly as its rounded value and rounding error
+__device__ __forceinline__ void f2_add_prod(F2 &a, float x, float y) {
+    const float p = x * y;
+    f2_add(a, p);
+    a.lo += fmaf(x, y, -p);
+}
+
+// block-wide sums of two compensated pairs; thread 0 gets them in FP64
+template <int NT_>
+__device__ __forceinline__ void block_sum2_f2(F2 a, F2 b, double &da, double &db) {
+    __shared__ float sh[4][NT_ / 32];
+    for (int off = 16; off; off >>= 1) {
+        const float ah = __shfl_xor_sync(0xffffffffu, a.hi, off), al = __shfl_xor_sync(0xffffffffu, a.lo, off);
+        const float bh = __shfl_xor_sync(0xffffffffu, b.hi, off), bl = __shfl_xor_sync(0xffffffffu, b.lo, off);
+        f2_add(a, ah);
+        a.lo += al;
+        f2_add(b, bh);
+        b.lo += bl;
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sh[0][w] = a.hi;
+        sh[1][w] = a.lo;
+        sh[2][w] = b.hi;
+        sh[3][w] = b.lo;
+    }
+    __syncthreads();
+    if (w == 0) {
+        F2 x, y;
+        x.hi = l < NT_ / 32 ? sh[0][l] : 0.f;
+        x.lo = l < NT_ / 32 ? sh[1][l] : 0.f;
+        y.hi = l < NT_ / 32 ? sh[2][l] : 0.f;
+        y.lo = l < NT_ / 32 ? sh[3][l] : 0.f;
+        for (int off = 16; off; off >>= 1) {
+            const float xh = __shfl_xor_sync(0xffffffffu, x.hi, off), xl = __shfl_xor_sync(0xffffffffu, x.lo, off);
+            const float yh = __shfl_xor_sync(0xffffffffu, y.hi, off), yl = __shfl_xor_sync(0xffffffffu, y.lo, off);
+            f2_add(x, xh);
+            x.lo += xl;
+            f2_add(y, yh);
+            y.lo += yl;
+        }
+        da = f2d_exact(x.hi) + f2d_exact(x.lo);
+        db = f2d_exact(y.hi) + f2d_exact(y.lo);
+    }
+}
+
+// an accumulator slot of the real-space product in FP32 (FP64 or, fixed, 2^-34 fixed point:
+// the integer's conversion and an exact power-of-two scale round once, as the FP64 path)
+__device__ __forceinline__ float acc_f32(const double *acc, size_t k, int fixed) {
+    return fixed ? (float)reinterpret_cast<const long long *>(acc)[k] * (1.0f / 17179869184.0f) : (float)acc[k];
+}
+
+// mu_0 (FP32) and the matvec input p := mu_0; the diagonal 1/alpha - self and alpha as FP32
+__global__ void k_init_guess_f(const double *__restrict__ guess, const double *__restrict__ E,
+                               const double *__restrict__ alpha, const int *__restrict__ perm, int n, int n_pad,
+                               float4 *__restrict__ mu, float4 *__restrict__ p, double self_coef,
+                               float2 *__restrict__ dga) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    const double al = alpha[s];
+    dga[s] = make_float2(al > 0.0 ? (float)(1.0 / al - self_coef) : 0.f, (float)al);
+    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s < n) {
+        if (guess) {
+            const int i = perm[s];
+            m = make_float4((float)guess[3 * i], (float)guess[3 * i + 1], (float)guess[3 * i + 2], 0.f);
+        } else {
+            m = make_float4((float)(al * E[s]), (float)(al * E[n_pad + s]), (float)(al * E[2 * n_pad + s]), 0.f);
+        }
+    }
+    mu[s] = m;
+    p[s] = m;
+}
+
+// r_0 = E - A mu_0 (formed in FP64 once per solve, stored in FP32), partial r.z and z.z of the
+// stored r; clears acc and p. The last block sets the initial state.
+__global__ void k_init_residual_f(const double *__restrict__ E, const float2 *__restrict__ dga,
+                                  const float4 *__restrict__ mu, double *__restrict__ acc,
+                                  const float *__restrict__ rec, int n_pad, float4 *__restrict__ r,
+                                  float4 *__restrict__ p, double *__restrict__ part, int fixed, PcgState *st, int n,
+                                  double tol, int max_iter) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    F2 rz = {0.f, 0.f}, zz = {0.f, 0.f};
+    if (s < n_pad) {
+        const float2 d = dga[s];
+        const float4 m = mu[s];
+        const float mv[3] = {m.x, m.y, m.z};
+        float rv[3];
+        for (int c = 0; c < 3; ++c) {
+            const int k = c * n_pad + s;
+            const double Amu = d.y > 0.f ? (double)mv[c] * d.x - acc_value(acc, k, fixed) - (double)rec[k] : 0.0;
+            rv[c] = d.y > 0.f ? (float)(E[k] - Amu) : 0.f;
+            acc[k] = 0.0;
+            const float z = d.y * rv[c];
+            f2_add_prod(rz, rv[c], z);
+            f2_add_prod(zz, z, z);
+        }
+        r[s] = make_float4(rv[0], rv[1], rv[2], 0.f);
+        p[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    double brz = 0.0, bzz = 0.0;
+    block_sum2_f2<NT>(rz, zz, brz, bzz);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = brz;
+        part[gridDim.x + blockIdx.x] = bzz;
+    }
+    if (!last_block(&st->blocks_done)) return;
+    double rzt, zzt;
+    sum_partials2(part, gridDim.x, rzt, zzt);
+    if (threadIdx.x != 0) return;
+    const double eps = AP_DEBYE * sqrt(zzt / n);
+    st->rz = rzt;
+    st->eps = eps;
+    st->eps0 = eps;
+    st->tol = tol;
+    st->iter = 0;
+    st->max_iter = max_iter;
+    st->beta = 0.0;
+    st->gamma = 0.0;
+    st->nonfinite = !isfinite(eps);
+    st->done = (eps <= tol) || st->nonfinite;
+    st->status = st->nonfinite ? AP_ERR_NONFINITE : AP_OK;
+    st->pq = st->rz_new = st->zz = 0.0;
+    st->guard = 0;
+}
+
+// p = alpha r + beta p
+__global__ void k_direction_f(const float4 *__restrict__ r, const float2 *__restrict__ dga, int n_pad,
+                              float4 *__restrict__ p, const PcgState *__restrict__ st) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    const float b = (float)st->beta, a = dga[s].y;
+    const float4 rv = r[s];
+    float4 v = p[s];
+    v.x = fmaf(a, rv.x, b * v.x);
+    v.y = fmaf(a, rv.y, b * v.y);
+    v.z = fmaf(a, rv.z, b * v.z);
+    p[s] = v;
+}
+
+// q = (1/alpha - self) p - T_real p - T_rec p; partial p.q; clears acc. The last block sets
+// gamma = (r.z) / (p.q).
+__global__ void k_apply_f(const float4 *__restrict__ p, const float2 *__restrict__ dga, double *__restrict__ acc,
+                          const float *__restrict__ rec, int n_pad, float4 *__restrict__ q, double *__restrict__ part,
+                          PcgState *st, int fixed) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    F2 pq = {0.f, 0.f}, none = {0.f, 0.f};
+    if (s < n_pad) {
+        const float d = dga[s].x;
+        const float4 v = p[s];
+        const float pv[3] = {v.x, v.y, v.z};
+        float qv[3];
+        for (int c = 0; c < 3; ++c) {
+            const int k = c * n_pad + s;
+            qv[c] = fmaf(pv[c], d, -acc_f32(acc, k, fixed)) - rec[k];
+            acc[k] = 0.0;
+            f2_add_prod(pq, pv[c], qv[c]);
+        }
+        q[s] = make_float4(qv[0], qv[1], qv[2], 0.f);
+    }
+    double bpq = 0.0, unused = 0.0;
+    block_sum2_f2<NT>(pq, none, bpq, unused);
+    if (threadIdx.x == 0) part[blockIdx.x] = bpq;
+    if (!last_block(&st->blocks_done)) return;
+    double tot = 0.0, dummy2 = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += NT) tot += __ldcg(part + k);
+    block_sum2<NT>(tot, dummy2);
+    if (threadIdx.x == 0) {
+        st->pq = tot;
+        st->gamma = st->rz / tot;
+    }
+}
+
+// mu += gamma p; r -= gamma q; partial r.z and z.z; the last block closes the iteration
+__global__ void k_update_f(const float4 *__restrict__ p, const float4 *__restrict__ q,
+                           const float2 *__restrict__ dga, int n_pad, float4 *__restrict__ mu,
+                           float4 *__restrict__ r, PcgState *st, double *__restrict__ part, int n,
+                           cudaGraphConditionalHandle h, int use_cond) {
+    const float g = (float)st->gamma;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    F2 rz = {0.f, 0.f}, zz = {0.f, 0.f};
+    if (s < n_pad) {
+        const float a = dga[s].y;
+        const float4 pv = p[s], qv = q[s];
+        float4 m = mu[s], rv = r[s];
+        m.x = fmaf(g, pv.x, m.x);
+        m.y = fmaf(g, pv.y, m.y);
+        m.z = fmaf(g, pv.z, m.z);
+        rv.x = fmaf(-g, qv.x, rv.x);
+        rv.y = fmaf(-g, qv.y, rv.y);
+        rv.z = fmaf(-g, qv.z, rv.z);
+        mu[s] = m;
+        r[s] = rv;
+        const float rr[3] = {rv.x, rv.y, rv.z};
+        for (int c = 0; c < 3; ++c) {
+            const float z = a * rr[c];
+            f2_add_prod(rz, rr[c], z);
+            f2_add_prod(zz, z, z);
+        }
+    }
+    double brz = 0.0, bzz = 0.0;
+    block_sum2_f2<NT>(rz, zz, brz, bzz);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = brz;
+        part[gridDim.x + blockIdx.x] = bzz;
+    }
+    if (!last_block(&st->blocks_done2)) return;
+    double rzn, zzt;
+    sum_partials2(part, gridDim.x, rzn, zzt);
+    if (threadIdx.x == 0) finish_iteration(st, rzn, zzt, n, h, use_cond);
+}
+
+// the FP32 dipoles to the caller's order in FP64
+__global__ void k_unsort_f4(const float4 *__restrict__ src, const int *__restrict__ iperm, int n,
+                            double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 v = src[iperm[i]];
+    out[3 * i] = v.x;
+    out[3 * i + 1] = v.y;
+    out[3 * i + 2] = v.z;
+}
+
 // T p: reciprocal branch on `aux`, real space on `main`, joined back into `main`
 template <class T>
 int matvec_into(ap_ctx *ctx, const void *p, cudaStream_t main, cudaStream_t aux) {
@@ -286,15 +522,26 @@ int enqueue_iteration(ap_ctx *ctx, cudaGraphConditionalHandle h, int use_cond, c
                       cudaStream_t aux) {
     typedef typename V4<T>::type T4;
     const int nb = ap_grid_for(ctx->n_pad, NT);
-    k_direction<T><<<nb, NT, 0, main>>>(ctx->r, ctx->alpha, ctx->n_pad, (T4 *)ctx->p, ctx->st);
-    AP_CUDA(cudaGetLastError());
-    int rc = matvec_into<T>(ctx, ctx->p, main, aux);
-    if (rc) return rc;
     double *part_pq = ctx->red_part, *part_rz = ctx->red_part + nb;
-    k_apply<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->dg, ctx->acc, (const T *)ctx->rec, ctx->n_pad, ctx->qv,
-                                     part_pq, ctx->st, ctx->fixed);
-    k_update<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
-                                      part_rz, ctx->n, h, use_cond);
+    if constexpr (std::is_same<T, float>::value) {
+        k_direction_f<<<nb, NT, 0, main>>>(ctx->r_f, ctx->dga_f, ctx->n_pad, (float4 *)ctx->p, ctx->st);
+        AP_CUDA(cudaGetLastError());
+        int rc = matvec_into<T>(ctx, ctx->p, main, aux);
+        if (rc) return rc;
+        k_apply_f<<<nb, NT, 0, main>>>((const float4 *)ctx->p, ctx->dga_f, ctx->acc, (const float *)ctx->rec,
+                                       ctx->n_pad, ctx->q_f, part_pq, ctx->st, ctx->fixed);
+        k_update_f<<<nb, NT, 0, main>>>((const float4 *)ctx->p, ctx->q_f, ctx->dga_f, ctx->n_pad, ctx->mu_f, ctx->r_f,
+                                        ctx->st, part_rz, ctx->n, h, use_cond);
+    } else {
+        k_direction<T><<<nb, NT, 0, main>>>(ctx->r, ctx->alpha, ctx->n_pad, (T4 *)ctx->p, ctx->st);
+        AP_CUDA(cudaGetLastError());
+        int rc = matvec_into<T>(ctx, ctx->p, main, aux);
+        if (rc) return rc;
+        k_apply<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->dg, ctx->acc, (const T *)ctx->rec, ctx->n_pad,
+                                         ctx->qv, part_pq, ctx->st, ctx->fixed);
+        k_update<T><<<nb, NT, 0, main>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r,
+                                          ctx->st, part_rz, ctx->n, h, use_cond);
+    }
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -365,15 +612,30 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
     cudaStream_t s = ctx->s0;
     AP_CUDA(cudaMemsetAsync(ctx->st, 0, sizeof(PcgState), s));
     AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, s));
-    k_init_guess<T><<<nb, NT, 0, s>>>(d_guess, ctx->E, ctx->alpha, ctx->perm, ctx->n, ctx->n_pad, ctx->mu,
-                                       (T4 *)ctx->p, self_coef(ctx), ctx->dg);
+    constexpr bool F32 = std::is_same<T, float>::value;   // FP32 vectors (mixed and fixed modes)
+    if (F32)
+        k_init_guess_f<<<nb, NT, 0, s>>>(d_guess, ctx->E, ctx->alpha, ctx->perm, ctx->n, ctx->n_pad, ctx->mu_f,
+                                         (float4 *)ctx->p, self_coef(ctx), ctx->dga_f);
+    else
+        k_init_guess<T><<<nb, NT, 0, s>>>(d_guess, ctx->E, ctx->alpha, ctx->perm, ctx->n, ctx->n_pad, ctx->mu,
+                                           (T4 *)ctx->p, self_coef(ctx), ctx->dg);
     AP_CUDA(cudaGetLastError());
     int rc = matvec_into<T>(ctx, ctx->p);
     if (rc) return rc;
-    k_init_residual<T><<<nb, NT, 0, s>>>(ctx->E, ctx->alpha, ctx->mu, ctx->acc, (const T *)ctx->rec, ctx->dg,
-                                          ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->red_part, ctx->fixed, ctx->st,
-                                          ctx->n, tol, max_iter);
+    if (F32)
+        k_init_residual_f<<<nb, NT, 0, s>>>(ctx->E, ctx->dga_f, ctx->mu_f, ctx->acc, (const float *)ctx->rec,
+                                            ctx->n_pad, ctx->r_f, (float4 *)ctx->p, ctx->red_part, ctx->fixed,
+                                            ctx->st, ctx->n, tol, max_iter);
+    else
+        k_init_residual<T><<<nb, NT, 0, s>>>(ctx->E, ctx->alpha, ctx->mu, ctx->acc, (const T *)ctx->rec, ctx->dg,
+                                              ctx->n_pad, ctx->r, (T4 *)ctx->p, ctx->red_part, ctx->fixed, ctx->st,
+                                              ctx->n, tol, max_iter);
     AP_CUDA(cudaGetLastError());
+    // the solution to the caller's order, in FP64
+    auto unsort_mu = [&](cudaStream_t st) {
+        if (F32) k_unsort_f4<<<ap_grid_for(ctx->n, 256), 256, 0, st>>>(ctx->mu_f, ctx->iperm, ctx->n, d_mu);
+        else unsort3(ctx, ctx->mu, d_mu, st);
+    };
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     AP_CUDA(cudaStreamIsCapturing(s, &cap));
     if (cap == cudaStreamCaptureStatusActive) {
@@ -403,7 +665,7 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
         cudaError_t ec = cudaStreamEndCapture(ctx->s2, &captured);
         if (rc) return rc;
         if (ec != cudaSuccess) return ap_fail(ctx, AP_ERR_CUDA, std::string("body capture: ") + cudaGetErrorString(ec));
-        unsort3(ctx, ctx->mu, d_mu, s);
+        unsort_mu(s);
         AP_CUDA(cudaGetLastError());
         return AP_OK;
     }
@@ -426,7 +688,7 @@ int solve_t(ap_ctx *ctx, const double *d_guess, double tol, int max_iter, double
             if (rc) return rc;
         }
     }
-    unsort3(ctx, ctx->mu, d_mu, s);
+    unsort_mu(s);
     AP_CUDA(cudaGetLastError());
     if (info) {
         AP_CUDA(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
@@ -463,12 +725,11 @@ int pcg_vectors_launch(ap_ctx *ctx, cudaStream_t s) {
         k_update<double><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
                                            part_rz, ctx->n, 0, 0);
     } else {
-        typedef V4<float>::type T4;
-        k_direction<float><<<nb, NT, 0, s>>>(ctx->r, ctx->alpha, ctx->n_pad, (T4 *)ctx->p, ctx->st);
-        k_apply<float><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->dg, ctx->acc, (const float *)ctx->rec, ctx->n_pad,
-                                         ctx->qv, part_pq, ctx->st, ctx->fixed);
-        k_update<float><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
-                                          part_rz, ctx->n, 0, 0);
+        k_direction_f<<<nb, NT, 0, s>>>(ctx->r_f, ctx->dga_f, ctx->n_pad, (float4 *)ctx->p, ctx->st);
+        k_apply_f<<<nb, NT, 0, s>>>((const float4 *)ctx->p, ctx->dga_f, ctx->acc, (const float *)ctx->rec, ctx->n_pad,
+                                    ctx->q_f, part_pq, ctx->st, ctx->fixed);
+        k_update_f<<<nb, NT, 0, s>>>((const float4 *)ctx->p, ctx->q_f, ctx->dga_f, ctx->n_pad, ctx->mu_f, ctx->r_f,
+                                     ctx->st, part_rz, ctx->n, 0, 0);
     }
     AP_CUDA(cudaGetLastError());
     return AP_OK;
