@@ -81,7 +81,7 @@ __device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a
 struct PairConsts2 {
     float2 ce;        // -beta^2 log2(e): e^{-beta^2 r^2} = 2^{ce r^2}
     float2 pb;        // A&S 7.1.26's p times beta: t = 1 / (1 + pb r)
-    float2 c1, c2;    // (2 beta^2)^n / (beta sqrt(pi)), n = 1, 2
+    float2 c1, c2, c3;   // (2 beta^2)^n / (beta sqrt(pi)), n = 1, 2, 3
     float2 ta;        // Thole a
     float2 nl2e;      // -log2(e)
 };
@@ -92,6 +92,7 @@ __host__ __device__ inline PairConsts2 make_consts2(const PairConsts<float> &pc)
     k.pb = make_float2(0.3275911f * pc.beta, 0.3275911f * pc.beta);
     k.c1 = make_float2(pc.c[1], pc.c[1]);
     k.c2 = make_float2(pc.c[2], pc.c[2]);
+    k.c3 = make_float2(pc.c[3], pc.c[3]);
     k.ta = make_float2(pc.thole_a, pc.thole_a);
     k.nl2e = make_float2(-l2e, -l2e);
     return k;
@@ -146,6 +147,37 @@ __device__ __forceinline__ void thole_oml(T s, T *oml) {
     if (NMAX > 1) oml[1] = (T(1) + s) * e;
     if (NMAX > 2) oml[2] = (T(1) + s + T(0.6) * s * s) * e;
     if (NMAX > 3) oml[3] = (T(1) + s + s * s * (T(18.0 / 35.0) + T(9.0 / 35.0) * s)) * e;
+}
+
+// R_1, R_2, R_3 with the scale sigma of each side (exa, exb: excluded pairs, sigma = 0, whose
+// R_n = B_n - U_n), for two pair sides at once: the terms of screened<float, 3> and
+// thole_oml<float, 3>
+__device__ __forceinline__ void radial123_x2(const PairConsts2 &k, float2 r2, float2 ww, bool exa, bool exb,
+                                             float2 &R1, float2 &R2, float2 &R3) {
+    const float2 rinv = rsqrt2(r2);
+    const float2 r = mul2(r2, rinv), rinv2 = mul2(rinv, rinv);
+    const float2 e2 = ex2_2(mul2(r2, k.ce));
+    const float2 t = rcp2(fma2(k.pb, r, splat2(1.0f)));
+    const float2 poly = mul2(t, fma2(t, fma2(t, fma2(t, fma2(t, splat2(1.061405429f), splat2(-1.453152027f)),
+                                                      splat2(1.421413741f)),
+                                             splat2(-0.284496736f)),
+                                     splat2(0.254829592f)));
+    const float2 b0 = mul2(mul2(poly, e2), rinv);
+    const float2 b1 = mul2(fma2(k.c1, e2, b0), rinv2);
+    const float2 u1 = mul2(rinv, rinv2);
+    const float2 b2 = mul2(fma2(splat2(3.0f), b1, mul2(k.c2, e2)), rinv2);
+    const float2 u2 = mul2(mul2(splat2(3.0f), u1), rinv2);
+    const float2 b3 = mul2(fma2(splat2(5.0f), b2, mul2(k.c3, e2)), rinv2);
+    const float2 u3 = mul2(mul2(splat2(5.0f), u2), rinv2);
+    const float2 s = mul2(mul2(r2, r), mul2(ww, k.ta));
+    const float2 e = ex2_2(mul2(s, k.nl2e));
+    const float2 s1 = add2(splat2(1.0f), s);
+    float2 o1 = e, o2 = mul2(s1, e), o3 = mul2(fma2(splat2(0.6f), mul2(s, s), s1), e);
+    if (exa) o1.x = o2.x = o3.x = 1.0f;
+    if (exb) o1.y = o2.y = o3.y = 1.0f;
+    R1 = sub2(b1, mul2(o1, u1));
+    R2 = sub2(b2, mul2(o2, u2));
+    R3 = sub2(b3, mul2(o3, u3));
 }
 
 // First index i in [lo, hi] with start[i] >= a, for a nondecreasing start[] with

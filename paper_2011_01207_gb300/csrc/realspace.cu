@@ -76,6 +76,157 @@ struct PfSmem {
     unsigned words[64];             // pair bits: rows of the i atoms, then columns of the j atoms
 };
 
+// One side of the permanent field: the field at the target of the source's (q, d, Q), with
+// R = x_target - x_source and the pair's exclusion bit (sigma = 0 in R_n)
+template <class T>
+__device__ __forceinline__ void pf_contract(T R1, T R2, T R3, T dx, T dy, T dz, const typename V4<T>::type &m,
+                                            const typename V4<T>::type &qa, T qyz, T qzz, T &g0, T &g1, T &g2) {
+    const T dR = m.y * dx + m.z * dy + m.w * dz;
+    const T Qx = qa.x * dx + qa.y * dy + qa.z * dz;
+    const T Qy = qa.y * dx + qa.w * dy + qyz * dz;
+    const T Qz = qa.z * dx + qyz * dy + qzz * dz;
+    const T RQR = Qx * dx + Qy * dy + Qz * dz;
+    const T fac = m.x * R1 + dR * R2 + RQR * R3 * T(1.0 / 3.0);
+    const T q2 = T(2.0 / 3.0) * R2;
+    g0 = fac * dx - R1 * m.y - q2 * Qx;
+    g1 = fac * dy - R1 * m.z - q2 * Qy;
+    g2 = fac * dz - R1 * m.w - q2 * Qz;
+}
+
+template <class T, bool MINIMG, class SM>
+__device__ __forceinline__ void pf_side(SM &S, const PairConsts<T> &pc, const typename V4<T>::type &self, int tg,
+                                        int src, T &g0, T &g1, T &g2) {
+    typedef typename V4<T>::type T4;
+    const int sl = src & 31;   // the source's lane within its half
+    const bool exb = tg < 32 ? (S.ex[tg] >> sl) & 1u : (S.ex[sl] >> (tg - 32)) & 1u;
+    const T4 o = S.pos[src], m = S.qd[src], qa = S.qa[src];
+    const T qyz = S.qb[0][src], qzz = S.qb[1][src];
+    T dx, dy, dz;
+    pair_vector<T, MINIMG>(pc, self.x, self.y, self.z, o.x, o.y, o.z, T(0), T(0), T(0), dx, dy, dz);
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+    T B[3], U[3], oml[3];
+    screened<T, 3>(pc, r, rinv, rinv2, B, U);
+    thole_oml<T, 3>(pc.thole_a * r2 * r * self.w * o.w, oml);
+    const T R1 = B[0] - (exb ? U[0] : oml[0] * U[0]);
+    const T R2 = B[1] - (exb ? U[1] : oml[1] * U[1]);
+    const T R3 = B[2] - (exb ? U[2] : oml[2] * U[2]);
+    pf_contract<T>(R1, R2, R3, dx, dy, dz, m, qa, qyz, qzz, g0, g1, g2);
+}
+
+// the walk over a lane's share of the item's sides, as matvec_walk (plain stores on leaving a
+// target, atomics for the last one)
+template <class T, bool MINIMG, class PA, class SM>
+__device__ __forceinline__ void pf_walk(SM &S, SideSlice &slice, const PairConsts<T> &pc) {
+    typedef typename V4<T>::type T4;
+    int cur = -1;
+    T4 self;
+    self.x = self.y = self.z = self.w = T(0);
+    T f0 = 0, f1 = 0, f2 = 0;
+    while (slice.left > 0) {
+        int tg, src;
+        slice.next(S.words, tg, src);
+        if (tg != cur) {
+            if (cur >= 0) {
+                PA::shared_put(&S.acc[0][cur], f0);
+                PA::shared_put(&S.acc[1][cur], f1);
+                PA::shared_put(&S.acc[2][cur], f2);
+            }
+            f0 = f1 = f2 = T(0);
+            cur = tg;
+            self = S.pos[tg];
+        }
+        T g0, g1, g2;
+        pf_side<T, MINIMG>(S, pc, self, tg, src, g0, g1, g2);
+        f0 += g0;
+        f1 += g1;
+        f2 += g2;
+    }
+    __syncwarp();   // the plain stores land before the last targets are added
+    if (cur >= 0) {
+        PA::shared_add(&S.acc[0][cur], f0);
+        PA::shared_add(&S.acc[1][cur], f1);
+        PA::shared_add(&S.acc[2][cur], f2);
+    }
+}
+
+// FP32: two consecutive sides per step, their R_1..R_3 in packed f32x2 arithmetic
+// (radial123_x2), the multipole contractions per side; an odd last side takes the scalar path
+template <bool MINIMG, class PA, class SM>
+__device__ __forceinline__ void pf_walk_x2(SM &S, SideSlice &slice, const PairConsts<float> &pc,
+                                           const PairConsts2 &k) {
+    int cur = -1;
+    float4 self = make_float4(0.f, 0.f, 0.f, 0.f);
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    auto leave = [&](int next, const float4 &nself) {
+        if (cur >= 0) {
+            PA::shared_put(&S.acc[0][cur], f0);
+            PA::shared_put(&S.acc[1][cur], f1);
+            PA::shared_put(&S.acc[2][cur], f2);
+        }
+        cur = next;
+        self = nself;
+    };
+    while (slice.left > 1) {
+        int ta, sa, tb, sb;
+        slice.next(S.words, ta, sa);
+        slice.next(S.words, tb, sb);
+        if (ta != cur) {
+            leave(ta, S.pos[ta]);
+            f0 = f1 = f2 = 0.f;
+        }
+        const float4 selfb = tb == ta ? self : S.pos[tb];
+        const int la = sa & 31, lb = sb & 31;
+        const bool exa = ta < 32 ? (S.ex[ta] >> la) & 1u : (S.ex[la] >> (ta - 32)) & 1u;
+        const bool exb = tb < 32 ? (S.ex[tb] >> lb) & 1u : (S.ex[lb] >> (tb - 32)) & 1u;
+        const float4 oa = S.pos[sa], ob = S.pos[sb];
+        float dxa, dya, dza, dxb, dyb, dzb;
+        pair_vector<float, MINIMG>(pc, self.x, self.y, self.z, oa.x, oa.y, oa.z, 0.f, 0.f, 0.f, dxa, dya, dza);
+        pair_vector<float, MINIMG>(pc, selfb.x, selfb.y, selfb.z, ob.x, ob.y, ob.z, 0.f, 0.f, 0.f, dxb, dyb, dzb);
+        const float2 dx = make_float2(dxa, dxb), dy = make_float2(dya, dyb), dz = make_float2(dza, dzb);
+        const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+        float2 R1, R2, R3;
+        radial123_x2(k, r2, make_float2(self.w * oa.w, selfb.w * ob.w), exa, exb, R1, R2, R3);
+        float g0, g1, g2;
+        pf_contract<float>(R1.x, R2.x, R3.x, dxa, dya, dza, S.qd[sa], S.qa[sa], S.qb[0][sa], S.qb[1][sa], g0, g1,
+                           g2);
+        f0 += g0;
+        f1 += g1;
+        f2 += g2;
+        pf_contract<float>(R1.y, R2.y, R3.y, dxb, dyb, dzb, S.qd[sb], S.qa[sb], S.qb[0][sb], S.qb[1][sb], g0, g1,
+                           g2);
+        if (tb == cur) {
+            f0 += g0;
+            f1 += g1;
+            f2 += g2;
+        } else {
+            leave(tb, selfb);
+            f0 = g0;
+            f1 = g1;
+            f2 = g2;
+        }
+    }
+    if (slice.left > 0) {
+        int tg, src;
+        slice.next(S.words, tg, src);
+        if (tg != cur) {
+            leave(tg, S.pos[tg]);
+            f0 = f1 = f2 = 0.f;
+        }
+        float g0, g1, g2;
+        pf_side<float, MINIMG>(S, pc, self, tg, src, g0, g1, g2);
+        f0 += g0;
+        f1 += g1;
+        f2 += g2;
+    }
+    __syncwarp();   // the plain stores land before the last targets are added
+    if (cur >= 0) {
+        PA::shared_add(&S.acc[0][cur], f0);
+        PA::shared_add(&S.acc[1][cur], f1);
+        PA::shared_add(&S.acc[2][cur], f2);
+    }
+}
+
 template <class T>
 __host__ __device__ constexpr int pf_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
@@ -89,6 +240,8 @@ __global__ void __launch_bounds__(128, 8) k_perm_field(
     __shared__ PfSmem<T, typename PA::shared_t> smem[pf_warps<T>()];
     PfSmem<T, typename PA::shared_t> &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
+    PairConsts2 k2;
+    if constexpr (std::is_same<T, float>::value) k2 = make_consts2(pc);
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
     long t0, t1;
@@ -159,59 +312,8 @@ __global__ void __launch_bounds__(128, 8) k_perm_field(
         SideSlice slice;
         slice.load(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], wa.pstart[(size_t)t * 32 + lane],
                  lane, S.words);
-        // A lane that moves on from a target is the only lane that ever leaves it (the
-        // shares are contiguous runs of the target-sorted sides; any other lane with sides
-        // of that target holds it as its last one): a plain store, and the last target of
-        // every lane is added atomically after the walk.
-        int cur = -1;
-        T4 self;
-        self.x = self.y = self.z = self.w = T(0);
-        T f0 = 0, f1 = 0, f2 = 0;
-        while (slice.left > 0) {
-            int tg, src;
-            slice.next(S.words, tg, src);
-            const int sl = src & 31;   // the source's lane within its half
-            if (tg != cur) {
-                if (cur >= 0) {
-                    PA::shared_put(&S.acc[0][cur], f0);
-                    PA::shared_put(&S.acc[1][cur], f1);
-                    PA::shared_put(&S.acc[2][cur], f2);
-                }
-                f0 = f1 = f2 = T(0);
-                cur = tg;
-                self = S.pos[tg];
-            }
-            const bool exb = tg < 32 ? (S.ex[tg] >> sl) & 1u : (S.ex[sl] >> (tg - 32)) & 1u;
-            const T4 o = S.pos[src], m = S.qd[src], qa = S.qa[src];
-            const T qyz = S.qb[0][src], qzz = S.qb[1][src];
-            T dx, dy, dz;
-            pair_vector<T, MINIMG>(pc, self.x, self.y, self.z, o.x, o.y, o.z, T(0), T(0), T(0), dx, dy, dz);
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
-            T B[3], U[3], oml[3];
-            screened<T, 3>(pc, r, rinv, rinv2, B, U);
-            thole_oml<T, 3>(pc.thole_a * r2 * r * self.w * o.w, oml);
-            const T R1 = B[0] - (exb ? U[0] : oml[0] * U[0]);
-            const T R2 = B[1] - (exb ? U[1] : oml[1] * U[1]);
-            const T R3 = B[2] - (exb ? U[2] : oml[2] * U[2]);
-            // field at the target of the source's (q, d, Q), R = x_target - x_source
-            const T dR = m.y * dx + m.z * dy + m.w * dz;
-            const T Qx = qa.x * dx + qa.y * dy + qa.z * dz;
-            const T Qy = qa.y * dx + qa.w * dy + qyz * dz;
-            const T Qz = qa.z * dx + qyz * dy + qzz * dz;
-            const T RQR = Qx * dx + Qy * dy + Qz * dz;
-            const T fac = m.x * R1 + dR * R2 + RQR * R3 * T(1.0 / 3.0);
-            const T q2 = T(2.0 / 3.0) * R2;
-            f0 += fac * dx - R1 * m.y - q2 * Qx;
-            f1 += fac * dy - R1 * m.z - q2 * Qy;
-            f2 += fac * dz - R1 * m.w - q2 * Qz;
-        }
-        __syncwarp();   // the plain stores land before the last targets are added
-        if (cur >= 0) {
-            PA::shared_add(&S.acc[0][cur], f0);
-            PA::shared_add(&S.acc[1][cur], f1);
-            PA::shared_add(&S.acc[2][cur], f2);
-        }
+        if constexpr (std::is_same<T, float>::value) pf_walk_x2<MINIMG, PA>(S, slice, pc, k2);
+        else pf_walk<T, MINIMG, PA>(S, slice, pc);
         __syncwarp();
         PA::run_add(ax, S.acc[0][lane]);
         PA::run_add(ay, S.acc[1][lane]);
@@ -417,6 +519,9 @@ __global__ void __launch_bounds__(128, mv_blocks_per_sm<T>()) k_matvec(
     PA::run_zero(ay);
     PA::run_zero(az);
     for (long t = t0; t < t1; ++t) {
+        // the short-range field skips, before staging anything, the items whose atoms are all
+        // farther apart than the short radius; block I's sums carry over
+        if (SHORT && !__any_sync(0xffffffffu, (wa.sstart[(size_t)t * 32 + lane] >> 11) != 0u)) continue;
         const int2 it = wa.work[t];
         __syncwarp();   // every lane is done with the previous item's staging
         if (it.x != curI) {
