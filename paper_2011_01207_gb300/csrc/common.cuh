@@ -258,7 +258,8 @@ int short_matvec_launch(ap_ctx *ctx, const void *p, double *out, cudaStream_t s)
 int real_forces_launch(ap_ctx *ctx, cudaStream_t s);
 int pme_init(ap_ctx *ctx);
 int pme_multipole_field(ap_ctx *ctx, cudaStream_t s);              // permanent: grid2 keeps phi_M
-int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s);  // T_rec p -> rec
+// T_rec p -> rec; grid_cleared: the caller has zeroed the context's grid (no clearing here)
+int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s, bool grid_cleared = false);
 int dipole_operator_into(ap_ctx *ctx, cudaStream_t main, cudaStream_t aux);   // T p, both branches
 // a set of PME work grids and cuFFT plans (the context owns one; others allow concurrent passes)
 struct PmeBufs {

@@ -401,11 +401,22 @@ __global__ void k_init_residual_f(const double *__restrict__ E, const float2 *__
     st->guard = 0;
 }
 
-// p = alpha r + beta p
+// p = alpha r + beta p; clears the real-space accumulator and the PME grid for the next product
+// (here rather than in k_apply_f, whose last-block fence would wait for these stores, or as a
+// separate clearing step at the head of the reciprocal branch, which is the longer branch of
+// the product)
 __global__ void k_direction_f(const float4 *__restrict__ r, const float2 *__restrict__ dga, int n_pad,
-                              float4 *__restrict__ p, const PcgState *__restrict__ st) {
+                              float4 *__restrict__ p, const PcgState *__restrict__ st, double *__restrict__ acc,
+                              float *__restrict__ grid, size_t ngrid) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    float4 *g4 = reinterpret_cast<float4 *>(grid);   // cudaMalloc'd: 16-byte aligned
+    for (size_t i = s; i < ngrid / 4; i += stride) g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s < (int)(ngrid & 3)) grid[(ngrid & ~(size_t)3) + s] = 0.f;
     if (s >= n_pad) return;
+    acc[s] = 0.0;
+    acc[n_pad + s] = 0.0;
+    acc[2 * (size_t)n_pad + s] = 0.0;
     const float b = (float)st->beta, a = dga[s].y;
     const float4 rv = r[s];
     float4 v = p[s];
@@ -415,9 +426,9 @@ __global__ void k_direction_f(const float4 *__restrict__ r, const float2 *__rest
     p[s] = v;
 }
 
-// q = (1/alpha - self) p - T_real p - T_rec p; partial p.q; clears acc. The last block sets
+// q = (1/alpha - self) p - T_real p - T_rec p; partial p.q. The last block sets
 // gamma = (r.z) / (p.q).
-__global__ void k_apply_f(const float4 *__restrict__ p, const float2 *__restrict__ dga, double *__restrict__ acc,
+__global__ void k_apply_f(const float4 *__restrict__ p, const float2 *__restrict__ dga, const double *__restrict__ acc,
                           const float *__restrict__ rec, int n_pad, float4 *__restrict__ q, double *__restrict__ part,
                           PcgState *st, int fixed) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -430,7 +441,6 @@ __global__ void k_apply_f(const float4 *__restrict__ p, const float2 *__restrict
         for (int c = 0; c < 3; ++c) {
             const int k = c * n_pad + s;
             qv[c] = fmaf(pv[c], d, -acc_f32(acc, k, fixed)) - rec[k];
-            acc[k] = 0.0;
             f2_add_prod(pq, pv[c], qv[c]);
         }
         q[s] = make_float4(qv[0], qv[1], qv[2], 0.f);
@@ -500,10 +510,10 @@ __global__ void k_unsort_f4(const float4 *__restrict__ src, const int *__restric
 
 // T p: reciprocal branch on `aux`, real space on `main`, joined back into `main`
 template <class T>
-int matvec_into(ap_ctx *ctx, const void *p, cudaStream_t main, cudaStream_t aux) {
+int matvec_into(ap_ctx *ctx, const void *p, cudaStream_t main, cudaStream_t aux, bool grid_cleared = false) {
     AP_CUDA(cudaEventRecord(ctx->ev_fork, main));
     AP_CUDA(cudaStreamWaitEvent(aux, ctx->ev_fork, 0));
-    int rc = pme_dipole_field(ctx, p, aux);
+    int rc = pme_dipole_field(ctx, p, aux, grid_cleared);
     if (rc) return rc;
     rc = real_matvec_launch(ctx, p, main);
     if (rc) return rc;
@@ -524,9 +534,10 @@ int enqueue_iteration(ap_ctx *ctx, cudaGraphConditionalHandle h, int use_cond, c
     const int nb = ap_grid_for(ctx->n_pad, NT);
     double *part_pq = ctx->red_part, *part_rz = ctx->red_part + nb;
     if constexpr (std::is_same<T, float>::value) {
-        k_direction_f<<<nb, NT, 0, main>>>(ctx->r_f, ctx->dga_f, ctx->n_pad, (float4 *)ctx->p, ctx->st);
+        k_direction_f<<<nb, NT, 0, main>>>(ctx->r_f, ctx->dga_f, ctx->n_pad, (float4 *)ctx->p, ctx->st, ctx->acc,
+                                           (float *)ctx->grid, ctx->ngrid);
         AP_CUDA(cudaGetLastError());
-        int rc = matvec_into<T>(ctx, ctx->p, main, aux);
+        int rc = matvec_into<T>(ctx, ctx->p, main, aux, true);   // the grid was cleared above
         if (rc) return rc;
         k_apply_f<<<nb, NT, 0, main>>>((const float4 *)ctx->p, ctx->dga_f, ctx->acc, (const float *)ctx->rec,
                                        ctx->n_pad, ctx->q_f, part_pq, ctx->st, ctx->fixed);
@@ -725,7 +736,8 @@ int pcg_vectors_launch(ap_ctx *ctx, cudaStream_t s) {
         k_update<double><<<nb, NT, 0, s>>>((const T4 *)ctx->p, ctx->qv, ctx->alpha, ctx->n_pad, ctx->mu, ctx->r, ctx->st,
                                            part_rz, ctx->n, 0, 0);
     } else {
-        k_direction_f<<<nb, NT, 0, s>>>(ctx->r_f, ctx->dga_f, ctx->n_pad, (float4 *)ctx->p, ctx->st);
+        k_direction_f<<<nb, NT, 0, s>>>(ctx->r_f, ctx->dga_f, ctx->n_pad, (float4 *)ctx->p, ctx->st, ctx->acc,
+                                        (float *)ctx->grid, ctx->ngrid);
         k_apply_f<<<nb, NT, 0, s>>>((const float4 *)ctx->p, ctx->dga_f, ctx->acc, (const float *)ctx->rec, ctx->n_pad,
                                     ctx->q_f, part_pq, ctx->st, ctx->fixed);
         k_update_f<<<nb, NT, 0, s>>>((const float4 *)ctx->p, ctx->q_f, ctx->dga_f, ctx->n_pad, ctx->mu_f, ctx->r_f,

@@ -497,12 +497,12 @@ int fft_roundtrip(ap_ctx *ctx, const PmeBufs &b, T *in, T *out, cudaStream_t s) 
 // multipoles (multi = true). Mixed/FP64 modes: FP32/T atomics on a cleared grid. AP_FIXED:
 // 64-bit fixed-point atomics on ctx->grid_fx (kept cleared), then converted into the grid.
 template <class T>
-int spread_t(ap_ctx *ctx, const PmeBufs &bf, const void *src, bool multi, cudaStream_t s) {
+int spread_t(ap_ctx *ctx, const PmeBufs &bf, const void *src, bool multi, cudaStream_t s, bool cleared = false) {
     typedef typename V4<T>::type T4;
     PmeConsts<T> pc = pme_consts<T>(ctx);
     const bool fx = ctx->fixed != 0;
     void *g = fx ? (void *)bf.grid_fx : bf.grid;
-    if (!fx) AP_CUDA(cudaMemsetAsync(bf.grid, 0, sizeof(T) * ctx->ngrid, s));
+    if (!fx && !cleared) AP_CUDA(cudaMemsetAsync(bf.grid, 0, sizeof(T) * ctx->ngrid, s));
     if (multi) {
         auto kern = fx ? k_spread_multipoles5<T, true> : k_spread_multipoles5<T, false>;
         kern<<<lane5_blocks(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->dipd,
@@ -534,10 +534,8 @@ int multipole_field_t(ap_ctx *ctx, cudaStream_t s) {
 }
 
 template <class T>
-int dipole_field_t(ap_ctx *ctx, const void *p, void *rec_out, const PmeBufs &bf, cudaStream_t s) {
-    typedef typename V4<T>::type T4;
-    PmeConsts<T> pc = pme_consts<T>(ctx);
-    int r = spread_t<T>(ctx, bf, p, false, s);
+int dipole_field_t(ap_ctx *ctx, const void *p, void *rec_out, const PmeBufs &bf, cudaStream_t s, bool cleared) {
+    int r = spread_t<T>(ctx, bf, p, false, s, cleared);
     if (r) return r;
     r = fft_roundtrip<T>(ctx, bf, (T *)bf.grid, (T *)bf.grid, s);
     if (r) return r;
@@ -705,16 +703,16 @@ int pme_multipole_field(ap_ctx *ctx, cudaStream_t s) {
     return ctx->prec == AP_FP64 ? multipole_field_t<double>(ctx, s) : multipole_field_t<float>(ctx, s);
 }
 
-int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s) {
+int pme_dipole_field(ap_ctx *ctx, const void *p, cudaStream_t s, bool grid_cleared) {
     const PmeBufs bf = own_bufs(ctx);
-    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, ctx->rec, bf, s)
-                                : dipole_field_t<float>(ctx, p, ctx->rec, bf, s);
+    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, ctx->rec, bf, s, grid_cleared)
+                                : dipole_field_t<float>(ctx, p, ctx->rec, bf, s, grid_cleared);
 }
 
 int pme_dipole_field_into(ap_ctx *ctx, const void *p, void *rec_out, const PmeBufs *bufs, cudaStream_t s) {
     const PmeBufs bf = bufs ? *bufs : own_bufs(ctx);
-    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, rec_out, bf, s)
-                                : dipole_field_t<float>(ctx, p, rec_out, bf, s);
+    return ctx->prec == AP_FP64 ? dipole_field_t<double>(ctx, p, rec_out, bf, s, false)
+                                : dipole_field_t<float>(ctx, p, rec_out, bf, s, false);
 }
 
 // a second set of grids and cuFFT plans of the context's sizes (for concurrent passes)
