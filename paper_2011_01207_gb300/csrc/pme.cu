@@ -197,11 +197,80 @@ __global__ void k_gather_field(const int4 *__restrict__ stb, const typename V4<T
     out[2 * n_pad + i] = -gz * pc.s[2];
 }
 
-// The spreads run five threads per atom (one per z-plane t3 of its stencil), a warp holding
-// six atoms in lanes 0-29, lanes 30 and 31 idle. One thread per atom left most of the GPU's
-// thread slots empty (96,000 threads for 311,296 slots) and kept too few reductions in flight
-// for the L2's atomic unit (dipole spread 42.8 -> 38.4 us per launch at 96,000 atoms). Each
-// thread forms the x and y stencils and its own plane's z weights, and covers that plane's 25
+// One thread per atom (the spreads of large systems, whose atoms alone fill the GPU's thread
+// slots): the whole 5 x 5 x 5 stencil, 25 rows of five points.
+template <class T, bool FX>
+__global__ void k_spread_multipoles(const typename V4<T>::type *__restrict__ posq,
+                                    const typename V4<T>::type *__restrict__ dipd,
+                                    const typename V4<T>::type *__restrict__ quad0,
+                                    const typename V4<T>::type *__restrict__ quad1, void *__restrict__ grid,
+                                    PmeConsts<T> pc, const int4 *__restrict__ stb,
+                                    const typename V4<T>::type *__restrict__ stw) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pc.n) return;
+    typename V4<T>::type a = posq[i], b = dipd[i], c = quad0[i], d = quad1[i];
+    Stencil<T> st;
+    make_stencil<T, 2>(pc, stb[i], stw[i], st);
+    const T sx = pc.s[0], sy = pc.s[1], sz = pc.s[2];
+    const T q = a.w, dx = b.x * sx, dy = b.y * sy, dz = b.z * sz;
+    const T third = T(1.0 / 3.0);
+    const T Qxx = c.x * sx * sx * third, Qyy = c.w * sy * sy * third, Qzz = d.y * sz * sz * third;
+    const T Qxy = c.y * sx * sy * T(2.0 / 3.0), Qxz = c.z * sx * sz * T(2.0 / 3.0), Qyz = d.x * sy * sz * T(2.0 / 3.0);
+    const int Kx = pc.K[0], Ky = pc.K[1];
+#pragma unroll
+    for (int t3 = 0; t3 < 5; ++t3) {
+        const T z0 = st.th[2][t3], z1 = st.d1[2][t3], z2 = st.d2[2][t3];
+#pragma unroll
+        for (int t2 = 0; t2 < 5; ++t2) {
+            const T y0 = st.th[1][t2], y1 = st.d1[1][t2], y2 = st.d2[1][t2];
+            const T A = q * y0 * z0 + dy * y1 * z0 + dz * y0 * z1 + Qyy * y2 * z0 + Qzz * y0 * z2 + Qyz * y1 * z1;
+            const T Bc = dx * y0 * z0 + Qxy * y1 * z0 + Qxz * y0 * z1;
+            const T Cc = Qxx * y0 * z0;
+            const size_t row = ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
+            T v[5];
+#pragma unroll
+            for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc + st.d2[0][t1] * Cc;
+            grid_row5<T, FX>(grid, row, st.k[0], v, Kx);
+        }
+    }
+}
+
+// spread induced dipoles p --------------------------------------------------------------
+template <class T, bool FX>
+__global__ void k_spread_dipoles(const int4 *__restrict__ stb, const typename V4<T>::type *__restrict__ stw,
+                                 const typename V4<T>::type *__restrict__ pv, void *__restrict__ grid,
+                                 PmeConsts<T> pc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pc.n) return;
+    typename V4<T>::type b = pv[i];
+    Stencil<T> st;
+    make_stencil<T, 1>(pc, stb[i], stw[i], st);
+    const T px = b.x * pc.s[0], py = b.y * pc.s[1], pz = b.z * pc.s[2];
+    const int Kx = pc.K[0], Ky = pc.K[1];
+#pragma unroll
+    for (int t3 = 0; t3 < 5; ++t3) {
+        const T z0 = st.th[2][t3], z1 = st.d1[2][t3];
+#pragma unroll
+        for (int t2 = 0; t2 < 5; ++t2) {
+            const T y0 = st.th[1][t2], y1 = st.d1[1][t2];
+            const T A = py * y1 * z0 + pz * y0 * z1;
+            const T Bc = px * y0 * z0;
+            const size_t row = ((size_t)st.k[2][t3] * Ky + st.k[1][t2]) * Kx;
+            T v[5];
+#pragma unroll
+            for (int t1 = 0; t1 < 5; ++t1) v[t1] = st.th[0][t1] * A + st.d1[0][t1] * Bc;
+            grid_row5<T, FX>(grid, row, st.k[0], v, Kx);
+        }
+    }
+}
+
+// Systems of up to two waves of five threads per atom spread with five threads per atom (one
+// per z-plane t3 of its stencil), a warp holding six atoms in lanes 0-29, lanes 30 and 31
+// idle. One thread per atom left most of the GPU's thread slots empty (96,000 threads for
+// 311,296 slots) and kept too few reductions in flight for the L2 (dipole spread 42.8 ->
+// 38.4 us per launch at 96,000 atoms); at 1,065,000 atoms the slots are full either way and
+// the five threads' repeated x and y stencils cost more (277 against 295 us). Each thread
+// forms the x and y stencils and its own plane's z weights, and covers that plane's 25
 // points.
 struct Lane5 {
     int t3;        // this thread's z-plane of the stencil
@@ -502,16 +571,30 @@ int spread_t(ap_ctx *ctx, const PmeBufs &bf, const void *src, bool multi, cudaSt
     PmeConsts<T> pc = pme_consts<T>(ctx);
     const bool fx = ctx->fixed != 0;
     void *g = fx ? (void *)bf.grid_fx : bf.grid;
+    // five threads per atom while they make at most two waves of the GPU's thread slots
+    const bool five = 5L * ctx->n <= 2L * 2048 * ctx->sm_count;
     if (!fx && !cleared) AP_CUDA(cudaMemsetAsync(bf.grid, 0, sizeof(T) * ctx->ngrid, s));
     if (multi) {
-        auto kern = fx ? k_spread_multipoles5<T, true> : k_spread_multipoles5<T, false>;
-        kern<<<lane5_blocks(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->dipd,
-                                                        (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, g, pc,
-                                                        ctx->stb, (const T4 *)ctx->stw);
+        if (five) {
+            auto kern = fx ? k_spread_multipoles5<T, true> : k_spread_multipoles5<T, false>;
+            kern<<<lane5_blocks(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->dipd,
+                                                            (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, g, pc,
+                                                            ctx->stb, (const T4 *)ctx->stw);
+        } else {
+            auto kern = fx ? k_spread_multipoles<T, true> : k_spread_multipoles<T, false>;
+            kern<<<ap_grid_for(ctx->n, 128), 128, 0, s>>>((const T4 *)ctx->posq, (const T4 *)ctx->dipd,
+                                                           (const T4 *)ctx->quad0, (const T4 *)ctx->quad1, g, pc,
+                                                           ctx->stb, (const T4 *)ctx->stw);
+        }
     } else {
         const int th = ctx->tune_pme_threads;
-        auto kern = fx ? k_spread_dipoles5<T, true> : k_spread_dipoles5<T, false>;
-        kern<<<lane5_blocks(ctx->n, th), th, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T4 *)src, g, pc);
+        if (five) {
+            auto kern = fx ? k_spread_dipoles5<T, true> : k_spread_dipoles5<T, false>;
+            kern<<<lane5_blocks(ctx->n, th), th, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T4 *)src, g, pc);
+        } else {
+            auto kern = fx ? k_spread_dipoles<T, true> : k_spread_dipoles<T, false>;
+            kern<<<ap_grid_for(ctx->n, th), th, 0, s>>>(ctx->stb, (const T4 *)ctx->stw, (const T4 *)src, g, pc);
+        }
     }
     AP_CUDA(cudaGetLastError());
     if (fx) {
