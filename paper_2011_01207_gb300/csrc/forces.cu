@@ -110,7 +110,10 @@ __device__ __forceinline__ void mu_dot_field_grad(T q, const T *d, const T *Q /*
 //   dU/dd_t / (-f)  += -R_1 mu_s + R_2 (mu_s.R) R
 //   dU/dQ_t / (-f/3) += R_2 sym(mu_s R) - R_3 (mu_s.R) R R
 // so the pair's force is evaluated once per side (twice per pair) in exchange for lanes
-// that only ever see in-range pairs.
+// that only ever see in-range pairs. In FP32 a lane takes two sides per step with their
+// radial terms in packed f32x2 arithmetic (fo_walk_x2): 255.9 -> 229.9 us at 96,000 atoms,
+// at 96 registers and 5 CTAs per SM (the same walk at 80 registers, 6 per SM, spilled more
+// and took 243.7 us).
 template <class T, class A>
 struct FoSmem {
     typename V4<T>::type pos[64];   // x, y, z, Thole factor: [0,32) block I, [32,64) the item's j atoms
@@ -126,6 +129,159 @@ struct FoSmem {
 template <class T>
 constexpr int fo_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
+// the target atom of a pair side: position and Thole factor, charge and dipole, quadrupole
+template <class T>
+struct FoTarget {
+    typename V4<T>::type pos, qd, qa, mu;
+    T qyz, qzz;
+};
+template <class T, class SM>
+__device__ __forceinline__ void fo_target(const SM &S, int t, FoTarget<T> &g) {
+    g.pos = S.pos[t];
+    g.qd = S.qd[t];
+    g.qa = S.qa[t];
+    g.mu = S.mu[t];
+    g.qyz = S.qb[0][t];
+    g.qzz = S.qb[1][t];
+}
+
+// one side's terms, given its R = x_target - x_source and its radial functions Rd (with the
+// pair's scale), Ru (unscaled): the force, dU/dd and dU/dQ of the target (unscaled sums), and
+// with VS the side's F R^T
+template <class T, bool VS, class SM>
+__device__ __forceinline__ void fo_side_terms(const SM &S, const FoTarget<T> &g, int src, T dx, T dy, T dz,
+                                              const T *Rd, const T *Ru, T *f, T *vs) {
+    typedef typename V4<T>::type T4;
+    const T4 om = S.qd[src], oa = S.qa[src], ou = S.mu[src];
+    const T oyz = S.qb[0][src], ozz = S.qb[1][src];
+    const T mt[3] = {g.mu.x, g.mu.y, g.mu.z}, ms[3] = {ou.x, ou.y, ou.z};
+    const T ds[3] = {om.y, om.z, om.w}, ndt[3] = {-g.qd.y, -g.qd.z, -g.qd.w};
+    const T Qs[6] = {oa.x, oa.y, oa.z, oa.w, oyz, ozz};
+    const T Qt[6] = {g.qa.x, g.qa.y, g.qa.z, g.qa.w, g.qyz, g.qzz};
+    T A[3], Bv[3];
+    mu_dot_field_grad<T>(om.x, ds, Qs, mt, dx, dy, dz, Rd[0], Rd[1], Rd[2], Rd[3], A);
+    mu_dot_field_grad<T>(g.qd.x, ndt, Qt, ms, dx, dy, dz, Rd[0], Rd[1], Rd[2], Rd[3], Bv);
+    const T mts = mt[0] * ms[0] + mt[1] * ms[1] + mt[2] * ms[2];
+    const T mtr = mt[0] * dx + mt[1] * dy + mt[2] * dz;
+    const T msr = ms[0] * dx + ms[1] * dy + ms[2] * dz;
+    const T cR = Ru[1] * mts - Ru[2] * mtr * msr;
+    const T R[3] = {dx, dy, dz};
+    T fs[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        fs[k] = A[k] - Bv[k] + cR * R[k] + Ru[1] * (mt[k] * msr + ms[k] * mtr);
+        f[k] += fs[k];
+        f[3 + k] += -Rd[0] * ms[k] + Rd[1] * msr * R[k];
+    }
+    if constexpr (VS) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) vs[3 * a + b] += fs[a] * R[b];
+    }
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        f[6 + k] += Rd[1] * (ms[ia[k]] * R[ib[k]] + R[ia[k]] * ms[ib[k]]) - Rd[2] * msr * R[ia[k]] * R[ib[k]];
+}
+
+// one side in full (scalar radial terms)
+template <class T, bool MINIMG, bool VS, class SM>
+__device__ __forceinline__ void fo_side(const SM &S, const PairConsts<T> &pc, const FoTarget<T> &g, int tg, int src,
+                                        T *f, T *vs) {
+    typedef typename V4<T>::type T4;
+    const int sl = src & 31;   // the source's lane within its half
+    const bool exb = tg < 32 ? (S.ex[tg] >> sl) & 1u : (S.ex[sl] >> (tg - 32)) & 1u;
+    const T4 o = S.pos[src];
+    T dx, dy, dz;
+    pair_vector<T, MINIMG>(pc, g.pos.x, g.pos.y, g.pos.z, o.x, o.y, o.z, T(0), T(0), T(0), dx, dy, dz);
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+    T B[4], U[4], oml[4];
+    screened<T, 4>(pc, r, rinv, rinv2, B, U);
+    thole_oml<T, 4>(pc.thole_a * r2 * r * g.pos.w * o.w, oml);
+    T Rd[4], Ru[3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Rd[k] = B[k] - (exb ? U[k] : oml[k] * U[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Ru[k] = B[k] - oml[k] * U[k];
+    fo_side_terms<T, VS>(S, g, src, dx, dy, dz, Rd, Ru, f, vs);
+}
+
+// The walk over a lane's share of the item's sides (plain stores on leaving a target, the last
+// target left in `cur` for the caller's atomic add)
+template <class T, bool MINIMG, bool VS, class PA, class SM>
+__device__ __forceinline__ void fo_walk(SM &S, SideSlice &slice, const PairConsts<T> &pc, const T *scf, int &cur,
+                                        T *f, T *vs) {
+    FoTarget<T> g;
+    while (slice.left > 0) {
+        int tg, src;
+        slice.next(S.words, tg, src);
+        if (tg != cur) {
+            if (cur >= 0) {   // the only lane that leaves this target: a plain store
+#pragma unroll
+                for (int k = 0; k < 12; ++k) PA::shared_put(&S.acc[k][cur], f[k] * scf[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 12; ++k) f[k] = T(0);
+            cur = tg;
+            fo_target<T>(S, tg, g);
+        }
+        fo_side<T, MINIMG, VS>(S, pc, g, tg, src, f, vs);
+    }
+}
+
+// FP32: two consecutive sides per step, their radial terms in packed f32x2 arithmetic
+// (radial_forces_x2), the multipole terms per side; an odd last side takes the scalar path
+template <bool MINIMG, bool VS, class PA, class SM>
+__device__ __forceinline__ void fo_walk_x2(SM &S, SideSlice &slice, const PairConsts<float> &pc,
+                                           const PairConsts2 &k, const float *scf, int &cur, float *f, float *vs) {
+    FoTarget<float> g;
+    auto enter = [&](int t) {
+        if (cur >= 0) {   // the only lane that leaves this target: a plain store
+#pragma unroll
+            for (int q = 0; q < 12; ++q) PA::shared_put(&S.acc[q][cur], f[q] * scf[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q) f[q] = 0.f;
+        cur = t;
+        fo_target<float>(S, t, g);
+    };
+    while (slice.left > 1) {
+        int ta, sa, tb, sb;
+        slice.next(S.words, ta, sa);
+        slice.next(S.words, tb, sb);
+        if (ta != cur) enter(ta);
+        const float4 pb = tb == ta ? g.pos : S.pos[tb];
+        const int la = sa & 31, lb = sb & 31;
+        const bool exa = ta < 32 ? (S.ex[ta] >> la) & 1u : (S.ex[la] >> (ta - 32)) & 1u;
+        const bool exb = tb < 32 ? (S.ex[tb] >> lb) & 1u : (S.ex[lb] >> (tb - 32)) & 1u;
+        const float4 oa = S.pos[sa], ob = S.pos[sb];
+        float dxa, dya, dza, dxb, dyb, dzb;
+        pair_vector<float, MINIMG>(pc, g.pos.x, g.pos.y, g.pos.z, oa.x, oa.y, oa.z, 0.f, 0.f, 0.f, dxa, dya, dza);
+        pair_vector<float, MINIMG>(pc, pb.x, pb.y, pb.z, ob.x, ob.y, ob.z, 0.f, 0.f, 0.f, dxb, dyb, dzb);
+        const float2 dx = make_float2(dxa, dxb), dy = make_float2(dya, dyb), dz = make_float2(dza, dzb);
+        const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+        float2 Rd2[4], Ru2[3];
+        radial_forces_x2(k, r2, make_float2(g.pos.w * oa.w, pb.w * ob.w), exa, exb, Rd2, Ru2);
+        {
+            const float Rd[4] = {Rd2[0].x, Rd2[1].x, Rd2[2].x, Rd2[3].x}, Ru[3] = {Ru2[0].x, Ru2[1].x, Ru2[2].x};
+            fo_side_terms<float, VS>(S, g, sa, dxa, dya, dza, Rd, Ru, f, vs);
+        }
+        if (tb != cur) enter(tb);
+        {
+            const float Rd[4] = {Rd2[0].y, Rd2[1].y, Rd2[2].y, Rd2[3].y}, Ru[3] = {Ru2[0].y, Ru2[1].y, Ru2[2].y};
+            fo_side_terms<float, VS>(S, g, sb, dxb, dyb, dzb, Rd, Ru, f, vs);
+        }
+    }
+    if (slice.left > 0) {
+        int tg, src;
+        slice.next(S.words, tg, src);
+        if (tg != cur) enter(tg);
+        fo_side<float, MINIMG, VS>(S, pc, g, tg, src, f, vs);
+    }
+}
+
 // VIR: also the pairs' virial. Without per-pair minimum image every position of an item is
 // relative to block I's origin, and the item holds both sides of each of its pairs, whose
 // forces are opposite; so the item's sum over pairs of (dU/dR) R^T = -sum over sides of
@@ -133,7 +289,7 @@ constexpr int fo_warps() { return sizeof(T) == 4 ? 4 : 2; }
 // per-target sums the kernel keeps anyway. With per-pair minimum image (small boxes) the
 // sides' F R^T are summed as they come.
 template <class T, bool MINIMG, bool FX, bool VIR>
-__global__ void __launch_bounds__(128, VIR ? 4 : 6) k_pair_forces(
+__global__ void __launch_bounds__(128, VIR ? 4 : 5) k_pair_forces(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq,
     const typename V4<T>::type *__restrict__ dipd, const typename V4<T>::type *__restrict__ quad0,
     const typename V4<T>::type *__restrict__ quad1, const typename V4<T>::type *__restrict__ muv,
@@ -144,6 +300,8 @@ __global__ void __launch_bounds__(128, VIR ? 4 : 6) k_pair_forces(
     __shared__ FoSmem<T, typename PA::shared_t> smem[fo_warps<T>()];
     FoSmem<T, typename PA::shared_t> &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
+    PairConsts2 k2;
+    if constexpr (std::is_same<T, float>::value) k2 = make_consts2(pc);
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
     long t0, t1;
@@ -231,84 +389,16 @@ __global__ void __launch_bounds__(128, VIR ? 4 : 6) k_pair_forces(
         slice.load(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], wa.pstart[(size_t)t * 32 + lane],
                  lane, S.words);
         int cur = -1;
-        T4 self, sm, sa, smu;
-        T syz = 0, szz = 0;
-        self.x = self.y = self.z = self.w = T(0);
-        sm = sa = smu = self;
         T f[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) f[k] = T(0);
         T vs[9];                    // sum of F_side R^T over this lane's sides (VIR, MINIMG)
 #pragma unroll
         for (int k = 0; k < 9; ++k) vs[k] = T(0);
-        while (slice.left > 0) {
-            int tg, src;
-            slice.next(S.words, tg, src);
-            const int sl = src & 31;   // the source's lane within its half
-            if (tg != cur) {
-                if (cur >= 0) {   // the only lane that leaves this target: a plain store
-#pragma unroll
-                    for (int k = 0; k < 12; ++k) PA::shared_put(&S.acc[k][cur], f[k] * scf[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < 12; ++k) f[k] = T(0);
-                cur = tg;
-                self = S.pos[tg];
-                sm = S.qd[tg];
-                sa = S.qa[tg];
-                smu = S.mu[tg];
-                syz = S.qb[0][tg];
-                szz = S.qb[1][tg];
-            }
-            const bool exb = tg < 32 ? (S.ex[tg] >> sl) & 1u : (S.ex[sl] >> (tg - 32)) & 1u;
-            const T4 o = S.pos[src], om = S.qd[src], oa = S.qa[src], ou = S.mu[src];
-            const T oyz = S.qb[0][src], ozz = S.qb[1][src];
-            T dx = self.x - o.x, dy = self.y - o.y, dz = self.z - o.z;
-            if (MINIMG) {
-                dx -= pc.L[0] * ap_rint(dx * pc.iL[0]);
-                dy -= pc.L[1] * ap_rint(dy * pc.iL[1]);
-                dz -= pc.L[2] * ap_rint(dz * pc.iL[2]);
-            }
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
-            T B[4], U[4], oml[4];
-            screened<T, 4>(pc, r, rinv, rinv2, B, U);
-            thole_oml<T, 4>(pc.thole_a * r2 * r * self.w * o.w, oml);
-            T Rd[4], Ru[3];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) Rd[k] = B[k] - (exb ? U[k] : oml[k] * U[k]);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) Ru[k] = B[k] - oml[k] * U[k];
-            const T mt[3] = {smu.x, smu.y, smu.z}, ms[3] = {ou.x, ou.y, ou.z};
-            const T ds[3] = {om.y, om.z, om.w}, ndt[3] = {-sm.y, -sm.z, -sm.w};
-            const T Qs[6] = {oa.x, oa.y, oa.z, oa.w, oyz, ozz};
-            const T Qt[6] = {sa.x, sa.y, sa.z, sa.w, syz, szz};
-            T A[3], Bv[3];
-            mu_dot_field_grad<T>(om.x, ds, Qs, mt, dx, dy, dz, Rd[0], Rd[1], Rd[2], Rd[3], A);
-            mu_dot_field_grad<T>(sm.x, ndt, Qt, ms, dx, dy, dz, Rd[0], Rd[1], Rd[2], Rd[3], Bv);
-            const T mts = mt[0] * ms[0] + mt[1] * ms[1] + mt[2] * ms[2];
-            const T mtr = mt[0] * dx + mt[1] * dy + mt[2] * dz;
-            const T msr = ms[0] * dx + ms[1] * dy + ms[2] * dz;
-            const T cR = Ru[1] * mts - Ru[2] * mtr * msr;
-            const T R[3] = {dx, dy, dz};
-            T fs[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                fs[k] = A[k] - Bv[k] + cR * R[k] + Ru[1] * (mt[k] * msr + ms[k] * mtr);
-                f[k] += fs[k];
-                f[3 + k] += -Rd[0] * ms[k] + Rd[1] * msr * R[k];
-            }
-            if constexpr (VIR && MINIMG) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) vs[3 * a + b] += fs[a] * R[b];
-            }
-            const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-            for (int k = 0; k < 6; ++k)
-                f[6 + k] += Rd[1] * (ms[ia[k]] * R[ib[k]] + R[ia[k]] * ms[ib[k]]) - Rd[2] * msr * R[ia[k]] * R[ib[k]];
-        }
+        if constexpr (std::is_same<T, float>::value)
+            fo_walk_x2<MINIMG, VIR && MINIMG, PA>(S, slice, pc, k2, scf, cur, f, vs);
+        else
+            fo_walk<T, MINIMG, VIR && MINIMG, PA>(S, slice, pc, scf, cur, f, vs);
         __syncwarp();   // the plain stores land before the last targets are added
         if (cur >= 0) {
 #pragma unroll

@@ -29,6 +29,24 @@ struct PairConsts {
     int n;             // real atoms; slots >= n are padding
 };
 
+// pair vector R = x_i - x_j: minimum image per pair (MINIMG), or plus a fixed image shift
+template <class T, bool MINIMG>
+__device__ __forceinline__ void pair_vector(const PairConsts<T> &pc, T xi, T yi, T zi, T xj, T yj, T zj,
+                                            T sx, T sy, T sz, T &dx, T &dy, T &dz) {
+    dx = xi - xj;
+    dy = yi - yj;
+    dz = zi - zj;
+    if (MINIMG) {
+        dx -= pc.L[0] * ap_rint(dx * pc.iL[0]);
+        dy -= pc.L[1] * ap_rint(dy * pc.iL[1]);
+        dz -= pc.L[2] * ap_rint(dz * pc.iL[2]);
+    } else {
+        dx += sx;
+        dy += sy;
+        dz += sz;
+    }
+}
+
 // erfc(x) given e2 = exp(-x^2), x >= 0. FP32: the rational approximation of Abramowitz &
 // Stegun, Handbook of Mathematical Functions (1964), formula 7.1.26,
 //   erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-x^2},  t = 1 / (1 + p x),
@@ -81,7 +99,7 @@ __device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a
 struct PairConsts2 {
     float2 ce;        // -beta^2 log2(e): e^{-beta^2 r^2} = 2^{ce r^2}
     float2 pb;        // A&S 7.1.26's p times beta: t = 1 / (1 + pb r)
-    float2 c1, c2, c3;   // (2 beta^2)^n / (beta sqrt(pi)), n = 1, 2, 3
+    float2 c1, c2, c3, c4;   // (2 beta^2)^n / (beta sqrt(pi)), n = 1..4
     float2 ta;        // Thole a
     float2 nl2e;      // -log2(e)
 };
@@ -93,6 +111,7 @@ __host__ __device__ inline PairConsts2 make_consts2(const PairConsts<float> &pc)
     k.c1 = make_float2(pc.c[1], pc.c[1]);
     k.c2 = make_float2(pc.c[2], pc.c[2]);
     k.c3 = make_float2(pc.c[3], pc.c[3]);
+    k.c4 = make_float2(pc.c[4], pc.c[4]);
     k.ta = make_float2(pc.thole_a, pc.thole_a);
     k.nl2e = make_float2(-l2e, -l2e);
     return k;
@@ -178,6 +197,46 @@ __device__ __forceinline__ void radial123_x2(const PairConsts2 &k, float2 r2, fl
     R1 = sub2(b1, mul2(o1, u1));
     R2 = sub2(b2, mul2(o2, u2));
     R3 = sub2(b3, mul2(o3, u3));
+}
+
+// The force kernel's radial terms for two pair sides at once: Rd_n = B_n - (1 - sigma
+// lambda_(2n+1)) U_n for n = 1..4 with each side's exclusion scale (exa, exb: sigma = 0),
+// and Ru_n = B_n - (1 - lambda_(2n+1)) U_n for n = 1..3 (sigma = 1); the terms of
+// screened<float, 4> and thole_oml<float, 4>
+__device__ __forceinline__ void radial_forces_x2(const PairConsts2 &k, float2 r2, float2 ww, bool exa, bool exb,
+                                                 float2 *Rd, float2 *Ru) {
+    const float2 rinv = rsqrt2(r2);
+    const float2 r = mul2(r2, rinv), rinv2 = mul2(rinv, rinv);
+    const float2 e2 = ex2_2(mul2(r2, k.ce));
+    const float2 t = rcp2(fma2(k.pb, r, splat2(1.0f)));
+    const float2 poly = mul2(t, fma2(t, fma2(t, fma2(t, fma2(t, splat2(1.061405429f), splat2(-1.453152027f)),
+                                                      splat2(1.421413741f)),
+                                             splat2(-0.284496736f)),
+                                     splat2(0.254829592f)));
+    const float2 b0 = mul2(mul2(poly, e2), rinv);
+    float2 b[4], u[4];
+    b[0] = mul2(fma2(k.c1, e2, b0), rinv2);
+    u[0] = mul2(rinv, rinv2);
+    b[1] = mul2(fma2(splat2(3.0f), b[0], mul2(k.c2, e2)), rinv2);
+    u[1] = mul2(mul2(splat2(3.0f), u[0]), rinv2);
+    b[2] = mul2(fma2(splat2(5.0f), b[1], mul2(k.c3, e2)), rinv2);
+    u[2] = mul2(mul2(splat2(5.0f), u[1]), rinv2);
+    b[3] = mul2(fma2(splat2(7.0f), b[2], mul2(k.c4, e2)), rinv2);
+    u[3] = mul2(mul2(splat2(7.0f), u[2]), rinv2);
+    const float2 s = mul2(mul2(r2, r), mul2(ww, k.ta));
+    const float2 e = ex2_2(mul2(s, k.nl2e));
+    const float2 s1 = add2(splat2(1.0f), s), ss = mul2(s, s);
+    float2 o[4];
+    o[0] = e;
+    o[1] = mul2(s1, e);
+    o[2] = mul2(fma2(splat2(0.6f), ss, s1), e);
+    o[3] = mul2(fma2(ss, fma2(splat2(9.0f / 35.0f), s, splat2(18.0f / 35.0f)), s1), e);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        const float2 ru = sub2(b[n], mul2(o[n], u[n])), rx = sub2(b[n], u[n]);
+        if (n < 3) Ru[n] = ru;
+        Rd[n] = make_float2(exa ? rx.x : ru.x, exb ? rx.y : ru.y);
+    }
 }
 
 // First index i in [lo, hi] with start[i] >= a, for a nondecreasing start[] with

@@ -21,23 +21,6 @@
 
 namespace {
 
-template <class T, bool MINIMG>
-__device__ __forceinline__ void pair_vector(const PairConsts<T> &pc, T xi, T yi, T zi, T xj, T yj, T zj,
-                                            T sx, T sy, T sz, T &dx, T &dy, T &dz) {
-    dx = xi - xj;
-    dy = yi - yj;
-    dz = zi - zj;
-    if (MINIMG) {
-        dx -= pc.L[0] * ap_rint(dx * pc.iL[0]);
-        dy -= pc.L[1] * ap_rint(dy * pc.iL[1]);
-        dz -= pc.L[2] * ap_rint(dz * pc.iL[2]);
-    } else {
-        dx += sx;
-        dy += sy;
-        dz += sz;
-    }
-}
-
 // running sums of block I's atom `slot` (three components) to the global accumulators
 template <class PA>
 __device__ __forceinline__ void flush3(double *acc, int n_pad, int slot, const typename PA::run_t &a,
