@@ -569,6 +569,136 @@ struct Mv2Smem {
     unsigned words[64];
 };
 
+// one side's contribution to both sets' fields at its target, given R and (R1, R2)
+template <class T>
+__device__ __forceinline__ void mv2_terms(T dx, T dy, T dz, T R1, T R2, const typename V4<T>::type &po,
+                                          const typename V4<T>::type &pq, T *g) {
+    const T pr0 = (po.x * dx + po.y * dy + po.z * dz) * R2;
+    const T pr1 = (pq.x * dx + pq.y * dy + pq.z * dz) * R2;
+    g[0] = pr0 * dx - R1 * po.x;
+    g[1] = pr0 * dy - R1 * po.y;
+    g[2] = pr0 * dz - R1 * po.z;
+    g[3] = pr1 * dx - R1 * pq.x;
+    g[4] = pr1 * dy - R1 * pq.y;
+    g[5] = pr1 * dz - R1 * pq.z;
+}
+
+// the two-set walk (ownership as in matvec_walk)
+template <class T, bool MINIMG, class PA, class SM>
+__device__ __forceinline__ void matvec2_walk(SM &S, SideSlice &sl, const PairConsts<T> &pc) {
+    typedef typename V4<T>::type T4;
+    int cur = -1;
+    T4 self;
+    self.x = self.y = self.z = self.w = T(0);
+    T f[6] = {0, 0, 0, 0, 0, 0};
+    while (sl.left > 0) {
+        int tg, src;
+        sl.next(S.words, tg, src);
+        if (tg != cur) {
+            if (cur >= 0) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) PA::shared_put(&S.acc[c][cur], f[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) f[c] = T(0);
+            cur = tg;
+            self = S.pos[tg];
+        }
+        const T4 other = S.pos[src];
+        T dx, dy, dz;
+        pair_vector<T, MINIMG>(pc, self.x, self.y, self.z, other.x, other.y, other.z, T(0), T(0), T(0), dx, dy, dz);
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+        T B[2], U[2], oml[2];
+        screened<T, 2>(pc, r, rinv, rinv2, B, U);
+        thole_oml<T, 2>(pc.thole_a * r2 * r * self.w * other.w, oml);
+        T g[6];
+        mv2_terms<T>(dx, dy, dz, B[0] - oml[0] * U[0], B[1] - oml[1] * U[1], S.p[0][src], S.p[1][src], g);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) f[c] += g[c];
+    }
+    __syncwarp();   // the plain stores land before the last targets are added
+    if (cur >= 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) PA::shared_add(&S.acc[c][cur], f[c]);
+    }
+}
+
+// FP32: two consecutive sides per step, (R1, R2) of both in packed f32x2 arithmetic
+template <bool MINIMG, class PA, class SM>
+__device__ __forceinline__ void matvec2_walk_x2(SM &S, SideSlice &sl, const PairConsts<float> &pc,
+                                                const PairConsts2 &k) {
+    int cur = -1;
+    float4 self = make_float4(0.f, 0.f, 0.f, 0.f);
+    float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto leave = [&](int next, const float4 &nself) {
+        if (cur >= 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) PA::shared_put(&S.acc[c][cur], f[c]);
+        }
+        cur = next;
+        self = nself;
+    };
+    while (sl.left > 1) {
+        int ta, sa, tb, sb;
+        sl.next(S.words, ta, sa);
+        sl.next(S.words, tb, sb);
+        if (ta != cur) {
+            leave(ta, S.pos[ta]);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) f[c] = 0.f;
+        }
+        const float4 selfb = tb == ta ? self : S.pos[tb];
+        const float4 oa = S.pos[sa], ob = S.pos[sb];
+        float dxa, dya, dza, dxb, dyb, dzb;
+        pair_vector<float, MINIMG>(pc, self.x, self.y, self.z, oa.x, oa.y, oa.z, 0.f, 0.f, 0.f, dxa, dya, dza);
+        pair_vector<float, MINIMG>(pc, selfb.x, selfb.y, selfb.z, ob.x, ob.y, ob.z, 0.f, 0.f, 0.f, dxb, dyb, dzb);
+        const float2 dx = make_float2(dxa, dxb), dy = make_float2(dya, dyb), dz = make_float2(dza, dzb);
+        const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+        float2 R1, R2;
+        radial12_x2(k, r2, make_float2(self.w * oa.w, selfb.w * ob.w), R1, R2);
+        float g[6];
+        mv2_terms<float>(dxa, dya, dza, R1.x, R2.x, S.p[0][sa], S.p[1][sa], g);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) f[c] += g[c];
+        mv2_terms<float>(dxb, dyb, dzb, R1.y, R2.y, S.p[0][sb], S.p[1][sb], g);
+        if (tb == cur) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) f[c] += g[c];
+        } else {
+            leave(tb, selfb);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) f[c] = g[c];
+        }
+    }
+    if (sl.left > 0) {
+        int tg, src;
+        sl.next(S.words, tg, src);
+        if (tg != cur) {
+            leave(tg, S.pos[tg]);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) f[c] = 0.f;
+        }
+        const float4 other = S.pos[src];
+        float dx, dy, dz;
+        pair_vector<float, MINIMG>(pc, self.x, self.y, self.z, other.x, other.y, other.z, 0.f, 0.f, 0.f, dx, dy, dz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+        float B[2], U[2], oml[2];
+        screened<float, 2>(pc, r, rinv, rinv2, B, U);
+        thole_oml<float, 2>(pc.thole_a * r2 * r * self.w * other.w, oml);
+        float g[6];
+        mv2_terms<float>(dx, dy, dz, B[0] - oml[0] * U[0], B[1] - oml[1] * U[1], S.p[0][src], S.p[1][src], g);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) f[c] += g[c];
+    }
+    __syncwarp();   // the plain stores land before the last targets are added
+    if (cur >= 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) PA::shared_add(&S.acc[c][cur], f[c]);
+    }
+}
+
 template <class T, bool MINIMG, bool FX>
 __global__ void __launch_bounds__(128) k_matvec2(
     WorkArgs wa, const typename V4<T>::type *__restrict__ posq, const typename V4<T>::type *__restrict__ dipd,
@@ -579,6 +709,8 @@ __global__ void __launch_bounds__(128) k_matvec2(
     __shared__ Mv2Smem<T, typename PA::shared_t> smem[4];
     Mv2Smem<T, typename PA::shared_t> &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
+    PairConsts2 k2;
+    if constexpr (std::is_same<T, float>::value) k2 = make_consts2(pc);
     const long gw = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nw = ((long)gridDim.x * blockDim.x) >> 5;
     long t0, t1;
@@ -629,48 +761,8 @@ __global__ void __launch_bounds__(128) k_matvec2(
         SideSlice sl;
         sl.load(wa.pmask[(size_t)t * 32 + lane], wa.pmask_t[(size_t)t * 32 + lane], wa.pstart[(size_t)t * 32 + lane],
                  lane, S.words);
-        // as in k_matvec: plain stores on leaving a target, atomics for the last one
-        int cur = -1;
-        T4 self;
-        self.x = self.y = self.z = self.w = T(0);
-        T f[6] = {0, 0, 0, 0, 0, 0};
-        while (sl.left > 0) {
-            int tg, src;
-            sl.next(S.words, tg, src);
-            if (tg != cur) {
-                if (cur >= 0) {
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) PA::shared_put(&S.acc[c][cur], f[c]);
-                }
-#pragma unroll
-                for (int c = 0; c < 6; ++c) f[c] = T(0);
-                cur = tg;
-                self = S.pos[tg];
-            }
-            const T4 other = S.pos[src], po = S.p[0][src], pq = S.p[1][src];
-            T dx, dy, dz;
-            pair_vector<T, MINIMG>(pc, self.x, self.y, self.z, other.x, other.y, other.z, T(0), T(0), T(0), dx, dy, dz);
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            const T rinv = ap_rsqrt(r2), r = r2 * rinv, rinv2 = rinv * rinv;
-            T B[2], U[2], oml[2];
-            screened<T, 2>(pc, r, rinv, rinv2, B, U);
-            thole_oml<T, 2>(pc.thole_a * r2 * r * self.w * other.w, oml);
-            const T R1 = B[0] - oml[0] * U[0];
-            const T R2 = B[1] - oml[1] * U[1];
-            const T pr0 = (po.x * dx + po.y * dy + po.z * dz) * R2;
-            const T pr1 = (pq.x * dx + pq.y * dy + pq.z * dz) * R2;
-            f[0] += pr0 * dx - R1 * po.x;
-            f[1] += pr0 * dy - R1 * po.y;
-            f[2] += pr0 * dz - R1 * po.z;
-            f[3] += pr1 * dx - R1 * pq.x;
-            f[4] += pr1 * dy - R1 * pq.y;
-            f[5] += pr1 * dz - R1 * pq.z;
-        }
-        __syncwarp();   // the plain stores land before the last targets are added
-        if (cur >= 0) {
-#pragma unroll
-            for (int c = 0; c < 6; ++c) PA::shared_add(&S.acc[c][cur], f[c]);
-        }
+        if constexpr (std::is_same<T, float>::value) matvec2_walk_x2<MINIMG, PA>(S, sl, pc, k2);
+        else matvec2_walk<T, MINIMG, PA>(S, sl, pc);
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < 6; ++c) PA::run_add(a[c], S.acc[c][lane]);
