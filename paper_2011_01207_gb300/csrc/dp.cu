@@ -25,6 +25,7 @@
 // gradient of -(f/2) sum_listed (sigma_d mu_p,I + sigma_p mu_d,I) . F_lambda including its
 // multipole-orientation (frame) terms.
 #include "common.cuh"
+#include "vec_f32.cuh"
 
 #include <type_traits>
 
@@ -47,7 +48,8 @@ struct DpBuffers {
     double2 *scales = nullptr;    // (sigma_d, sigma_p)
     double *E2 = nullptr;         // [2][3][n_pad] E_d, E_p (slot order)
     double *corr = nullptr;       // [2][3][n_pad] listed-pair field terms (FP64 or fixed point)
-    double *mu2 = nullptr, *r2 = nullptr, *q2 = nullptr;   // [2][3][n_pad]
+    double *mu2 = nullptr, *r2 = nullptr, *q2 = nullptr;   // [2][3][n_pad] (FP64 mode)
+    float4 *mu2f = nullptr, *r2f = nullptr, *q2f = nullptr;  // [2][n_pad] (mixed and fixed modes)
     void *p2 = nullptr;           // T4 [2][n_pad] search directions
     double *acc2 = nullptr;       // [3][n_pad] real-space accumulator of the second set
     void *rec2 = nullptr;         // T [3][n_pad] reciprocal field of the second set
@@ -261,6 +263,58 @@ __global__ void k_dp_fields(const double *__restrict__ E, double *__restrict__ c
 }
 
 // ---- lockstep PCG on the two systems -----------------------------------------------------
+// the initial state from the totals r.z and z.z of both systems (thread 0 of the last block)
+__device__ void dp_init_state(DpState *st, const double *tot, int n, double tol, int max_iter) {
+    st->tol = tol;
+    st->iter = 0;
+    st->max_iter = max_iter;
+    st->guard = 0;
+    st->status = AP_OK;
+    st->nonfinite = 0;
+    for (int k = 0; k < 2; ++k) {
+        st->rz[k] = tot[2 * k];
+        st->eps[k] = st->eps0[k] = AP_DEBYE * sqrt(tot[2 * k + 1] / n);
+        st->beta[k] = st->gamma[k] = st->pq[k] = 0.0;
+        if (!isfinite(st->eps[k])) st->nonfinite = 1;
+    }
+    st->done = (fmax(st->eps[0], st->eps[1]) <= tol) || st->nonfinite;
+    if (st->nonfinite) st->status = AP_ERR_NONFINITE;
+}
+
+// gamma_k from the totals p_k.q_k
+__device__ void dp_set_gamma(DpState *st, const double *tot) {
+    for (int k = 0; k < 2; ++k) {
+        st->pq[k] = tot[k];
+        // a recurrence that has converged exactly (r.z = 0) stays where it is
+        st->gamma[k] = (st->rz[k] != 0.0) ? st->rz[k] / tot[k] : 0.0;
+    }
+}
+
+// closes an iteration from the totals r.z and z.z: eps_k, the stop decision on the larger
+// one, beta_k, and the WHILE condition (never beyond max_iter iterations)
+__device__ void dp_close_iteration(DpState *st, const double *tot, int n, cudaGraphConditionalHandle h,
+                                   int use_cond) {
+    st->iter += 1;
+    st->guard += 1;
+    bool bad = false;
+    for (int k = 0; k < 2; ++k) {
+        st->eps[k] = AP_DEBYE * sqrt(tot[2 * k + 1] / n);
+        bad = bad || !isfinite(st->eps[k]) || !isfinite(st->gamma[k]);
+        st->beta[k] = (st->rz[k] != 0.0) ? tot[2 * k] / st->rz[k] : 0.0;
+        st->rz[k] = tot[2 * k];
+    }
+    if (bad) st->nonfinite = 1;
+    if (fmax(st->eps[0], st->eps[1]) <= st->tol || bad) {
+        st->done = 1;
+        st->status = bad ? AP_ERR_NONFINITE : AP_OK;
+    } else if (st->iter >= st->max_iter) {
+        st->done = 1;
+        st->status = AP_NOT_CONVERGED;
+    }
+    if (use_cond) cudaGraphSetConditional(h, (!st->done && st->guard < st->max_iter) ? 1u : 0u);
+}
+
+
 template <class T>
 __global__ void k_dp_guess(const double *__restrict__ gd, const double *__restrict__ gp,
                            const double *__restrict__ E2, const double *__restrict__ alpha,
@@ -326,21 +380,7 @@ __global__ void k_dp_init_residual(const double *__restrict__ E2, const double *
     if (!last_block(&st->blocks_done)) return;
     double tot[4];
     sum_parts<4>(part, gridDim.x, tot);
-    if (threadIdx.x != 0) return;
-    st->tol = tol;
-    st->iter = 0;
-    st->max_iter = max_iter;
-    st->guard = 0;
-    st->status = AP_OK;
-    st->nonfinite = 0;
-    for (int k = 0; k < 2; ++k) {
-        st->rz[k] = tot[2 * k];
-        st->eps[k] = st->eps0[k] = AP_DEBYE * sqrt(tot[2 * k + 1] / n);
-        st->beta[k] = st->gamma[k] = st->pq[k] = 0.0;
-        if (!isfinite(st->eps[k])) st->nonfinite = 1;
-    }
-    st->done = (fmax(st->eps[0], st->eps[1]) <= tol) || st->nonfinite;
-    if (st->nonfinite) st->status = AP_ERR_NONFINITE;
+    if (threadIdx.x == 0) dp_init_state(st, tot, n, tol, max_iter);
 }
 
 __global__ void k_dp_set_cond(cudaGraphConditionalHandle h, const DpState *st) {
@@ -394,12 +434,7 @@ __global__ void k_dp_apply(const typename V4<T>::type *__restrict__ p2, const do
     if (!last_block(&st->blocks_done)) return;
     double tot[2];
     sum_parts<2>(part, gridDim.x, tot);
-    if (threadIdx.x != 0) return;
-    for (int k = 0; k < 2; ++k) {
-        st->pq[k] = tot[k];
-        // a recurrence that has converged exactly (r.z = 0) stays where it is
-        st->gamma[k] = (st->rz[k] != 0.0) ? st->rz[k] / tot[k] : 0.0;
-    }
+    if (threadIdx.x == 0) dp_set_gamma(st, tot);
 }
 
 // mu_k += gamma_k p_k; r_k -= gamma_k q_k; partial r.z and z.z; the last block closes the
@@ -435,25 +470,181 @@ __global__ void k_dp_update(const typename V4<T>::type *__restrict__ p2, const d
     if (!last_block(&st->blocks_done2)) return;
     double tot[4];
     sum_parts<4>(part, gridDim.x, tot);
-    if (threadIdx.x != 0) return;
-    st->iter += 1;
-    st->guard += 1;
-    bool bad = false;
+    if (threadIdx.x == 0) dp_close_iteration(st, tot, n, h, use_cond);
+}
+
+// ---- the same lockstep iteration with FP32 vectors (mixed and fixed-point modes): mu, r, q
+// and p of both systems as float4 per slot, the diagonal and alpha as a float2; dot products
+// and norms as compensated FP32 sums finished in FP64 (vec_f32.cuh), as the single-set PCG
+
+__global__ void k_dp_guess_f(const double *__restrict__ gd, const double *__restrict__ gp,
+                             const double *__restrict__ E2, const double *__restrict__ alpha,
+                             const int *__restrict__ perm, int n, int n_pad, float4 *__restrict__ mu2,
+                             float4 *__restrict__ p2, double self_coef, float2 *__restrict__ dga) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    const double al = alpha[s];
+    dga[s] = make_float2(al > 0.0 ? (float)(1.0 / al - self_coef) : 0.f, (float)al);
     for (int k = 0; k < 2; ++k) {
-        st->eps[k] = AP_DEBYE * sqrt(tot[2 * k + 1] / n);
-        bad = bad || !isfinite(st->eps[k]) || !isfinite(st->gamma[k]);
-        st->beta[k] = (st->rz[k] != 0.0) ? tot[2 * k] / st->rz[k] : 0.0;
-        st->rz[k] = tot[2 * k];
+        const double *g = k ? gp : gd;
+        float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (s < n) {
+            if (g) {
+                const int i = perm[s];
+                m = make_float4((float)g[3 * i], (float)g[3 * i + 1], (float)g[3 * i + 2], 0.f);
+            } else {
+                const double *e = E2 + (size_t)k * 3 * n_pad;
+                m = make_float4((float)(al * e[s]), (float)(al * e[n_pad + s]), (float)(al * e[2 * (size_t)n_pad + s]),
+                                0.f);
+            }
+        }
+        mu2[(size_t)k * n_pad + s] = m;
+        p2[(size_t)k * n_pad + s] = m;
     }
-    if (bad) st->nonfinite = 1;
-    if (fmax(st->eps[0], st->eps[1]) <= st->tol || bad) {
-        st->done = 1;
-        st->status = bad ? AP_ERR_NONFINITE : AP_OK;
-    } else if (st->iter >= st->max_iter) {
-        st->done = 1;
-        st->status = AP_NOT_CONVERGED;
+}
+
+// the compensated sums a[0..3] of the block, partials part[k][block]
+__device__ __forceinline__ void dp_block_parts4(const F2 *a, double *part) {
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    block_sum2_f2<NT>(a[0], a[1], t[0], t[1]);
+    __syncthreads();
+    block_sum2_f2<NT>(a[2], a[3], t[2], t[3]);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) part[k * gridDim.x + blockIdx.x] = t[k];
+}
+
+// r_k = E_k - A mu_k (formed in FP64 once per solve, stored in FP32); clears the accumulators
+// and the directions; partial r.z and z.z of both systems. The last block sets the state.
+__global__ void k_dp_init_residual_f(const double *__restrict__ E2, const float2 *__restrict__ dga,
+                                     const float4 *__restrict__ mu2, DpVecs v, int n_pad, int n,
+                                     float4 *__restrict__ r2, float4 *__restrict__ p2, double *__restrict__ part,
+                                     DpState *st, double tol, int max_iter, int fixed) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    F2 red[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    if (s < n_pad) {
+        const float2 d = dga[s];
+        for (int k = 0; k < 2; ++k) {
+            const float *rec = (const float *)v.rec[k];
+            const float4 m = mu2[(size_t)k * n_pad + s];
+            const float mv[3] = {m.x, m.y, m.z};
+            float rv[3];
+            for (int c = 0; c < 3; ++c) {
+                const size_t i = (size_t)k * 3 * n_pad + (size_t)c * n_pad + s, j = (size_t)c * n_pad + s;
+                const double Amu = d.y > 0.f ? (double)mv[c] * d.x - acc_value(v.acc[k], j, fixed) - (double)rec[j] : 0.0;
+                rv[c] = d.y > 0.f ? (float)(E2[i] - Amu) : 0.f;
+                v.acc[k][j] = 0.0;
+                const float z = d.y * rv[c];
+                f2_add_prod(red[2 * k], rv[c], z);
+                f2_add_prod(red[2 * k + 1], z, z);
+            }
+            r2[(size_t)k * n_pad + s] = make_float4(rv[0], rv[1], rv[2], 0.f);
+            p2[(size_t)k * n_pad + s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
-    if (use_cond) cudaGraphSetConditional(h, (!st->done && st->guard < st->max_iter) ? 1u : 0u);
+    dp_block_parts4(red, part);
+    if (!last_block(&st->blocks_done)) return;
+    double tot[4];
+    sum_parts<4>(part, gridDim.x, tot);
+    if (threadIdx.x == 0) dp_init_state(st, tot, n, tol, max_iter);
+}
+
+// p_k = alpha r_k + beta_k p_k
+__global__ void k_dp_direction_f(const float4 *__restrict__ r2, const float2 *__restrict__ dga, int n_pad,
+                                 float4 *__restrict__ p2, const DpState *__restrict__ st) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    const float a = dga[s].y;
+    for (int k = 0; k < 2; ++k) {
+        const float b = (float)st->beta[k];
+        const float4 r = r2[(size_t)k * n_pad + s];
+        float4 p = p2[(size_t)k * n_pad + s];
+        p.x = fmaf(a, r.x, b * p.x);
+        p.y = fmaf(a, r.y, b * p.y);
+        p.z = fmaf(a, r.z, b * p.z);
+        p2[(size_t)k * n_pad + s] = p;
+    }
+}
+
+// q_k = A p_k; partial p_k.q_k; clears the accumulators. The last block sets gamma_k.
+__global__ void k_dp_apply_f(const float4 *__restrict__ p2, const float2 *__restrict__ dga, DpVecs v, int n_pad,
+                             float4 *__restrict__ q2, double *__restrict__ part, DpState *st, int fixed) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    F2 red[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    if (s < n_pad) {
+        const float d = dga[s].x;
+        for (int k = 0; k < 2; ++k) {
+            const float *rec = (const float *)v.rec[k];
+            const float4 pv = p2[(size_t)k * n_pad + s];
+            const float pp[3] = {pv.x, pv.y, pv.z};
+            float qq[3];
+            for (int c = 0; c < 3; ++c) {
+                const size_t j = (size_t)c * n_pad + s;
+                qq[c] = fmaf(pp[c], d, -acc_f32(v.acc[k], j, fixed)) - rec[j];
+                v.acc[k][j] = 0.0;
+                f2_add_prod(red[k], pp[c], qq[c]);
+            }
+            q2[(size_t)k * n_pad + s] = make_float4(qq[0], qq[1], qq[2], 0.f);
+        }
+    }
+    double t0 = 0.0, t1 = 0.0;
+    block_sum2_f2<NT>(red[0], red[1], t0, t1);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t0;
+        part[gridDim.x + blockIdx.x] = t1;
+    }
+    if (!last_block(&st->blocks_done)) return;
+    double tot[2];
+    sum_parts<2>(part, gridDim.x, tot);
+    if (threadIdx.x == 0) dp_set_gamma(st, tot);
+}
+
+// mu_k += gamma_k p_k; r_k -= gamma_k q_k; partial r.z and z.z; the last block closes the
+// iteration
+__global__ void k_dp_update_f(const float4 *__restrict__ p2, const float4 *__restrict__ q2,
+                              const float2 *__restrict__ dga, int n_pad, float4 *__restrict__ mu2,
+                              float4 *__restrict__ r2, DpState *st, double *__restrict__ part, int n,
+                              cudaGraphConditionalHandle h, int use_cond) {
+    const float g[2] = {(float)st->gamma[0], (float)st->gamma[1]};
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    F2 red[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    if (s < n_pad) {
+        const float a = dga[s].y;
+        for (int k = 0; k < 2; ++k) {
+            const size_t i = (size_t)k * n_pad + s;
+            const float4 pv = p2[i], qv = q2[i];
+            float4 m = mu2[i], rv = r2[i];
+            m.x = fmaf(g[k], pv.x, m.x);
+            m.y = fmaf(g[k], pv.y, m.y);
+            m.z = fmaf(g[k], pv.z, m.z);
+            rv.x = fmaf(-g[k], qv.x, rv.x);
+            rv.y = fmaf(-g[k], qv.y, rv.y);
+            rv.z = fmaf(-g[k], qv.z, rv.z);
+            mu2[i] = m;
+            r2[i] = rv;
+            const float rr[3] = {rv.x, rv.y, rv.z};
+            for (int c = 0; c < 3; ++c) {
+                const float z = a * rr[c];
+                f2_add_prod(red[2 * k], rr[c], z);
+                f2_add_prod(red[2 * k + 1], z, z);
+            }
+        }
+    }
+    dp_block_parts4(red, part);
+    if (!last_block(&st->blocks_done2)) return;
+    double tot[4];
+    sum_parts<4>(part, gridDim.x, tot);
+    if (threadIdx.x == 0) dp_close_iteration(st, tot, n, h, use_cond);
+}
+
+// FP32 dipoles of one system to the caller's order in FP64
+__global__ void k_dp_unsort_f4(const float4 *__restrict__ src, const int *__restrict__ iperm, int n,
+                               double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 v = src[iperm[i]];
+    out[3 * i] = v.x;
+    out[3 * i + 1] = v.y;
+    out[3 * i + 2] = v.z;
 }
 
 double self_coef_of(const ap_ctx *ctx) { return 4.0 * std::pow(ctx->prm.ewald_beta, 3) / (3.0 * AP_SQRT_PI); }
@@ -496,14 +687,25 @@ int enqueue_iteration(ap_ctx *ctx, cudaGraphConditionalHandle h, int use_cond, c
     typedef typename V4<T>::type T4;
     DpBuffers *B = dpb(ctx);
     const int nb = ap_grid_for(ctx->n_pad, NT);
-    k_dp_direction<T><<<nb, NT, 0, main>>>(B->r2, ctx->alpha, ctx->n_pad, (T4 *)B->p2, B->st);
-    AP_CUDA(cudaGetLastError());
-    int rc = matvec2<T>(ctx, main, aux);
-    if (rc) return rc;
-    k_dp_apply<T><<<nb, NT, 0, main>>>((const T4 *)B->p2, ctx->dg, vecs_of(ctx), ctx->n_pad, B->q2, B->part, B->st,
-                                        ctx->fixed);
-    k_dp_update<T><<<nb, NT, 0, main>>>((const T4 *)B->p2, B->q2, ctx->alpha, ctx->n_pad, B->mu2, B->r2, B->st,
-                                         B->part, ctx->n, h, use_cond);
+    if constexpr (std::is_same<T, float>::value) {
+        k_dp_direction_f<<<nb, NT, 0, main>>>(B->r2f, ctx->dga_f, ctx->n_pad, (float4 *)B->p2, B->st);
+        AP_CUDA(cudaGetLastError());
+        int rc = matvec2<T>(ctx, main, aux);
+        if (rc) return rc;
+        k_dp_apply_f<<<nb, NT, 0, main>>>((const float4 *)B->p2, ctx->dga_f, vecs_of(ctx), ctx->n_pad, B->q2f,
+                                          B->part, B->st, ctx->fixed);
+        k_dp_update_f<<<nb, NT, 0, main>>>((const float4 *)B->p2, B->q2f, ctx->dga_f, ctx->n_pad, B->mu2f, B->r2f,
+                                           B->st, B->part, ctx->n, h, use_cond);
+    } else {
+        k_dp_direction<T><<<nb, NT, 0, main>>>(B->r2, ctx->alpha, ctx->n_pad, (T4 *)B->p2, B->st);
+        AP_CUDA(cudaGetLastError());
+        int rc = matvec2<T>(ctx, main, aux);
+        if (rc) return rc;
+        k_dp_apply<T><<<nb, NT, 0, main>>>((const T4 *)B->p2, ctx->dg, vecs_of(ctx), ctx->n_pad, B->q2, B->part,
+                                            B->st, ctx->fixed);
+        k_dp_update<T><<<nb, NT, 0, main>>>((const T4 *)B->p2, B->q2, ctx->alpha, ctx->n_pad, B->mu2, B->r2, B->st,
+                                             B->part, ctx->n, h, use_cond);
+    }
     AP_CUDA(cudaGetLastError());
     return AP_OK;
 }
@@ -576,13 +778,22 @@ int solve_t(ap_ctx *ctx, const double *gd, const double *gp, double tol, int max
     AP_CUDA(cudaMemsetAsync(B->st, 0, sizeof(DpState), s));
     AP_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 3 * ctx->n_pad, s));
     AP_CUDA(cudaMemsetAsync(B->acc2, 0, sizeof(double) * 3 * ctx->n_pad, s));
-    k_dp_guess<T><<<nb, NT, 0, s>>>(gd, gp, B->E2, ctx->alpha, ctx->perm, ctx->n, ctx->n_pad, B->mu2, (T4 *)B->p2,
-                                     self_coef_of(ctx), ctx->dg);
+    constexpr bool F32 = std::is_same<T, float>::value;   // FP32 vectors (mixed and fixed modes)
+    if (F32)
+        k_dp_guess_f<<<nb, NT, 0, s>>>(gd, gp, B->E2, ctx->alpha, ctx->perm, ctx->n, ctx->n_pad, B->mu2f,
+                                       (float4 *)B->p2, self_coef_of(ctx), ctx->dga_f);
+    else
+        k_dp_guess<T><<<nb, NT, 0, s>>>(gd, gp, B->E2, ctx->alpha, ctx->perm, ctx->n, ctx->n_pad, B->mu2, (T4 *)B->p2,
+                                         self_coef_of(ctx), ctx->dg);
     AP_CUDA(cudaGetLastError());
     int rc = matvec2<T>(ctx, s, ctx->s1);
     if (rc) return rc;
-    k_dp_init_residual<T><<<nb, NT, 0, s>>>(B->E2, ctx->alpha, B->mu2, vecs_of(ctx), ctx->dg, ctx->n_pad, ctx->n,
-                                             B->r2, (T4 *)B->p2, B->part, B->st, tol, max_iter, ctx->fixed);
+    if (F32)
+        k_dp_init_residual_f<<<nb, NT, 0, s>>>(B->E2, ctx->dga_f, B->mu2f, vecs_of(ctx), ctx->n_pad, ctx->n, B->r2f,
+                                               (float4 *)B->p2, B->part, B->st, tol, max_iter, ctx->fixed);
+    else
+        k_dp_init_residual<T><<<nb, NT, 0, s>>>(B->E2, ctx->alpha, B->mu2, vecs_of(ctx), ctx->dg, ctx->n_pad, ctx->n,
+                                                 B->r2, (T4 *)B->p2, B->part, B->st, tol, max_iter, ctx->fixed);
     AP_CUDA(cudaGetLastError());
     if (!B->exec_tried) {
         rc = build_graph<T>(ctx);
@@ -599,8 +810,13 @@ int solve_t(ap_ctx *ctx, const double *gd, const double *gp, double tol, int max
             if (rc) return rc;
         }
     }
-    unsort3(ctx, B->mu2, d_mu_d, s);
-    unsort3(ctx, B->mu2 + (size_t)3 * ctx->n_pad, d_mu_p, s);
+    if (F32) {
+        k_dp_unsort_f4<<<ap_grid_for(ctx->n, 256), 256, 0, s>>>(B->mu2f, ctx->iperm, ctx->n, d_mu_d);
+        k_dp_unsort_f4<<<ap_grid_for(ctx->n, 256), 256, 0, s>>>(B->mu2f + ctx->n_pad, ctx->iperm, ctx->n, d_mu_p);
+    } else {
+        unsort3(ctx, B->mu2, d_mu_d, s);
+        unsort3(ctx, B->mu2 + (size_t)3 * ctx->n_pad, d_mu_p, s);
+    }
     AP_CUDA(cudaGetLastError());
     if (info) {
         AP_CUDA(cudaMemcpyAsync(B->st_host, B->st, sizeof(DpState), cudaMemcpyDeviceToHost, s));
@@ -865,6 +1081,9 @@ int reserve_all(ap_ctx *ctx) {
     if ((r = dmalloc(ctx, &B->mu2, sizeof(double) * 6 * np))) return r;
     if ((r = dmalloc(ctx, &B->r2, sizeof(double) * 6 * np))) return r;
     if ((r = dmalloc(ctx, &B->q2, sizeof(double) * 6 * np))) return r;
+    if ((r = dmalloc(ctx, &B->mu2f, sizeof(float4) * 2 * np))) return r;
+    if ((r = dmalloc(ctx, &B->r2f, sizeof(float4) * 2 * np))) return r;
+    if ((r = dmalloc(ctx, &B->q2f, sizeof(float4) * 2 * np))) return r;
     if ((r = dmalloc(ctx, (char **)&B->p2, 4 * tsz * 2 * np))) return r;
     if ((r = dmalloc(ctx, &B->acc2, sizeof(double) * 3 * np))) return r;
     if ((r = dmalloc(ctx, (char **)&B->rec2, tsz * 3 * np))) return r;
@@ -1010,7 +1229,7 @@ void dp_release_impl(ap_ctx *ctx) {
     if (!B) return;
     if (B->exec) cudaGraphExecDestroy(B->exec);
     void *ptrs[] = {B->pairs, B->scales, B->E2, B->corr, B->mu2, B->r2, B->q2, B->p2, B->acc2, B->rec2, B->part,
-                    B->st, B->mus, B->cbuf, B->e_scr, B->flag, B->mz, B->gsc};
+                    B->st, B->mus, B->cbuf, B->e_scr, B->flag, B->mz, B->gsc, B->mu2f, B->r2f, B->q2f};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (B->st_host) cudaFreeHost(B->st_host);

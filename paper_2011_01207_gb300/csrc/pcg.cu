@@ -16,7 +16,7 @@
 // launch with no host round trip per iteration (the paper's host-synchronous loop is what
 // made DHFR drop to 12 ns/day, Sec. 3).
 #include "common.cuh"
-#include "pair_math.cuh"
+#include "vec_f32.cuh"
 
 #include <cmath>
 #include <cstdlib>
@@ -274,58 +274,6 @@ __global__ void k_update(const typename V4<T>::type *__restrict__ p, const doubl
 // converted exactly to FP64 and the last block adds the partials in FP64 in a fixed order.
 // (GB300 issues FP64 at a small fraction of its FP32 rate; the FP64 kernels above spent a
 // few microseconds per iteration on it.)
-
-// a += x y, the product carried exactly as its rounded value and rounding error
-__device__ __forceinline__ void f2_add_prod(F2 &a, float x, float y) {
-    const float p = x * y;
-    f2_add(a, p);
-    a.lo += fmaf(x, y, -p);
-}
-
-// block-wide sums of two compensated pairs; thread 0 gets them in FP64
-template <int NT_>
-__device__ __forceinline__ void block_sum2_f2(F2 a, F2 b, double &da, double &db) {
-    __shared__ float sh[4][NT_ / 32];
-    for (int off = 16; off; off >>= 1) {
-        const float ah = __shfl_xor_sync(0xffffffffu, a.hi, off), al = __shfl_xor_sync(0xffffffffu, a.lo, off);
-        const float bh = __shfl_xor_sync(0xffffffffu, b.hi, off), bl = __shfl_xor_sync(0xffffffffu, b.lo, off);
-        f2_add(a, ah);
-        a.lo += al;
-        f2_add(b, bh);
-        b.lo += bl;
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        sh[0][w] = a.hi;
-        sh[1][w] = a.lo;
-        sh[2][w] = b.hi;
-        sh[3][w] = b.lo;
-    }
-    __syncthreads();
-    if (w == 0) {
-        F2 x, y;
-        x.hi = l < NT_ / 32 ? sh[0][l] : 0.f;
-        x.lo = l < NT_ / 32 ? sh[1][l] : 0.f;
-        y.hi = l < NT_ / 32 ? sh[2][l] : 0.f;
-        y.lo = l < NT_ / 32 ? sh[3][l] : 0.f;
-        for (int off = 16; off; off >>= 1) {
-            const float xh = __shfl_xor_sync(0xffffffffu, x.hi, off), xl = __shfl_xor_sync(0xffffffffu, x.lo, off);
-            const float yh = __shfl_xor_sync(0xffffffffu, y.hi, off), yl = __shfl_xor_sync(0xffffffffu, y.lo, off);
-            f2_add(x, xh);
-            x.lo += xl;
-            f2_add(y, yh);
-            y.lo += yl;
-        }
-        da = f2d_exact(x.hi) + f2d_exact(x.lo);
-        db = f2d_exact(y.hi) + f2d_exact(y.lo);
-    }
-}
-
-// an accumulator slot of the real-space product in FP32 (FP64 or, fixed, 2^-34 fixed point:
-// the integer's conversion and an exact power-of-two scale round once, as the FP64 path)
-__device__ __forceinline__ float acc_f32(const double *acc, size_t k, int fixed) {
-    return fixed ? (float)reinterpret_cast<const long long *>(acc)[k] * (1.0f / 17179869184.0f) : (float)acc[k];
-}
 
 // mu_0 (FP32) and the matvec input p := mu_0; the diagonal 1/alpha - self and alpha as FP32
 __global__ void k_init_guess_f(const double *__restrict__ guess, const double *__restrict__ E,
